@@ -1,0 +1,630 @@
+/*
+ * FP64 CPU oracle of one generation of tensorized RVEA (arXiv 2404.01159).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, __graft_entry__.smoke() and the
+ * CPU-baseline legs of bench.py.  The CUDA library never includes or loads it.
+ *
+ * This file is deliberately plain: every step is the paper's formula written
+ * out in double precision, in the paper's order, with no blocking or fusion.
+ * Loops over independent rows carry an OpenMP pragma; no reduction crosses
+ * threads, so results do not depend on the thread count.
+ *
+ * Parity pins (tests/test_oracle_*.py) check this file against closed forms,
+ * invariants, known-answer vectors and brute force; see the header of each
+ * function for what it follows.
+ */
+#include "rvea_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;
+
+void orc_set_threads(int32_t n) { g_threads = n < 1 ? 1 : n; }
+int32_t orc_get_threads(void) { return g_threads; }
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, Salmon et al. SC'11, Sec. 3-4: ten rounds of the S-box     */
+/* (two 32x32->64 multiplies by 0xD2511F53 and 0xCD9E8D57, XOR with the      */
+/* other counter words and the round key), key bumped by the Weyl constants  */
+/* 0x9E3779B9 / 0xBB67AE85 between rounds.                                   */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void philox(const orc_params *p, uint32_t c0, uint32_t c1, uint32_t c2,
+                   uint32_t c3, uint32_t out[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* A uniform on [0,1) with 24 random bits: exact in float and double. */
+static double u24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* Box-Muller (Box & Muller 1958): N(0,1) from two uniforms, u1 in (0,1]. */
+static double box_muller(uint32_t w0, uint32_t w1)
+{
+    double u1 = 1.0 - u24(w0);
+    double u2 = u24(w1);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* Event of probability q fires iff R < q, for R = k * 2^-24:
+ * k < ceil(q * 2^24).  q = 0 never fires, q >= 1 always fires. */
+static uint32_t event_threshold(double q)
+{
+    double x = ceil(q * 16777216.0);
+    if (x < 0.0) x = 0.0;
+    if (x > 16777216.0) x = 16777216.0;
+    return (uint32_t)x;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reference vectors.  The paper takes unit vectors V0 as input (Algorithm 2 */
+/* and Sec. 3.1) without fixing their construction; the reading used is the  */
+/* Das-Dennis simplex lattice {k / H : k_i >= 0, sum k_i = H} of the original */
+/* RVEA, listed in lexicographic order of (k_1..k_{m-1}), then normalised.   */
+/* ------------------------------------------------------------------------ */
+int64_t orc_lattice_count(int32_t m, int32_t H)
+{
+    /* C(H + m - 1, m - 1) */
+    int64_t c = 1;
+    for (int32_t i = 1; i <= m - 1; ++i)
+        c = c * (int64_t)(H + i) / i;
+    return c;
+}
+
+static int32_t lattice_rec(int32_t m, int32_t pos, int32_t left, int32_t *cur,
+                           int32_t *K, int32_t N, int32_t row)
+{
+    if (pos == m - 1) {
+        if (row >= N) return row + 1;
+        cur[pos] = left;
+        for (int32_t k = 0; k < m; ++k) K[(int64_t)row * m + k] = cur[k];
+        return row + 1;
+    }
+    for (int32_t k = 0; k <= left; ++k) {
+        cur[pos] = k;
+        row = lattice_rec(m, pos + 1, left - k, cur, K, N, row);
+    }
+    return row;
+}
+
+int32_t orc_lattice(int32_t m, int32_t H, int32_t N, int32_t *K)
+{
+    if (m < 1 || H < 0 || orc_lattice_count(m, H) != N) return -1;
+    int32_t *cur = (int32_t *)calloc((size_t)m, sizeof(int32_t));
+    int32_t rows = lattice_rec(m, 0, H, cur, K, N, 0);
+    free(cur);
+    return rows;
+}
+
+void orc_lattice_unit(int32_t m, int32_t N, const int32_t *K, double *V0)
+{
+    for (int32_t j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (int32_t k = 0; k < m; ++k) {
+            double v = (double)K[(int64_t)j * m + k];
+            s += v * v;
+        }
+        double nrm = sqrt(s);
+        for (int32_t k = 0; k < m; ++k)
+            V0[(int64_t)j * m + k] = (double)K[(int64_t)j * m + k] / nrm;
+    }
+}
+
+static double dot(const double *a, const double *b, int32_t m)
+{
+    double s = 0.0;
+    for (int32_t k = 0; k < m; ++k) s += a[k] * b[k];
+    return s;
+}
+
+static double clamp1(double c)
+{
+    if (c > 1.0) return 1.0;
+    if (c < -1.0) return -1.0;
+    return c;
+}
+
+/* Eq. 5 and Algorithm 1 (Gamma line): gamma_j = min over i != j of the angle
+ * between v_i and v_j.  The printed Gamma line takes a row minimum over the
+ * full arccos matrix, whose diagonal is zero; Eq. 5 excludes i = j, which is
+ * the reading used.  Clamped below at 1e-12 so the APD division is finite. */
+void orc_gamma(int32_t m, int32_t r, const double *V, double *gamma)
+{
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int32_t j = 0; j < r; ++j) {
+        const double *vj = V + (int64_t)j * m;
+        double nj = sqrt(dot(vj, vj, m));
+        double best = INFINITY;
+        for (int32_t i = 0; i < r; ++i) {
+            if (i == j) continue;
+            const double *vi = V + (int64_t)i * m;
+            double ni = sqrt(dot(vi, vi, m));
+            double a = acos(clamp1(dot(vi, vj, m) / (ni * nj)));
+            if (a < best) best = a;
+        }
+        if (!(best >= 1e-12)) best = 1e-12;
+        gamma[j] = best;
+    }
+}
+
+/* Objective range of the current population, used by the adaptation. */
+void orc_objective_range(int32_t m, int32_t n, const double *F, const uint8_t *valid,
+                         double *range)
+{
+    for (int32_t k = 0; k < m; ++k) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int32_t i = 0; i < n; ++i) {
+            if (valid && !valid[i]) continue;
+            double f = F[(int64_t)i * m + k];
+            if (f < lo) lo = f;
+            if (f > hi) hi = f;
+        }
+        range[k] = (hi >= lo) ? hi - lo : 0.0;
+    }
+}
+
+/* Algorithm 2 ("update reference vectors ... from V_t and V0"): the formula is
+ * not printed; the reading is the original RVEA adaptation, V_j = V0_j (.)
+ * range / ||V0_j (.) range||, with each range component floored at 1e-12. */
+void orc_adapt(int32_t m, int32_t r, const double *V0, const double *range, double *V)
+{
+    for (int32_t j = 0; j < r; ++j) {
+        double s = 0.0;
+        for (int32_t k = 0; k < m; ++k) {
+            double rk = range[k] < 1e-12 ? 1e-12 : range[k];
+            double v = V0[(int64_t)j * m + k] * rk;
+            s += v * v;
+        }
+        double nrm = sqrt(s);
+        for (int32_t k = 0; k < m; ++k) {
+            double rk = range[k] < 1e-12 ? 1e-12 : range[k];
+            V[(int64_t)j * m + k] = V0[(int64_t)j * m + k] * rk / nrm;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initialisation (Algorithm 2, "initialize population P0 with n randomized  */
+/* individuals").  DTLZ: uniform on [L,U]; neuroevolution: N(0, 0.1^2)      */
+/* weights clipped to [L,U].                                                 */
+/* ------------------------------------------------------------------------ */
+void orc_init_population(const orc_params *p, double *X)
+{
+    const int32_t N = p->N, d = p->d;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int32_t i = 0; i < N; ++i) {
+        for (int32_t j = 0; j < d; ++j) {
+            uint32_t w[4];
+            double x;
+            if (p->problem == ORC_NEURO) {
+                philox(p, (uint32_t)j, (uint32_t)i, 0u, ORC_TAG_INIT, w);
+                x = 0.1 * box_muller(w[0], w[1]);
+                if (x < p->L) x = p->L;
+                if (x > p->U) x = p->U;
+            } else {
+                philox(p, (uint32_t)(j / 4), (uint32_t)i, 0u, ORC_TAG_INIT, w);
+                x = p->L + (p->U - p->L) * u24(w[j % 4]);
+            }
+            X[(int64_t)i * d + j] = x;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Objectives.  The paper names DTLZ1/DTLZ2 (Sec. 4.1, Appendix C) without   */
+/* printing them; the formulas are the standard DTLZ definitions with        */
+/* 1-based x, g over x_m..x_d, k = d - m + 1.                                */
+/* ------------------------------------------------------------------------ */
+static void dtlz2(int32_t m, int32_t d, const double *x, double *f)
+{
+    double g = 0.0;
+    for (int32_t j = m - 1; j < d; ++j) g += (x[j] - 0.5) * (x[j] - 0.5);
+    for (int32_t k = 1; k <= m; ++k) {
+        /* f_k = (1+g) prod_{i < m-k+1} cos(x_i pi/2) [* sin(x_{m-k+1} pi/2) if k>1] */
+        double v = 1.0 + g;
+        for (int32_t i = 1; i <= m - k; ++i) v *= cos(x[i - 1] * M_PI / 2.0);
+        if (k > 1) v *= sin(x[m - k] * M_PI / 2.0);
+        f[k - 1] = v;
+    }
+}
+
+static void dtlz1(int32_t m, int32_t d, const double *x, double *f)
+{
+    int32_t kk = d - m + 1;
+    double s = 0.0;
+    for (int32_t j = m - 1; j < d; ++j) {
+        double y = x[j] - 0.5;
+        s += y * y - cos(20.0 * M_PI * y);
+    }
+    double g = 100.0 * ((double)kk + s);
+    for (int32_t k = 1; k <= m; ++k) {
+        double v = 0.5 * (1.0 + g);
+        for (int32_t i = 1; i <= m - k; ++i) v *= x[i - 1];
+        if (k > 1) v *= 1.0 - x[m - k];
+        f[k - 1] = v;
+    }
+}
+
+/* Process noise of the synthetic rollout: xi[s][k] ~ N(0,1), one draw per
+ * step s and state component k, shared by every policy of generation t
+ * (common random numbers). */
+void orc_neuro_noise(const orc_params *p, const orc_neuro *nd, int32_t t, double *xi)
+{
+    for (int32_t s = 0; s < nd->steps; ++s)
+        for (int32_t k = 0; k < nd->ns; ++k) {
+            uint32_t w[4];
+            philox(p, (uint32_t)k, (uint32_t)s, (uint32_t)t, ORC_TAG_NOISE, w);
+            xi[(int64_t)s * nd->ns + k] = box_muller(w[0], w[1]);
+        }
+}
+
+/* Neuroevolution objective (the linear-dynamics stand-in for the paper's
+ * Brax tasks, Sec. 4.3): policy x = [W1 (h1 x ns), b1, W2 (h2 x h1), b2,
+ * W3 (na x h2), b3], tanh on every layer, s_0 = 0,
+ * s_{tau+1} = A s_tau + B u_tau + sigma xi_tau;
+ * f1 = -sum_tau s_{tau+1}[0], f2 = sum_tau ||u_tau||^2. */
+static void neuro_rollout(const orc_neuro *nd, const double *x, const double *xi,
+                          double *f)
+{
+    const int32_t ns = nd->ns, na = nd->na, h1 = nd->h1, h2 = nd->h2;
+    const double *W1 = x, *b1 = W1 + (int64_t)h1 * ns;
+    const double *W2 = b1 + h1, *b2 = W2 + (int64_t)h2 * h1;
+    const double *W3 = b2 + h2, *b3 = W3 + (int64_t)na * h2;
+    double s[64], sn[64], a1[256], a2[256], u[64];
+    for (int32_t k = 0; k < ns; ++k) s[k] = 0.0;
+    double f1 = 0.0, f2 = 0.0;
+    for (int32_t tau = 0; tau < nd->steps; ++tau) {
+        for (int32_t o = 0; o < h1; ++o) {
+            double z = b1[o];
+            for (int32_t i = 0; i < ns; ++i) z += W1[(int64_t)o * ns + i] * s[i];
+            a1[o] = tanh(z);
+        }
+        for (int32_t o = 0; o < h2; ++o) {
+            double z = b2[o];
+            for (int32_t i = 0; i < h1; ++i) z += W2[(int64_t)o * h1 + i] * a1[i];
+            a2[o] = tanh(z);
+        }
+        for (int32_t o = 0; o < na; ++o) {
+            double z = b3[o];
+            for (int32_t i = 0; i < h2; ++i) z += W3[(int64_t)o * h2 + i] * a2[i];
+            u[o] = tanh(z);
+        }
+        for (int32_t k = 0; k < ns; ++k) {
+            double z = 0.0;
+            for (int32_t i = 0; i < ns; ++i) z += nd->A[(int64_t)k * ns + i] * s[i];
+            for (int32_t i = 0; i < na; ++i) z += nd->B[(int64_t)k * na + i] * u[i];
+            sn[k] = z + nd->sigma * xi[(int64_t)tau * ns + k];
+        }
+        for (int32_t k = 0; k < ns; ++k) s[k] = sn[k];
+        f1 -= s[0];
+        for (int32_t o = 0; o < na; ++o) f2 += u[o] * u[o];
+    }
+    f[0] = f1;
+    f[1] = f2;
+}
+
+void orc_evaluate(const orc_params *p, int32_t n, const double *X, double *F,
+                  const orc_neuro *nd, int32_t t)
+{
+    const int32_t m = p->m, d = p->d;
+    double *xi = NULL;
+    if (p->problem == ORC_NEURO) {
+        xi = (double *)malloc(sizeof(double) * (size_t)nd->steps * (size_t)nd->ns);
+        orc_neuro_noise(p, nd, t, xi);
+    }
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1)
+    for (int32_t i = 0; i < n; ++i) {
+        const double *x = X + (int64_t)i * d;
+        double *f = F + (int64_t)i * m;
+        if (p->problem == ORC_DTLZ2) dtlz2(m, d, x, f);
+        else if (p->problem == ORC_DTLZ1) dtlz1(m, d, x, f);
+        else neuro_rollout(nd, x, xi, f);
+    }
+    free(xi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reproduction, Appendix B.                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Mating: Appendix B partitions X into X1, X2 without saying how parents are
+ * chosen.  Reading: 2*ceil(N/2) draws uniformly with replacement from the K
+ * valid members (ascending slot order); draws 0..P-1 form X1 and P..2P-1
+ * form X2.  Index of draw e = (w_e * K) >> 32 on the 32-bit word w_e. */
+void orc_mating(const orc_params *p, int32_t t, int32_t K, const int32_t *vlist,
+                int32_t *parents)
+{
+    const int32_t P = (p->N + 1) / 2;
+    for (int32_t e = 0; e < 2 * P; ++e) {
+        uint32_t w[4];
+        philox(p, (uint32_t)(e / 4), 0u, (uint32_t)t, ORC_TAG_MATE, w);
+        uint32_t idx = (uint32_t)(((uint64_t)w[e % 4] * (uint64_t)(uint32_t)K) >> 32);
+        parents[e] = vlist[idx];
+    }
+}
+
+/* Tensorized SBX, Appendix B (the two B equations and X_cross):
+ *   B  = sgn(R1 - 1/2) [H(1/2 - Mc)(2Mc)^(1/(eta+1)) + (1 - H(1/2 - Mc))(2 - 2Mc)^(-1/(eta+1))]
+ *   B  = [1 - rep(H(R3 - p_c))] [(1 - H(R2 - 1/2)) B + H(R2 - 1/2)] + rep(H(R3 - p_c))
+ *   X_cross = [((1+B) X1 + (1-B) X2)/2 ; ((1-B) X1 + (1+B) X2)/2]
+ * R1 and R2 enter only through sgn(R1 - 1/2) and H(R2 - 1/2): each is read as
+ * a fair coin (bit 0 and bit 1 of the word that carries Mc).  The pair gate
+ * H(R3 - p_c) is 0 (crossover happens) iff R3 < p_c.
+ * X1, X2: P x d; Xcross: 2P x d. */
+void orc_sbx(const orc_params *p, int32_t t, const double *X1, const double *X2,
+             double *Xcross)
+{
+    const int32_t P = (p->N + 1) / 2, d = p->d;
+    const double eta = p->eta_c;
+    const uint32_t Tc = event_threshold(p->p_c);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int32_t pr = 0; pr < P; ++pr) {
+        uint32_t g[4];
+        philox(p, (uint32_t)pr, 0u, (uint32_t)t, ORC_TAG_PAIR, g);
+        double no_cross = ((g[0] >> 8) < Tc) ? 0.0 : 1.0;   /* H(R3 - p_c) */
+        for (int32_t j = 0; j < d; ++j) {
+            uint32_t w[4];
+            philox(p, (uint32_t)(j / 4), (uint32_t)pr, (uint32_t)t, ORC_TAG_SBX, w);
+            uint32_t word = w[j % 4];
+            double Mc = u24(word);
+            double sgn = (word & 1u) ? 1.0 : -1.0;               /* sgn(R1 - 1/2) */
+            double keep = (word & 2u) ? 1.0 : 0.0;               /* H(R2 - 1/2)   */
+            double h = (Mc < 0.5) ? 1.0 : 0.0;                   /* H(1/2 - Mc)   */
+            double beta = h * pow(2.0 * Mc, 1.0 / (eta + 1.0))
+                        + (1.0 - h) * pow(2.0 - 2.0 * Mc, -1.0 / (eta + 1.0));
+            double B = sgn * beta;
+            B = (1.0 - no_cross) * ((1.0 - keep) * B + keep) + no_cross;
+            double x1 = X1[(int64_t)pr * d + j], x2 = X2[(int64_t)pr * d + j];
+            Xcross[(int64_t)pr * d + j] = ((1.0 + B) * x1 + (1.0 - B) * x2) / 2.0;
+            Xcross[(int64_t)(pr + P) * d + j] = ((1.0 - B) * x1 + (1.0 + B) * x2) / 2.0;
+        }
+    }
+}
+
+/* Tensorized polynomial mutation, Appendix B (C, X_mut and Delta):
+ *   C = H(p_m/d - R4),  X_mut = X_cross + Delta (.) C,
+ *   Delta = (U-L)[(2M + (1-2M)(1-d1)^(xi+1))^(1/(xi+1)) - 1]   if M < 1/2
+ *         = (U-L)[1 - (2(1-M) + 2(M-1/2)(1-d2)^(xi+1))^(1/(xi+1))]  if M > 1/2
+ *   d1 = (x-L)/(U-L), d2 = (U-x)/(U-L).
+ * The site fires iff R4 < p_m/d.  The formula assumes x in [L,U] while SBX
+ * can leave the box: the reading clips to [L,U] before and after.
+ * Xc holds the N kept offspring rows (the first N rows of X_cross), mutated
+ * in place; mask (N x d, may be NULL) receives C. */
+void orc_mutation(const orc_params *p, int32_t t, double *Xc, uint8_t *mask)
+{
+    const int32_t N = p->N, P = (p->N + 1) / 2, d = p->d;
+    const double L = p->L, U = p->U, xi = p->eta_m;
+    const uint32_t Tm = event_threshold(p->p_m / (double)d);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int32_t c = 0; c < N; ++c) {
+        int32_t pr = c < P ? c : c - P;
+        int32_t second = c < P ? 0 : 1;
+        for (int32_t j = 0; j < d; ++j) {
+            uint32_t wh[4], wl[4];
+            philox(p, (uint32_t)(j / 8), (uint32_t)pr, (uint32_t)t, ORC_TAG_MUTHI, wh);
+            philox(p, (uint32_t)j, (uint32_t)c, (uint32_t)t, ORC_TAG_MUTLO, wl);
+            int b = j % 8;
+            uint32_t hi8 = (wh[2 * second + b / 4] >> (8 * (b % 4))) & 0xFFu;
+            uint32_t lo16 = wl[0] >> 16;
+            uint32_t r4 = (hi8 << 16) | lo16;           /* R4 = r4 * 2^-24 */
+            double C = (r4 < Tm) ? 1.0 : 0.0;           /* H(p_m/d - R4)   */
+            double M = u24(wl[1]);
+            double x = Xc[(int64_t)c * d + j];
+            if (x < L) x = L;
+            if (x > U) x = U;
+            double d1 = (x - L) / (U - L), d2 = (U - x) / (U - L);
+            double lo = (M < 0.5) ? 1.0 : 0.0;          /* H(0.5 - M) */
+            double up = (M > 0.5) ? 1.0 : 0.0;          /* H(M - 0.5) */
+            double delta = 0.0;
+            if (lo > 0.0)
+                delta = (U - L) * (pow(2.0 * M + (1.0 - 2.0 * M) * pow(1.0 - d1, xi + 1.0),
+                                       1.0 / (xi + 1.0)) - 1.0);
+            else if (up > 0.0)
+                delta = (U - L) * (1.0 - pow(2.0 * (1.0 - M) + 2.0 * (M - 0.5) * pow(1.0 - d2, xi + 1.0),
+                                             1.0 / (xi + 1.0)));
+            x = x + delta * C;
+            if (x < L) x = L;
+            if (x > U) x = U;
+            Xc[(int64_t)c * d + j] = x;
+            if (mask) mask[(int64_t)c * d + j] = (uint8_t)C;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Selection, Algorithm 1 with Eqs. 2-5.                                     */
+/*   z* = min over the population (lines 3-4), F' = F - z*                   */
+/*   Theta = arccos(F' V^T / (||F'|| ||V||)) (line 5)                        */
+/*   A = RowMin index of Theta (line 6, Eq. 2), ties to the lower index      */
+/*   APD_i = (1 + m (t/t_max)^alpha theta_i / gamma_{A_i}) ||f'_i|| (Eq. 4)  */
+/*   survivor_j = column argmin of APD over {i : A_i = j}, inf elsewhere     */
+/*   (lines 7-15); a column with no member is an invalid slot (Sec. 3.2).    */
+/* Theta is evaluated one row at a time; only its row minimum is kept.       */
+/* A solution equal to z* has 0/0 cosines: read as cos = 0 for every j, so   */
+/* A_i = 0, theta_i = pi/2 and APD_i = 0.                                    */
+/* ------------------------------------------------------------------------ */
+void orc_select(int32_t m, int32_t n, const double *F, const uint8_t *valid,
+                int32_t r, const double *V, const double *gamma,
+                int32_t t, int32_t t_max, double alpha,
+                double *zstar, int32_t *assoc, double *theta, double *apd,
+                int32_t *survivor)
+{
+    double z[64];
+    for (int32_t k = 0; k < m; ++k) {
+        z[k] = INFINITY;
+        for (int32_t i = 0; i < n; ++i) {
+            if (valid && !valid[i]) continue;
+            double f = F[(int64_t)i * m + k];
+            if (f < z[k]) z[k] = f;
+        }
+        if (zstar) zstar[k] = z[k];
+    }
+    const double pen = (double)m * pow((double)t / (double)t_max, alpha);
+    double *vn = (double *)malloc(sizeof(double) * (size_t)r);
+    double *th_all = (double *)malloc(sizeof(double) * (size_t)n);
+    double *apd_all = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int32_t j = 0; j < r; ++j)
+        vn[j] = sqrt(dot(V + (int64_t)j * m, V + (int64_t)j * m, m));
+
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int32_t i = 0; i < n; ++i) {
+        if (valid && !valid[i]) {
+            assoc[i] = -1;
+            th_all[i] = NAN;
+            apd_all[i] = INFINITY;
+            continue;
+        }
+        double fp[64];
+        for (int32_t k = 0; k < m; ++k) fp[k] = F[(int64_t)i * m + k] - z[k];
+        double nf = sqrt(dot(fp, fp, m));
+        int32_t best_j = 0;
+        double best_th = INFINITY;
+        for (int32_t j = 0; j < r; ++j) {
+            double c = (nf > 0.0) ? dot(fp, V + (int64_t)j * m, m) / (nf * vn[j]) : 0.0;
+            double th = acos(clamp1(c));
+            if (th < best_th) { best_th = th; best_j = j; }
+        }
+        assoc[i] = best_j;
+        th_all[i] = best_th;
+        apd_all[i] = (1.0 + pen * best_th / gamma[best_j]) * nf;
+    }
+
+    /* column argmin, scanned serially in increasing i: ties go to lower i */
+    double *best = (double *)malloc(sizeof(double) * (size_t)r);
+    for (int32_t j = 0; j < r; ++j) { best[j] = INFINITY; survivor[j] = -1; }
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t j = assoc[i];
+        if (j < 0) continue;
+        if (survivor[j] < 0 || apd_all[i] < best[j]) {
+            best[j] = apd_all[i];
+            survivor[j] = i;
+        }
+    }
+    if (theta) memcpy(theta, th_all, sizeof(double) * (size_t)n);
+    if (apd) memcpy(apd, apd_all, sizeof(double) * (size_t)n);
+    free(best);
+    free(apd_all);
+    free(th_all);
+    free(vn);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One generation of Algorithm 2 on a population held in vector-slot order:  */
+/* X (N x d), F (N x m), valid (N); V, gamma (N = r).  Offspring Q_t, union   */
+/* with the valid parents (parents take combined indices j, children N + c), */
+/* selection with V_t, then, every round(f_r t_max) generations, adaptation  */
+/* of V from V0 and gamma.  Inspection outputs may be NULL.  Returns the     */
+/* number of surviving slots.                                                */
+/* ------------------------------------------------------------------------ */
+int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
+                       const orc_neuro *nd,
+                       double *X, double *F, uint8_t *valid, double *V, double *gamma,
+                       double *Xchild, double *Fchild, int32_t *parents,
+                       int32_t *assoc, int32_t *survivor)
+{
+    const int32_t N = p->N, d = p->d, m = p->m, P = (p->N + 1) / 2;
+    int32_t *vlist = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t K = 0;
+    for (int32_t j = 0; j < N; ++j)
+        if (valid[j]) vlist[K++] = j;
+    if (K == 0) { free(vlist); return -1; }
+
+    int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * P));
+    orc_mating(p, t, K, vlist, par);
+    double *X1 = (double *)malloc(sizeof(double) * (size_t)P * d);
+    double *X2 = (double *)malloc(sizeof(double) * (size_t)P * d);
+    for (int32_t q = 0; q < P; ++q) {
+        memcpy(X1 + (int64_t)q * d, X + (int64_t)par[q] * d, sizeof(double) * (size_t)d);
+        memcpy(X2 + (int64_t)q * d, X + (int64_t)par[P + q] * d, sizeof(double) * (size_t)d);
+    }
+    double *Xc = (double *)malloc(sizeof(double) * (size_t)(2 * P) * d);
+    orc_sbx(p, t, X1, X2, Xc);
+    free(X1);
+    free(X2);
+    /* keep the first N rows of X_cross */
+    orc_mutation(p, t, Xc, NULL);
+    double *Fc = (double *)malloc(sizeof(double) * (size_t)N * m);
+    orc_evaluate(p, N, Xc, Fc, nd, t);
+
+    /* combined population: parents (slot order) then children */
+    const int32_t n = 2 * N;
+    double *Fall = (double *)malloc(sizeof(double) * (size_t)n * m);
+    uint8_t *vall = (uint8_t *)malloc((size_t)n);
+    memcpy(Fall, F, sizeof(double) * (size_t)N * m);
+    memcpy(Fall + (int64_t)N * m, Fc, sizeof(double) * (size_t)N * m);
+    for (int32_t j = 0; j < N; ++j) { vall[j] = valid[j]; vall[N + j] = 1; }
+    int32_t *as = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *sv = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    orc_select(m, n, Fall, vall, N, V, gamma, t, p->t_max, p->alpha,
+               NULL, as, NULL, NULL, sv);
+
+    if (Xchild) memcpy(Xchild, Xc, sizeof(double) * (size_t)N * d);
+    if (Fchild) memcpy(Fchild, Fc, sizeof(double) * (size_t)N * m);
+    if (parents) memcpy(parents, par, sizeof(int32_t) * (size_t)(2 * P));
+    if (assoc) memcpy(assoc, as, sizeof(int32_t) * (size_t)n);
+    if (survivor) memcpy(survivor, sv, sizeof(int32_t) * (size_t)N);
+
+    /* P_{t+1}: slot j holds the survivor of vector j */
+    double *Xn = (double *)malloc(sizeof(double) * (size_t)N * d);
+    double *Fn = (double *)malloc(sizeof(double) * (size_t)N * m);
+    int32_t alive = 0;
+    for (int32_t j = 0; j < N; ++j) {
+        int32_t i = sv[j];
+        if (i < 0) {
+            valid[j] = 0;
+            for (int32_t k = 0; k < d; ++k) Xn[(int64_t)j * d + k] = NAN;
+            for (int32_t k = 0; k < m; ++k) Fn[(int64_t)j * m + k] = NAN;
+            continue;
+        }
+        valid[j] = 1;
+        ++alive;
+        const double *xs = (i < N) ? X + (int64_t)i * d : Xc + (int64_t)(i - N) * d;
+        const double *fs = Fall + (int64_t)i * m;
+        memcpy(Xn + (int64_t)j * d, xs, sizeof(double) * (size_t)d);
+        memcpy(Fn + (int64_t)j * m, fs, sizeof(double) * (size_t)m);
+    }
+    memcpy(X, Xn, sizeof(double) * (size_t)N * d);
+    memcpy(F, Fn, sizeof(double) * (size_t)N * m);
+
+    /* reference-vector adaptation every round(f_r * t_max) generations */
+    int32_t period = (int32_t)floor(p->f_r * (double)p->t_max + 0.5);
+    if (period < 1) period = 1;
+    if (t % period == 0) {
+        double range[64];
+        orc_objective_range(m, N, F, valid, range);
+        orc_adapt(m, N, V0, range, V);
+        orc_gamma(m, N, V, gamma);
+    }
+
+    free(Xn); free(Fn); free(as); free(sv); free(vall); free(Fall);
+    free(Fc); free(Xc); free(par); free(vlist);
+    return alive;
+}

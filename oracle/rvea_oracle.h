@@ -1,0 +1,92 @@
+/*
+ * FP64 CPU oracle of one generation of tensorized RVEA.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link,
+ * load or call this code: only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py use it.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * Every function states the passage of arXiv 2404.01159 ("GPU-accelerated
+ * Evolutionary Multiobjective Optimization Using Tensorized RVEA") it follows.
+ * Where the paper is silent the reading used is stated beside the function.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
+ * Numbers: As Easy as 1, 2, 3", SC'11), written here from that definition.
+ * Counter layout (key = seed lo/hi 32 bits; c2 = generation t; c3 = tag):
+ *   INIT   (j/4, i, 0, 1)  word j%4   -> x_ij = L + (U-L) * u24
+ *   MATE   (e/4, 0, t, 2)  word e%4   -> parent draw e, index (w*K)>>32
+ *   PAIR   (p,   0, t, 3)  word 0     -> R3 of pair p (u24)
+ *   SBX    (j/4, p, t, 4)  word j%4   -> Mc = u24(w), sign coin bit0, keep coin bit1
+ *   MUTHI  (j/8, p, t, 5)  byte j%8 of words 0-1 (first child) / 2-3 (second)
+ *   MUTLO  (j,   c, t, 6)  word0>>16 = low 16 bits of R4, word1 -> M_mut (u24)
+ *   INIT   (j,   i, 0, 1)  words 0,1 -> Box-Muller N(0,1) (neuroevolution weights)
+ *   NOISE  (k,   s, t, 7)  words 0,1 -> Box-Muller N(0,1), state component k, step s
+ * where u24(w) = (w >> 8) * 2^-24 and R4[c,j] = ((hi8 << 16) | lo16) * 2^-24.
+ */
+#ifndef RVEA_ORACLE_H
+#define RVEA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2 };
+enum { ORC_TAG_INIT = 1, ORC_TAG_MATE = 2, ORC_TAG_PAIR = 3, ORC_TAG_SBX = 4,
+       ORC_TAG_MUTHI = 5, ORC_TAG_MUTLO = 6, ORC_TAG_NOISE = 7 };
+
+typedef struct {
+    int32_t m, d, N, H;
+    int32_t problem;
+    int32_t t_max;
+    double alpha, f_r, eta_c, eta_m, p_c, p_m, L, U;
+    uint64_t seed;
+} orc_params;
+
+/* Synthetic linear-dynamics rollout used as the neuroevolution objective. */
+typedef struct {
+    int32_t ns, na, h1, h2;   /* state, action, hidden sizes (17, 6, 64, 64)   */
+    int32_t steps;            /* rollout length                                */
+    double sigma;             /* process-noise standard deviation              */
+    const double *A;          /* ns x ns, row-major                            */
+    const double *B;          /* ns x na, row-major                            */
+} orc_neuro;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+int64_t orc_lattice_count(int32_t m, int32_t H);
+int32_t orc_lattice(int32_t m, int32_t H, int32_t N, int32_t *K);
+void orc_lattice_unit(int32_t m, int32_t N, const int32_t *K, double *V0);
+void orc_gamma(int32_t m, int32_t r, const double *V, double *gamma);
+void orc_objective_range(int32_t m, int32_t n, const double *F, const uint8_t *valid,
+                         double *range);
+void orc_adapt(int32_t m, int32_t r, const double *V0, const double *range, double *V);
+
+void orc_init_population(const orc_params *p, double *X);
+void orc_evaluate(const orc_params *p, int32_t n, const double *X, double *F,
+                  const orc_neuro *nd, int32_t t);
+void orc_neuro_noise(const orc_params *p, const orc_neuro *nd, int32_t t, double *xi);
+void orc_mating(const orc_params *p, int32_t t, int32_t K, const int32_t *vlist,
+                int32_t *parents);
+void orc_sbx(const orc_params *p, int32_t t, const double *X1, const double *X2,
+             double *Xcross);
+void orc_mutation(const orc_params *p, int32_t t, double *Xc, uint8_t *mask);
+void orc_select(int32_t m, int32_t n, const double *F, const uint8_t *valid,
+                int32_t r, const double *V, const double *gamma,
+                int32_t t, int32_t t_max, double alpha,
+                double *zstar, int32_t *assoc, double *theta, double *apd,
+                int32_t *survivor);
+int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
+                       const orc_neuro *nd,
+                       double *X, double *F, uint8_t *valid, double *V, double *gamma,
+                       double *Xchild, double *Fchild, int32_t *parents,
+                       int32_t *assoc, int32_t *survivor);
+
+void orc_set_threads(int32_t n);
+int32_t orc_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,194 @@
+"""Pins of the oracle's reproduction operators and objectives (Appendix B and
+the DTLZ definitions): invariants, degenerate cases that reduce to identity,
+closed-form distributions (KS tests) and hand-worked objective values.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _params(orc, **kw):
+    base = dict(m=3, d=64, N=210, H=19, problem=orc.DTLZ2, t_max=100, seed=7)
+    base.update(kw)
+    return orc.make_params(**base)
+
+
+def _parents(p, seed=0):
+    rng = np.random.default_rng(seed)
+    P = (p.N + 1) // 2
+    return rng.uniform(0.05, 0.95, (P, p.d)), rng.uniform(0.05, 0.95, (P, p.d))
+
+
+def test_sbx_mean_preserved(orc):
+    p = _params(orc)
+    X1, X2 = _parents(p)
+    Xc = orc.sbx(p, 3, X1, X2)
+    P = X1.shape[0]
+    lhs = Xc[:P] + Xc[P:]
+    assert np.allclose(lhs, X1 + X2, rtol=0, atol=4 * np.finfo(float).eps * 2)
+
+
+def test_sbx_no_crossover_is_identity(orc):
+    p = _params(orc, p_c=0.0)
+    X1, X2 = _parents(p, 1)
+    Xc = orc.sbx(p, 5, X1, X2)
+    P = X1.shape[0]
+    assert np.array_equal(Xc[:P], X1) and np.array_equal(Xc[P:], X2)
+
+
+def _beta_cdf(b, eta):
+    b = np.asarray(b)
+    return np.where(b <= 1.0, 0.5 * b ** (eta + 1), 1.0 - 0.5 * b ** (-(eta + 1)))
+
+
+@pytest.mark.parametrize("eta", [20.0, 2.0])
+def test_sbx_spread_distribution(orc, eta):
+    p = _params(orc, d=256, N=400, eta_c=eta)
+    X1, X2 = _parents(p, 2)
+    Xc = orc.sbx(p, 11, X1, X2)
+    P = X1.shape[0]
+    B = (Xc[:P] - Xc[P:]) / (X1 - X2)       # recovers B per site
+    kept = np.isclose(B, 1.0, rtol=0, atol=1e-9)
+    frac_keep = kept.mean()
+    n = kept.size
+    assert abs(frac_keep - 0.5) < 5 * math.sqrt(0.25 / n)
+    Bs = B[~kept]
+    frac_neg = (Bs < 0).mean()
+    assert abs(frac_neg - 0.5) < 5 * math.sqrt(0.25 / Bs.size)
+    beta = np.abs(Bs)
+    res = stats.kstest(beta, lambda b: _beta_cdf(b, eta))
+    assert res.pvalue > 1e-3, res
+
+
+def test_sbx_pair_gate_rate(orc):
+    p = _params(orc, d=8, N=4000, p_c=0.3)
+    X1, X2 = _parents(p, 3)
+    Xc = orc.sbx(p, 2, X1, X2)
+    P = X1.shape[0]
+    crossed = np.any(Xc[:P] != X1, axis=1)
+    # a crossed pair keeps every variable with prob 2^-8 only
+    assert abs(crossed.mean() - 0.3) < 5 * math.sqrt(0.3 * 0.7 / P)
+
+
+def test_mutation_rate_zero_identity(orc):
+    p = _params(orc, p_m=0.0)
+    rng = np.random.default_rng(4)
+    Xc = rng.uniform(0, 1, (p.N, p.d))
+    Xm, mask = orc.mutation(p, 3, Xc)
+    assert mask.sum() == 0
+    assert np.array_equal(Xm, Xc)
+
+
+def test_mutation_clips_into_box(orc):
+    p = _params(orc, p_m=float(64))   # every site
+    rng = np.random.default_rng(5)
+    Xc = rng.uniform(-0.5, 1.5, (p.N, p.d))
+    Xm, mask = orc.mutation(p, 3, Xc)
+    assert mask.all()
+    assert Xm.min() >= 0.0 and Xm.max() <= 1.0
+
+
+def test_mutation_site_frequency(orc):
+    p = _params(orc, d=50, N=2000)
+    Xc = np.full((p.N, p.d), 0.5)
+    _, mask = orc.mutation(p, 9, Xc)
+    n = mask.size
+    q = math.ceil((1 << 24) / 50) / (1 << 24)     # R4 < 1/d on the 24-bit grid
+    k = int(mask.sum())
+    assert stats.binomtest(k, n, q).pvalue > 1e-3
+    assert abs(q - 1 / 50) < 1e-7
+
+
+def _pm_cdf(q, x, eta):
+    """CDF of the mutation step (x' - x)/(U-L) of Deb's polynomial mutation
+    at an interior x with U-L = 1, derived from the Appendix B formula with
+    M uniform on [0, 1)."""
+    q = np.asarray(q, dtype=np.float64)
+    a = (1 - x) ** (eta + 1)      # (1 - delta1)^(eta+1), delta1 = x
+    b = x ** (eta + 1)            # (1 - delta2)^(eta+1), delta2 = 1 - x
+    neg = ((1 + q) ** (eta + 1) - a) / (2 * (1 - a))
+    pos = 0.5 + (1 - (1 - q) ** (eta + 1)) / (2 * (1 - b))
+    return np.clip(np.where(q < 0, neg, pos), 0, 1)
+
+
+@pytest.mark.parametrize("x", [0.3, 0.85])
+def test_mutation_step_distribution(orc, x):
+    eta = 20.0
+    p = _params(orc, d=100, N=400, p_m=100.0, eta_m=eta)
+    Xc = np.full((p.N, p.d), x)
+    Xm, mask = orc.mutation(p, 4, Xc)
+    assert mask.all()
+    steps = (Xm - x).ravel()
+    res = stats.kstest(steps, lambda q: _pm_cdf(q, x, eta))
+    assert res.pvalue > 1e-3, res
+    assert steps.min() >= -x - 1e-12 and steps.max() <= 1 - x + 1e-12
+
+
+def _hand_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "dtlz_hand.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            a, b = line.split(";")
+            a = a.split()
+            prob, m, d = int(a[0]), int(a[1]), int(a[2])
+            x = [float(v) for v in a[3:]]
+            fx = [float(v) for v in b.split()]
+            rows.append((prob, m, d, x, fx))
+    return rows
+
+
+def test_dtlz_hand_worked(orc):
+    rows = _hand_rows()
+    assert len(rows) == 3
+    for prob, m, d, x, fx in rows:
+        p = orc.make_params(m=m, d=d, N=1, H=0, problem=prob)
+        F = orc.evaluate(p, np.array([x]))
+        assert np.allclose(F[0], fx, rtol=1e-13, atol=1e-13), (prob, F[0], fx)
+
+
+@pytest.mark.parametrize("m,d", [(2, 12), (3, 12), (5, 30), (3, 5000)])
+def test_dtlz_fronts(orc, m, d):
+    rng = np.random.default_rng(m * 1000 + d)
+    X = np.full((64, d), 0.5)
+    X[:, : m - 1] = rng.uniform(0, 1, (64, m - 1))     # g = 0: on the front
+    F2 = orc.evaluate(orc.make_params(m=m, d=d, N=64, H=0, problem=orc.DTLZ2), X)
+    assert np.allclose(np.linalg.norm(F2, axis=1), 1.0, rtol=0, atol=1e-15)
+    F1 = orc.evaluate(orc.make_params(m=m, d=d, N=64, H=0, problem=orc.DTLZ1), X)
+    # DTLZ1's g sums k terms of (0 - cos 0) = -1 on top of k: exact zero
+    assert np.allclose(F1.sum(1), 0.5, rtol=0, atol=1e-12)
+    # off the front, g > 0 raises every objective
+    X2 = X.copy()
+    X2[:, m - 1:] = 0.3
+    assert (orc.evaluate(orc.make_params(m=m, d=d, N=64, H=0, problem=orc.DTLZ2), X2)
+            >= F2 - 1e-15).all()
+
+
+def test_init_population(orc):
+    p = _params(orc, d=13, N=105, H=13, seed=123)
+    X = orc.init_population(p)
+    assert X.min() >= 0.0 and X.max() < 1.0
+    # 24-bit grid: exactly representable in float32
+    assert np.array_equal(X.astype(np.float32).astype(np.float64), X)
+    assert stats.kstest(X.ravel(), "uniform").pvalue > 1e-3
+    # first word of individual 0 comes from counter (0, 0, 0, INIT)
+    w = orc.philox([0, 0, 0, orc.TAG_INIT], [123, 0])
+    assert X[0, 0] == (w[0] >> 8) / 2 ** 24 and X[0, 3] == (w[3] >> 8) / 2 ** 24
+
+
+def test_mating_uniform_over_valid(orc):
+    p = _params(orc, N=20000)
+    vlist = np.array([2, 5, 6, 11], dtype=np.int32)
+    par = orc.mating(p, 7, vlist)
+    assert set(np.unique(par)) <= set(vlist.tolist())
+    counts = np.array([(par == v).sum() for v in vlist])
+    assert stats.chisquare(counts).pvalue > 1e-3
+    # draw e uses word e % 4 of counter (e/4, 0, t, MATE) and (w*K) >> 32
+    w = orc.philox([1, 0, 7, orc.TAG_MATE], [7, 0])
+    assert par[5] == vlist[(w[1] * 4) >> 32]
