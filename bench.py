@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of one RVEA generation (the whole hot path) on GB300.
+
+A step is one generation: reproduction + evaluation, selection, finalize
+(+ reference-vector adaptation and gamma every round(f_r t_max) generations).
+Default workload: DTLZ1, m = 3, d = 5000, N = NV = 9870 (H = 139), the
+large-scale configuration.  The metric is generations per second; the
+roofline entry reports the reproduction kernel against the measured HBM copy
+bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path
+has no exchange step): value = all generations of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RVEA generations/s & HBM GB/s vs roofline (plain vs batched); serve p50/p99"
+
+WORKLOADS = {
+    "dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000),
+    "dtlz2_m3_d12_N105": dict(m=3, d=12, N=105, H=13, problem=0, t_max=100),
+}
+COMMON = dict(alpha=2.0, f_r=0.1, eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
+
+
+def repro_bytes(wl) -> int:
+    """Algorithmic bytes of one reproduction launch: read 2*ceil(N/2) parent
+    rows, write N child rows, d float32 each (objectives are O(N m))."""
+    P = (wl["N"] + 1) // 2
+    return (2 * P + wl["N"]) * wl["d"] * 4
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("k_repro.cu", "rvea_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2404_01159_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per reproduction launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_repro_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    sha, traffic = None, None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("source_sha:"):
+                sha = line.split(":", 1)[1].strip()
+            if line.startswith("dram_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1].strip())
+    return traffic if sha == source_sha() else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.ok = False
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100",
+                                       "-i", gpu_id], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+            return
+        self.first = threading.Event()
+        self.live = False
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        self.first.wait(timeout=10)
+        self.ok = True
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.first.set()
+            if self.live:
+                self.rows.append([x.strip() for x in line.split(",")])
+
+    def start(self):
+        self.live = True
+
+    def stop(self):
+        self.live = False
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_baseline(wl, seconds=20.0):
+    """The FP64 oracle, as it stands, on the host cores: whole generations of
+    the same workload from a seeded initial population, as many as fit in
+    about `seconds` (at least one)."""
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    p = orc.make_params(m=wl["m"], d=wl["d"], N=wl["N"], H=wl["H"], problem=wl["problem"],
+                        t_max=wl["t_max"], seed=0, **COMMON)
+    V0, st = orc.initial_state(p)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.generation(p, V0, st)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "generations/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} whole FP64 oracle generation(s) of the same workload, "
+                      f"{dt:.1f} s on {cores} host threads (OpenMP over rows)"}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    p = orc.make_params(m=wl["m"], d=wl["d"], N=wl["N"], H=wl["H"], problem=wl["problem"],
+                        t_max=wl["t_max"], seed=0, **COMMON)
+    V0, st = orc.initial_state(p)
+    for _ in range(min(args.warmup, 1)):
+        orc.generation(p, V0, st)
+    budget = 150.0
+    n = 0
+    t0 = time.perf_counter()
+    while n < args.steps:
+        orc.generation(p, V0, st)
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "generations/s",
+            "n_gpus": 0, "steps": n, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox initial population, closed-form objective)",
+            "config": {"workload": args.workload, **wl, **COMMON},
+            "cpu_baseline": {"value": v, "unit": "generations/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{n} of the requested {args.steps} generations "
+                                       f"(bounded to ~{budget:.0f} s), FP64 oracle"},
+            "e2e": {"value": v, "unit": "generations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dtlz1_m3_d5000_N9870", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2404_01159_gb300 import Run
+    from paper_2404_01159_gb300._native import lib
+    lib()
+
+    K, W = args.steps, max(3, args.warmup)
+    kw = dict(wl, **COMMON)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput (graph replays) -------------------------
+    run = Run(seed=1000 + rank, **kw)
+    run.step(W)
+    torch.cuda.synchronize()
+    t_first = run.t
+    props = torch.cuda.get_device_properties(local)
+    gid = str(getattr(props, "uuid", "")) or str(local)
+    if gid and not gid.startswith("GPU-") and len(gid) >= 32:
+        gid = "GPU-" + gid
+    sampler = ClockSampler(gid) if rank == 0 else None
+    barrier()
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run.step(K)
+    e1.record()
+    e1.synchronize()
+    if sampler:
+        sampler.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    run.sync_status()
+    p_adapt = max(1, int(kw["f_r"] * kw["t_max"] + 0.5))
+    n_adapt = sum(1 for t in range(t_first, t_first + K) if t % p_adapt == 0)
+    launches = 3 * K + n_adapt
+    del run
+
+    # ---- per-kernel device time (CUDA events around every launch) -----------
+    Kp = min(K, 500)
+    prun = Run(seed=2000 + rank, **kw)
+    prun.step(W)
+    phases = prun.step_profiled(Kp)
+    prun.sync_status()
+    del prun
+    repro_ms = phases[0] / Kp
+    bytes_rep = repro_bytes(wl)
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_rep / (repro_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API, host buffers --------------------
+    N, m, d = wl["N"], wl["m"], wl["d"]
+    hF = torch.empty((N, m), dtype=torch.float32, pin_memory=True)
+    hV = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+    hX = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
+    Ke = K
+    barrier()
+    t0 = time.perf_counter()
+    erun = Run(seed=3000 + rank, **kw)            # host config -> device state
+    for _ in range(Ke):
+        erun.step(1)
+        erun.objectives(hF, hV)                  # per-generation result to host
+    erun.population(hX, hV)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    erun.sync_status()
+    ws_bytes = erun.workspace_nbytes
+    del erun
+    h2d_init = N * m * 8 * 2 + N * 16 + 4096       # lattice (f64 x2), float copy, tables
+    d2h = Ke * (N * m * 4 + N) + N * d * 4 + N
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_seconds)
+    value = world * K / (ms * 1e-3)
+    clocks = sampler.summary() if sampler else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "generations/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Philox initial population, closed-form DTLZ objective)",
+        "config": {"workload": args.workload, **wl, **COMMON,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"no flush: {2 * N * d * 4 / 1e6:.0f} MB moved per generation "
+                         f"> 129 MB L2 (inputs larger than L2)",
+                   "generations": f"t = {t_first}..{t_first + K - 1}"},
+        "roofline": {"kernel": "k_repro (mating+SBX+PM+DTLZ eval)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": profiled_traffic(args.workload),
+                     "algorithmic_bytes_per_launch": bytes_rep,
+                     "avg_launch_ms": repro_ms,
+                     "timing": f"CUDA events around each launch, {Kp} generations"},
+        "phase_ms_per_generation": {"repro": phases[0] / Kp, "select": phases[1] / Kp,
+                                    "finalize": phases[2] / Kp, "gamma": phases[3] / Kp},
+        "whole_generation_hbm_gbs": bytes_rep / (ms / K * 1e-3) / 1e9,
+        "whole_generation_frac": bytes_rep / (ms / K * 1e-3) / 1e9 / hbm_peak,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * Ke / e2e_s, "unit": "generations/s",
+                "h2d_bytes_per_step": h2d_init / Ke, "d2h_bytes_per_step": d2h / Ke,
+                "what": "init from host config + per-generation objectives to pinned host "
+                        "+ final population to pinned host"},
+        "gpu_launches": launches,
+        "workspace_bytes": ws_bytes,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

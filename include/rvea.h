@@ -1,0 +1,210 @@
+/*
+ * rvea.h -- C ABI of the GB300 (sm_103a) tensorized-RVEA library.
+ *
+ * One call of rvea_step runs whole generations of RVEA (arXiv 2404.01159,
+ * Algorithm 2) for a population resident in device memory:
+ *   reproduction  -- SBX crossover and polynomial mutation, Appendix B
+ *   evaluation    -- DTLZ1 / DTLZ2 (Sec. 4.1) or a policy rollout (Sec. 4.3)
+ *   selection     -- ideal point, angle association, APD and per-vector
+ *                    argmin, Algorithm 1 with Eqs. 2-5
+ *   adaptation    -- reference-vector rescaling and gamma (Eq. 5) every
+ *                    round(f_r * t_max) generations
+ *
+ * Conventions shared by every entry point:
+ *  - Memory: the caller owns all device memory.  It allocates the workspace
+ *    (rvea_workspace_bytes) and every output buffer; the library allocates
+ *    nothing on the device and keeps only a small host handle.  A workspace
+ *    must stay allocated, untouched, until rvea_free.
+ *  - Pointers: an argument documented as "host or device" may be a device
+ *    pointer, a pinned (page-locked) host pointer or ordinary pageable host
+ *    memory; the kind is found with cudaPointerGetAttributes.
+ *  - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *    All work is enqueued asynchronously on it; results written to host
+ *    memory are complete only after the stream is synchronised.
+ *  - Layouts: row-major, C order.  Population rows and reference vectors are
+ *    reported in reference-vector slot order: row j holds the survivor kept
+ *    by vector j, or an invalid slot (valid[j] = 0, values NaN) when no
+ *    solution associated with vector j (Sec. 3.2, end of Algorithm 1).
+ *  - Errors: status codes only; nothing throws across this boundary.  Faults
+ *    found on the device (a timed-out wait, an out-of-range index) set a
+ *    device status word that rvea_sync_status reports.
+ */
+#ifndef RVEA_H
+#define RVEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rvea_run rvea_run;   /* opaque host handle */
+
+typedef enum {
+    RVEA_OK = 0,
+    RVEA_ERR_ARG = -1,      /* an argument is out of range                 */
+    RVEA_ERR_LATTICE = -2,  /* N != C(H+m-1, m-1)                           */
+    RVEA_ERR_NOMEM = -3,    /* workspace or scratch smaller than required  */
+    RVEA_ERR_CUDA = -4,     /* a CUDA runtime call failed                  */
+    RVEA_ERR_TIMEOUT = -5,  /* a bounded device wait gave up               */
+    RVEA_ERR_STATE = -6,    /* call not valid in the run's current state   */
+    RVEA_ERR_DEVICE = -7    /* a device-side check failed (bad index)      */
+} rvea_status;
+
+typedef enum {
+    RVEA_DTLZ2_SPHERE = 0,  /* spherical front, |f| = 1 on the front       */
+    RVEA_DTLZ1_LINEAR = 1,  /* multimodal linear front, sum f = 1/2        */
+    RVEA_NEURO_LINEAR = 2   /* MLP policy rollout on linear dynamics       */
+} rvea_problem;
+
+/* Synthetic linear dynamics of the neuroevolution objective (the stand-in
+ * for the paper's Brax tasks, Sec. 4.3 and Appendix C):
+ *   policy x = [W1 (h1 x ns), b1 (h1), W2 (h2 x h1), b2 (h2), W3 (na x h2), b3 (na)],
+ *   u = tanh(W3 tanh(W2 tanh(W1 s + b1) + b2) + b3), s_0 = 0,
+ *   s' = A s + B u + sigma * xi,  xi ~ N(0, I) per step, shared by all
+ *   policies of one generation;
+ *   f1 = -sum_steps s'[0],  f2 = sum_steps |u|^2.
+ * A (ns x ns) and B (ns x na) are host pointers, row-major, read during the
+ * rvea_init_ex call only.  Supported sizes: ns <= 32, na <= 16, h1 = h2 = 64. */
+typedef struct {
+    int ns, na, h1, h2;
+    int steps;
+    double sigma;
+    const double *A;
+    const double *B;
+} rvea_neuro_dynamics;
+
+/* All parameters of one optimisation run. */
+typedef struct {
+    int m;            /* objectives, 2..16                                   */
+    int d;            /* decision variables, m..(1<<22)                      */
+    int N;            /* population = number of reference vectors, 2..32768 */
+    int H;            /* lattice divisions; N must equal C(H+m-1, m-1)        */
+    int problem;      /* rvea_problem                                        */
+    int t_max;        /* generations of the run (APD penalty schedule), >= 1 */
+    double alpha;     /* APD penalty exponent, Eq. 4, > 0                    */
+    double f_r;       /* adaptation frequency: every round(f_r*t_max) gens  */
+    double eta_c;     /* SBX distribution index, > 0                         */
+    double eta_m;     /* mutation distribution index xi, > 0                 */
+    double p_c;       /* crossover probability per pair, [0,1]               */
+    double p_m;       /* mutation rate: per-site probability p_m / d, >= 0   */
+    double lower;     /* box [lower, upper] of every decision variable       */
+    double upper;
+    uint64_t seed;    /* Philox4x32-10 key                                   */
+    const rvea_neuro_dynamics *neuro;   /* required iff problem == NEURO     */
+} rvea_config;
+
+/* Bytes of device workspace a run of this shape needs (0 if invalid). */
+size_t rvea_workspace_bytes(int m, int d, int N);
+
+/* Create a run: builds the Das-Dennis lattice V0 (unit vectors), gamma(V0),
+ * draws and evaluates the initial population (Algorithm 2, initialisation)
+ * on `cuda_stream`.  The population uses p_c = 1, p_m = 1 (per-site 1/d),
+ * box [0,1] for DTLZ and [-1,1] for the rollout problem.
+ * dev_workspace: device pointer, 256-byte aligned, >= rvea_workspace_bytes.
+ * Errors: RVEA_ERR_LATTICE if N != C(H+m-1,m-1); RVEA_ERR_ARG for m < 2,
+ * d < m, t_max < 1, eta <= 0, f_r outside (0,1], unknown problem;
+ * RVEA_ERR_NOMEM if `bytes` is too small.  *out is set only on success. */
+rvea_status rvea_init(int m, int d, int N, int H, double alpha, double f_r,
+                      double eta_c, double eta_m, uint64_t seed,
+                      int problem, int t_max, void *dev_workspace, size_t bytes,
+                      void *cuda_stream, rvea_run **out);
+
+/* As rvea_init with every parameter explicit (needed for the rollout). */
+rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t bytes,
+                         void *cuda_stream, rvea_run **out);
+
+/* Enqueue n_generations >= 0 generations on `cuda_stream` (asynchronous;
+ * no host synchronisation).  Generation t is the run's next generation
+ * index (1-based); a run may continue past t_max, the penalty term
+ * (t/t_max)^alpha then exceeding 1. */
+rvea_status rvea_step(rvea_run *run, int n_generations, void *cuda_stream);
+
+/* One generation of each of n_runs distinct runs, packed into one launch
+ * per phase.  Every run's result is identical to what rvea_step(run, 1)
+ * gives.  All runs must live on the current device. */
+rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream);
+
+/* Copy the population (N x d float32, slot order) and the valid flags
+ * (N uint8, may be NULL).  dst, valid: host or device. */
+rvea_status rvea_population(const rvea_run *run, float *dst, uint8_t *valid,
+                            void *cuda_stream);
+
+/* Copy the objective values (N x m float32, slot order) and valid flags. */
+rvea_status rvea_objectives(const rvea_run *run, float *dst, uint8_t *valid,
+                            void *cuda_stream);
+
+/* Synchronise `run`'s last stream and report the device status word:
+ * RVEA_OK, RVEA_ERR_TIMEOUT or RVEA_ERR_DEVICE. */
+rvea_status rvea_sync_status(rvea_run *run);
+
+/* Release the host handle (the caller frees the workspace afterwards). */
+void rvea_free(rvea_run *run);
+
+const char *rvea_status_str(rvea_status s);
+
+/* ---- inspection, checkpoint and teacher forcing ---------------------- */
+
+/* Index of the next generation rvea_step will run (1 after init). */
+int rvea_generation(const rvea_run *run);
+
+/* As rvea_step with direct launches, a CUDA event recorded on `cuda_stream`
+ * around every kernel, and a synchronisation at the end; adds the measured
+ * device milliseconds per phase into phase_ms[0..3] (reproduction+
+ * evaluation, selection, finalize, gamma).  phase_ms: host, n_phases >= 4.
+ * Same results as rvea_step. */
+rvea_status rvea_step_profiled(rvea_run *run, int n_generations, void *cuda_stream,
+                               double *phase_ms, int n_phases);
+
+/* Full run state in slot order: X (N x d f32), F (N x m f32), valid (N u8),
+ * V (N x m f64, current reference vectors), gamma (N f64).  Any output may
+ * be NULL.  Host or device pointers.  Together with rvea_generation this is
+ * a checkpoint: Philox is counter-based, so no generator state exists. */
+rvea_status rvea_export_state(const rvea_run *run, float *X, float *F, uint8_t *valid,
+                              double *V, double *gamma, void *cuda_stream);
+
+/* Replace the run state (same layouts as rvea_export_state; all required)
+ * and set the next generation index to t >= 1.  F is taken as given. */
+rvea_status rvea_import_state(rvea_run *run, const float *X, const float *F,
+                              const uint8_t *valid, const double *V,
+                              const double *gamma, int t, void *cuda_stream);
+
+/* Offspring of the last completed generation, in child order c = 0..N-1
+ * (c < ceil(N/2): first child of pair c; otherwise second child of pair
+ * c - ceil(N/2)): X (N x d f32), F (N x m f32).  Valid until the next step. */
+rvea_status rvea_offspring(const rvea_run *run, float *X, float *F, void *cuda_stream);
+
+/* Selection of the last completed generation over the 2N combined
+ * solutions (parents i = j in slot order, then children i = N + c):
+ * assoc (2N i32; reference vector of each solution, -1 for an invalid
+ * parent) and survivor (N i32; combined index kept by vector j, or -1). */
+rvea_status rvea_last_selection(const rvea_run *run, int32_t *assoc, int32_t *survivor,
+                                void *cuda_stream);
+
+/* ---- stateless operators ---------------------------------------------- */
+
+/* Scratch bytes rvea_select needs for n solutions, r vectors. */
+size_t rvea_select_scratch_bytes(int n, int r, int m);
+
+/* Environmental selection of Algorithm 1 on n solutions:
+ * F (n x m f32, device), valid (n u8, device, NULL = all valid),
+ * V (r x m f32, device, unit rows), gamma (r f32, device) -> assoc (n i32,
+ * device), survivor (r i32, device: index of the solution kept by vector j
+ * or -1).  t, t_max, alpha enter the APD penalty (Eq. 4).  scratch: device,
+ * >= rvea_select_scratch_bytes(n, r, m), contents need no initialisation.
+ * Limits: m <= 16, n < 2^31. */
+rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid,
+                        int r, const float *V, const float *gamma,
+                        int t, int t_max, float alpha,
+                        int32_t *assoc, int32_t *survivor,
+                        void *scratch, size_t scratch_bytes, void *cuda_stream);
+
+/* gamma_j = min over i != j of the angle between v_i and v_j (Eq. 5), FP64.
+ * V (r x m f64, device, unit rows) -> gamma (r f64, device). */
+rvea_status rvea_gamma(int m, int r, const double *V, double *gamma, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVEA_H */

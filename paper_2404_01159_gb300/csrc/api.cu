@@ -1,0 +1,842 @@
+// Host side of the C ABI declared in include/rvea.h.
+//
+// The library keeps a small host handle per run; every device byte belongs
+// to the caller's workspace.  The workspace holds the population pool, the
+// objective and reference-vector arrays, the control block, the run's device
+// descriptor and its work-item tables.  rvea_step enqueues, per generation,
+// reproduction -> selection -> finalize (-> gamma on adaptation
+// generations), as direct launches or as replays of a CUDA graph that covers
+// one adaptation period.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/rvea.h"
+#include "rvea_device.cuh"
+
+namespace rvea {
+__global__ void k_repro(const __grid_constant__ BatchDir dir);
+__global__ void k_init(const __grid_constant__ BatchDir dir);
+__global__ void k_select(const __grid_constant__ BatchDir dir);
+__global__ void k_finalize(const __grid_constant__ BatchDir dir);
+__global__ void k_gamma(const __grid_constant__ BatchDir dir, int force);
+__global__ void k_gamma_op(const __grid_constant__ RunDesc D);
+__global__ void k_init_lists(const __grid_constant__ BatchDir dir);
+__global__ void k_gather_pop(const RunDesc *Rp, float *dst, uint8_t *valid);
+__global__ void k_gather_obj(const RunDesc *Rp, float *dst, uint8_t *valid);
+__global__ void k_gather_children(const RunDesc *Rp, float *X, float *F);
+__global__ void k_copy_selection(const RunDesc *Rp, int *assoc, int *surv);
+__global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin, int t);
+__global__ void k_op_prep(const RunDesc *Rp);
+__global__ void k_op_zstar(const RunDesc *Rp);
+__global__ void k_op_finish(const RunDesc *Rp);
+int repro_smem_total(int TS, int m, int G);
+}  // namespace rvea
+
+using namespace rvea;
+
+// ---------------------------------------------------------------------------
+// shapes, layout
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kSMs = 152;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int pow2ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct Shape {
+  int m, m4, d, d_pad, G, N, P, n_comb, team, ppc;
+  int n_repro, n_init, n_sel, nblk;
+};
+
+// Threads per pair: ~3 groups of 8 variables per thread, a power of two in
+// [1, 256].  It depends on d only, so the reduction tree of g does too.
+Shape make_shape(int m, int d, int N) {
+  Shape s;
+  s.m = m;
+  s.m4 = (m + 3) / 4;
+  s.d = d;
+  s.d_pad = (d + 7) / 8 * 8;
+  s.G = s.d_pad / 8;
+  s.N = N;
+  s.P = (N + 1) / 2;
+  s.n_comb = 2 * N;
+  s.team = std::min(256, std::max(1, pow2ceil((s.G + 2) / 3)));
+  s.ppc = kReproThreads / s.team;
+  s.n_repro = (s.P + s.ppc - 1) / s.ppc;
+  s.n_init = (N + s.ppc - 1) / s.ppc;
+  s.nblk = (s.n_comb + kSelThreads - 1) / kSelThreads;
+  // selection: solution blocks x vector chunks, >= ~4 CTAs per SM overall
+  const int tiles = (N + kVTile - 1) / kVTile;
+  int nch = std::max(1, std::min(tiles, (4 * kSMs + s.nblk - 1) / s.nblk));
+  const int tpc = (tiles + nch - 1) / nch;
+  nch = (tiles + tpc - 1) / tpc;
+  s.n_sel = s.nblk * nch;
+  return s;
+}
+
+struct Layout {
+  size_t X, F, slotmap, vlist, child, best, amax, assoc, surv, blk, V32, V64, V0, g64, g32,
+      ctl, desc, repro, init, sel, stage, noise, dynA, dynB, total;
+};
+
+Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.X = take((size_t)2 * s.N * s.d_pad * sizeof(float));
+  L.F = take((size_t)s.m * s.n_comb * sizeof(float));
+  L.slotmap = take((size_t)s.N * 4);
+  L.vlist = take((size_t)s.N * 4);
+  L.child = take((size_t)2 * s.N * 4);
+  L.best = take((size_t)s.N * 8);
+  L.amax = take((size_t)s.n_comb * 8);
+  L.assoc = take((size_t)s.n_comb * 4);
+  L.surv = take((size_t)s.N * 4);
+  L.blk = take((size_t)s.nblk * 4);
+  L.V32 = take((size_t)s.N * s.m4 * 16);
+  L.V64 = take((size_t)s.N * s.m * 8);
+  L.V0 = take((size_t)s.N * s.m * 8);
+  L.g64 = take((size_t)s.N * 8);
+  L.g32 = take((size_t)s.N * 4);
+  L.ctl = take(sizeof(Ctl));
+  L.desc = take(sizeof(RunDesc));
+  L.repro = take((size_t)s.n_repro * sizeof(ReproItem));
+  L.init = take((size_t)s.n_init * sizeof(ReproItem));
+  L.sel = take((size_t)s.n_sel * sizeof(SelItem));
+  L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
+  L.noise = take((size_t)steps_max * ns_max * 4);
+  L.dynA = take((size_t)ns_max * ns_max * 4);
+  L.dynB = take((size_t)ns_max * na_max * 4);
+  L.total = o;
+  return L;
+}
+
+int64_t lattice_size(int m, int H) {
+  // C(H+m-1, m-1), saturating at 2^40
+  long double c = 1.0L;
+  for (int i = 1; i <= m - 1; ++i) {
+    c = c * (long double)(H + i) / (long double)i;
+    if (c > 1e12L) return (int64_t)1 << 40;
+  }
+  return (int64_t)llroundl(c);
+}
+
+// Das-Dennis lattice {k in N^m : sum k = H}, lexicographic in k_1..k_{m-1},
+// each row scaled to unit length (FP64: one sqrt and one division per
+// component, both correctly rounded).
+void build_lattice(int m, int H, int N, std::vector<double> &V0) {
+  V0.assign((size_t)N * m, 0.0);
+  std::vector<int> k(m, 0);
+  k[m - 1] = H;
+  for (int row = 0; row < N; ++row) {
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) s += (double)k[q] * (double)k[q];
+    const double nrm = std::sqrt(s);
+    for (int q = 0; q < m; ++q) V0[(size_t)row * m + q] = (double)k[q] / nrm;
+    // next composition: increase the rightmost k_q (q < m-1) that can grow
+    int q = m - 2;
+    while (q >= 0) {
+      int used = 0;
+      for (int u = 0; u <= q; ++u) used += k[u];
+      if (used < H) break;
+      --q;
+    }
+    if (q < 0) break;
+    k[q] += 1;
+    for (int u = q + 1; u < m - 1; ++u) k[u] = 0;
+    int used = 0;
+    for (int u = 0; u < m - 1; ++u) used += k[u];
+    k[m - 1] = H - used;
+  }
+}
+
+uint32_t event_threshold24(double q) {
+  double x = std::ceil(q * 16777216.0);
+  if (x < 0.0) x = 0.0;
+  if (x > 16777216.0) x = 16777216.0;
+  return (uint32_t)x;
+}
+
+std::once_flag g_attr_once;
+cudaError_t g_attr_err = cudaSuccess;
+
+void set_kernel_attrs() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int cap = optin - 2048;   // leave room for static shared memory
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void *f) {
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (r != cudaSuccess && e == cudaSuccess) e = r;
+  };
+  set((const void *)k_repro);
+  set((const void *)k_init);
+  set((const void *)k_select);
+  set((const void *)k_finalize);
+  g_attr_err = e;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the run handle
+// ---------------------------------------------------------------------------
+struct rvea_run {
+  rvea_config cfg;
+  Shape sh;
+  Layout lay;
+  uint8_t *ws = nullptr;
+  int p_adapt = 1;
+  int t = 1;                      // host mirror of ctl->t
+  int device = 0;
+  RunDesc hd;                     // host copy of the device descriptor
+  RunDesc *d_desc = nullptr;
+  int repro_smem = 0, init_smem = 0, sel_smem = 0, fin_smem = 0;
+  cudaStream_t last_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t block_graph = nullptr;
+  bool use_graph = true;
+  bool has_last_gen = false;      // a generation ran since init / import
+};
+
+namespace {
+
+rvea_status cuerr(cudaError_t e) { return e == cudaSuccess ? RVEA_OK : RVEA_ERR_CUDA; }
+
+#define RV_TRY(x)                                    \
+  do {                                               \
+    const cudaError_t _e = (x);                      \
+    if (_e != cudaSuccess) return RVEA_ERR_CUDA;     \
+  } while (0)
+
+void dir_single(BatchDir &dir, const rvea_run *r, const void *items, int n_items) {
+  dir.n = 1;
+  dir.prefix[0] = 0;
+  dir.prefix[1] = n_items;
+  dir.desc[0] = r->d_desc;
+  dir.items[0] = items;
+}
+
+template <class T>
+T *wsp(const rvea_run *r, size_t off) {
+  return reinterpret_cast<T *>(r->ws + off);
+}
+
+// Enqueue one generation of every run in `runs` (one launch per phase).
+rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, bool gamma_by_flag) {
+  static thread_local BatchDir dr, ds, df;
+  int pr = 0, ps = 0;
+  int smr = 0, sms = 0, smf = 0;
+  dr.n = ds.n = df.n = n;
+  for (int q = 0; q < n; ++q) {
+    const rvea_run *r = runs[q];
+    dr.prefix[q] = pr;
+    ds.prefix[q] = ps;
+    df.prefix[q] = q;
+    dr.desc[q] = ds.desc[q] = df.desc[q] = r->d_desc;
+    dr.items[q] = wsp<ReproItem>(r, r->lay.repro);
+    ds.items[q] = wsp<SelItem>(r, r->lay.sel);
+    df.items[q] = nullptr;
+    pr += r->sh.n_repro;
+    ps += r->sh.n_sel;
+    smr = std::max(smr, r->repro_smem);
+    sms = std::max(sms, r->sel_smem);
+    smf = std::max(smf, r->fin_smem);
+  }
+  dr.prefix[n] = pr;
+  ds.prefix[n] = ps;
+  df.prefix[n] = n;
+  k_repro<<<pr, kReproThreads, smr, st>>>(dr);
+  k_select<<<ps, kSelThreads, sms, st>>>(ds);
+  k_finalize<<<n, kFinThreads, smf, st>>>(df);
+  if (gamma_by_flag) {
+    k_gamma<<<2 * kSMs, 256, 0, st>>>(df, 0);
+  }
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status launch_gamma_force(rvea_run *r, cudaStream_t st) {
+  static thread_local BatchDir d;
+  dir_single(d, r, nullptr, 1);
+  const int nb = (r->sh.N + 31) / 32;
+  k_gamma<<<std::min(nb, 4 * kSMs), 256, 0, st>>>(d, 1);
+  return cuerr(cudaGetLastError());
+}
+
+// One generation of a single run; gamma is enqueued by the host when the
+// generation adapts (t % p_adapt == 0), so no launch is spent otherwise.
+rvea_status enqueue_one(rvea_run *r, cudaStream_t st) {
+  rvea_run *one[1] = {r};
+  rvea_status s = launch_generation(one, 1, st, false);
+  if (s != RVEA_OK) return s;
+  if (r->t % r->p_adapt == 0) s = launch_gamma_force(r, st);
+  return s;
+}
+
+rvea_status ensure_block_graph(rvea_run *r) {
+  if (r->block_graph) return RVEA_OK;
+  if (!r->cap_stream) RV_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+  RV_TRY(cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int t_save = r->t;
+  rvea_status s = RVEA_OK;
+  // a period that starts at t = 1 (mod p): p-1 plain generations, then one
+  // that adapts
+  for (int q = 0; q < r->p_adapt && s == RVEA_OK; ++q) {
+    r->t = (q == r->p_adapt - 1) ? r->p_adapt : 1;
+    s = enqueue_one(r, r->cap_stream);
+  }
+  r->t = t_save;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(r->cap_stream, &g);
+  if (s != RVEA_OK) { if (g) cudaGraphDestroy(g); return s; }
+  if (e != cudaSuccess) return RVEA_ERR_CUDA;
+  const cudaError_t e2 = cudaGraphInstantiate(&r->block_graph, g, 0);
+  cudaGraphDestroy(g);
+  return cuerr(e2);
+}
+
+// Device-usable address of a pointer that is device, managed or pinned host.
+void *dev_addr(void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  if (a.type == cudaMemoryTypeUnregistered) return nullptr;
+  return p;
+}
+
+rvea_status validate(const rvea_config *c) {
+  if (!c) return RVEA_ERR_ARG;
+  if (c->m < 2 || c->m > kMaxM || c->d < c->m || c->d > (1 << 22) || c->N < 2 || c->N > 32768)
+    return RVEA_ERR_ARG;
+  if (c->t_max < 1 || !(c->eta_c > 0) || !(c->eta_m > 0) || !(c->f_r > 0) || c->f_r > 1 ||
+      !(c->alpha > 0) || !(c->p_c >= 0) || c->p_c > 1 || !(c->p_m >= 0) || !(c->upper > c->lower))
+    return RVEA_ERR_ARG;
+  if (c->problem < 0 || c->problem > 2) return RVEA_ERR_ARG;
+  if (c->problem == RVEA_NEURO_LINEAR) return RVEA_ERR_ARG;   // rollout kernel not built here
+  if (c->H < 0 || lattice_size(c->m, c->H) != (int64_t)c->N) return RVEA_ERR_LATTICE;
+  return RVEA_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+size_t rvea_workspace_bytes(int m, int d, int N) {
+  if (m < 2 || m > kMaxM || d < m || d > (1 << 22) || N < 2 || N > 32768) return 0;
+  const Shape s = make_shape(m, d, N);
+  return make_layout(s, 0, 0, 0).total;
+}
+
+const char *rvea_status_str(rvea_status s) {
+  switch (s) {
+    case RVEA_OK: return "ok";
+    case RVEA_ERR_ARG: return "invalid argument";
+    case RVEA_ERR_LATTICE: return "N does not match the lattice size C(H+m-1, m-1)";
+    case RVEA_ERR_NOMEM: return "workspace or scratch too small";
+    case RVEA_ERR_CUDA: return "CUDA runtime error";
+    case RVEA_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case RVEA_ERR_STATE: return "invalid in the run's current state";
+    case RVEA_ERR_DEVICE: return "device-side index check failed";
+  }
+  return "unknown status";
+}
+
+rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t bytes,
+                         void *cuda_stream, rvea_run **out) {
+  if (!out) return RVEA_ERR_ARG;
+  const rvea_status v = validate(cfg);
+  if (v != RVEA_OK) return v;
+  if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255)) return RVEA_ERR_ARG;
+  const Shape sh = make_shape(cfg->m, cfg->d, cfg->N);
+  const Layout lay = make_layout(sh, 0, 0, 0);
+  if (bytes < lay.total) return RVEA_ERR_NOMEM;
+  std::call_once(g_attr_once, set_kernel_attrs);
+  if (g_attr_err != cudaSuccess) return RVEA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+  rvea_run *r = new (std::nothrow) rvea_run();
+  if (!r) return RVEA_ERR_NOMEM;
+  r->cfg = *cfg;
+  r->cfg.neuro = nullptr;
+  r->sh = sh;
+  r->lay = lay;
+  r->ws = static_cast<uint8_t *>(dev_workspace);
+  r->p_adapt = std::max(1, (int)std::floor(cfg->f_r * (double)cfg->t_max + 0.5));
+  r->t = 1;
+  cudaGetDevice(&r->device);
+  const char *ng = std::getenv("RVEA_NO_GRAPH");
+  r->use_graph = !(ng && ng[0] == '1');
+
+  RunDesc &D = r->hd;
+  std::memset(&D, 0, sizeof(D));
+  D.m = sh.m; D.m4 = sh.m4; D.d = sh.d; D.d_pad = sh.d_pad; D.G = sh.G;
+  D.N = sh.N; D.P = sh.P; D.n_comb = sh.n_comb; D.problem = cfg->problem;
+  D.t_max = cfg->t_max; D.p_adapt = r->p_adapt; D.team = sh.team; D.op_mode = 0;
+  D.L = (float)cfg->lower; D.U = (float)cfg->upper; D.alpha = (float)cfg->alpha;
+  D.inv_eta_c1 = (float)(1.0 / (cfg->eta_c + 1.0));
+  D.eta_m = (float)cfg->eta_m;
+  D.T_c = event_threshold24(cfg->p_c);
+  D.T_m = event_threshold24(cfg->p_m / (double)cfg->d);
+  D.key0 = (uint32_t)cfg->seed;
+  D.key1 = (uint32_t)(cfg->seed >> 32);
+  D.X = wsp<float>(r, lay.X);
+  D.F = wsp<float>(r, lay.F);
+  D.slotmap = wsp<int>(r, lay.slotmap);
+  D.vlist = wsp<int>(r, lay.vlist);
+  D.child_slot = wsp<int>(r, lay.child);
+  D.best = wsp<unsigned long long>(r, lay.best);
+  D.amax = wsp<unsigned long long>(r, lay.amax);
+  D.assoc = wsp<int>(r, lay.assoc);
+  D.surv = wsp<int>(r, lay.surv);
+  D.blk_cnt = wsp<int>(r, lay.blk);
+  D.V32 = wsp<float>(r, lay.V32);
+  D.V64 = wsp<double>(r, lay.V64);
+  D.V0 = wsp<double>(r, lay.V0);
+  D.gamma64 = wsp<double>(r, lay.g64);
+  D.gamma32 = wsp<float>(r, lay.g32);
+  D.ctl = wsp<Ctl>(r, lay.ctl);
+  r->d_desc = wsp<RunDesc>(r, lay.desc);
+
+  r->repro_smem = repro_smem_total(sh.team, sh.m, sh.G);
+  r->init_smem = sh.ppc * std::max(1, sh.m - 1) * 4;
+  r->sel_smem = 2 * kVTile * sh.m4 * 16;
+  r->fin_smem = sh.N * 4 + ((2 * sh.N + 3) & ~3);
+
+  // host tables
+  std::vector<ReproItem> rep(sh.n_repro), ini(sh.n_init);
+  for (int q = 0; q < sh.n_repro; ++q) rep[q].pair0 = q * sh.ppc;
+  for (int q = 0; q < sh.n_init; ++q) ini[q].pair0 = q * sh.ppc;
+  std::vector<SelItem> sel;
+  sel.reserve(sh.n_sel);
+  {
+    const int tiles = (sh.N + kVTile - 1) / kVTile;
+    const int nch = sh.n_sel / sh.nblk;
+    const int tpc = (tiles + nch - 1) / nch;
+    for (int b = 0; b < sh.nblk; ++b)
+      for (int c = 0; c < nch; ++c) {
+        SelItem it;
+        it.sblk = b;
+        it.v0 = std::min(sh.N, c * tpc * kVTile);
+        it.v1 = std::min(sh.N, (c + 1) * tpc * kVTile);
+        it.nchunks = nch;
+        sel.push_back(it);
+      }
+  }
+  std::vector<double> V0;
+  build_lattice(sh.m, cfg->H, sh.N, V0);
+  std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f);
+  for (int j = 0; j < sh.N; ++j)
+    for (int k = 0; k < sh.m; ++k) V32[(size_t)j * sh.m4 * 4 + k] = (float)V0[(size_t)j * sh.m + k];
+  Ctl c0;
+  std::memset(&c0, 0, sizeof(c0));
+  c0.t = 1;
+  c0.K = sh.N;
+  for (int k = 0; k < kMaxM; ++k) c0.zkey[k] = 0xFFFFFFFFu;
+
+  rvea_status s = RVEA_OK;
+  auto up = [&](size_t off, const void *src, size_t n) {
+    if (s == RVEA_OK && cudaMemcpyAsync(r->ws + off, src, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      s = RVEA_ERR_CUDA;
+  };
+  if (cudaMemsetAsync(r->ws, 0, lay.total, st) != cudaSuccess) s = RVEA_ERR_CUDA;
+  up(lay.desc, &D, sizeof(D));
+  up(lay.repro, rep.data(), rep.size() * sizeof(ReproItem));
+  up(lay.init, ini.data(), ini.size() * sizeof(ReproItem));
+  up(lay.sel, sel.data(), sel.size() * sizeof(SelItem));
+  up(lay.V0, V0.data(), V0.size() * 8);
+  up(lay.V64, V0.data(), V0.size() * 8);
+  up(lay.V32, V32.data(), V32.size() * 4);
+  up(lay.ctl, &c0, sizeof(c0));
+  if (s == RVEA_OK) {
+    static thread_local BatchDir d;
+    dir_single(d, r, wsp<ReproItem>(r, lay.init), sh.n_init);
+    k_init<<<sh.n_init, kReproThreads, r->init_smem, st>>>(d);
+    dir_single(d, r, nullptr, 1);
+    k_init_lists<<<dim3((sh.N + 255) / 256, 1), 256, 0, st>>>(d);
+    s = cuerr(cudaGetLastError());
+    if (s == RVEA_OK) s = launch_gamma_force(r, st);
+  }
+  // pageable host sources above must stay valid until their copies are done
+  if (s == RVEA_OK) s = cuerr(cudaStreamSynchronize(st));
+  if (s != RVEA_OK) {
+    delete r;
+    return s;
+  }
+  r->last_stream = st;
+  *out = r;
+  return RVEA_OK;
+}
+
+rvea_status rvea_init(int m, int d, int N, int H, double alpha, double f_r, double eta_c,
+                      double eta_m, uint64_t seed, int problem, int t_max, void *dev_workspace,
+                      size_t bytes, void *cuda_stream, rvea_run **out) {
+  rvea_config c;
+  std::memset(&c, 0, sizeof(c));
+  c.m = m; c.d = d; c.N = N; c.H = H; c.problem = problem; c.t_max = t_max;
+  c.alpha = alpha; c.f_r = f_r; c.eta_c = eta_c; c.eta_m = eta_m;
+  c.p_c = 1.0; c.p_m = 1.0; c.lower = 0.0; c.upper = 1.0; c.seed = seed;
+  c.neuro = nullptr;
+  if (problem == RVEA_NEURO_LINEAR) return RVEA_ERR_ARG;   // needs rvea_init_ex
+  return rvea_init_ex(&c, dev_workspace, bytes, cuda_stream, out);
+}
+
+rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
+  if (!r || G < 0) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  r->last_stream = st;
+  while (G > 0) {
+    const int p = r->p_adapt;
+    if (r->use_graph && p > 1 && G >= p && (r->t % p) == 1) {
+      rvea_status s = ensure_block_graph(r);
+      if (s != RVEA_OK) return s;
+      RV_TRY(cudaGraphLaunch(r->block_graph, st));
+      r->t += p;
+      G -= p;
+      r->has_last_gen = true;
+      continue;
+    }
+    const rvea_status s = enqueue_one(r, st);
+    if (s != RVEA_OK) return s;
+    r->t += 1;
+    G -= 1;
+    r->has_last_gen = true;
+  }
+  return RVEA_OK;
+}
+
+rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream) {
+  if (!runs || n_runs < 1 || n_runs > kMaxBatch) return RVEA_ERR_ARG;
+  for (int q = 0; q < n_runs; ++q) {
+    if (!runs[q]) return RVEA_ERR_ARG;
+    for (int u = 0; u < q; ++u)
+      if (runs[u] == runs[q]) return RVEA_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const rvea_status s = launch_generation(runs, n_runs, st, true);
+  if (s != RVEA_OK) return s;
+  for (int q = 0; q < n_runs; ++q) {
+    runs[q]->t += 1;
+    runs[q]->last_stream = st;
+    runs[q]->has_last_gen = true;
+  }
+  return RVEA_OK;
+}
+
+int rvea_generation(const rvea_run *r) { return r ? r->t : -1; }
+
+rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *phase_ms,
+                               int n_phases) {
+  if (!r || G < 0 || !phase_ms || n_phases < 4) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  r->last_stream = st;
+  for (int q = 0; q < n_phases; ++q) phase_ms[q] = 0.0;
+  if (G == 0) return RVEA_OK;
+  // events around every launch of every generation, on the launching stream
+  std::vector<cudaEvent_t> ev((size_t)G * 5);
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto &x : ev) if (x) cudaEventDestroy(x);
+      return RVEA_ERR_CUDA;
+    }
+  rvea_status s = RVEA_OK;
+  static thread_local BatchDir dr, ds, df, dg;
+  const rvea_run *one = r;
+  dir_single(dr, one, wsp<ReproItem>(r, r->lay.repro), r->sh.n_repro);
+  dir_single(ds, one, wsp<SelItem>(r, r->lay.sel), r->sh.n_sel);
+  dir_single(df, one, nullptr, 1);
+  dir_single(dg, one, nullptr, 1);
+  const int nbg = std::min((r->sh.N + 31) / 32, 4 * kSMs);
+  for (int g = 0; g < G && s == RVEA_OK; ++g) {
+    cudaEvent_t *e = &ev[(size_t)g * 5];
+    cudaEventRecord(e[0], st);
+    k_repro<<<r->sh.n_repro, kReproThreads, r->repro_smem, st>>>(dr);
+    cudaEventRecord(e[1], st);
+    k_select<<<r->sh.n_sel, kSelThreads, r->sel_smem, st>>>(ds);
+    cudaEventRecord(e[2], st);
+    k_finalize<<<1, kFinThreads, r->fin_smem, st>>>(df);
+    cudaEventRecord(e[3], st);
+    if (r->t % r->p_adapt == 0) k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
+    cudaEventRecord(e[4], st);
+    s = cuerr(cudaGetLastError());
+    r->t += 1;
+    r->has_last_gen = true;
+  }
+  if (s == RVEA_OK) s = cuerr(cudaStreamSynchronize(st));
+  for (int g = 0; g < G && s == RVEA_OK; ++g) {
+    const cudaEvent_t *e = &ev[(size_t)g * 5];
+    for (int q = 0; q < 4; ++q) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e[q], e[q + 1]) != cudaSuccess) { s = RVEA_ERR_CUDA; break; }
+      phase_ms[q] += ms;
+    }
+  }
+  for (auto &x : ev) cudaEventDestroy(x);
+  return s;
+}
+
+rvea_status rvea_population(const rvea_run *r, float *dst, uint8_t *valid, void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const Shape &sh = r->sh;
+  float *dx = dev_addr(dst) ? static_cast<float *>(dev_addr(dst)) : nullptr;
+  uint8_t *dv = dev_addr(valid) ? static_cast<uint8_t *>(dev_addr(valid)) : nullptr;
+  if ((dst && !dx) || (valid && !dv)) {
+    // pageable destination: flags and slot map through the staging area,
+    // rows one copy each
+    uint8_t *sv = wsp<uint8_t>(r, r->lay.stage);
+    k_gather_pop<<<sh.N, 256, 0, st>>>(r->d_desc, nullptr, sv);
+    RV_TRY(cudaGetLastError());
+    std::vector<int> map(sh.N);
+    RV_TRY(cudaMemcpyAsync(map.data(), r->hd.slotmap, sh.N * 4, cudaMemcpyDeviceToHost, st));
+    RV_TRY(cudaStreamSynchronize(st));
+    if (valid) {
+      for (int j = 0; j < sh.N; ++j) valid[j] = map[j] >= 0 ? 1 : 0;
+    }
+    if (dst) {
+      for (int j = 0; j < sh.N; ++j) {
+        float *o = dst + (size_t)j * sh.d;
+        if (map[j] < 0) {
+          for (int k = 0; k < sh.d; ++k) o[k] = std::nanf("");
+        } else {
+          RV_TRY(cudaMemcpy(o, r->hd.X + (size_t)map[j] * sh.d_pad, sh.d * 4, cudaMemcpyDeviceToHost));
+        }
+      }
+    }
+    return RVEA_OK;
+  }
+  k_gather_pop<<<sh.N, 256, 0, st>>>(r->d_desc, dx, dv);
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_objectives(const rvea_run *r, float *dst, uint8_t *valid, void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const Shape &sh = r->sh;
+  float *dx = static_cast<float *>(dev_addr(dst));
+  uint8_t *dv = static_cast<uint8_t *>(dev_addr(valid));
+  if ((dst && !dx) || (valid && !dv)) {
+    float *sf = wsp<float>(r, r->lay.stage);
+    uint8_t *sv = reinterpret_cast<uint8_t *>(sf + (size_t)sh.N * sh.m);
+    k_gather_obj<<<(sh.N + 255) / 256, 256, 0, st>>>(r->d_desc, sf, sv);
+    RV_TRY(cudaGetLastError());
+    if (dst) RV_TRY(cudaMemcpyAsync(dst, sf, (size_t)sh.N * sh.m * 4, cudaMemcpyDeviceToHost, st));
+    if (valid) RV_TRY(cudaMemcpyAsync(valid, sv, sh.N, cudaMemcpyDeviceToHost, st));
+    return RVEA_OK;
+  }
+  k_gather_obj<<<(sh.N + 255) / 256, 256, 0, st>>>(r->d_desc, dx, dv);
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_export_state(const rvea_run *r, float *X, float *F, uint8_t *valid, double *V,
+                              double *gamma, void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  rvea_status s = RVEA_OK;
+  if (X || valid) s = rvea_population(r, X, valid, cuda_stream);
+  if (s == RVEA_OK && F) s = rvea_objectives(r, F, nullptr, cuda_stream);
+  if (s != RVEA_OK) return s;
+  const size_t nv = (size_t)r->sh.N * r->sh.m * 8;
+  if (V) RV_TRY(cudaMemcpyAsync(V, r->hd.V64, nv, cudaMemcpyDefault, st));
+  if (gamma) RV_TRY(cudaMemcpyAsync(gamma, r->hd.gamma64, (size_t)r->sh.N * 8, cudaMemcpyDefault, st));
+  return RVEA_OK;
+}
+
+rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const uint8_t *valid,
+                              const double *V, const double *gamma, int t, void *cuda_stream) {
+  if (!r || !X || !F || !valid || !V || !gamma || t < 1) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const Shape &sh = r->sh;
+  float *sf = wsp<float>(r, r->lay.stage);
+  uint8_t *sv = reinterpret_cast<uint8_t *>(sf + (size_t)sh.N * sh.m);
+  RV_TRY(cudaMemcpy2DAsync(r->hd.X, (size_t)sh.d_pad * 4, X, (size_t)sh.d * 4, (size_t)sh.d * 4,
+                           sh.N, cudaMemcpyDefault, st));
+  RV_TRY(cudaMemcpyAsync(sf, F, (size_t)sh.N * sh.m * 4, cudaMemcpyDefault, st));
+  RV_TRY(cudaMemcpyAsync(sv, valid, sh.N, cudaMemcpyDefault, st));
+  RV_TRY(cudaMemcpyAsync(r->hd.V64, V, (size_t)sh.N * sh.m * 8, cudaMemcpyDefault, st));
+  RV_TRY(cudaMemcpyAsync(r->hd.gamma64, gamma, (size_t)sh.N * 8, cudaMemcpyDefault, st));
+  k_import<<<1, kFinThreads, 0, st>>>(r->d_desc, sf, sv, t);
+  RV_TRY(cudaGetLastError());
+  RV_TRY(cudaStreamSynchronize(st));
+  r->t = t;
+  r->last_stream = st;
+  r->has_last_gen = false;
+  return RVEA_OK;
+}
+
+rvea_status rvea_offspring(const rvea_run *r, float *X, float *F, void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  if (!r->has_last_gen) return RVEA_ERR_STATE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  float *dx = static_cast<float *>(dev_addr(X));
+  float *df = static_cast<float *>(dev_addr(F));
+  if ((X && !dx) || (F && !df)) return RVEA_ERR_ARG;   // device or pinned memory only
+  k_gather_children<<<r->sh.N, 256, 0, st>>>(r->d_desc, dx, df);
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_last_selection(const rvea_run *r, int32_t *assoc, int32_t *survivor,
+                                void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  if (!r->has_last_gen) return RVEA_ERR_STATE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int *da = static_cast<int *>(dev_addr(assoc));
+  int *ds = static_cast<int *>(dev_addr(survivor));
+  if ((assoc && !da) || (survivor && !ds)) return RVEA_ERR_ARG;
+  k_copy_selection<<<(r->sh.n_comb + 255) / 256, 256, 0, st>>>(r->d_desc, da, ds);
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_sync_status(rvea_run *r) {
+  if (!r) return RVEA_ERR_ARG;
+  if (cudaStreamSynchronize(r->last_stream) != cudaSuccess) return RVEA_ERR_CUDA;
+  int status = 0;
+  if (cudaMemcpy(&status, &r->hd.ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RVEA_ERR_CUDA;
+  if (status & ST_TIMEOUT) return RVEA_ERR_TIMEOUT;
+  if (status & ST_BADINDEX) return RVEA_ERR_DEVICE;
+  return RVEA_OK;
+}
+
+void rvea_free(rvea_run *r) {
+  if (!r) return;
+  if (r->block_graph) cudaGraphExecDestroy(r->block_graph);
+  if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
+  delete r;
+}
+
+// ---- stateless operators --------------------------------------------------
+
+namespace {
+struct OpLayout {
+  size_t ctl, desc, best, amax, blk, items, total;
+};
+OpLayout op_layout(int n, int r) {
+  OpLayout L;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t at = o;
+    o = align256(o + b);
+    return at;
+  };
+  const int nblk = (n + kSelThreads - 1) / kSelThreads;
+  const int tiles = (r + kVTile - 1) / kVTile;
+  L.ctl = take(sizeof(Ctl));
+  L.desc = take(sizeof(RunDesc));
+  L.best = take((size_t)r * 8);
+  L.amax = take((size_t)n * 8);
+  L.blk = take((size_t)nblk * 4);
+  L.items = take((size_t)nblk * tiles * sizeof(SelItem));
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t rvea_select_scratch_bytes(int n, int r, int m) {
+  if (n < 1 || r < 1 || m < 2 || m > kMaxM) return 0;
+  return op_layout(n, r).total + (size_t)r * kMaxM * 16;   // + padded V copy
+}
+
+rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid, int r,
+                        const float *V, const float *gamma, int t, int t_max, float alpha,
+                        int32_t *assoc, int32_t *survivor, void *scratch, size_t scratch_bytes,
+                        void *cuda_stream) {
+  if (m < 2 || m > kMaxM || n < 1 || r < 1 || !F || !V || !gamma || !assoc || !survivor ||
+      !scratch || t_max < 1 || !(alpha > 0.0f))
+    return RVEA_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(scratch) & 255) return RVEA_ERR_ARG;
+  if (scratch_bytes < rvea_select_scratch_bytes(n, r, m)) return RVEA_ERR_NOMEM;
+  std::call_once(g_attr_once, set_kernel_attrs);
+  if (g_attr_err != cudaSuccess) return RVEA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const OpLayout L = op_layout(n, r);
+  uint8_t *ws = static_cast<uint8_t *>(scratch);
+  const int m4 = (m + 3) / 4;
+  float *V32 = reinterpret_cast<float *>(ws + L.total);
+  // zero-padded float4 rows of V
+  RV_TRY(cudaMemsetAsync(V32, 0, (size_t)r * m4 * 16, st));
+  RV_TRY(cudaMemcpy2DAsync(V32, (size_t)m4 * 16, V, (size_t)m * 4, (size_t)m * 4, r,
+                           cudaMemcpyDeviceToDevice, st));
+  RunDesc D;
+  std::memset(&D, 0, sizeof(D));
+  D.m = m; D.m4 = m4; D.N = r; D.n_comb = n; D.t_max = t_max; D.alpha = alpha;
+  D.op_mode = 1; D.t_op = t;
+  D.best = reinterpret_cast<unsigned long long *>(ws + L.best);
+  D.amax = reinterpret_cast<unsigned long long *>(ws + L.amax);
+  D.blk_cnt = reinterpret_cast<int *>(ws + L.blk);
+  D.assoc = assoc;
+  D.V32 = V32;
+  D.gamma32 = const_cast<float *>(gamma);
+  D.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+  D.F_aos = F;
+  D.valid_in = valid;
+  D.survivor_out = survivor;
+  // items: every solution block x every tile-sized vector chunk
+  const int nblk = (n + kSelThreads - 1) / kSelThreads;
+  const int tiles = (r + kVTile - 1) / kVTile;
+  int nch = std::max(1, std::min(tiles, (4 * kSMs + nblk - 1) / nblk));
+  const int tpc = (tiles + nch - 1) / nch;
+  nch = (tiles + tpc - 1) / tpc;
+  std::vector<SelItem> items;
+  items.reserve((size_t)nblk * nch);
+  for (int b = 0; b < nblk; ++b)
+    for (int c = 0; c < nch; ++c)
+      items.push_back(SelItem{b, std::min(r, c * tpc * kVTile), std::min(r, (c + 1) * tpc * kVTile), nch});
+  RunDesc *dD = reinterpret_cast<RunDesc *>(ws + L.desc);
+  RV_TRY(cudaMemcpyAsync(dD, &D, sizeof(D), cudaMemcpyHostToDevice, st));
+  RV_TRY(cudaMemcpyAsync(ws + L.items, items.data(), items.size() * sizeof(SelItem),
+                         cudaMemcpyHostToDevice, st));
+  k_op_prep<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, st>>>(dD);
+  k_op_zstar<<<(n + 255) / 256, 256, 0, st>>>(dD);
+  static thread_local BatchDir d;
+  d.n = 1;
+  d.prefix[0] = 0;
+  d.prefix[1] = (int)items.size();
+  d.desc[0] = dD;
+  d.items[0] = ws + L.items;
+  k_select<<<(unsigned)items.size(), kSelThreads, 2 * kVTile * m4 * 16, st>>>(d);
+  k_op_finish<<<(r + 255) / 256, 256, 0, st>>>(dD);
+  // the pageable host sources of the two copies above were staged before
+  // cudaMemcpyAsync returned, so nothing here waits for the stream
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_gamma(int m, int r, const double *V, double *gamma, void *cuda_stream) {
+  if (m < 2 || m > kMaxM || r < 2 || !V || !gamma) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // the descriptor travels in the kernel parameter block: no scratch needed
+  RunDesc D;
+  std::memset(&D, 0, sizeof(D));
+  D.m = m;
+  D.N = r;
+  D.V64 = const_cast<double *>(V);
+  D.gamma64 = gamma;
+  D.gamma32 = nullptr;
+  const int nb = (r + 31) / 32;
+  k_gamma_op<<<nb, 256, 0, st>>>(D);
+  return cuerr(cudaGetLastError());
+}
+
+}  // extern "C"

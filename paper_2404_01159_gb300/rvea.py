@@ -1,0 +1,221 @@
+"""Python binding of the RVEA library: torch owns the device memory and the
+streams, the CUDA library does every step of every generation.
+
+    run = Run(m=3, d=5000, N=9870, H=139, problem=DTLZ1_LINEAR, t_max=1000)
+    run.step(1000)
+    F, valid = run.objectives()
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, NEURO_LINEAR, Config, NeuroDynamics,
+                      RveaError, check, lib)
+
+__all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
+           "DTLZ2_SPHERE", "DTLZ1_LINEAR", "NEURO_LINEAR", "lattice_size"]
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def lattice_size(m: int, H: int) -> int:
+    from math import comb
+    return comb(H + m - 1, m - 1)
+
+
+def workspace_bytes(m: int, d: int, N: int) -> int:
+    return int(lib().rvea_workspace_bytes(m, d, N))
+
+
+class Run:
+    """One optimisation run whose state stays resident on the device."""
+
+    def __init__(self, m: int, d: int, N: int, H: int, problem: int = DTLZ2_SPHERE,
+                 t_max: int = 100, alpha: float = 2.0, f_r: float = 0.1,
+                 eta_c: float = 20.0, eta_m: float = 20.0, p_c: float = 1.0,
+                 p_m: float = 1.0, lower: Optional[float] = None,
+                 upper: Optional[float] = None, seed: int = 0, neuro=None,
+                 device=None, stream=None):
+        self.device = torch.device("cuda" if device is None else device)
+        if lower is None:
+            lower = -1.0 if problem == NEURO_LINEAR else 0.0
+        if upper is None:
+            upper = 1.0
+        self.m, self.d, self.N, self.H = m, d, N, H
+        self.problem, self.t_max = problem, t_max
+        L = lib()
+        nbytes = int(L.rvea_workspace_bytes(m, d, N))
+        if nbytes == 0:
+            raise RveaError(-1, "rvea_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self._ws_raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self.workspace_nbytes = nbytes
+        cfg = Config(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
+                     lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None)
+        self._neuro_keep = None
+        if neuro is not None:
+            A = np.ascontiguousarray(neuro["A"], dtype=np.float64)
+            B = np.ascontiguousarray(neuro["B"], dtype=np.float64)
+            nd = NeuroDynamics(A.shape[0], B.shape[1], neuro.get("h1", 64), neuro.get("h2", 64),
+                               neuro.get("steps", 1000), neuro.get("sigma", 0.01),
+                               A.ctypes.data_as(C.POINTER(C.c_double)),
+                               B.ctypes.data_as(C.POINTER(C.c_double)))
+            self._neuro_keep = (A, B, nd)
+            cfg.neuro = C.pointer(nd)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(L.rvea_init_ex(C.byref(cfg), C.c_void_p(self._ws_ptr), nbytes,
+                                 C.c_void_p(_stream(stream)), C.byref(self._h)), "rvea_init_ex")
+
+    # -- lifetime ------------------------------------------------------------
+    def free(self) -> None:
+        if self._h:
+            lib().rvea_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def t(self) -> int:
+        """Index of the next generation (1 after initialisation)."""
+        return int(lib().rvea_generation(self._h))
+
+    # -- generations ---------------------------------------------------------
+    def step(self, generations: int = 1, stream=None) -> None:
+        check(lib().rvea_step(self._h, int(generations), C.c_void_p(_stream(stream))), "rvea_step")
+
+    def step_profiled(self, generations: int, stream=None):
+        """Run generations with per-kernel CUDA events; returns the summed
+        device milliseconds of (reproduction, selection, finalize, gamma)."""
+        ms = (C.c_double * 4)()
+        check(lib().rvea_step_profiled(self._h, int(generations), C.c_void_p(_stream(stream)),
+                                       ms, 4), "rvea_step_profiled")
+        return [float(x) for x in ms]
+
+    def sync_status(self) -> None:
+        check(lib().rvea_sync_status(self._h), "device status")
+
+    # -- results -------------------------------------------------------------
+    def population(self, out: Optional[torch.Tensor] = None, valid: Optional[torch.Tensor] = None,
+                   stream=None):
+        if out is None:
+            out = torch.empty((self.N, self.d), dtype=torch.float32, device=self.device)
+        if valid is None:
+            valid = torch.empty(self.N, dtype=torch.uint8, device=self.device)
+        check(lib().rvea_population(self._h, _ptr(out), _ptr(valid), C.c_void_p(_stream(stream))),
+              "rvea_population")
+        return out, valid
+
+    def objectives(self, out: Optional[torch.Tensor] = None, valid: Optional[torch.Tensor] = None,
+                   stream=None):
+        if out is None:
+            out = torch.empty((self.N, self.m), dtype=torch.float32, device=self.device)
+        if valid is None:
+            valid = torch.empty(self.N, dtype=torch.uint8, device=self.device)
+        check(lib().rvea_objectives(self._h, _ptr(out), _ptr(valid), C.c_void_p(_stream(stream))),
+              "rvea_objectives")
+        return out, valid
+
+    def export_state(self, stream=None) -> dict:
+        dev = self.device
+        X = torch.empty((self.N, self.d), dtype=torch.float32, device=dev)
+        F = torch.empty((self.N, self.m), dtype=torch.float32, device=dev)
+        valid = torch.empty(self.N, dtype=torch.uint8, device=dev)
+        V = torch.empty((self.N, self.m), dtype=torch.float64, device=dev)
+        g = torch.empty(self.N, dtype=torch.float64, device=dev)
+        check(lib().rvea_export_state(self._h, _ptr(X), _ptr(F), _ptr(valid), _ptr(V), _ptr(g),
+                                      C.c_void_p(_stream(stream))), "rvea_export_state")
+        return dict(X=X, F=F, valid=valid, V=V, gamma=g, t=self.t)
+
+    def import_state(self, X, F, valid, V, gamma, t: int, stream=None) -> None:
+        dev = self.device
+        X = torch.as_tensor(X, dtype=torch.float32, device=dev).contiguous()
+        F = torch.as_tensor(F, dtype=torch.float32, device=dev).contiguous()
+        valid = torch.as_tensor(valid, dtype=torch.uint8, device=dev).contiguous()
+        V = torch.as_tensor(V, dtype=torch.float64, device=dev).contiguous()
+        gamma = torch.as_tensor(gamma, dtype=torch.float64, device=dev).contiguous()
+        check(lib().rvea_import_state(self._h, _ptr(X), _ptr(F), _ptr(valid), _ptr(V),
+                                      _ptr(gamma), int(t), C.c_void_p(_stream(stream))),
+              "rvea_import_state")
+
+    def offspring(self, stream=None):
+        X = torch.empty((self.N, self.d), dtype=torch.float32, device=self.device)
+        F = torch.empty((self.N, self.m), dtype=torch.float32, device=self.device)
+        check(lib().rvea_offspring(self._h, _ptr(X), _ptr(F), C.c_void_p(_stream(stream))),
+              "rvea_offspring")
+        return X, F
+
+    def last_selection(self, stream=None):
+        assoc = torch.empty(2 * self.N, dtype=torch.int32, device=self.device)
+        surv = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        check(lib().rvea_last_selection(self._h, _ptr(assoc), _ptr(surv),
+                                        C.c_void_p(_stream(stream))), "rvea_last_selection")
+        return assoc, surv
+
+
+def step_batch(runs: Sequence[Run], stream=None) -> None:
+    """One generation of every run in `runs`, one launch per phase."""
+    arr = (C.c_void_p * len(runs))(*[r.handle.value for r in runs])
+    check(lib().rvea_step_batch(arr, len(runs), C.c_void_p(_stream(stream))), "rvea_step_batch")
+
+
+def select(F: torch.Tensor, valid: Optional[torch.Tensor], V: torch.Tensor, gam: torch.Tensor,
+           t: int, t_max: int, alpha: float, scratch: Optional[torch.Tensor] = None, stream=None):
+    """Environmental selection (Algorithm 1) of n solutions against r vectors.
+
+    F (n, m) float32, valid (n,) uint8 or None, V (r, m) float32 unit rows,
+    gam (r,) float32 -> (assoc (n,) int32, survivor (r,) int32)."""
+    n, m = F.shape
+    r = V.shape[0]
+    dev = F.device
+    F = F.contiguous().float()
+    V = V.contiguous().float()
+    gam = gam.contiguous().float()
+    if valid is not None:
+        valid = valid.contiguous().to(torch.uint8)
+    need = int(lib().rvea_select_scratch_bytes(n, r, m))
+    if scratch is None:
+        raw = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        sp = (raw.data_ptr() + 255) & ~255
+    else:
+        raw = scratch
+        sp = scratch.data_ptr()
+    assoc = torch.empty(n, dtype=torch.int32, device=dev)
+    surv = torch.empty(r, dtype=torch.int32, device=dev)
+    check(lib().rvea_select(m, n, _ptr(F), _ptr(valid), r, _ptr(V), _ptr(gam), int(t),
+                            int(t_max), float(alpha), _ptr(assoc), _ptr(surv), C.c_void_p(sp),
+                            need, C.c_void_p(_stream(stream))), "rvea_select")
+    torch.cuda.current_stream(dev).synchronize() if stream is None else None
+    del raw
+    return assoc, surv
+
+
+def gamma(V: torch.Tensor, stream=None) -> torch.Tensor:
+    """Minimum angle from each unit row of V (r, m) float64 to the others."""
+    V = V.contiguous().double()
+    r, m = V.shape
+    g = torch.empty(r, dtype=torch.float64, device=V.device)
+    check(lib().rvea_gamma(m, r, _ptr(V), _ptr(g), C.c_void_p(_stream(stream))), "rvea_gamma")
+    return g

@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI boundary: the library builds for sm_103a, loads,
+exports every function that include/rvea.h declares, and rejects invalid
+arguments before touching a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rvea.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rvea_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2404_01159_gb300 import _native
+    return _native
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["rvea_workspace_bytes", "rvea_init", "rvea_step", "rvea_step_batch",
+                     "rvea_population", "rvea_objectives", "rvea_sync_status", "rvea_free",
+                     "rvea_status_str"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    native.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", native.lib_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(rvea_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_workspace_sizes(native):
+    L = native.lib()
+    b1 = L.rvea_workspace_bytes(3, 5000, 9870)
+    # the pool (2N rows of d floats) dominates
+    assert 2 * 9870 * 5000 * 4 <= b1 < 2 * 9870 * 5000 * 4 * 1.02
+    assert L.rvea_workspace_bytes(1, 10, 10) == 0
+    assert L.rvea_workspace_bytes(3, 2, 10) == 0
+    assert L.rvea_workspace_bytes(3, 12, 40000) == 0
+
+
+def test_status_strings(native):
+    L = native.lib()
+    for s in range(0, -8, -1):
+        assert L.rvea_status_str(s)
+    assert b"lattice" in L.rvea_status_str(native.ERR_LATTICE)
+
+
+def test_init_rejects_bad_arguments_without_gpu(native):
+    L = native.lib()
+    h = C.c_void_p()
+    ws = C.c_void_p(1 << 20)   # never dereferenced: validation fails first
+
+    def init(m, d, N, H, t_max=100, alpha=2.0, f_r=0.1, eta=20.0, problem=0):
+        return L.rvea_init(m, d, N, H, alpha, f_r, eta, eta, 0, problem, t_max, ws,
+                           1 << 30, None, C.byref(h))
+    assert init(3, 12, 100, 13) == native.ERR_LATTICE
+    assert init(1, 12, 105, 13) == native.ERR_ARG
+    assert init(3, 2, 105, 13) == native.ERR_ARG
+    assert init(3, 12, 105, 13, t_max=0) == native.ERR_ARG
+    assert init(3, 12, 105, 13, f_r=1.5) == native.ERR_ARG
+    assert init(3, 12, 105, 13, eta=0.0) == native.ERR_ARG
+    assert init(3, 12, 105, 13, problem=7) == native.ERR_ARG
+    assert not h.value

@@ -1,0 +1,238 @@
+"""GPU <-> oracle parity of the CUDA path, called through the C ABI.
+
+Every case compares the CUDA library with the FP64 oracle on the same seeded
+inputs, element by element, under the tolerances of tests/gpu_util.py.
+Sizes span several CTAs / tiles with ragged tails; the full-size case runs
+the 9870 x 5000 DTLZ1 workload in the launch configuration bench.py times.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import (assert_children, assert_objectives, igd, make_run, params,  # noqa: E402
+                      selection_mismatches, to_np)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_01159_gb300 import _native
+    _native.lib()
+
+
+# (m, d, N, H, problem): cfg0 shape, a ragged DTLZ1 case spanning several
+# reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10.
+SHAPES = [
+    (3, 12, 105, 13, 0),
+    (3, 1001, 210, 19, 1),
+    (2, 203, 100, 99, 0),
+    (5, 77, 126, 5, 1),
+    (10, 30, 220, 3, 0),
+    (3, 3, 105, 13, 1),
+    (3, 300, 1275, 49, 0),
+]
+
+
+def _state_to_oracle(orc, st):
+    s = to_np(st)
+    return orc.State(s["X"].astype(np.float64), s["F"].astype(np.float64), s["valid"],
+                     s["V"], s["gamma"], s["t"])
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_init_matches_oracle(orc, shape):
+    m, d, N, H, prob = shape
+    p = params(orc, m, d, N, H, prob, seed=11)
+    run = make_run(p)
+    st = to_np(run.export_state())
+    X0 = orc.init_population(p)
+    assert np.array_equal(st["X"].astype(np.float64), X0)        # bit-exact
+    assert_objectives(st["F"], orc.evaluate(p, X0))
+    V0 = orc.lattice_unit(orc.lattice(m, H))
+    assert np.array_equal(st["V"], V0)                            # bit-exact lattice
+    assert np.allclose(st["gamma"], orc.gamma(V0), rtol=1e-10, atol=0)
+    assert st["valid"].all() and st["t"] == 1
+    run.sync_status()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_teacher_forced_generations(orc, shape):
+    m, d, N, H, prob = shape
+    p = params(orc, m, d, N, H, prob, t_max=40, seed=5)        # adapts every 4th gen
+    V0 = orc.lattice_unit(orc.lattice(m, H))
+    run = make_run(p)
+    for gen in range(9):
+        st = run.export_state()
+        ost = _state_to_oracle(orc, st)
+        t = ost.t
+        Fpar = ost.F.copy()
+        vpar = ost.valid.copy()
+        out = orc.generation(p, V0, ost)
+        run.step(1)
+        gx, gf = run.offspring()
+        ga, gsurv = run.last_selection()
+        gx, gf = gx.cpu().numpy(), gf.cpu().numpy()
+        assert_children(gx, out["Xchild"], p.L, p.U)
+        assert_objectives(gf, out["Fchild"])
+        # the oracle's evaluation of the GPU's own children isolates the
+        # float32 objective arithmetic
+        assert_objectives(gf, orc.evaluate(p, gx.astype(np.float64), t), rtol=2e-6)
+        Fc = np.concatenate([np.nan_to_num(Fpar), out["Fchild"]])
+        vc = np.concatenate([vpar, np.ones(N, np.uint8)])
+        o = orc.select(Fc, vc, to_np(st)["V"], to_np(st)["gamma"], t, p.t_max, p.alpha)
+        assert np.array_equal(o["survivor"], out["survivor"])
+        bad_a, bad_s = selection_mismatches(Fc, vc, to_np(st)["V"], ga.cpu().numpy(),
+                                            gsurv.cpu().numpy(), o, tie_rel=1e-5)
+        assert not bad_a and not bad_s, (gen, bad_a[:5], bad_s[:5])
+        # the adapted reference vectors and gamma follow the GPU's survivors
+        nst = to_np(run.export_state())
+        assert nst["t"] == t + 1
+        if t % orc.adapt_period(p) == 0:
+            rng = orc.objective_range(nst["F"].astype(np.float64), nst["valid"])
+            Vw = orc.adapt(V0, rng)
+            assert np.allclose(nst["V"], Vw, rtol=0, atol=1e-15)
+            assert np.allclose(nst["gamma"], orc.gamma(Vw), rtol=1e-10, atol=0)
+        else:
+            assert np.array_equal(nst["V"], to_np(st)["V"])
+    run.sync_status()
+
+
+@pytest.mark.parametrize("m,n,r,seed", [(3, 700, 1300, 0), (2, 257, 100, 1), (5, 1000, 126, 2),
+                                        (7, 300, 600, 3), (10, 513, 220, 4), (3, 1, 5, 5)])
+def test_select_operator(orc, m, n, r, seed):
+    from paper_2404_01159_gb300 import select
+    rng = np.random.default_rng(seed)
+    F32 = (rng.uniform(0, 2, (n, m)) ** 2).astype(np.float32)
+    valid = (rng.uniform(size=n) > 0.1).astype(np.uint8)
+    valid[0] = 1
+    V = np.abs(rng.normal(size=(r, m)))
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    V32 = V.astype(np.float32)
+    V64 = V32.astype(np.float64)
+    gam = orc.gamma(V64)
+    gam32 = gam.astype(np.float32)
+    for t in (1, 7, 10):
+        ga, gs = select(torch.tensor(F32, device="cuda"), torch.tensor(valid, device="cuda"),
+                        torch.tensor(V32, device="cuda"), torch.tensor(gam32, device="cuda"),
+                        t, 10, 2.0)
+        o = orc.select(F32.astype(np.float64), valid, V64, gam32.astype(np.float64), t, 10, 2.0)
+        bad_a, bad_s = selection_mismatches(F32.astype(np.float64), valid, V64,
+                                            ga.cpu().numpy(), gs.cpu().numpy(), o)
+        assert not bad_a and not bad_s, (t, bad_a[:5], bad_s[:5])
+
+
+def test_select_operator_ties_and_ideal_point(orc):
+    from paper_2404_01159_gb300 import select
+    # duplicated solutions (exact APD ties: lower index wins) and a solution at z*
+    F = np.array([[0.0, 0.0], [1.0, 0.5], [1.0, 0.5], [0.25, 2.0], [0.25, 2.0]], np.float32)
+    V = np.array([[1.0, 0.0], [0.0, 1.0], [0.6, 0.8], [0.8, 0.6]], np.float32)
+    V64 = V.astype(np.float64)
+    gam = orc.gamma(V64).astype(np.float32)
+    ga, gs = select(torch.tensor(F, device="cuda"), None, torch.tensor(V, device="cuda"),
+                    torch.tensor(gam, device="cuda"), 3, 10, 2.0)
+    o = orc.select(F.astype(np.float64), None, V64, gam.astype(np.float64), 3, 10, 2.0)
+    assert np.array_equal(ga.cpu().numpy(), o["assoc"])
+    assert np.array_equal(gs.cpu().numpy(), o["survivor"])
+    assert gs.cpu().numpy()[0] == 0
+
+
+@pytest.mark.parametrize("m,H", [(3, 13), (2, 99), (5, 5), (10, 3), (3, 139)])
+def test_gamma_operator(orc, m, H):
+    from paper_2404_01159_gb300 import gamma
+    V0 = orc.lattice_unit(orc.lattice(m, H))
+    for V in (V0, orc.adapt(V0, np.linspace(0.5, 3.0, m))):
+        g = gamma(torch.tensor(V, device="cuda")).cpu().numpy()
+        assert np.allclose(g, orc.gamma(V), rtol=1e-10, atol=0)
+
+
+def test_free_running_quality_dtlz2(orc):
+    p = params(orc, 3, 12, 105, 13, 0, t_max=100, seed=3)
+    run = make_run(p)
+    run.step(100)
+    F, valid = run.objectives()
+    F, valid = F.cpu().numpy(), valid.cpu().numpy().astype(bool)
+    front = orc.lattice_unit(orc.lattice(3, 30))
+    assert valid.sum() >= 90
+    assert igd(F[valid].astype(np.float64), front) < 0.1
+    run.sync_status()
+
+
+def test_checkpoint_roundtrip_bit_identical(orc):
+    p = params(orc, 3, 1001, 210, 19, 1, t_max=40, seed=9)
+    a = make_run(p)
+    a.step(7)
+    st = a.export_state()
+    b = make_run(params(orc, 3, 1001, 210, 19, 1, t_max=40, seed=9))
+    b.import_state(st["X"], st["F"], st["valid"], st["V"], st["gamma"], st["t"])
+    a.step(6)
+    b.step(6)
+    sa, sb = to_np(a.export_state()), to_np(b.export_state())
+    for k in ("X", "F", "valid", "V", "gamma"):
+        assert np.array_equal(sa[k], sb[k], equal_nan=True), k
+    assert sa["t"] == sb["t"] == 14
+
+
+def test_graph_replay_equals_direct_launches(orc):
+    p = params(orc, 3, 12, 105, 13, 0, t_max=100, seed=4)   # adaptation period 10
+    a, b = make_run(p), make_run(p)
+    a.step(35)                        # graph replays of whole periods
+    for _ in range(35):
+        b.step(1)                     # one generation per call
+    sa, sb = to_np(a.export_state()), to_np(b.export_state())
+    for k in ("X", "F", "valid", "V", "gamma"):
+        assert np.array_equal(sa[k], sb[k], equal_nan=True), k
+
+
+def test_batch_equals_alone(orc):
+    from paper_2404_01159_gb300 import step_batch
+    shapes = [(3, 12, 105, 13, 0, 1), (3, 1001, 210, 19, 1, 2), (10, 30, 220, 3, 0, 3),
+              (2, 203, 100, 99, 1, 4)]
+    ps = [params(orc, m, d, N, H, pr, t_max=30, seed=s) for (m, d, N, H, pr, s) in shapes]
+    alone = [make_run(p) for p in ps]
+    batch = [make_run(p) for p in ps]
+    for _ in range(12):
+        for r in alone:
+            r.step(1)
+        step_batch(batch)
+    for ra, rb in zip(alone, batch):
+        sa, sb = to_np(ra.export_state()), to_np(rb.export_state())
+        for k in ("X", "F", "valid", "V", "gamma"):
+            assert np.array_equal(sa[k], sb[k], equal_nan=True), k
+        rb.sync_status()
+
+
+def test_full_size_dtlz1_sampled(orc):
+    """The 9870 x 5000 DTLZ1 workload of the benchmark, one teacher-forced
+    generation at full size: every objective, a sample of child rows, and the
+    whole selection."""
+    import os
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        m, d, N, H = 3, 5000, 9870, 139
+        p = params(orc, m, d, N, H, 1, t_max=1000, seed=0)
+        run = make_run(p)
+        run.step(2)
+        st = run.export_state()
+        ost = _state_to_oracle(orc, st)
+        t = ost.t
+        Fpar, vpar = ost.F.copy(), ost.valid.copy()
+        V0 = orc.lattice_unit(orc.lattice(m, H))
+        out = orc.generation(p, V0, ost)
+        run.step(1)
+        gx, gf = run.offspring()
+        ga, gs = run.last_selection()
+        rows = np.random.default_rng(0).choice(N, 64, replace=False)
+        assert_children(gx[rows].cpu().numpy(), out["Xchild"][rows])
+        assert_objectives(gf.cpu().numpy(), out["Fchild"])
+        Fc = np.concatenate([np.nan_to_num(Fpar), out["Fchild"]])
+        vc = np.concatenate([vpar, np.ones(N, np.uint8)])
+        o = orc.select(Fc, vc, to_np(st)["V"], to_np(st)["gamma"], t, p.t_max, p.alpha)
+        bad_a, bad_s = selection_mismatches(Fc, vc, to_np(st)["V"], ga.cpu().numpy(),
+                                            gs.cpu().numpy(), o, tie_rel=1e-5)
+        assert not bad_a and not bad_s, (bad_a[:5], bad_s[:5])
+        run.sync_status()
+    finally:
+        orc.set_threads(1)
