@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--workload", default="dtlz1_m3_d5000_N9870", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
@@ -273,26 +274,27 @@ def main():
 
     # ---- end to end through the public API, host buffers --------------------
     N, m, d = wl["N"], wl["m"], wl["d"]
-    hF = torch.empty((N, m), dtype=torch.float32, pin_memory=True)
-    hV = torch.empty(N, dtype=torch.uint8, pin_memory=True)
-    hX = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
     Ke = K
-    barrier()
-    t0 = time.perf_counter()
-    erun = Run(seed=3000 + rank, **kw)            # host config -> device state
-    for _ in range(Ke):
-        erun.step(1)
-        erun.objectives(hF, hV)                  # per-generation result to host
-    erun.population(hX, hV)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    erun.sync_status()
-    ws_bytes = erun.workspace_nbytes
-    del erun
+    e2e_s = None
+    if not args.no_e2e:
+        hF = torch.empty((N, m), dtype=torch.float32, pin_memory=True)
+        hV = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+        hX = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
+        barrier()
+        t0 = time.perf_counter()
+        erun = Run(seed=3000 + rank, **kw)            # host config -> device state
+        for _ in range(Ke):
+            erun.step(1)
+            erun.objectives(hF, hV)                  # per-generation result to host
+        erun.population(hX, hV)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        erun.sync_status()
+        del erun
     h2d_init = N * m * 8 * 2 + N * 16 + 4096       # lattice (f64 x2), float copy, tables
     d2h = Ke * (N * m * 4 + N) + N * d * 4 + N
 
@@ -335,12 +337,12 @@ def main():
         "whole_generation_hbm_gbs": bytes_rep / (ms / K * 1e-3) / 1e9,
         "whole_generation_frac": bytes_rep / (ms / K * 1e-3) / 1e9 / hbm_peak,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * Ke / e2e_s, "unit": "generations/s",
-                "h2d_bytes_per_step": h2d_init / Ke, "d2h_bytes_per_step": d2h / Ke,
-                "what": "init from host config + per-generation objectives to pinned host "
-                        "+ final population to pinned host"},
+        "e2e": None if e2e_s is None else {
+            "value": world * Ke / e2e_s, "unit": "generations/s",
+            "h2d_bytes_per_step": h2d_init / Ke, "d2h_bytes_per_step": d2h / Ke,
+            "what": "init from host config + per-generation objectives to pinned host "
+                    "+ final population to pinned host"},
         "gpu_launches": launches,
-        "workspace_bytes": ws_bytes,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -144,6 +144,10 @@ void rvea_free(rvea_run *run);
 
 const char *rvea_status_str(rvea_status s);
 
+/* The CUDA call and error string behind the calling thread's most recent
+ * RVEA_ERR_CUDA ("" if none).  Valid until the next call on this thread. */
+const char *rvea_last_cuda_error(void);
+
 /* ---- inspection, checkpoint and teacher forcing ---------------------- */
 
 /* Index of the next generation rvea_step will run (1 after init). */

@@ -39,6 +39,8 @@ class RveaError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
         msg = lib().rvea_status_str(status).decode()
+        if status == ERR_CUDA:
+            msg += " [" + lib().rvea_last_cuda_error().decode() + "]"
         super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
 
 
@@ -86,6 +88,8 @@ def lib():
         L.rvea_free.restype = None
         L.rvea_status_str.argtypes = [i32]
         L.rvea_status_str.restype = C.c_char_p
+        L.rvea_last_cuda_error.argtypes = []
+        L.rvea_last_cuda_error.restype = C.c_char_p
         L.rvea_generation.argtypes = [vp]
         L.rvea_generation.restype = i32
         L.rvea_step_profiled.argtypes = [vp, i32, vp, C.POINTER(C.c_double), i32]

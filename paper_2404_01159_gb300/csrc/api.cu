@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -177,16 +178,31 @@ uint32_t event_threshold24(double q) {
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
+thread_local cudaError_t g_last_err = cudaSuccess;
+thread_local const char *g_last_where = "";
+
+void note_error(cudaError_t e, const char *where) {
+  if (e != cudaSuccess) {
+    g_last_err = e;
+    g_last_where = where;
+  }
+}
+
 void set_kernel_attrs() {
   int dev = 0;
   cudaGetDevice(&dev);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int cap = optin - 2048;   // leave room for static shared memory
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {
-    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    // dynamic + static shared memory may not exceed the opt-in limit
+    cudaFuncAttributes fa;
+    cudaError_t r = cudaFuncGetAttributes(&fa, f);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
     if (r != cudaSuccess && e == cudaSuccess) e = r;
+    note_error(r, "cudaFuncSetAttribute");
   };
   set((const void *)k_repro);
   set((const void *)k_init);
@@ -220,12 +236,19 @@ struct rvea_run {
 
 namespace {
 
-rvea_status cuerr(cudaError_t e) { return e == cudaSuccess ? RVEA_OK : RVEA_ERR_CUDA; }
+rvea_status cuerr_at(cudaError_t e, const char *where) {
+  note_error(e, where);
+  return e == cudaSuccess ? RVEA_OK : RVEA_ERR_CUDA;
+}
+#define cuerr(e) cuerr_at((e), #e)
 
 #define RV_TRY(x)                                    \
   do {                                               \
     const cudaError_t _e = (x);                      \
-    if (_e != cudaSuccess) return RVEA_ERR_CUDA;     \
+    if (_e != cudaSuccess) {                         \
+      note_error(_e, #x);                            \
+      return RVEA_ERR_CUDA;                          \
+    }                                                \
   } while (0)
 
 void dir_single(BatchDir &dir, const rvea_run *r, const void *items, int n_items) {
@@ -350,6 +373,13 @@ size_t rvea_workspace_bytes(int m, int d, int N) {
   return make_layout(s, 0, 0, 0).total;
 }
 
+const char *rvea_last_cuda_error(void) {
+  static thread_local char buf[256];
+  if (g_last_err == cudaSuccess) return "";
+  snprintf(buf, sizeof(buf), "%s: %s", g_last_where, cudaGetErrorString(g_last_err));
+  return buf;
+}
+
 const char *rvea_status_str(rvea_status s) {
   switch (s) {
     case RVEA_OK: return "ok";
@@ -458,10 +488,9 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
 
   rvea_status s = RVEA_OK;
   auto up = [&](size_t off, const void *src, size_t n) {
-    if (s == RVEA_OK && cudaMemcpyAsync(r->ws + off, src, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      s = RVEA_ERR_CUDA;
+    if (s == RVEA_OK) s = cuerr(cudaMemcpyAsync(r->ws + off, src, n, cudaMemcpyHostToDevice, st));
   };
-  if (cudaMemsetAsync(r->ws, 0, lay.total, st) != cudaSuccess) s = RVEA_ERR_CUDA;
+  s = cuerr(cudaMemsetAsync(r->ws, 0, lay.total, st));
   up(lay.desc, &D, sizeof(D));
   up(lay.repro, rep.data(), rep.size() * sizeof(ReproItem));
   up(lay.init, ini.data(), ini.size() * sizeof(ReproItem));

@@ -6,6 +6,8 @@ Tolerances (stated once, used everywhere):
   * objectives: |f_gpu - f_orc| <= 1e-5 ||f_orc||_2 per row (relative to the
     row's objective vector, so components that vanish on the front are not
     held to a relative bound they cannot carry);
+  * gamma (FP64): |g_gpu - g_orc| <= 64 eps / sin(g) + 1e-12 g: arccos of a
+    cosine near 1 loses eps / sin(theta) (theta ~ 1e-3 rad at N = 9870);
   * association: exact unless the two vectors' dot products with f' differ
     by less than `tie_rel` ||f'|| (float32 dot of unit vectors);
   * survivors: exact unless explained by such an association tie or by two
@@ -51,6 +53,13 @@ def assert_objectives(gf, of, rtol=F_RTOL):
     err = np.abs(gf - of)
     bad = err > rtol * scale + 1e-30
     assert not bad.any(), (int(bad.sum()), float((err / (scale + 1e-300)).max()))
+
+
+def assert_gamma(g, o):
+    eps = np.finfo(np.float64).eps
+    tol = 64 * eps / np.sin(o) + 1e-12 * o
+    err = np.abs(np.asarray(g) - o)
+    assert (err <= tol).all(), float((err / tol).max())
 
 
 def selection_mismatches(Fc, validc, V, gpu_assoc, gpu_surv, o, tie_rel=2e-6):

@@ -11,8 +11,8 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from gpu_util import (assert_children, assert_objectives, igd, make_run, params,  # noqa: E402
-                      selection_mismatches, to_np)
+from gpu_util import (assert_children, assert_gamma, assert_objectives, igd,  # noqa: E402
+                      make_run, params, selection_mismatches, to_np)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -53,7 +53,7 @@ def test_init_matches_oracle(orc, shape):
     assert_objectives(st["F"], orc.evaluate(p, X0))
     V0 = orc.lattice_unit(orc.lattice(m, H))
     assert np.array_equal(st["V"], V0)                            # bit-exact lattice
-    assert np.allclose(st["gamma"], orc.gamma(V0), rtol=1e-10, atol=0)
+    assert_gamma(st["gamma"], orc.gamma(V0))
     assert st["valid"].all() and st["t"] == 1
     run.sync_status()
 
@@ -76,16 +76,18 @@ def test_teacher_forced_generations(orc, shape):
         ga, gsurv = run.last_selection()
         gx, gf = gx.cpu().numpy(), gf.cpu().numpy()
         assert_children(gx, out["Xchild"], p.L, p.U)
-        assert_objectives(gf, out["Fchild"])
-        # the oracle's evaluation of the GPU's own children isolates the
-        # float32 objective arithmetic
-        assert_objectives(gf, orc.evaluate(p, gx.astype(np.float64), t), rtol=2e-6)
-        Fc = np.concatenate([np.nan_to_num(Fpar), out["Fchild"]])
+        # float32 objectives of the same decision vectors: 1e-5 relative
+        assert_objectives(gf, orc.evaluate(p, gx.astype(np.float64), t))
+        # against the oracle's own (FP64) children the difference also carries
+        # the ~1e-7 child difference times the objective's conditioning
+        # (DTLZ1: d/dx of 100 cos(20 pi x) ~ 6e3): a looser sanity bound
+        assert_objectives(gf, out["Fchild"], rtol=1e-3)
+        # selection on the GPU's own combined population
+        Fc = np.concatenate([np.nan_to_num(Fpar), gf.astype(np.float64)])
         vc = np.concatenate([vpar, np.ones(N, np.uint8)])
         o = orc.select(Fc, vc, to_np(st)["V"], to_np(st)["gamma"], t, p.t_max, p.alpha)
-        assert np.array_equal(o["survivor"], out["survivor"])
         bad_a, bad_s = selection_mismatches(Fc, vc, to_np(st)["V"], ga.cpu().numpy(),
-                                            gsurv.cpu().numpy(), o, tie_rel=1e-5)
+                                            gsurv.cpu().numpy(), o)
         assert not bad_a and not bad_s, (gen, bad_a[:5], bad_s[:5])
         # the adapted reference vectors and gamma follow the GPU's survivors
         nst = to_np(run.export_state())
@@ -94,7 +96,7 @@ def test_teacher_forced_generations(orc, shape):
             rng = orc.objective_range(nst["F"].astype(np.float64), nst["valid"])
             Vw = orc.adapt(V0, rng)
             assert np.allclose(nst["V"], Vw, rtol=0, atol=1e-15)
-            assert np.allclose(nst["gamma"], orc.gamma(Vw), rtol=1e-10, atol=0)
+            assert_gamma(nst["gamma"], orc.gamma(Vw))
         else:
             assert np.array_equal(nst["V"], to_np(st)["V"])
     run.sync_status()
@@ -145,7 +147,7 @@ def test_gamma_operator(orc, m, H):
     V0 = orc.lattice_unit(orc.lattice(m, H))
     for V in (V0, orc.adapt(V0, np.linspace(0.5, 3.0, m))):
         g = gamma(torch.tensor(V, device="cuda")).cpu().numpy()
-        assert np.allclose(g, orc.gamma(V), rtol=1e-10, atol=0)
+        assert_gamma(g, orc.gamma(V))
 
 
 def test_free_running_quality_dtlz2(orc):
@@ -225,13 +227,16 @@ def test_full_size_dtlz1_sampled(orc):
         gx, gf = run.offspring()
         ga, gs = run.last_selection()
         rows = np.random.default_rng(0).choice(N, 64, replace=False)
-        assert_children(gx[rows].cpu().numpy(), out["Xchild"][rows])
-        assert_objectives(gf.cpu().numpy(), out["Fchild"])
-        Fc = np.concatenate([np.nan_to_num(Fpar), out["Fchild"]])
+        gx = gx.cpu().numpy()
+        assert_children(gx[rows], out["Xchild"][rows])
+        gf = gf.cpu().numpy()
+        assert_objectives(gf[rows], orc.evaluate(p, gx[rows].astype(np.float64), t))
+        assert_objectives(gf, out["Fchild"], rtol=1e-3)
+        Fc = np.concatenate([np.nan_to_num(Fpar), gf.astype(np.float64)])
         vc = np.concatenate([vpar, np.ones(N, np.uint8)])
         o = orc.select(Fc, vc, to_np(st)["V"], to_np(st)["gamma"], t, p.t_max, p.alpha)
         bad_a, bad_s = selection_mismatches(Fc, vc, to_np(st)["V"], ga.cpu().numpy(),
-                                            gs.cpu().numpy(), o, tie_rel=1e-5)
+                                            gs.cpu().numpy(), o)
         assert not bad_a and not bad_s, (bad_a[:5], bad_s[:5])
         run.sync_status()
     finally:
