@@ -204,6 +204,27 @@ rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid,
                         int32_t *assoc, int32_t *survivor,
                         void *scratch, size_t scratch_bytes, void *cuda_stream);
 
+/* rvea_select for callers that cannot allocate device memory -- for example
+ * an execution step of an inference-server or framework plugin whose host
+ * owns every device byte and forbids allocation while work is enqueued, or a
+ * process whose device memory is all reserved by another caching allocator.
+ * (The paper has no counterpart: this is a deployment variant of rvea_select.)
+ * Same arguments and results as rvea_select, bit for bit, without the
+ * scratch argument: the scratch is a 4 MiB array inside the library, reserved
+ * on every GPU that loads the library until the process exits.  Limits:
+ * n <= 65536, r <= 16384, and the shape's scratch must fit the 4 MiB;
+ * larger sizes return RVEA_ERR_NOMEM before any GPU work.  The call itself
+ * allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ * The first call on a device looks up the array's device address and sets
+ * the selection kernel's shared-memory limit, with that device current:
+ * make that first call before any stream capture.  Every call shares the one
+ * array and clears what it reads; calls whose GPU work overlaps (e.g. on
+ * unordered streams) race and corrupt each other's results. */
+rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *valid,
+                                int r, const float *V, const float *gamma,
+                                int t, int t_max, float alpha,
+                                int32_t *assoc, int32_t *survivor, void *cuda_stream);
+
 /* gamma_j = min over i != j of the angle between v_i and v_j (Eq. 5), FP64.
  * V (r x m f64, device, unit rows) -> gamma (r f64, device). */
 rvea_status rvea_gamma(int m, int r, const double *V, double *gamma, void *cuda_stream);

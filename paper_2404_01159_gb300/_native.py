@@ -106,6 +106,8 @@ def lib():
         L.rvea_select_scratch_bytes.restype = sz
         L.rvea_select.argtypes = [i32, i32, vp, vp, i32, vp, vp, i32, i32, flt, vp, vp, vp, sz, vp]
         L.rvea_select.restype = i32
+        L.rvea_select_noalloc.argtypes = [i32, i32, vp, vp, i32, vp, vp, i32, i32, flt, vp, vp, vp]
+        L.rvea_select_noalloc.restype = i32
         L.rvea_gamma.argtypes = [i32, i32, vp, vp, vp]
         L.rvea_gamma.restype = i32
         _lib = L

@@ -1,0 +1,180 @@
+// rvea_select_noalloc: environmental selection for callers that cannot
+// allocate device memory.
+//
+// Some callers cannot call cudaMalloc (or any allocator) at the point where
+// they want a selection: code running under a fixed, pre-planned device
+// memory budget (an inference-server or plugin execution step, where the
+// host framework owns every byte and forbids allocation while work is being
+// enqueued), or code whose device memory is entirely reserved by another
+// framework's caching allocator.  For them this file keeps the scratch that
+// rvea_select would take from the caller in a file-scope device array of a
+// fixed maximum size, reserved when the library is loaded.
+//
+// The same kernels as rvea_select run on that array, so results are the same
+// bit for bit.  Every call shares the one array: two calls whose work
+// overlaps on the GPU (different streams, no ordering between them) race and
+// corrupt each other's results; calls on one stream, or otherwise ordered,
+// are safe.  The array keeps the previous call's contents; every field a
+// call reads is cleared by the call itself before use.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/rvea.h"
+#include "rvea_device.cuh"
+
+namespace rvea {
+__global__ void k_select(const __grid_constant__ BatchDir dir);
+__global__ void k_op_prep(const RunDesc *Rp);
+__global__ void k_op_zstar(const RunDesc *Rp);
+__global__ void k_op_finish(const RunDesc *Rp);
+}  // namespace rvea
+
+using namespace rvea;
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(4) << 20;   // 4 MiB per device
+constexpr int kNoAllocMaxN = 65536;                  // solutions
+constexpr int kNoAllocMaxR = 16384;                  // reference vectors
+constexpr int kDevicesMax = 64;
+constexpr int kSMCount = 152;
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// device symbol: its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_select_scratch[kNoAllocBytes];
+
+std::mutex g_mu;
+void *g_scratch_addr[kDevicesMax] = {};
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Carve {
+  size_t ctl, desc, best, amax, blk, items, v32, total;
+};
+
+Carve carve(int n, int r, int m, int n_items) {
+  Carve c;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t at = o;
+    o = up256(o + b);
+    return at;
+  };
+  const int nblk = (n + kSelThreads - 1) / kSelThreads;
+  c.ctl = take(sizeof(Ctl));
+  c.desc = take(sizeof(RunDesc));
+  c.best = take((size_t)r * 8);
+  c.amax = take((size_t)n * 8);
+  c.blk = take((size_t)nblk * 4);
+  c.items = take((size_t)n_items * sizeof(SelItem));
+  c.v32 = take((size_t)r * ((m + 3) / 4) * 16);
+  c.total = o;
+  return c;
+}
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current).  The same one-time set-up lets the
+// selection kernel use more than 48 KB of dynamic shared memory (needed for
+// m > 8), as the other entry points do on their first call.
+rvea_status scratch_for_current_device(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevicesMax) return RVEA_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_select_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return RVEA_ERR_CUDA;
+    }
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void *)k_select) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return RVEA_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+  return RVEA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *valid, int r,
+                                const float *V, const float *gamma, int t, int t_max,
+                                float alpha, int32_t *assoc, int32_t *survivor,
+                                void *cuda_stream) {
+  if (m < 2 || m > kMaxM || n < 1 || r < 1 || !F || !V || !gamma || !assoc || !survivor ||
+      t_max < 1 || !(alpha > 0.0f))
+    return RVEA_ERR_ARG;
+  // work items: every block of 256 solutions x chunks of whole vector tiles
+  const int nblk = (n + kSelThreads - 1) / kSelThreads;
+  const int tiles = (r + kVTile - 1) / kVTile;
+  int nch = std::max(1, std::min(tiles, (4 * kSMCount + nblk - 1) / nblk));
+  const int tpc = (tiles + nch - 1) / nch;
+  nch = (tiles + tpc - 1) / tpc;
+  const int n_items = nblk * nch;
+  if (n > kNoAllocMaxN || r > kNoAllocMaxR) return RVEA_ERR_NOMEM;
+  const Carve c = carve(n, r, m, n_items);
+  if (c.total > kNoAllocBytes) return RVEA_ERR_NOMEM;
+
+  unsigned char *ws = nullptr;
+  const rvea_status s0 = scratch_for_current_device(&ws);
+  if (s0 != RVEA_OK) return s0;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int m4 = (m + 3) / 4;
+  float *V32 = reinterpret_cast<float *>(ws + c.v32);
+  // zero-padded float4 rows of V (the padding must read as zero)
+  if (cudaMemsetAsync(V32, 0, (size_t)r * m4 * 16, st) != cudaSuccess) return RVEA_ERR_CUDA;
+  if (cudaMemcpy2DAsync(V32, (size_t)m4 * 16, V, (size_t)m * 4, (size_t)m * 4, r,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return RVEA_ERR_CUDA;
+  RunDesc D;
+  std::memset(&D, 0, sizeof(D));
+  D.m = m; D.m4 = m4; D.N = r; D.n_comb = n; D.t_max = t_max; D.alpha = alpha;
+  D.op_mode = 1; D.t_op = t;
+  D.best = reinterpret_cast<unsigned long long *>(ws + c.best);
+  D.amax = reinterpret_cast<unsigned long long *>(ws + c.amax);
+  D.blk_cnt = reinterpret_cast<int *>(ws + c.blk);
+  D.assoc = assoc;
+  D.V32 = V32;
+  D.gamma32 = const_cast<float *>(gamma);
+  D.ctl = reinterpret_cast<Ctl *>(ws + c.ctl);
+  D.F_aos = F;
+  D.valid_in = valid;
+  D.survivor_out = survivor;
+  std::vector<SelItem> items;
+  items.reserve(n_items);
+  for (int b = 0; b < nblk; ++b)
+    for (int q = 0; q < nch; ++q)
+      items.push_back(SelItem{b, std::min(r, q * tpc * kVTile), std::min(r, (q + 1) * tpc * kVTile), nch});
+  RunDesc *dD = reinterpret_cast<RunDesc *>(ws + c.desc);
+  // pageable sources: staged by the driver before these calls return
+  if (cudaMemcpyAsync(dD, &D, sizeof(D), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(ws + c.items, items.data(), items.size() * sizeof(SelItem),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RVEA_ERR_CUDA;
+  // k_op_prep clears best, amax, the arrival counters and the control block
+  k_op_prep<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, st>>>(dD);
+  k_op_zstar<<<(n + 255) / 256, 256, 0, st>>>(dD);
+  static thread_local BatchDir dir;
+  dir.n = 1;
+  dir.prefix[0] = 0;
+  dir.prefix[1] = n_items;
+  dir.desc[0] = dD;
+  dir.items[0] = ws + c.items;
+  k_select<<<(unsigned)n_items, kSelThreads, 2 * kVTile * m4 * 16, st>>>(dir);
+  k_op_finish<<<(r + 255) / 256, 256, 0, st>>>(dD);
+  return cudaGetLastError() == cudaSuccess ? RVEA_OK : RVEA_ERR_CUDA;
+}
+
+}  // extern "C"
