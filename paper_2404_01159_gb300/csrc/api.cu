@@ -23,6 +23,9 @@
 
 namespace rvea {
 __global__ void k_repro(const __grid_constant__ BatchDir dir);
+__global__ void k_repro1_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_init(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
@@ -37,7 +40,6 @@ __global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin
 __global__ void k_op_prep(const RunDesc *Rp);
 __global__ void k_op_zstar(const RunDesc *Rp);
 __global__ void k_op_finish(const RunDesc *Rp);
-int repro_smem_total(int TS, int m, int G);
 }  // namespace rvea
 
 using namespace rvea;
@@ -58,12 +60,14 @@ int pow2ceil(int x) {
 }
 
 struct Shape {
-  int m, m4, d, d_pad, G, N, P, n_comb, team, ppc;
-  int n_repro, n_init, n_sel, nblk;
+  int m, m4, d, d_pad, G, N, P, n_comb, team, ppc, nseg;
+  int n_repro, n_init, n_sel, nblk, nch, chunk;
 };
 
-// Threads per pair: ~3 groups of 8 variables per thread, a power of two in
-// [1, 256].  It depends on d only, so the reduction tree of g does too.
+// Reproduction teams: TS lanes (a power of two <= 32) per work unit of
+// kLaneGroups*TS groups of 8 variables; a pair has nseg = ceil(G / (kLaneGroups TS))
+// units.
+// Both depend on d only, so the reduction tree of g does too.
 Shape make_shape(int m, int d, int N) {
   Shape s;
   s.m = m;
@@ -74,23 +78,22 @@ Shape make_shape(int m, int d, int N) {
   s.N = N;
   s.P = (N + 1) / 2;
   s.n_comb = 2 * N;
-  s.team = std::min(256, std::max(1, pow2ceil((s.G + 2) / 3)));
-  s.ppc = kReproThreads / s.team;
-  s.n_repro = (s.P + s.ppc - 1) / s.ppc;
+  s.team = std::min(32, std::max(1, pow2ceil((s.G + kLaneGroups - 1) / kLaneGroups)));
+  s.ppc = kReproThreads / s.team;                 // work units per CTA
+  s.nseg = (s.G + kLaneGroups * s.team - 1) / (kLaneGroups * s.team);
+  s.n_repro = (s.P * s.nseg + s.ppc - 1) / s.ppc;
   s.n_init = (N + s.ppc - 1) / s.ppc;
-  s.nblk = (s.n_comb + kSelThreads - 1) / kSelThreads;
-  // selection: solution blocks x vector chunks, >= ~4 CTAs per SM overall
-  const int tiles = (N + kVTile - 1) / kVTile;
-  int nch = std::max(1, std::min(tiles, (4 * kSMs + s.nblk - 1) / s.nblk));
-  const int tpc = (tiles + nch - 1) / nch;
-  nch = (tiles + tpc - 1) / tpc;
-  s.n_sel = s.nblk * nch;
+  const SelPlan sp = sel_plan(s.n_comb, N, s.m4, kSMs);
+  s.nblk = sp.nblk;
+  s.nch = sp.nch;
+  s.chunk = sp.chunk;
+  s.n_sel = s.nblk * s.nch;
   return s;
 }
 
 struct Layout {
-  size_t X, F, slotmap, vlist, child, best, amax, assoc, surv, blk, V32, V64, V0, g64, g32,
-      ctl, desc, repro, init, sel, stage, noise, dynA, dynB, total;
+  size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V64, V0, g64, g32,
+      ctl, desc, repro, init, sel, stage, psum, hbuf, pcnt, noise, dynA, dynB, total;
 };
 
 Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
@@ -103,14 +106,17 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   };
   L.X = take((size_t)2 * s.N * s.d_pad * sizeof(float));
   L.F = take((size_t)s.m * s.n_comb * sizeof(float));
-  L.slotmap = take((size_t)s.N * 4);
+  L.slotmap = take((size_t)2 * s.N * 4);
+  L.vbits = take((size_t)((s.N + 31) / 32) * 4);
+  L.obits = take((size_t)((2 * s.N + 31) / 32) * 4);
+  L.zpart = take((size_t)((s.N + 1023) / 1024) * 2 * kMaxM * 4);
   L.vlist = take((size_t)s.N * 4);
   L.child = take((size_t)2 * s.N * 4);
   L.best = take((size_t)s.N * 8);
   L.amax = take((size_t)s.n_comb * 8);
   L.assoc = take((size_t)s.n_comb * 4);
   L.surv = take((size_t)s.N * 4);
-  L.blk = take((size_t)s.nblk * 4);
+  L.blk = take((size_t)s.nblk * 4);   // selection blocks of kSelBlock solutions
   L.V32 = take((size_t)s.N * s.m4 * 16);
   L.V64 = take((size_t)s.N * s.m * 8);
   L.V0 = take((size_t)s.N * s.m * 8);
@@ -122,6 +128,9 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.init = take((size_t)s.n_init * sizeof(ReproItem));
   L.sel = take((size_t)s.n_sel * sizeof(SelItem));
   L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
+  L.psum = take((size_t)s.P * 2 * s.nseg * 4);
+  L.hbuf = take((size_t)s.P * 2 * kMaxM * 4);
+  L.pcnt = take((size_t)s.P * 4);
   L.noise = take((size_t)steps_max * ns_max * 4);
   L.dynA = take((size_t)ns_max * ns_max * 4);
   L.dynB = take((size_t)ns_max * na_max * 4);
@@ -205,9 +214,12 @@ void set_kernel_attrs() {
     note_error(r, "cudaFuncSetAttribute");
   };
   set((const void *)k_repro);
+  set((const void *)k_repro1_dtlz1);
+  set((const void *)k_repro1_dtlz2);
+  set((const void *)k_repro1_neuro);
   set((const void *)k_init);
   set((const void *)k_select);
-  set((const void *)k_finalize);
+
   g_attr_err = e;
 }
 
@@ -257,6 +269,7 @@ void dir_single(BatchDir &dir, const rvea_run *r, const void *items, int n_items
   dir.prefix[1] = n_items;
   dir.desc[0] = r->d_desc;
   dir.items[0] = items;
+  dir.key[0] = make_uint2(r->hd.key0, r->hd.key1);
 }
 
 template <class T>
@@ -264,18 +277,33 @@ T *wsp(const rvea_run *r, size_t off) {
   return reinterpret_cast<T *>(r->ws + off);
 }
 
+// Reproduction of one run: the kernel instance for its problem, round keys
+// in the parameter block.
+void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t st) {
+  const RoundKeys rk = round_keys(r->hd.key0, r->hd.key1);
+  switch (r->hd.problem) {
+    case PROB_DTLZ1: k_repro1_dtlz1<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
+    case PROB_DTLZ2: k_repro1_dtlz2<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
+    default: k_repro1_neuro<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
+  }
+}
+
 // Enqueue one generation of every run in `runs` (one launch per phase).
 rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, bool gamma_by_flag) {
-  static thread_local BatchDir dr, ds, df;
-  int pr = 0, ps = 0;
+  static thread_local BatchDir dr, ds, df, dd;
+  int pr = 0, ps = 0, pd = 0;
   int smr = 0, sms = 0, smf = 0;
-  dr.n = ds.n = df.n = n;
+  dr.n = ds.n = df.n = dd.n = n;
   for (int q = 0; q < n; ++q) {
     const rvea_run *r = runs[q];
     dr.prefix[q] = pr;
     ds.prefix[q] = ps;
     df.prefix[q] = q;
-    dr.desc[q] = ds.desc[q] = df.desc[q] = r->d_desc;
+    dd.prefix[q] = pd;
+    dr.desc[q] = ds.desc[q] = df.desc[q] = dd.desc[q] = r->d_desc;
+    dr.key[q] = ds.key[q] = df.key[q] = dd.key[q] = make_uint2(r->hd.key0, r->hd.key1);
+    dd.items[q] = nullptr;
+    pd += (r->sh.N + 1023) / 1024;
     dr.items[q] = wsp<ReproItem>(r, r->lay.repro);
     ds.items[q] = wsp<SelItem>(r, r->lay.sel);
     df.items[q] = nullptr;
@@ -288,9 +316,13 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   dr.prefix[n] = pr;
   ds.prefix[n] = ps;
   df.prefix[n] = n;
-  k_repro<<<pr, kReproThreads, smr, st>>>(dr);
+  dd.prefix[n] = pd;
+  if (n == 1)
+    launch_repro1(runs[0], dr, pr, st);
+  else
+    k_repro<<<pr, kReproThreads, smr, st>>>(dr);
   k_select<<<ps, kSelThreads, sms, st>>>(ds);
-  k_finalize<<<n, kFinThreads, smf, st>>>(df);
+  k_finalize<<<pd, 1024, 0, st>>>(dd);
   if (gamma_by_flag) {
     k_gamma<<<2 * kSMs, 256, 0, st>>>(df, 0);
   }
@@ -424,7 +456,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   std::memset(&D, 0, sizeof(D));
   D.m = sh.m; D.m4 = sh.m4; D.d = sh.d; D.d_pad = sh.d_pad; D.G = sh.G;
   D.N = sh.N; D.P = sh.P; D.n_comb = sh.n_comb; D.problem = cfg->problem;
-  D.t_max = cfg->t_max; D.p_adapt = r->p_adapt; D.team = sh.team; D.op_mode = 0;
+  D.t_max = cfg->t_max; D.p_adapt = r->p_adapt; D.team = sh.team; D.nseg = sh.nseg;
+  D.op_mode = 0;
   D.L = (float)cfg->lower; D.U = (float)cfg->upper; D.alpha = (float)cfg->alpha;
   D.inv_eta_c1 = (float)(1.0 / (cfg->eta_c + 1.0));
   D.eta_m = (float)cfg->eta_m;
@@ -435,6 +468,9 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.X = wsp<float>(r, lay.X);
   D.F = wsp<float>(r, lay.F);
   D.slotmap = wsp<int>(r, lay.slotmap);
+  D.vbits = wsp<uint32_t>(r, lay.vbits);
+  D.obits = wsp<uint32_t>(r, lay.obits);
+  D.zpart = wsp<uint32_t>(r, lay.zpart);
   D.vlist = wsp<int>(r, lay.vlist);
   D.child_slot = wsp<int>(r, lay.child);
   D.best = wsp<unsigned long long>(r, lay.best);
@@ -448,12 +484,15 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gamma64 = wsp<double>(r, lay.g64);
   D.gamma32 = wsp<float>(r, lay.g32);
   D.ctl = wsp<Ctl>(r, lay.ctl);
+  D.psum = wsp<float>(r, lay.psum);
+  D.hbuf = wsp<float>(r, lay.hbuf);
+  D.pcnt = wsp<int>(r, lay.pcnt);
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
-  r->repro_smem = repro_smem_total(sh.team, sh.m, sh.G);
+  r->repro_smem = 0;
   r->init_smem = sh.ppc * std::max(1, sh.m - 1) * 4;
-  r->sel_smem = 2 * kVTile * sh.m4 * 16;
-  r->fin_smem = sh.N * 4 + ((2 * sh.N + 3) & ~3);
+  r->sel_smem = std::min(sh.N, sh.chunk) * sh.m4 * 16;
+  r->fin_smem = 0;
 
   // host tables
   std::vector<ReproItem> rep(sh.n_repro), ini(sh.n_init);
@@ -461,20 +500,15 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   for (int q = 0; q < sh.n_init; ++q) ini[q].pair0 = q * sh.ppc;
   std::vector<SelItem> sel;
   sel.reserve(sh.n_sel);
-  {
-    const int tiles = (sh.N + kVTile - 1) / kVTile;
-    const int nch = sh.n_sel / sh.nblk;
-    const int tpc = (tiles + nch - 1) / nch;
-    for (int b = 0; b < sh.nblk; ++b)
-      for (int c = 0; c < nch; ++c) {
-        SelItem it;
-        it.sblk = b;
-        it.v0 = std::min(sh.N, c * tpc * kVTile);
-        it.v1 = std::min(sh.N, (c + 1) * tpc * kVTile);
-        it.nchunks = nch;
-        sel.push_back(it);
-      }
-  }
+  for (int b = 0; b < sh.nblk; ++b)
+    for (int c = 0; c < sh.nch; ++c) {
+      SelItem it;
+      it.sblk = b;
+      it.v0 = std::min(sh.N, c * sh.chunk);
+      it.v1 = std::min(sh.N, (c + 1) * sh.chunk);
+      it.nchunks = sh.nch;
+      sel.push_back(it);
+    }
   std::vector<double> V0;
   build_lattice(sh.m, cfg->H, sh.N, V0);
   std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f);
@@ -591,21 +625,23 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
       return RVEA_ERR_CUDA;
     }
   rvea_status s = RVEA_OK;
-  static thread_local BatchDir dr, ds, df, dg;
+  static thread_local BatchDir dr, ds, df, dg, dd;
   const rvea_run *one = r;
   dir_single(dr, one, wsp<ReproItem>(r, r->lay.repro), r->sh.n_repro);
   dir_single(ds, one, wsp<SelItem>(r, r->lay.sel), r->sh.n_sel);
   dir_single(df, one, nullptr, 1);
   dir_single(dg, one, nullptr, 1);
+  const int nbd = (r->sh.N + 1023) / 1024;
+  dir_single(dd, one, nullptr, nbd);
   const int nbg = std::min((r->sh.N + 31) / 32, 4 * kSMs);
   for (int g = 0; g < G && s == RVEA_OK; ++g) {
     cudaEvent_t *e = &ev[(size_t)g * 5];
     cudaEventRecord(e[0], st);
-    k_repro<<<r->sh.n_repro, kReproThreads, r->repro_smem, st>>>(dr);
+    launch_repro1(r, dr, r->sh.n_repro, st);
     cudaEventRecord(e[1], st);
     k_select<<<r->sh.n_sel, kSelThreads, r->sel_smem, st>>>(ds);
     cudaEventRecord(e[2], st);
-    k_finalize<<<1, kFinThreads, r->fin_smem, st>>>(df);
+    k_finalize<<<nbd, 1024, 0, st>>>(dd);
     cudaEventRecord(e[3], st);
     if (r->t % r->p_adapt == 0) k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
     cudaEventRecord(e[4], st);
@@ -639,7 +675,8 @@ rvea_status rvea_population(const rvea_run *r, float *dst, uint8_t *valid, void 
     k_gather_pop<<<sh.N, 256, 0, st>>>(r->d_desc, nullptr, sv);
     RV_TRY(cudaGetLastError());
     std::vector<int> map(sh.N);
-    RV_TRY(cudaMemcpyAsync(map.data(), r->hd.slotmap, sh.N * 4, cudaMemcpyDeviceToHost, st));
+    RV_TRY(cudaMemcpyAsync(map.data(), r->hd.slotmap + (size_t)(r->t & 1) * sh.N, sh.N * 4,
+                           cudaMemcpyDeviceToHost, st));
     RV_TRY(cudaStreamSynchronize(st));
     if (valid) {
       for (int j = 0; j < sh.N; ++j) valid[j] = map[j] >= 0 ? 1 : 0;
@@ -770,7 +807,7 @@ OpLayout op_layout(int n, int r) {
     o = align256(o + b);
     return at;
   };
-  const int nblk = (n + kSelThreads - 1) / kSelThreads;
+  const int nblk = (n + kSelBlock - 1) / kSelBlock;
   const int tiles = (r + kVTile - 1) / kVTile;
   L.ctl = take(sizeof(Ctl));
   L.desc = take(sizeof(RunDesc));
@@ -822,17 +859,13 @@ rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid, int 
   D.F_aos = F;
   D.valid_in = valid;
   D.survivor_out = survivor;
-  // items: every solution block x every tile-sized vector chunk
-  const int nblk = (n + kSelThreads - 1) / kSelThreads;
-  const int tiles = (r + kVTile - 1) / kVTile;
-  int nch = std::max(1, std::min(tiles, (4 * kSMs + nblk - 1) / nblk));
-  const int tpc = (tiles + nch - 1) / nch;
-  nch = (tiles + tpc - 1) / tpc;
+  // items: every solution block x every vector chunk
+  const SelPlan sp = sel_plan(n, r, m4, kSMs);
   std::vector<SelItem> items;
-  items.reserve((size_t)nblk * nch);
-  for (int b = 0; b < nblk; ++b)
-    for (int c = 0; c < nch; ++c)
-      items.push_back(SelItem{b, std::min(r, c * tpc * kVTile), std::min(r, (c + 1) * tpc * kVTile), nch});
+  items.reserve((size_t)sp.nblk * sp.nch);
+  for (int b = 0; b < sp.nblk; ++b)
+    for (int c = 0; c < sp.nch; ++c)
+      items.push_back(SelItem{b, std::min(r, c * sp.chunk), std::min(r, (c + 1) * sp.chunk), sp.nch});
   RunDesc *dD = reinterpret_cast<RunDesc *>(ws + L.desc);
   RV_TRY(cudaMemcpyAsync(dD, &D, sizeof(D), cudaMemcpyHostToDevice, st));
   RV_TRY(cudaMemcpyAsync(ws + L.items, items.data(), items.size() * sizeof(SelItem),
@@ -845,7 +878,7 @@ rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid, int 
   d.prefix[1] = (int)items.size();
   d.desc[0] = dD;
   d.items[0] = ws + L.items;
-  k_select<<<(unsigned)items.size(), kSelThreads, 2 * kVTile * m4 * 16, st>>>(d);
+  k_select<<<(unsigned)items.size(), kSelThreads, std::min(r, sp.chunk) * m4 * 16, st>>>(d);
   k_op_finish<<<(r + 255) / 256, 256, 0, st>>>(dD);
   // the pageable host sources of the two copies above were staged before
   // cudaMemcpyAsync returned, so nothing here waits for the stream

@@ -41,92 +41,159 @@ __device__ int block_exclusive_scan(int v, int *s_warp, int *total) {
   return before;
 }
 
-__global__ void __launch_bounds__(kFinThreads)
+// ---- finalize ---------------------------------------------------------------
+// Every thread decodes one reference vector j: the survivor of j (best[j])
+// becomes slot j of P_{t+1}.  The CTAs publish compact bitmaps -- valid slots
+// (one warp ballot per 32 vectors) and occupied pool rows (atomicOr) -- and
+// their own minimum / maximum of the survivors' objectives.  The last CTA to
+// finish (an arrival counter, no spinning) builds the ascending list of valid
+// slots (mating of the next generation), the ascending list of free pool rows
+// (its offspring), the next z*, and on adaptation generations rescales V0 by
+// the survivors' objective range in FP64.
+constexpr int kFinDecode = 1024;   // threads (vectors) per finalize CTA
+
+// Writes, in ascending order, the positions of the set bits of words
+// [w0, w1) of `bits` (bit b of word w is element 32 w + b) starting at
+// out[base]; at most `limit` elements in total.  One warp, coalesced stores.
+__device__ __forceinline__ int warp_compact(const uint32_t *bits, int w0, int w1, int *out,
+                                           int base, int limit) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int w = w0; w < w1 && base < limit; ++w) {
+    const uint32_t word = bits[w];
+    const bool set = (word >> lane) & 1u;
+    const int at = base + __popc(word & lt);
+    if (set && at < limit) out[at] = 32 * w + lane;
+    base += __popc(word);
+  }
+  return base;
+}
+
+__global__ void __launch_bounds__(kFinDecode)
 k_finalize(const __grid_constant__ BatchDir dir) {
-  extern __shared__ __align__(16) int s_map[];     // [N] new slot map, then [2N] bytes occ
-  __shared__ int s_warp[32];
-  __shared__ unsigned s_zmin[kMaxM], s_zmax[kMaxM];
-  __shared__ int s_total;
-  const RunDesc &R = *dir.desc[blockIdx.x];
+  __shared__ unsigned s_lo[32][kMaxM], s_hi[32][kMaxM];
+  __shared__ unsigned s_z[2 * kMaxM];
+  __shared__ int s_cnt[2][32];
+  __shared__ double s_rng[kMaxM];
+  __shared__ int s_last;
+  __shared__ uint32_t s_free[2048];   // complement of the occupied-row bitmap
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int blk = blockIdx.x - dir.prefix[run];
+  const int nblk = dir.prefix[run + 1] - dir.prefix[run];
+  const int j = blk * kFinDecode + threadIdx.x;
   const int N = R.N, n2 = 2 * N, m = R.m;
   const int t = R.ctl->t;
-  const int *cur = R.child_slot + (t & 1) * N;
-  int *nxt = R.child_slot + ((t + 1) & 1) * N;
-  uint8_t *occ = reinterpret_cast<uint8_t *>(s_map + N);
-  const int tid = threadIdx.x;
+  const int *cur = R.slotmap + (t & 1) * N;
+  int *nmap = R.slotmap + ((t + 1) & 1) * N;
+  const int *ccur = R.child_slot + (t & 1) * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  for (int w = tid; w < (n2 + 3) / 4; w += kFinThreads) reinterpret_cast<int *>(occ)[w] = 0;
-  if (tid < kMaxM) { s_zmin[tid] = 0xFFFFFFFFu; s_zmax[tid] = 0u; }
-  __syncthreads();
-  for (int j = tid; j < N; j += kFinThreads) {
+  // ---- decode ---------------------------------------------------------------
+  int s = -1;
+  if (j < N) {
     const unsigned long long key = R.best[j];
     R.best[j] = ~0ull;
-    int s = -1, i = -1;
+    int i = -1;
     if (key != ~0ull) {
       i = (int)(uint32_t)(key & 0xFFFFFFFFull);
-      if (i >= 0 && i < N) s = R.slotmap[i];
-      else if (i >= N && i < n2) s = cur[i - N];
+      if (i >= 0 && i < N) s = cur[i];
+      else if (i >= N && i < n2) s = ccur[i - N];
       if (s < 0 || s >= n2) { set_status(R.ctl, ST_BADINDEX); s = -1; i = -1; }
-      else occ[s] = 1;
     }
-    s_map[j] = s;
+    nmap[j] = s;
     R.surv[j] = i;
+    if (s >= 0) atomicOr(&R.obits[s >> 5], 1u << (s & 31));
   }
-  __syncthreads();
-
-  // new slot map and ascending valid list
-  const int ch = (N + kFinThreads - 1) / kFinThreads;
-  const int a0 = min(N, tid * ch), a1 = min(N, a0 + ch);
-  int cnt = 0;
-  for (int j = a0; j < a1; ++j) cnt += (s_map[j] >= 0);
-  int pos = block_exclusive_scan(cnt, s_warp, &s_total);
-  const int K = s_total;
-  for (int j = a0; j < a1; ++j) {
-    const int s = s_map[j];
-    R.slotmap[j] = s;
-    if (s >= 0) {
-      R.vlist[pos++] = j;
-      for (int k = 0; k < m; ++k) {
-        const unsigned o = f2ord(R.F[(size_t)k * n2 + s]);
-        atomicMin(&s_zmin[k], o);
-        atomicMax(&s_zmax[k], o);
-      }
+  const uint32_t vmask = __ballot_sync(0xffffffffu, s >= 0);
+  if (lane == 0 && j < N) R.vbits[j >> 5] = vmask;
+  for (int k = 0; k < m; ++k) {
+    unsigned lo = 0xFFFFFFFFu, hi = 0u;
+    if (s >= 0) lo = hi = f2ord(R.F[(size_t)k * n2 + s]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
     }
+    if (lane == 0) { s_lo[warp][k] = lo; s_hi[warp][k] = hi; }
   }
-  // free rows, ascending, first N of them
-  const int ch2 = (n2 + kFinThreads - 1) / kFinThreads;
-  const int b0 = min(n2, tid * ch2), b1 = min(n2, b0 + ch2);
-  int fc = 0;
-  for (int s = b0; s < b1; ++s) fc += (occ[s] == 0);
-  int fpos = block_exclusive_scan(fc, s_warp, &s_total);
-  for (int s = b0; s < b1 && fpos < N; ++s)
-    if (occ[s] == 0) nxt[fpos++] = s;
   __syncthreads();
+  if (threadIdx.x < m) {
+    unsigned lo = 0xFFFFFFFFu, hi = 0u;
+    for (int w = 0; w < kFinDecode / 32; ++w) {
+      lo = min(lo, s_lo[w][threadIdx.x]);
+      hi = max(hi, s_hi[w][threadIdx.x]);
+    }
+    R.zpart[(size_t)blk * 2 * kMaxM + threadIdx.x] = lo;
+    R.zpart[(size_t)blk * 2 * kMaxM + kMaxM + threadIdx.x] = hi;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&R.ctl->fin_cnt, 1) == nblk - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
 
-  if (tid < m) R.ctl->zkey[tid] = s_zmin[tid];
+  // ---- last CTA: lists, z*, adaptation ---------------------------------------
+  const int tid = threadIdx.x;
+  const int nvw = (N + 31) >> 5, now = (n2 + 31) >> 5, nzb = nblk;
+  for (int w = tid; w < now; w += kFinDecode) {
+    uint32_t o = __ldcg(R.obits + w);
+    if (w == now - 1 && (n2 & 31)) o |= ~((1u << (n2 & 31)) - 1u);   // beyond 2N
+    s_free[w] = ~o;
+    R.obits[w] = 0u;   // empty for the next generation
+  }
+  if (tid < 2 * kMaxM) s_z[tid] = tid < kMaxM ? 0xFFFFFFFFu : 0u;
+  __syncthreads();
+  for (int q = tid; q < nzb * m; q += kFinDecode) {
+    const int b = q / m, k = q - (q / m) * m;
+    atomicMin(&s_z[k], __ldcg(R.zpart + (size_t)b * 2 * kMaxM + k));
+    atomicMax(&s_z[kMaxM + k], __ldcg(R.zpart + (size_t)b * 2 * kMaxM + kMaxM + k));
+  }
+  // warp w owns words [w * per, (w+1) * per) of each bitmap
+  const int perv = (nvw + 31) / 32, pero = (now + 31) / 32;
+  const int v0 = min(nvw, warp * perv), v1 = min(nvw, v0 + perv);
+  const int o0 = min(now, warp * pero), o1 = min(now, o0 + pero);
+  int cv = 0, cf = 0;
+  for (int w = v0 + lane; w < v1; w += 32) cv += __popc(__ldcg(R.vbits + w));
+  for (int w = o0 + lane; w < o1; w += 32) cf += __popc(s_free[w]);
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    cv += __shfl_xor_sync(0xffffffffu, cv, off);
+    cf += __shfl_xor_sync(0xffffffffu, cf, off);
+  }
+  if (lane == 0) { s_cnt[0][warp] = cv; s_cnt[1][warp] = cf; }
+  __syncthreads();
+  int bv = 0, bf = 0, K = 0;
+  for (int w = 0; w < 32; ++w) {
+    if (w < warp) { bv += s_cnt[0][w]; bf += s_cnt[1][w]; }
+    K += s_cnt[0][w];
+  }
+  warp_compact(R.vbits, v0, v1, R.vlist, bv, N);
+  warp_compact(s_free, o0, o1, R.child_slot + ((t + 1) & 1) * N, bf, N);
+
+  if (tid < m) R.ctl->zkey[tid] = s_z[tid];
   const bool adapt = (t % R.p_adapt) == 0;
   if (adapt && K > 0) {
     // range_k = max - min over the survivors, floored at 1e-12, in FP64
-    __shared__ double s_rng[kMaxM];
     if (tid < m) {
-      const double hi = (double)ord2f(s_zmax[tid]), lo = (double)ord2f(s_zmin[tid]);
-      const double r = hi - lo;
+      const double r = (double)ord2f(s_z[kMaxM + tid]) - (double)ord2f(s_z[tid]);
       s_rng[tid] = r < 1e-12 ? 1e-12 : r;
     }
     __syncthreads();
-    for (int j = tid; j < N; j += kFinThreads) {
-      const double *v0 = R.V0 + (size_t)j * m;
+    for (int jj = tid; jj < N; jj += kFinDecode) {
+      const double *v0p = R.V0 + (size_t)jj * m;
       double w[kMaxM];
       double s2 = 0.0;
       for (int k = 0; k < m; ++k) {
-        w[k] = v0[k] * s_rng[k];
+        w[k] = v0p[k] * s_rng[k];
         s2 += w[k] * w[k];
       }
       const double nrm = sqrt(s2);
-      float *v32 = R.V32 + (size_t)j * R.m4 * 4;
+      float *v32 = R.V32 + (size_t)jj * R.m4 * 4;
       for (int k = 0; k < m; ++k) {
         const double v = w[k] / nrm;
-        R.V64[(size_t)j * m + k] = v;
+        R.V64[(size_t)jj * m + k] = v;
         v32[k] = (float)v;
       }
     }
@@ -134,51 +201,107 @@ k_finalize(const __grid_constant__ BatchDir dir) {
   if (tid == 0) {
     R.ctl->K = K;
     R.ctl->adapted = adapt ? 1 : 0;
+    R.ctl->fin_cnt = 0;
     R.ctl->t = t + 1;
   }
 }
 
 // gamma_j = min_{i != j} angle(v_i, v_j) (Eq. 5), FP64.  arccos is
 // decreasing, so gamma_j = acos(max_{i != j} v_i.v_j) for unit rows.  A float
-// pass finds max32; only the i whose float dot is within 1e-5 of it (the
-// float error of a dot of unit vectors is below 1e-6) are re-evaluated in
-// FP64, so the FP64 maximum is exact.  One block = 32 vectors x 8 slices of i.
-__device__ void gamma_block(const RunDesc &R, int jb) {
-  const int N = R.N, m = R.m;
+// pass finds max32 over reference-vector tiles staged in shared memory; only
+// the i whose float dot is within 1e-5 of it (the float error of a dot of
+// unit vectors is below 1e-6) are re-evaluated in FP64, so the FP64 maximum
+// is exact.  One block = 32 vectors j x 8 interleaved slices of i.
+constexpr int kGTileF4 = 2048;   // float4s of one shared-memory tile (32 KB)
+
+__device__ __forceinline__ void gamma_load_tile(const RunDesc &R, int base, int nv, int m4,
+                                                float4 *tile) {
+  const int m = R.m;
+  for (int q = threadIdx.x; q < nv * m4; q += blockDim.x) {
+    if (R.V32) {
+      tile[q] = reinterpret_cast<const float4 *>(R.V32)[(size_t)base * m4 + q];
+    } else {
+      const int i = base + q / m4, c = 4 * (q % m4);
+      const double *v = R.V64 + (size_t)i * m;
+      tile[q] = make_float4(c < m ? (float)v[c] : 0.f, c + 1 < m ? (float)v[c + 1] : 0.f,
+                            c + 2 < m ? (float)v[c + 2] : 0.f, c + 3 < m ? (float)v[c + 3] : 0.f);
+    }
+  }
+}
+
+// FP64 dot of two rows; a call, so the rare recheck stays a real branch
+// instead of being predicated into every iteration of the float scan.
+__device__ __noinline__ double dot64(const double *a, const double *b, int m) {
+  double e = 0.0;
+  for (int k = 0; k < m; ++k) e += a[k] * b[k];
+  return e;
+}
+
+template <int M>
+__device__ void gamma_block_t(const RunDesc &R, int jb, float4 *tile) {
+  constexpr int M4 = (M + 3) / 4;
+  const int N = R.N;
   const int jl = threadIdx.x >> 3, sl = threadIdx.x & 7;
   const int j = jb * 32 + jl;
   const bool act = j < N;
-  const int per = (N + 7) / 8;
-  const int i0 = sl * per, i1 = min(N, i0 + per);
-  double vj[kMaxM];
-  float vj32[kMaxM];
-  for (int k = 0; k < kMaxM; ++k) { vj[k] = 0.0; vj32[k] = 0.f; }
-  if (act)
-    for (int k = 0; k < m; ++k) { vj[k] = R.V64[(size_t)j * m + k]; vj32[k] = (float)vj[k]; }
-  float mx = -INFINITY;
+  float vf[M4 * 4];
+#pragma unroll
+  for (int k = 0; k < M4 * 4; ++k) vf[k] = 0.f;
   if (act) {
-    for (int i = i0; i < i1; ++i) {
-      if (i == j) continue;
-      const double *vi = R.V64 + (size_t)i * m;
-      float d = (float)vi[0] * vj32[0];
-      for (int k = 1; k < m; ++k) d = fmaf((float)vi[k], vj32[k], d);
-      mx = fmaxf(mx, d);
+    if (R.V32) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) vf[k] = R.V32[(size_t)j * M4 * 4 + k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < M; ++k) vf[k] = (float)R.V64[(size_t)j * M + k];
+    }
+  }
+  const double *vjp = R.V64 + (size_t)(act ? j : 0) * M;
+  constexpr int kGTile = kGTileF4 / M4;
+  float mx = -INFINITY;
+  for (int base = 0; base < N; base += kGTile) {
+    const int nv = min(kGTile, N - base);
+    __syncthreads();
+    gamma_load_tile(R, base, nv, M4, tile);
+    __syncthreads();
+    if (act) {
+#pragma unroll 4
+      for (int u = sl; u < nv; u += 8) {
+        float d = 0.f;
+#pragma unroll
+        for (int q = 0; q < M4; ++q) {
+          const float4 v = tile[u * M4 + q];
+          d = fmaf(vf[4 * q], v.x, d);
+          d = fmaf(vf[4 * q + 1], v.y, d);
+          d = fmaf(vf[4 * q + 2], v.z, d);
+          d = fmaf(vf[4 * q + 3], v.w, d);
+        }
+        if (base + u != j) mx = fmaxf(mx, d);
+      }
     }
   }
 #pragma unroll
   for (int off = 1; off < 8; off <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   const float thr = mx - 1e-5f;
   double best = -2.0;
-  if (act) {
-    for (int i = i0; i < i1; ++i) {
-      if (i == j) continue;
-      const double *vi = R.V64 + (size_t)i * m;
-      float d = (float)vi[0] * vj32[0];
-      for (int k = 1; k < m; ++k) d = fmaf((float)vi[k], vj32[k], d);
-      if (d >= thr) {
-        double e = 0.0;
-        for (int k = 0; k < m; ++k) e += vi[k] * vj[k];
-        best = fmax(best, e);
+  for (int base = 0; base < N; base += kGTile) {
+    const int nv = min(kGTile, N - base);
+    __syncthreads();
+    gamma_load_tile(R, base, nv, M4, tile);
+    __syncthreads();
+    if (act) {
+      for (int u = sl; u < nv; u += 8) {
+        float d = 0.f;
+#pragma unroll
+        for (int q = 0; q < M4; ++q) {
+          const float4 v = tile[u * M4 + q];
+          d = fmaf(vf[4 * q], v.x, d);
+          d = fmaf(vf[4 * q + 1], v.y, d);
+          d = fmaf(vf[4 * q + 2], v.z, d);
+          d = fmaf(vf[4 * q + 3], v.w, d);
+        }
+        const int i = base + u;
+        if (d >= thr && i != j) best = fmax(best, dot64(R.V64 + (size_t)i * M, vjp, M));
       }
     }
   }
@@ -189,6 +312,27 @@ __device__ void gamma_block(const RunDesc &R, int jb) {
     if (!(g >= 1e-12)) g = 1e-12;
     R.gamma64[j] = g;
     if (R.gamma32) R.gamma32[j] = (float)g;
+  }
+}
+
+__device__ void gamma_block(const RunDesc &R, int jb) {
+  __shared__ float4 tile[kGTileF4];
+  switch (R.m) {
+    case 2: gamma_block_t<2>(R, jb, tile); return;
+    case 3: gamma_block_t<3>(R, jb, tile); return;
+    case 4: gamma_block_t<4>(R, jb, tile); return;
+    case 5: gamma_block_t<5>(R, jb, tile); return;
+    case 6: gamma_block_t<6>(R, jb, tile); return;
+    case 7: gamma_block_t<7>(R, jb, tile); return;
+    case 8: gamma_block_t<8>(R, jb, tile); return;
+    case 9: gamma_block_t<9>(R, jb, tile); return;
+    case 10: gamma_block_t<10>(R, jb, tile); return;
+    case 11: gamma_block_t<11>(R, jb, tile); return;
+    case 12: gamma_block_t<12>(R, jb, tile); return;
+    case 13: gamma_block_t<13>(R, jb, tile); return;
+    case 14: gamma_block_t<14>(R, jb, tile); return;
+    case 15: gamma_block_t<15>(R, jb, tile); return;
+    default: gamma_block_t<16>(R, jb, tile); return;
   }
 }
 
@@ -214,7 +358,7 @@ __global__ void __launch_bounds__(256) k_gamma_op(const __grid_constant__ RunDes
 __global__ void k_gather_pop(const RunDesc *__restrict__ Rp, float *dst, uint8_t *valid) {
   const RunDesc &R = *Rp;
   const int j = blockIdx.x;
-  const int s = R.slotmap[j];
+  const int s = R.slotmap[(R.ctl->t & 1) * R.N + j];
   if (threadIdx.x == 0 && valid) valid[j] = s >= 0 ? 1 : 0;
   if (!dst) return;
   float *o = dst + (size_t)j * R.d;
@@ -226,7 +370,7 @@ __global__ void k_gather_obj(const RunDesc *__restrict__ Rp, float *dst, uint8_t
   const RunDesc &R = *Rp;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= R.N) return;
-  const int s = R.slotmap[j];
+  const int s = R.slotmap[(R.ctl->t & 1) * R.N + j];
   if (valid) valid[j] = s >= 0 ? 1 : 0;
   if (!dst) return;
   for (int k = 0; k < R.m; ++k)
@@ -266,7 +410,7 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
   __syncthreads();
   for (int j = tid; j < N; j += kFinThreads) {
     const bool v = vin[j] != 0;
-    R.slotmap[j] = v ? j : -1;
+    R.slotmap[(t & 1) * N + j] = v ? j : -1;
     for (int k = 0; k < m; ++k) {
       const float f = Fin[(size_t)j * m + k];
       R.F[(size_t)k * n2 + j] = f;
@@ -279,7 +423,8 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
     R.surv[j] = -1;
   }
   for (int i = tid; i < n2; i += kFinThreads) { R.amax[i] = 0ull; R.assoc[i] = -1; }
-  for (int b = tid; b < (n2 + kSelThreads - 1) / kSelThreads; b += kFinThreads) R.blk_cnt[b] = 0;
+  for (int w = tid; w < (n2 + 31) / 32; w += kFinThreads) R.obits[w] = 0u;
+  for (int b = tid; b < (n2 + kSelBlock - 1) / kSelBlock; b += kFinThreads) R.blk_cnt[b] = 0;
   // valid list
   const int ch = (N + kFinThreads - 1) / kFinThreads;
   const int a0 = min(N, tid * ch), a1 = min(N, a0 + ch);
@@ -315,7 +460,7 @@ __global__ void k_init_lists(const __grid_constant__ BatchDir dir) {
   const int N = R.N;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < N) {
-    R.slotmap[j] = j;
+    R.slotmap[1 * N + j] = j;   // t = 1 reads buffer (1 & 1)
     R.vlist[j] = j;
     R.child_slot[1 * N + j] = N + j;   // t = 1 uses buffer (1 & 1)
     R.child_slot[j] = N + j;
@@ -323,7 +468,7 @@ __global__ void k_init_lists(const __grid_constant__ BatchDir dir) {
     R.surv[j] = -1;
   }
   for (int i = j; i < 2 * N; i += gridDim.x * blockDim.x) { R.amax[i] = 0ull; R.assoc[i] = -1; }
-  if (j < (2 * N + kSelThreads - 1) / kSelThreads) R.blk_cnt[j] = 0;
+  if (j < (2 * N + kSelBlock - 1) / kSelBlock) R.blk_cnt[j] = 0;
   if (j == 0) {
     R.ctl->t = 1;
     R.ctl->K = N;

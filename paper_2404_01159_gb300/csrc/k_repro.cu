@@ -3,10 +3,20 @@
 // k_repro fuses, per pair of children (Appendix B of arXiv 2404.01159):
 //   mating draw -> SBX (the two B equations and X_cross) -> clip -> polynomial
 //   mutation (C, Delta, X_mut) -> clip -> DTLZ evaluation -> ideal point z*.
-// A "team" of TS threads (TS a power of two fixed by d alone) owns one pair;
-// thread `lane` of the team handles the 8-variable groups lane, lane+TS, ...
-// Each group is two 16-byte vector loads per parent and two 16-byte stores
-// per child, so a warp moves contiguous 1 KiB spans of each row.
+//
+// Work decomposition.  A team of TS lanes (TS a power of two <= 32, fixed by d
+// alone) owns one work unit: one segment of kLaneGroups*TS consecutive
+// 8-variable groups of one pair; lane l handles groups l, l+TS, l+2TS, ...
+// of the segment.  Each group is two 16-byte loads per parent and two 16-byte stores
+// per child, so a warp moves contiguous 512-byte spans.  Teams never wait on
+// other warps: the phases below synchronise with __syncwarp only.  A pair
+// with several segments (d > 2048) combines the segments' partial sums of g
+// in the last segment to finish (an arrival counter per pair, no spinning),
+// always in segment order, so the reduction tree depends on d alone.
+//
+// Arithmetic on adjacent variables runs in packed .f32x2 instructions (the
+// children of SBX and the evaluation): same IEEE operations, half the issue
+// slots.  g is accumulated per lane as (even variables, odd variables).
 //
 // Random numbers (Philox4x32-10, counter = (c0, c1, t, tag), key = seed):
 //   PAIR  (p, 0, t)      word 0    : pair gate R3 (crossover iff u24 < p_c)
@@ -22,7 +32,9 @@
 
 namespace rvea {
 
-constexpr int kQueueCap = 512;
+constexpr int kWarpQ = 64;        // candidate queue entries per warp
+constexpr int kBmWords = kLaneGroups * 16;    // per warp: 32 lanes x kLaneGroups x 16 bits
+constexpr int kWarpWords = kBmWords + kWarpQ + 4;   // bitmap + queue + count
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
   return fminf(fmaxf(x, lo), hi);
@@ -43,16 +55,63 @@ __device__ __noinline__ float poly_mutate(float x, float M, float L, float U, fl
   return clampf(x + delta, L, U);
 }
 
-// g-term of one variable.  DTLZ2: (x-1/2)^2.  DTLZ1: (x-1/2)^2 - cos(20 pi (x-1/2))
-// + 1, written as y^2 + 2 sin^2(10 pi y) (identical, free of cancellation);
-// the k = d-m+1 constant is absorbed by the +1 of each term.
-__device__ __forceinline__ float g_term(int problem, float x) {
-  const float y = x - 0.5f;
+// Taylor coefficients of sin(pi r), through r^13 (|r| <= 1/2: the first
+// omitted term is below 7e-10).
+constexpr double kPI = 3.14159265358979323846;
+constexpr float kS1 = (float)kPI;
+constexpr float kS3 = (float)(-kPI * kPI * kPI / 6.0);
+constexpr float kS5 = (float)(kPI * kPI * kPI * kPI * kPI / 120.0);
+constexpr float kS7 = (float)(-kPI * kPI * kPI * kPI * kPI * kPI * kPI / 5040.0);
+constexpr float kS9 = (float)(kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI / 362880.0);
+constexpr float kS11 =
+    (float)(-kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI / 39916800.0);
+constexpr float kS13 = (float)(kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI *
+                               kPI * kPI / 6227020800.0);
+
+// g-terms of two adjacent variables x = (x_j, x_j+1), added into acc.
+// DTLZ2: (x-1/2)^2.  DTLZ1: (x-1/2)^2 - cos(20 pi (x-1/2)) + 1 = y^2 + 2 sin^2(10 pi y)
+// (identical, free of cancellation; the k = d-m+1 constant is the +1 of each
+// term).  sin^2 has period 1 in 10y: 10y is reduced by its nearest integer
+// first (one fma, one rounding), then sin(pi r) from its Taylor series.
+__device__ __forceinline__ float2 g_terms2(int problem, float2 x, float2 acc) {
+  const float2 y = add2(x, splat2(-0.5f));
+  acc = fma2(y, y, acc);
   if (problem == PROB_DTLZ1) {
-    const float s = sinpif(10.0f * y);
-    return fmaf(2.0f * s, s, y * y);
+    const float2 z = mul2(y, splat2(10.0f));
+    const float2 nn = make_float2(rintf(-z.x), rintf(-z.y));
+    const float2 r = fma2(splat2(10.0f), y, nn);
+    const float2 r2 = mul2(r, r);
+    float2 p = fma2(r2, splat2(kS13), splat2(kS11));
+    p = fma2(r2, p, splat2(kS9));
+    p = fma2(r2, p, splat2(kS7));
+    p = fma2(r2, p, splat2(kS5));
+    p = fma2(r2, p, splat2(kS3));
+    p = fma2(r2, p, splat2(kS1));
+    const float2 s = mul2(r, p);
+    acc = fma2(add2(s, s), s, acc);
   }
-  return y * y;
+  return acc;
+}
+
+// Scalar form of the same terms (bit-identical per element), used where a
+// group holds x_1..x_{m-1} or the ragged end of the row.
+__device__ __forceinline__ float g_term1(int problem, float x, float acc) {
+  const float y = x + (-0.5f);
+  acc = fmaf(y, y, acc);
+  if (problem == PROB_DTLZ1) {
+    const float z = y * 10.0f;
+    const float r = fmaf(10.0f, y, rintf(-z));
+    const float r2 = r * r;
+    float p = fmaf(r2, kS13, kS11);
+    p = fmaf(r2, p, kS9);
+    p = fmaf(r2, p, kS7);
+    p = fmaf(r2, p, kS5);
+    p = fmaf(r2, p, kS3);
+    p = fmaf(r2, p, kS1);
+    const float s = r * p;
+    acc = fmaf(s + s, s, acc);
+  }
+  return acc;
 }
 
 // Objectives from g and the first m-1 variables (standard DTLZ forms).
@@ -76,260 +135,339 @@ __device__ void dtlz_objectives(int problem, int m, float gsum, const float *hea
   }
 }
 
-// Sum of `v` over a team of TS threads in a fixed tree that depends on TS
-// only (xor butterfly inside a warp, then warp partials in index order).
-// Every thread of the CTA must call it.  Valid in the team's first thread.
-__device__ __forceinline__ float2 team_sum2(float2 v, int TS, float2 *red) {
-  const int lim = TS < 32 ? TS : 32;
+// Sum over a team of TS <= 32 lanes: xor butterfly (every lane of the team
+// ends with the same bits).  All 32 lanes of the warp must call it.
+__device__ __forceinline__ float2 team_sum2(float2 v, int TS) {
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
-    if (off < lim) {
+    if (off < TS) {
       v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
       v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
     }
   }
-  if (TS <= 32) return v;
-  const int warp = threadIdx.x >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[warp] = v;
-  __syncthreads();
-  float2 s = make_float2(0.f, 0.f);
-  if ((threadIdx.x & (TS - 1)) == 0) {
-    const int w0 = warp, nw = TS >> 5;
-    s = red[w0];
-    for (int w = 1; w < nw; ++w) { s.x += red[w0 + w].x; s.y += red[w0 + w].y; }
+  return v;
+}
+
+// Sites of one child in one group from the 8 high bytes of R4 (lo = bytes
+// 0-3, hi = bytes 4-7): `sure` = bytes below thr (the site fires whatever
+// the low 16 bits are), `cand` = bytes equal to thr (the low bits decide).
+__device__ __forceinline__ void site_bytes(uint32_t lo, uint32_t hi, uint32_t thr,
+                                           uint32_t &sure, uint32_t &cand) {
+  sure = 0u;
+  cand = 0u;
+  if (thr >= 256u) {
+    sure = 0xFFu;
+    return;
   }
-  return s;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t by = ((b < 4 ? lo : hi) >> (8 * (b & 3))) & 0xFFu;
+    if (by < thr) sure |= 1u << b;
+    else if (by == thr) cand |= 1u << b;
+  }
 }
 
-// Shared-memory layout of one reproduction CTA (bytes), shared with the host
-// through repro_smem_bytes().
-struct ReproSmem {
-  int head_off, bm_off, q_off, total;
-};
-__host__ __device__ inline ReproSmem repro_smem_layout(int TS, int m, int G) {
-  const int ppc = kReproThreads / TS;
-  ReproSmem s;
-  s.head_off = 0;
-  const int head_bytes = ppc * 2 * (m > 1 ? m - 1 : 1) * 4;
-  s.bm_off = (head_bytes + 15) & ~15;
-  const int bm_bytes = ((ppc * 2 * G) + 3) & ~3;
-  s.q_off = (s.bm_off + bm_bytes + 15) & ~15;
-  s.total = s.q_off + kQueueCap * 4;
-  return s;
+// True if any of the four words holds a zero byte (the classic test).
+__device__ __forceinline__ bool any_zero_byte(uint4 w) {
+  const uint32_t a = (w.x - 0x01010101u) & ~w.x, b = (w.y - 0x01010101u) & ~w.y;
+  const uint32_t c = (w.z - 0x01010101u) & ~w.z, e = (w.w - 0x01010101u) & ~w.w;
+  return ((a | b | c | e) & 0x80808080u) != 0u;
 }
 
-__device__ __forceinline__ void bm_set(uint32_t *bm, int byte_index, int bit) {
-  atomicOr(&bm[byte_index >> 2], 1u << (((byte_index & 3) << 3) + bit));
-}
-__device__ __forceinline__ uint32_t bm_get(const uint32_t *bm, int byte_index) {
-  return (bm[byte_index >> 2] >> ((byte_index & 3) << 3)) & 0xFFu;
+// 2^x with one MUFU.EX2 (PTX ex2.approx, relative error ~2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-__global__ void __launch_bounds__(kReproThreads)
-k_repro(const __grid_constant__ BatchDir dir) {
-  extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ int s_par[kReproThreads][2];
-  __shared__ int s_chd[kReproThreads][2];
-  __shared__ int s_nocross[kReproThreads];
-  __shared__ int s_qn;
-  __shared__ float2 s_red[kReproThreads / 32];
+// SBX spread factor of one variable: word q carries Mc (top 24 bits), the
+// sign coin (bit 0) and the keep coin (bit 1); keep or no crossover -> 1.
+__device__ __forceinline__ float sbx_B(uint32_t q, bool nocross, float ie) {
+  const float Mc = u24f(q);
+  const bool lowb = Mc < 0.5f;
+  const float base = lowb ? 2.0f * Mc : 2.0f - 2.0f * Mc;
+  const float beta = ex2_approx((lowb ? ie : -ie) * __log2f(base));
+  const float B = (q & 1u) ? beta : -beta;
+  return ((q & 2u) || nocross) ? 1.0f : B;
+}
+
+// Children of two adjacent variables: c1 = ((1+B) x1 + (1-B) x2) / 2,
+// c2 = ((1-B) x1 + (1+B) x2) / 2, clipped to [L, U].
+__device__ __forceinline__ void sbx_pair(float2 x1, float2 x2, float2 B, float L, float U,
+                                         float2 &c1, float2 &c2) {
+  const float2 P = add2(splat2(1.0f), B), Q = sub2(splat2(1.0f), B);
+  c1 = mul2(splat2(0.5f), fma2(P, x1, mul2(Q, x2)));
+  c2 = mul2(splat2(0.5f), fma2(Q, x1, mul2(P, x2)));
+  c1 = make_float2(clampf(c1.x, L, U), clampf(c1.y, L, U));
+  c2 = make_float2(clampf(c2.x, L, U), clampf(c2.y, L, U));
+}
+
+// Last segment of pair p to arrive: g of both children from the segments'
+// partial sums in segment order, then the objectives and the ideal point.
+__device__ __noinline__ void finish_pair(const RunDesc &R, int p, int S, int ch1, int ch2) {
+  __threadfence();
+  const float *ps = R.psum + (size_t)p * 2 * S;
+  const float *hb = R.hbuf + (size_t)p * 2 * kMaxM;
+  const int m = R.m, mh = m - 1, n2 = 2 * R.N;
+  float g1 = 0.f, g2 = 0.f;
+  for (int sg = 0; sg < S; ++sg) {
+    g1 += __ldcg(ps + sg);
+    g2 += __ldcg(ps + S + sg);
+  }
+  float head[kMaxM], f[kMaxM];
+  for (int j = 0; j < mh; ++j) head[j] = __ldcg(hb + j);
+  dtlz_objectives(R.problem, m, g1, head, f);
+  for (int kk = 0; kk < m; ++kk) {
+    R.F[(size_t)kk * n2 + ch1] = f[kk];
+    atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
+  }
+  if (ch2 >= 0) {
+    for (int j = 0; j < mh; ++j) head[j] = __ldcg(hb + kMaxM + j);
+    dtlz_objectives(R.problem, m, g2, head, f);
+    for (int kk = 0; kk < m; ++kk) {
+      R.F[(size_t)kk * n2 + ch2] = f[kk];
+      atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
+    }
+  }
+  R.pcnt[p] = 0;
+}
+
+template <int PROB, class KP>
+__device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
+  __shared__ uint32_t s_w[kReproThreads / 32][kWarpWords];
 
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const ReproItem it = static_cast<const ReproItem *>(dir.items[run])[blockIdx.x - dir.prefix[run]];
-  const int TS = R.team, ppc = kReproThreads / TS;
-  const int team = threadIdx.x / TS, lane = threadIdx.x & (TS - 1);
+  const int TS = R.team, tpw = 32 / TS, S = R.nseg, SG = TS * kLaneGroups;
   const int m = R.m, d = R.d, G = R.G, N = R.N, P = R.P;
-  const int p = it.pair0 + team;
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const int tw = wl / TS, lane = wl & (TS - 1), tbase = tw * TS;
+  const int unit = it.pair0 + warp * tpw + tw;
+  const int p = unit / S, seg = unit - p * S;
   const bool active = p < P;
   const int t = R.ctl->t;
-  const uint32_t k0 = R.key0, k1 = R.key1;
-  const ReproSmem lay = repro_smem_layout(TS, m, G);
-  float *s_head = reinterpret_cast<float *>(dyn + lay.head_off);
-  uint32_t *s_bm = reinterpret_cast<uint32_t *>(dyn + lay.bm_off);
-  uint32_t *s_q = reinterpret_cast<uint32_t *>(dyn + lay.q_off);
   const int *cslot = R.child_slot + (t & 1) * N;
+  uint32_t *bmw = s_w[warp];
+  uint16_t *bm = reinterpret_cast<uint16_t *>(bmw) + tw * SG;   // [SG] of this team: c1 | c2 << 8
+  uint32_t *q = s_w[warp] + kBmWords;
+  uint32_t *qn = s_w[warp] + kBmWords + kWarpQ;
 
-  // ---- phase 0: mating draws and pair gate, one thread per pair ----------
-  if (threadIdx.x < ppc) {
-    const int q = it.pair0 + threadIdx.x;
-    int a = -1, b = -1, c1 = -1, c2 = -1, nc = 1;
-    if (q < P) {
-      const uint32_t K = (uint32_t)R.ctl->K;
-      const int e[2] = {q, q + P};
-      int sl[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint4 w = philox((uint32_t)(e[h] >> 2), 0u, (uint32_t)t, TAG_MATE, k0, k1);
-        const uint32_t idx = __umulhi(word(w, e[h] & 3), K);
+  for (int w = 0; w < kBmWords; w += 32) bmw[w + wl] = 0u;
+  if (wl == 0) *qn = 0u;
+
+  // ---- phase 0: the pair's two mating draws and crossover gate ------------
+  uint32_t v0 = 0, v1 = 0, v2 = 0;
+  if (active) {
+    for (int c = lane; c < 3; c += TS) {
+      if (c < 2) {
+        const int e = c == 0 ? p : p + P;
+        const uint4 w = philox_k((uint32_t)(e >> 2), 0u, (uint32_t)t, TAG_MATE, kp);
+        const uint32_t idx = __umulhi(word(w, e & 3), (uint32_t)R.ctl->K);
         const int j = R.vlist[idx];
-        int s = (j >= 0 && j < N) ? R.slotmap[j] : -1;
-        if (s < 0 || s >= 2 * N) { set_status(R.ctl, ST_BADINDEX); s = 0; }
-        sl[h] = s;
+        int sl = (j >= 0 && j < N) ? R.slotmap[(t & 1) * N + j] : -1;
+        if (sl < 0 || sl >= 2 * N) { set_status(R.ctl, ST_BADINDEX); sl = 0; }
+        if (c == 0) v0 = (uint32_t)sl; else v1 = (uint32_t)sl;
+      } else {
+        const uint4 g = philox_k((uint32_t)p, 0u, (uint32_t)t, TAG_PAIR, kp);
+        v2 = ((g.x >> 8) < R.T_c) ? 0u : 1u;
       }
-      a = sl[0]; b = sl[1];
-      const uint4 g = philox((uint32_t)q, 0u, (uint32_t)t, TAG_PAIR, k0, k1);
-      nc = ((g.x >> 8) < R.T_c) ? 0 : 1;
-      c1 = cslot[q];
-      c2 = (q + P < N) ? cslot[q + P] : -1;
-      if (c1 < 0 || c1 >= 2 * N) { set_status(R.ctl, ST_BADINDEX); c1 = 0; }
-      if (c2 >= 2 * N) { set_status(R.ctl, ST_BADINDEX); c2 = -1; }
     }
-    s_par[threadIdx.x][0] = a; s_par[threadIdx.x][1] = b;
-    s_chd[threadIdx.x][0] = c1; s_chd[threadIdx.x][1] = c2;
-    s_nocross[threadIdx.x] = nc;
   }
-  // clear the mutation bitmaps
-  const int bm_words = (ppc * 2 * G + 3) >> 2;
-  for (int w = threadIdx.x; w < bm_words; w += kReproThreads) s_bm[w] = 0u;
-  if (threadIdx.x == 0) s_qn = 0;
-  __syncthreads();
-
-  const int has2 = active ? (s_chd[team][1] >= 0) : 0;
+  const int par1 = (int)__shfl_sync(0xffffffffu, v0, tbase);
+  const int par2 = (int)__shfl_sync(0xffffffffu, v1, tbase + (1 & (TS - 1)));
+  const bool nocross = __shfl_sync(0xffffffffu, v2, tbase + (2 & (TS - 1))) != 0u;
+  int ch1 = -1, ch2 = -1;
+  if (active) {
+    ch1 = cslot[p];
+    ch2 = (p + P < N) ? cslot[p + P] : -1;
+    if (ch1 < 0 || ch1 >= 2 * N) { set_status(R.ctl, ST_BADINDEX); ch1 = 0; }
+    if (ch2 >= 2 * N) { set_status(R.ctl, ST_BADINDEX); ch2 = -1; }
+  }
+  const bool has2 = ch2 >= 0;
+  const int g0 = seg * SG;
   const uint32_t thr_hi = R.T_m >> 16, thr_lo = R.T_m & 0xFFFFu;
+  // run constants used inside the loops, in registers: the child-row stores
+  // could alias the descriptor, which would force a reload after each store
+  float4 *const X4 = reinterpret_cast<float4 *>(R.X);
+  const uint32_t rq = (uint32_t)R.d_pad >> 2;      // float4s per row
+  const uint32_t o1 = (uint32_t)par1 * rq, o2 = (uint32_t)par2 * rq;
+  const uint32_t T_m = R.T_m;
+  const float L = R.L, U = R.U, ie = R.inv_eta_c1, eta_m = R.eta_m;
+  float *const hb = R.hbuf + (size_t)p * 2 * kMaxM;
+  __syncwarp();
 
-  // ---- phase A: mutation sites from the high byte of R4 ------------------
-  if (active && R.T_m > 0) {
-    for (int g = lane; g < G; g += TS) {
-      const uint4 w = philox((uint32_t)g, (uint32_t)p, (uint32_t)t, TAG_MUTHI, k0, k1);
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        if (s == 1 && !has2) break;
-        const uint32_t lo = s ? w.z : w.x, hi = s ? w.w : w.y;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int j = 8 * g + b;
-          if (j >= d) break;
-          const uint32_t h8 = ((b < 4 ? lo : hi) >> (8 * (b & 3))) & 0xFFu;
-          if (h8 < thr_hi) {
-            bm_set(s_bm, (team * 2 + s) * G + g, b);
-          } else if (h8 == thr_hi) {
-            const int qi = atomicAdd(&s_qn, 1);
-            if (qi < kQueueCap) {
-              s_q[qi] = ((uint32_t)team << 24) | ((uint32_t)s << 23) | (uint32_t)j;
-            } else {  // queue full: resolve here
-              const int c = s ? p + P : p;
-              const uint4 wl = philox((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTLO, k0, k1);
-              if ((wl.x >> 16) < thr_lo) bm_set(s_bm, (team * 2 + s) * G + g, b);
-            }
-          }
+  // ---- phase A: mutation sites from the high byte of R4 -------------------
+  if (active && T_m > 0) {
+#pragma unroll 1
+    for (int k = 0; k < kLaneGroups; ++k) {
+      const int gl = lane + k * TS, g = g0 + gl;
+      if (g >= G) break;
+      const uint4 w = philox_k((uint32_t)g, (uint32_t)p, (uint32_t)t, TAG_MUTHI, kp);
+      if (thr_hi == 0u && !any_zero_byte(w)) continue;   // 97% of groups for d >= 256
+      const uint32_t vmask = 8 * g + 8 <= d ? 0xFFu : (1u << (d - 8 * g)) - 1u;
+      uint32_t sure1, cand1, sure2, cand2;
+      site_bytes(w.x, w.y, thr_hi, sure1, cand1);
+      site_bytes(w.z, w.w, thr_hi, sure2, cand2);
+      if (!has2) { sure2 = 0u; cand2 = 0u; }
+      bm[gl] = (uint16_t)((sure1 & vmask) | ((sure2 & vmask) << 8));
+      uint32_t cand = (cand1 & vmask) | ((cand2 & vmask) << 8);
+      while (cand) {
+        const int bit = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        const int s2 = bit >> 3, b = bit & 7;
+        const int j = 8 * g + b;
+        const uint32_t qi = atomicAdd(qn, 1u);
+        if (qi < (uint32_t)kWarpQ) {
+          q[qi] = ((uint32_t)tw << 24) | ((uint32_t)s2 << 23) | (uint32_t)j;
+        } else {   // queue full: resolve here
+          const int c = s2 ? p + P : p;
+          const uint4 wl2 = philox_k((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTLO, kp);
+          if ((wl2.x >> 16) < thr_lo) bm[gl] |= (uint16_t)(1u << bit);
         }
       }
     }
   }
-  __syncthreads();
-  // ---- phase A2: resolve queued candidates with the low 16 bits ----------
+  __syncwarp();
+  // ---- phase A2: resolve the queued candidates with the low 16 bits -------
   {
-    const int qn = min(s_qn, kQueueCap);
-    for (int qi = threadIdx.x; qi < qn; qi += kReproThreads) {
-      const uint32_t e = s_q[qi];
-      const int tm = (int)(e >> 24), s = (int)((e >> 23) & 1u), j = (int)(e & 0x7FFFFFu);
-      const int pq = it.pair0 + tm;
-      const int c = s ? pq + P : pq;
-      const uint4 wl = philox((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTLO, k0, k1);
-      if ((wl.x >> 16) < thr_lo) bm_set(s_bm, (tm * 2 + s) * G + (j >> 3), j & 7);
+    const uint32_t nq = min(*qn, (uint32_t)kWarpQ);
+    for (uint32_t e = wl; e < nq; e += 32) {
+      const uint32_t en = q[e];
+      const int tq = (int)(en >> 24), s2 = (int)((en >> 23) & 1u), j = (int)(en & 0x7FFFFFu);
+      const int uq = it.pair0 + warp * tpw + tq;
+      const int pq = uq / S;
+      const int c = s2 ? pq + P : pq;
+      const uint4 wl2 = philox_k((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTLO, kp);
+      if ((wl2.x >> 16) < thr_lo) {
+        const int gl = (j >> 3) - (uq - pq * S) * SG;
+        const int hw = tq * SG + gl;   // 16-bit entry of the warp's bitmap
+        atomicOr(&bmw[hw >> 1], 1u << (((hw & 1) << 4) + (s2 << 3) + (j & 7)));
+      }
     }
   }
-  __syncthreads();
+  __syncwarp();
 
   // ---- phase B: SBX, clip, mutation, evaluation, store --------------------
-  float2 acc = make_float2(0.f, 0.f);
+  float2 acc1 = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+  const bool eval = PROB != PROB_NEURO;
   const int mh = m - 1;
-  float *head = s_head + team * 2 * (mh > 0 ? mh : 1);
   if (active) {
-    const float *x1p = R.X + (size_t)s_par[team][0] * R.d_pad;
-    const float *x2p = R.X + (size_t)s_par[team][1] * R.d_pad;
-    float *y1p = R.X + (size_t)s_chd[team][0] * R.d_pad;
-    float *y2p = has2 ? R.X + (size_t)s_chd[team][1] * R.d_pad : nullptr;
-    const bool nocross = s_nocross[team] != 0;
-    const float L = R.L, U = R.U, ie = R.inv_eta_c1;
-    const bool eval = R.problem != PROB_NEURO;
-    for (int g = lane; g < G; g += TS) {
-      const float4 *a4 = reinterpret_cast<const float4 *>(x1p + 8 * g);
-      const float4 *b4 = reinterpret_cast<const float4 *>(x2p + 8 * g);
-      const float4 xa0 = __ldg(a4), xa1 = __ldg(a4 + 1);
-      const float4 xb0 = __ldg(b4), xb1 = __ldg(b4 + 1);
-      const uint4 r0 = philox((uint32_t)(2 * g), (uint32_t)p, (uint32_t)t, TAG_SBX, k0, k1);
-      const uint4 r1 = philox((uint32_t)(2 * g + 1), (uint32_t)p, (uint32_t)t, TAG_SBX, k0, k1);
-      const float x1v[8] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x, xa1.y, xa1.z, xa1.w};
-      const float x2v[8] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x, xb1.y, xb1.z, xb1.w};
-      const uint32_t wv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-      float c1[8], c2[8];
+    float4 *const Y4 = X4;
+    const uint32_t q1 = (uint32_t)ch1 * rq, q2 = has2 ? (uint32_t)ch2 * rq : 0u;
+#pragma unroll 1
+    for (int k = 0; k < kLaneGroups; ++k) {
+      const int gl = lane + k * TS, g = g0 + gl;
+      if (g >= G) break;
+      const uint32_t mb = bm[gl];
+      const bool plain = 8 * g >= mh && 8 * g + 8 <= d;
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const uint32_t w = wv[v];
-        const float Mc = u24f(w);
-        const bool lowb = Mc < 0.5f;
-        const float base = lowb ? 2.0f * Mc : 2.0f - 2.0f * Mc;
-        const float beta = exp2f((lowb ? ie : -ie) * __log2f(base));
-        float B = (w & 1u) ? beta : -beta;
-        if ((w & 2u) || nocross) B = 1.0f;
-        const float x1 = x1v[v], x2 = x2v[v];
-        c1[v] = clampf(0.5f * ((1.0f + B) * x1 + (1.0f - B) * x2), L, U);
-        c2[v] = clampf(0.5f * ((1.0f - B) * x1 + (1.0f + B) * x2), L, U);
-      }
-      const uint32_t mb1 = bm_get(s_bm, (team * 2 + 0) * G + g);
-      const uint32_t mb2 = has2 ? bm_get(s_bm, (team * 2 + 1) * G + g) : 0u;
-      if (mb1 | mb2) {
+      for (int h = 0; h < 2; ++h) {
+        const float4 xa = __ldg(X4 + o1 + 2 * g + h), xb = __ldg(X4 + o2 + 2 * g + h);
+        const uint4 r = philox_k((uint32_t)(2 * g + h), (uint32_t)p, (uint32_t)t, TAG_SBX, kp);
+        float2 a0, a1, b0, b1;   // children 1 and 2, variables (0,1) and (2,3)
+        sbx_pair(make_float2(xa.x, xa.y), make_float2(xb.x, xb.y),
+                 make_float2(sbx_B(r.x, nocross, ie), sbx_B(r.y, nocross, ie)), L, U, a0, b0);
+        sbx_pair(make_float2(xa.z, xa.w), make_float2(xb.z, xb.w),
+                 make_float2(sbx_B(r.z, nocross, ie), sbx_B(r.w, nocross, ie)), L, U, a1, b1);
+        const uint32_t h1 = (mb >> (4 * h)) & 0xFu, h2 = has2 ? (mb >> (8 + 4 * h)) & 0xFu : 0u;
+        if (h1 | h2) {
+          float c1[4] = {a0.x, a0.y, a1.x, a1.y}, c2[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          if (mb1 & (1u << v)) {
-            const uint4 wl = philox((uint32_t)(8 * g + v), (uint32_t)p, (uint32_t)t, TAG_MUTLO, k0, k1);
-            c1[v] = poly_mutate(c1[v], u24f(wl.y), L, U, R.eta_m);
+          for (int v = 0; v < 4; ++v) {
+            const int j = 8 * g + 4 * h + v;
+            if (h1 & (1u << v)) {
+              const uint4 w = philox_k((uint32_t)j, (uint32_t)p, (uint32_t)t, TAG_MUTLO, kp);
+              c1[v] = poly_mutate(c1[v], u24f(w.y), L, U, eta_m);
+            }
+            if (h2 & (1u << v)) {
+              const uint4 w = philox_k((uint32_t)j, (uint32_t)(p + P), (uint32_t)t, TAG_MUTLO, kp);
+              c2[v] = poly_mutate(c2[v], u24f(w.y), L, U, eta_m);
+            }
           }
-          if (mb2 & (1u << v)) {
-            const uint4 wl = philox((uint32_t)(8 * g + v), (uint32_t)(p + P), (uint32_t)t, TAG_MUTLO, k0, k1);
-            c2[v] = poly_mutate(c2[v], u24f(wl.y), L, U, R.eta_m);
-          }
+          a0 = make_float2(c1[0], c1[1]); a1 = make_float2(c1[2], c1[3]);
+          b0 = make_float2(c2[0], c2[1]); b1 = make_float2(c2[2], c2[3]);
         }
-      }
-      if (eval) {
+        if (eval) {
+          if (plain) {
+            acc1 = g_terms2(PROB, a0, acc1);
+            acc1 = g_terms2(PROB, a1, acc1);
+            acc2 = g_terms2(PROB, b0, acc2);
+            acc2 = g_terms2(PROB, b1, acc2);
+          } else {   // a group holding x_1..x_{m-1} or the ragged end of the row
+            const float c1[4] = {a0.x, a0.y, a1.x, a1.y}, c2[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int j = 8 * g + v;
-          if (j < d) {
-            if (j >= mh) {
-              acc.x += g_term(R.problem, c1[v]);
-              acc.y += g_term(R.problem, c2[v]);
-            } else {
-              head[j] = c1[v];
-              head[mh + j] = c2[v];
+            for (int v = 0; v < 4; ++v) {
+              const int j = 8 * g + 4 * h + v;
+              if (j < mh) {
+                hb[j] = c1[v];
+                hb[kMaxM + j] = c2[v];
+              } else if (j < d) {
+                if (v & 1) {
+                  acc1.y = g_term1(PROB, c1[v], acc1.y);
+                  acc2.y = g_term1(PROB, c2[v], acc2.y);
+                } else {
+                  acc1.x = g_term1(PROB, c1[v], acc1.x);
+                  acc2.x = g_term1(PROB, c2[v], acc2.x);
+                }
+              }
             }
           }
         }
-      }
-      float4 *o1 = reinterpret_cast<float4 *>(y1p + 8 * g);
-      o1[0] = make_float4(c1[0], c1[1], c1[2], c1[3]);
-      o1[1] = make_float4(c1[4], c1[5], c1[6], c1[7]);
-      if (y2p) {
-        float4 *o2 = reinterpret_cast<float4 *>(y2p + 8 * g);
-        o2[0] = make_float4(c2[0], c2[1], c2[2], c2[3]);
-        o2[1] = make_float4(c2[4], c2[5], c2[6], c2[7]);
+        Y4[q1 + 2 * g + h] = make_float4(a0.x, a0.y, a1.x, a1.y);
+        if (has2) Y4[q2 + 2 * g + h] = make_float4(b0.x, b0.y, b1.x, b1.y);
       }
     }
   }
-  if (R.problem == PROB_NEURO) return;   // objectives come from the rollout kernel
-  const float2 gs = team_sum2(acc, TS, s_red);
-  __syncthreads();   // head[] written by other lanes of the team
+  if (!eval) return;   // objectives come from the rollout kernel
+
+  // ---- combine: team sum, then segments in order, then objectives ---------
+  const float2 gs = team_sum2(make_float2(acc1.x + acc1.y, acc2.x + acc2.y), TS);
   if (active && lane == 0) {
-    float f[kMaxM];
-    const int n2 = 2 * N;
-    dtlz_objectives(R.problem, m, gs.x, head, f);
-    const int s1 = s_chd[team][0];
-    for (int k = 0; k < m; ++k) {
-      R.F[(size_t)k * n2 + s1] = f[k];
-      atomicMin(&R.ctl->zkey[k], f2ord(f[k]));
-    }
-    if (has2) {
-      dtlz_objectives(R.problem, m, gs.y, head + mh, f);
-      const int s2 = s_chd[team][1];
-      for (int k = 0; k < m; ++k) {
-        R.F[(size_t)k * n2 + s2] = f[k];
-        atomicMin(&R.ctl->zkey[k], f2ord(f[k]));
-      }
-    }
+    float *ps = R.psum + (size_t)p * 2 * S;
+    ps[seg] = gs.x;
+    ps[S + seg] = gs.y;
   }
+  __threadfence();   // this lane's child rows, head values and partials
+  __syncwarp();
+  if (active && lane == 0) {
+    const int prev = atomicAdd(&R.pcnt[p], 1);
+    if (prev == S - 1) finish_pair(R, p, S, ch1, ch2);
+  }
+}
+
+template <class KP>
+__device__ __forceinline__ void repro_dispatch(const BatchDir &dir, const KP &kp) {
+  const int run = dir_find(dir, blockIdx.x);
+  switch (dir.desc[run]->problem) {
+    case PROB_DTLZ1: repro_body<PROB_DTLZ1>(dir, kp); return;
+    case PROB_DTLZ2: repro_body<PROB_DTLZ2>(dir, kp); return;
+    default: repro_body<PROB_NEURO>(dir, kp); return;
+  }
+}
+
+// One run of a known problem: the Philox round keys come in the parameter
+// block.
+__global__ void __launch_bounds__(kReproThreads, 3)
+k_repro1_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {
+  repro_body<PROB_DTLZ1>(dir, KeyConst{rk});
+}
+__global__ void __launch_bounds__(kReproThreads, 3)
+k_repro1_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {
+  repro_body<PROB_DTLZ2>(dir, KeyConst{rk});
+}
+__global__ void __launch_bounds__(kReproThreads, 3)
+k_repro1_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {
+  repro_body<PROB_NEURO>(dir, KeyConst{rk});
+}
+
+// A batch of runs: each CTA's round keys follow from its run's key.
+__global__ void __launch_bounds__(kReproThreads, 3)
+k_repro(const __grid_constant__ BatchDir dir) {
+  const int run = dir_find(dir, blockIdx.x);
+  repro_dispatch(dir, KeyRun{dir.key[run].x, dir.key[run].y});
 }
 
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
@@ -338,7 +476,6 @@ k_repro(const __grid_constant__ BatchDir dir) {
 __global__ void __launch_bounds__(kReproThreads)
 k_init(const __grid_constant__ BatchDir dir) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ float2 s_red[kReproThreads / 32];
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const ReproItem it = static_cast<const ReproItem *>(dir.items[run])[blockIdx.x - dir.prefix[run]];
@@ -347,7 +484,7 @@ k_init(const __grid_constant__ BatchDir dir) {
   const int m = R.m, d = R.d, G = R.G, N = R.N;
   const int i = it.pair0 + team;   // one team per individual
   const bool active = i < N;
-  const uint32_t k0 = R.key0, k1 = R.key1;
+  const uint32_t k0 = dir.key[run].x, k1 = dir.key[run].y;
   const int mh = m - 1;
   float *head = reinterpret_cast<float *>(dyn) + team * (mh > 0 ? mh : 1);
   float2 acc = make_float2(0.f, 0.f);
@@ -375,7 +512,7 @@ k_init(const __grid_constant__ BatchDir dir) {
         const int j = 8 * g + v;
         if (j >= d) x[v] = 0.0f;   // zero padding
         else if (R.problem != PROB_NEURO) {
-          if (j >= mh) acc.x += g_term(R.problem, x[v]);
+          if (j >= mh) acc.x = g_term1(R.problem, x[v], acc.x);
           else head[j] = x[v];
         }
       }
@@ -385,7 +522,7 @@ k_init(const __grid_constant__ BatchDir dir) {
     }
   }
   if (R.problem == PROB_NEURO) return;
-  const float2 gs = team_sum2(acc, TS, s_red);
+  const float2 gs = team_sum2(acc, TS);
   __syncthreads();
   if (active && lane == 0) {
     float f[kMaxM];
@@ -396,7 +533,5 @@ k_init(const __grid_constant__ BatchDir dir) {
     }
   }
 }
-
-int repro_smem_total(int TS, int m, int G) { return repro_smem_layout(TS, m, G).total; }
 
 }  // namespace rvea

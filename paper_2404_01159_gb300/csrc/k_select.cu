@@ -25,129 +25,192 @@ namespace rvea {
 __device__ __forceinline__ int sol_slot(const RunDesc &R, int i) {
   if (i >= R.n_comb) return -1;
   if (R.op_mode) return (R.valid_in == nullptr || R.valid_in[i]) ? i : -1;
-  if (i < R.N) return R.slotmap[i];
-  return R.child_slot[(R.ctl->t & 1) * R.N + (i - R.N)];
+  const int par = R.ctl->t & 1;
+  if (i < R.N) return R.slotmap[par * R.N + i];
+  return R.child_slot[par * R.N + (i - R.N)];
 }
 
 __device__ __forceinline__ float sol_f(const RunDesc &R, int slot, int k) {
   return R.op_mode ? R.F_aos[(size_t)slot * R.m + k] : R.F[(size_t)k * R.n_comb + slot];
 }
 
-// Running argmax of f'.v over one shared-memory tile, dot accumulated in the
-// fixed order f0 v0, then fma over k = 1..m-1.
+// Dot product f'.v in one fixed order (first product, then fma over k);
+// the scan and the rescan below evaluate it identically, bit for bit.
 template <int M>
-__device__ __forceinline__ void scan_tile(const float4 *__restrict__ tv, int nv, int jbase,
-                                          const float *fpin, float &best, int &bj) {
+__device__ __forceinline__ float dotv(const float *fp, const float4 *v) {
+  float d = __fmul_rn(fp[0], v[0].x);
+#pragma unroll
+  for (int k = 1; k < M; ++k) {
+    const float4 q = v[k >> 2];
+    const float c = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+    d = fmaf(fp[k], c, d);
+  }
+  return d;
+}
+
+// Chunk scan for two solutions: the running maximum of each 32-vector
+// sub-tile costs one FMNMX per dot; a sub-tile replaces the best only on a
+// strict improvement, so `sub` is the first sub-tile holding the maximum.
+template <int M>
+__device__ void scan_chunk(const float4 *__restrict__ sv, int nv, const float *fpa,
+                           const float *fpb, float &besta, int &suba, float &bestb, int &subb) {
+  constexpr int M4 = (M + 3) / 4;
+  float fa[M], fb[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) { fa[k] = fpa[k]; fb[k] = fpb[k]; }
+  for (int sub = 0; sub * 32 < nv; ++sub) {
+    const int n = min(32, nv - sub * 32);
+    const float4 *p = sv + (size_t)sub * 32 * M4;
+    float ma = -INFINITY, mb = -INFINITY;
+    if (n == 32) {
+#pragma unroll 8
+      for (int jj = 0; jj < 32; ++jj) {
+        float4 v[M4];
+#pragma unroll
+        for (int q = 0; q < M4; ++q) v[q] = p[jj * M4 + q];
+        ma = fmaxf(ma, dotv<M>(fa, v));
+        mb = fmaxf(mb, dotv<M>(fb, v));
+      }
+    } else {
+      for (int jj = 0; jj < n; ++jj) {
+        float4 v[M4];
+#pragma unroll
+        for (int q = 0; q < M4; ++q) v[q] = p[jj * M4 + q];
+        ma = fmaxf(ma, dotv<M>(fa, v));
+        mb = fmaxf(mb, dotv<M>(fb, v));
+      }
+    }
+    if (ma > besta) { besta = ma; suba = sub; }
+    if (mb > bestb) { bestb = mb; subb = sub; }
+  }
+}
+
+// First vector of sub-tile `sub` whose dot equals `best` (same arithmetic).
+template <int M>
+__device__ int find_first(const float4 *__restrict__ sv, int nv, int sub, const float *fpin,
+                          float best) {
   constexpr int M4 = (M + 3) / 4;
   float fp[M];
 #pragma unroll
   for (int k = 0; k < M; ++k) fp[k] = fpin[k];
-#pragma unroll 4
-  for (int jj = 0; jj < nv; ++jj) {
-    float v[M4 * 4];
+  const int j0 = sub * 32, j1 = min(nv, j0 + 32);
+  for (int jj = j0; jj < j1; ++jj) {
+    float4 v[M4];
 #pragma unroll
-    for (int q = 0; q < M4; ++q) {
-      const float4 t4 = tv[jj * M4 + q];
-      v[4 * q] = t4.x; v[4 * q + 1] = t4.y; v[4 * q + 2] = t4.z; v[4 * q + 3] = t4.w;
-    }
-    float dot = fp[0] * v[0];
-#pragma unroll
-    for (int k = 1; k < M; ++k) dot = fmaf(fp[k], v[k], dot);
-    if (dot > best) { best = dot; bj = jbase + jj; }
+    for (int q = 0; q < M4; ++q) v[q] = sv[(size_t)jj * M4 + q];
+    if (dotv<M>(fp, v) == best) return jj;
   }
+  return j0;
 }
 
-__device__ __forceinline__ void scan_tile_rt(const float4 *__restrict__ tv, int nv, int jbase,
-                                             int m, int m4, const float *fp, float &best,
-                                             int &bj) {
+template <int M>
+__device__ void scan_pair(const float4 *sv, int nv, const float *fpa, const float *fpb,
+                          bool va, bool vb, int &ja, float &ba, int &jb, float &bb) {
+  int sa = 0, sb = 0;
+  ba = -INFINITY;
+  bb = -INFINITY;
+  scan_chunk<M>(sv, nv, fpa, fpb, ba, sa, bb, sb);
+  ja = va ? find_first<M>(sv, nv, sa, fpa, ba) : 0;
+  jb = vb ? find_first<M>(sv, nv, sb, fpb, bb) : 0;
+}
+
+__device__ void scan_pair_rt(int m, const float4 *sv, int nv, const float *fpa, const float *fpb,
+                             bool va, bool vb, int &ja, float &ba, int &jb, float &bb) {
   switch (m) {
-    case 2: scan_tile<2>(tv, nv, jbase, fp, best, bj); return;
-    case 3: scan_tile<3>(tv, nv, jbase, fp, best, bj); return;
-    case 4: scan_tile<4>(tv, nv, jbase, fp, best, bj); return;
-    case 5: scan_tile<5>(tv, nv, jbase, fp, best, bj); return;
-    case 6: scan_tile<6>(tv, nv, jbase, fp, best, bj); return;
-    case 8: scan_tile<8>(tv, nv, jbase, fp, best, bj); return;
-    case 10: scan_tile<10>(tv, nv, jbase, fp, best, bj); return;
-    default: break;
-  }
-  for (int jj = 0; jj < nv; ++jj) {
-    const float *v = reinterpret_cast<const float *>(tv + jj * m4);
-    float dot = fp[0] * v[0];
-    for (int k = 1; k < m; ++k) dot = fmaf(fp[k], v[k], dot);
-    if (dot > best) { best = dot; bj = jbase + jj; }
+    case 2: scan_pair<2>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 3: scan_pair<3>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 4: scan_pair<4>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 5: scan_pair<5>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 6: scan_pair<6>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 7: scan_pair<7>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 8: scan_pair<8>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 9: scan_pair<9>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 10: scan_pair<10>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 11: scan_pair<11>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 12: scan_pair<12>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 13: scan_pair<13>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 14: scan_pair<14>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    case 15: scan_pair<15>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
+    default: scan_pair<16>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
   }
 }
 
+// APD (Eq. 4) of a solution and its vote in best[j].
+__device__ __forceinline__ void apd_vote(const RunDesc &R, int i, const float *fp) {
+  const int m = R.m;
+  const unsigned long long key = atomicExch(&R.amax[i], 0ull);
+  const int j = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+  const float dot = ord2f((unsigned)(key >> 32));
+  float s = fp[0] * fp[0];
+  for (int k = 1; k < m; ++k) s = fmaf(fp[k], fp[k], s);
+  const float nf = sqrtf(s);
+  float theta = 1.5707963267948966f;
+  if (nf > 0.0f) theta = acosf(fminf(1.0f, fmaxf(-1.0f, dot / nf)));
+  const int t = R.op_mode ? R.t_op : R.ctl->t;
+  const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
+  if (j < 0 || j >= R.N) {
+    set_status(R.ctl, ST_BADINDEX);
+    return;
+  }
+  const float apd = (1.0f + pen * theta / R.gamma32[j]) * nf;
+  R.assoc[i] = j;
+  atomicMin(&R.best[j], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
+}
+
+// One item: 256 solutions (two per thread) x one chunk of reference vectors,
+// the chunk staged in shared memory by one 1-D TMA bulk copy.
 __global__ void __launch_bounds__(kSelThreads)
 k_select(const __grid_constant__ BatchDir dir) {
-  extern __shared__ __align__(128) float4 s_v[];     // [2][kVTile * m4]
-  __shared__ __align__(8) uint64_t s_bar[2];
+  extern __shared__ __align__(128) float4 s_v[];     // [chunk vectors * m4]
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_last;
 
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const SelItem it = static_cast<const SelItem *>(dir.items[run])[blockIdx.x - dir.prefix[run]];
   const int m = R.m, m4 = R.m4;
-  const int i = it.sblk * kSelThreads + threadIdx.x;
-  const int slot = sol_slot(R, i);
-
-  float fp[kMaxM];
-#pragma unroll
-  for (int k = 0; k < kMaxM; ++k) fp[k] = 0.0f;
-  if (slot >= 0) {
-    for (int k = 0; k < m; ++k) fp[k] = sol_f(R, slot, k) - ord2f(R.ctl->zkey[k]);
+  const int ia = it.sblk * 2 * kSelThreads + threadIdx.x, ib = ia + kSelThreads;
+  const int sa = sol_slot(R, ia), sb = sol_slot(R, ib);
+  if (!R.op_mode && blockIdx.x == dir.prefix[run] && threadIdx.x < kMaxM) {
+    R.ctl->znext[threadIdx.x] = 0xFFFFFFFFu;   // built by the next kernel
+    R.ctl->zhi[threadIdx.x] = 0u;
   }
-
-  // ---- stream reference-vector tiles of [v0, v1) -------------------------
-  const int nv_all = it.v1 - it.v0;
-  const int ntiles = (nv_all + kVTile - 1) / kVTile;
-  const float4 *Vg = reinterpret_cast<const float4 *>(R.V32);
-  const int tile_f4 = kVTile * m4;
+  const int nv = it.v1 - it.v0;
+  const uint32_t bytes = (uint32_t)(nv * m4 * 16);
   if (threadIdx.x == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
+    mbar_init(&s_bar, 1);
     fence_mbar_init();
+    mbar_expect_tx(&s_bar, bytes);
+    tma_load_1d(s_v, reinterpret_cast<const float4 *>(R.V32) + (size_t)it.v0 * m4, bytes, &s_bar);
   }
-  __syncthreads();
-  auto issue = [&](int k) {
-    const int j0 = it.v0 + k * kVTile;
-    const int nv = min(kVTile, it.v1 - j0);
-    const uint32_t bytes = (uint32_t)(nv * m4 * 16);
-    uint64_t *bar = &s_bar[k & 1];
-    mbar_expect_tx(bar, bytes);
-    tma_load_1d(s_v + (k & 1) * tile_f4, Vg + (size_t)j0 * m4, bytes, bar);
-  };
-  if (threadIdx.x == 0) {
-    if (ntiles > 0) issue(0);
-    if (ntiles > 1) issue(1);
+  float fpa[kMaxM], fpb[kMaxM];
+#pragma unroll
+  for (int k = 0; k < kMaxM; ++k) { fpa[k] = 0.0f; fpb[k] = 0.0f; }
+  for (int k = 0; k < m; ++k) {
+    const float z = ord2f(R.ctl->zkey[k]);
+    if (sa >= 0) fpa[k] = sol_f(R, sa, k) - z;
+    if (sb >= 0) fpb[k] = sol_f(R, sb, k) - z;
   }
-  float best = -INFINITY;
-  int bj = it.v0;
-  bool ok = true;
-  for (int k = 0; k < ntiles; ++k) {
-    if (!mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimit)) ok = false;
-    if (__syncthreads_or(!ok)) {
-      // a bulk copy never completed: flag it, then give the copies in flight
-      // a bounded chance to land before this CTA's shared memory goes away
-      if (threadIdx.x == 0) {
-        set_status(R.ctl, ST_TIMEOUT);
-        for (int q = k; q < min(k + 2, ntiles); ++q)
-          mbar_wait(&s_bar[q & 1], (uint32_t)((q >> 1) & 1), kWaitLimit);
-      }
-      __syncthreads();
-      return;
+  __syncthreads();   // barrier initialised before anyone waits on it
+  const bool ok = mbar_wait(&s_bar, 0u, kWaitLimit);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      set_status(R.ctl, ST_TIMEOUT);
+      mbar_wait(&s_bar, 0u, kWaitLimit);   // give the copy a bounded chance to land
     }
-    const int j0 = it.v0 + k * kVTile;
-    const int nv = min(kVTile, it.v1 - j0);
-    if (slot >= 0) scan_tile_rt(s_v + (k & 1) * tile_f4, nv, j0, m, m4, fp, best, bj);
-    __syncthreads();   // every thread is done with this buffer
-    if (threadIdx.x == 0 && k + 2 < ntiles) issue(k + 2);
+    __syncthreads();
+    return;
   }
-
-  if (slot >= 0) {
-    const unsigned long long key =
-        ((unsigned long long)f2ord(best) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)bj);
-    atomicMax(&R.amax[i], key);
+  if (sa >= 0 || sb >= 0) {
+    int ja, jb;
+    float ba, bb;
+    scan_pair_rt(m, s_v, nv, fpa, fpb, sa >= 0, sb >= 0, ja, ba, jb, bb);
+    if (sa >= 0)
+      atomicMax(&R.amax[ia], ((unsigned long long)f2ord(ba) << 32) |
+                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(it.v0 + ja)));
+    if (sb >= 0)
+      atomicMax(&R.amax[ib], ((unsigned long long)f2ord(bb) << 32) |
+                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(it.v0 + jb)));
   }
   __threadfence();
   __syncthreads();
@@ -160,27 +223,10 @@ k_select(const __grid_constant__ BatchDir dir) {
 
   // ---- last chunk of this block: APD and per-vector argmin ---------------
   __threadfence();
-  if (slot >= 0) {
-    const unsigned long long key = atomicExch(&R.amax[i], 0ull);
-    const int j = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
-    const float dot = ord2f((unsigned)(key >> 32));
-    float s = fp[0] * fp[0];
-    for (int k = 1; k < m; ++k) s = fmaf(fp[k], fp[k], s);
-    const float nf = sqrtf(s);
-    float theta = 1.5707963267948966f;
-    if (nf > 0.0f) theta = acosf(fminf(1.0f, fmaxf(-1.0f, dot / nf)));
-    const int t = R.op_mode ? R.t_op : R.ctl->t;
-    const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
-    if (j < 0 || j >= R.N) {
-      set_status(R.ctl, ST_BADINDEX);
-    } else {
-      const float apd = (1.0f + pen * theta / R.gamma32[j]) * nf;
-      R.assoc[i] = j;
-      atomicMin(&R.best[j], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
-    }
-  } else if (i < R.n_comb) {
-    R.assoc[i] = -1;
-  }
+  if (sa >= 0) apd_vote(R, ia, fpa);
+  else if (ia < R.n_comb) R.assoc[ia] = -1;
+  if (sb >= 0) apd_vote(R, ib, fpb);
+  else if (ib < R.n_comb) R.assoc[ib] = -1;
   if (threadIdx.x == 0) R.blk_cnt[it.sblk] = 0;
 }
 
@@ -192,7 +238,7 @@ __global__ void k_op_prep(const RunDesc *__restrict__ Rp) {
   const int nth = gridDim.x * blockDim.x;
   for (int j = tid; j < R.N; j += nth) R.best[j] = ~0ull;
   for (int i = tid; i < R.n_comb; i += nth) R.amax[i] = 0ull;
-  const int nblk = (R.n_comb + kSelThreads - 1) / kSelThreads;
+  const int nblk = (R.n_comb + 2 * kSelThreads - 1) / (2 * kSelThreads);
   for (int b = tid; b < nblk; b += nth) R.blk_cnt[b] = 0;
   if (tid == 0) {
     R.ctl->t = R.t_op;

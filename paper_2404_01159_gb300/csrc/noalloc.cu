@@ -64,7 +64,7 @@ Carve carve(int n, int r, int m, int n_items) {
     o = up256(o + b);
     return at;
   };
-  const int nblk = (n + kSelThreads - 1) / kSelThreads;
+  const int nblk = (n + kSelBlock - 1) / kSelBlock;
   c.ctl = take(sizeof(Ctl));
   c.desc = take(sizeof(RunDesc));
   c.best = take((size_t)r * 8);
@@ -116,12 +116,10 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   if (m < 2 || m > kMaxM || n < 1 || r < 1 || !F || !V || !gamma || !assoc || !survivor ||
       t_max < 1 || !(alpha > 0.0f))
     return RVEA_ERR_ARG;
-  // work items: every block of 256 solutions x chunks of whole vector tiles
-  const int nblk = (n + kSelThreads - 1) / kSelThreads;
-  const int tiles = (r + kVTile - 1) / kVTile;
-  int nch = std::max(1, std::min(tiles, (4 * kSMCount + nblk - 1) / nblk));
-  const int tpc = (tiles + nch - 1) / nch;
-  nch = (tiles + tpc - 1) / tpc;
+  // work items: every block of solutions x every chunk of vectors
+  const int m4 = (m + 3) / 4;
+  const SelPlan sp = sel_plan(n, r, m4, kSMCount);
+  const int nblk = sp.nblk, nch = sp.nch;
   const int n_items = nblk * nch;
   if (n > kNoAllocMaxN || r > kNoAllocMaxR) return RVEA_ERR_NOMEM;
   const Carve c = carve(n, r, m, n_items);
@@ -131,7 +129,6 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   const rvea_status s0 = scratch_for_current_device(&ws);
   if (s0 != RVEA_OK) return s0;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const int m4 = (m + 3) / 4;
   float *V32 = reinterpret_cast<float *>(ws + c.v32);
   // zero-padded float4 rows of V (the padding must read as zero)
   if (cudaMemsetAsync(V32, 0, (size_t)r * m4 * 16, st) != cudaSuccess) return RVEA_ERR_CUDA;
@@ -156,7 +153,7 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   items.reserve(n_items);
   for (int b = 0; b < nblk; ++b)
     for (int q = 0; q < nch; ++q)
-      items.push_back(SelItem{b, std::min(r, q * tpc * kVTile), std::min(r, (q + 1) * tpc * kVTile), nch});
+      items.push_back(SelItem{b, std::min(r, q * sp.chunk), std::min(r, (q + 1) * sp.chunk), nch});
   RunDesc *dD = reinterpret_cast<RunDesc *>(ws + c.desc);
   // pageable sources: staged by the driver before these calls return
   if (cudaMemcpyAsync(dD, &D, sizeof(D), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -172,7 +169,7 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   dir.prefix[1] = n_items;
   dir.desc[0] = dD;
   dir.items[0] = ws + c.items;
-  k_select<<<(unsigned)n_items, kSelThreads, 2 * kVTile * m4 * 16, st>>>(dir);
+  k_select<<<(unsigned)n_items, kSelThreads, std::min(r, sp.chunk) * m4 * 16, st>>>(dir);
   k_op_finish<<<(r + 255) / 256, 256, 0, st>>>(dD);
   return cudaGetLastError() == cudaSuccess ? RVEA_OK : RVEA_ERR_CUDA;
 }

@@ -15,7 +15,9 @@ namespace rvea {
 
 constexpr int kMaxM = 16;          // objectives
 constexpr int kReproThreads = 256; // CTA size of the reproduction kernel
-constexpr int kSelThreads = 256;   // solutions per selection CTA
+constexpr int kLaneGroups = 8;     // 8-variable groups per lane per reproduction unit
+constexpr int kSelThreads = 128;   // selection CTA size (two solutions per thread)
+constexpr int kSelBlock = 2 * kSelThreads;   // solutions per selection work item
 constexpr int kVTile = 512;        // reference vectors per shared-memory tile
 constexpr int kFinThreads = 1024;  // CTA size of the per-run finalize kernel
 
@@ -36,7 +38,10 @@ struct Ctl {
   int K;               // number of valid population slots
   int status;          // ST_* bits
   int adapted;         // set by finalize on adaptation generations
-  unsigned zkey[kMaxM];  // ideal point z*, order-preserving uint encoding
+  int fin_cnt;         // arrival counter of the finalize CTAs
+  unsigned zkey[kMaxM];   // ideal point z*, order-preserving uint encoding
+  unsigned znext[kMaxM];  // minimum over the survivors (next z*), being built
+  unsigned zhi[kMaxM];    // maximum over the survivors (adaptation range)
 };
 
 struct RunDesc {
@@ -47,7 +52,8 @@ struct RunDesc {
   int n_comb;          // solutions entering selection (2N for a run)
   int problem;
   int t_max, p_adapt;
-  int team;            // threads per pair in reproduction (function of d)
+  int team;            // threads per reproduction team (power of two <= 32, function of d)
+  int nseg;            // segments per pair: a team handles 4*team groups of one pair
   int op_mode;         // 1: stateless selection (identity slots, AoS F)
   // parameters
   float L, U, alpha, inv_eta_c1, eta_m;
@@ -56,14 +62,20 @@ struct RunDesc {
   // state (pointers into the workspace)
   float *X;            // [2N][d_pad] population pool (physical slots)
   float *F;            // [m][2N]    objectives per physical slot (SoA)
-  int *slotmap;        // [N]        vector slot j -> physical slot, -1 invalid
+  int *slotmap;        // [2][N]     vector slot j -> physical slot (-1 invalid), by t & 1
+  uint32_t *vbits;     // [ceil(N/32)]  valid flags of P_{t+1} (bit j)
+  uint32_t *obits;     // [ceil(2N/32)] occupied pool rows of P_{t+1} (bit s)
+  uint32_t *zpart;     // [ceil(N/1024)][2][kMaxM] per-block survivor min / max
   int *vlist;          // [N]        ascending valid j (K entries)
   int *child_slot;     // [2][N]     physical slot of child c, by t & 1
   unsigned long long *best;   // [N]   packed (APD bits, combined index) minima
   unsigned long long *amax;   // [n_comb] packed (cosine bits, ~vector) maxima
   int *assoc;          // [n_comb]   vector of each solution, -1 if invalid
   int *surv;           // [N]        combined index kept by vector j, -1 if none
-  int *blk_cnt;        // [n_comb/256] arrival counters of selection blocks
+  float *psum;         // [P][2][nseg] partial g sums of the segments of each pair
+  float *hbuf;         // [P][2][kMaxM] first m-1 variables of each child
+  int *pcnt;           // [P]        arrival counters of the segments of each pair
+  int *blk_cnt;        // [n_comb/256] arrival counters of the selection blocks
   float *V32;          // [N][m4*4]  reference vectors, zero padded
   double *V64;         // [N][m]
   double *V0;          // [N][m]     initial unit lattice
@@ -83,11 +95,12 @@ struct RunDesc {
   float sigma;
 };
 
-// Work item of the reproduction kernel: one CTA, consecutive pairs of one run
-// (or consecutive individuals for the initialisation kernel).
+// Work item of the reproduction kernel: one CTA, consecutive work units of one
+// run (a unit is one segment of one pair; for the initialisation kernel, one
+// individual).
 struct ReproItem { int pair0; };
 // Work item of the selection kernel: one block of 256 solutions x one chunk
-// of reference vectors.
+// of reference vectors (the chunk fits in shared memory).
 struct SelItem { int sblk; int v0; int v1; int nchunks; };
 
 // Runs served by one launch, passed by value as a kernel parameter: CTA b
@@ -100,7 +113,31 @@ struct BatchDir {
   int prefix[kMaxBatch + 1];
   const RunDesc *desc[kMaxBatch];
   const void *items[kMaxBatch];
+  uint2 key[kMaxBatch];   // Philox key of each run (uniform operands)
 };
+
+// Selection work plan: blocks of kSelBlock solutions x chunks of whole
+// kVTile-vector tiles, at least ~8 CTAs per SM overall, each chunk small
+// enough to sit in shared memory (kSelChunkBytes).
+constexpr int kSelChunkBytes = 96 * 1024;
+struct SelPlan {
+  int nblk, nch, chunk;   // solution blocks, chunks, vectors per chunk
+};
+inline SelPlan sel_plan(int n, int r, int m4, int sms) {
+  SelPlan p;
+  p.nblk = (n + kSelBlock - 1) / kSelBlock;
+  const int tiles = (r + kVTile - 1) / kVTile;
+  int cap = kSelChunkBytes / (m4 * 16) / kVTile;
+  if (cap < 1) cap = 1;
+  int nch = (8 * sms + p.nblk - 1) / p.nblk;
+  if (nch > tiles) nch = tiles;
+  if (nch < 1) nch = 1;
+  int tpc = (tiles + nch - 1) / nch;
+  if (tpc > cap) tpc = cap;
+  p.nch = (tiles + tpc - 1) / tpc;
+  p.chunk = tpc * kVTile;
+  return p;
+}
 
 __device__ __forceinline__ int dir_find(const BatchDir &dir, int b) {
   int lo = 0, hi = dir.n - 1;
@@ -110,6 +147,33 @@ __device__ __forceinline__ int dir_find(const BatchDir &dir, int b) {
   }
   return lo;
 }
+
+// Round keys of Philox4x32-10 for one key: k_r = key + r * (W0, W1).  Passed
+// by value as a kernel parameter, each round's key is a constant-bank
+// operand instead of a register.
+struct RoundKeys {
+  uint32_t k[20];
+};
+inline RoundKeys round_keys(uint32_t k0, uint32_t k1) {
+  RoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    rk.k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return rk;
+}
+
+// Key providers for philox_k: keys from a RoundKeys parameter, or computed.
+struct KeyConst {
+  const RoundKeys &rk;
+  __device__ __forceinline__ uint32_t k(int i) const { return rk.k[i]; }
+};
+struct KeyRun {
+  uint32_t k0, k1;
+  __device__ __forceinline__ uint32_t k(int i) const {
+    return (i & 1) ? k1 + (uint32_t)(i >> 1) * 0xBB67AE85u : k0 + (uint32_t)(i >> 1) * 0x9E3779B9u;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
@@ -126,6 +190,19 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2,
     const uint32_t n0 = bh ^ c1 ^ k0, n2 = ah ^ c3 ^ k1;
     c0 = n0; c1 = b; c2 = n2; c3 = a;
     k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+template <class KP>
+__device__ __forceinline__ uint4 philox_k(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          const KP &kp) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = 0xD2511F53u * c0, ah = __umulhi(0xD2511F53u, c0);
+    const uint32_t b = 0xCD9E8D57u * c2, bh = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = bh ^ c1 ^ kp.k(2 * r), n2 = ah ^ c3 ^ kp.k(2 * r + 1);
+    c0 = n0; c1 = b; c2 = n2; c3 = a;
   }
   return make_uint4(c0, c1, c2, c3);
 }
@@ -152,6 +229,38 @@ __device__ __forceinline__ float ord2f(unsigned o) {
 __device__ __forceinline__ void set_status(Ctl *ctl, int bits) {
   atomicOr(&ctl->status, bits);
 }
+
+// ---------------------------------------------------------------------------
+// Packed float pairs (Blackwell .f32x2 arithmetic): one instruction does the
+// same IEEE operation on both halves as two scalar instructions would.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long f2u(float2 a) {
+  return *reinterpret_cast<unsigned long long *>(&a);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long a) {
+  return *reinterpret_cast<float2 *>(&a);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 
 // ---------------------------------------------------------------------------
 // mbarrier / bulk-copy (TMA) helpers, inline PTX.
