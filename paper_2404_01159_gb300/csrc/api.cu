@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <new>
 #include <vector>
 
@@ -40,6 +41,8 @@ __global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin
 __global__ void k_op_prep(const RunDesc *Rp);
 __global__ void k_op_zstar(const RunDesc *Rp);
 __global__ void k_op_finish(const RunDesc *Rp);
+__global__ void k_select_pruned(const RunDesc *Rp);
+__global__ void k_tiles(const RunDesc *Rp);
 }  // namespace rvea
 
 using namespace rvea;
@@ -62,7 +65,18 @@ int pow2ceil(int x) {
 struct Shape {
   int m, m4, d, d_pad, G, N, P, n_comb, team, ppc, nseg;
   int n_repro, n_init, n_sel, nblk, nch, chunk;
+  int tmax;     // tiles of the pruned selection (0: not used)
 };
+
+// Pruned selection: m <= 4 and the tile-ordered vectors plus the tile table
+// fit one CTA's shared memory (about 12k vectors).
+constexpr int kPruneMinN = 1000;
+constexpr size_t kPruneSmemCap = 200 * 1024;
+int prune_tiles_bound(int N) { return N / 16 + 2; }
+size_t prune_smem(int N, int T) {
+  const size_t bS = ((size_t)T * 8 + 15) & ~size_t(15);
+  return (size_t)N * 16 + (size_t)T * 16 + 2 * bS;
+}
 
 // Reproduction teams: TS lanes (a power of two <= 32) per work unit of
 // kLaneGroups*TS groups of 8 variables; a pair has nseg = ceil(G / (kLaneGroups TS))
@@ -88,12 +102,16 @@ Shape make_shape(int m, int d, int N) {
   s.nch = sp.nch;
   s.chunk = sp.chunk;
   s.n_sel = s.nblk * s.nch;
+  s.tmax = 0;
+  if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap)
+    s.tmax = prune_tiles_bound(N);
   return s;
 }
 
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V64, V0, g64, g32,
-      ctl, desc, repro, init, sel, stage, psum, hbuf, pcnt, noise, dynA, dynB, total;
+      ctl, desc, repro, init, sel, stage, psum, hbuf, pcnt, Vt, tperm, trng, tcen, tcs, noise,
+      dynA, dynB, total;
 };
 
 Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
@@ -131,6 +149,12 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
   L.hbuf = take((size_t)s.P * 2 * kMaxM * 4);
   L.pcnt = take((size_t)s.P * 4);
+  const size_t T = (size_t)s.tmax;
+  L.Vt = take(s.tmax ? (size_t)s.N * 16 : 0);
+  L.tperm = take(s.tmax ? (size_t)s.N * 4 : 0);
+  L.trng = take(T * 8 + 16);
+  L.tcen = take(T * 16);
+  L.tcs = take(T * 8 + 16);
   L.noise = take((size_t)steps_max * ns_max * 4);
   L.dynA = take((size_t)ns_max * ns_max * 4);
   L.dynB = take((size_t)ns_max * na_max * 4);
@@ -177,6 +201,46 @@ void build_lattice(int m, int H, int N, std::vector<double> &V0) {
   }
 }
 
+// Spatially compact tiles of <= 32 reference vectors: recursive split of
+// the initial lattice along its widest coordinate (cuts at multiples of 32
+// while the part is large, then in halves).  Returns the tile-order
+// permutation and each tile's (first position, count).
+void build_tiles(const std::vector<double> &V0, int N, int m, std::vector<int> &perm,
+                 std::vector<int2> &rng) {
+  perm.resize(N);
+  for (int j = 0; j < N; ++j) perm[j] = j;
+  rng.clear();
+  std::vector<std::pair<int, int>> todo{{0, N}};
+  while (!todo.empty()) {
+    const auto [a, b] = todo.back();
+    todo.pop_back();
+    const int n = b - a;
+    if (n <= 32) {
+      rng.push_back(make_int2(a, n));
+      continue;
+    }
+    int axis = 0;
+    double spread = -1.0;
+    for (int k = 0; k < m; ++k) {
+      double lo = 1e300, hi = -1e300;
+      for (int q = a; q < b; ++q) {
+        const double v = V0[(size_t)perm[q] * m + k];
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+      if (hi - lo > spread) { spread = hi - lo; axis = k; }
+    }
+    std::stable_sort(perm.begin() + a, perm.begin() + b, [&](int x, int y) {
+      return V0[(size_t)x * m + axis] < V0[(size_t)y * m + axis];
+    });
+    int h = n / 2;
+    if (n > 64) h = std::max(32, h / 32 * 32);
+    todo.push_back({a + h, b});
+    todo.push_back({a, a + h});
+  }
+  std::sort(rng.begin(), rng.end(), [](int2 x, int2 y) { return x.x < y.x; });
+}
+
 uint32_t event_threshold24(double q) {
   double x = std::ceil(q * 16777216.0);
   if (x < 0.0) x = 0.0;
@@ -219,6 +283,7 @@ void set_kernel_attrs() {
   set((const void *)k_repro1_neuro);
   set((const void *)k_init);
   set((const void *)k_select);
+  set((const void *)k_select_pruned);
 
   g_attr_err = e;
 }
@@ -239,6 +304,7 @@ struct rvea_run {
   RunDesc hd;                     // host copy of the device descriptor
   RunDesc *d_desc = nullptr;
   int repro_smem = 0, init_smem = 0, sel_smem = 0, fin_smem = 0;
+  int prune_smem_bytes = 0, num_sms = 152;
   cudaStream_t last_stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t block_graph = nullptr;
@@ -321,7 +387,10 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     launch_repro1(runs[0], dr, pr, st);
   else
     k_repro<<<pr, kReproThreads, smr, st>>>(dr);
-  k_select<<<ps, kSelThreads, sms, st>>>(ds);
+  if (n == 1 && runs[0]->hd.ntiles > 0)
+    k_select_pruned<<<runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st>>>(runs[0]->d_desc);
+  else
+    k_select<<<ps, kSelThreads, sms, st>>>(ds);
   k_finalize<<<pd, 1024, 0, st>>>(dd);
   if (gamma_by_flag) {
     k_gamma<<<2 * kSMs, 256, 0, st>>>(df, 0);
@@ -337,13 +406,24 @@ rvea_status launch_gamma_force(rvea_run *r, cudaStream_t st) {
   return cuerr(cudaGetLastError());
 }
 
-// One generation of a single run; gamma is enqueued by the host when the
-// generation adapts (t % p_adapt == 0), so no launch is spent otherwise.
+// Tile table of the pruned selection after a change of V.
+rvea_status launch_tiles(rvea_run *r, cudaStream_t st) {
+  if (r->hd.ntiles == 0) return RVEA_OK;
+  k_tiles<<<(r->hd.ntiles + 7) / 8, 256, 0, st>>>(r->d_desc);
+  return cuerr(cudaGetLastError());
+}
+
+// One generation of a single run; gamma (and the tile table) are enqueued by
+// the host when the generation adapts (t % p_adapt == 0), so no launch is
+// spent otherwise.
 rvea_status enqueue_one(rvea_run *r, cudaStream_t st) {
   rvea_run *one[1] = {r};
   rvea_status s = launch_generation(one, 1, st, false);
   if (s != RVEA_OK) return s;
-  if (r->t % r->p_adapt == 0) s = launch_gamma_force(r, st);
+  if (r->t % r->p_adapt == 0) {
+    s = launch_gamma_force(r, st);
+    if (s == RVEA_OK) s = launch_tiles(r, st);
+  }
   return s;
 }
 
@@ -511,6 +591,22 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     }
   std::vector<double> V0;
   build_lattice(sh.m, cfg->H, sh.N, V0);
+  std::vector<int> tperm;
+  std::vector<int2> trng;
+  if (sh.tmax > 0) {
+    build_tiles(V0, sh.N, sh.m, tperm, trng);
+    if ((int)trng.size() > sh.tmax) trng.clear();   // cannot happen; keeps the bound honest
+  }
+  D.ntiles = (int)trng.size();
+  if (D.ntiles > 0) {
+    D.Vt = wsp<float4>(r, lay.Vt);
+    D.tperm = wsp<int>(r, lay.tperm);
+    D.trng = wsp<int2>(r, lay.trng);
+    D.tcen = wsp<float4>(r, lay.tcen);
+    D.tcs = wsp<float2>(r, lay.tcs);
+    r->prune_smem_bytes = (int)prune_smem(sh.N, D.ntiles);
+  }
+  cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
   std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f);
   for (int j = 0; j < sh.N; ++j)
     for (int k = 0; k < sh.m; ++k) V32[(size_t)j * sh.m4 * 4 + k] = (float)V0[(size_t)j * sh.m + k];
@@ -533,6 +629,10 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.V64, V0.data(), V0.size() * 8);
   up(lay.V32, V32.data(), V32.size() * 4);
   up(lay.ctl, &c0, sizeof(c0));
+  if (D.ntiles > 0) {
+    up(lay.tperm, tperm.data(), tperm.size() * 4);
+    up(lay.trng, trng.data(), trng.size() * sizeof(int2));
+  }
   if (s == RVEA_OK) {
     static thread_local BatchDir d;
     dir_single(d, r, wsp<ReproItem>(r, lay.init), sh.n_init);
@@ -541,6 +641,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     k_init_lists<<<dim3((sh.N + 255) / 256, 1), 256, 0, st>>>(d);
     s = cuerr(cudaGetLastError());
     if (s == RVEA_OK) s = launch_gamma_force(r, st);
+    if (s == RVEA_OK) s = launch_tiles(r, st);
   }
   // pageable host sources above must stay valid until their copies are done
   if (s == RVEA_OK) s = cuerr(cudaStreamSynchronize(st));
@@ -639,11 +740,17 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     cudaEventRecord(e[0], st);
     launch_repro1(r, dr, r->sh.n_repro, st);
     cudaEventRecord(e[1], st);
-    k_select<<<r->sh.n_sel, kSelThreads, r->sel_smem, st>>>(ds);
+    if (r->hd.ntiles > 0)
+      k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
+    else
+      k_select<<<r->sh.n_sel, kSelThreads, r->sel_smem, st>>>(ds);
     cudaEventRecord(e[2], st);
     k_finalize<<<nbd, 1024, 0, st>>>(dd);
     cudaEventRecord(e[3], st);
-    if (r->t % r->p_adapt == 0) k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
+    if (r->t % r->p_adapt == 0) {
+      k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
+      launch_tiles(r, st);
+    }
     cudaEventRecord(e[4], st);
     s = cuerr(cudaGetLastError());
     r->t += 1;
@@ -745,6 +852,7 @@ rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const
   RV_TRY(cudaMemcpyAsync(r->hd.gamma64, gamma, (size_t)sh.N * 8, cudaMemcpyDefault, st));
   k_import<<<1, kFinThreads, 0, st>>>(r->d_desc, sf, sv, t);
   RV_TRY(cudaGetLastError());
+  if (launch_tiles(r, st) != RVEA_OK) return RVEA_ERR_CUDA;
   RV_TRY(cudaStreamSynchronize(st));
   r->t = t;
   r->last_stream = st;

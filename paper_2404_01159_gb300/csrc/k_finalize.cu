@@ -202,6 +202,7 @@ k_finalize(const __grid_constant__ BatchDir dir) {
     R.ctl->K = K;
     R.ctl->adapted = adapt ? 1 : 0;
     R.ctl->fin_cnt = 0;
+    R.ctl->sel_cnt = 0;
     R.ctl->t = t + 1;
   }
 }
@@ -450,6 +451,8 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
     R.ctl->t = t;
     R.ctl->status = 0;
     R.ctl->adapted = 0;
+    R.ctl->fin_cnt = 0;
+    R.ctl->sel_cnt = 0;
   }
 }
 

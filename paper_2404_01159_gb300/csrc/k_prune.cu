@@ -1,0 +1,271 @@
+// Exact pruned association for m <= 4 (Algorithm 1 lines 5-6, Eq. 2).
+//
+// The reference vectors are grouped into spatially compact tiles of <= 32
+// (a k-d split of the initial lattice, fixed for the run).  Each tile has a
+// float32 unit centre c and an angle rho that bounds the angle from c to
+// every member.  For a solution f' (norm nf), once some vector reaches the
+// float dot `best`, a tile whose centre makes an angle phi with f' can hold
+// a larger dot only if phi <= acos(best / nf) + rho, i.e. only if
+//   f'.c >= best cos(rho) - sqrt(nf^2 - best^2) sin(rho)      (1)
+// (cos(acos(b) + rho) = b cos rho - sqrt(1 - b^2) sin rho).  The test is
+// evaluated with margins that cover every float32 rounding involved -- the
+// dots of f' with c and with the members (<= 1e-6 nf each for unit rows and
+// m <= 16), the norms of the float32 rows, the computed square root -- and
+// with cos(rho) rounded down and sin(rho) rounded up: a tile that fails it
+// holds only dots strictly below `best`.  The tiles that pass are scanned
+// with exactly the arithmetic of the full scan (same order of products),
+// keeping the larger dot and, on equal dots, the smaller vector index.  The
+// result is therefore the full scan's result bit for bit, found after
+// scanning ~2 tiles instead of all of them (lattice of 9870 vectors, m = 3).
+//
+// One persistent CTA per SM stages the tile-ordered vectors and the tile
+// table in shared memory with TMA bulk copies; its warps take four solutions
+// at a time from a work counter, eight lanes per solution, and cast each
+// solution's APD vote (Eq. 4) directly.
+#include "rvea_device.cuh"
+
+namespace rvea {
+
+constexpr int kPruneThreads = 1024;
+constexpr int kPruneCand = 4;   // candidate tiles kept per lane before the fallback
+
+// f'.v in the fixed order of the full scan: first product, then fma over k.
+template <int M>
+__device__ __forceinline__ float pdot(const float *f, float4 v) {
+  float d = __fmul_rn(f[0], v.x);
+  if (M > 1) d = fmaf(f[1], v.y, d);
+  if (M > 2) d = fmaf(f[2], v.z, d);
+  if (M > 3) d = fmaf(f[3], v.w, d);
+  return d;
+}
+
+// Vector index of tile-order position q: kept in the unused fourth lane of
+// the float4 row for m <= 3, read from the permutation for m = 4.
+template <int M>
+__device__ __forceinline__ int vidx(const RunDesc &R, float4 v, int q) {
+  return M < 4 ? __float_as_int(v.w) : R.tperm[q];
+}
+
+// Keeps (best, bj): larger dot, then smaller vector index.
+__device__ __forceinline__ void keep(float d, int j, float &best, int &bj) {
+  if (d > best || (d == best && j < bj)) { best = d; bj = j; }
+}
+
+template <int M>
+__device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
+                           const float2 *sCS, const int2 *sR) {
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int T = R.ntiles, N = R.N, n = R.n_comb, m = R.m;
+  const int t_gen = R.ctl->t;
+  const float pen = (float)m * powf((float)t_gen / (float)R.t_max, R.alpha);
+  float z[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) z[k] = k < M ? ord2f(R.ctl->zkey[k]) : 0.f;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&R.ctl->sel_cnt, 4);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    const int i = base + (lane >> 3);
+    int slot = -1;
+    if (i < n) {
+      const int par = t_gen & 1;
+      slot = i < N ? R.slotmap[par * N + i] : R.child_slot[par * N + (i - N)];
+    }
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    if (slot >= 0) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) f[k] = R.F[(size_t)k * n + slot] - z[k];
+    }
+    float s2 = f[0] * f[0];
+#pragma unroll
+    for (int k = 1; k < M; ++k) s2 = fmaf(f[k], f[k], s2);
+    const float nf = sqrtf(s2);
+
+    // pass 1: the tile whose centre is closest in angle
+    float dc1 = -INFINITY;
+    int t1 = 0;
+    for (int t = sub; t < T; t += 8) {
+      const float dc = pdot<M>(f, sC[t]);
+      if (dc > dc1) { dc1 = dc; t1 = t; }
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, dc1, off);
+      const int ot = __shfl_xor_sync(0xffffffffu, t1, off);
+      if (od > dc1 || (od == dc1 && ot < t1)) { dc1 = od; t1 = ot; }
+    }
+    // scan that tile
+    float best = -INFINITY;
+    int bj = 0x7FFFFFFF;
+    {
+      const int2 rg = sR[t1];
+      for (int q = sub; q < rg.y; q += 8) {
+        const float4 v = sV[rg.x + q];
+        keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) keep(__shfl_xor_sync(0xffffffffu, best, off),
+                                               __shfl_xor_sync(0xffffffffu, bj, off), best, bj);
+    // threshold (1) with margins
+    const float Bn = (best - 1e-6f * nf) * (1.0f - 4e-7f);
+    const float Sn = sqrtf(fmaxf(0.0f, (nf - Bn) + 4e-7f * nf) * (nf + fabsf(Bn)));
+    const float slack = 3e-6f * nf;
+    // pass 2: tiles that may hold a larger (or equal) dot
+    int cand[kPruneCand];
+    int nc = 0;
+    bool over = false;
+    for (int t = sub; t < T; t += 8) {
+      const float2 cs = sCS[t];
+      const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
+      if (t != t1 && pdot<M>(f, sC[t]) >= thr) {
+        if (nc < kPruneCand) {
+#pragma unroll
+          for (int c = 0; c < kPruneCand; ++c)
+            if (c == nc) cand[c] = t;
+          ++nc;
+        } else {
+          over = true;
+        }
+      }
+    }
+    // scan the candidates in lockstep (same instructions, per-lane tiles)
+    int ncmax = nc;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) ncmax = max(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, off));
+#pragma unroll
+    for (int c = 0; c < kPruneCand; ++c) {
+      if (c >= ncmax) break;
+      if (c < nc) {
+        const int2 rg = sR[cand[c]];
+        for (int q = 0; q < rg.y; ++q) {
+          const float4 v = sV[rg.x + q];
+          keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
+        }
+      }
+    }
+    if (over) {   // more candidates than kept: test and scan the rest here
+      int seen = 0;
+      for (int t = sub; t < T; t += 8) {
+        const float2 cs = sCS[t];
+        const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
+        if (t != t1 && pdot<M>(f, sC[t]) >= thr) {
+          if (seen++ < kPruneCand) continue;   // scanned above
+          const int2 rg = sR[t];
+          for (int q = 0; q < rg.y; ++q) {
+            const float4 v = sV[rg.x + q];
+            keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) keep(__shfl_xor_sync(0xffffffffu, best, off),
+                                               __shfl_xor_sync(0xffffffffu, bj, off), best, bj);
+    // APD (Eq. 4) and the vote of this solution in best[j]
+    if (sub == 0 && i < n) {
+      if (slot < 0) {
+        R.assoc[i] = -1;
+      } else if (bj < 0 || bj >= N) {
+        set_status(R.ctl, ST_BADINDEX);
+      } else {
+        float theta = 1.5707963267948966f;
+        if (nf > 0.0f) theta = acosf(fminf(1.0f, fmaxf(-1.0f, best / nf)));
+        const float apd = (1.0f + pen * theta / R.gamma32[bj]) * nf;
+        R.assoc[i] = bj;
+        atomicMin(&R.best[bj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDesc *__restrict__ Rp) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar;
+  const RunDesc &R = *Rp;
+  const int N = R.N, T = R.ntiles;
+  // layout: Vt [N] float4 | centres [T] float4 | (cos, sin) [T] float2 | ranges [T] int2
+  const uint32_t bV = (uint32_t)N * 16, bC = (uint32_t)T * 16, bS = (uint32_t)T * 8;
+  const uint32_t bSr = (bS + 15u) & ~15u;
+  float4 *sV = reinterpret_cast<float4 *>(smem);
+  float4 *sC = reinterpret_cast<float4 *>(smem + bV);
+  float2 *sCS = reinterpret_cast<float2 *>(smem + bV + bC);
+  int2 *sR = reinterpret_cast<int2 *>(smem + bV + bC + bSr);
+  if (blockIdx.x == 0 && threadIdx.x < kMaxM) {
+    R.ctl->znext[threadIdx.x] = 0xFFFFFFFFu;   // built by the finalize kernel
+    R.ctl->zhi[threadIdx.x] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
+    tma_load_1d(sV, R.Vt, bV, &s_bar);
+    tma_load_1d(sC, R.tcen, bC, &s_bar);
+    tma_load_1d(sCS, R.tcs, bSr, &s_bar);
+    tma_load_1d(sR, R.trng, bSr, &s_bar);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&s_bar, 0u, kWaitLimit);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      set_status(R.ctl, ST_TIMEOUT);
+      mbar_wait(&s_bar, 0u, kWaitLimit);
+    }
+    __syncthreads();
+    return;
+  }
+  switch (R.m) {
+    case 2: prune_loop<2>(R, sV, sC, sCS, sR); break;
+    case 3: prune_loop<3>(R, sV, sC, sCS, sR); break;
+    default: prune_loop<4>(R, sV, sC, sCS, sR); break;
+  }
+}
+
+// Tile table after a change of V: members in tile order, float32 centres,
+// and conservative (cos rho, sin rho) computed in FP64 from the float32 rows.
+// One warp per tile.
+__global__ void k_tiles(const RunDesc *__restrict__ Rp) {
+  const RunDesc &R = *Rp;
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= R.ntiles) return;
+  const int2 rg = R.trng[t];
+  const int m4 = R.m4;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < rg.y) {
+    const int j = R.tperm[rg.x + lane];
+    v = reinterpret_cast<const float4 *>(R.V32)[(size_t)j * m4];
+    float4 vt = v;
+    if (R.m < 4) vt.w = __int_as_float(j);   // the member's vector index rides along
+    R.Vt[rg.x + lane] = vt;
+  }
+  // centre: normalised mean of the members
+  float sx = v.x, sy = v.y, sz = v.z, sw = v.w;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+    sz += __shfl_xor_sync(0xffffffffu, sz, off);
+    sw += __shfl_xor_sync(0xffffffffu, sw, off);
+  }
+  const double cn = sqrt((double)sx * sx + (double)sy * sy + (double)sz * sz + (double)sw * sw);
+  const float4 c = make_float4((float)(sx / cn), (float)(sy / cn), (float)(sz / cn), (float)(sw / cn));
+  // rho: the largest angle centre-member, both float32 rows normalised in FP64
+  double cmin = 1.0;
+  if (lane < rg.y) {
+    const double vn = sqrt((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w);
+    const double ccn = sqrt((double)c.x * c.x + (double)c.y * c.y + (double)c.z * c.z + (double)c.w * c.w);
+    const double cosang = ((double)v.x * c.x + (double)v.y * c.y + (double)v.z * c.z + (double)v.w * c.w) / (vn * ccn);
+    cmin = fmin(1.0, cosang);
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) cmin = fmin(cmin, __shfl_xor_sync(0xffffffffu, cmin, off));
+  if (lane == 0) {
+    const double rho = fmin(1.5707963267948966, acos(fmax(-1.0, cmin)) + 1e-6);
+    R.tcen[t] = c;
+    R.tcs[t] = make_float2(__double2float_rd(cos(rho)), __double2float_ru(sin(rho)));
+  }
+}
+
+}  // namespace rvea

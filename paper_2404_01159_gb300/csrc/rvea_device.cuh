@@ -39,6 +39,7 @@ struct Ctl {
   int status;          // ST_* bits
   int adapted;         // set by finalize on adaptation generations
   int fin_cnt;         // arrival counter of the finalize CTAs
+  int sel_cnt;         // work counter of the pruned selection kernel
   unsigned zkey[kMaxM];   // ideal point z*, order-preserving uint encoding
   unsigned znext[kMaxM];  // minimum over the survivors (next z*), being built
   unsigned zhi[kMaxM];    // maximum over the survivors (adaptation range)
@@ -82,6 +83,13 @@ struct RunDesc {
   double *gamma64;     // [N]
   float *gamma32;      // [N]
   Ctl *ctl;
+  // pruned selection: reference vectors grouped into spatially compact tiles
+  int ntiles;          // 0: the pruned kernel is not used for this run
+  float4 *Vt;          // [N]        V32 in tile order (m <= 4)
+  int *tperm;          // [N]        tile-order position -> vector index j
+  int2 *trng;          // [ntiles]   (first position, count <= 32) of each tile
+  float4 *tcen;        // [ntiles]   unit centre of each tile (float32)
+  float2 *tcs;         // [ntiles]   (cos rho, sin rho), rho >= max angle centre-member
   // stateless-selection views (op_mode)
   const float *F_aos;  // [n][m]
   const uint8_t *valid_in;  // [n] or null

@@ -189,9 +189,14 @@ def test_graph_replay_equals_direct_launches(orc):
 
 
 def test_batch_equals_alone(orc):
+    """A run stepped alone and the same run inside a batch give identical bits.
+    Alone, runs with m <= 4 and N >= 1000 take the pruned association kernel;
+    in a batch every run takes the full scan, so this also checks that the
+    pruning is exact."""
     from paper_2404_01159_gb300 import step_batch
     shapes = [(3, 12, 105, 13, 0, 1), (3, 1001, 210, 19, 1, 2), (10, 30, 220, 3, 0, 3),
-              (2, 203, 100, 99, 1, 4)]
+              (2, 203, 100, 99, 1, 4), (3, 64, 1275, 49, 1, 5), (2, 40, 1200, 1199, 0, 6),
+              (4, 20, 1771, 20, 0, 7)]
     ps = [params(orc, m, d, N, H, pr, t_max=30, seed=s) for (m, d, N, H, pr, s) in shapes]
     alone = [make_run(p) for p in ps]
     batch = [make_run(p) for p in ps]
