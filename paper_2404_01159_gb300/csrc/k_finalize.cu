@@ -127,9 +127,13 @@ k_finalize(const __grid_constant__ BatchDir dir) {
     R.zpart[(size_t)blk * 2 * kMaxM + threadIdx.x] = lo;
     R.zpart[(size_t)blk * 2 * kMaxM + kMaxM + threadIdx.x] = hi;
   }
-  __threadfence();
+  // the barrier orders every thread's writes before thread 0's (cumulative)
+  // fence, which orders them before its arrival
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&R.ctl->fin_cnt, 1) == nblk - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&R.ctl->fin_cnt, 1) == nblk - 1;
+  }
   __syncthreads();
   if (!s_last) return;
   __threadfence();

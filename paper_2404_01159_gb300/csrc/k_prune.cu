@@ -81,11 +81,16 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
 #pragma unroll
     for (int k = 1; k < M; ++k) s2 = fmaf(f[k], f[k], s2);
     const float nf = sqrtf(s2);
+    // invalid parents take no part; f' = 0 has every dot +0, where the full
+    // scan keeps vector 0 -- neither needs the search (all lanes still run
+    // the shuffles below, over empty loops)
+    const bool live = slot >= 0 && nf > 0.0f;
+    const int TT = live ? T : 0;
 
     // pass 1: the tile whose centre is closest in angle
     float dc1 = -INFINITY;
     int t1 = 0;
-    for (int t = sub; t < T; t += 8) {
+    for (int t = sub; t < TT; t += 8) {
       const float dc = pdot<M>(f, sC[t]);
       if (dc > dc1) { dc1 = dc; t1 = t; }
     }
@@ -99,7 +104,7 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     float best = -INFINITY;
     int bj = 0x7FFFFFFF;
     {
-      const int2 rg = sR[t1];
+      const int2 rg = live ? sR[t1] : make_int2(0, 0);
       for (int q = sub; q < rg.y; q += 8) {
         const float4 v = sV[rg.x + q];
         keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
@@ -116,7 +121,7 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     int cand[kPruneCand];
     int nc = 0;
     bool over = false;
-    for (int t = sub; t < T; t += 8) {
+    for (int t = sub; t < TT; t += 8) {
       const float2 cs = sCS[t];
       const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
       if (t != t1 && pdot<M>(f, sC[t]) >= thr) {
@@ -147,7 +152,7 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     }
     if (over) {   // more candidates than kept: test and scan the rest here
       int seen = 0;
-      for (int t = sub; t < T; t += 8) {
+      for (int t = sub; t < TT; t += 8) {
         const float2 cs = sCS[t];
         const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
         if (t != t1 && pdot<M>(f, sC[t]) >= thr) {
@@ -163,6 +168,7 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) keep(__shfl_xor_sync(0xffffffffu, best, off),
                                                __shfl_xor_sync(0xffffffffu, bj, off), best, bj);
+    if (slot >= 0 && !live) { best = 0.0f; bj = 0; }
     // APD (Eq. 4) and the vote of this solution in best[j]
     if (sub == 0 && i < n) {
       if (slot < 0) {

@@ -430,9 +430,11 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
     ps[seg] = gs.x;
     ps[S + seg] = gs.y;
   }
-  __threadfence();   // this lane's child rows, head values and partials
+  // the warp barrier orders the team's writes (child rows, head values,
+  // partials) before the leader's cumulative fence and its arrival
   __syncwarp();
   if (active && lane == 0) {
+    __threadfence();
     const int prev = atomicAdd(&R.pcnt[p], 1);
     if (prev == S - 1) finish_pair(R, p, S, ch1, ch2);
   }

@@ -212,9 +212,9 @@ k_select(const __grid_constant__ BatchDir dir) {
       atomicMax(&R.amax[ib], ((unsigned long long)f2ord(bb) << 32) |
                                  (unsigned long long)(0xFFFFFFFFu - (uint32_t)(it.v0 + jb)));
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();   // cumulative: orders the block's atomics before the arrival
     const int prev = atomicAdd(&R.blk_cnt[it.sblk], 1);
     s_last = (prev == it.nchunks - 1);
   }
