@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 DTLZ2, DTLZ1, NEURO = 0, 1, 2
-TAG_INIT, TAG_MATE, TAG_PAIR, TAG_SBX, TAG_MUTHI, TAG_MUTLO, TAG_NOISE = 1, 2, 3, 4, 5, 6, 7
+TAG_INIT, TAG_MATE, TAG_PAIR, TAG_SBX, TAG_MUTSITE, TAG_MUTMAG, TAG_NOISE = 1, 2, 3, 4, 5, 6, 7
 
 
 class Params(C.Structure):

@@ -414,48 +414,120 @@ void orc_sbx(const orc_params *p, int32_t t, const double *X1, const double *X2,
  *   Delta = (U-L)[(2M + (1-2M)(1-d1)^(xi+1))^(1/(xi+1)) - 1]   if M < 1/2
  *         = (U-L)[1 - (2(1-M) + 2(M-1/2)(1-d2)^(xi+1))^(1/(xi+1))]  if M > 1/2
  *   d1 = (x-L)/(U-L), d2 = (U-x)/(U-L).
- * The site fires iff R4 < p_m/d.  The formula assumes x in [L,U] while SBX
- * can leave the box: the reading clips to [L,U] before and after.
+ * The formula assumes x in [L,U] while SBX can leave the box: the reading
+ * clips to [L,U] before and after.
+ *
+ * The mask C.  Appendix B draws one uniform R4 per site: the sites of a row
+ * are independent events of probability q.  Here q is p_m/d on the 24-bit
+ * grid, q = ceil(2^24 p_m/d) 2^-24 (q >= 1: every site; q = 0: none), and the
+ * mask of row c is drawn in the equivalent count-then-subset form of that
+ * law: the number of sites k ~ Binomial(d, q), then a uniform k-subset of
+ * the d positions (given its size, the set of independent Bernoulli events
+ * is a uniform subset).  Both steps use Philox at counter (i/4, c, t, MUTSITE),
+ * word i%4, for draw i = 0, 1, 2, ...:
+ *   draw 0:  k = #{ i < min(d, 32) : w >= thr_i },  thr_i = floor(2^32 CDF(i))
+ *            (saturated at 2^32), CDF of Binomial(d, q) summed in FP64 from
+ *            pmf(0) = (1-q)^d (square-and-multiply over the bits of d, least
+ *            significant first) and pmf(i+1) = pmf(i) * (d-i) / (i+1) * (q/(1-q));
+ *   draws 1..k: Floyd's subset sampler: for i = 0..k-1, J = d-k+i,
+ *            r = (w * (J+1)) >> 32 (uniform in [0, J]); add J if r is already
+ *            in the set, else add r.
+ * Counts are capped at 32 (the caller keeps p_m <= 8, where the mass above 32
+ * is below 2^-32).  The magnitude of site (c, j) is M = u24(word 1) of Philox
+ * at (j, c, t, MUTMAG).
  * Xc holds the N kept offspring rows (the first N rows of X_cross), mutated
  * in place; mask (N x d, may be NULL) receives C. */
+static double pow_uint(double b, int32_t e)
+{
+    double r = 1.0;
+    while (e > 0) {
+        if (e & 1) r *= b;
+        b *= b;
+        e >>= 1;
+    }
+    return r;
+}
+
+/* thresholds of the site count; returns how many are below 2^32 (<= 32) */
+static int32_t site_count_thresholds(double q, int32_t d, uint64_t thr[32])
+{
+    const int32_t K = d < 32 ? d : 32;
+    const double ratio = q / (1.0 - q);
+    double pmf = pow_uint(1.0 - q, d), cdf = 0.0;
+    int32_t n = 0;
+    for (int32_t i = 0; i < K; ++i) {
+        if (i > 0) pmf = pmf * (double)(d - (i - 1)) / (double)i * ratio;
+        cdf += pmf;
+        if (cdf >= 1.0) break;
+        thr[n++] = (uint64_t)floor(cdf * 4294967296.0);
+    }
+    return n;
+}
+
+/* mutation sites of child row c (count-then-subset form above); returns k */
+static int32_t mutation_sites(const orc_params *p, int32_t t, int32_t c, int32_t n_thr,
+                              const uint64_t *thr, int32_t *sites)
+{
+    const int32_t d = p->d;
+    uint32_t w[4];
+    philox(p, 0u, (uint32_t)c, (uint32_t)t, ORC_TAG_MUTSITE, w);
+    int32_t k = 0;
+    for (int32_t i = 0; i < n_thr; ++i)
+        if ((uint64_t)w[0] >= thr[i]) k = i + 1;
+    for (int32_t i = 0; i < k; ++i) {
+        const int32_t e = i + 1;
+        if (e % 4 == 0) philox(p, (uint32_t)(e / 4), (uint32_t)c, (uint32_t)t, ORC_TAG_MUTSITE, w);
+        const uint32_t J = (uint32_t)(d - k + i);
+        uint32_t r = (uint32_t)(((uint64_t)w[e % 4] * (uint64_t)(J + 1u)) >> 32);
+        for (int32_t l = 0; l < i; ++l)
+            if ((uint32_t)sites[l] == r) { r = J; break; }
+        sites[i] = (int32_t)r;
+    }
+    return k;
+}
+
 void orc_mutation(const orc_params *p, int32_t t, double *Xc, uint8_t *mask)
 {
-    const int32_t N = p->N, P = (p->N + 1) / 2, d = p->d;
+    const int32_t N = p->N, d = p->d;
     const double L = p->L, U = p->U, xi = p->eta_m;
     const uint32_t Tm = event_threshold(p->p_m / (double)d);
+    const double q = (double)Tm / 16777216.0;
+    uint64_t thr[32];
+    const int32_t n_thr = (Tm > 0u && Tm < (1u << 24)) ? site_count_thresholds(q, d, thr) : 0;
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int32_t c = 0; c < N; ++c) {
-        int32_t pr = c < P ? c : c - P;
-        int32_t second = c < P ? 0 : 1;
+        uint8_t *C = (uint8_t *)calloc((size_t)d, 1);
+        if (Tm >= (1u << 24)) {
+            memset(C, 1, (size_t)d);
+        } else if (Tm > 0u) {
+            int32_t sites[32];
+            const int32_t k = mutation_sites(p, t, c, n_thr, thr, sites);
+            for (int32_t i = 0; i < k; ++i) C[sites[i]] = 1;
+        }
         for (int32_t j = 0; j < d; ++j) {
-            uint32_t wh[4], wl[4];
-            philox(p, (uint32_t)(j / 8), (uint32_t)pr, (uint32_t)t, ORC_TAG_MUTHI, wh);
-            philox(p, (uint32_t)j, (uint32_t)c, (uint32_t)t, ORC_TAG_MUTLO, wl);
-            int b = j % 8;
-            uint32_t hi8 = (wh[2 * second + b / 4] >> (8 * (b % 4))) & 0xFFu;
-            uint32_t lo16 = wl[0] >> 16;
-            uint32_t r4 = (hi8 << 16) | lo16;           /* R4 = r4 * 2^-24 */
-            double C = (r4 < Tm) ? 1.0 : 0.0;           /* H(p_m/d - R4)   */
-            double M = u24(wl[1]);
             double x = Xc[(int64_t)c * d + j];
             if (x < L) x = L;
             if (x > U) x = U;
-            double d1 = (x - L) / (U - L), d2 = (U - x) / (U - L);
-            double lo = (M < 0.5) ? 1.0 : 0.0;          /* H(0.5 - M) */
-            double up = (M > 0.5) ? 1.0 : 0.0;          /* H(M - 0.5) */
             double delta = 0.0;
-            if (lo > 0.0)
-                delta = (U - L) * (pow(2.0 * M + (1.0 - 2.0 * M) * pow(1.0 - d1, xi + 1.0),
-                                       1.0 / (xi + 1.0)) - 1.0);
-            else if (up > 0.0)
-                delta = (U - L) * (1.0 - pow(2.0 * (1.0 - M) + 2.0 * (M - 0.5) * pow(1.0 - d2, xi + 1.0),
-                                             1.0 / (xi + 1.0)));
-            x = x + delta * C;
+            if (C[j]) {
+                uint32_t wm[4];
+                philox(p, (uint32_t)j, (uint32_t)c, (uint32_t)t, ORC_TAG_MUTMAG, wm);
+                const double M = u24(wm[1]);
+                const double d1 = (x - L) / (U - L), d2 = (U - x) / (U - L);
+                if (M < 0.5)          /* H(0.5 - M) */
+                    delta = (U - L) * (pow(2.0 * M + (1.0 - 2.0 * M) * pow(1.0 - d1, xi + 1.0),
+                                           1.0 / (xi + 1.0)) - 1.0);
+                else if (M > 0.5)     /* H(M - 0.5) */
+                    delta = (U - L) * (1.0 - pow(2.0 * (1.0 - M) + 2.0 * (M - 0.5) * pow(1.0 - d2, xi + 1.0),
+                                                 1.0 / (xi + 1.0)));
+            }
+            x = x + delta * (double)C[j];
             if (x < L) x = L;
             if (x > U) x = U;
             Xc[(int64_t)c * d + j] = x;
-            if (mask) mask[(int64_t)c * d + j] = (uint8_t)C;
+            if (mask) mask[(int64_t)c * d + j] = C[j];
         }
+        free(C);
     }
 }
 

@@ -17,11 +17,12 @@
  *   MATE   (e/4, 0, t, 2)  word e%4   -> parent draw e, index (w*K)>>32
  *   PAIR   (p,   0, t, 3)  word 0     -> R3 of pair p (u24)
  *   SBX    (j/4, p, t, 4)  word j%4   -> Mc = u24(w), sign coin bit0, keep coin bit1
- *   MUTHI  (j/8, p, t, 5)  byte j%8 of words 0-1 (first child) / 2-3 (second)
- *   MUTLO  (j,   c, t, 6)  word0>>16 = low 16 bits of R4, word1 -> M_mut (u24)
+ *   MUTSITE(i/4, c, t, 5)  word i%4 -> draw i of child c's mutation sites:
+ *                          draw 0 the site count, draws 1..k Floyd's subset
+ *   MUTMAG (j,   c, t, 6)  word1 -> M_mut (u24) of site j of child c
  *   INIT   (j,   i, 0, 1)  words 0,1 -> Box-Muller N(0,1) (neuroevolution weights)
  *   NOISE  (k,   s, t, 7)  words 0,1 -> Box-Muller N(0,1), state component k, step s
- * where u24(w) = (w >> 8) * 2^-24 and R4[c,j] = ((hi8 << 16) | lo16) * 2^-24.
+ * where u24(w) = (w >> 8) * 2^-24.
  */
 #ifndef RVEA_ORACLE_H
 #define RVEA_ORACLE_H
@@ -34,7 +35,7 @@ extern "C" {
 
 enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2 };
 enum { ORC_TAG_INIT = 1, ORC_TAG_MATE = 2, ORC_TAG_PAIR = 3, ORC_TAG_SBX = 4,
-       ORC_TAG_MUTHI = 5, ORC_TAG_MUTLO = 6, ORC_TAG_NOISE = 7 };
+       ORC_TAG_MUTSITE = 5, ORC_TAG_MUTMAG = 6, ORC_TAG_NOISE = 7 };
 
 typedef struct {
     int32_t m, d, N, H;

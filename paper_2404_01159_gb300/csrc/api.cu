@@ -248,6 +248,34 @@ uint32_t event_threshold24(double q) {
   return (uint32_t)x;
 }
 
+// Site-count thresholds of polynomial mutation.  The sites of a child row are
+// independent events of probability q (Appendix B: one uniform per site
+// against p_m/d); the kernel draws them as a count k ~ Binomial(d, q) and a
+// uniform k-subset, the same law.  Draw 0 of the row gives the count
+// k = #{i : w >= thr_i}, thr_i = floor(2^32 CDF(i)) for the i < min(d, 32)
+// with CDF(i) < 1.  CDF is summed in FP64 from pmf(0) = (1-q)^d (square and
+// multiply over the bits of d, least significant first) and
+// pmf(i+1) = pmf(i) * (d-i) / (i+1) * (q/(1-q)); this file is compiled
+// without floating-point contraction, so the sums are the plain IEEE ones.
+int site_count_thresholds(double q, int d, uint32_t *thr) {
+  const int K = std::min(d, kMaxSites);
+  const double ratio = q / (1.0 - q);
+  double b = 1.0 - q, pmf = 1.0;
+  for (int e = d; e > 0; e >>= 1) {
+    if (e & 1) pmf *= b;
+    b *= b;
+  }
+  double cdf = 0.0;
+  int n = 0;
+  for (int i = 0; i < K; ++i) {
+    if (i > 0) pmf = pmf * (double)(d - (i - 1)) / (double)i * ratio;
+    cdf += pmf;
+    if (cdf >= 1.0) break;
+    thr[n++] = (uint32_t)std::floor(cdf * 4294967296.0);
+  }
+  return n;
+}
+
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
@@ -466,6 +494,8 @@ rvea_status validate(const rvea_config *c) {
   if (c->t_max < 1 || !(c->eta_c > 0) || !(c->eta_m > 0) || !(c->f_r > 0) || c->f_r > 1 ||
       !(c->alpha > 0) || !(c->p_c >= 0) || c->p_c > 1 || !(c->p_m >= 0) || !(c->upper > c->lower))
     return RVEA_ERR_ARG;
+  // mutation: up to 8 expected sites per row (the count is capped at 32), or every site
+  if (c->p_m > 8.0 && c->p_m < (double)c->d) return RVEA_ERR_ARG;
   if (c->problem < 0 || c->problem > 2) return RVEA_ERR_ARG;
   if (c->problem == RVEA_NEURO_LINEAR) return RVEA_ERR_ARG;   // rollout kernel not built here
   if (c->H < 0 || lattice_size(c->m, c->H) != (int64_t)c->N) return RVEA_ERR_LATTICE;
@@ -543,6 +573,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.eta_m = (float)cfg->eta_m;
   D.T_c = event_threshold24(cfg->p_c);
   D.T_m = event_threshold24(cfg->p_m / (double)cfg->d);
+  if (D.T_m > 0u && D.T_m < (1u << 24))
+    D.n_mthr = site_count_thresholds((double)D.T_m / 16777216.0, sh.d, D.mthr);
   D.key0 = (uint32_t)cfg->seed;
   D.key1 = (uint32_t)(cfg->seed >> 32);
   D.X = wsp<float>(r, lay.X);

@@ -22,19 +22,20 @@
 //   PAIR  (p, 0, t)      word 0    : pair gate R3 (crossover iff u24 < p_c)
 //   MATE  (e/4, 0, t)    word e%4  : parent draw e -> list[(w*K) >> 32]
 //   SBX   (j/4, p, t)    word j%4  : Mc = u24, sign coin bit 0, keep coin bit 1
-//   MUTHI (j/8, p, t)    byte j%8 of words 0-1 / 2-3: high 8 bits of R4
-//   MUTLO (j, c, t)      word 0>>16: low 16 bits of R4; word 1: M_mut = u24
-// The site test R4 < p_m/d, i.e. (hi8<<16 | lo16) < T_m, is decided from hi8
-// alone unless hi8 == T_m>>16; only those rare candidates (1 in 256 sites
-// for d >= 256) need the MUTLO word, so they are queued in shared memory and
-// resolved together before the main pass instead of diverging inside it.
+//   MUTSITE (i/4, c, t)  word i%4  : draw i of the mutation sites of child c
+//   MUTMAG  (j, c, t)    word 1    : M_mut = u24 of site j of child c
+// Mutation sites: Appendix B fires each site independently with probability
+// q = p_m/d (on the 24-bit grid).  The same law is drawn per child row as a
+// count k ~ Binomial(d, q) (draw 0 against the host's 32-bit CDF thresholds)
+// and a uniform k-subset (Floyd's sampler, draws 1..k, r = (w (J+1)) >> 32),
+// so a row costs one or two Philox calls instead of one draw per site.  One
+// lane per child builds the list and marks the sites of its team's segment
+// in a shared-memory bitmap before the main pass.
 #include "rvea_device.cuh"
 
 namespace rvea {
 
-constexpr int kWarpQ = 64;        // candidate queue entries per warp
 constexpr int kBmWords = kLaneGroups * 16;    // per warp: 32 lanes x kLaneGroups x 16 bits
-constexpr int kWarpWords = kBmWords + kWarpQ + 4;   // bitmap + queue + count
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
   return fminf(fmaxf(x, lo), hi);
@@ -148,30 +149,32 @@ __device__ __forceinline__ float2 team_sum2(float2 v, int TS) {
   return v;
 }
 
-// Sites of one child in one group from the 8 high bytes of R4 (lo = bytes
-// 0-3, hi = bytes 4-7): `sure` = bytes below thr (the site fires whatever
-// the low 16 bits are), `cand` = bytes equal to thr (the low bits decide).
-__device__ __forceinline__ void site_bytes(uint32_t lo, uint32_t hi, uint32_t thr,
-                                           uint32_t &sure, uint32_t &cand) {
-  sure = 0u;
-  cand = 0u;
-  if (thr >= 256u) {
-    sure = 0xFFu;
-    return;
+// Mutation sites of child row c (count, then Floyd's uniform subset), marked
+// in the team's bitmap where they fall in groups [g0, g0 + SG) (16-bit entry
+// gl: bits 0-7 child 1, bits 8-15 child 2).
+template <class KP>
+__device__ __noinline__ void mark_sites(const RunDesc &R, const KP &kp, int c, int s2, int t,
+                                        int g0, int SG, uint32_t *bmw, int ebase) {
+  const int d = R.d;
+  uint4 w = philox_k(0u, (uint32_t)c, (uint32_t)t, TAG_MUTSITE, kp);
+  const int nthr = R.n_mthr;
+  int k = 0;
+  while (k < nthr && w.x >= R.mthr[k]) ++k;
+  int sites[kMaxSites];
+  for (int i = 0; i < k; ++i) {
+    const int e = i + 1;
+    if ((e & 3) == 0) w = philox_k((uint32_t)(e >> 2), (uint32_t)c, (uint32_t)t, TAG_MUTSITE, kp);
+    const uint32_t J = (uint32_t)(d - k + i);
+    uint32_t r = __umulhi(word(w, e & 3), J + 1u);
+    for (int l = 0; l < i; ++l)
+      if ((uint32_t)sites[l] == r) { r = J; break; }
+    sites[i] = (int)r;
+    const int gl = (int)(r >> 3) - g0;
+    if (gl >= 0 && gl < SG) {
+      const int hw = ebase + gl;
+      atomicOr(&bmw[hw >> 1], 1u << (((hw & 1) << 4) + (s2 << 3) + (r & 7)));
+    }
   }
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const uint32_t by = ((b < 4 ? lo : hi) >> (8 * (b & 3))) & 0xFFu;
-    if (by < thr) sure |= 1u << b;
-    else if (by == thr) cand |= 1u << b;
-  }
-}
-
-// True if any of the four words holds a zero byte (the classic test).
-__device__ __forceinline__ bool any_zero_byte(uint4 w) {
-  const uint32_t a = (w.x - 0x01010101u) & ~w.x, b = (w.y - 0x01010101u) & ~w.y;
-  const uint32_t c = (w.z - 0x01010101u) & ~w.z, e = (w.w - 0x01010101u) & ~w.w;
-  return ((a | b | c | e) & 0x80808080u) != 0u;
 }
 
 // 2^x with one MUFU.EX2 (PTX ex2.approx, relative error ~2^-22).
@@ -235,7 +238,7 @@ __device__ __noinline__ void finish_pair(const RunDesc &R, int p, int S, int ch1
 
 template <int PROB, class KP>
 __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
-  __shared__ uint32_t s_w[kReproThreads / 32][kWarpWords];
+  __shared__ uint32_t s_w[kReproThreads / 32][kBmWords];
 
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
@@ -251,12 +254,9 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   const int *cslot = R.child_slot + (t & 1) * N;
   uint32_t *bmw = s_w[warp];
   uint16_t *bm = reinterpret_cast<uint16_t *>(bmw) + tw * SG;   // [SG] of this team: c1 | c2 << 8
-  uint32_t *q = s_w[warp] + kBmWords;
-  uint32_t *qn = s_w[warp] + kBmWords + kWarpQ;
 
 #pragma unroll
   for (int w = 0; w < kBmWords; w += 32) bmw[w + wl] = 0u;
-  if (wl == 0) *qn = 0u;
 
   // ---- phase 0: the pair's two mating draws and crossover gate ------------
   uint32_t v0 = 0, v1 = 0, v2 = 0;
@@ -288,7 +288,6 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   }
   const bool has2 = ch2 >= 0;
   const int g0 = seg * SG;
-  const uint32_t thr_hi = R.T_m >> 16, thr_lo = R.T_m & 0xFFFFu;
   // run constants used inside the loops, in registers: the child-row stores
   // could alias the descriptor, which would force a reload after each store
   float4 *const X4 = reinterpret_cast<float4 *>(R.X);
@@ -299,53 +298,19 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   float *const hb = R.hbuf + (size_t)p * 2 * kMaxM;
   __syncwarp();
 
-  // ---- phase A: mutation sites from the high byte of R4 -------------------
+  // ---- phase A: mutation sites of this segment ----------------------------
   if (active && T_m > 0) {
+    if (T_m >= (1u << 24)) {   // every site
 #pragma unroll 1
-    for (int k = 0; k < kLaneGroups; ++k) {
-      const int gl = lane + k * TS, g = g0 + gl;
-      if (g >= G) break;
-      const uint4 w = philox_k((uint32_t)g, (uint32_t)p, (uint32_t)t, TAG_MUTHI, kp);
-      if (thr_hi == 0u && !any_zero_byte(w)) continue;   // 97% of groups for d >= 256
-      const uint32_t vmask = 8 * g + 8 <= d ? 0xFFu : (1u << (d - 8 * g)) - 1u;
-      uint32_t sure1, cand1, sure2, cand2;
-      site_bytes(w.x, w.y, thr_hi, sure1, cand1);
-      site_bytes(w.z, w.w, thr_hi, sure2, cand2);
-      if (!has2) { sure2 = 0u; cand2 = 0u; }
-      bm[gl] = (uint16_t)((sure1 & vmask) | ((sure2 & vmask) << 8));
-      uint32_t cand = (cand1 & vmask) | ((cand2 & vmask) << 8);
-      while (cand) {
-        const int bit = __ffs(cand) - 1;
-        cand &= cand - 1u;
-        const int s2 = bit >> 3, b = bit & 7;
-        const int j = 8 * g + b;
-        const uint32_t qi = atomicAdd(qn, 1u);
-        if (qi < (uint32_t)kWarpQ) {
-          q[qi] = ((uint32_t)tw << 24) | ((uint32_t)s2 << 23) | (uint32_t)j;
-        } else {   // queue full: resolve here
-          const int c = s2 ? p + P : p;
-          const uint4 wl2 = philox_k((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTLO, kp);
-          if ((wl2.x >> 16) < thr_lo) bm[gl] |= (uint16_t)(1u << bit);
-        }
+      for (int k = 0; k < kLaneGroups; ++k) {
+        const int gl = lane + k * TS, g = g0 + gl;
+        if (g >= G) break;
+        const uint32_t vmask = 8 * g + 8 <= d ? 0xFFu : (1u << (d - 8 * g)) - 1u;
+        bm[gl] = (uint16_t)(vmask | (has2 ? vmask << 8 : 0u));
       }
-    }
-  }
-  __syncwarp();
-  // ---- phase A2: resolve the queued candidates with the low 16 bits -------
-  {
-    const uint32_t nq = min(*qn, (uint32_t)kWarpQ);
-    for (uint32_t e = wl; e < nq; e += 32) {
-      const uint32_t en = q[e];
-      const int tq = (int)(en >> 24), s2 = (int)((en >> 23) & 1u), j = (int)(en & 0x7FFFFFu);
-      const int uq = it.pair0 + warp * tpw + tq;
-      const int pq = uq / S;
-      const int c = s2 ? pq + P : pq;
-      const uint4 wl2 = philox_k((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTLO, kp);
-      if ((wl2.x >> 16) < thr_lo) {
-        const int gl = (j >> 3) - (uq - pq * S) * SG;
-        const int hw = tq * SG + gl;   // 16-bit entry of the warp's bitmap
-        atomicOr(&bmw[hw >> 1], 1u << (((hw & 1) << 4) + (s2 << 3) + (j & 7)));
-      }
+    } else {
+      for (int c = lane; c < 2; c += TS)
+        if (c == 0 || has2) mark_sites(R, kp, c ? p + P : p, c, t, g0, SG, bmw, tw * SG);
     }
   }
   __syncwarp();
@@ -379,11 +344,11 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
           for (int v = 0; v < 4; ++v) {
             const int j = 8 * g + 4 * h + v;
             if (h1 & (1u << v)) {
-              const uint4 w = philox_k((uint32_t)j, (uint32_t)p, (uint32_t)t, TAG_MUTLO, kp);
+              const uint4 w = philox_k((uint32_t)j, (uint32_t)p, (uint32_t)t, TAG_MUTMAG, kp);
               c1[v] = poly_mutate(c1[v], u24f(w.y), L, U, eta_m);
             }
             if (h2 & (1u << v)) {
-              const uint4 w = philox_k((uint32_t)j, (uint32_t)(p + P), (uint32_t)t, TAG_MUTLO, kp);
+              const uint4 w = philox_k((uint32_t)j, (uint32_t)(p + P), (uint32_t)t, TAG_MUTMAG, kp);
               c2[v] = poly_mutate(c2[v], u24f(w.y), L, U, eta_m);
             }
           }

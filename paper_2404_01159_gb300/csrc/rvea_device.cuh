@@ -20,11 +20,12 @@ constexpr int kSelThreads = 128;   // selection CTA size (two solutions per thre
 constexpr int kSelBlock = 2 * kSelThreads;   // solutions per selection work item
 constexpr int kVTile = 512;        // reference vectors per shared-memory tile
 constexpr int kFinThreads = 1024;  // CTA size of the per-run finalize kernel
+constexpr int kMaxSites = 32;      // cap of the mutation-site count of one row
 
 // Philox counter tags (word 3 of the counter).
 enum : uint32_t {
   TAG_INIT = 1, TAG_MATE = 2, TAG_PAIR = 3, TAG_SBX = 4,
-  TAG_MUTHI = 5, TAG_MUTLO = 6, TAG_NOISE = 7
+  TAG_MUTSITE = 5, TAG_MUTMAG = 6, TAG_NOISE = 7
 };
 
 enum : int { PROB_DTLZ2 = 0, PROB_DTLZ1 = 1, PROB_NEURO = 2 };
@@ -59,6 +60,8 @@ struct RunDesc {
   // parameters
   float L, U, alpha, inv_eta_c1, eta_m;
   uint32_t T_c, T_m;   // 24-bit event thresholds (fires iff k < T)
+  int n_mthr;          // site-count thresholds in use (<= kMaxSites)
+  uint32_t mthr[kMaxSites];   // site count of a row = #{i < n_mthr : w >= mthr[i]}
   uint32_t key0, key1; // Philox key = seed
   // state (pointers into the workspace)
   float *X;            // [2N][d_pad] population pool (physical slots)

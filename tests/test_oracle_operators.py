@@ -104,6 +104,53 @@ def test_mutation_site_frequency(orc):
     assert abs(q - 1 / 50) < 1e-7
 
 
+def _q24(p_m, d):
+    """Per-site mutation probability p_m/d on the 24-bit grid."""
+    return math.ceil((1 << 24) * p_m / d) / (1 << 24)
+
+
+def test_mutation_subset_law(orc):
+    """Appendix B draws one uniform per site, so the sites of a row are
+    independent Bernoulli(q) events.  The oracle draws the count and then a
+    uniform subset; on d = 4 every one of the 16 masks must appear with
+    probability q^|S| (1-q)^(4-|S|)."""
+    p = _params(orc, d=4, N=20000, p_m=1.6)
+    _, mask = orc.mutation(p, 6, np.full((p.N, p.d), 0.5))
+    q = _q24(1.6, 4)
+    code = mask.astype(np.int64) @ (1 << np.arange(4))
+    obs = np.bincount(code, minlength=16)
+    size = np.array([bin(s).count("1") for s in range(16)])
+    exp = p.N * q ** size * (1 - q) ** (4 - size)
+    res = stats.chisquare(obs, exp)
+    assert res.pvalue > 1e-3, (obs, exp)
+
+
+def test_mutation_count_law(orc):
+    """Row site counts follow Binomial(d, q)."""
+    d, p_m = 300, 1.0
+    p = _params(orc, d=d, N=20000, p_m=p_m)
+    _, mask = orc.mutation(p, 8, np.full((p.N, p.d), 0.5))
+    q = _q24(p_m, d)
+    k = mask.sum(axis=1)
+    obs = np.array([(k == i).sum() for i in range(5)] + [(k >= 5).sum()])
+    pmf = stats.binom.pmf(np.arange(5), d, q)
+    exp = p.N * np.append(pmf, 1 - pmf.sum())
+    res = stats.chisquare(obs, exp)
+    assert res.pvalue > 1e-3, (obs, exp)
+
+
+def test_mutation_positions_uniform(orc):
+    """Every position is equally likely to be a site (the subset step's draw
+    ranges); a skew towards the last positions would show here."""
+    d = 40
+    p = _params(orc, d=d, N=20000, p_m=3.0)
+    _, mask = orc.mutation(p, 2, np.full((p.N, p.d), 0.5))
+    obs = mask.sum(axis=0)
+    res = stats.chisquare(obs)
+    assert res.pvalue > 1e-3, obs
+    assert abs(obs.sum() / mask.size - _q24(3.0, d)) < 5 * math.sqrt(_q24(3.0, d) / mask.size)
+
+
 def _pm_cdf(q, x, eta):
     """CDF of the mutation step (x' - x)/(U-L) of Deb's polynomial mutation
     at an interior x with U-L = 1, derived from the Appendix B formula with
