@@ -206,6 +206,54 @@ __device__ __forceinline__ void sbx_pair(float2 x1, float2 x2, float2 B, float L
   c2 = make_float2(clampf(c2.x, L, U), clampf(c2.y, L, U));
 }
 
+// Four adjacent variables of both children: (a0, a1) child 1, (b0, b1) child 2.
+struct Quad { float2 a0, a1, b0, b1; };
+
+// Polynomial mutation of the marked variables of a quad (bits of h1 / h2 for
+// children c1 / c2; first variable j0).  Rare (about one site per row), so
+// kept out of the main loop's instruction stream.
+template <class KP>
+__device__ __noinline__ Quad mutate_quad(Quad q, uint32_t h1, uint32_t h2, int j0, int c1, int c2,
+                                         int t, float L, float U, float eta_m, const KP &kp) {
+  float x[8] = {q.a0.x, q.a0.y, q.a1.x, q.a1.y, q.b0.x, q.b0.y, q.b1.x, q.b1.y};
+  const uint32_t bits = h1 | (h2 << 4);
+#pragma unroll 1
+  for (int b = 0; b < 8; ++b) {
+    if (!(bits & (1u << b))) continue;
+    const int v = b & 3, c = b < 4 ? c1 : c2;
+    const uint4 w = philox_k((uint32_t)(j0 + v), (uint32_t)c, (uint32_t)t, TAG_MUTMAG, kp);
+    x[b] = poly_mutate(x[b], u24f(w.y), L, U, eta_m);
+  }
+  return Quad{make_float2(x[0], x[1]), make_float2(x[2], x[3]), make_float2(x[4], x[5]),
+              make_float2(x[6], x[7])};
+}
+
+// Evaluation terms of a quad that holds x_1..x_{m-1} (kept in hb for the
+// objectives) or the ragged end of the row; returns the accumulators
+// (child 1 in a0, child 2 in a1), given in acc.a0 / acc.a1.
+template <int PROB>
+__device__ __noinline__ Quad eval_edge(Quad q, Quad acc, int j0, int mh, int d, float *hb) {
+  const float c1[4] = {q.a0.x, q.a0.y, q.a1.x, q.a1.y}, c2[4] = {q.b0.x, q.b0.y, q.b1.x, q.b1.y};
+  float2 acc1 = acc.a0, acc2 = acc.a1;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = j0 + v;
+    if (j < mh) {
+      hb[j] = c1[v];
+      hb[kMaxM + j] = c2[v];
+    } else if (j < d) {
+      if (v & 1) {
+        acc1.y = g_term1(PROB, c1[v], acc1.y);
+        acc2.y = g_term1(PROB, c2[v], acc2.y);
+      } else {
+        acc1.x = g_term1(PROB, c1[v], acc1.x);
+        acc2.x = g_term1(PROB, c2[v], acc2.x);
+      }
+    }
+  }
+  return Quad{acc1, acc2, acc1, acc2};
+}
+
 // Last segment of pair p to arrive: g of both children from the segments'
 // partial sums in segment order, then the objectives and the ideal point.
 __device__ __noinline__ void finish_pair(const RunDesc &R, int p, int S, int ch1, int ch2) {
@@ -339,21 +387,9 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
                  make_float2(sbx_B(r.z, nocross, ie), sbx_B(r.w, nocross, ie)), L, U, a1, b1);
         const uint32_t h1 = (mb >> (4 * h)) & 0xFu, h2 = has2 ? (mb >> (8 + 4 * h)) & 0xFu : 0u;
         if (h1 | h2) {
-          float c1[4] = {a0.x, a0.y, a1.x, a1.y}, c2[4] = {b0.x, b0.y, b1.x, b1.y};
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int j = 8 * g + 4 * h + v;
-            if (h1 & (1u << v)) {
-              const uint4 w = philox_k((uint32_t)j, (uint32_t)p, (uint32_t)t, TAG_MUTMAG, kp);
-              c1[v] = poly_mutate(c1[v], u24f(w.y), L, U, eta_m);
-            }
-            if (h2 & (1u << v)) {
-              const uint4 w = philox_k((uint32_t)j, (uint32_t)(p + P), (uint32_t)t, TAG_MUTMAG, kp);
-              c2[v] = poly_mutate(c2[v], u24f(w.y), L, U, eta_m);
-            }
-          }
-          a0 = make_float2(c1[0], c1[1]); a1 = make_float2(c1[2], c1[3]);
-          b0 = make_float2(c2[0], c2[1]); b1 = make_float2(c2[2], c2[3]);
+          const Quad o = mutate_quad(Quad{a0, a1, b0, b1}, h1, h2, 8 * g + 4 * h, p, p + P, t, L, U,
+                                     eta_m, kp);
+          a0 = o.a0; a1 = o.a1; b0 = o.b0; b1 = o.b1;
         }
         if (eval) {
           if (plain) {
@@ -362,23 +398,10 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
             acc2 = g_terms2(PROB, b0, acc2);
             acc2 = g_terms2(PROB, b1, acc2);
           } else {   // a group holding x_1..x_{m-1} or the ragged end of the row
-            const float c1[4] = {a0.x, a0.y, a1.x, a1.y}, c2[4] = {b0.x, b0.y, b1.x, b1.y};
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const int j = 8 * g + 4 * h + v;
-              if (j < mh) {
-                hb[j] = c1[v];
-                hb[kMaxM + j] = c2[v];
-              } else if (j < d) {
-                if (v & 1) {
-                  acc1.y = g_term1(PROB, c1[v], acc1.y);
-                  acc2.y = g_term1(PROB, c2[v], acc2.y);
-                } else {
-                  acc1.x = g_term1(PROB, c1[v], acc1.x);
-                  acc2.x = g_term1(PROB, c2[v], acc2.x);
-                }
-              }
-            }
+            const Quad o = eval_edge<PROB>(Quad{a0, a1, b0, b1}, Quad{acc1, acc2, acc1, acc2},
+                                           8 * g + 4 * h, mh, d, hb);
+            acc1 = o.a0;
+            acc2 = o.a1;
           }
         }
         Y4[q1 + 2 * g + h] = make_float4(a0.x, a0.y, a1.x, a1.y);
