@@ -27,6 +27,9 @@ __global__ void k_repro(const __grid_constant__ BatchDir dir);
 __global__ void k_repro1_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1s_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1s_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1s_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_init(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
@@ -63,7 +66,7 @@ int pow2ceil(int x) {
 }
 
 struct Shape {
-  int m, m4, d, d_pad, G, N, P, n_comb, team, ppc, nseg;
+  int m, m4, d, d_pad, G, N, P, n_comb, team, ppc, nseg, sg;
   int n_repro, n_init, n_sel, nblk, nch, chunk;
   int tmax;     // tiles of the pruned selection (0: not used)
 };
@@ -79,8 +82,8 @@ size_t prune_smem(int N, int T) {
 }
 
 // Reproduction teams: TS lanes (a power of two <= 32) per work unit of
-// kLaneGroups*TS groups of 8 variables; a pair has nseg = ceil(G / (kLaneGroups TS))
-// units.
+// up to kLaneGroups*TS groups of 8 variables; a pair has nseg = ceil(G / (kLaneGroups TS))
+// units of sg = ceil(G / nseg) groups each.
 // Both depend on d only, so the reduction tree of g does too.
 Shape make_shape(int m, int d, int N) {
   Shape s;
@@ -95,6 +98,7 @@ Shape make_shape(int m, int d, int N) {
   s.team = std::min(32, std::max(1, pow2ceil((s.G + kLaneGroups - 1) / kLaneGroups)));
   s.ppc = kReproThreads / s.team;                 // work units per CTA
   s.nseg = (s.G + kLaneGroups * s.team - 1) / (kLaneGroups * s.team);
+  s.sg = (s.G + s.nseg - 1) / s.nseg;   // balanced segments: no mostly idle last one
   s.n_repro = (s.P * s.nseg + s.ppc - 1) / s.ppc;
   s.n_init = (N + s.ppc - 1) / s.ppc;
   const SelPlan sp = sel_plan(s.n_comb, N, s.m4, kSMs);
@@ -109,8 +113,8 @@ Shape make_shape(int m, int d, int N) {
 }
 
 struct Layout {
-  size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V64, V0, g64, g32,
-      ctl, desc, repro, init, sel, stage, psum, hbuf, pcnt, Vt, tperm, trng, tcen, tcs, noise,
+  size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
+      ctl, desc, repro, init, sel, stage, psum, pcnt, Vt, tperm, trng, tcen, tcs, noise,
       dynA, dynB, total;
 };
 
@@ -136,6 +140,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.surv = take((size_t)s.N * 4);
   L.blk = take((size_t)s.nblk * 4);   // selection blocks of kSelBlock solutions
   L.V32 = take((size_t)s.N * s.m4 * 16);
+  L.V32lo = take((size_t)s.N * s.m * 4);
   L.V64 = take((size_t)s.N * s.m * 8);
   L.V0 = take((size_t)s.N * s.m * 8);
   L.g64 = take((size_t)s.N * 8);
@@ -147,7 +152,6 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.sel = take((size_t)s.n_sel * sizeof(SelItem));
   L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
-  L.hbuf = take((size_t)s.P * 2 * kMaxM * 4);
   L.pcnt = take((size_t)s.P * 4);
   const size_t T = (size_t)s.tmax;
   L.Vt = take(s.tmax ? (size_t)s.N * 16 : 0);
@@ -309,6 +313,9 @@ void set_kernel_attrs() {
   set((const void *)k_repro1_dtlz1);
   set((const void *)k_repro1_dtlz2);
   set((const void *)k_repro1_neuro);
+  set((const void *)k_repro1s_dtlz1);
+  set((const void *)k_repro1s_dtlz2);
+  set((const void *)k_repro1s_neuro);
   set((const void *)k_init);
   set((const void *)k_select);
   set((const void *)k_select_pruned);
@@ -372,9 +379,18 @@ T *wsp(const rvea_run *r, size_t off) {
 }
 
 // Reproduction of one run: the kernel instance for its problem, round keys
-// in the parameter block.
+// in the parameter block; 32-lane teams stage the parents in shared memory.
 void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t st) {
   const RoundKeys rk = round_keys(r->hd.key0, r->hd.key1);
+  const int sm = r->repro_smem;
+  if (sm > 0) {
+    switch (r->hd.problem) {
+      case PROB_DTLZ1: k_repro1s_dtlz1<<<grid, kReproThreads, sm, st>>>(dr, rk); break;
+      case PROB_DTLZ2: k_repro1s_dtlz2<<<grid, kReproThreads, sm, st>>>(dr, rk); break;
+      default: k_repro1s_neuro<<<grid, kReproThreads, sm, st>>>(dr, rk); break;
+    }
+    return;
+  }
   switch (r->hd.problem) {
     case PROB_DTLZ1: k_repro1_dtlz1<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
     case PROB_DTLZ2: k_repro1_dtlz2<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
@@ -566,7 +582,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   std::memset(&D, 0, sizeof(D));
   D.m = sh.m; D.m4 = sh.m4; D.d = sh.d; D.d_pad = sh.d_pad; D.G = sh.G;
   D.N = sh.N; D.P = sh.P; D.n_comb = sh.n_comb; D.problem = cfg->problem;
-  D.t_max = cfg->t_max; D.p_adapt = r->p_adapt; D.team = sh.team; D.nseg = sh.nseg;
+  D.t_max = cfg->t_max; D.p_adapt = r->p_adapt; D.team = sh.team; D.nseg = sh.nseg; D.sg = sh.sg;
   D.op_mode = 0;
   D.L = (float)cfg->lower; D.U = (float)cfg->upper; D.alpha = (float)cfg->alpha;
   D.inv_eta_c1 = (float)(1.0 / (cfg->eta_c + 1.0));
@@ -591,17 +607,17 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.surv = wsp<int>(r, lay.surv);
   D.blk_cnt = wsp<int>(r, lay.blk);
   D.V32 = wsp<float>(r, lay.V32);
+  D.V32lo = wsp<float>(r, lay.V32lo);
   D.V64 = wsp<double>(r, lay.V64);
   D.V0 = wsp<double>(r, lay.V0);
   D.gamma64 = wsp<double>(r, lay.g64);
   D.gamma32 = wsp<float>(r, lay.g32);
   D.ctl = wsp<Ctl>(r, lay.ctl);
   D.psum = wsp<float>(r, lay.psum);
-  D.hbuf = wsp<float>(r, lay.hbuf);
   D.pcnt = wsp<int>(r, lay.pcnt);
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
-  r->repro_smem = 0;
+  r->repro_smem = sh.team == 32 ? kStagedSmem : 0;   // staged path: one 32-lane team per warp
   r->init_smem = sh.ppc * std::max(1, sh.m - 1) * 4;
   r->sel_smem = std::min(sh.N, sh.chunk) * sh.m4 * 16;
   r->fin_smem = 0;
@@ -639,9 +655,13 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     r->prune_smem_bytes = (int)prune_smem(sh.N, D.ntiles);
   }
   cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
-  std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f);
+  std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f), V32lo((size_t)sh.N * sh.m);
   for (int j = 0; j < sh.N; ++j)
-    for (int k = 0; k < sh.m; ++k) V32[(size_t)j * sh.m4 * 4 + k] = (float)V0[(size_t)j * sh.m + k];
+    for (int k = 0; k < sh.m; ++k) {
+      const double v = V0[(size_t)j * sh.m + k];
+      V32[(size_t)j * sh.m4 * 4 + k] = (float)v;
+      V32lo[(size_t)j * sh.m + k] = (float)(v - (double)(float)v);
+    }
   Ctl c0;
   std::memset(&c0, 0, sizeof(c0));
   c0.t = 1;
@@ -660,6 +680,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.V0, V0.data(), V0.size() * 8);
   up(lay.V64, V0.data(), V0.size() * 8);
   up(lay.V32, V32.data(), V32.size() * 4);
+  up(lay.V32lo, V32lo.data(), V32lo.size() * 4);
   up(lay.ctl, &c0, sizeof(c0));
   if (D.ntiles > 0) {
     up(lay.tperm, tperm.data(), tperm.size() * 4);

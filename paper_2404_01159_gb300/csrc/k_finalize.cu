@@ -199,6 +199,7 @@ k_finalize(const __grid_constant__ BatchDir dir) {
         const double v = w[k] / nrm;
         R.V64[(size_t)jj * m + k] = v;
         v32[k] = (float)v;
+        R.V32lo[(size_t)jj * m + k] = (float)(v - (double)(float)v);
       }
     }
   }
@@ -423,6 +424,10 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
     }
     float *v32 = R.V32 + (size_t)j * R.m4 * 4;
     for (int k = 0; k < R.m4 * 4; ++k) v32[k] = k < m ? (float)R.V64[(size_t)j * m + k] : 0.0f;
+    for (int k = 0; k < m; ++k) {
+      const double v = R.V64[(size_t)j * m + k];
+      R.V32lo[(size_t)j * m + k] = (float)(v - (double)(float)v);
+    }
     R.gamma32[j] = (float)R.gamma64[j];
     R.best[j] = ~0ull;
     R.surv[j] = -1;

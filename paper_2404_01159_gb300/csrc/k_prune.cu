@@ -176,9 +176,8 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
       } else if (bj < 0 || bj >= N) {
         set_status(R.ctl, ST_BADINDEX);
       } else {
-        float theta = 1.5707963267948966f;
-        if (nf > 0.0f) theta = acosf(fminf(1.0f, fmaxf(-1.0f, best / nf)));
-        const float apd = (1.0f + pen * theta / R.gamma32[bj]) * nf;
+        const float apd = apd_chord(f, M, R.V32 + (size_t)bj * R.m4 * 4, R.V32lo + (size_t)bj * M,
+                                    R.gamma32[bj], pen);
         R.assoc[i] = bj;
         atomicMin(&R.best[bj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
       }

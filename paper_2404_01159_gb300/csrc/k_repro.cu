@@ -5,14 +5,23 @@
 //   mutation (C, Delta, X_mut) -> clip -> DTLZ evaluation -> ideal point z*.
 //
 // Work decomposition.  A team of TS lanes (TS a power of two <= 32, fixed by d
-// alone) owns one work unit: one segment of kLaneGroups*TS consecutive
-// 8-variable groups of one pair; lane l handles groups l, l+TS, l+2TS, ...
-// of the segment.  Each group is two 16-byte loads per parent and two 16-byte stores
-// per child, so a warp moves contiguous 512-byte spans.  Teams never wait on
-// other warps: the phases below synchronise with __syncwarp only.  A pair
-// with several segments (d > 2048) combines the segments' partial sums of g
-// in the last segment to finish (an arrival counter per pair, no spinning),
-// always in segment order, so the reduction tree depends on d alone.
+// alone) owns one work unit: one segment of sg consecutive 8-variable groups
+// of one pair (the pair's G groups split into nseg near-equal segments of at
+// most kLaneGroups*TS groups).  Teams never wait on other warps: the phases
+// below synchronise with __syncwarp only.  A pair with several segments
+// combines the segments' partial sums of g in the last segment to finish (an
+// arrival counter per pair, no spinning), always in segment order, so the
+// reduction tree depends on d alone.
+//
+// The main pass does SBX, clip and the g-terms of both children, four
+// variables (one float4) at a time, and stores the crossed children.  Only
+// the float4s holding x_1..x_{m-1} (kept out of g) or the end of the row take
+// an out-of-line edge path.  Mutation is sparse (about one site per row), so
+// it is a second pass over the segment's sites: reload the crossed value,
+// mutate, store, and correct the lane's g sum by term(new) - term(old).
+// Parents are read either straight from global memory (teams of fewer than
+// 32 lanes) or, for 32-lane teams, from a ring of shared-memory chunks filled
+// by TMA bulk copies, so that each warp keeps its next chunk in flight.
 //
 // Arithmetic on adjacent variables runs in packed .f32x2 instructions (the
 // children of SBX and the evaluation): same IEEE operations, half the issue
@@ -28,14 +37,10 @@
 // q = p_m/d (on the 24-bit grid).  The same law is drawn per child row as a
 // count k ~ Binomial(d, q) (draw 0 against the host's 32-bit CDF thresholds)
 // and a uniform k-subset (Floyd's sampler, draws 1..k, r = (w (J+1)) >> 32),
-// so a row costs one or two Philox calls instead of one draw per site.  One
-// lane per child builds the list and marks the sites of its team's segment
-// in a shared-memory bitmap before the main pass.
+// so a row costs one or two Philox calls instead of one draw per site.
 #include "rvea_device.cuh"
 
 namespace rvea {
-
-constexpr int kBmWords = kLaneGroups * 16;    // per warp: 32 lanes x kLaneGroups x 16 bits
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) {
   return fminf(fmaxf(x, lo), hi);
@@ -149,13 +154,121 @@ __device__ __forceinline__ float2 team_sum2(float2 v, int TS) {
   return v;
 }
 
-// Mutation sites of child row c (count, then Floyd's uniform subset), marked
-// in the team's bitmap where they fall in groups [g0, g0 + SG) (16-bit entry
-// gl: bits 0-7 child 1, bits 8-15 child 2).
-template <class KP>
-__device__ __noinline__ void mark_sites(const RunDesc &R, const KP &kp, int c, int s2, int t,
-                                        int g0, int SG, uint32_t *bmw, int ebase) {
+// 2^x and log2 x with one MUFU instruction each (PTX ex2/lg2.approx,
+// relative error ~2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// SBX spread factor of one variable (Appendix B: beta from Mc, sign from R1,
+// B = 1 where R2 keeps the variable or the pair does not cross).  Word q
+// carries Mc = (q >> 8) 2^-24, the sign coin (bit 0) and the keep coin
+// (bit 1).  Mc < 1/2 iff bit 31 is clear; then 2 Mc = u 2^-23, otherwise
+// 2 - 2 Mc = (2^24 - u) 2^-23, both exact, so log2 of the base is
+// log2(integer) - 23.
+__device__ __forceinline__ float sbx_B(uint32_t q, bool nocross, float ie) {
+  const uint32_t u = q >> 8;
+  const bool lowb = (int32_t)q >= 0;
+  const float lb = lg2_approx((float)(lowb ? u : 0x1000000u - u)) - 23.0f;
+  const float beta = ex2_approx((lowb ? ie : -ie) * lb);
+  const float B = (q & 1u) ? beta : -beta;
+  return ((q & 2u) || nocross) ? 1.0f : B;
+}
+
+// Children of two adjacent variables: with s = x1 + x2 and e = x1 - x2,
+// c1 = ((1+B) x1 + (1-B) x2) / 2 = (s + B e) / 2 and c2 = s - c1, clipped to
+// [L, U].  Equal parents give equal children exactly.
+__device__ __forceinline__ void sbx_pair(float2 x1, float2 x2, float2 B, float L, float U,
+                                         float2 &c1, float2 &c2) {
+  const float2 sm = add2(x1, x2), df = sub2(x1, x2);
+  c1 = mul2(splat2(0.5f), fma2(B, df, sm));
+  c2 = sub2(sm, c1);
+  c1 = make_float2(clampf(c1.x, L, U), clampf(c1.y, L, U));
+  c2 = make_float2(clampf(c2.x, L, U), clampf(c2.y, L, U));
+}
+
+// Main-pass work on four adjacent variables (float4 Q of the row) of both
+// children: SBX from Philox SBX (Q, p, t), clip, store, accumulate g-terms.
+template <int PROB, class KP>
+__device__ __forceinline__ void cross4(const float4 xa, const float4 xb, int Q, int p, int t,
+                                       bool nocross, float ie, float L, float U, const KP &kp,
+                                       float4 *y1, float4 *y2, float2 &acc1, float2 &acc2) {
+  const uint4 r = philox_k((uint32_t)Q, (uint32_t)p, (uint32_t)t, TAG_SBX, kp);
+  float2 a0, a1, b0, b1;   // children 1 and 2, variables (0,1) and (2,3)
+  sbx_pair(make_float2(xa.x, xa.y), make_float2(xb.x, xb.y),
+           make_float2(sbx_B(r.x, nocross, ie), sbx_B(r.y, nocross, ie)), L, U, a0, b0);
+  sbx_pair(make_float2(xa.z, xa.w), make_float2(xb.z, xb.w),
+           make_float2(sbx_B(r.z, nocross, ie), sbx_B(r.w, nocross, ie)), L, U, a1, b1);
+  if (PROB != PROB_NEURO) {
+    acc1 = g_terms2(PROB, a0, acc1);
+    acc1 = g_terms2(PROB, a1, acc1);
+    acc2 = g_terms2(PROB, b0, acc2);
+    acc2 = g_terms2(PROB, b1, acc2);
+  }
+  *y1 = make_float4(a0.x, a0.y, a1.x, a1.y);
+  if (y2) *y2 = make_float4(b0.x, b0.y, b1.x, b1.y);
+}
+
+// The same for a float4 that holds some of x_1..x_{m-1} (j < mh, kept out
+// of g) or reaches past the last variable (j >= d): g-terms per variable.
+template <int PROB, class KP>
+__device__ __noinline__ void cross4_edge(const float4 xa, const float4 xb, int Q, int p, int t,
+                                         bool nocross, float ie, float L, float U, const KP &kp,
+                                         float4 *y1, float4 *y2, float2 &acc1, float2 &acc2,
+                                         int mh, int d) {
+  float2 z1 = make_float2(0.f, 0.f), z2 = z1;
+  float4 c1, c2;
+  cross4<PROB_NEURO>(xa, xb, Q, p, t, nocross, ie, L, U, kp, &c1, &c2, z1, z2);
+  *y1 = c1;
+  if (y2) *y2 = c2;
+  if (PROB == PROB_NEURO) return;
+  const float u1[4] = {c1.x, c1.y, c1.z, c1.w}, u2[4] = {c2.x, c2.y, c2.z, c2.w};
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = 4 * Q + v;
+    if (j < mh || j >= d) continue;
+    if (v & 1) {
+      acc1.y = g_term1(PROB, u1[v], acc1.y);
+      acc2.y = g_term1(PROB, u2[v], acc2.y);
+    } else {
+      acc1.x = g_term1(PROB, u1[v], acc1.x);
+      acc2.x = g_term1(PROB, u2[v], acc2.x);
+    }
+  }
+}
+
+// Mutation of one crossed variable in place; returns term(new) - term(old).
+template <int PROB, class KP>
+__device__ __forceinline__ float mutate_one(float *px, int j, int c, int t, const RunDesc &R,
+                                            const KP &kp) {
+  const float x = __ldcg(px);
+  const uint4 w = philox_k((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTMAG, kp);
+  const float xn = poly_mutate(x, u24f(w.y), R.L, R.U, R.eta_m);
+  __stcg(px, xn);
+  return (PROB != PROB_NEURO && j >= R.m - 1) ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f)
+                                              : 0.0f;
+}
+
+// Polynomial mutation of child c (pool row `slot`) at its sites in
+// [jlo, jhi): site count, then Floyd's uniform subset; returns the change
+// of the row's g sum.  Every site when the per-site probability is 1.
+template <int PROB, class KP>
+__device__ __noinline__ float mutate_sites(const RunDesc &R, const KP &kp, int c, int slot, int t,
+                                           int jlo, int jhi) {
+  float *const row = R.X + (size_t)slot * R.d_pad;
+  float dg = 0.0f;
   const int d = R.d;
+  if (R.T_m >= (1u << 24)) {
+    for (int j = jlo; j < min(jhi, d); ++j) dg += mutate_one<PROB>(row + j, j, c, t, R, kp);
+    return dg;
+  }
   uint4 w = philox_k(0u, (uint32_t)c, (uint32_t)t, TAG_MUTSITE, kp);
   const int nthr = R.n_mthr;
   int k = 0;
@@ -169,130 +282,46 @@ __device__ __noinline__ void mark_sites(const RunDesc &R, const KP &kp, int c, i
     for (int l = 0; l < i; ++l)
       if ((uint32_t)sites[l] == r) { r = J; break; }
     sites[i] = (int)r;
-    const int gl = (int)(r >> 3) - g0;
-    if (gl >= 0 && gl < SG) {
-      const int hw = ebase + gl;
-      atomicOr(&bmw[hw >> 1], 1u << (((hw & 1) << 4) + (s2 << 3) + (r & 7)));
-    }
+    if ((int)r >= jlo && (int)r < jhi) dg += mutate_one<PROB>(row + r, (int)r, c, t, R, kp);
   }
-}
-
-// 2^x with one MUFU.EX2 (PTX ex2.approx, relative error ~2^-22).
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// SBX spread factor of one variable: word q carries Mc (top 24 bits), the
-// sign coin (bit 0) and the keep coin (bit 1); keep or no crossover -> 1.
-__device__ __forceinline__ float sbx_B(uint32_t q, bool nocross, float ie) {
-  const float Mc = u24f(q);
-  const bool lowb = Mc < 0.5f;
-  const float base = lowb ? 2.0f * Mc : 2.0f - 2.0f * Mc;
-  const float beta = ex2_approx((lowb ? ie : -ie) * __log2f(base));
-  const float B = (q & 1u) ? beta : -beta;
-  return ((q & 2u) || nocross) ? 1.0f : B;
-}
-
-// Children of two adjacent variables: c1 = ((1+B) x1 + (1-B) x2) / 2,
-// c2 = ((1-B) x1 + (1+B) x2) / 2, clipped to [L, U].
-__device__ __forceinline__ void sbx_pair(float2 x1, float2 x2, float2 B, float L, float U,
-                                         float2 &c1, float2 &c2) {
-  const float2 P = add2(splat2(1.0f), B), Q = sub2(splat2(1.0f), B);
-  c1 = mul2(splat2(0.5f), fma2(P, x1, mul2(Q, x2)));
-  c2 = mul2(splat2(0.5f), fma2(Q, x1, mul2(P, x2)));
-  c1 = make_float2(clampf(c1.x, L, U), clampf(c1.y, L, U));
-  c2 = make_float2(clampf(c2.x, L, U), clampf(c2.y, L, U));
-}
-
-// Four adjacent variables of both children: (a0, a1) child 1, (b0, b1) child 2.
-struct Quad { float2 a0, a1, b0, b1; };
-
-// Polynomial mutation of the marked variables of a quad (bits of h1 / h2 for
-// children c1 / c2; first variable j0).  Rare (about one site per row), so
-// kept out of the main loop's instruction stream.
-template <class KP>
-__device__ __noinline__ Quad mutate_quad(Quad q, uint32_t h1, uint32_t h2, int j0, int c1, int c2,
-                                         int t, float L, float U, float eta_m, const KP &kp) {
-  float x[8] = {q.a0.x, q.a0.y, q.a1.x, q.a1.y, q.b0.x, q.b0.y, q.b1.x, q.b1.y};
-  const uint32_t bits = h1 | (h2 << 4);
-#pragma unroll 1
-  for (int b = 0; b < 8; ++b) {
-    if (!(bits & (1u << b))) continue;
-    const int v = b & 3, c = b < 4 ? c1 : c2;
-    const uint4 w = philox_k((uint32_t)(j0 + v), (uint32_t)c, (uint32_t)t, TAG_MUTMAG, kp);
-    x[b] = poly_mutate(x[b], u24f(w.y), L, U, eta_m);
-  }
-  return Quad{make_float2(x[0], x[1]), make_float2(x[2], x[3]), make_float2(x[4], x[5]),
-              make_float2(x[6], x[7])};
-}
-
-// Evaluation terms of a quad that holds x_1..x_{m-1} (kept in hb for the
-// objectives) or the ragged end of the row; returns the accumulators
-// (child 1 in a0, child 2 in a1), given in acc.a0 / acc.a1.
-template <int PROB>
-__device__ __noinline__ Quad eval_edge(Quad q, Quad acc, int j0, int mh, int d, float *hb) {
-  const float c1[4] = {q.a0.x, q.a0.y, q.a1.x, q.a1.y}, c2[4] = {q.b0.x, q.b0.y, q.b1.x, q.b1.y};
-  float2 acc1 = acc.a0, acc2 = acc.a1;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int j = j0 + v;
-    if (j < mh) {
-      hb[j] = c1[v];
-      hb[kMaxM + j] = c2[v];
-    } else if (j < d) {
-      if (v & 1) {
-        acc1.y = g_term1(PROB, c1[v], acc1.y);
-        acc2.y = g_term1(PROB, c2[v], acc2.y);
-      } else {
-        acc1.x = g_term1(PROB, c1[v], acc1.x);
-        acc2.x = g_term1(PROB, c2[v], acc2.x);
-      }
-    }
-  }
-  return Quad{acc1, acc2, acc1, acc2};
+  return dg;
 }
 
 // Last segment of pair p to arrive: g of both children from the segments'
-// partial sums in segment order, then the objectives and the ideal point.
+// partial sums in segment order, x_1..x_{m-1} read back from the child rows
+// (after their mutation), then the objectives and the ideal point.
+template <int PROB>
 __device__ __noinline__ void finish_pair(const RunDesc &R, int p, int S, int ch1, int ch2) {
   __threadfence();
   const float *ps = R.psum + (size_t)p * 2 * S;
-  const float *hb = R.hbuf + (size_t)p * 2 * kMaxM;
-  const int m = R.m, mh = m - 1, n2 = 2 * R.N;
-  float g1 = 0.f, g2 = 0.f;
+  const int m = R.m, mh = m - 1, n2 = 2 * R.N, dp = R.d_pad;
+  float gg[2] = {0.f, 0.f};
   for (int sg = 0; sg < S; ++sg) {
-    g1 += __ldcg(ps + sg);
-    g2 += __ldcg(ps + S + sg);
+    gg[0] += __ldcg(ps + sg);
+    gg[1] += __ldcg(ps + S + sg);
   }
-  float head[kMaxM], f[kMaxM];
-  for (int j = 0; j < mh; ++j) head[j] = __ldcg(hb + j);
-  dtlz_objectives(R.problem, m, g1, head, f);
-  for (int kk = 0; kk < m; ++kk) {
-    R.F[(size_t)kk * n2 + ch1] = f[kk];
-    atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
-  }
-  if (ch2 >= 0) {
-    for (int j = 0; j < mh; ++j) head[j] = __ldcg(hb + kMaxM + j);
-    dtlz_objectives(R.problem, m, g2, head, f);
+  const int chs[2] = {ch1, ch2};
+  for (int c = 0; c < 2; ++c) {
+    if (chs[c] < 0) continue;
+    const float *row = R.X + (size_t)chs[c] * dp;
+    float head[kMaxM], f[kMaxM];
+    for (int j = 0; j < mh; ++j) head[j] = __ldcg(row + j);
+    dtlz_objectives(PROB, m, gg[c], head, f);
     for (int kk = 0; kk < m; ++kk) {
-      R.F[(size_t)kk * n2 + ch2] = f[kk];
+      R.F[(size_t)kk * n2 + chs[c]] = f[kk];
       atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
     }
   }
   R.pcnt[p] = 0;
 }
 
-template <int PROB, class KP>
+template <int PROB, bool STAGED, class KP>
 __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
-  __shared__ uint32_t s_w[kReproThreads / 32][kBmWords];
-
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const ReproItem it = static_cast<const ReproItem *>(dir.items[run])[blockIdx.x - dir.prefix[run]];
-  const int TS = R.team, tpw = 32 / TS, S = R.nseg, SG = TS * kLaneGroups;
-  const int m = R.m, d = R.d, G = R.G, N = R.N, P = R.P;
+  const int TS = R.team, tpw = 32 / TS, S = R.nseg, sg = R.sg;
+  const int d = R.d, G = R.G, N = R.N, P = R.P;
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   const int tw = wl / TS, lane = wl & (TS - 1), tbase = tw * TS;
   const int unit = it.pair0 + warp * tpw + tw;
@@ -300,11 +329,6 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   const bool active = p < P;
   const int t = R.ctl->t;
   const int *cslot = R.child_slot + (t & 1) * N;
-  uint32_t *bmw = s_w[warp];
-  uint16_t *bm = reinterpret_cast<uint16_t *>(bmw) + tw * SG;   // [SG] of this team: c1 | c2 << 8
-
-#pragma unroll
-  for (int w = 0; w < kBmWords; w += 32) bmw[w + wl] = 0u;
 
   // ---- phase 0: the pair's two mating draws and crossover gate ------------
   uint32_t v0 = 0, v1 = 0, v2 = 0;
@@ -335,81 +359,96 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
     if (ch2 >= 2 * N) { set_status(R.ctl, ST_BADINDEX); ch2 = -1; }
   }
   const bool has2 = ch2 >= 0;
-  const int g0 = seg * SG;
+  const int g0 = seg * sg, gE = min(G, g0 + sg);
   // run constants used inside the loops, in registers: the child-row stores
   // could alias the descriptor, which would force a reload after each store
   float4 *const X4 = reinterpret_cast<float4 *>(R.X);
   const uint32_t rq = (uint32_t)R.d_pad >> 2;      // float4s per row
-  const uint32_t o1 = (uint32_t)par1 * rq, o2 = (uint32_t)par2 * rq;
-  const uint32_t T_m = R.T_m;
-  const float L = R.L, U = R.U, ie = R.inv_eta_c1, eta_m = R.eta_m;
-  float *const hb = R.hbuf + (size_t)p * 2 * kMaxM;
-  __syncwarp();
+  const uint32_t q1 = (uint32_t)ch1 * rq, q2 = has2 ? (uint32_t)ch2 * rq : 0u;
+  const float L = R.L, U = R.U, ie = R.inv_eta_c1;
+  // float4s [Qs, Qe) hold neither x_1..x_{m-1} nor variables past d
+  const int mh = R.m - 1, Qs = (mh + 3) >> 2, Qe = d >> 2;
 
-  // ---- phase A: mutation sites of this segment ----------------------------
-  if (active && T_m > 0) {
-    if (T_m >= (1u << 24)) {   // every site
-#pragma unroll 1
-      for (int k = 0; k < kLaneGroups; ++k) {
-        const int gl = lane + k * TS, g = g0 + gl;
-        if (g >= G) break;
-        const uint32_t vmask = 8 * g + 8 <= d ? 0xFFu : (1u << (d - 8 * g)) - 1u;
-        bm[gl] = (uint16_t)(vmask | (has2 ? vmask << 8 : 0u));
-      }
-    } else {
-      for (int c = lane; c < 2; c += TS)
-        if (c == 0 || has2) mark_sites(R, kp, c ? p + P : p, c, t, g0, SG, bmw, tw * SG);
-    }
-  }
-  __syncwarp();
-
-  // ---- phase B: SBX, clip, mutation, evaluation, store --------------------
+  // ---- main pass: SBX, clip, g-terms, store --------------------------------
   float2 acc1 = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
-  const bool eval = PROB != PROB_NEURO;
-  const int mh = m - 1;
-  if (active) {
-    float4 *const Y4 = X4;
-    const uint32_t q1 = (uint32_t)ch1 * rq, q2 = has2 ? (uint32_t)ch2 * rq : 0u;
+  if (STAGED && active) {
+    // Parent segments staged in shared memory by the TMA engine: chunks of
+    // 32 groups (1 KB per parent) in a ring of kStages buffers, so each warp
+    // has the next chunks in flight while it works on one.  One team per
+    // warp (TS == 32): lane l takes float4s l and l + 32 of a chunk.
+    extern __shared__ __align__(128) unsigned char dsm[];
+    float4 *const sb = reinterpret_cast<float4 *>(dsm) + warp * (kStages * 128);
+    uint64_t *const bar =
+        reinterpret_cast<uint64_t *>(dsm + (kReproThreads / 32) * kStageWarpBytes) + warp * kStages;
+    if (wl == 0) {
+      for (int q = 0; q < kStages; ++q) mbar_init(&bar[q], 1);
+      fence_mbar_init();
+    }
+    __syncwarp();
+    const int nch = (gE - g0 + 31) >> 5;
+    const float *const Xf = R.X;
+    const size_t r1 = (size_t)par1 * R.d_pad, r2 = (size_t)par2 * R.d_pad;
+    auto issue = [&](int c) {
+      const int gs = g0 + 32 * c, q = c % kStages;
+      const uint32_t bytes = (uint32_t)(min(gE, gs + 32) - gs) * 32u;
+      fence_proxy_async_smem();   // this stage's earlier reads come first
+      mbar_expect_tx(&bar[q], 2u * bytes);
+      tma_load_1d(sb + q * 128, Xf + r1 + 8 * gs, bytes, &bar[q]);
+      tma_load_1d(sb + q * 128 + 64, Xf + r2 + 8 * gs, bytes, &bar[q]);
+    };
+    if (wl == 0)
+      for (int c = 0; c < min(kStages - 1, nch); ++c) issue(c);
+    int c = 0;
 #pragma unroll 1
-    for (int k = 0; k < kLaneGroups; ++k) {
-      const int gl = lane + k * TS, g = g0 + gl;
-      if (g >= G) break;
-      const uint32_t mb = bm[gl];
-      const bool plain = 8 * g >= mh && 8 * g + 8 <= d;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float4 xa = __ldg(X4 + o1 + 2 * g + h), xb = __ldg(X4 + o2 + 2 * g + h);
-        const uint4 r = philox_k((uint32_t)(2 * g + h), (uint32_t)p, (uint32_t)t, TAG_SBX, kp);
-        float2 a0, a1, b0, b1;   // children 1 and 2, variables (0,1) and (2,3)
-        sbx_pair(make_float2(xa.x, xa.y), make_float2(xb.x, xb.y),
-                 make_float2(sbx_B(r.x, nocross, ie), sbx_B(r.y, nocross, ie)), L, U, a0, b0);
-        sbx_pair(make_float2(xa.z, xa.w), make_float2(xb.z, xb.w),
-                 make_float2(sbx_B(r.z, nocross, ie), sbx_B(r.w, nocross, ie)), L, U, a1, b1);
-        const uint32_t h1 = (mb >> (4 * h)) & 0xFu, h2 = has2 ? (mb >> (8 + 4 * h)) & 0xFu : 0u;
-        if (h1 | h2) {
-          const Quad o = mutate_quad(Quad{a0, a1, b0, b1}, h1, h2, 8 * g + 4 * h, p, p + P, t, L, U,
-                                     eta_m, kp);
-          a0 = o.a0; a1 = o.a1; b0 = o.b0; b1 = o.b1;
+    for (; c < nch; ++c) {
+      if (wl == 0 && c + kStages - 1 < nch) issue(c + kStages - 1);
+      const int q = c % kStages;
+      if (!mbar_wait(&bar[q], (uint32_t)(c / kStages) & 1u, kWaitLimit)) break;
+      const int gs = g0 + 32 * c, n4 = 2 * (min(gE, gs + 32) - gs);
+      if (2 * gs >= Qs && 2 * gs + n4 <= Qe) {   // an interior chunk (warp-uniform)
+#pragma unroll 1
+        for (int qi = wl; qi < n4; qi += 32) {
+          const int Q = 2 * gs + qi;   // float4 index in the row: variables 4Q .. 4Q+3
+          cross4<PROB>(sb[q * 128 + qi], sb[q * 128 + 64 + qi], Q, p, t, nocross, ie, L, U, kp,
+                       X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2);
         }
-        if (eval) {
-          if (plain) {
-            acc1 = g_terms2(PROB, a0, acc1);
-            acc1 = g_terms2(PROB, a1, acc1);
-            acc2 = g_terms2(PROB, b0, acc2);
-            acc2 = g_terms2(PROB, b1, acc2);
-          } else {   // a group holding x_1..x_{m-1} or the ragged end of the row
-            const Quad o = eval_edge<PROB>(Quad{a0, a1, b0, b1}, Quad{acc1, acc2, acc1, acc2},
-                                           8 * g + 4 * h, mh, d, hb);
-            acc1 = o.a0;
-            acc2 = o.a1;
-          }
+      } else {
+        for (int qi = wl; qi < n4; qi += 32) {
+          const int Q = 2 * gs + qi;
+          cross4_edge<PROB>(sb[q * 128 + qi], sb[q * 128 + 64 + qi], Q, p, t, nocross, ie, L, U,
+                            kp, X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2, mh, d);
         }
-        Y4[q1 + 2 * g + h] = make_float4(a0.x, a0.y, a1.x, a1.y);
-        if (has2) Y4[q2 + 2 * g + h] = make_float4(b0.x, b0.y, b1.x, b1.y);
       }
+      __syncwarp();
+    }
+    if (c < nch) {   // a copy never arrived: flag it, let the copies in flight land
+      if (wl == 0) set_status(R.ctl, ST_TIMEOUT);
+      for (int e = c + 1; e < min(nch, c + kStages); ++e)
+        mbar_wait(&bar[e % kStages], (uint32_t)(e / kStages) & 1u, kWaitLimit);
+    }
+  } else if (active) {
+    const uint32_t o1 = (uint32_t)par1 * rq, o2 = (uint32_t)par2 * rq;
+#pragma unroll 1
+    for (int Q = 2 * g0 + lane; Q < 2 * gE; Q += TS) {
+      if (Q >= Qs && Q < Qe)
+        cross4<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kp,
+                     X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2);
+      else
+        cross4_edge<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kp,
+                          X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2, mh, d);
     }
   }
-  if (!eval) return;   // objectives come from the rollout kernel
+  // ---- mutation pass: the sites of this segment ----------------------------
+  __syncwarp();   // the crossed rows are visible to the whole team
+  if (active && R.T_m > 0) {
+    for (int c = lane; c < 2; c += TS) {
+      if (c == 1 && !has2) break;
+      const float dg = mutate_sites<PROB>(R, kp, c ? p + P : p, c ? ch2 : ch1, t, 8 * g0,
+                                          8 * gE);
+      if (c == 0) acc1.x += dg; else acc2.x += dg;
+    }
+  }
+  if (PROB == PROB_NEURO) return;   // objectives come from the rollout kernel
 
   // ---- combine: team sum, then segments in order, then objectives ---------
   const float2 gs = team_sum2(make_float2(acc1.x + acc1.y, acc2.x + acc2.y), TS);
@@ -418,46 +457,52 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
     ps[seg] = gs.x;
     ps[S + seg] = gs.y;
   }
-  // the warp barrier orders the team's writes (child rows, head values,
-  // partials) before the leader's cumulative fence and its arrival
+  // the warp barrier orders the team's writes (child rows, partials) before
+  // the leader's cumulative fence and its arrival
   __syncwarp();
   if (active && lane == 0) {
     __threadfence();
     const int prev = atomicAdd(&R.pcnt[p], 1);
-    if (prev == S - 1) finish_pair(R, p, S, ch1, ch2);
-  }
-}
-
-template <class KP>
-__device__ __forceinline__ void repro_dispatch(const BatchDir &dir, const KP &kp) {
-  const int run = dir_find(dir, blockIdx.x);
-  switch (dir.desc[run]->problem) {
-    case PROB_DTLZ1: repro_body<PROB_DTLZ1>(dir, kp); return;
-    case PROB_DTLZ2: repro_body<PROB_DTLZ2>(dir, kp); return;
-    default: repro_body<PROB_NEURO>(dir, kp); return;
+    if (prev == S - 1) finish_pair<PROB>(R, p, S, ch1, ch2);
   }
 }
 
 // One run of a known problem: the Philox round keys come in the parameter
-// block.
-__global__ void __launch_bounds__(kReproThreads, 3)
-k_repro1_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {
-  repro_body<PROB_DTLZ1>(dir, KeyConst{rk});
-}
-__global__ void __launch_bounds__(kReproThreads, 3)
-k_repro1_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {
-  repro_body<PROB_DTLZ2>(dir, KeyConst{rk});
-}
-__global__ void __launch_bounds__(kReproThreads, 3)
-k_repro1_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {
-  repro_body<PROB_NEURO>(dir, KeyConst{rk});
-}
+// block.  The _s instances stage the parent rows in shared memory (teams of
+// 32 lanes, d > 1024); the others load them directly.
+#define RVEA_REPRO1(name, PROB, STAGED)                                                    \
+  __global__ void __launch_bounds__(kReproThreads, 4)                                      \
+  name(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk) {       \
+    repro_body<PROB, STAGED>(dir, KeyConst{rk});                                           \
+  }
+RVEA_REPRO1(k_repro1_dtlz1, PROB_DTLZ1, false)
+RVEA_REPRO1(k_repro1_dtlz2, PROB_DTLZ2, false)
+RVEA_REPRO1(k_repro1_neuro, PROB_NEURO, false)
+RVEA_REPRO1(k_repro1s_dtlz1, PROB_DTLZ1, true)
+RVEA_REPRO1(k_repro1s_dtlz2, PROB_DTLZ2, true)
+RVEA_REPRO1(k_repro1s_neuro, PROB_NEURO, true)
+#undef RVEA_REPRO1
 
-// A batch of runs: each CTA's round keys follow from its run's key.
-__global__ void __launch_bounds__(kReproThreads, 3)
+// A batch of runs: each CTA's round keys follow from its run's key; runs with
+// 32-lane teams take the staged path (the launch then carries its shared
+// memory).
+__global__ void __launch_bounds__(kReproThreads, 4)
 k_repro(const __grid_constant__ BatchDir dir) {
   const int run = dir_find(dir, blockIdx.x);
-  repro_dispatch(dir, KeyRun{dir.key[run].x, dir.key[run].y});
+  const KeyRun kp{dir.key[run].x, dir.key[run].y};
+  const RunDesc &R = *dir.desc[run];
+  const bool staged = R.team == 32;
+  switch (R.problem) {
+    case PROB_DTLZ1:
+      if (staged) repro_body<PROB_DTLZ1, true>(dir, kp); else repro_body<PROB_DTLZ1, false>(dir, kp);
+      return;
+    case PROB_DTLZ2:
+      if (staged) repro_body<PROB_DTLZ2, true>(dir, kp); else repro_body<PROB_DTLZ2, false>(dir, kp);
+      return;
+    default:
+      if (staged) repro_body<PROB_NEURO, true>(dir, kp); else repro_body<PROB_NEURO, false>(dir, kp);
+      return;
+  }
 }
 
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
@@ -500,7 +545,7 @@ k_init(const __grid_constant__ BatchDir dir) {
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
         const int j = 8 * g + v;
-        if (j >= d) x[v] = 0.0f;   // zero padding
+        if (j >= d) x[v] = 0.5f;   // padding: a g-term of exactly zero on [0, 1]
         else if (R.problem != PROB_NEURO) {
           if (j >= mh) acc.x = g_term1(R.problem, x[v], acc.x);
           else head[j] = x[v];

@@ -140,19 +140,14 @@ __device__ __forceinline__ void apd_vote(const RunDesc &R, int i, const float *f
   const int m = R.m;
   const unsigned long long key = atomicExch(&R.amax[i], 0ull);
   const int j = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
-  const float dot = ord2f((unsigned)(key >> 32));
-  float s = fp[0] * fp[0];
-  for (int k = 1; k < m; ++k) s = fmaf(fp[k], fp[k], s);
-  const float nf = sqrtf(s);
-  float theta = 1.5707963267948966f;
-  if (nf > 0.0f) theta = acosf(fminf(1.0f, fmaxf(-1.0f, dot / nf)));
   const int t = R.op_mode ? R.t_op : R.ctl->t;
   const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
   if (j < 0 || j >= R.N) {
     set_status(R.ctl, ST_BADINDEX);
     return;
   }
-  const float apd = (1.0f + pen * theta / R.gamma32[j]) * nf;
+  const float apd = apd_chord(fp, m, R.V32 + (size_t)j * R.m4 * 4,
+                              R.V32lo ? R.V32lo + (size_t)j * m : nullptr, R.gamma32[j], pen);
   R.assoc[i] = j;
   atomicMin(&R.best[j], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
 }

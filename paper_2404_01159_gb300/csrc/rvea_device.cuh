@@ -21,6 +21,9 @@ constexpr int kSelBlock = 2 * kSelThreads;   // solutions per selection work ite
 constexpr int kVTile = 512;        // reference vectors per shared-memory tile
 constexpr int kFinThreads = 1024;  // CTA size of the per-run finalize kernel
 constexpr int kMaxSites = 32;      // cap of the mutation-site count of one row
+constexpr int kStages = 2;         // staged reproduction: chunks per warp in shared memory
+constexpr int kStageWarpBytes = kStages * 2 * 1024;   // per warp: kStages x 2 parents x 1 KB
+constexpr int kStagedSmem = (kReproThreads / 32) * (kStageWarpBytes + kStages * 8);
 
 // Philox counter tags (word 3 of the counter).
 enum : uint32_t {
@@ -55,7 +58,8 @@ struct RunDesc {
   int problem;
   int t_max, p_adapt;
   int team;            // threads per reproduction team (power of two <= 32, function of d)
-  int nseg;            // segments per pair: a team handles 4*team groups of one pair
+  int nseg;            // segments per pair
+  int sg;              // groups per segment, ceil(G / nseg) <= kLaneGroups * team
   int op_mode;         // 1: stateless selection (identity slots, AoS F)
   // parameters
   float L, U, alpha, inv_eta_c1, eta_m;
@@ -77,10 +81,10 @@ struct RunDesc {
   int *assoc;          // [n_comb]   vector of each solution, -1 if invalid
   int *surv;           // [N]        combined index kept by vector j, -1 if none
   float *psum;         // [P][2][nseg] partial g sums of the segments of each pair
-  float *hbuf;         // [P][2][kMaxM] first m-1 variables of each child
   int *pcnt;           // [P]        arrival counters of the segments of each pair
   int *blk_cnt;        // [n_comb/256] arrival counters of the selection blocks
   float *V32;          // [N][m4*4]  reference vectors, zero padded
+  float *V32lo;        // [N][m]     V64 - V32 rounded to float (null: zero)
   double *V64;         // [N][m]
   double *V0;          // [N][m]     initial unit lattice
   double *gamma64;     // [N]
@@ -285,6 +289,36 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 }
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// APD (Eq. 4) of a solution f' (float; f' >= 0) against its unit vector v,
+// APD = (1 + pen theta / gamma) |f'|.  theta comes from the chord,
+// |f' - |f'| v| = |f'| 2 sin(theta / 2), not from acos of the cosine: near
+// theta = 0 the cosine carries no information below float resolution, and
+// the penalty divides theta by gamma (about 1e-3 rad at N = 9870).  v is a
+// float pair hi + lo (the FP64 vector to ~1e-15; lo may be null), each
+// chord component is formed with two fmas, and the rounding of |f'| only
+// moves the chord along v, a second-order change, so theta keeps a relative
+// accuracy of a few float roundings on theta <= pi/2 (f', v >= 0).
+__device__ __forceinline__ float apd_chord(const float *fp, int m, const float *vhi,
+                                           const float *vlo, float gam, float pen) {
+  float s = 0.0f;
+  for (int k = 0; k < m; ++k) s = fmaf(fp[k], fp[k], s);
+  const float nf = sqrtf(s);
+  if (nf == 0.0f) return 0.0f;   // f' = 0: theta = pi/2 by convention, APD = 0
+  float w2 = 0.0f;
+  for (int k = 0; k < m; ++k) {
+    float w = fmaf(-nf, vhi[k], fp[k]);
+    if (vlo) w = fmaf(-nf, vlo[k], w);
+    w2 = fmaf(w, w, w2);
+  }
+  const float th = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(w2) / nf));
+  return (1.0f + pen * th / gam) * nf;
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),

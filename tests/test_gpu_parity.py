@@ -24,7 +24,9 @@ def _cuda():
 
 
 # (m, d, N, H, problem): cfg0 shape, a ragged DTLZ1 case spanning several
-# reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10.
+# reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10;
+# the last two (d > 1024) take the shared-memory-staged reproduction path,
+# with segments of several chunks, a partial last chunk and row padding.
 SHAPES = [
     (3, 12, 105, 13, 0),
     (3, 1001, 210, 19, 1),
@@ -33,6 +35,8 @@ SHAPES = [
     (10, 30, 220, 3, 0),
     (3, 3, 105, 13, 1),
     (3, 300, 1275, 49, 0),
+    (3, 2500, 105, 13, 1),
+    (2, 4099, 100, 99, 0),
 ]
 
 
@@ -60,11 +64,26 @@ def test_init_matches_oracle(orc, shape):
 
 @pytest.mark.parametrize("shape", SHAPES)
 def test_teacher_forced_generations(orc, shape):
+    _teacher_forced(orc, shape, 9)
+
+
+# Mutation rates other than one site per row: several sites per row (p_m = 4
+# and the largest accepted, 8, with sites in every segment of a staged row)
+# and every site (p_m = d).
+@pytest.mark.parametrize("shape,p_m", [((3, 300, 105, 13, 1), 8.0),
+                                       ((3, 2500, 105, 13, 0), 4.0),
+                                       ((3, 40, 105, 13, 0), 40.0),
+                                       ((2, 1500, 100, 99, 1), 1500.0)])
+def test_teacher_forced_mutation_rates(orc, shape, p_m):
+    _teacher_forced(orc, shape, 3, p_m=p_m)
+
+
+def _teacher_forced(orc, shape, gens, **kw):
     m, d, N, H, prob = shape
-    p = params(orc, m, d, N, H, prob, t_max=40, seed=5)        # adapts every 4th gen
+    p = params(orc, m, d, N, H, prob, t_max=40, seed=5, **kw)   # adapts every 4th gen
     V0 = orc.lattice_unit(orc.lattice(m, H))
     run = make_run(p)
-    for gen in range(9):
+    for gen in range(gens):
         st = run.export_state()
         ost = _state_to_oracle(orc, st)
         t = ost.t
