@@ -190,21 +190,171 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+BATCHED = "batched256_cfg3"
+
+
+def batch_bytes(insts) -> int:
+    """Algorithmic bytes of one batched generation: every run's parents read
+    (2 ceil(N/2) rows) and children written (N rows)."""
+    return sum((2 * ((i.N + 1) // 2) + i.N) * i.d * 4 for i in insts)
+
+
+def main_batched(args, rank, world, local):
+    """Uneven runs stepped together: one CUDA graph per batched generation,
+    plans from the autotuner; the same runs stepped one after another is the
+    sequential comparison."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2404_01159_gb300 import Batch, Run, autotune
+    from paper_2404_01159_gb300.workloads import batched_set
+    K, W = args.steps, max(3, args.warmup)
+    insts = batched_set(256, 500, seed0=rank * 256)
+    t0 = time.perf_counter()
+    runs = [Run(**i.run_kwargs()) for i in insts]
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plans = [autotune(r) for r in runs]
+    t_tune = time.perf_counter() - t0
+    batch = Batch(runs)
+    batch.step(W)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(local)
+    gid = str(getattr(props, "uuid", "")) or str(local)
+    if gid and not gid.startswith("GPU-") and len(gid) >= 32:
+        gid = "GPU-" + gid
+    sampler = ClockSampler(gid) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.step(K)
+    e1.record()
+    e1.synchronize()
+    if sampler:
+        sampler.stop()
+    ms = e0.elapsed_time(e1)
+    for r in runs:
+        r.sync_status()
+    # the same runs, one after another (each its own graph), K_seq generations each
+    Ks = max(3, min(K, 10))
+    for r in runs:
+        r.step(2)
+    torch.cuda.synchronize()
+    e0.record()
+    for r in runs:
+        r.step(Ks)
+    e1.record()
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    Kp = max(1, min(K, 20))
+    phases = batch.step_profiled(Kp)
+    batch.free()
+    nb = batch_bytes(insts)
+    hbm_peak, peak_kind = peaks()
+    value = len(runs) * K / (ms * 1e-3)
+    seq = len(runs) * Ks / (ms_seq * 1e-3)
+    achieved = nb / (ms / K * 1e-3) / 1e9
+    modes = {}
+    for pl in plans:
+        key = ("pruned-smem", "pruned-L1")[pl["sel_mode"] - 1] if pl["sel_mode"] else \
+            f"scan/{pl['sel_per_sm']}"
+        key += "+staged" if pl["repro_staged"] else "+direct"
+        modes[key] = modes.get(key, 0) + 1
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batched(insts, args.cpu_seconds)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "run-generations/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (256 seeded uneven runs, closed-form DTLZ objectives)",
+        "config": {"workload": BATCHED, "runs": len(runs),
+                   "m": "uniform {2,3,5,10}", "N": f"{min(i.N for i in insts)}..{max(i.N for i in insts)}",
+                   "d": f"{min(i.d for i in insts)}..{max(i.d for i in insts)} log-uniform",
+                   "t_max": 500, **{k: v for k, v in COMMON.items()},
+                   "workspace_gb": sum(r.workspace_nbytes for r in runs) / 1e9,
+                   "parallelism": "one CUDA graph per batched generation",
+                   "l2": f"no flush: {nb / 1e9:.1f} GB moved per batched generation > 129 MB L2",
+                   "plans": modes},
+        "sequential": {"value": seq, "unit": "run-generations/s", "steps_per_run": Ks,
+                       "what": "the same runs stepped one after another (rvea_step, "
+                               "graph per run)"},
+        "batched_over_sequential": value / seq,
+        "roofline": {"kernel": "whole batched generation (all phases of all runs)",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": nb,
+                     "avg_launch_ms": ms / K,
+                     "timing": f"CUDA events around {K} graph replays"},
+        "phase_ms_per_generation": {"repro": phases[0] / Kp, "select_pruned": phases[1] / Kp,
+                                    "select_scan": phases[2] / Kp, "finalize": phases[3] / Kp,
+                                    "gamma_tiles": phases[4] / Kp},
+        "setup_s": {"init": t_init, "autotune": t_tune},
+        "cpu_baseline": cpu,
+        "e2e": None,
+        "gpu_launches": K * 6,
+        "clocks": sampler.summary() if sampler else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_batched(insts, seconds=20.0):
+    """The FP64 oracle on the host cores over a bounded sample of the same
+    runs: one generation each of as many runs (in order) as fit in
+    `seconds`."""
+    from oracle import oracle as orc
+    orc.build()
+    threads = os.cpu_count() or 1
+    orc.set_threads(threads)
+    done, gens, t0 = 0, 0, time.perf_counter()
+    for i in insts:
+        p = orc.make_params(**i.run_kwargs())
+        V0, st = orc.initial_state(p)
+        orc.generation(p, V0, st)
+        gens += 1
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": gens / el, "unit": "run-generations/s", "cores": threads, "kind": "oracle",
+            "sample": f"one FP64 oracle generation (after its initialisation) of each of the "
+                      f"first {done} runs of the same set, initialisation included in the time"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dtlz1_m3_d5000_N9870", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="dtlz1_m3_d5000_N9870",
+                    choices=sorted(WORKLOADS) + [BATCHED])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == BATCHED:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle arm times the single-run workload only"}))
+            return
+        main_batched(args, rank, world, local)
+        return
+    wl = WORKLOADS[args.workload]
 
     if args.impl == "reference":
         run_reference(args, wl, rank, world)

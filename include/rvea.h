@@ -126,6 +126,66 @@ rvea_status rvea_step(rvea_run *run, int n_generations, void *cuda_stream);
  * gives.  All runs must live on the current device. */
 rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream);
 
+/* Kernel variants of a run (its "plan").  None of them changes a result bit:
+ *   sel_mode   0: association by the full scan of every reference vector
+ *                 (Algorithm 1, lines 5-6), tiled into work items of
+ *                 (256 solutions x a chunk of vectors), sel_per_sm items per
+ *                 SM (1..16): the chunk size;
+ *              (the full-scan table is kept for every mode, so sel_per_sm
+ *              is always 1..16);
+ *              1: the exact pruned search with its tile tables in shared
+ *                 memory (one run per launch); 2: the same search with the
+ *                 tables read through L1 (the form batches use).  Modes 1, 2
+ *                 need m <= 4 and N >= 1000;
+ *   repro_staged 1: parents staged in shared memory by TMA bulk copies
+ *                 (runs with d > 1024), 0: loaded directly.
+ * repro_us / sel_us: the autotuner's median launch times (0 if untuned). */
+typedef struct {
+    int sel_mode;
+    int sel_per_sm;
+    int repro_staged;
+    double repro_us;
+    double sel_us;
+} rvea_plan;
+
+/* The run's current plan. */
+rvea_status rvea_get_plan(const rvea_run *run, rvea_plan *out);
+
+/* Sets the plan (synchronises `cuda_stream`).  RVEA_ERR_ARG for a variant
+ * the run's shape does not have (see rvea_plan). */
+rvea_status rvea_set_plan(rvea_run *run, const rvea_plan *plan, void *cuda_stream);
+
+/* Autotuner: times every variant of the run's plan on its current
+ * generation -- the reproduction and association launches of a generation
+ * are idempotent, so the run is neither advanced nor changed -- and keeps
+ * the fastest of each phase.  Synchronous.  With use_cache != 0 a plan
+ * already tuned for the same (m, d, N, problem) in this process is reused
+ * without timing.  out (may be NULL) receives the plan and its times. */
+rvea_status rvea_autotune(rvea_run *run, void *cuda_stream, int use_cache, rvea_plan *out);
+
+/* A fixed set of runs stepped together: one batched generation (the
+ * reproduction of all runs, the pruned association of the runs whose plan
+ * uses it, the full scan of the others, finalize, and gamma plus the tile
+ * tables of the runs that adapt) captured once as a CUDA graph and replayed
+ * once per generation.  Each run's results are the bits rvea_step gives.
+ * The plans are read at creation: re-create the batch after rvea_set_plan
+ * or rvea_autotune.  1 <= n_runs <= 320, runs distinct; the runs must not
+ * be stepped otherwise while the batch is in use. */
+typedef struct rvea_batch rvea_batch;
+rvea_status rvea_batch_create(rvea_run *const *runs, int n_runs, rvea_batch **out);
+
+/* Enqueue n_generations >= 0 batched generations on `cuda_stream`. */
+rvea_status rvea_batch_step(rvea_batch *batch, int n_generations, void *cuda_stream);
+
+/* As rvea_batch_step with direct launches (no graph) and CUDA events around
+ * every phase; synchronous.  phase_ms[0..4] (n_phases >= 5) receive the
+ * summed device time of: reproduction, pruned association, full-scan
+ * association, finalize, gamma plus tile tables. */
+rvea_status rvea_batch_step_profiled(rvea_batch *batch, int n_generations, void *cuda_stream,
+                                     double *phase_ms, int n_phases);
+
+void rvea_batch_free(rvea_batch *batch);
+
 /* Copy the population (N x d float32, slot order) and the valid flags
  * (N uint8, may be NULL).  dst, valid: host or device. */
 rvea_status rvea_population(const rvea_run *run, float *dst, uint8_t *valid,

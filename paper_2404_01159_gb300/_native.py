@@ -35,6 +35,11 @@ class Config(C.Structure):
                 ("neuro", C.POINTER(NeuroDynamics))]
 
 
+class Plan(C.Structure):
+    _fields_ = [("sel_mode", C.c_int), ("sel_per_sm", C.c_int), ("repro_staged", C.c_int),
+                ("repro_us", C.c_double), ("sel_us", C.c_double)]
+
+
 class RveaError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -110,5 +115,19 @@ def lib():
         L.rvea_select_noalloc.restype = i32
         L.rvea_gamma.argtypes = [i32, i32, vp, vp, vp]
         L.rvea_gamma.restype = i32
+        L.rvea_get_plan.argtypes = [vp, C.POINTER(Plan)]
+        L.rvea_get_plan.restype = i32
+        L.rvea_set_plan.argtypes = [vp, C.POINTER(Plan), vp]
+        L.rvea_set_plan.restype = i32
+        L.rvea_autotune.argtypes = [vp, vp, i32, C.POINTER(Plan)]
+        L.rvea_autotune.restype = i32
+        L.rvea_batch_create.argtypes = [C.POINTER(C.c_void_p), i32, C.POINTER(C.c_void_p)]
+        L.rvea_batch_create.restype = i32
+        L.rvea_batch_step.argtypes = [vp, i32, vp]
+        L.rvea_batch_step.restype = i32
+        L.rvea_batch_step_profiled.argtypes = [vp, i32, vp, C.POINTER(C.c_double), i32]
+        L.rvea_batch_step_profiled.restype = i32
+        L.rvea_batch_free.argtypes = [vp]
+        L.rvea_batch_free.restype = None
         _lib = L
     return _lib

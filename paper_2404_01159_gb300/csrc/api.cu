@@ -14,7 +14,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <new>
 #include <vector>
@@ -46,6 +48,8 @@ __global__ void k_op_zstar(const RunDesc *Rp);
 __global__ void k_op_finish(const RunDesc *Rp);
 __global__ void k_select_pruned(const RunDesc *Rp);
 __global__ void k_tiles(const RunDesc *Rp);
+__global__ void k_select_pruned_batch(const __grid_constant__ BatchDir dir);
+__global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force);
 }  // namespace rvea
 
 using namespace rvea;
@@ -68,12 +72,14 @@ int pow2ceil(int x) {
 struct Shape {
   int m, m4, d, d_pad, G, N, P, n_comb, team, ppc, nseg, sg;
   int n_repro, n_init, n_sel, nblk, nch, chunk;
+  int n_sel_max;   // work items of the finest full-scan plan (table size)
   int tmax;     // tiles of the pruned selection (0: not used)
 };
 
 // Pruned selection: m <= 4 and the tile-ordered vectors plus the tile table
 // fit one CTA's shared memory (about 12k vectors).
 constexpr int kPruneMinN = 1000;
+constexpr int kSelPerSmMax = 16;   // full scan: the finest plan (work items per SM)
 constexpr size_t kPruneSmemCap = 200 * 1024;
 int prune_tiles_bound(int N) { return N / 16 + 2; }
 size_t prune_smem(int N, int T) {
@@ -106,6 +112,10 @@ Shape make_shape(int m, int d, int N) {
   s.nch = sp.nch;
   s.chunk = sp.chunk;
   s.n_sel = s.nblk * s.nch;
+  {
+    const SelPlan fine = sel_plan(s.n_comb, N, s.m4, kSMs, kSelPerSmMax);
+    s.n_sel_max = std::max(s.n_sel, fine.nblk * fine.nch);
+  }
   s.tmax = 0;
   if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap)
     s.tmax = prune_tiles_bound(N);
@@ -149,7 +159,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.desc = take(sizeof(RunDesc));
   L.repro = take((size_t)s.n_repro * sizeof(ReproItem));
   L.init = take((size_t)s.n_init * sizeof(ReproItem));
-  L.sel = take((size_t)s.n_sel * sizeof(SelItem));
+  L.sel = take((size_t)s.n_sel_max * sizeof(SelItem));
   L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
   L.pcnt = take((size_t)s.P * 4);
@@ -340,6 +350,13 @@ struct rvea_run {
   RunDesc *d_desc = nullptr;
   int repro_smem = 0, init_smem = 0, sel_smem = 0, fin_smem = 0;
   int prune_smem_bytes = 0, num_sms = 152;
+  // kernel variants (the plan): none of them changes the results
+  int sel_mode = 0;               // 0 full scan, 1 pruned (tables in shared memory), 2 pruned (L1)
+  int sel_per_sm = 8;             // full scan: work items per SM
+  int n_sel = 0;                  // full scan: work items of the current plan
+  bool tuned = false;
+  double tune_repro_us = 0.0, tune_sel_us = 0.0;
+  std::vector<SelItem> sel_host;  // source of the last upload of the item table
   cudaStream_t last_stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t block_graph = nullptr;
@@ -378,6 +395,21 @@ T *wsp(const rvea_run *r, size_t off) {
   return reinterpret_cast<T *>(r->ws + off);
 }
 
+// Item table of the full-scan association for the run's current plan
+// (sel_per_sm work items per SM), into sel_host; n_sel and the shared memory
+// of one chunk follow.
+void build_sel_items(rvea_run *r) {
+  const Shape &sh = r->sh;
+  const SelPlan sp = sel_plan(sh.n_comb, sh.N, sh.m4, kSMs, r->sel_per_sm);
+  r->sel_host.clear();
+  for (int b = 0; b < sp.nblk; ++b)
+    for (int c = 0; c < sp.nch; ++c)
+      r->sel_host.push_back(SelItem{b, std::min(sh.N, c * sp.chunk),
+                                    std::min(sh.N, (c + 1) * sp.chunk), sp.nch});
+  r->n_sel = (int)r->sel_host.size();
+  r->sel_smem = std::min(sh.N, sp.chunk) * sh.m4 * 16;
+}
+
 // Reproduction of one run: the kernel instance for its problem, round keys
 // in the parameter block; 32-lane teams stage the parents in shared memory.
 void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t st) {
@@ -398,47 +430,78 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
   }
 }
 
-// Enqueue one generation of every run in `runs` (one launch per phase).
-rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, bool gamma_by_flag) {
-  static thread_local BatchDir dr, ds, df, dd;
-  int pr = 0, ps = 0, pd = 0;
-  int smr = 0, sms = 0, smf = 0;
-  dr.n = ds.n = df.n = dd.n = n;
+// Enqueue one generation of every run in `runs` (one launch per phase): the
+// reproduction of all runs; the association of the pruned runs (one
+// persistent launch) and of the full-scan runs; finalize; with
+// gamma_by_flag, gamma and the tile tables of the runs that adapted.
+rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, bool gamma_by_flag,
+                              cudaEvent_t *ev = nullptr) {
+  static thread_local BatchDir dr, ds, dp, df, dd, dt;
+  int pr = 0, ps = 0, pp = 0, pd = 0, pt = 0;
+  int smr = 0, sms = 0, ns = 0, np = 0;
+  dr.n = df.n = dd.n = n;
   for (int q = 0; q < n; ++q) {
     const rvea_run *r = runs[q];
+    const uint2 key = make_uint2(r->hd.key0, r->hd.key1);
     dr.prefix[q] = pr;
-    ds.prefix[q] = ps;
     df.prefix[q] = q;
     dd.prefix[q] = pd;
-    dr.desc[q] = ds.desc[q] = df.desc[q] = dd.desc[q] = r->d_desc;
-    dr.key[q] = ds.key[q] = df.key[q] = dd.key[q] = make_uint2(r->hd.key0, r->hd.key1);
-    dd.items[q] = nullptr;
-    pd += (r->sh.N + 1023) / 1024;
+    dr.desc[q] = df.desc[q] = dd.desc[q] = r->d_desc;
+    dr.key[q] = df.key[q] = dd.key[q] = key;
     dr.items[q] = wsp<ReproItem>(r, r->lay.repro);
-    ds.items[q] = wsp<SelItem>(r, r->lay.sel);
-    df.items[q] = nullptr;
+    df.items[q] = dd.items[q] = nullptr;
+    pd += (r->sh.N + 1023) / 1024;
     pr += r->sh.n_repro;
-    ps += r->sh.n_sel;
     smr = std::max(smr, r->repro_smem);
-    sms = std::max(sms, r->sel_smem);
-    smf = std::max(smf, r->fin_smem);
+    if (r->sel_mode == 0) {
+      ds.prefix[ns] = ps;
+      ds.desc[ns] = r->d_desc;
+      ds.key[ns] = key;
+      ds.items[ns] = wsp<SelItem>(r, r->lay.sel);
+      ps += r->n_sel;
+      sms = std::max(sms, r->sel_smem);
+      ++ns;
+    } else {
+      dp.prefix[np] = pp;
+      dt.prefix[np] = pt;
+      dp.desc[np] = dt.desc[np] = r->d_desc;
+      dp.key[np] = dt.key[np] = key;
+      dp.items[np] = dt.items[np] = nullptr;
+      pp += (r->sh.n_comb + 3) / 4;
+      pt += (r->hd.ntiles + 7) / 8;
+      ++np;
+    }
   }
   dr.prefix[n] = pr;
-  ds.prefix[n] = ps;
   df.prefix[n] = n;
   dd.prefix[n] = pd;
+  ds.n = ns;
+  ds.prefix[ns] = ps;
+  dp.n = dt.n = np;
+  dp.prefix[np] = pp;
+  dt.prefix[np] = pt;
+  if (ev) cudaEventRecord(ev[0], st);
   if (n == 1)
     launch_repro1(runs[0], dr, pr, st);
   else
     k_repro<<<pr, kReproThreads, smr, st>>>(dr);
-  if (n == 1 && runs[0]->hd.ntiles > 0)
-    k_select_pruned<<<runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st>>>(runs[0]->d_desc);
-  else
-    k_select<<<ps, kSelThreads, sms, st>>>(ds);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (np > 0) {
+    if (n == 1 && runs[0]->sel_mode == 1)
+      k_select_pruned<<<runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st>>>(runs[0]->d_desc);
+    else
+      k_select_pruned_batch<<<runs[0]->num_sms, 1024, 0, st>>>(dp);
+  }
+  if (ev) cudaEventRecord(ev[2], st);
+  if (ns > 0) k_select<<<ps, kSelThreads, sms, st>>>(ds);
+  if (ev) cudaEventRecord(ev[3], st);
   k_finalize<<<pd, 1024, 0, st>>>(dd);
+  if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
     k_gamma<<<2 * kSMs, 256, 0, st>>>(df, 0);
+    if (np > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
   }
+  if (ev) cudaEventRecord(ev[5], st);
   return cuerr(cudaGetLastError());
 }
 
@@ -617,26 +680,16 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.pcnt = wsp<int>(r, lay.pcnt);
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
-  r->repro_smem = sh.team == 32 ? kStagedSmem : 0;   // staged path: one 32-lane team per warp
+  r->repro_smem = sh.team == 32 ? kStagedSmem : 0;   // staged path (the default for 32-lane teams)
   r->init_smem = sh.ppc * std::max(1, sh.m - 1) * 4;
-  r->sel_smem = std::min(sh.N, sh.chunk) * sh.m4 * 16;
   r->fin_smem = 0;
 
   // host tables
   std::vector<ReproItem> rep(sh.n_repro), ini(sh.n_init);
   for (int q = 0; q < sh.n_repro; ++q) rep[q].pair0 = q * sh.ppc;
   for (int q = 0; q < sh.n_init; ++q) ini[q].pair0 = q * sh.ppc;
-  std::vector<SelItem> sel;
-  sel.reserve(sh.n_sel);
-  for (int b = 0; b < sh.nblk; ++b)
-    for (int c = 0; c < sh.nch; ++c) {
-      SelItem it;
-      it.sblk = b;
-      it.v0 = std::min(sh.N, c * sh.chunk);
-      it.v1 = std::min(sh.N, (c + 1) * sh.chunk);
-      it.nchunks = sh.nch;
-      sel.push_back(it);
-    }
+  r->sel_per_sm = 8;
+  build_sel_items(r);
   std::vector<double> V0;
   build_lattice(sh.m, cfg->H, sh.N, V0);
   std::vector<int> tperm;
@@ -646,6 +699,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     if ((int)trng.size() > sh.tmax) trng.clear();   // cannot happen; keeps the bound honest
   }
   D.ntiles = (int)trng.size();
+  r->sel_mode = D.ntiles > 0 ? 1 : 0;
+  D.repro_staged = sh.team == 32 ? 1 : 0;
   if (D.ntiles > 0) {
     D.Vt = wsp<float4>(r, lay.Vt);
     D.tperm = wsp<int>(r, lay.tperm);
@@ -676,7 +731,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.desc, &D, sizeof(D));
   up(lay.repro, rep.data(), rep.size() * sizeof(ReproItem));
   up(lay.init, ini.data(), ini.size() * sizeof(ReproItem));
-  up(lay.sel, sel.data(), sel.size() * sizeof(SelItem));
+  up(lay.sel, r->sel_host.data(), r->sel_host.size() * sizeof(SelItem));
   up(lay.V0, V0.data(), V0.size() * 8);
   up(lay.V64, V0.data(), V0.size() * 8);
   up(lay.V32, V32.data(), V32.size() * 4);
@@ -762,6 +817,279 @@ rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream
   return RVEA_OK;
 }
 
+}  // extern "C"
+
+// ---- kernel variants and the autotuner ------------------------------------
+
+namespace {
+
+rvea_status apply_plan(rvea_run *r, const rvea_plan &pl, cudaStream_t st) {
+  if (pl.sel_mode < 0 || pl.sel_mode > 2 || (pl.sel_mode > 0 && r->hd.ntiles == 0))
+    return RVEA_ERR_ARG;
+  if (pl.sel_per_sm < 1 || pl.sel_per_sm > kSelPerSmMax) return RVEA_ERR_ARG;
+  if (pl.repro_staged && r->sh.team != 32) return RVEA_ERR_ARG;
+  const bool was_pruned = r->sel_mode > 0;
+  r->sel_mode = pl.sel_mode;
+  if (pl.sel_per_sm != r->sel_per_sm) {   // the full-scan table, kept valid in every mode
+    r->sel_per_sm = pl.sel_per_sm;
+    build_sel_items(r);
+    RV_TRY(cudaMemcpyAsync(r->ws + r->lay.sel, r->sel_host.data(),
+                           r->sel_host.size() * sizeof(SelItem), cudaMemcpyHostToDevice, st));
+  }
+  const int staged = pl.repro_staged ? 1 : 0;
+  if (staged != r->hd.repro_staged) {
+    r->hd.repro_staged = staged;
+    RV_TRY(cudaMemcpyAsync(&r->d_desc->repro_staged, &r->hd.repro_staged, sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+  }
+  r->repro_smem = staged ? kStagedSmem : 0;
+  // a run that was not kept up to date by the pruned path rebuilds its tiles
+  if (pl.sel_mode > 0 && !was_pruned) {
+    const rvea_status s = launch_tiles(r, st);
+    if (s != RVEA_OK) return s;
+  }
+  if (r->block_graph) {   // captured with the old variants
+    cudaGraphExecDestroy(r->block_graph);
+    r->block_graph = nullptr;
+  }
+  // host sources of the copies above live in the run; finish them here
+  RV_TRY(cudaStreamSynchronize(st));
+  return RVEA_OK;
+}
+
+rvea_plan current_plan(const rvea_run *r) {
+  rvea_plan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  pl.sel_mode = r->sel_mode;
+  pl.sel_per_sm = r->sel_per_sm;
+  pl.repro_staged = r->hd.repro_staged;
+  pl.repro_us = r->tune_repro_us;
+  pl.sel_us = r->tune_sel_us;
+  return pl;
+}
+
+struct TuneKey {
+  int m, d, N, problem;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(m, d, N, problem) < std::tie(o.m, o.d, o.N, o.problem);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, rvea_plan> g_tune_cache;
+
+}  // namespace
+
+extern "C" {
+
+rvea_status rvea_get_plan(const rvea_run *r, rvea_plan *out) {
+  if (!r || !out) return RVEA_ERR_ARG;
+  *out = current_plan(r);
+  return RVEA_OK;
+}
+
+rvea_status rvea_set_plan(rvea_run *r, const rvea_plan *pl, void *cuda_stream) {
+  if (!r || !pl) return RVEA_ERR_ARG;
+  return apply_plan(r, *pl, static_cast<cudaStream_t>(cuda_stream));
+}
+
+// Times every variant on the run's current generation without advancing it:
+// the reproduction and association launches of one generation are
+// idempotent (the same children, F and votes are written again; the pruned
+// kernels' work counter is reset around each launch), and finalize, which
+// does advance the run, is not timed.
+rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_plan *out) {
+  if (!r) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const TuneKey key{r->sh.m, r->sh.d, r->sh.N, r->cfg.problem};
+  if (use_cache) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      rvea_status s = apply_plan(r, it->second, st);
+      if (s != RVEA_OK) return s;
+      r->tune_repro_us = it->second.repro_us;
+      r->tune_sel_us = it->second.sel_us;
+      r->tuned = true;
+      if (out) *out = current_plan(r);
+      return RVEA_OK;
+    }
+  }
+  RV_TRY(cudaStreamSynchronize(st));
+  cudaEvent_t e0, e1;
+  RV_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RVEA_ERR_CUDA;
+  }
+  rvea_status s = RVEA_OK;
+  int *sel_cnt = &reinterpret_cast<Ctl *>(r->ws + r->lay.ctl)->sel_cnt;
+  constexpr int kReps = 3;
+  // median of kReps timed launches after one untimed one
+  auto timed = [&](auto &&launch, bool reset_cnt) -> double {
+    double ms[kReps];
+    for (int q = -1; q < kReps && s == RVEA_OK; ++q) {
+      if (reset_cnt && cudaMemsetAsync(sel_cnt, 0, sizeof(int), st) != cudaSuccess) s = RVEA_ERR_CUDA;
+      cudaEventRecord(e0, st);
+      launch();
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        s = RVEA_ERR_CUDA;
+        break;
+      }
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      if (q >= 0) ms[q] = f;
+    }
+    std::sort(ms, ms + kReps);
+    return ms[kReps / 2] * 1e3;
+  };
+  static thread_local BatchDir dr, ds, dp;
+  dir_single(dr, r, wsp<ReproItem>(r, r->lay.repro), r->sh.n_repro);
+  dir_single(dp, r, nullptr, (r->sh.n_comb + 3) / 4);
+  const rvea_plan before = current_plan(r);
+  rvea_plan best = before;
+  // reproduction: direct loads, and TMA staging for 32-lane teams
+  double best_rep = 1e30;
+  for (int staged = 0; staged <= (r->sh.team == 32 ? 1 : 0) && s == RVEA_OK; ++staged) {
+    r->repro_smem = staged ? kStagedSmem : 0;
+    const double us = timed([&] { launch_repro1(r, dr, r->sh.n_repro, st); }, false);
+    if (us < best_rep) { best_rep = us; best.repro_staged = staged; }
+  }
+  // association: the full scan at 4, 8 and 16 work items per SM, and the
+  // pruned search with its tables in shared memory or read through L1
+  double best_sel = 1e30;
+  if (r->hd.ntiles > 0 && s == RVEA_OK) s = launch_tiles(r, st);
+  const int per_sm[3] = {4, 8, 16};
+  for (int q = 0; q < 3 && s == RVEA_OK; ++q) {
+    r->sel_per_sm = per_sm[q];
+    build_sel_items(r);
+    if (cudaMemcpyAsync(r->ws + r->lay.sel, r->sel_host.data(), r->sel_host.size() * sizeof(SelItem),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) { s = RVEA_ERR_CUDA; break; }
+    dir_single(ds, r, wsp<SelItem>(r, r->lay.sel), r->n_sel);
+    const double us = timed([&] { k_select<<<r->n_sel, kSelThreads, r->sel_smem, st>>>(ds); }, false);
+    if (us < best_sel) { best_sel = us; best.sel_mode = 0; best.sel_per_sm = per_sm[q]; }
+  }
+  if (r->hd.ntiles > 0 && s == RVEA_OK) {
+    double us = timed([&] {
+      k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
+    }, true);
+    if (us < best_sel) { best_sel = us; best.sel_mode = 1; best.sel_per_sm = 8; }
+    us = timed([&] { k_select_pruned_batch<<<r->num_sms, 1024, 0, st>>>(dp); }, true);
+    if (us < best_sel) { best_sel = us; best.sel_mode = 2; best.sel_per_sm = 8; }
+    // the next real generation starts its pruned search from zero
+    if (cudaMemsetAsync(sel_cnt, 0, sizeof(int), st) != cudaSuccess) s = RVEA_ERR_CUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the tables above were rebuilt for the candidates: force the chosen plan
+  r->sel_per_sm = -1;
+  r->repro_smem = before.repro_staged ? kStagedSmem : 0;
+  if (s == RVEA_OK) s = apply_plan(r, best, st);
+  if (s != RVEA_OK) return s;
+  r->tune_repro_us = best_rep;
+  r->tune_sel_us = best_sel;
+  r->tuned = true;
+  best = current_plan(r);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  if (out) *out = best;
+  return RVEA_OK;
+}
+
+// ---- batches of runs as one CUDA graph -------------------------------------
+
+struct rvea_batch {
+  std::vector<rvea_run *> runs;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+rvea_status rvea_batch_create(rvea_run *const *runs, int n_runs, rvea_batch **out) {
+  if (!runs || !out || n_runs < 1 || n_runs > kMaxBatch) return RVEA_ERR_ARG;
+  for (int q = 0; q < n_runs; ++q) {
+    if (!runs[q]) return RVEA_ERR_ARG;
+    for (int u = 0; u < q; ++u)
+      if (runs[u] == runs[q]) return RVEA_ERR_ARG;
+  }
+  rvea_batch *b = new (std::nothrow) rvea_batch();
+  if (!b) return RVEA_ERR_NOMEM;
+  b->runs.assign(runs, runs + n_runs);
+  // one batched generation (all phases; gamma and tile tables by the
+  // adaptation flag), captured once and replayed per generation
+  rvea_status s = RVEA_OK;
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) s = RVEA_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  if (s == RVEA_OK && cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    s = RVEA_ERR_CUDA;
+  if (s == RVEA_OK) {
+    const rvea_status sl = launch_generation(b->runs.data(), n_runs, b->cap, true);
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (sl != RVEA_OK) s = sl;
+    else if (e != cudaSuccess) s = RVEA_ERR_CUDA;
+  }
+  if (s == RVEA_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) s = RVEA_ERR_CUDA;
+  if (g) cudaGraphDestroy(g);
+  if (s != RVEA_OK) {
+    cudaGetLastError();
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return RVEA_OK;
+}
+
+rvea_status rvea_batch_step(rvea_batch *b, int G, void *cuda_stream) {
+  if (!b || G < 0) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  for (int q = 0; q < G; ++q) RV_TRY(cudaGraphLaunch(b->exec, st));
+  for (rvea_run *r : b->runs) {
+    r->t += G;
+    r->last_stream = st;
+    if (G > 0) r->has_last_gen = true;
+  }
+  return RVEA_OK;
+}
+
+rvea_status rvea_batch_step_profiled(rvea_batch *b, int G, void *cuda_stream, double *phase_ms,
+                                     int n_phases) {
+  if (!b || G < 0 || !phase_ms || n_phases < 5) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  for (int q = 0; q < n_phases; ++q) phase_ms[q] = 0.0;
+  cudaEvent_t ev[6];
+  for (int q = 0; q < 6; ++q)
+    if (cudaEventCreate(&ev[q]) != cudaSuccess) {
+      for (int u = 0; u < q; ++u) cudaEventDestroy(ev[u]);
+      return RVEA_ERR_CUDA;
+    }
+  rvea_status s = RVEA_OK;
+  for (int g = 0; g < G && s == RVEA_OK; ++g) {
+    s = launch_generation(b->runs.data(), (int)b->runs.size(), st, true, ev);
+    if (s == RVEA_OK && cudaEventSynchronize(ev[5]) != cudaSuccess) s = RVEA_ERR_CUDA;
+    for (int q = 0; q < 5 && s == RVEA_OK; ++q) {
+      float f = 0.f;
+      cudaEventElapsedTime(&f, ev[q], ev[q + 1]);
+      phase_ms[q] += f;
+    }
+    for (rvea_run *r : b->runs) {
+      r->t += 1;
+      r->last_stream = st;
+      r->has_last_gen = true;
+    }
+  }
+  for (int q = 0; q < 6; ++q) cudaEventDestroy(ev[q]);
+  return s;
+}
+
+void rvea_batch_free(rvea_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
 int rvea_generation(const rvea_run *r) { return r ? r->t : -1; }
 
 rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *phase_ms,
@@ -782,9 +1110,11 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   static thread_local BatchDir dr, ds, df, dg, dd;
   const rvea_run *one = r;
   dir_single(dr, one, wsp<ReproItem>(r, r->lay.repro), r->sh.n_repro);
-  dir_single(ds, one, wsp<SelItem>(r, r->lay.sel), r->sh.n_sel);
+  dir_single(ds, one, wsp<SelItem>(r, r->lay.sel), r->n_sel);
   dir_single(df, one, nullptr, 1);
   dir_single(dg, one, nullptr, 1);
+  static thread_local BatchDir dpb;
+  dir_single(dpb, one, nullptr, (r->sh.n_comb + 3) / 4);
   const int nbd = (r->sh.N + 1023) / 1024;
   dir_single(dd, one, nullptr, nbd);
   const int nbg = std::min((r->sh.N + 31) / 32, 4 * kSMs);
@@ -793,10 +1123,12 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     cudaEventRecord(e[0], st);
     launch_repro1(r, dr, r->sh.n_repro, st);
     cudaEventRecord(e[1], st);
-    if (r->hd.ntiles > 0)
+    if (r->sel_mode == 1)
       k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
+    else if (r->sel_mode == 2)
+      k_select_pruned_batch<<<r->num_sms, 1024, 0, st>>>(dpb);
     else
-      k_select<<<r->sh.n_sel, kSelThreads, r->sel_smem, st>>>(ds);
+      k_select<<<r->n_sel, kSelThreads, r->sel_smem, st>>>(ds);
     cudaEventRecord(e[2], st);
     k_finalize<<<nbd, 1024, 0, st>>>(dd);
     cudaEventRecord(e[3], st);

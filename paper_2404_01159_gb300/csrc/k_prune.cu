@@ -51,21 +51,23 @@ __device__ __forceinline__ void keep(float d, int j, float &best, int &bj) {
   if (d > best || (d == best && j < bj)) { best = d; bj = j; }
 }
 
-template <int M>
-__device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
-                           const float2 *sCS, const int2 *sR) {
+// Tables read from shared memory (staged) or through L1 (G = true).
+template <bool G, class T>
+__device__ __forceinline__ T tld(const T *p) {
+  if constexpr (G) return __ldg(p);
+  else return *p;
+}
+
+// Solutions base .. base+3 of one run, eight lanes each: association by the
+// pruned search, then the APD vote.
+template <int M, bool G>
+__device__ __forceinline__ void prune_group(const RunDesc &R, int base, const float4 *sV,
+                                            const float4 *sC, const float2 *sCS, const int2 *sR,
+                                            const float *z, float pen) {
   const int lane = threadIdx.x & 31, sub = lane & 7;
-  const int T = R.ntiles, N = R.N, n = R.n_comb, m = R.m;
+  const int T = R.ntiles, N = R.N, n = R.n_comb;
   const int t_gen = R.ctl->t;
-  const float pen = (float)m * powf((float)t_gen / (float)R.t_max, R.alpha);
-  float z[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) z[k] = k < M ? ord2f(R.ctl->zkey[k]) : 0.f;
-  for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&R.ctl->sel_cnt, 4);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n) break;
+  {
     const int i = base + (lane >> 3);
     int slot = -1;
     if (i < n) {
@@ -91,7 +93,7 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     float dc1 = -INFINITY;
     int t1 = 0;
     for (int t = sub; t < TT; t += 8) {
-      const float dc = pdot<M>(f, sC[t]);
+      const float dc = pdot<M>(f, tld<G>(sC + t));
       if (dc > dc1) { dc1 = dc; t1 = t; }
     }
 #pragma unroll
@@ -104,9 +106,9 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     float best = -INFINITY;
     int bj = 0x7FFFFFFF;
     {
-      const int2 rg = live ? sR[t1] : make_int2(0, 0);
+      const int2 rg = live ? tld<G>(sR + t1) : make_int2(0, 0);
       for (int q = sub; q < rg.y; q += 8) {
-        const float4 v = sV[rg.x + q];
+        const float4 v = tld<G>(sV + rg.x + q);
         keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
       }
     }
@@ -122,9 +124,9 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     int nc = 0;
     bool over = false;
     for (int t = sub; t < TT; t += 8) {
-      const float2 cs = sCS[t];
+      const float2 cs = tld<G>(sCS + t);
       const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
-      if (t != t1 && pdot<M>(f, sC[t]) >= thr) {
+      if (t != t1 && pdot<M>(f, tld<G>(sC + t)) >= thr) {
         if (nc < kPruneCand) {
 #pragma unroll
           for (int c = 0; c < kPruneCand; ++c)
@@ -143,9 +145,9 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     for (int c = 0; c < kPruneCand; ++c) {
       if (c >= ncmax) break;
       if (c < nc) {
-        const int2 rg = sR[cand[c]];
+        const int2 rg = tld<G>(sR + cand[c]);
         for (int q = 0; q < rg.y; ++q) {
-          const float4 v = sV[rg.x + q];
+          const float4 v = tld<G>(sV + rg.x + q);
           keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
         }
       }
@@ -153,13 +155,13 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     if (over) {   // more candidates than kept: test and scan the rest here
       int seen = 0;
       for (int t = sub; t < TT; t += 8) {
-        const float2 cs = sCS[t];
+        const float2 cs = tld<G>(sCS + t);
         const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
-        if (t != t1 && pdot<M>(f, sC[t]) >= thr) {
+        if (t != t1 && pdot<M>(f, tld<G>(sC + t)) >= thr) {
           if (seen++ < kPruneCand) continue;   // scanned above
-          const int2 rg = sR[t];
+          const int2 rg = tld<G>(sR + t);
           for (int q = 0; q < rg.y; ++q) {
-            const float4 v = sV[rg.x + q];
+            const float4 v = tld<G>(sV + rg.x + q);
             keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
           }
         }
@@ -182,6 +184,25 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
         atomicMin(&R.best[bj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
       }
     }
+  }
+}
+
+// One run, tables in shared memory: warps take four solutions at a time from
+// the run's work counter.
+template <int M>
+__device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
+                           const float2 *sCS, const int2 *sR) {
+  const int lane = threadIdx.x & 31;
+  const float pen = (float)R.m * powf((float)R.ctl->t / (float)R.t_max, R.alpha);
+  float z[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) z[k] = k < M ? ord2f(R.ctl->zkey[k]) : 0.f;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&R.ctl->sel_cnt, 4);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= R.n_comb) break;
+    prune_group<M, false>(R, base, sV, sC, sCS, sR, z, pen);
   }
 }
 
@@ -227,13 +248,46 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
   }
 }
 
+// A batch of runs in one persistent launch: groups of four solutions are
+// numbered across the runs (dir.prefix counts groups) and taken from the
+// work counter of the first run; the tables are read through L1 (the tile
+// centres of a run, ~16 B per tile, stay resident).  CTA 0 resets each run's
+// survivor extrema, which the finalize kernel rebuilds.
+__global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const __grid_constant__ BatchDir dir) {
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0)
+    for (int q = 0; q < dir.n; ++q)
+      if (threadIdx.x < kMaxM) {
+        dir.desc[q]->ctl->znext[threadIdx.x] = 0xFFFFFFFFu;
+        dir.desc[q]->ctl->zhi[threadIdx.x] = 0u;
+      }
+  Ctl *cc = dir.desc[0]->ctl;
+  const int total = dir.prefix[dir.n];
+  for (;;) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(&cc->sel_cnt, 1);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) break;
+    const int run = dir_find(dir, g);
+    const RunDesc &R = *dir.desc[run];
+    const int base = 4 * (g - dir.prefix[run]);
+    const float pen = (float)R.m * powf((float)R.ctl->t / (float)R.t_max, R.alpha);
+    float z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = k < R.m ? ord2f(R.ctl->zkey[k]) : 0.f;
+    switch (R.m) {
+      case 2: prune_group<2, true>(R, base, R.Vt, R.tcen, R.tcs, R.trng, z, pen); break;
+      case 3: prune_group<3, true>(R, base, R.Vt, R.tcen, R.tcs, R.trng, z, pen); break;
+      default: prune_group<4, true>(R, base, R.Vt, R.tcen, R.tcs, R.trng, z, pen); break;
+    }
+  }
+}
+
 // Tile table after a change of V: members in tile order, float32 centres,
 // and conservative (cos rho, sin rho) computed in FP64 from the float32 rows.
 // One warp per tile.
-__global__ void k_tiles(const RunDesc *__restrict__ Rp) {
-  const RunDesc &R = *Rp;
+__device__ __forceinline__ void tile_one(const RunDesc &R, int t) {
   const int lane = threadIdx.x & 31;
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (t >= R.ntiles) return;
   const int2 rg = R.trng[t];
   const int m4 = R.m4;
@@ -271,6 +325,19 @@ __global__ void k_tiles(const RunDesc *__restrict__ Rp) {
     R.tcen[t] = c;
     R.tcs[t] = make_float2(__double2float_rd(cos(rho)), __double2float_ru(sin(rho)));
   }
+}
+
+__global__ void k_tiles(const RunDesc *__restrict__ Rp) {
+  tile_one(*Rp, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+}
+
+// The same over a batch (dir.prefix counts CTAs of 8 tiles): runs whose
+// vectors were adapted this generation (all runs with force).
+__global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force) {
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  if (!force && R.ctl->adapted == 0) return;
+  tile_one(R, (blockIdx.x - dir.prefix[run]) * (blockDim.x >> 5) + (threadIdx.x >> 5));
 }
 
 }  // namespace rvea

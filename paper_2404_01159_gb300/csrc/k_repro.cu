@@ -491,7 +491,7 @@ k_repro(const __grid_constant__ BatchDir dir) {
   const int run = dir_find(dir, blockIdx.x);
   const KeyRun kp{dir.key[run].x, dir.key[run].y};
   const RunDesc &R = *dir.desc[run];
-  const bool staged = R.team == 32;
+  const bool staged = R.repro_staged != 0 && R.team == 32;
   switch (R.problem) {
     case PROB_DTLZ1:
       if (staged) repro_body<PROB_DTLZ1, true>(dir, kp); else repro_body<PROB_DTLZ1, false>(dir, kp);

@@ -59,6 +59,7 @@ struct RunDesc {
   int t_max, p_adapt;
   int team;            // threads per reproduction team (power of two <= 32, function of d)
   int nseg;            // segments per pair
+  int repro_staged;    // 1: parents staged in shared memory by TMA (32-lane teams)
   int sg;              // groups per segment, ceil(G / nseg) <= kLaneGroups * team
   int op_mode;         // 1: stateless selection (identity slots, AoS F)
   // parameters
@@ -132,19 +133,20 @@ struct BatchDir {
 };
 
 // Selection work plan: blocks of kSelBlock solutions x chunks of whole
-// kVTile-vector tiles, at least ~8 CTAs per SM overall, each chunk small
-// enough to sit in shared memory (kSelChunkBytes).
+// kVTile-vector tiles, at least ~per_sm CTAs per SM overall (the tuning knob
+// of the full scan), each chunk small enough to sit in shared memory
+// (kSelChunkBytes).
 constexpr int kSelChunkBytes = 96 * 1024;
 struct SelPlan {
   int nblk, nch, chunk;   // solution blocks, chunks, vectors per chunk
 };
-inline SelPlan sel_plan(int n, int r, int m4, int sms) {
+inline SelPlan sel_plan(int n, int r, int m4, int sms, int per_sm = 8) {
   SelPlan p;
   p.nblk = (n + kSelBlock - 1) / kSelBlock;
   const int tiles = (r + kVTile - 1) / kVTile;
   int cap = kSelChunkBytes / (m4 * 16) / kVTile;
   if (cap < 1) cap = 1;
-  int nch = (8 * sms + p.nblk - 1) / p.nblk;
+  int nch = (per_sm * sms + p.nblk - 1) / p.nblk;
   if (nch > tiles) nch = tiles;
   if (nch < 1) nch = 1;
   int tpc = (tiles + nch - 1) / nch;

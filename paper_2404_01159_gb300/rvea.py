@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 import numpy as np
 import torch
 
-from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, NEURO_LINEAR, Config, NeuroDynamics,
+from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, NEURO_LINEAR, Config, NeuroDynamics, Plan,
                       RveaError, check, lib)
 
 __all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
@@ -173,6 +173,71 @@ class Run:
         check(lib().rvea_last_selection(self._h, _ptr(assoc), _ptr(surv),
                                         C.c_void_p(_stream(stream))), "rvea_last_selection")
         return assoc, surv
+
+
+def _plan_dict(pl) -> dict:
+    return {"sel_mode": pl.sel_mode, "sel_per_sm": pl.sel_per_sm,
+            "repro_staged": pl.repro_staged, "repro_us": pl.repro_us, "sel_us": pl.sel_us}
+
+
+def get_plan(run: "Run") -> dict:
+    """The run's kernel variants (see rvea_plan in include/rvea.h)."""
+    pl = Plan()
+    check(lib().rvea_get_plan(run.handle, C.byref(pl)), "rvea_get_plan")
+    return _plan_dict(pl)
+
+
+def set_plan(run: "Run", sel_mode: int, sel_per_sm: int = 8, repro_staged: int = 0,
+             stream=None) -> None:
+    """Choose the run's kernel variants; none changes its results."""
+    pl = Plan(sel_mode, sel_per_sm, repro_staged, 0.0, 0.0)
+    check(lib().rvea_set_plan(run.handle, C.byref(pl), C.c_void_p(_stream(stream))),
+          "rvea_set_plan")
+
+
+def autotune(run: "Run", use_cache: bool = True, stream=None) -> dict:
+    """Time every kernel variant on the run's current generation (which is
+    left unchanged) and keep the fastest; returns the plan and its times."""
+    pl = Plan()
+    check(lib().rvea_autotune(run.handle, C.c_void_p(_stream(stream)), int(use_cache),
+                              C.byref(pl)), "rvea_autotune")
+    return _plan_dict(pl)
+
+
+class Batch:
+    """A fixed set of runs stepped together: one batched generation captured
+    as a CUDA graph, replayed per generation (rvea_batch_*)."""
+
+    def __init__(self, runs: Sequence["Run"]):
+        self.runs = list(runs)
+        arr = (C.c_void_p * len(self.runs))(*[r.handle.value for r in self.runs])
+        h = C.c_void_p()
+        check(lib().rvea_batch_create(arr, len(self.runs), C.byref(h)), "rvea_batch_create")
+        self._h = h
+
+    def step(self, generations: int = 1, stream=None) -> None:
+        check(lib().rvea_batch_step(self._h, int(generations), C.c_void_p(_stream(stream))),
+              "rvea_batch_step")
+
+    def step_profiled(self, generations: int, stream=None) -> list:
+        """Device ms summed over `generations` per phase: reproduction, pruned
+        association, full-scan association, finalize, gamma + tile tables."""
+        ph = (C.c_double * 5)()
+        check(lib().rvea_batch_step_profiled(self._h, int(generations),
+                                             C.c_void_p(_stream(stream)), ph, 5),
+              "rvea_batch_step_profiled")
+        return list(ph)
+
+    def free(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rvea_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def step_batch(runs: Sequence[Run], stream=None) -> None:

@@ -1,0 +1,103 @@
+"""The batched engine: kernel variants (plans), the autotuner and batches
+captured as CUDA graphs.  Every variant must leave the results unchanged bit
+for bit, so each case compares exported run states exactly."""
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import make_run, params, to_np  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _same(ra, rb):
+    sa, sb = to_np(ra.export_state()), to_np(rb.export_state())
+    for k in ("X", "F", "valid", "V", "gamma", "t"):
+        assert np.array_equal(sa[k], sb[k], equal_nan=True), k
+
+
+# (m, d, N, H, problem): pruned search and TMA-staged reproduction available;
+# pruned only; staged only (m = 5 has no pruned search).
+SHAPES = [(3, 2500, 1275, 49, 1), (2, 300, 1200, 1199, 0), (5, 1500, 126, 5, 0)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_plan_gives_the_same_bits(orc, shape):
+    from paper_2404_01159_gb300 import get_plan, set_plan
+    m, d, N, H, prob = shape
+    p = params(orc, m, d, N, H, prob, t_max=40, seed=9)   # adapts every 4th generation
+    ref = make_run(p)
+    base = get_plan(ref)
+    modes = [(0, 4), (0, 8), (0, 16)] + ([(1, 8), (2, 8)] if base["sel_mode"] > 0 else [])
+    staged = [0, 1] if d > 1024 else [0]
+    ref.step(10)
+    for (mode, per_sm), st in itertools.product(modes, staged):
+        run = make_run(p)
+        set_plan(run, mode, per_sm, st)
+        got = get_plan(run)
+        assert (got["sel_mode"], got["repro_staged"]) == (mode, st)
+        run.step(10)
+        _same(ref, run)
+        run.sync_status()
+
+
+def test_variant_the_shape_lacks_is_refused(orc):
+    from paper_2404_01159_gb300 import RveaError, set_plan
+    run = make_run(params(orc, 5, 40, 126, 5, 0))
+    with pytest.raises(RveaError):
+        set_plan(run, 1)          # no pruned search for m = 5
+    with pytest.raises(RveaError):
+        set_plan(run, 0, 8, 1)    # no staged reproduction for d <= 1024
+    with pytest.raises(RveaError):
+        set_plan(run, 0, 99, 0)   # work items per SM out of range
+
+
+def test_autotune_leaves_the_run_unchanged(orc):
+    from paper_2404_01159_gb300 import autotune
+    p = params(orc, 3, 2500, 1275, 49, 1, t_max=40, seed=4)
+    tuned, plain = make_run(p), make_run(p)
+    plan = autotune(tuned, use_cache=False)
+    assert plan["repro_us"] > 0 and plan["sel_us"] > 0
+    tuned.step(5)
+    plain.step(5)
+    autotune(tuned, use_cache=False)     # mid-run, on an adaptation boundary's neighbour
+    tuned.step(7)
+    plain.step(7)
+    _same(plain, tuned)
+    # the cache returns the same plan without timing
+    again = make_run(p)
+    cached = autotune(again, use_cache=True)
+    assert (cached["sel_mode"], cached["sel_per_sm"], cached["repro_staged"]) == \
+        (plan["sel_mode"], plan["sel_per_sm"], plan["repro_staged"])
+
+
+def test_batch_graph_equals_alone(orc):
+    """Uneven runs (m = 2..10, d from 3 to 2500, pruned and full-scan
+    association, staged and direct reproduction, different adaptation
+    periods) stepped as one CUDA graph per batched generation."""
+    from paper_2404_01159_gb300 import Batch, autotune, set_plan
+    shapes = [(3, 12, 105, 13, 0, 1, 30), (3, 2500, 1275, 49, 1, 2, 40), (10, 30, 220, 3, 0, 3, 50),
+              (2, 300, 1200, 1199, 0, 4, 20), (5, 1500, 126, 5, 1, 5, 30), (3, 3, 105, 13, 1, 6, 60),
+              (4, 64, 1771, 20, 0, 7, 40)]
+    ps = [params(orc, m, d, N, H, pr, t_max=tm, seed=s) for (m, d, N, H, pr, s, tm) in shapes]
+    alone = [make_run(p) for p in ps]
+    batch = [make_run(p) for p in ps]
+    autotune(batch[1])
+    set_plan(batch[3], 0, 16, 0)   # a pruned-capable run on the full scan
+    b = Batch(batch)
+    for _ in range(3):
+        for r in alone:
+            r.step(5)
+        b.step(5)
+    for ra, rb in zip(alone, batch):
+        _same(ra, rb)
+        rb.sync_status()
+    b.free()
