@@ -25,7 +25,12 @@
 #include "rvea_device.cuh"
 
 namespace rvea {
-__global__ void k_repro(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_neuro(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz1s(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz2s(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_neuros(const __grid_constant__ BatchDir dir);
 __global__ void k_repro1_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
@@ -80,6 +85,7 @@ struct Shape {
 // fit one CTA's shared memory (about 12k vectors).
 constexpr int kPruneMinN = 1000;
 constexpr int kSelPerSmMax = 16;   // full scan: the finest plan (work items per SM)
+constexpr int kPruneChunkHost = 2048;   // solutions per work chunk of the batched pruned search
 constexpr size_t kPruneSmemCap = 200 * 1024;
 int prune_tiles_bound(int N) { return N / 16 + 2; }
 size_t prune_smem(int N, int T) {
@@ -319,7 +325,12 @@ void set_kernel_attrs() {
     if (r != cudaSuccess && e == cudaSuccess) e = r;
     note_error(r, "cudaFuncSetAttribute");
   };
-  set((const void *)k_repro);
+  set((const void *)k_reprob_dtlz1);
+  set((const void *)k_reprob_dtlz2);
+  set((const void *)k_reprob_neuro);
+  set((const void *)k_reprob_dtlz1s);
+  set((const void *)k_reprob_dtlz2s);
+  set((const void *)k_reprob_neuros);
   set((const void *)k_repro1_dtlz1);
   set((const void *)k_repro1_dtlz2);
   set((const void *)k_repro1_neuro);
@@ -329,6 +340,7 @@ void set_kernel_attrs() {
   set((const void *)k_init);
   set((const void *)k_select);
   set((const void *)k_select_pruned);
+  set((const void *)k_select_pruned_batch);
 
   g_attr_err = e;
 }
@@ -436,9 +448,9 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
 // gamma_by_flag, gamma and the tile tables of the runs that adapted.
 rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, bool gamma_by_flag,
                               cudaEvent_t *ev = nullptr) {
-  static thread_local BatchDir dr, ds, dp, df, dd, dt;
+  static thread_local BatchDir dr, ds, dp, df, dd, dt, dg[6];
   int pr = 0, ps = 0, pp = 0, pd = 0, pt = 0;
-  int smr = 0, sms = 0, ns = 0, np = 0;
+  int smr = 0, sms = 0, smp = 0, ns = 0, np = 0;
   dr.n = df.n = dd.n = n;
   for (int q = 0; q < n; ++q) {
     const rvea_run *r = runs[q];
@@ -467,7 +479,8 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       dp.desc[np] = dt.desc[np] = r->d_desc;
       dp.key[np] = dt.key[np] = key;
       dp.items[np] = dt.items[np] = nullptr;
-      pp += (r->sh.n_comb + 3) / 4;
+      pp += (r->sh.n_comb + kPruneChunkHost - 1) / kPruneChunkHost;
+      smp = std::max(smp, r->prune_smem_bytes);
       pt += (r->hd.ntiles + 7) / 8;
       ++np;
     }
@@ -481,16 +494,43 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   dp.prefix[np] = pp;
   dt.prefix[np] = pt;
   if (ev) cudaEventRecord(ev[0], st);
-  if (n == 1)
+  if (n == 1) {
     launch_repro1(runs[0], dr, pr, st);
-  else
-    k_repro<<<pr, kReproThreads, smr, st>>>(dr);
+  } else {
+    // one launch per (problem, load path) group, each with its own directory
+    int pg[6] = {0, 0, 0, 0, 0, 0};
+    for (int g = 0; g < 6; ++g) dg[g].n = 0;
+    for (int q = 0; q < n; ++q) {
+      const rvea_run *r = runs[q];
+      const int g = r->hd.problem * 2 + (r->repro_smem > 0 ? 1 : 0);
+      BatchDir &D = dg[g];
+      D.prefix[D.n] = pg[g];
+      D.desc[D.n] = r->d_desc;
+      D.key[D.n] = make_uint2(r->hd.key0, r->hd.key1);
+      D.items[D.n] = wsp<ReproItem>(r, r->lay.repro);
+      pg[g] += r->sh.n_repro;
+      ++D.n;
+    }
+    for (int g = 0; g < 6; ++g) {
+      if (dg[g].n == 0) continue;
+      dg[g].prefix[dg[g].n] = pg[g];
+      const int sm = (g & 1) ? kStagedSmem : 0;
+      switch (g) {
+        case 0: k_reprob_dtlz2<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+        case 1: k_reprob_dtlz2s<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+        case 2: k_reprob_dtlz1<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+        case 3: k_reprob_dtlz1s<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+        case 4: k_reprob_neuro<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+        default: k_reprob_neuros<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+      }
+    }
+  }
   if (ev) cudaEventRecord(ev[1], st);
   if (np > 0) {
     if (n == 1 && runs[0]->sel_mode == 1)
       k_select_pruned<<<runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st>>>(runs[0]->d_desc);
     else
-      k_select_pruned_batch<<<runs[0]->num_sms, 1024, 0, st>>>(dp);
+      k_select_pruned_batch<<<runs[0]->num_sms, 1024, smp, st>>>(dp);
   }
   if (ev) cudaEventRecord(ev[2], st);
   if (ns > 0) k_select<<<ps, kSelThreads, sms, st>>>(ds);
@@ -945,7 +985,7 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
   };
   static thread_local BatchDir dr, ds, dp;
   dir_single(dr, r, wsp<ReproItem>(r, r->lay.repro), r->sh.n_repro);
-  dir_single(dp, r, nullptr, (r->sh.n_comb + 3) / 4);
+  dir_single(dp, r, nullptr, (r->sh.n_comb + kPruneChunkHost - 1) / kPruneChunkHost);
   const rvea_plan before = current_plan(r);
   rvea_plan best = before;
   // reproduction: direct loads, and TMA staging for 32-lane teams
@@ -974,7 +1014,9 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
       k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
     }, true);
     if (us < best_sel) { best_sel = us; best.sel_mode = 1; best.sel_per_sm = 8; }
-    us = timed([&] { k_select_pruned_batch<<<r->num_sms, 1024, 0, st>>>(dp); }, true);
+    us = timed([&] {
+      k_select_pruned_batch<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(dp);
+    }, true);
     if (us < best_sel) { best_sel = us; best.sel_mode = 2; best.sel_per_sm = 8; }
     // the next real generation starts its pruned search from zero
     if (cudaMemsetAsync(sel_cnt, 0, sizeof(int), st) != cudaSuccess) s = RVEA_ERR_CUDA;
@@ -1114,7 +1156,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   dir_single(df, one, nullptr, 1);
   dir_single(dg, one, nullptr, 1);
   static thread_local BatchDir dpb;
-  dir_single(dpb, one, nullptr, (r->sh.n_comb + 3) / 4);
+  dir_single(dpb, one, nullptr, (r->sh.n_comb + kPruneChunkHost - 1) / kPruneChunkHost);
   const int nbd = (r->sh.N + 1023) / 1024;
   dir_single(dd, one, nullptr, nbd);
   const int nbg = std::min((r->sh.N + 31) / 32, 4 * kSMs);
@@ -1126,7 +1168,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     if (r->sel_mode == 1)
       k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
     else if (r->sel_mode == 2)
-      k_select_pruned_batch<<<r->num_sms, 1024, 0, st>>>(dpb);
+      k_select_pruned_batch<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(dpb);
     else
       k_select<<<r->n_sel, kSelThreads, r->sel_smem, st>>>(ds);
     cudaEventRecord(e[2], st);

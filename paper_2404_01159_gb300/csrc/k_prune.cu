@@ -248,37 +248,81 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
   }
 }
 
-// A batch of runs in one persistent launch: groups of four solutions are
-// numbered across the runs (dir.prefix counts groups) and taken from the
-// work counter of the first run; the tables are read through L1 (the tile
-// centres of a run, ~16 B per tile, stay resident).  CTA 0 resets each run's
-// survivor extrema, which the finalize kernel rebuilds.
+// A batch of runs in one persistent launch.  Work comes in chunks of
+// kPruneChunk solutions of one run (dir.prefix counts chunks), taken by whole
+// CTAs from the work counter of the first run; a CTA stages the tables of
+// the chunk's run in shared memory with TMA unless they are already there
+// (chunks come in run order, so a CTA reloads about once per run it visits).
+// CTA 0 resets each run's survivor extrema, which finalize rebuilds.
+constexpr int kPruneChunk = 2048;
+
 __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const __grid_constant__ BatchDir dir) {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_chunk;
+  const int warp = threadIdx.x >> 5;
   if (blockIdx.x == 0)
     for (int q = 0; q < dir.n; ++q)
       if (threadIdx.x < kMaxM) {
         dir.desc[q]->ctl->znext[threadIdx.x] = 0xFFFFFFFFu;
         dir.desc[q]->ctl->zhi[threadIdx.x] = 0u;
       }
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
   Ctl *cc = dir.desc[0]->ctl;
   const int total = dir.prefix[dir.n];
+  int cached = -1;
+  uint32_t phase = 0;
   for (;;) {
-    int g = 0;
-    if (lane == 0) g = atomicAdd(&cc->sel_cnt, 1);
-    g = __shfl_sync(0xffffffffu, g, 0);
-    if (g >= total) break;
-    const int run = dir_find(dir, g);
+    __syncthreads();   // the previous chunk is done with the tables
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&cc->sel_cnt, 1);
+    __syncthreads();
+    const int c = s_chunk;
+    if (c >= total) break;
+    const int run = dir_find(dir, c);
     const RunDesc &R = *dir.desc[run];
-    const int base = 4 * (g - dir.prefix[run]);
+    const int N = R.N, T = R.ntiles;
+    const uint32_t bV = (uint32_t)N * 16, bC = (uint32_t)T * 16, bS = (uint32_t)T * 8;
+    const uint32_t bSr = (bS + 15u) & ~15u;
+    float4 *sV = reinterpret_cast<float4 *>(smem);
+    float4 *sC = reinterpret_cast<float4 *>(smem + bV);
+    float2 *sCS = reinterpret_cast<float2 *>(smem + bV + bC);
+    int2 *sR = reinterpret_cast<int2 *>(smem + bV + bC + bSr);
+    if (run != cached) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
+        tma_load_1d(sV, R.Vt, bV, &s_bar);
+        tma_load_1d(sC, R.tcen, bC, &s_bar);
+        tma_load_1d(sCS, R.tcs, bSr, &s_bar);
+        tma_load_1d(sR, R.trng, bSr, &s_bar);
+      }
+      const bool ok = mbar_wait(&s_bar, phase, kWaitLimit);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          set_status(R.ctl, ST_TIMEOUT);
+          mbar_wait(&s_bar, phase ^ 1u, kWaitLimit);
+        }
+        __syncthreads();
+        return;
+      }
+      cached = run;
+    }
     const float pen = (float)R.m * powf((float)R.ctl->t / (float)R.t_max, R.alpha);
     float z[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) z[k] = k < R.m ? ord2f(R.ctl->zkey[k]) : 0.f;
-    switch (R.m) {
-      case 2: prune_group<2, true>(R, base, R.Vt, R.tcen, R.tcs, R.trng, z, pen); break;
-      case 3: prune_group<3, true>(R, base, R.Vt, R.tcen, R.tcs, R.trng, z, pen); break;
-      default: prune_group<4, true>(R, base, R.Vt, R.tcen, R.tcs, R.trng, z, pen); break;
+    const int base0 = (c - dir.prefix[run]) * kPruneChunk;
+    const int nsol = min(kPruneChunk, R.n_comb - base0);
+    for (int g = 4 * warp; g < nsol; g += 4 * (kPruneThreads / 32)) {
+      switch (R.m) {
+        case 2: prune_group<2, false>(R, base0 + g, sV, sC, sCS, sR, z, pen); break;
+        case 3: prune_group<3, false>(R, base0 + g, sV, sC, sCS, sR, z, pen); break;
+        default: prune_group<4, false>(R, base0 + g, sV, sC, sCS, sR, z, pen); break;
+      }
     }
   }
 }

@@ -483,27 +483,21 @@ RVEA_REPRO1(k_repro1s_dtlz2, PROB_DTLZ2, true)
 RVEA_REPRO1(k_repro1s_neuro, PROB_NEURO, true)
 #undef RVEA_REPRO1
 
-// A batch of runs: each CTA's round keys follow from its run's key; runs with
-// 32-lane teams take the staged path (the launch then carries its shared
-// memory).
-__global__ void __launch_bounds__(kReproThreads, 4)
-k_repro(const __grid_constant__ BatchDir dir) {
-  const int run = dir_find(dir, blockIdx.x);
-  const KeyRun kp{dir.key[run].x, dir.key[run].y};
-  const RunDesc &R = *dir.desc[run];
-  const bool staged = R.repro_staged != 0 && R.team == 32;
-  switch (R.problem) {
-    case PROB_DTLZ1:
-      if (staged) repro_body<PROB_DTLZ1, true>(dir, kp); else repro_body<PROB_DTLZ1, false>(dir, kp);
-      return;
-    case PROB_DTLZ2:
-      if (staged) repro_body<PROB_DTLZ2, true>(dir, kp); else repro_body<PROB_DTLZ2, false>(dir, kp);
-      return;
-    default:
-      if (staged) repro_body<PROB_NEURO, true>(dir, kp); else repro_body<PROB_NEURO, false>(dir, kp);
-      return;
+// A batch of runs of one problem and one load path: each CTA's round keys
+// follow from its run's key.  The host launches one instance per (problem,
+// load path) group present in the batch.
+#define RVEA_REPROB(name, PROB, STAGED)                                                    \
+  __global__ void __launch_bounds__(kReproThreads, 4) name(const __grid_constant__ BatchDir dir) { \
+    const int run = dir_find(dir, blockIdx.x);                                             \
+    repro_body<PROB, STAGED>(dir, KeyRun{dir.key[run].x, dir.key[run].y});                 \
   }
-}
+RVEA_REPROB(k_reprob_dtlz1, PROB_DTLZ1, false)
+RVEA_REPROB(k_reprob_dtlz2, PROB_DTLZ2, false)
+RVEA_REPROB(k_reprob_neuro, PROB_NEURO, false)
+RVEA_REPROB(k_reprob_dtlz1s, PROB_DTLZ1, true)
+RVEA_REPROB(k_reprob_dtlz2s, PROB_DTLZ2, true)
+RVEA_REPROB(k_reprob_neuros, PROB_NEURO, true)
+#undef RVEA_REPROB
 
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
 // objectives.  DTLZ: x = L + (U-L) u24 from INIT (j/4, i, 0) word j%4.
