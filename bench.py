@@ -309,6 +309,98 @@ def main_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+SERVE = "serve_cfg4"
+
+
+def main_serve(args, rank, world, local):
+    """Serving: Poisson arrivals of runs (m, d, N, budget drawn per request),
+    admitted by an HBM budget, their generations batched across live runs
+    each step; time-to-result from arrival to the step that finished it."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2404_01159_gb300 import Server
+    from paper_2404_01159_gb300.workloads import request_stream
+    reqs = request_stream(args.serve_rate, args.serve_seconds, seed=rank)
+    budget = int(args.serve_budget_gb * 1e9)
+    srv = Server(budget, max_live=args.serve_max_live, autotune=True)
+    props = torch.cuda.get_device_properties(local)
+    gid = str(getattr(props, "uuid", "")) or str(local)
+    if gid and not gid.startswith("GPU-") and len(gid) >= 32:
+        gid = "GPU-" + gid
+    sampler = ClockSampler(gid) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    arrival, budget_of, lat = {}, {}, []
+    k, steps, gens_done, live_sum = 0, 0, 0, 0
+    cap_s = args.serve_seconds + args.serve_drain_seconds
+    outstanding = 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k][0] <= now:
+            at, inst = reqs[k]
+            rid = srv.submit(inst.m, inst.d, inst.N, inst.H, inst.problem, inst.generations,
+                             seed=inst.seed)
+            arrival[rid], budget_of[rid] = at, inst.generations
+            k += 1
+            outstanding += 1
+        if outstanding == 0:
+            if k >= len(reqs):
+                break
+            time.sleep(max(0.0, min(0.01, reqs[k][0] - now)))
+            continue
+        st = srv.step()
+        torch.cuda.current_stream().synchronize()
+        steps += 1
+        live_sum += st["live"] + st["admitted"]
+        tdone = time.perf_counter() - t0
+        for rid in srv.poll():
+            srv.fetch(rid)
+            lat.append(tdone - arrival.pop(rid))
+            gens_done += budget_of.pop(rid)
+            outstanding -= 1
+        if tdone > cap_s:
+            break
+    wall = time.perf_counter() - t0
+    if sampler:
+        sampler.stop()
+    srv.free()
+    if rank != 0:
+        return
+    lat.sort()
+    pct = (lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None)
+    line = {
+        "metric": METRIC,
+        "value": gens_done / wall,
+        "unit": "run-generations/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": 0,
+        "ms_per_step": wall / max(1, steps) * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Poisson request stream, closed-form DTLZ objectives)",
+        "config": {"workload": SERVE, "rate_per_s": args.serve_rate,
+                   "arrivals_s": args.serve_seconds, "requests": len(reqs),
+                   "hbm_budget_gb": args.serve_budget_gb, "max_live": args.serve_max_live,
+                   "m": "uniform {2,3,5,10}", "N": "100..9870", "d": "30..5000 log-uniform",
+                   "generations": "U{50..1000}", **COMMON},
+        "serve": {"completed": len(lat), "submitted": k, "unfinished": outstanding,
+                  "p50_s": pct(0.50), "p99_s": pct(0.99), "mean_live_runs": live_sum / max(1, steps),
+                  "wall_s": wall,
+                  "what": "time-to-result = end of the step that finished the run - arrival; "
+                          "wall-clock, the loop synchronises after every step"},
+        "roofline": None,
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": sampler.summary() if sampler else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batched(insts, seconds=20.0):
     """The FP64 oracle on the host cores over a bounded sample of the same
     runs: one generation each of as many runs (in order) as fit in
@@ -339,7 +431,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dtlz1_m3_d5000_N9870",
-                    choices=sorted(WORKLOADS) + [BATCHED])
+                    choices=sorted(WORKLOADS) + [BATCHED, SERVE])
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window")
+    ap.add_argument("--serve-drain-seconds", type=float, default=60.0,
+                    help="time allowed after the arrival window")
+    ap.add_argument("--serve-budget-gb", type=float, default=80.0)
+    ap.add_argument("--serve-max-live", type=int, default=320)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
@@ -347,6 +445,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == SERVE:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle arm times the single-run workload only"}))
+            return
+        main_serve(args, rank, world, local)
+        return
     if args.workload == BATCHED:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":

@@ -285,6 +285,56 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
                                 int t, int t_max, float alpha,
                                 int32_t *assoc, int32_t *survivor, void *cuda_stream);
 
+/* ---- serving loop (continuous batching) ---------------------------------
+ * Not in the paper: a request loop over independent runs.  Requests (a run
+ * configuration and a generation budget) queue on the host.  Each
+ * rvea_server_step first admits queued requests, in arrival order, while
+ * their workspaces fit the caller's device arena (the HBM budget) and fewer
+ * than max_live runs are live -- admission initialises the run on the
+ * device and, with autotune != 0, picks its kernel variants (rvea_autotune,
+ * cached per shape) -- and then enqueues one generation of every live run,
+ * packed into batched launches (rvea_step_batch, 320 runs each).  A run
+ * whose budget is spent leaves the batch; its state stays in the arena until
+ * rvea_server_fetch copies the result out and frees the memory.  Every
+ * run's result is the bits it gets stepped alone.  Not thread-safe. */
+typedef struct rvea_server rvea_server;
+typedef struct {
+    int live;             /* runs in the batch after this step            */
+    int queued;           /* requests waiting for admission               */
+    int finished;         /* budgets spent, results not yet fetched       */
+    int admitted;         /* requests admitted by this step               */
+    size_t arena_used;    /* arena bytes held by live and finished runs   */
+    long long generations;/* run-generations enqueued since creation      */
+} rvea_server_stats;
+
+/* dev_arena: device memory owned by the caller, 256-byte aligned, used for
+ * every run's workspace; max_live >= 1. */
+rvea_status rvea_server_create(void *dev_arena, size_t arena_bytes, int max_live, int autotune,
+                               rvea_server **out);
+
+/* Queue a request (DTLZ problems; cfg->neuro must be NULL); *id_out gets its
+ * id (1, 2, ...).  Validation of cfg happens at admission. */
+rvea_status rvea_server_submit(rvea_server *srv, const rvea_config *cfg, int generations,
+                               int64_t *id_out);
+
+/* Admission, then one generation of every live run, on `cuda_stream`.
+ * Admission synchronises the stream (initialisation uploads).  stats may be
+ * NULL.  A request that fails validation at admission returns its error. */
+rvea_status rvea_server_step(rvea_server *srv, void *cuda_stream, rvea_server_stats *stats);
+
+/* Ids of runs whose budget was spent since the last poll (up to cap); their
+ * results are complete once the stream of the step that finished them is. */
+rvea_status rvea_server_poll(rvea_server *srv, int64_t *ids, int cap, int *n_out);
+
+/* Copy a finished run's population (N x d) and objectives (N x m, valid
+ * flags N) to X / F / valid (host or device; each may be NULL), synchronise
+ * the stream and release the run.  RVEA_ERR_STATE if id is not finished or
+ * already fetched. */
+rvea_status rvea_server_fetch(rvea_server *srv, int64_t id, float *X, float *F, uint8_t *valid,
+                              void *cuda_stream);
+
+void rvea_server_free(rvea_server *srv);
+
 /* gamma_j = min over i != j of the angle between v_i and v_j (Eq. 5), FP64.
  * V (r x m f64, device, unit rows) -> gamma (r f64, device). */
 rvea_status rvea_gamma(int m, int r, const double *V, double *gamma, void *cuda_stream);

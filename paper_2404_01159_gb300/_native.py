@@ -40,6 +40,11 @@ class Plan(C.Structure):
                 ("repro_us", C.c_double), ("sel_us", C.c_double)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("live", C.c_int), ("queued", C.c_int), ("finished", C.c_int),
+                ("admitted", C.c_int), ("arena_used", C.c_size_t), ("generations", C.c_longlong)]
+
+
 class RveaError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -129,5 +134,17 @@ def lib():
         L.rvea_batch_step_profiled.restype = i32
         L.rvea_batch_free.argtypes = [vp]
         L.rvea_batch_free.restype = None
+        L.rvea_server_create.argtypes = [vp, sz, i32, i32, C.POINTER(C.c_void_p)]
+        L.rvea_server_create.restype = i32
+        L.rvea_server_submit.argtypes = [vp, C.POINTER(Config), i32, C.POINTER(C.c_int64)]
+        L.rvea_server_submit.restype = i32
+        L.rvea_server_step.argtypes = [vp, vp, C.POINTER(ServerStats)]
+        L.rvea_server_step.restype = i32
+        L.rvea_server_poll.argtypes = [vp, C.POINTER(C.c_int64), i32, C.POINTER(C.c_int)]
+        L.rvea_server_poll.restype = i32
+        L.rvea_server_fetch.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
+        L.rvea_server_fetch.restype = i32
+        L.rvea_server_free.argtypes = [vp]
+        L.rvea_server_free.restype = None
         _lib = L
     return _lib

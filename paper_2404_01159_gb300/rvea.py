@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 import numpy as np
 import torch
 
-from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, NEURO_LINEAR, Config, NeuroDynamics, Plan,
+from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, NEURO_LINEAR, Config, NeuroDynamics, Plan, ServerStats,
                       RveaError, check, lib)
 
 __all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
@@ -231,6 +231,71 @@ class Batch:
     def free(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().rvea_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop with continuous batching (rvea_server_*): requests queue,
+    are admitted between steps while their workspaces fit the arena (the HBM
+    budget), and every step runs one generation of every live run."""
+
+    def __init__(self, arena_bytes: int, max_live: int = 1 << 30, autotune: bool = True,
+                 device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self._arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=self.device)
+        base = (self._arena.data_ptr() + 255) & ~255
+        h = C.c_void_p()
+        check(lib().rvea_server_create(C.c_void_p(base), int(arena_bytes), int(max_live),
+                                       int(autotune), C.byref(h)), "rvea_server_create")
+        self._h = h
+        self.meta = {}
+
+    def submit(self, m: int, d: int, N: int, H: int, problem: int, generations: int,
+               t_max: Optional[int] = None, alpha: float = 2.0, f_r: float = 0.1,
+               eta_c: float = 20.0, eta_m: float = 20.0, p_c: float = 1.0, p_m: float = 1.0,
+               seed: int = 0) -> int:
+        cfg = Config(m, d, N, H, problem, generations if t_max is None else t_max, alpha, f_r,
+                     eta_c, eta_m, p_c, p_m, 0.0, 1.0, seed & 0xFFFFFFFFFFFFFFFF, None)
+        rid = C.c_int64()
+        check(lib().rvea_server_submit(self._h, C.byref(cfg), int(generations), C.byref(rid)),
+              "rvea_server_submit")
+        self.meta[rid.value] = (m, d, N)
+        return rid.value
+
+    def step(self, stream=None) -> dict:
+        st = ServerStats()
+        check(lib().rvea_server_step(self._h, C.c_void_p(_stream(stream)), C.byref(st)),
+              "rvea_server_step")
+        return {"live": st.live, "queued": st.queued, "finished": st.finished,
+                "admitted": st.admitted, "arena_used": st.arena_used,
+                "generations": st.generations}
+
+    def poll(self, cap: int = 4096) -> list:
+        ids = (C.c_int64 * cap)()
+        n = C.c_int()
+        check(lib().rvea_server_poll(self._h, ids, cap, C.byref(n)), "rvea_server_poll")
+        return [ids[q] for q in range(n.value)]
+
+    def fetch(self, rid: int, stream=None):
+        """(X (N, d), F (N, m), valid (N,)) on the device; releases the run."""
+        m, d, N = self.meta.pop(rid)
+        X = torch.empty((N, d), dtype=torch.float32, device=self.device)
+        F = torch.empty((N, m), dtype=torch.float32, device=self.device)
+        v = torch.empty(N, dtype=torch.uint8, device=self.device)
+        check(lib().rvea_server_fetch(self._h, C.c_int64(rid), _ptr(X), _ptr(F), _ptr(v),
+                                      C.c_void_p(_stream(stream))), "rvea_server_fetch")
+        return X, F, v
+
+    def free(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rvea_server_free(self._h)
             self._h = None
 
     def __del__(self):
