@@ -95,8 +95,13 @@ typedef struct {
     const rvea_neuro_dynamics *neuro;   /* required iff problem == NEURO     */
 } rvea_config;
 
-/* Bytes of device workspace a run of this shape needs (0 if invalid). */
+/* Bytes of device workspace a run of this shape needs (0 if invalid).
+ * DTLZ problems only; the rollout problem adds its noise table and dynamics:
+ * use rvea_workspace_bytes_ex. */
 size_t rvea_workspace_bytes(int m, int d, int N);
+
+/* Bytes of device workspace the run `cfg` needs (0 if cfg is invalid). */
+size_t rvea_workspace_bytes_ex(const rvea_config *cfg);
 
 /* Create a run: builds the Das-Dennis lattice V0 (unit vectors), gamma(V0),
  * draws and evaluates the initial population (Algorithm 2, initialisation)

@@ -80,6 +80,8 @@ def lib():
         run_pp = C.POINTER(C.c_void_p)
         L.rvea_workspace_bytes.argtypes = [i32, i32, i32]
         L.rvea_workspace_bytes.restype = sz
+        L.rvea_workspace_bytes_ex.argtypes = [C.POINTER(Config)]
+        L.rvea_workspace_bytes_ex.restype = sz
         L.rvea_init.argtypes = [i32, i32, i32, i32, dbl, dbl, dbl, dbl, u64, i32, i32, vp, sz, vp, run_pp]
         L.rvea_init.restype = i32
         L.rvea_init_ex.argtypes = [C.POINTER(Config), vp, sz, vp, run_pp]

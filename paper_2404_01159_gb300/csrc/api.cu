@@ -53,6 +53,8 @@ __global__ void k_op_zstar(const RunDesc *Rp);
 __global__ void k_op_finish(const RunDesc *Rp);
 __global__ void k_select_pruned(const RunDesc *Rp);
 __global__ void k_tiles(const RunDesc *Rp);
+__global__ void k_noise(const __grid_constant__ BatchDir dir, int init);
+__global__ void k_rollout(const __grid_constant__ BatchDir dir, int init);
 __global__ void k_select_pruned_batch(const __grid_constant__ BatchDir dir);
 __global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force);
 }  // namespace rvea
@@ -86,6 +88,7 @@ struct Shape {
 constexpr int kPruneMinN = 1000;
 constexpr int kSelPerSmMax = 16;   // full scan: the finest plan (work items per SM)
 constexpr int kPruneChunkHost = 2048;   // solutions per work chunk of the batched pruned search
+constexpr int kRollPolicies = 2;        // policies (warps) per CTA of the rollout kernel
 constexpr size_t kPruneSmemCap = 200 * 1024;
 int prune_tiles_bound(int N) { return N / 16 + 2; }
 size_t prune_smem(int N, int T) {
@@ -525,6 +528,32 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       }
     }
   }
+  {
+    // evaluation of the rollout problem's children: noise of generation t,
+    // then one warp per policy
+    static thread_local BatchDir dn, dro;
+    int nn = 0, pn = 0, pro = 0;
+    for (int q = 0; q < n; ++q) {
+      const rvea_run *r = runs[q];
+      if (r->hd.problem != PROB_NEURO) continue;
+      const uint2 key = make_uint2(r->hd.key0, r->hd.key1);
+      dn.prefix[nn] = pn;
+      dro.prefix[nn] = pro;
+      dn.desc[nn] = dro.desc[nn] = r->d_desc;
+      dn.key[nn] = dro.key[nn] = key;
+      dn.items[nn] = dro.items[nn] = nullptr;
+      pn += (r->hd.steps * r->hd.ns + 255) / 256;
+      pro += (r->sh.N + kRollPolicies - 1) / kRollPolicies;
+      ++nn;
+    }
+    if (nn > 0) {
+      dn.n = dro.n = nn;
+      dn.prefix[nn] = pn;
+      dro.prefix[nn] = pro;
+      k_noise<<<pn, 256, 0, st>>>(dn, 0);
+      k_rollout<<<pro, 32 * kRollPolicies, 0, st>>>(dro, 0);
+    }
+  }
   if (ev) cudaEventRecord(ev[1], st);
   if (np > 0) {
     if (n == 1 && runs[0]->sel_mode == 1)
@@ -616,7 +645,17 @@ rvea_status validate(const rvea_config *c) {
   // mutation: up to 8 expected sites per row (the count is capped at 32), or every site
   if (c->p_m > 8.0 && c->p_m < (double)c->d) return RVEA_ERR_ARG;
   if (c->problem < 0 || c->problem > 2) return RVEA_ERR_ARG;
-  if (c->problem == RVEA_NEURO_LINEAR) return RVEA_ERR_ARG;   // rollout kernel not built here
+  if (c->problem == RVEA_NEURO_LINEAR) {
+    // the rollout's shape: h1 = h2 = 64 (the tensor-core tiling), ns <= 32
+    // (one lane per state component), na <= 16 (one 16-row tile), and d the
+    // size of the policy vector
+    const rvea_neuro_dynamics *nd = c->neuro;
+    if (!nd || !nd->A || !nd->B || nd->h1 != 64 || nd->h2 != 64 || nd->ns < 1 || nd->ns > 32 ||
+        nd->na < 1 || nd->na > 16 || nd->steps < 1 || !(nd->sigma >= 0) || c->m != 2)
+      return RVEA_ERR_ARG;
+    if (c->d != nd->h1 * nd->ns + nd->h1 + nd->h2 * nd->h1 + nd->h2 + nd->na * nd->h2 + nd->na)
+      return RVEA_ERR_ARG;
+  }
   if (c->H < 0 || lattice_size(c->m, c->H) != (int64_t)c->N) return RVEA_ERR_LATTICE;
   return RVEA_OK;
 }
@@ -627,6 +666,13 @@ rvea_status validate(const rvea_config *c) {
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
+
+size_t rvea_workspace_bytes_ex(const rvea_config *cfg) {
+  if (!cfg || validate(cfg) != RVEA_OK) return 0;
+  const Shape s = make_shape(cfg->m, cfg->d, cfg->N);
+  const rvea_neuro_dynamics *nd = cfg->problem == RVEA_NEURO_LINEAR ? cfg->neuro : nullptr;
+  return make_layout(s, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0).total;
+}
 
 size_t rvea_workspace_bytes(int m, int d, int N) {
   if (m < 2 || m > kMaxM || d < m || d > (1 << 22) || N < 2 || N > 32768) return 0;
@@ -662,7 +708,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   if (v != RVEA_OK) return v;
   if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255)) return RVEA_ERR_ARG;
   const Shape sh = make_shape(cfg->m, cfg->d, cfg->N);
-  const Layout lay = make_layout(sh, 0, 0, 0);
+  const rvea_neuro_dynamics *nd = cfg->problem == RVEA_NEURO_LINEAR ? cfg->neuro : nullptr;
+  const Layout lay = make_layout(sh, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0);
   if (bytes < lay.total) return RVEA_ERR_NOMEM;
   std::call_once(g_attr_once, set_kernel_attrs);
   if (g_attr_err != cudaSuccess) return RVEA_ERR_CUDA;
@@ -698,6 +745,16 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.key1 = (uint32_t)(cfg->seed >> 32);
   D.X = wsp<float>(r, lay.X);
   D.F = wsp<float>(r, lay.F);
+  std::vector<float> dynA, dynB;
+  if (nd) {
+    D.ns = nd->ns; D.na = nd->na; D.h1 = nd->h1; D.h2 = nd->h2; D.steps = nd->steps;
+    D.sigma = (float)nd->sigma;
+    D.noise = wsp<float>(r, lay.noise);
+    D.dynA = wsp<float>(r, lay.dynA);
+    D.dynB = wsp<float>(r, lay.dynB);
+    dynA.assign(nd->A, nd->A + (size_t)nd->ns * nd->ns);
+    dynB.assign(nd->B, nd->B + (size_t)nd->ns * nd->na);
+  }
   D.slotmap = wsp<int>(r, lay.slotmap);
   D.vbits = wsp<uint32_t>(r, lay.vbits);
   D.obits = wsp<uint32_t>(r, lay.obits);
@@ -777,6 +834,10 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.V32, V32.data(), V32.size() * 4);
   up(lay.V32lo, V32lo.data(), V32lo.size() * 4);
   up(lay.ctl, &c0, sizeof(c0));
+  if (nd) {
+    up(lay.dynA, dynA.data(), dynA.size() * 4);
+    up(lay.dynB, dynB.data(), dynB.size() * 4);
+  }
   if (D.ntiles > 0) {
     up(lay.tperm, tperm.data(), tperm.size() * 4);
     up(lay.trng, trng.data(), trng.size() * sizeof(int2));
@@ -785,6 +846,12 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     static thread_local BatchDir d;
     dir_single(d, r, wsp<ReproItem>(r, lay.init), sh.n_init);
     k_init<<<sh.n_init, kReproThreads, r->init_smem, st>>>(d);
+    if (nd) {   // the initial population's rollouts (noise of t = 0)
+      dir_single(d, r, nullptr, (nd->steps * nd->ns + 255) / 256);
+      k_noise<<<(nd->steps * nd->ns + 255) / 256, 256, 0, st>>>(d, 1);
+      dir_single(d, r, nullptr, (sh.N + kRollPolicies - 1) / kRollPolicies);
+      k_rollout<<<(sh.N + kRollPolicies - 1) / kRollPolicies, 32 * kRollPolicies, 0, st>>>(d, 1);
+    }
     dir_single(d, r, nullptr, 1);
     k_init_lists<<<dim3((sh.N + 255) / 256, 1), 256, 0, st>>>(d);
     s = cuerr(cudaGetLastError());
@@ -1155,7 +1222,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   dir_single(ds, one, wsp<SelItem>(r, r->lay.sel), r->n_sel);
   dir_single(df, one, nullptr, 1);
   dir_single(dg, one, nullptr, 1);
-  static thread_local BatchDir dpb;
+  static thread_local BatchDir dpb, dn1, dro1;
   dir_single(dpb, one, nullptr, (r->sh.n_comb + kPruneChunkHost - 1) / kPruneChunkHost);
   const int nbd = (r->sh.N + 1023) / 1024;
   dir_single(dd, one, nullptr, nbd);
@@ -1164,6 +1231,14 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     cudaEvent_t *e = &ev[(size_t)g * 5];
     cudaEventRecord(e[0], st);
     launch_repro1(r, dr, r->sh.n_repro, st);
+    if (r->hd.problem == PROB_NEURO) {
+      const int nb_noise = (r->hd.steps * r->hd.ns + 255) / 256;
+      const int nb_roll = (r->sh.N + kRollPolicies - 1) / kRollPolicies;
+      dir_single(dn1, one, nullptr, nb_noise);
+      dir_single(dro1, one, nullptr, nb_roll);
+      k_noise<<<nb_noise, 256, 0, st>>>(dn1, 0);
+      k_rollout<<<nb_roll, 32 * kRollPolicies, 0, st>>>(dro1, 0);
+    }
     cudaEventRecord(e[1], st);
     if (r->sel_mode == 1)
       k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);

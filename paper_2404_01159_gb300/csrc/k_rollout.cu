@@ -1,0 +1,267 @@
+// Neuroevolution objective: the synthetic linear-dynamics rollout of every
+// policy (the stand-in for the paper's Brax control tasks, Sec. 4.3).
+//
+// Policy x = [W1 (h1 x ns), b1, W2 (h2 x h1), b2, W3 (na x h2), b3] with
+// h1 = h2 = 64, ns <= 32, na <= 16; tanh on every layer; s_0 = 0,
+// s_{tau+1} = A s_tau + B u_tau + sigma xi_tau for tau < steps;
+// f1 = -sum_tau s_{tau+1}[0], f2 = sum_tau |u_tau|^2.  xi_tau[k] is one
+// Box-Muller draw from Philox NOISE (k, tau, t), shared by every policy of
+// generation t (common random numbers); t = 0 for the initial population.
+//
+// One warp runs one policy for all steps.  The three layers are GEMVs with a
+// different matrix per policy, so they run on the tensor cores as
+// mma.sync m16n8k16 (BF16 operands, FP32 accumulate) with the weights as the
+// A operand and the activation vector as column 0 of B: one column of the
+// eight is used, the price of a matrix-vector product on an MMA tile.
+// A rollout of 1000 steps amplifies rounding: one BF16 pass misses 1e-2 on
+// the objectives of sensitive policies, so every product is taken in three
+// BF16 passes over a hi/lo split of both operands (w = w_hi + w_lo,
+// v = v_hi + v_lo; W v ~ W_hi v_hi + W_lo v_hi + W_hi v_lo, FP32 accumulate),
+// which leaves errors near FP32 level.  The hi fragments of the weights stay
+// in registers for the whole rollout (W1 padded to K = 32, W3 to M = 16: 112
+// registers a lane), the lo fragments in shared memory (lane-major, one
+// 16-byte load per tile); biases ride in the accumulator initialisers.
+// Between layers the column-0 outputs (lanes 4i hold rows i and i + 8 of each
+// 16-row tile) are split, packed to BF16 pairs and moved to the B fragments
+// of the next layer with four shuffles per 16-row tile.  The dynamics stay in
+// FP32 on the CUDA cores (lane k owns state component k; A, B rows in shared
+// memory).
+#include "rvea_device.cuh"
+
+namespace rvea {
+
+constexpr int kRollWarps = 2;      // policies per CTA (static shared memory < 48 KB)
+constexpr int kRollNsMax = 32;     // state components (one per lane)
+constexpr int kRollNaMax = 16;     // actions (one 16-row tile)
+constexpr int kRollH = 64;         // hidden units of both hidden layers
+constexpr int kRollTiles = 28;     // 16x16 weight tiles: W1 4x2, W2 4x4, W3 1x4
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// D = A (16x16, row) * B (16x8, col) + C, BF16 inputs, FP32 accumulate.
+__device__ __forceinline__ void mma16816(float &d0, float &d1, float &d2, float &d3,
+                                         const uint32_t *a, uint32_t b0, uint32_t b1, float c0,
+                                         float c1, float c2, float c3) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%11,%12,%13};"
+      : "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1),
+        "f"(c2), "f"(c3));
+}
+
+__device__ __forceinline__ float bf16_lo(float v) {   // v - bf16(v), exact in float
+  uint32_t p;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(0.0f), "f"(v));
+  return v - __uint_as_float(p << 16);
+}
+
+// BF16 pair (hi, lo split) of two floats: hi = bf16(a), bf16(b); lo = the
+// rounded remainders.
+__device__ __forceinline__ void split_pack(float a, float b, uint32_t &hi, uint32_t &lo) {
+  hi = pack_bf16x2(a, b);
+  lo = pack_bf16x2(bf16_lo(a), bf16_lo(b));
+}
+
+// A fragments (hi and lo) of the 16x16 tile (mt, kt) of a row-major matrix
+// W (Mv x Kv, zero outside): lane (g = lane/4, q = lane%4) holds rows g, g+8
+// and columns 2q, 2q+1, 2q+8, 2q+9 of the tile.
+__device__ __forceinline__ void load_afrag(uint32_t *a, uint4 *lo, const float *W, int Mv, int Kv,
+                                           int mt, int kt, int lane) {
+  const int g = lane >> 2, q = lane & 3;
+  const int r0 = mt * 16 + g, r1 = r0 + 8, c0 = kt * 16 + 2 * q, c1 = c0 + 8;
+  auto at = [&](int r, int c) { return (r < Mv && c < Kv) ? __ldg(W + (size_t)r * Kv + c) : 0.0f; };
+  uint4 l;
+  split_pack(at(r0, c0), at(r0, c0 + 1), a[0], l.x);
+  split_pack(at(r1, c0), at(r1, c0 + 1), a[1], l.y);
+  split_pack(at(r0, c1), at(r0, c1 + 1), a[2], l.z);
+  split_pack(at(r1, c1), at(r1, c1 + 1), a[3], l.w);
+  *lo = l;
+}
+
+// Three-pass product of one tile: d += A_hi B_hi + A_lo B_hi + A_hi B_lo.
+__device__ __forceinline__ void mma3(float *d, const uint32_t *ah, const uint4 &al, uint32_t bh0,
+                                     uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  const uint32_t a_lo[4] = {al.x, al.y, al.z, al.w};
+  mma16816(d[0], d[1], d[2], d[3], ah, bh0, bh1, d[0], d[1], d[2], d[3]);
+  mma16816(d[0], d[1], d[2], d[3], a_lo, bh0, bh1, d[0], d[1], d[2], d[3]);
+  mma16816(d[0], d[1], d[2], d[3], ah, bl0, bl1, d[0], d[1], d[2], d[3]);
+}
+
+// Column 0 of a 16-row output tile (lanes 4i: c0 = row i, c2 = row i+8),
+// after tanh, as the B fragments, hi and lo (rows 16t..16t+15 of the next
+// input), of lanes 0..3; other lanes receive values of unused columns.
+__device__ __forceinline__ void tile_to_b(float c0, float c2, int lane, uint32_t *b) {
+  uint32_t ph, pl;
+  split_pack(tanh_approx(c0), tanh_approx(c2), ph, pl);
+  const int q = lane & 3;
+  const uint32_t xh = __shfl_sync(0xffffffffu, ph, 8 * q), yh = __shfl_sync(0xffffffffu, ph, 8 * q + 4);
+  const uint32_t xl = __shfl_sync(0xffffffffu, pl, 8 * q), yl = __shfl_sync(0xffffffffu, pl, 8 * q + 4);
+  b[0] = __byte_perm(xh, yh, 0x5410);   // hi, rows 2q, 2q+1
+  b[1] = __byte_perm(xh, yh, 0x7632);   // hi, rows 2q+8, 2q+9
+  b[2] = __byte_perm(xl, yl, 0x5410);   // lo
+  b[3] = __byte_perm(xl, yl, 0x7632);
+}
+
+// Noise table of generation t for each run of the directory:
+// noise[tau][k] = xi_tau[k], Box-Muller from Philox NOISE (k, tau, t) with
+// u1 = 1 - u24(word 0) in (0, 1] and u2 = u24(word 1).  One thread per entry;
+// dir.prefix counts CTAs of 256 entries.
+__global__ void k_noise(const __grid_constant__ BatchDir dir, int init) {
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int e = (blockIdx.x - dir.prefix[run]) * blockDim.x + threadIdx.x;
+  if (e >= R.steps * R.ns) return;
+  const int tau = e / R.ns, k = e - tau * R.ns;
+  const int t = init ? 0 : R.ctl->t;
+  const uint4 w = philox((uint32_t)k, (uint32_t)tau, (uint32_t)t, TAG_NOISE, dir.key[run].x,
+                         dir.key[run].y);
+  const float u1 = 1.0f - u24f(w.x), u2 = u24f(w.y);
+  R.noise[e] = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// Rollouts of a directory of runs: dir.prefix counts CTAs of kRollWarps
+// policies.  init: the initial population (rows 0..N-1, noise of t = 0);
+// otherwise the N children of generation t (rows child_slot[t & 1]).
+__global__ void __launch_bounds__(kRollWarps * 32)
+k_rollout(const __grid_constant__ BatchDir dir, int init) {
+  __shared__ float sA[kRollNsMax * kRollNsMax], sB[kRollNsMax * kRollNaMax];
+  __shared__ uint4 sLo[kRollWarps * kRollTiles * 32];   // lo weight fragments, per warp
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ns = R.ns, na = R.na, steps = R.steps, N = R.N;
+  for (int e = threadIdx.x; e < ns * ns; e += blockDim.x) sA[e] = R.dynA[e];
+  for (int e = threadIdx.x; e < ns * na; e += blockDim.x) sB[e] = R.dynB[e];
+  __syncthreads();
+  const int c = (blockIdx.x - dir.prefix[run]) * kRollWarps + warp;
+  if (c >= N) return;
+  const int t = R.ctl->t;
+  int slot = c;
+  if (!init) slot = R.child_slot[(t & 1) * N + c];
+  if (slot < 0 || slot >= 2 * N) {
+    if (lane == 0) set_status(R.ctl, ST_BADINDEX);
+    return;
+  }
+  const float *x = R.X + (size_t)slot * R.d_pad;
+  const float *W1 = x, *b1 = W1 + kRollH * ns, *W2 = b1 + kRollH, *b2 = W2 + kRollH * kRollH;
+  const float *W3 = b2 + kRollH, *b3 = W3 + na * kRollH;
+  // weights as BF16 A fragments for the whole rollout: hi in registers, lo
+  // in this warp's shared-memory slab (tile-major, lane-minor)
+  uint4 *const slo = sLo + warp * (kRollTiles * 32);
+  uint32_t a1[4][2][4], a2[4][4][4], a3[4][4];
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt) {
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt)
+      load_afrag(a1[mt][kt], slo + (mt * 2 + kt) * 32 + lane, W1, kRollH, ns, mt, kt, lane);
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt)
+      load_afrag(a2[mt][kt], slo + (8 + mt * 4 + kt) * 32 + lane, W2, kRollH, kRollH, mt, kt, lane);
+  }
+#pragma unroll
+  for (int kt = 0; kt < 4; ++kt) load_afrag(a3[kt], slo + (24 + kt) * 32 + lane, W3, na, kRollH, 0, kt, lane);
+  __syncwarp();
+  // biases in the accumulator layout (rows g, g+8 of each tile)
+  const int g = lane >> 2;
+  float bb1[4][2], bb2[4][2], bb3[2];
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt) {
+    bb1[mt][0] = __ldg(b1 + mt * 16 + g);
+    bb1[mt][1] = __ldg(b1 + mt * 16 + g + 8);
+    bb2[mt][0] = __ldg(b2 + mt * 16 + g);
+    bb2[mt][1] = __ldg(b2 + mt * 16 + g + 8);
+  }
+  bb3[0] = g < na ? __ldg(b3 + g) : 0.0f;
+  bb3[1] = g + 8 < na ? __ldg(b3 + g + 8) : 0.0f;
+
+  const float sigma = R.sigma;
+  const float *xi = R.noise;
+  const int q = lane & 3;
+  float s = 0.0f;              // lane k < ns: s[k]; other lanes 0
+  float f1 = 0.0f, f2 = 0.0f;
+#pragma unroll 1
+  for (int tau = 0; tau < steps; ++tau) {
+    // layer 1: K = ns padded to 32 (lanes >= ns hold s = 0)
+    uint32_t bk[4][4];
+    {
+      const float v0 = __shfl_sync(0xffffffffu, s, 2 * q), v1 = __shfl_sync(0xffffffffu, s, 2 * q + 1);
+      const float v2 = __shfl_sync(0xffffffffu, s, 2 * q + 8), v3 = __shfl_sync(0xffffffffu, s, 2 * q + 9);
+      const float v4 = __shfl_sync(0xffffffffu, s, 2 * q + 16), v5 = __shfl_sync(0xffffffffu, s, 2 * q + 17);
+      const float v6 = __shfl_sync(0xffffffffu, s, 2 * q + 24), v7 = __shfl_sync(0xffffffffu, s, 2 * q + 25);
+      split_pack(v0, v1, bk[0][0], bk[0][2]);
+      split_pack(v2, v3, bk[0][1], bk[0][3]);
+      split_pack(v4, v5, bk[1][0], bk[1][2]);
+      split_pack(v6, v7, bk[1][1], bk[1][3]);
+    }
+    float h[4][4];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+      h[mt][0] = h[mt][1] = bb1[mt][0];
+      h[mt][2] = h[mt][3] = bb1[mt][1];
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt)
+        mma3(h[mt], a1[mt][kt], slo[(mt * 2 + kt) * 32 + lane], bk[kt][0], bk[kt][1], bk[kt][2],
+             bk[kt][3]);
+    }
+    // layer 2
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) tile_to_b(h[kt][0], h[kt][2], lane, bk[kt]);
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+      h[mt][0] = h[mt][1] = bb2[mt][0];
+      h[mt][2] = h[mt][3] = bb2[mt][1];
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt)
+        mma3(h[mt], a2[mt][kt], slo[(8 + mt * 4 + kt) * 32 + lane], bk[kt][0], bk[kt][1],
+             bk[kt][2], bk[kt][3]);
+    }
+    // layer 3 (one 16-row tile, rows < na used)
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) tile_to_b(h[kt][0], h[kt][2], lane, bk[kt]);
+    float o[4] = {bb3[0], bb3[0], bb3[1], bb3[1]};
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt)
+      mma3(o, a3[kt], slo[(24 + kt) * 32 + lane], bk[kt][0], bk[kt][1], bk[kt][2], bk[kt][3]);
+    // u_o = tanh(row o of column 0): lane 4o (o < 8) holds rows o and o + 8
+    const float ulo = tanh_approx(o[0]), uhi = tanh_approx(o[2]);
+    if (q == 0) {
+      if (g < na) f2 = fmaf(ulo, ulo, f2);
+      if (g + 8 < na) f2 = fmaf(uhi, uhi, f2);
+    }
+    // dynamics in FP32: lane k computes s'[k]
+    float z = 0.0f;
+    const float *Ar = sA + lane * ns, *Br = sB + lane * na;
+    for (int i = 0; i < ns; ++i) {
+      const float si = __shfl_sync(0xffffffffu, s, i);
+      if (lane < ns) z = fmaf(Ar[i], si, z);
+    }
+    for (int oo = 0; oo < na; ++oo) {
+      const float uo = __shfl_sync(0xffffffffu, oo < 8 ? ulo : uhi, 4 * (oo & 7));
+      if (lane < ns) z = fmaf(Br[oo], uo, z);
+    }
+    s = lane < ns ? fmaf(sigma, __ldg(xi + (size_t)tau * ns + lane), z) : 0.0f;
+    f1 -= __shfl_sync(0xffffffffu, s, 0);
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, off);
+  if (lane == 0) {
+    const int n2 = 2 * N;
+    R.F[slot] = f1;
+    R.F[(size_t)n2 + slot] = f2;
+    atomicMin(&R.ctl->zkey[0], f2ord(f1));
+    atomicMin(&R.ctl->zkey[1], f2ord(f2));
+  }
+}
+
+}  // namespace rvea

@@ -56,14 +56,6 @@ class Run:
         self.m, self.d, self.N, self.H = m, d, N, H
         self.problem, self.t_max = problem, t_max
         L = lib()
-        nbytes = int(L.rvea_workspace_bytes(m, d, N))
-        if nbytes == 0:
-            raise RveaError(-1, "rvea_workspace_bytes")
-        with torch.cuda.device(self.device):
-            self._ws_raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
-        base = self._ws_raw.data_ptr()
-        self._ws_ptr = (base + 255) & ~255
-        self.workspace_nbytes = nbytes
         cfg = Config(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
                      lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None)
         self._neuro_keep = None
@@ -76,6 +68,14 @@ class Run:
                                B.ctypes.data_as(C.POINTER(C.c_double)))
             self._neuro_keep = (A, B, nd)
             cfg.neuro = C.pointer(nd)
+        nbytes = int(L.rvea_workspace_bytes_ex(C.byref(cfg)))
+        if nbytes == 0:
+            raise RveaError(-1, "rvea_workspace_bytes_ex: invalid configuration")
+        with torch.cuda.device(self.device):
+            self._ws_raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self.workspace_nbytes = nbytes
         self._h = C.c_void_p()
         with torch.cuda.device(self.device):
             check(L.rvea_init_ex(C.byref(cfg), C.c_void_p(self._ws_ptr), nbytes,

@@ -86,3 +86,20 @@ def request_stream(rate_per_s: float = 200.0, duration_s: float = 60.0,
             return out
         out.append((t, instance(1_000_000 + seed * 100_000 + s)))
         s += 1
+
+
+def neuro_dynamics(seed: int = 0, ns: int = 17, na: int = 6, steps: int = 1000,
+                   sigma: float = 0.01) -> dict:
+    """Synthetic linear dynamics of the neuroevolution workload: A (ns x ns)
+    Gaussian scaled to spectral radius 0.95 (eigenvalues in FP64), B (ns x na)
+    Gaussian; process noise N(0, sigma^2)."""
+    rng = np.random.default_rng([0xD1A, seed])
+    A = rng.normal(size=(ns, ns))
+    A *= 0.95 / float(np.max(np.abs(np.linalg.eigvals(A))))
+    B = rng.normal(size=(ns, na))
+    return {"A": A, "B": B, "steps": steps, "sigma": sigma, "h1": 64, "h2": 64}
+
+
+def policy_size(ns: int = 17, na: int = 6, h1: int = 64, h2: int = 64) -> int:
+    """d of an MLP policy ns -> h1 -> h2 -> na with biases."""
+    return h1 * ns + h1 + h2 * h1 + h2 + na * h2 + na

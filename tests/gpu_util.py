@@ -1,6 +1,7 @@
 """Shared helpers of the GPU parity tests (comparison rules and run set-up).
 
 Tolerances (stated once, used everywhere):
+  * rollout objectives (BF16 policy GEMMs): 1e-2 of max(|f|, median |f_k|);
   * random words, masks, mating indices, lattice, initial population: exact;
   * decision variables: |x_gpu - x_orc| <= 1e-5 (U - L)   (float32 SBX/PM);
   * objectives: |f_gpu - f_orc| <= 1e-5 ||f_orc||_2 per row (relative to the
@@ -53,6 +54,22 @@ def assert_objectives(gf, of, rtol=F_RTOL):
     err = np.abs(gf - of)
     bad = err > rtol * scale + 1e-30
     assert not bad.any(), (int(bad.sum()), float((err / (scale + 1e-300)).max()))
+
+
+ROLL_RTOL = 1e-2
+
+
+def assert_rollout_objectives(gf, of, rtol=ROLL_RTOL):
+    """Rollout objectives (BF16 policy GEMMs, FP32 accumulate) against the
+    FP64 oracle: |f_gpu - f_orc| <= rtol max(|f_orc|, s_k), s_k the median
+    |f_k| of the population (f1 = -sum s[0] can pass near zero, where a
+    relative bound carries no meaning)."""
+    gf = np.asarray(gf, dtype=np.float64)
+    scale = np.maximum(np.abs(of), np.median(np.abs(of), axis=0, keepdims=True))
+    err = np.abs(gf - of)
+    bad = err > rtol * scale
+    assert not bad.any(), (int(bad.sum()), float((err / scale).max()))
+    return float((err / scale).max())
 
 
 def assert_gamma(g, o):
