@@ -14,16 +14,17 @@
 // A operand and the activation vector as column 0 of B: one column of the
 // eight is used, the price of a matrix-vector product on an MMA tile.
 // A rollout of 1000 steps amplifies rounding: one BF16 pass misses 1e-2 on
-// the objectives of sensitive policies, so every product is taken in three
-// BF16 passes over a hi/lo split of both operands (w = w_hi + w_lo,
-// v = v_hi + v_lo; W v ~ W_hi v_hi + W_lo v_hi + W_hi v_lo, FP32 accumulate),
-// which leaves errors near FP32 level.  The hi fragments of the weights stay
+// the objectives of sensitive policies, so both operands are split into BF16
+// hi and lo parts (w = w_hi + w_lo, v = v_hi + v_lo) and every product takes
+// two MMAs: B carries v_hi in column 0 and v_lo in column 1, so
+// A_hi B + A_lo B accumulates W v_hi in column 0 and W v_lo in column 1, and
+// their sum is W v with errors near FP32 level (FP32 accumulate).  The hi fragments of the weights stay
 // in registers for the whole rollout (W1 padded to K = 32, W3 to M = 16: 112
 // registers a lane), the lo fragments in shared memory (lane-major, one
 // 16-byte load per tile); biases ride in the accumulator initialisers.
-// Between layers the column-0 outputs (lanes 4i hold rows i and i + 8 of each
-// 16-row tile) are split, packed to BF16 pairs and moved to the B fragments
-// of the next layer with four shuffles per 16-row tile.  The dynamics stay in
+// Between layers the outputs (lanes 4i hold rows i and i + 8 of each 16-row
+// tile, columns 0 and 1 summed) are split, packed to BF16 pairs and moved to
+// the B fragments of the next layer with four shuffles per 16-row tile.  The dynamics stay in
 // FP32 on the CUDA cores (lane k owns state component k; A, B rows in shared
 // memory).
 #include "rvea_device.cuh"
@@ -60,17 +61,11 @@ __device__ __forceinline__ void mma16816(float &d0, float &d1, float &d2, float 
         "f"(c2), "f"(c3));
 }
 
-__device__ __forceinline__ float bf16_lo(float v) {   // v - bf16(v), exact in float
-  uint32_t p;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(0.0f), "f"(v));
-  return v - __uint_as_float(p << 16);
-}
-
 // BF16 pair (hi, lo split) of two floats: hi = bf16(a), bf16(b); lo = the
-// rounded remainders.
+// rounded remainders a - hi_a, b - hi_b (exact in float).
 __device__ __forceinline__ void split_pack(float a, float b, uint32_t &hi, uint32_t &lo) {
   hi = pack_bf16x2(a, b);
-  lo = pack_bf16x2(bf16_lo(a), bf16_lo(b));
+  lo = pack_bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xFFFF0000u));
 }
 
 // A fragments (hi and lo) of the 16x16 tile (mt, kt) of a row-major matrix
@@ -89,28 +84,28 @@ __device__ __forceinline__ void load_afrag(uint32_t *a, uint4 *lo, const float *
   *lo = l;
 }
 
-// Three-pass product of one tile: d += A_hi B_hi + A_lo B_hi + A_hi B_lo.
-__device__ __forceinline__ void mma3(float *d, const uint32_t *ah, const uint4 &al, uint32_t bh0,
-                                     uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+// Two-pass product of one tile: d += A_hi B + A_lo B, B = [v_hi | v_lo | ...].
+__device__ __forceinline__ void mma2(float *d, const uint32_t *ah, const uint4 &al, uint32_t b0,
+                                     uint32_t b1) {
   const uint32_t a_lo[4] = {al.x, al.y, al.z, al.w};
-  mma16816(d[0], d[1], d[2], d[3], ah, bh0, bh1, d[0], d[1], d[2], d[3]);
-  mma16816(d[0], d[1], d[2], d[3], a_lo, bh0, bh1, d[0], d[1], d[2], d[3]);
-  mma16816(d[0], d[1], d[2], d[3], ah, bl0, bl1, d[0], d[1], d[2], d[3]);
+  mma16816(d[0], d[1], d[2], d[3], ah, b0, b1, d[0], d[1], d[2], d[3]);
+  mma16816(d[0], d[1], d[2], d[3], a_lo, b0, b1, d[0], d[1], d[2], d[3]);
 }
 
-// Column 0 of a 16-row output tile (lanes 4i: c0 = row i, c2 = row i+8),
-// after tanh, as the B fragments, hi and lo (rows 16t..16t+15 of the next
-// input), of lanes 0..3; other lanes receive values of unused columns.
-__device__ __forceinline__ void tile_to_b(float c0, float c2, int lane, uint32_t *b) {
+// Rows r (c0 + c1: columns 0 and 1 summed) and r + 8 (c2 + c3) of a 16-row
+// output tile, held by lanes 4i, after tanh, as the B fragment of the next
+// layer (rows 16t..16t+15 of its input): the hi parts in column 0 (lanes
+// 0..3), the lo parts in column 1 (lanes 4..7); other lanes receive values
+// of unused columns.
+__device__ __forceinline__ void tile_to_b(float v0, float v8, int lane, uint32_t *b) {
   uint32_t ph, pl;
-  split_pack(tanh_approx(c0), tanh_approx(c2), ph, pl);
+  split_pack(tanh_approx(v0), tanh_approx(v8), ph, pl);
   const int q = lane & 3;
   const uint32_t xh = __shfl_sync(0xffffffffu, ph, 8 * q), yh = __shfl_sync(0xffffffffu, ph, 8 * q + 4);
   const uint32_t xl = __shfl_sync(0xffffffffu, pl, 8 * q), yl = __shfl_sync(0xffffffffu, pl, 8 * q + 4);
-  b[0] = __byte_perm(xh, yh, 0x5410);   // hi, rows 2q, 2q+1
-  b[1] = __byte_perm(xh, yh, 0x7632);   // hi, rows 2q+8, 2q+9
-  b[2] = __byte_perm(xl, yl, 0x5410);   // lo
-  b[3] = __byte_perm(xl, yl, 0x7632);
+  const bool hi = lane < 4;
+  b[0] = hi ? __byte_perm(xh, yh, 0x5410) : __byte_perm(xl, yl, 0x5410);   // rows 2q, 2q+1
+  b[1] = hi ? __byte_perm(xh, yh, 0x7632) : __byte_perm(xl, yl, 0x7632);   // rows 2q+8, 2q+9
 }
 
 // Noise table of generation t for each run of the directory:
@@ -193,64 +188,79 @@ k_rollout(const __grid_constant__ BatchDir dir, int init) {
 #pragma unroll 1
   for (int tau = 0; tau < steps; ++tau) {
     // layer 1: K = ns padded to 32 (lanes >= ns hold s = 0)
-    uint32_t bk[4][4];
+    uint32_t bk[4][2];
     {
       const float v0 = __shfl_sync(0xffffffffu, s, 2 * q), v1 = __shfl_sync(0xffffffffu, s, 2 * q + 1);
       const float v2 = __shfl_sync(0xffffffffu, s, 2 * q + 8), v3 = __shfl_sync(0xffffffffu, s, 2 * q + 9);
       const float v4 = __shfl_sync(0xffffffffu, s, 2 * q + 16), v5 = __shfl_sync(0xffffffffu, s, 2 * q + 17);
       const float v6 = __shfl_sync(0xffffffffu, s, 2 * q + 24), v7 = __shfl_sync(0xffffffffu, s, 2 * q + 25);
-      split_pack(v0, v1, bk[0][0], bk[0][2]);
-      split_pack(v2, v3, bk[0][1], bk[0][3]);
-      split_pack(v4, v5, bk[1][0], bk[1][2]);
-      split_pack(v6, v7, bk[1][1], bk[1][3]);
+      uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+      split_pack(v0, v1, h0, l0);
+      split_pack(v2, v3, h1, l1);
+      split_pack(v4, v5, h2, l2);
+      split_pack(v6, v7, h3, l3);
+      const bool hi = lane < 4;   // column 0: hi parts, column 1: lo parts
+      bk[0][0] = hi ? h0 : l0;
+      bk[0][1] = hi ? h1 : l1;
+      bk[1][0] = hi ? h2 : l2;
+      bk[1][1] = hi ? h3 : l3;
     }
     float h[4][4];
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {
-      h[mt][0] = h[mt][1] = bb1[mt][0];
-      h[mt][2] = h[mt][3] = bb1[mt][1];
+      h[mt][0] = bb1[mt][0];
+      h[mt][2] = bb1[mt][1];
+      h[mt][1] = h[mt][3] = 0.0f;
 #pragma unroll
       for (int kt = 0; kt < 2; ++kt)
-        mma3(h[mt], a1[mt][kt], slo[(mt * 2 + kt) * 32 + lane], bk[kt][0], bk[kt][1], bk[kt][2],
-             bk[kt][3]);
+        mma2(h[mt], a1[mt][kt], slo[(mt * 2 + kt) * 32 + lane], bk[kt][0], bk[kt][1]);
     }
     // layer 2
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) tile_to_b(h[kt][0], h[kt][2], lane, bk[kt]);
+    for (int kt = 0; kt < 4; ++kt) tile_to_b(h[kt][0] + h[kt][1], h[kt][2] + h[kt][3], lane, bk[kt]);
 #pragma unroll
-    for (int mt = 0; mt < 4; ++mt) {
-      h[mt][0] = h[mt][1] = bb2[mt][0];
-      h[mt][2] = h[mt][3] = bb2[mt][1];
+    for (int mt = 0; mt < 4; ++mt) {   // two accumulation chains per tile (k-tiles 0-1, 2-3)
+      float g2[4] = {0.f, 0.f, 0.f, 0.f};
+      h[mt][0] = bb2[mt][0];
+      h[mt][2] = bb2[mt][1];
+      h[mt][1] = h[mt][3] = 0.0f;
+      mma2(h[mt], a2[mt][0], slo[(8 + mt * 4 + 0) * 32 + lane], bk[0][0], bk[0][1]);
+      mma2(g2, a2[mt][2], slo[(8 + mt * 4 + 2) * 32 + lane], bk[2][0], bk[2][1]);
+      mma2(h[mt], a2[mt][1], slo[(8 + mt * 4 + 1) * 32 + lane], bk[1][0], bk[1][1]);
+      mma2(g2, a2[mt][3], slo[(8 + mt * 4 + 3) * 32 + lane], bk[3][0], bk[3][1]);
 #pragma unroll
-      for (int kt = 0; kt < 4; ++kt)
-        mma3(h[mt], a2[mt][kt], slo[(8 + mt * 4 + kt) * 32 + lane], bk[kt][0], bk[kt][1],
-             bk[kt][2], bk[kt][3]);
+      for (int e = 0; e < 4; ++e) h[mt][e] += g2[e];
     }
     // layer 3 (one 16-row tile, rows < na used)
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt) tile_to_b(h[kt][0], h[kt][2], lane, bk[kt]);
-    float o[4] = {bb3[0], bb3[0], bb3[1], bb3[1]};
+    for (int kt = 0; kt < 4; ++kt) tile_to_b(h[kt][0] + h[kt][1], h[kt][2] + h[kt][3], lane, bk[kt]);
+    // four independent accumulation chains (one per k-tile), summed after
+    float o[4] = {bb3[0], 0.0f, bb3[1], 0.0f}, o1[4] = {0.f, 0.f, 0.f, 0.f};
+    float o2[4] = {0.f, 0.f, 0.f, 0.f}, o3[4] = {0.f, 0.f, 0.f, 0.f};
+    mma2(o, a3[0], slo[24 * 32 + lane], bk[0][0], bk[0][1]);
+    mma2(o1, a3[1], slo[25 * 32 + lane], bk[1][0], bk[1][1]);
+    mma2(o2, a3[2], slo[26 * 32 + lane], bk[2][0], bk[2][1]);
+    mma2(o3, a3[3], slo[27 * 32 + lane], bk[3][0], bk[3][1]);
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt)
-      mma3(o, a3[kt], slo[(24 + kt) * 32 + lane], bk[kt][0], bk[kt][1], bk[kt][2], bk[kt][3]);
-    // u_o = tanh(row o of column 0): lane 4o (o < 8) holds rows o and o + 8
-    const float ulo = tanh_approx(o[0]), uhi = tanh_approx(o[2]);
+    for (int e = 0; e < 4; ++e) o[e] += (o1[e] + o2[e]) + o3[e];
+    // u_o = tanh(row o): lane 4o (o < 8) holds rows o and o + 8
+    const float ulo = tanh_approx(o[0] + o[1]), uhi = tanh_approx(o[2] + o[3]);
     if (q == 0) {
       if (g < na) f2 = fmaf(ulo, ulo, f2);
       if (g + 8 < na) f2 = fmaf(uhi, uhi, f2);
     }
     // dynamics in FP32: lane k computes s'[k]
-    float z = 0.0f;
+    float za = 0.0f, zb = 0.0f;   // two chains: A s and B u
     const float *Ar = sA + lane * ns, *Br = sB + lane * na;
     for (int i = 0; i < ns; ++i) {
       const float si = __shfl_sync(0xffffffffu, s, i);
-      if (lane < ns) z = fmaf(Ar[i], si, z);
+      if (lane < ns) za = fmaf(Ar[i], si, za);
     }
     for (int oo = 0; oo < na; ++oo) {
       const float uo = __shfl_sync(0xffffffffu, oo < 8 ? ulo : uhi, 4 * (oo & 7));
-      if (lane < ns) z = fmaf(Br[oo], uo, z);
+      if (lane < ns) zb = fmaf(Br[oo], uo, zb);
     }
-    s = lane < ns ? fmaf(sigma, __ldg(xi + (size_t)tau * ns + lane), z) : 0.0f;
+    s = lane < ns ? fmaf(sigma, __ldg(xi + (size_t)tau * ns + lane), za + zb) : 0.0f;
     f1 -= __shfl_sync(0xffffffffu, s, 0);
   }
 #pragma unroll
