@@ -86,6 +86,7 @@ struct Shape {
 // Pruned selection: m <= 4 and the tile-ordered vectors plus the tile table
 // fit one CTA's shared memory (about 12k vectors).
 constexpr int kPruneMinN = 1000;
+constexpr int kTileLeaf = 64;      // vectors per k-d tile of the pruned search (<= 64)
 constexpr int kSelPerSmMax = 16;   // full scan: the finest plan (work items per SM)
 constexpr int kPruneChunkHost = 2048;   // solutions per work chunk of the batched pruned search
 constexpr int kRollPolicies = 2;        // policies (warps) per CTA of the rollout kernel
@@ -238,7 +239,7 @@ void build_tiles(const std::vector<double> &V0, int N, int m, std::vector<int> &
     const auto [a, b] = todo.back();
     todo.pop_back();
     const int n = b - a;
-    if (n <= 32) {
+    if (n <= kTileLeaf) {
       rng.push_back(make_int2(a, n));
       continue;
     }
@@ -257,7 +258,7 @@ void build_tiles(const std::vector<double> &V0, int N, int m, std::vector<int> &
       return V0[(size_t)x * m + axis] < V0[(size_t)y * m + axis];
     });
     int h = n / 2;
-    if (n > 64) h = std::max(32, h / 32 * 32);
+    if (n > 2 * kTileLeaf) h = std::max(kTileLeaf, h / kTileLeaf * kTileLeaf);
     todo.push_back({a + h, b});
     todo.push_back({a, a + h});
   }

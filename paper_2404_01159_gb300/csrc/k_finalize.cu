@@ -54,17 +54,32 @@ constexpr int kFinDecode = 1024;   // threads (vectors) per finalize CTA
 
 // Writes, in ascending order, the positions of the set bits of words
 // [w0, w1) of `bits` (bit b of word w is element 32 w + b) starting at
-// out[base]; at most `limit` elements in total.  One warp, coalesced stores.
+// out[base]; at most `limit` elements in total.  One warp: lane l loads word
+// w0 + 32 i + l, so the loads of a round are independent (one round for up to
+// 32 words); a warp scan of the popcounts gives each word its offset.
 __device__ __forceinline__ int warp_compact(const uint32_t *bits, int w0, int w1, int *out,
                                            int base, int limit) {
   const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  for (int w = w0; w < w1 && base < limit; ++w) {
-    const uint32_t word = bits[w];
-    const bool set = (word >> lane) & 1u;
-    const int at = base + __popc(word & lt);
-    if (set && at < limit) out[at] = 32 * w + lane;
-    base += __popc(word);
+  for (int r = w0; r < w1; r += 32) {
+    const int w = r + lane;
+    const uint32_t word = w < w1 ? bits[w] : 0u;
+    const int c = __popc(word);
+    int incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const int at = base + incl - c;
+    // then word by word from registers: lane = bit, coalesced stores
+    const uint32_t lt = (1u << lane) - 1u;
+    const int nw = min(32, w1 - r);
+    for (int i = 0; i < nw; ++i) {
+      const uint32_t wi = __shfl_sync(0xffffffffu, word, i);
+      const int pos = __shfl_sync(0xffffffffu, at, i) + __popc(wi & lt);
+      if (((wi >> lane) & 1u) && pos < limit) out[pos] = 32 * (r + i) + lane;
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
   }
   return base;
 }

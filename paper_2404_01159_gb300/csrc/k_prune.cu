@@ -1,6 +1,6 @@
 // Exact pruned association for m <= 4 (Algorithm 1 lines 5-6, Eq. 2).
 //
-// The reference vectors are grouped into spatially compact tiles of <= 32
+// The reference vectors are grouped into spatially compact tiles of <= 64
 // (a k-d split of the initial lattice, fixed for the run).  Each tile has a
 // float32 unit centre c and an angle rho that bounds the angle from c to
 // every member.  For a solution f' (norm nf), once some vector reaches the
@@ -333,18 +333,23 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const 
 __device__ __forceinline__ void tile_one(const RunDesc &R, int t) {
   const int lane = threadIdx.x & 31;
   if (t >= R.ntiles) return;
-  const int2 rg = R.trng[t];
+  const int2 rg = R.trng[t];   // up to 2 x 32 members: lane takes q = lane, lane + 32
   const int m4 = R.m4;
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (lane < rg.y) {
-    const int j = R.tperm[rg.x + lane];
-    v = reinterpret_cast<const float4 *>(R.V32)[(size_t)j * m4];
-    float4 vt = v;
-    if (R.m < 4) vt.w = __int_as_float(j);   // the member's vector index rides along
-    R.Vt[rg.x + lane] = vt;
+  float4 v[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = lane + 32 * h;
+    v[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < rg.y) {
+      const int j = R.tperm[rg.x + q];
+      v[h] = reinterpret_cast<const float4 *>(R.V32)[(size_t)j * m4];
+      float4 vt = v[h];
+      if (R.m < 4) vt.w = __int_as_float(j);   // the member's vector index rides along
+      R.Vt[rg.x + q] = vt;
+    }
   }
   // centre: normalised mean of the members
-  float sx = v.x, sy = v.y, sz = v.z, sw = v.w;
+  float sx = v[0].x + v[1].x, sy = v[0].y + v[1].y, sz = v[0].z + v[1].z, sw = v[0].w + v[1].w;
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     sx += __shfl_xor_sync(0xffffffffu, sx, off);
@@ -356,11 +361,15 @@ __device__ __forceinline__ void tile_one(const RunDesc &R, int t) {
   const float4 c = make_float4((float)(sx / cn), (float)(sy / cn), (float)(sz / cn), (float)(sw / cn));
   // rho: the largest angle centre-member, both float32 rows normalised in FP64
   double cmin = 1.0;
-  if (lane < rg.y) {
-    const double vn = sqrt((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w);
-    const double ccn = sqrt((double)c.x * c.x + (double)c.y * c.y + (double)c.z * c.z + (double)c.w * c.w);
-    const double cosang = ((double)v.x * c.x + (double)v.y * c.y + (double)v.z * c.z + (double)v.w * c.w) / (vn * ccn);
-    cmin = fmin(1.0, cosang);
+  const double ccn = sqrt((double)c.x * c.x + (double)c.y * c.y + (double)c.z * c.z + (double)c.w * c.w);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (lane + 32 * h < rg.y) {
+      const float4 u = v[h];
+      const double vn = sqrt((double)u.x * u.x + (double)u.y * u.y + (double)u.z * u.z + (double)u.w * u.w);
+      const double cosang = ((double)u.x * c.x + (double)u.y * c.y + (double)u.z * c.z + (double)u.w * c.w) / (vn * ccn);
+      cmin = fmin(cmin, cosang);
+    }
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) cmin = fmin(cmin, __shfl_xor_sync(0xffffffffu, cmin, off));

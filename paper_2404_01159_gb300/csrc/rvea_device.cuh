@@ -95,7 +95,7 @@ struct RunDesc {
   int ntiles;          // 0: the pruned kernel is not used for this run
   float4 *Vt;          // [N]        V32 in tile order (m <= 4)
   int *tperm;          // [N]        tile-order position -> vector index j
-  int2 *trng;          // [ntiles]   (first position, count <= 32) of each tile
+  int2 *trng;          // [ntiles]   (first position, count <= 64) of each tile
   float4 *tcen;        // [ntiles]   unit centre of each tile (float32)
   float2 *tcs;         // [ntiles]   (cos rho, sin rho), rho >= max angle centre-member
   // stateless-selection views (op_mode)
