@@ -37,6 +37,23 @@ WORKLOADS = {
 COMMON = dict(alpha=2.0, f_r=0.1, eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The maximum of x over the ranks of the process group (x if none): a
+    replica run is as slow as its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job generations/s of `world` replicas of `steps` generations each,
+    timed by the slowest rank."""
+    return world * steps / (ms_max * 1e-3)
+
+
 def repro_bytes(wl) -> int:
     """Algorithmic bytes of one reproduction launch: read 2*ceil(N/2) parent
     rows, write N child rows, d float32 each (objectives are O(N m))."""
@@ -627,10 +644,7 @@ def main():
         sampler.stop()
     barrier()
     ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     run.sync_status()
     p_adapt = max(1, int(kw["f_r"] * kw["t_max"] + 0.5))
     n_adapt = sum(1 for t in range(t_first, t_first + K) if t % p_adapt == 0)
@@ -666,10 +680,7 @@ def main():
         erun.population(hX, hV)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
         erun.sync_status()
         del erun
     h2d_init = N * m * 8 * 2 + N * 16 + 4096       # lattice (f64 x2), float copy, tables
@@ -682,7 +693,7 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_seconds)
-    value = world * K / (ms * 1e-3)
+    value = replica_value(world, K, ms)
     clocks = sampler.summary() if sampler else None
     line = {
         "metric": METRIC,

@@ -405,19 +405,18 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
       const int q = c % kStages;
       if (!mbar_wait(&bar[q], (uint32_t)(c / kStages) & 1u, kWaitLimit)) break;
       const int gs = g0 + 32 * c, n4 = 2 * (min(gE, gs + 32) - gs);
+      const float4 *const sa = sb + q * 128;          // this chunk: parent 1, then parent 2
+      float4 *const y1 = X4 + q1 + 2 * gs;            // the chunk's first float4 of each child
+      float4 *const y2 = has2 ? X4 + q2 + 2 * gs : nullptr;
       if (2 * gs >= Qs && 2 * gs + n4 <= Qe) {   // an interior chunk (warp-uniform)
 #pragma unroll 1
-        for (int qi = wl; qi < n4; qi += 32) {
-          const int Q = 2 * gs + qi;   // float4 index in the row: variables 4Q .. 4Q+3
-          cross4<PROB>(sb[q * 128 + qi], sb[q * 128 + 64 + qi], Q, p, t, nocross, ie, L, U, kp,
-                       X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2);
-        }
+        for (int qi = wl; qi < n4; qi += 32)   // float4 2 gs + qi: variables 4Q .. 4Q+3
+          cross4<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie, L, U, kp, y1 + qi,
+                       y2 ? y2 + qi : nullptr, acc1, acc2);
       } else {
-        for (int qi = wl; qi < n4; qi += 32) {
-          const int Q = 2 * gs + qi;
-          cross4_edge<PROB>(sb[q * 128 + qi], sb[q * 128 + 64 + qi], Q, p, t, nocross, ie, L, U,
-                            kp, X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2, mh, d);
-        }
+        for (int qi = wl; qi < n4; qi += 32)
+          cross4_edge<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie, L, U, kp,
+                            y1 + qi, y2 ? y2 + qi : nullptr, acc1, acc2, mh, d);
       }
       __syncwarp();
     }
