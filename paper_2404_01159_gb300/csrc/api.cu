@@ -411,6 +411,25 @@ T *wsp(const rvea_run *r, size_t off) {
   return reinterpret_cast<T *>(r->ws + off);
 }
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// its predecessor in the stream finishes; every kernel of a generation waits
+// (griddepcontrol.wait) before reading its predecessor's results.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                cudaStream_t st, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_error(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...), "cudaLaunchKernelEx");
+}
+
 // Item table of the full-scan association for the run's current plan
 // (sel_per_sm work items per SM), into sel_host; n_sel and the shared memory
 // of one chunk follow.
@@ -433,16 +452,16 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
   const int sm = r->repro_smem;
   if (sm > 0) {
     switch (r->hd.problem) {
-      case PROB_DTLZ1: k_repro1s_dtlz1<<<grid, kReproThreads, sm, st>>>(dr, rk); break;
-      case PROB_DTLZ2: k_repro1s_dtlz2<<<grid, kReproThreads, sm, st>>>(dr, rk); break;
-      default: k_repro1s_neuro<<<grid, kReproThreads, sm, st>>>(dr, rk); break;
+      case PROB_DTLZ1: launch_pdl(k_repro1s_dtlz1, grid, kReproThreads, sm, st, dr, rk); break;
+      case PROB_DTLZ2: launch_pdl(k_repro1s_dtlz2, grid, kReproThreads, sm, st, dr, rk); break;
+      default: launch_pdl(k_repro1s_neuro, grid, kReproThreads, sm, st, dr, rk); break;
     }
     return;
   }
   switch (r->hd.problem) {
-    case PROB_DTLZ1: k_repro1_dtlz1<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
-    case PROB_DTLZ2: k_repro1_dtlz2<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
-    default: k_repro1_neuro<<<grid, kReproThreads, 0, st>>>(dr, rk); break;
+    case PROB_DTLZ1: launch_pdl(k_repro1_dtlz1, grid, kReproThreads, 0, st, dr, rk); break;
+    case PROB_DTLZ2: launch_pdl(k_repro1_dtlz2, grid, kReproThreads, 0, st, dr, rk); break;
+    default: launch_pdl(k_repro1_neuro, grid, kReproThreads, 0, st, dr, rk); break;
   }
 }
 
@@ -520,12 +539,12 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       dg[g].prefix[dg[g].n] = pg[g];
       const int sm = (g & 1) ? kStagedSmem : 0;
       switch (g) {
-        case 0: k_reprob_dtlz2<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
-        case 1: k_reprob_dtlz2s<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
-        case 2: k_reprob_dtlz1<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
-        case 3: k_reprob_dtlz1s<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
-        case 4: k_reprob_neuro<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
-        default: k_reprob_neuros<<<pg[g], kReproThreads, sm, st>>>(dg[g]); break;
+        case 0: launch_pdl(k_reprob_dtlz2, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 1: launch_pdl(k_reprob_dtlz2s, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 2: launch_pdl(k_reprob_dtlz1, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 3: launch_pdl(k_reprob_dtlz1s, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 4: launch_pdl(k_reprob_neuro, pg[g], kReproThreads, sm, st, dg[g]); break;
+        default: launch_pdl(k_reprob_neuros, pg[g], kReproThreads, sm, st, dg[g]); break;
       }
     }
   }
@@ -551,21 +570,22 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       dn.n = dro.n = nn;
       dn.prefix[nn] = pn;
       dro.prefix[nn] = pro;
-      k_noise<<<pn, 256, 0, st>>>(dn, 0);
-      k_rollout<<<pro, 32 * kRollPolicies, 0, st>>>(dro, 0);
+      launch_pdl(k_noise, pn, 256, 0, st, dn, 0);
+      launch_pdl(k_rollout, pro, 32 * kRollPolicies, 0, st, dro, 0);
     }
   }
   if (ev) cudaEventRecord(ev[1], st);
   if (np > 0) {
     if (n == 1 && runs[0]->sel_mode == 1)
-      k_select_pruned<<<runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st>>>(runs[0]->d_desc);
+      launch_pdl(k_select_pruned, runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st,
+                 (const RunDesc *)runs[0]->d_desc);
     else
-      k_select_pruned_batch<<<runs[0]->num_sms, 1024, smp, st>>>(dp);
+      launch_pdl(k_select_pruned_batch, runs[0]->num_sms, 1024, smp, st, dp);
   }
   if (ev) cudaEventRecord(ev[2], st);
-  if (ns > 0) k_select<<<ps, kSelThreads, sms, st>>>(ds);
+  if (ns > 0) launch_pdl(k_select, ps, kSelThreads, sms, st, ds);
   if (ev) cudaEventRecord(ev[3], st);
-  k_finalize<<<pd, 1024, 0, st>>>(dd);
+  launch_pdl(k_finalize, pd, 1024, 0, st, dd);
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
     k_gamma<<<2 * kSMs, 256, 0, st>>>(df, 0);

@@ -86,6 +86,8 @@ __device__ __forceinline__ int warp_compact(const uint32_t *bits, int w0, int w1
 
 __global__ void __launch_bounds__(kFinDecode)
 k_finalize(const __grid_constant__ BatchDir dir) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned s_lo[32][kMaxM], s_hi[32][kMaxM];
   __shared__ unsigned s_z[2 * kMaxM];
   __shared__ int s_cnt[2][32];
@@ -361,6 +363,7 @@ __device__ void gamma_block(const RunDesc &R, int jb) {
 // run when `force`) has its vector blocks of 32 spread over the grid.
 __global__ void __launch_bounds__(256)
 k_gamma(const __grid_constant__ BatchDir dir, int force) {
+  pdl_wait();
   for (int r = 0; r < dir.n; ++r) {
     const RunDesc &R = *dir.desc[r];
     if (!force && R.ctl->adapted == 0) continue;

@@ -218,10 +218,6 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
   float4 *sC = reinterpret_cast<float4 *>(smem + bV);
   float2 *sCS = reinterpret_cast<float2 *>(smem + bV + bC);
   int2 *sR = reinterpret_cast<int2 *>(smem + bV + bC + bSr);
-  if (blockIdx.x == 0 && threadIdx.x < kMaxM) {
-    R.ctl->znext[threadIdx.x] = 0xFFFFFFFFu;   // built by the finalize kernel
-    R.ctl->zhi[threadIdx.x] = 0u;
-  }
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
@@ -241,6 +237,10 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
     __syncthreads();
     return;
   }
+  // the tables (k_tiles, earlier than the predecessor) are staged above; the
+  // population's objectives come from the reproduction kernel
+  pdl_wait();
+  pdl_trigger();
   switch (R.m) {
     case 2: prune_loop<2>(R, sV, sC, sCS, sR); break;
     case 3: prune_loop<3>(R, sV, sC, sCS, sR); break;
@@ -253,7 +253,6 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
 // CTAs from the work counter of the first run; a CTA stages the tables of
 // the chunk's run in shared memory with TMA unless they are already there
 // (chunks come in run order, so a CTA reloads about once per run it visits).
-// CTA 0 resets each run's survivor extrema, which finalize rebuilds.
 constexpr int kPruneChunk = 2048;
 
 __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const __grid_constant__ BatchDir dir) {
@@ -261,12 +260,8 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const 
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_chunk;
   const int warp = threadIdx.x >> 5;
-  if (blockIdx.x == 0)
-    for (int q = 0; q < dir.n; ++q)
-      if (threadIdx.x < kMaxM) {
-        dir.desc[q]->ctl->znext[threadIdx.x] = 0xFFFFFFFFu;
-        dir.desc[q]->ctl->zhi[threadIdx.x] = 0u;
-      }
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
@@ -381,12 +376,14 @@ __device__ __forceinline__ void tile_one(const RunDesc &R, int t) {
 }
 
 __global__ void k_tiles(const RunDesc *__restrict__ Rp) {
+  pdl_wait();
   tile_one(*Rp, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
 }
 
 // The same over a batch (dir.prefix counts CTAs of 8 tiles): runs whose
 // vectors were adapted this generation (all runs with force).
 __global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force) {
+  pdl_wait();
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   if (!force && R.ctl->adapted == 0) return;

@@ -317,6 +317,8 @@ __device__ __noinline__ void finish_pair(const RunDesc &R, int p, int S, int ch1
 
 template <int PROB, bool STAGED, class KP>
 __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
+  pdl_wait();      // the previous generation's lists and slot maps
+  pdl_trigger();
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const ReproItem it = static_cast<const ReproItem *>(dir.items[run])[blockIdx.x - dir.prefix[run]];

@@ -113,6 +113,7 @@ __device__ __forceinline__ void tile_to_b(float v0, float v8, int lane, uint32_t
 // u1 = 1 - u24(word 0) in (0, 1] and u2 = u24(word 1).  One thread per entry;
 // dir.prefix counts CTAs of 256 entries.
 __global__ void k_noise(const __grid_constant__ BatchDir dir, int init) {
+  pdl_wait();
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const int e = (blockIdx.x - dir.prefix[run]) * blockDim.x + threadIdx.x;
@@ -130,6 +131,7 @@ __global__ void k_noise(const __grid_constant__ BatchDir dir, int init) {
 // otherwise the N children of generation t (rows child_slot[t & 1]).
 __global__ void __launch_bounds__(kRollWarps * 32)
 k_rollout(const __grid_constant__ BatchDir dir, int init) {
+  pdl_wait();
   __shared__ float sA[kRollNsMax * kRollNsMax], sB[kRollNsMax * kRollNaMax];
   __shared__ uint4 sLo[kRollWarps * kRollTiles * 32];   // lo weight fragments, per warp
   const int run = dir_find(dir, blockIdx.x);

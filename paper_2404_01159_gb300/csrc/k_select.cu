@@ -156,6 +156,8 @@ __device__ __forceinline__ void apd_vote(const RunDesc &R, int i, const float *f
 // the chunk staged in shared memory by one 1-D TMA bulk copy.
 __global__ void __launch_bounds__(kSelThreads)
 k_select(const __grid_constant__ BatchDir dir) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(128) float4 s_v[];     // [chunk vectors * m4]
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_last;
@@ -166,10 +168,6 @@ k_select(const __grid_constant__ BatchDir dir) {
   const int m = R.m, m4 = R.m4;
   const int ia = it.sblk * 2 * kSelThreads + threadIdx.x, ib = ia + kSelThreads;
   const int sa = sol_slot(R, ia), sb = sol_slot(R, ib);
-  if (!R.op_mode && blockIdx.x == dir.prefix[run] && threadIdx.x < kMaxM) {
-    R.ctl->znext[threadIdx.x] = 0xFFFFFFFFu;   // built by the next kernel
-    R.ctl->zhi[threadIdx.x] = 0u;
-  }
   const int nv = it.v1 - it.v0;
   const uint32_t bytes = (uint32_t)(nv * m4 * 16);
   if (threadIdx.x == 0) {

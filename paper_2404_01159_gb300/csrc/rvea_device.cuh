@@ -45,8 +45,6 @@ struct Ctl {
   int fin_cnt;         // arrival counter of the finalize CTAs
   int sel_cnt;         // work counter of the pruned selection kernel
   unsigned zkey[kMaxM];   // ideal point z*, order-preserving uint encoding
-  unsigned znext[kMaxM];  // minimum over the survivors (next z*), being built
-  unsigned zhi[kMaxM];    // maximum over the survivors (adaptation range)
 };
 
 struct RunDesc {
@@ -315,6 +313,18 @@ __device__ __forceinline__ float apd_chord(const float *fp, int m, const float *
   }
   const float th = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(w2) / nf));
   return (1.0f + pen * th / gam) * nf;
+}
+
+// Programmatic dependent launch.  The kernels of a generation are launched
+// with programmatic stream serialisation, so a kernel's CTAs may start while
+// its predecessor's last CTAs still run: each kernel waits (griddepcontrol
+// .wait: the predecessor has completed and its writes are visible) before it
+// reads anything the predecessor wrote, and only then lets its own successor
+// start (launch_dependents).  Waiting before triggering keeps the ordering
+// transitive.  In a kernel launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Orders this thread's generic-proxy shared-memory accesses before later
