@@ -473,7 +473,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
                               cudaEvent_t *ev = nullptr) {
   static thread_local BatchDir dr, ds, dp, df, dd, dt, dg[6];
   int pr = 0, ps = 0, pp = 0, pd = 0, pt = 0;
-  int smr = 0, sms = 0, smp = 0, ns = 0, np = 0;
+  int sms = 0, smp = 0, ns = 0, np = 0;
   dr.n = df.n = dd.n = n;
   for (int q = 0; q < n; ++q) {
     const rvea_run *r = runs[q];
@@ -487,7 +487,6 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     df.items[q] = dd.items[q] = nullptr;
     pd += (r->sh.N + 1023) / 1024;
     pr += r->sh.n_repro;
-    smr = std::max(smr, r->repro_smem);
     if (r->sel_mode == 0) {
       ds.prefix[ns] = ps;
       ds.desc[ns] = r->d_desc;
