@@ -9,7 +9,7 @@
 // adaptation generations rescales V0 by the survivors' objective range in
 // FP64 (Algorithm 2, "update reference vectors").  gamma (Eq. 5) follows in
 // k_gamma.
-#include "rvea_device.cuh"
+#include "finalize_steps.cuh"
 
 namespace rvea {
 
@@ -50,103 +50,20 @@ __device__ int block_exclusive_scan(int v, int *s_warp, int *total) {
 // slots (mating of the next generation), the ascending list of free pool rows
 // (its offspring), the next z*, and on adaptation generations rescales V0 by
 // the survivors' objective range in FP64.
-constexpr int kFinDecode = 1024;   // threads (vectors) per finalize CTA
-
-// Writes, in ascending order, the positions of the set bits of words
-// [w0, w1) of `bits` (bit b of word w is element 32 w + b) starting at
-// out[base]; at most `limit` elements in total.  One warp: lane l loads word
-// w0 + 32 i + l, so the loads of a round are independent (one round for up to
-// 32 words); a warp scan of the popcounts gives each word its offset.
-__device__ __forceinline__ int warp_compact(const uint32_t *bits, int w0, int w1, int *out,
-                                           int base, int limit) {
-  const int lane = threadIdx.x & 31;
-  for (int r = w0; r < w1; r += 32) {
-    const int w = r + lane;
-    const uint32_t word = w < w1 ? bits[w] : 0u;
-    const int c = __popc(word);
-    int incl = c;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += y;
-    }
-    const int at = base + incl - c;
-    // then word by word from registers: lane = bit, coalesced stores
-    const uint32_t lt = (1u << lane) - 1u;
-    const int nw = min(32, w1 - r);
-    for (int i = 0; i < nw; ++i) {
-      const uint32_t wi = __shfl_sync(0xffffffffu, word, i);
-      const int pos = __shfl_sync(0xffffffffu, at, i) + __popc(wi & lt);
-      if (((wi >> lane) & 1u) && pos < limit) out[pos] = 32 * (r + i) + lane;
-    }
-    base += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  return base;
-}
 
 __global__ void __launch_bounds__(kFinDecode)
 k_finalize(const __grid_constant__ BatchDir dir) {
   pdl_wait();
   pdl_trigger();
-  __shared__ unsigned s_lo[32][kMaxM], s_hi[32][kMaxM];
-  __shared__ unsigned s_z[2 * kMaxM];
-  __shared__ int s_cnt[2][32];
-  __shared__ double s_rng[kMaxM];
+  __shared__ FinShared sh;
   __shared__ int s_last;
-  __shared__ uint32_t s_free[2048];   // complement of the occupied-row bitmap
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const int blk = blockIdx.x - dir.prefix[run];
   const int nblk = dir.prefix[run + 1] - dir.prefix[run];
-  const int j = blk * kFinDecode + threadIdx.x;
-  const int N = R.N, n2 = 2 * N, m = R.m;
-  const int t = R.ctl->t;
-  const int *cur = R.slotmap + (t & 1) * N;
-  int *nmap = R.slotmap + ((t + 1) & 1) * N;
-  const int *ccur = R.child_slot + (t & 1) * N;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  // ---- decode ---------------------------------------------------------------
-  int s = -1;
-  if (j < N) {
-    const unsigned long long key = R.best[j];
-    R.best[j] = ~0ull;
-    int i = -1;
-    if (key != ~0ull) {
-      i = (int)(uint32_t)(key & 0xFFFFFFFFull);
-      if (i >= 0 && i < N) s = cur[i];
-      else if (i >= N && i < n2) s = ccur[i - N];
-      if (s < 0 || s >= n2) { set_status(R.ctl, ST_BADINDEX); s = -1; i = -1; }
-    }
-    nmap[j] = s;
-    R.surv[j] = i;
-    if (s >= 0) atomicOr(&R.obits[s >> 5], 1u << (s & 31));
-  }
-  const uint32_t vmask = __ballot_sync(0xffffffffu, s >= 0);
-  if (lane == 0 && j < N) R.vbits[j >> 5] = vmask;
-  for (int k = 0; k < m; ++k) {
-    unsigned lo = 0xFFFFFFFFu, hi = 0u;
-    if (s >= 0) lo = hi = f2ord(R.F[(size_t)k * n2 + s]);
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-    }
-    if (lane == 0) { s_lo[warp][k] = lo; s_hi[warp][k] = hi; }
-  }
-  __syncthreads();
-  if (threadIdx.x < m) {
-    unsigned lo = 0xFFFFFFFFu, hi = 0u;
-    for (int w = 0; w < kFinDecode / 32; ++w) {
-      lo = min(lo, s_lo[w][threadIdx.x]);
-      hi = max(hi, s_hi[w][threadIdx.x]);
-    }
-    R.zpart[(size_t)blk * 2 * kMaxM + threadIdx.x] = lo;
-    R.zpart[(size_t)blk * 2 * kMaxM + kMaxM + threadIdx.x] = hi;
-  }
-  // the barrier orders every thread's writes before thread 0's (cumulative)
-  // fence, which orders them before its arrival
-  __syncthreads();
+  fin_decode(R, blk, sh);
+  // the barrier (in fin_decode) orders every thread's writes before thread
+  // 0's (cumulative) fence, which orders them before its arrival
   if (threadIdx.x == 0) {
     __threadfence();
     s_last = atomicAdd(&R.ctl->fin_cnt, 1) == nblk - 1;
@@ -154,79 +71,7 @@ k_finalize(const __grid_constant__ BatchDir dir) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-
-  // ---- last CTA: lists, z*, adaptation ---------------------------------------
-  const int tid = threadIdx.x;
-  const int nvw = (N + 31) >> 5, now = (n2 + 31) >> 5, nzb = nblk;
-  for (int w = tid; w < now; w += kFinDecode) {
-    uint32_t o = __ldcg(R.obits + w);
-    if (w == now - 1 && (n2 & 31)) o |= ~((1u << (n2 & 31)) - 1u);   // beyond 2N
-    s_free[w] = ~o;
-    R.obits[w] = 0u;   // empty for the next generation
-  }
-  if (tid < 2 * kMaxM) s_z[tid] = tid < kMaxM ? 0xFFFFFFFFu : 0u;
-  __syncthreads();
-  for (int q = tid; q < nzb * m; q += kFinDecode) {
-    const int b = q / m, k = q - (q / m) * m;
-    atomicMin(&s_z[k], __ldcg(R.zpart + (size_t)b * 2 * kMaxM + k));
-    atomicMax(&s_z[kMaxM + k], __ldcg(R.zpart + (size_t)b * 2 * kMaxM + kMaxM + k));
-  }
-  // warp w owns words [w * per, (w+1) * per) of each bitmap
-  const int perv = (nvw + 31) / 32, pero = (now + 31) / 32;
-  const int v0 = min(nvw, warp * perv), v1 = min(nvw, v0 + perv);
-  const int o0 = min(now, warp * pero), o1 = min(now, o0 + pero);
-  int cv = 0, cf = 0;
-  for (int w = v0 + lane; w < v1; w += 32) cv += __popc(__ldcg(R.vbits + w));
-  for (int w = o0 + lane; w < o1; w += 32) cf += __popc(s_free[w]);
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    cv += __shfl_xor_sync(0xffffffffu, cv, off);
-    cf += __shfl_xor_sync(0xffffffffu, cf, off);
-  }
-  if (lane == 0) { s_cnt[0][warp] = cv; s_cnt[1][warp] = cf; }
-  __syncthreads();
-  int bv = 0, bf = 0, K = 0;
-  for (int w = 0; w < 32; ++w) {
-    if (w < warp) { bv += s_cnt[0][w]; bf += s_cnt[1][w]; }
-    K += s_cnt[0][w];
-  }
-  warp_compact(R.vbits, v0, v1, R.vlist, bv, N);
-  warp_compact(s_free, o0, o1, R.child_slot + ((t + 1) & 1) * N, bf, N);
-
-  if (tid < m) R.ctl->zkey[tid] = s_z[tid];
-  const bool adapt = (t % R.p_adapt) == 0;
-  if (adapt && K > 0) {
-    // range_k = max - min over the survivors, floored at 1e-12, in FP64
-    if (tid < m) {
-      const double r = (double)ord2f(s_z[kMaxM + tid]) - (double)ord2f(s_z[tid]);
-      s_rng[tid] = r < 1e-12 ? 1e-12 : r;
-    }
-    __syncthreads();
-    for (int jj = tid; jj < N; jj += kFinDecode) {
-      const double *v0p = R.V0 + (size_t)jj * m;
-      double w[kMaxM];
-      double s2 = 0.0;
-      for (int k = 0; k < m; ++k) {
-        w[k] = v0p[k] * s_rng[k];
-        s2 += w[k] * w[k];
-      }
-      const double nrm = sqrt(s2);
-      float *v32 = R.V32 + (size_t)jj * R.m4 * 4;
-      for (int k = 0; k < m; ++k) {
-        const double v = w[k] / nrm;
-        R.V64[(size_t)jj * m + k] = v;
-        v32[k] = (float)v;
-        R.V32lo[(size_t)jj * m + k] = (float)(v - (double)(float)v);
-      }
-    }
-  }
-  if (tid == 0) {
-    R.ctl->K = K;
-    R.ctl->adapted = adapt ? 1 : 0;
-    R.ctl->fin_cnt = 0;
-    R.ctl->sel_cnt = 0;
-    R.ctl->t = t + 1;
-  }
+  fin_lists(R, nblk, sh);
 }
 
 // gamma_j = min_{i != j} angle(v_i, v_j) (Eq. 5), FP64.  arccos is
