@@ -25,8 +25,10 @@ def _cuda():
 
 # (m, d, N, H, problem): cfg0 shape, a ragged DTLZ1 case spanning several
 # reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10;
-# the last two (d > 1024) take the shared-memory-staged reproduction path,
-# with segments of several chunks, a partial last chunk and row padding.
+# (d > 1024) take the shared-memory-staged reproduction path, with segments
+# of several chunks, a partial last chunk and row padding; the last two have
+# 2100 pairs, more than one reproduction CTA's worth of pair draws, on both
+# load paths.
 SHAPES = [
     (3, 12, 105, 13, 0),
     (3, 1001, 210, 19, 1),
@@ -37,6 +39,8 @@ SHAPES = [
     (3, 300, 1275, 49, 0),
     (3, 2500, 105, 13, 1),
     (2, 4099, 100, 99, 0),
+    (2, 30, 4200, 4199, 1),
+    (2, 1100, 4200, 4199, 0),
 ]
 
 
