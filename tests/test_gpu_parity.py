@@ -26,9 +26,9 @@ def _cuda():
 # (m, d, N, H, problem): cfg0 shape, a ragged DTLZ1 case spanning several
 # reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10;
 # (d > 1024) take the shared-memory-staged reproduction path, with segments
-# of several chunks, a partial last chunk and row padding; the last two have
-# 2100 pairs, more than one reproduction CTA's worth of pair draws, on both
-# load paths.
+# of several chunks, a partial last chunk and row padding; the last two are
+# large populations (N = 4200, 2100 pairs) on the register and the staged
+# load path.
 SHAPES = [
     (3, 12, 105, 13, 0),
     (3, 1001, 210, 19, 1),
