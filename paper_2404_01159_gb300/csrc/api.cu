@@ -37,6 +37,9 @@ __global__ void k_repro1_neuro(const __grid_constant__ BatchDir dir, const __gri
 __global__ void k_repro1s_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1s_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1s_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_mutate_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_mutate_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_mutate_neuro(const __grid_constant__ BatchDir dir);
 __global__ void k_init(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
@@ -134,7 +137,7 @@ Shape make_shape(int m, int d, int N) {
 
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
-      ctl, desc, repro, init, sel, stage, psum, pcnt, Vt, tperm, trng, tcen, tcs, noise,
+      ctl, desc, repro, init, sel, stage, psum, Vt, tperm, trng, tcen, tcs, noise,
       dynA, dynB, total;
 };
 
@@ -172,7 +175,6 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.sel = take((size_t)s.n_sel_max * sizeof(SelItem));
   L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
-  L.pcnt = take((size_t)s.P * 4);
   const size_t T = (size_t)s.tmax;
   L.Vt = take(s.tmax ? (size_t)s.N * 16 : 0);
   L.tperm = take(s.tmax ? (size_t)s.N * 4 : 0);
@@ -465,6 +467,20 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
   }
 }
 
+// Mutation and evaluation of the children of a run reproduced by 32-lane
+// teams (d > 1024), after its reproduction kernel; nothing for other runs.
+void launch_mutate1(const rvea_run *r, cudaStream_t st) {
+  if (r->sh.team != 32) return;
+  static thread_local BatchDir dm;
+  const int nb = (r->sh.N + kMutThreads - 1) / kMutThreads;
+  dir_single(dm, r, nullptr, nb);
+  switch (r->hd.problem) {
+    case PROB_DTLZ1: launch_pdl(k_mutate_dtlz1, nb, kMutThreads, 0, st, dm); break;
+    case PROB_DTLZ2: launch_pdl(k_mutate_dtlz2, nb, kMutThreads, 0, st, dm); break;
+    default: launch_pdl(k_mutate_neuro, nb, kMutThreads, 0, st, dm); break;
+  }
+}
+
 // Enqueue one generation of every run in `runs` (one launch per phase): the
 // reproduction of all runs; the association of the pruned runs (one
 // persistent launch) and of the full-scan runs; finalize; with
@@ -518,6 +534,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   if (ev) cudaEventRecord(ev[0], st);
   if (n == 1) {
     launch_repro1(runs[0], dr, pr, st);
+    launch_mutate1(runs[0], st);
   } else {
     // one launch per (problem, load path) group, each with its own directory
     int pg[6] = {0, 0, 0, 0, 0, 0};
@@ -544,6 +561,30 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
         case 3: launch_pdl(k_reprob_dtlz1s, pg[g], kReproThreads, sm, st, dg[g]); break;
         case 4: launch_pdl(k_reprob_neuro, pg[g], kReproThreads, sm, st, dg[g]); break;
         default: launch_pdl(k_reprob_neuros, pg[g], kReproThreads, sm, st, dg[g]); break;
+      }
+    }
+    // mutation / evaluation of the 32-lane-team runs, one launch per problem
+    static thread_local BatchDir dm[3];
+    int pm[3] = {0, 0, 0};
+    for (int g = 0; g < 3; ++g) dm[g].n = 0;
+    for (int q = 0; q < n; ++q) {
+      const rvea_run *r = runs[q];
+      if (r->sh.team != 32) continue;
+      BatchDir &D = dm[r->hd.problem];
+      D.prefix[D.n] = pm[r->hd.problem];
+      D.desc[D.n] = r->d_desc;
+      D.key[D.n] = make_uint2(r->hd.key0, r->hd.key1);
+      D.items[D.n] = nullptr;
+      pm[r->hd.problem] += (r->sh.N + kMutThreads - 1) / kMutThreads;
+      ++D.n;
+    }
+    for (int g = 0; g < 3; ++g) {
+      if (dm[g].n == 0) continue;
+      dm[g].prefix[dm[g].n] = pm[g];
+      switch (g) {
+        case PROB_DTLZ1: launch_pdl(k_mutate_dtlz1, pm[g], kMutThreads, 0, st, dm[g]); break;
+        case PROB_DTLZ2: launch_pdl(k_mutate_dtlz2, pm[g], kMutThreads, 0, st, dm[g]); break;
+        default: launch_pdl(k_mutate_neuro, pm[g], kMutThreads, 0, st, dm[g]); break;
       }
     }
   }
@@ -794,7 +835,6 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gamma32 = wsp<float>(r, lay.g32);
   D.ctl = wsp<Ctl>(r, lay.ctl);
   D.psum = wsp<float>(r, lay.psum);
-  D.pcnt = wsp<int>(r, lay.pcnt);
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
   r->repro_smem = sh.team == 32 ? kStagedSmem : 0;   // staged path (the default for 32-lane teams)
@@ -1082,6 +1122,12 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
     const double us = timed([&] { launch_repro1(r, dr, r->sh.n_repro, st); }, false);
     if (us < best_rep) { best_rep = us; best.repro_staged = staged; }
   }
+  // the children complete (mutated, evaluated) before the association is
+  // timed on them, as the real generation will see them
+  if (s == RVEA_OK) {
+    launch_mutate1(r, st);
+    if (cudaGetLastError() != cudaSuccess) s = RVEA_ERR_CUDA;
+  }
   // association: the full scan at 4, 8 and 16 work items per SM, and the
   // pruned search with its tables in shared memory or read through L1
   double best_sel = 1e30;
@@ -1251,6 +1297,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     cudaEvent_t *e = &ev[(size_t)g * 5];
     cudaEventRecord(e[0], st);
     launch_repro1(r, dr, r->sh.n_repro, st);
+    launch_mutate1(r, st);
     if (r->hd.problem == PROB_NEURO) {
       const int nb_noise = (r->hd.steps * r->hd.ns + 255) / 256;
       const int nb_roll = (r->sh.N + kRollPolicies - 1) / kRollPolicies;

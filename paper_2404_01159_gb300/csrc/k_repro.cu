@@ -8,17 +8,19 @@
 // alone) owns one work unit: one segment of sg consecutive 8-variable groups
 // of one pair (the pair's G groups split into nseg near-equal segments of at
 // most kLaneGroups*TS groups).  Teams never wait on other warps: the phases
-// below synchronise with __syncwarp only.  A pair with several segments
-// combines the segments' partial sums of g in the last segment to finish (an
-// arrival counter per pair, no spinning), always in segment order, so the
-// reduction tree depends on d alone.
+// below synchronise with __syncwarp only.  Teams of fewer than 32 lanes own a
+// whole pair (one segment) and finish it: mutation, g, objectives.  32-lane
+// teams (d > 1024) store their segments' partial sums of g and leave the
+// mutation and the evaluation to k_mutate, which adds the partials in
+// segment order, so the reduction tree depends on d alone.
 //
 // The main pass does SBX, clip and the g-terms of both children, four
 // variables (one float4) at a time, and stores the crossed children.  Only
 // the float4s holding x_1..x_{m-1} (kept out of g) or the end of the row take
 // an out-of-line edge path.  Mutation is sparse (about one site per row), so
-// it is a second pass over the segment's sites: reload the crossed value,
-// mutate, store, and correct the lane's g sum by term(new) - term(old).
+// it is a second pass over the row's sites (in this kernel for teams of fewer
+// than 32 lanes, in k_mutate for the others): reload the crossed value,
+// mutate, store, and correct the g sum by term(new) - term(old).
 // Parents are read either straight from global memory (teams of fewer than
 // 32 lanes) or, for 32-lane teams, from a ring of shared-memory chunks filled
 // by TMA bulk copies, so that each warp keeps its next chunk in flight.
@@ -218,9 +220,9 @@ __device__ __forceinline__ void cross4(const float4 xa, const float4 xb, int Q, 
 
 // The same for a float4 that holds some of x_1..x_{m-1} (j < mh, kept out
 // of g) or reaches past the last variable (j >= d): g-terms per variable.
-template <int PROB, class KP>
+template <int PROB>
 __device__ __noinline__ void cross4_edge(const float4 xa, const float4 xb, int Q, int p, int t,
-                                         bool nocross, float ie, float L, float U, const KP &kp,
+                                         bool nocross, float ie, float L, float U, const KeyRun kp,
                                          float4 *y1, float4 *y2, float2 &acc1, float2 &acc2,
                                          int mh, int d) {
   float2 z1 = make_float2(0.f, 0.f), z2 = z1;
@@ -245,9 +247,9 @@ __device__ __noinline__ void cross4_edge(const float4 xa, const float4 xb, int Q
 }
 
 // Mutation of one crossed variable in place; returns term(new) - term(old).
-template <int PROB, class KP>
+template <int PROB>
 __device__ __forceinline__ float mutate_one(float *px, int j, int c, int t, const RunDesc &R,
-                                            const KP &kp) {
+                                            const KeyRun &kp) {
   const float x = __ldcg(px);
   const uint4 w = philox_k((uint32_t)j, (uint32_t)c, (uint32_t)t, TAG_MUTMAG, kp);
   const float xn = poly_mutate(x, u24f(w.y), R.L, R.U, R.eta_m);
@@ -259,8 +261,8 @@ __device__ __forceinline__ float mutate_one(float *px, int j, int c, int t, cons
 // Polynomial mutation of child c (pool row `slot`) at its sites in
 // [jlo, jhi): site count, then Floyd's uniform subset; returns the change
 // of the row's g sum.  Every site when the per-site probability is 1.
-template <int PROB, class KP>
-__device__ __noinline__ float mutate_sites(const RunDesc &R, const KP &kp, int c, int slot, int t,
+template <int PROB>
+__device__ __noinline__ float mutate_sites(const RunDesc &R, const KeyRun kp, int c, int slot, int t,
                                            int jlo, int jhi) {
   float *const row = R.X + (size_t)slot * R.d_pad;
   float dg = 0.0f;
@@ -287,32 +289,26 @@ __device__ __noinline__ float mutate_sites(const RunDesc &R, const KP &kp, int c
   return dg;
 }
 
-// Last segment of pair p to arrive: g of both children from the segments'
-// partial sums in segment order, x_1..x_{m-1} read back from the child rows
-// (after their mutation), then the objectives and the ideal point.
+// Objectives of one child (pool row `slot`) from its g and x_1..x_{m-1} read
+// back from the row (after its mutation), and its share of the ideal point.
 template <int PROB>
-__device__ __noinline__ void finish_pair(const RunDesc &R, int p, int S, int ch1, int ch2) {
-  __threadfence();
-  const float *ps = R.psum + (size_t)p * 2 * S;
-  const int m = R.m, mh = m - 1, n2 = 2 * R.N, dp = R.d_pad;
-  float gg[2] = {0.f, 0.f};
-  for (int sg = 0; sg < S; ++sg) {
-    gg[0] += __ldcg(ps + sg);
-    gg[1] += __ldcg(ps + S + sg);
+__device__ __forceinline__ void evaluate_child(const RunDesc &R, int slot, float g) {
+  const int m = R.m, mh = m - 1, n2 = 2 * R.N;
+  const float *row = R.X + (size_t)slot * R.d_pad;
+  float head[kMaxM], f[kMaxM];
+  for (int j = 0; j < mh; ++j) head[j] = __ldcg(row + j);
+  dtlz_objectives(PROB, m, g, head, f);
+  for (int kk = 0; kk < m; ++kk) {
+    R.F[(size_t)kk * n2 + slot] = f[kk];
+    atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
   }
-  const int chs[2] = {ch1, ch2};
-  for (int c = 0; c < 2; ++c) {
-    if (chs[c] < 0) continue;
-    const float *row = R.X + (size_t)chs[c] * dp;
-    float head[kMaxM], f[kMaxM];
-    for (int j = 0; j < mh; ++j) head[j] = __ldcg(row + j);
-    dtlz_objectives(PROB, m, gg[c], head, f);
-    for (int kk = 0; kk < m; ++kk) {
-      R.F[(size_t)kk * n2 + chs[c]] = f[kk];
-      atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
-    }
-  }
-  R.pcnt[p] = 0;
+}
+
+// A pair of a team of fewer than 32 lanes (one segment): both children.
+template <int PROB>
+__device__ __noinline__ void finish_pair(const RunDesc &R, float g1, float g2, int ch1, int ch2) {
+  evaluate_child<PROB>(R, ch1, g1);
+  if (ch2 >= 0) evaluate_child<PROB>(R, ch2, g2);
 }
 
 template <int PROB, bool STAGED, class KP>
@@ -368,6 +364,9 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   const uint32_t rq = (uint32_t)R.d_pad >> 2;      // float4s per row
   const uint32_t q1 = (uint32_t)ch1 * rq, q2 = has2 ? (uint32_t)ch2 * rq : 0u;
   const float L = R.L, U = R.U, ie = R.inv_eta_c1;
+  // the keys as the out-of-line functions take them (a value, not a
+  // reference to the parameter block)
+  const KeyRun kr{R.key0, R.key1};
   // float4s [Qs, Qe) hold neither x_1..x_{m-1} nor variables past d
   const int mh = R.m - 1, Qs = (mh + 3) >> 2, Qe = d >> 2;
 
@@ -417,7 +416,7 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
                        y2 ? y2 + qi : nullptr, acc1, acc2);
       } else {
         for (int qi = wl; qi < n4; qi += 32)
-          cross4_edge<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie, L, U, kp,
+          cross4_edge<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie, L, U, kr,
                             y1 + qi, y2 ? y2 + qi : nullptr, acc1, acc2, mh, d);
       }
       __syncwarp();
@@ -435,36 +434,35 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
         cross4<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kp,
                      X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2);
       else
-        cross4_edge<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kp,
+        cross4_edge<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kr,
                           X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2, mh, d);
     }
   }
   // ---- mutation pass: the sites of this segment ----------------------------
+  // (32-lane teams leave their sites to k_mutate, except when every variable
+  // mutates)
   __syncwarp();   // the crossed rows are visible to the whole team
-  if (active && R.T_m > 0) {
+  if (active && R.T_m > 0 && (TS < 32 || R.T_m >= (1u << 24))) {
     for (int c = lane; c < 2; c += TS) {
       if (c == 1 && !has2) break;
-      const float dg = mutate_sites<PROB>(R, kp, c ? p + P : p, c ? ch2 : ch1, t, 8 * g0,
+      const float dg = mutate_sites<PROB>(R, kr, c ? p + P : p, c ? ch2 : ch1, t, 8 * g0,
                                           8 * gE);
       if (c == 0) acc1.x += dg; else acc2.x += dg;
     }
   }
   if (PROB == PROB_NEURO) return;   // objectives come from the rollout kernel
 
-  // ---- combine: team sum, then segments in order, then objectives ---------
+  // ---- combine: team sum; one segment finishes here, several in k_mutate --
   const float2 gs = team_sum2(make_float2(acc1.x + acc1.y, acc2.x + acc2.y), TS);
+  __syncwarp();   // the team's mutations are visible to its leader
   if (active && lane == 0) {
-    float *ps = R.psum + (size_t)p * 2 * S;
-    ps[seg] = gs.x;
-    ps[S + seg] = gs.y;
-  }
-  // the warp barrier orders the team's writes (child rows, partials) before
-  // the leader's cumulative fence and its arrival
-  __syncwarp();
-  if (active && lane == 0) {
-    __threadfence();
-    const int prev = atomicAdd(&R.pcnt[p], 1);
-    if (prev == S - 1) finish_pair<PROB>(R, p, S, ch1, ch2);
+    if (TS == 32) {
+      float *ps = R.psum + (size_t)p * 2 * S;
+      ps[seg] = gs.x;
+      ps[S + seg] = gs.y;
+    } else {
+      finish_pair<PROB>(R, gs.x, gs.y, ch1, ch2);
+    }
   }
 }
 
@@ -499,6 +497,46 @@ RVEA_REPROB(k_reprob_dtlz1s, PROB_DTLZ1, true)
 RVEA_REPROB(k_reprob_dtlz2s, PROB_DTLZ2, true)
 RVEA_REPROB(k_reprob_neuros, PROB_NEURO, true)
 #undef RVEA_REPROB
+
+// Mutation and evaluation of the children of runs reproduced by 32-lane
+// teams (d > 1024), after their reproduction kernel: one thread per child
+// (draw index cd: child 1 of pair cd, or child 2 of pair cd - P), with the
+// same count-then-subset sites as the in-kernel pass; g is the pair's
+// segment partials in segment order plus the sites' term changes in draw
+// order; then the objectives and the ideal point.  Moving this tail out of
+// the reproduction kernel leaves its warps no serial per-pair chain and no
+// cross-warp arrival.  When every variable mutates (per-site probability
+// 1) the reproduction kernel has already mutated.
+template <int PROB>
+__device__ __forceinline__ void mutate_body(const BatchDir &dir) {
+  pdl_wait();      // the children of this generation
+  pdl_trigger();
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int cd = (blockIdx.x - dir.prefix[run]) * kMutThreads + threadIdx.x;
+  const int N = R.N, P = R.P;
+  if (cd >= N) return;
+  const int t = R.ctl->t;
+  int slot = R.child_slot[(t & 1) * N + cd];
+  if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); return; }
+  float dg = 0.0f;
+  if (R.T_m > 0 && R.T_m < (1u << 24))
+    dg = mutate_sites<PROB>(R, KeyRun{R.key0, R.key1}, cd, slot, t, 0, R.d);
+  if (PROB == PROB_NEURO) return;   // objectives come from the rollout kernel
+  const int S = R.nseg, p = cd < P ? cd : cd - P;
+  const float *ps = R.psum + (size_t)p * 2 * S + (cd < P ? 0 : S);
+  float g = 0.0f;
+  for (int q = 0; q < S; ++q) g += __ldcg(ps + q);
+  evaluate_child<PROB>(R, slot, g + dg);
+}
+#define RVEA_MUTATE(name, PROB)                                                            \
+  __global__ void __launch_bounds__(kMutThreads) name(const __grid_constant__ BatchDir dir) { \
+    mutate_body<PROB>(dir);                                                                \
+  }
+RVEA_MUTATE(k_mutate_dtlz1, PROB_DTLZ1)
+RVEA_MUTATE(k_mutate_dtlz2, PROB_DTLZ2)
+RVEA_MUTATE(k_mutate_neuro, PROB_NEURO)
+#undef RVEA_MUTATE
 
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
 // objectives.  DTLZ: x = L + (U-L) u24 from INIT (j/4, i, 0) word j%4.

@@ -15,6 +15,7 @@ namespace rvea {
 
 constexpr int kMaxM = 16;          // objectives
 constexpr int kReproThreads = 256; // CTA size of the reproduction kernel
+constexpr int kMutThreads = 128;   // CTA size of the mutation / evaluation kernel (one child a thread)
 constexpr int kLaneGroups = 8;     // 8-variable groups per lane per reproduction unit
 constexpr int kSelThreads = 128;   // selection CTA size (two solutions per thread)
 constexpr int kSelBlock = 2 * kSelThreads;   // solutions per selection work item
@@ -80,7 +81,6 @@ struct RunDesc {
   int *assoc;          // [n_comb]   vector of each solution, -1 if invalid
   int *surv;           // [N]        combined index kept by vector j, -1 if none
   float *psum;         // [P][2][nseg] partial g sums of the segments of each pair
-  int *pcnt;           // [P]        arrival counters of the segments of each pair
   int *blk_cnt;        // [n_comb/256] arrival counters of the selection blocks
   float *V32;          // [N][m4*4]  reference vectors, zero padded
   float *V32lo;        // [N][m]     V64 - V32 rounded to float (null: zero)

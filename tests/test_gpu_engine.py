@@ -68,11 +68,11 @@ def test_autotune_leaves_the_run_unchanged(orc):
     assert plan["repro_us"] > 0 and plan["sel_us"] > 0
     tuned.step(5)
     plain.step(5)
-    autotune(tuned, use_cache=False)     # mid-run, on an adaptation boundary's neighbour
+    plan = autotune(tuned, use_cache=False)   # mid-run, on an adaptation boundary's neighbour
     tuned.step(7)
     plain.step(7)
     _same(plain, tuned)
-    # the cache returns the same plan without timing
+    # the cache returns the shape's latest tuned plan without timing
     again = make_run(p)
     cached = autotune(again, use_cache=True)
     assert (cached["sel_mode"], cached["sel_per_sm"], cached["repro_staged"]) == \
