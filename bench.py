@@ -266,6 +266,7 @@ def main_batched(args, rank, world, local):
     ms_seq = e0.elapsed_time(e1)
     Kp = max(1, min(K, 20))
     phases = batch.step_profiled(Kp)
+    launches_per_step = batch.launches_per_step()
     batch.free()
     nb = batch_bytes(insts)
     hbm_peak, peak_kind = peaks()
@@ -320,7 +321,7 @@ def main_batched(args, rank, world, local):
         "setup_s": {"init": t_init, "autotune": t_tune},
         "cpu_baseline": cpu,
         "e2e": None,
-        "gpu_launches": K * 6,
+        "gpu_launches": K * launches_per_step,
         "clocks": sampler.summary() if sampler else None,
     }
     print(json.dumps(line), flush=True)
@@ -367,6 +368,7 @@ def main_neuro(args, rank, world, local):
     ms = e0.elapsed_time(e1)
     Kp = max(1, min(K, 5))
     phases = batch.step_profiled(Kp)
+    launches_per_step = batch.launches_per_step()
     for r in runs:
         r.sync_status()
     batch.free()
@@ -414,7 +416,7 @@ def main_neuro(args, rank, world, local):
                                     "gamma_tiles": phases[4] / Kp},
         "cpu_baseline": cpu,
         "e2e": None,
-        "gpu_launches": K * 7,
+        "gpu_launches": K * launches_per_step,
         "clocks": sampler.summary() if sampler else None,
     }
     print(json.dumps(line), flush=True)
@@ -648,7 +650,8 @@ def main():
     run.sync_status()
     p_adapt = max(1, int(kw["f_r"] * kw["t_max"] + 0.5))
     n_adapt = sum(1 for t in range(t_first, t_first + K) if t % p_adapt == 0)
-    launches = 3 * K + n_adapt
+    launches = (K - n_adapt) * run.launches_per_generation(False) + \
+        n_adapt * run.launches_per_generation(True)
     del run
 
     # ---- per-kernel device time (CUDA events around every launch) -----------
@@ -713,15 +716,17 @@ def main():
                    "l2": f"no flush: {2 * N * d * 4 / 1e6:.0f} MB moved per generation "
                          f"> 129 MB L2 (inputs larger than L2)",
                    "generations": f"t = {t_first}..{t_first + K - 1}"},
-        "roofline": {"kernel": "k_repro (mating+SBX+PM+DTLZ eval)", "bound": "hbm",
+        "roofline": {"kernel": "k_repro (mating + SBX + g-terms; mutation and evaluation "
+                               "in k_mutate when d > 1024)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": profiled_traffic(args.workload),
                      "algorithmic_bytes_per_launch": bytes_rep,
                      "avg_launch_ms": repro_ms,
                      "timing": f"CUDA events around each launch, {Kp} generations"},
-        "phase_ms_per_generation": {"repro": phases[0] / Kp, "select": phases[1] / Kp,
-                                    "finalize": phases[2] / Kp, "gamma": phases[3] / Kp},
+        "phase_ms_per_generation": {"repro": phases[0] / Kp, "mutate_eval": phases[4] / Kp,
+                                    "select": phases[1] / Kp, "finalize": phases[2] / Kp,
+                                    "gamma": phases[3] / Kp},
         "whole_generation_hbm_gbs": bytes_rep / (ms / K * 1e-3) / 1e9,
         "whole_generation_frac": bytes_rep / (ms / K * 1e-3) / 1e9 / hbm_peak,
         "cpu_baseline": cpu,

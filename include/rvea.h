@@ -182,6 +182,11 @@ rvea_status rvea_batch_create(rvea_run *const *runs, int n_runs, rvea_batch **ou
 /* Enqueue n_generations >= 0 batched generations on `cuda_stream`. */
 rvea_status rvea_batch_step(rvea_batch *batch, int n_generations, void *cuda_stream);
 
+/* Kernel launches of one batched generation (the kernel nodes of its graph;
+ * gamma and the tile tables launch every generation and act on their flag);
+ * -1 if batch is NULL. */
+int rvea_batch_launches_per_step(const rvea_batch *batch);
+
 /* As rvea_batch_step with direct launches (no graph) and CUDA events around
  * every phase; synchronous.  phase_ms[0..4] (n_phases >= 5) receive the
  * summed device time of: reproduction, pruned association, full-scan
@@ -220,11 +225,20 @@ int rvea_generation(const rvea_run *run);
 
 /* As rvea_step with direct launches, a CUDA event recorded on `cuda_stream`
  * around every kernel, and a synchronisation at the end; adds the measured
- * device milliseconds per phase into phase_ms[0..3] (reproduction+
- * evaluation, selection, finalize, gamma).  phase_ms: host, n_phases >= 4.
- * Same results as rvea_step. */
+ * device milliseconds per phase into phase_ms: [0] the reproduction kernel
+ * (with mutation and evaluation when d <= 1024), [1] selection, [2]
+ * finalize, [3] gamma and the tile table, [4] the kernels that finish the
+ * children after it (mutation and evaluation when d > 1024, the rollout
+ * evaluation of the neuroevolution problem).  With n_phases == 4, [4] is
+ * added into [0].  phase_ms: host, n_phases >= 4.  Same results as
+ * rvea_step. */
 rvea_status rvea_step_profiled(rvea_run *run, int n_generations, void *cuda_stream,
                                double *phase_ms, int n_phases);
+
+/* Kernel launches rvea_step enqueues for one generation of `run` (adapting:
+ * a generation with t % ceil(f_r t_max) == 0, which also rescales V); -1 if
+ * run is NULL. */
+int rvea_launches_per_generation(const rvea_run *run, int adapting);
 
 /* Full run state in slot order: X (N x d f32), F (N x m f32), valid (N u8),
  * V (N x m f64, current reference vectors), gamma (N f64).  Any output may

@@ -104,6 +104,8 @@ def lib():
         L.rvea_last_cuda_error.restype = C.c_char_p
         L.rvea_generation.argtypes = [vp]
         L.rvea_generation.restype = i32
+        L.rvea_launches_per_generation.argtypes = [vp, i32]
+        L.rvea_launches_per_generation.restype = i32
         L.rvea_step_profiled.argtypes = [vp, i32, vp, C.POINTER(C.c_double), i32]
         L.rvea_step_profiled.restype = i32
         L.rvea_export_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -132,6 +134,8 @@ def lib():
         L.rvea_batch_create.restype = i32
         L.rvea_batch_step.argtypes = [vp, i32, vp]
         L.rvea_batch_step.restype = i32
+        L.rvea_batch_launches_per_step.argtypes = [vp]
+        L.rvea_batch_launches_per_step.restype = i32
         L.rvea_batch_step_profiled.argtypes = [vp, i32, vp, C.POINTER(C.c_double), i32]
         L.rvea_batch_step_profiled.restype = i32
         L.rvea_batch_free.argtypes = [vp]

@@ -1179,6 +1179,7 @@ struct rvea_batch {
   std::vector<rvea_run *> runs;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int kernels = 0;   // kernel nodes of the captured generation
 };
 
 rvea_status rvea_batch_create(rvea_run *const *runs, int n_runs, rvea_batch **out) {
@@ -1205,6 +1206,18 @@ rvea_status rvea_batch_create(rvea_run *const *runs, int n_runs, rvea_batch **ou
     else if (e != cudaSuccess) s = RVEA_ERR_CUDA;
   }
   if (s == RVEA_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) s = RVEA_ERR_CUDA;
+  if (s == RVEA_OK) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) s = RVEA_ERR_CUDA;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (s == RVEA_OK && nn > 0 && cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess)
+      s = RVEA_ERR_CUDA;
+    for (size_t q = 0; q < nn && s == RVEA_OK; ++q) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nodes[q], &ty) != cudaSuccess) s = RVEA_ERR_CUDA;
+      else if (ty == cudaGraphNodeTypeKernel) ++b->kernels;
+    }
+  }
   if (g) cudaGraphDestroy(g);
   if (s != RVEA_OK) {
     cudaGetLastError();
@@ -1215,6 +1228,8 @@ rvea_status rvea_batch_create(rvea_run *const *runs, int n_runs, rvea_batch **ou
   *out = b;
   return RVEA_OK;
 }
+
+int rvea_batch_launches_per_step(const rvea_batch *b) { return b ? b->kernels : -1; }
 
 rvea_status rvea_batch_step(rvea_batch *b, int G, void *cuda_stream) {
   if (!b || G < 0) return RVEA_ERR_ARG;
@@ -1267,6 +1282,15 @@ void rvea_batch_free(rvea_batch *b) {
 
 int rvea_generation(const rvea_run *r) { return r ? r->t : -1; }
 
+int rvea_launches_per_generation(const rvea_run *r, int adapting) {
+  if (!r) return -1;
+  int n = 3;                                        // reproduction, selection, finalize
+  if (r->sh.team == 32) n += 1;                     // k_mutate
+  if (r->hd.problem == PROB_NEURO) n += 2;          // noise, rollout
+  if (adapting) n += 1 + (r->hd.ntiles > 0 ? 1 : 0);   // gamma, tile table
+  return n;
+}
+
 rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *phase_ms,
                                int n_phases) {
   if (!r || G < 0 || !phase_ms || n_phases < 4) return RVEA_ERR_ARG;
@@ -1275,7 +1299,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   for (int q = 0; q < n_phases; ++q) phase_ms[q] = 0.0;
   if (G == 0) return RVEA_OK;
   // events around every launch of every generation, on the launching stream
-  std::vector<cudaEvent_t> ev((size_t)G * 5);
+  std::vector<cudaEvent_t> ev((size_t)G * 6);
   for (auto &e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) {
       for (auto &x : ev) if (x) cudaEventDestroy(x);
@@ -1294,9 +1318,10 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   dir_single(dd, one, nullptr, nbd);
   const int nbg = std::min((r->sh.N + 31) / 32, 4 * kSMs);
   for (int g = 0; g < G && s == RVEA_OK; ++g) {
-    cudaEvent_t *e = &ev[(size_t)g * 5];
+    cudaEvent_t *e = &ev[(size_t)g * 6];
     cudaEventRecord(e[0], st);
     launch_repro1(r, dr, r->sh.n_repro, st);
+    cudaEventRecord(e[5], st);
     launch_mutate1(r, st);
     if (r->hd.problem == PROB_NEURO) {
       const int nb_noise = (r->hd.steps * r->hd.ns + 255) / 256;
@@ -1326,12 +1351,14 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     r->has_last_gen = true;
   }
   if (s == RVEA_OK) s = cuerr(cudaStreamSynchronize(st));
+  // e[0] reproduction e[5] children e[1] selection e[2] finalize e[3] gamma e[4]
+  const int from[5] = {0, 1, 2, 3, 5}, to[5] = {5, 2, 3, 4, 1};
   for (int g = 0; g < G && s == RVEA_OK; ++g) {
-    const cudaEvent_t *e = &ev[(size_t)g * 5];
-    for (int q = 0; q < 4; ++q) {
+    const cudaEvent_t *e = &ev[(size_t)g * 6];
+    for (int q = 0; q < 5; ++q) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, e[q], e[q + 1]) != cudaSuccess) { s = RVEA_ERR_CUDA; break; }
-      phase_ms[q] += ms;
+      if (cudaEventElapsedTime(&ms, e[from[q]], e[to[q]]) != cudaSuccess) { s = RVEA_ERR_CUDA; break; }
+      phase_ms[(q == 4 && n_phases < 5) ? 0 : q] += ms;
     }
   }
   for (auto &x : ev) cudaEventDestroy(x);

@@ -501,33 +501,109 @@ RVEA_REPROB(k_reprob_neuros, PROB_NEURO, true)
 // Mutation and evaluation of the children of runs reproduced by 32-lane
 // teams (d > 1024), after their reproduction kernel: one thread per child
 // (draw index cd: child 1 of pair cd, or child 2 of pair cd - P), with the
-// same count-then-subset sites as the in-kernel pass; g is the pair's
-// segment partials in segment order plus the sites' term changes in draw
-// order; then the objectives and the ideal point.  Moving this tail out of
-// the reproduction kernel leaves its warps no serial per-pair chain and no
-// cross-warp arrival.  When every variable mutates (per-site probability
+// same count-then-subset sites as mutate_sites; g is the pair's segment
+// partials in segment order plus the sites' term changes in draw order; then
+// the objectives and the ideal point.  Moving this tail out of the
+// reproduction kernel leaves its warps no serial per-pair chain and no
+// cross-warp arrival.  A warp first draws its 32 children's sites into
+// shared memory, then mutates them spread over its lanes (about one round of
+// 32 for one site per row on average), so a child with several sites does
+// not hold up the others.  When every variable mutates (per-site probability
 // 1) the reproduction kernel has already mutated.
+struct MutShared {
+  uint32_t j[kMutThreads / 32][32 * kMaxSites];   // site variable
+  float dg[kMutThreads / 32][32 * kMaxSites];     // term(new) - term(old)
+  uint8_t own[kMutThreads / 32][32 * kMaxSites];  // lane of the child
+  int slot[kMutThreads / 32][32];
+  unsigned zmin[kMutThreads / 32][kMaxM];
+};
+
 template <int PROB>
 __device__ __forceinline__ void mutate_body(const BatchDir &dir) {
   pdl_wait();      // the children of this generation
   pdl_trigger();
+  __shared__ MutShared sh;
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
-  const int cd = (blockIdx.x - dir.prefix[run]) * kMutThreads + threadIdx.x;
-  const int N = R.N, P = R.P;
-  if (cd >= N) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cd0 = (blockIdx.x - dir.prefix[run]) * kMutThreads + warp * 32, cd = cd0 + lane;
+  const int N = R.N, P = R.P, m = R.m, d = R.d;
   const int t = R.ctl->t;
-  int slot = R.child_slot[(t & 1) * N + cd];
-  if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); return; }
-  float dg = 0.0f;
-  if (R.T_m > 0 && R.T_m < (1u << 24))
-    dg = mutate_sites<PROB>(R, KeyRun{R.key0, R.key1}, cd, slot, t, 0, R.d);
+  const KeyRun kr{R.key0, R.key1};
+  int slot = -1;
+  if (cd < N) {
+    slot = R.child_slot[(t & 1) * N + cd];
+    if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); slot = -1; }
+  }
+  sh.slot[warp][lane] = slot;
+  // ---- the sites: count k ~ Binomial(d, q), then Floyd's subset -----------
+  int k = 0;
+  if (slot >= 0 && R.T_m > 0 && R.T_m < (1u << 24)) {
+    uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+    const int nthr = R.n_mthr;
+    while (k < nthr && w.x >= R.mthr[k]) ++k;
+  }
+  int incl = k;   // warp prefix of the counts: this child's entries start at off
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int off = incl - k, total = __shfl_sync(0xffffffffu, incl, 31);
+  if (k > 0) {
+    uint32_t *const js = sh.j[warp] + off;
+    uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+    for (int i = 0; i < k; ++i) {
+      const int e = i + 1;
+      if ((e & 3) == 0) w = philox_k((uint32_t)(e >> 2), (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+      const uint32_t J = (uint32_t)(d - k + i);
+      uint32_t r = __umulhi(word(w, e & 3), J + 1u);
+      for (int l = 0; l < i; ++l)
+        if (js[l] == r) { r = J; break; }
+      js[i] = r;
+      sh.own[warp][off + i] = (uint8_t)lane;
+    }
+  }
+  __syncwarp();
+  // ---- the mutations, one site a lane ------------------------------------
+  for (int e = lane; e < total; e += 32) {
+    const int o = sh.own[warp][e];
+    const uint32_t j = sh.j[warp][e];
+    float *const px = R.X + (size_t)sh.slot[warp][o] * R.d_pad + j;
+    const float x = __ldcg(px);
+    const uint4 w = philox_k(j, (uint32_t)(cd0 + o), (uint32_t)t, TAG_MUTMAG, kr);
+    const float xn = poly_mutate(x, u24f(w.y), R.L, R.U, R.eta_m);
+    __stcg(px, xn);
+    sh.dg[warp][e] = (PROB != PROB_NEURO && (int)j >= m - 1)
+                         ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f) : 0.0f;
+  }
+  __syncwarp();   // the mutated rows and term changes are visible to the warp
   if (PROB == PROB_NEURO) return;   // objectives come from the rollout kernel
-  const int S = R.nseg, p = cd < P ? cd : cd - P;
-  const float *ps = R.psum + (size_t)p * 2 * S + (cd < P ? 0 : S);
-  float g = 0.0f;
-  for (int q = 0; q < S; ++q) g += __ldcg(ps + q);
-  evaluate_child<PROB>(R, slot, g + dg);
+  float f[kMaxM];
+  if (slot >= 0) {
+    float dg = 0.0f;
+    for (int i = 0; i < k; ++i) dg += sh.dg[warp][off + i];
+    const int S = R.nseg, p = cd < P ? cd : cd - P;
+    const float *ps = R.psum + (size_t)p * 2 * S + (cd < P ? 0 : S);
+    float g = 0.0f;
+    for (int q = 0; q < S; ++q) g += __ldcg(ps + q);
+    const float *row = R.X + (size_t)slot * R.d_pad;
+    float head[kMaxM];
+    for (int jj = 0; jj < m - 1; ++jj) head[jj] = __ldcg(row + jj);
+    dtlz_objectives(PROB, m, g + dg, head, f);
+    for (int kk = 0; kk < m; ++kk) R.F[(size_t)kk * 2 * N + slot] = f[kk];
+  }
+  // the ideal point: a CTA's minimum per objective, then one atomic each
+  for (int kk = 0; kk < m; ++kk) {
+    const unsigned v = __reduce_min_sync(0xffffffffu, slot >= 0 ? f2ord(f[kk]) : 0xFFFFFFFFu);
+    if (lane == 0) sh.zmin[warp][kk] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    unsigned v = 0xFFFFFFFFu;
+    for (int w = 0; w < kMutThreads / 32; ++w) v = min(v, sh.zmin[w][threadIdx.x]);
+    if (v != 0xFFFFFFFFu) atomicMin(&R.ctl->zkey[threadIdx.x], v);
+  }
 }
 #define RVEA_MUTATE(name, PROB)                                                            \
   __global__ void __launch_bounds__(kMutThreads) name(const __grid_constant__ BatchDir dir) { \

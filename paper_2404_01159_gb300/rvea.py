@@ -108,11 +108,16 @@ class Run:
 
     def step_profiled(self, generations: int, stream=None):
         """Run generations with per-kernel CUDA events; returns the summed
-        device milliseconds of (reproduction, selection, finalize, gamma)."""
-        ms = (C.c_double * 4)()
+        device milliseconds of (reproduction kernel, selection, finalize,
+        gamma, the kernels finishing the children after reproduction)."""
+        ms = (C.c_double * 5)()
         check(lib().rvea_step_profiled(self._h, int(generations), C.c_void_p(_stream(stream)),
-                                       ms, 4), "rvea_step_profiled")
+                                       ms, 5), "rvea_step_profiled")
         return [float(x) for x in ms]
+
+    def launches_per_generation(self, adapting: bool) -> int:
+        """Kernel launches one generation enqueues (adapting: it rescales V)."""
+        return int(lib().rvea_launches_per_generation(self._h, 1 if adapting else 0))
 
     def sync_status(self) -> None:
         check(lib().rvea_sync_status(self._h), "device status")
@@ -218,6 +223,10 @@ class Batch:
     def step(self, generations: int = 1, stream=None) -> None:
         check(lib().rvea_batch_step(self._h, int(generations), C.c_void_p(_stream(stream))),
               "rvea_batch_step")
+
+    def launches_per_step(self) -> int:
+        """Kernel launches of one batched generation (nodes of its graph)."""
+        return int(lib().rvea_batch_launches_per_step(self._h))
 
     def step_profiled(self, generations: int, stream=None) -> list:
         """Device ms summed over `generations` per phase: reproduction, pruned

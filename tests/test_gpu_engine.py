@@ -101,3 +101,23 @@ def test_batch_graph_equals_alone(orc):
         _same(ra, rb)
         rb.sync_status()
     b.free()
+
+
+def test_launch_counts(orc):
+    """The launches a generation enqueues: reproduction, [mutation and
+    evaluation when d > 1024], selection, finalize, [gamma and the tile table
+    when it adapts]; a batched generation counts the kernel nodes of its
+    graph."""
+    from paper_2404_01159_gb300 import Batch
+    big = make_run(params(orc, 3, 2500, 1275, 49, 1, t_max=40, seed=4))
+    small = make_run(params(orc, 3, 12, 105, 13, 0, t_max=40, seed=5))
+    assert big.launches_per_generation(False) == 4
+    assert big.launches_per_generation(True) in (5, 6)
+    assert small.launches_per_generation(False) == 3
+    assert small.launches_per_generation(True) in (4, 5)
+    b = Batch([big, small])
+    try:
+        # >= 1 reproduction group, 1 mutation group, >= 1 selection, finalize, gamma
+        assert 5 <= b.launches_per_step() <= 9
+    finally:
+        b.free()
