@@ -508,11 +508,15 @@ RVEA_REPROB(k_reprob_neuros, PROB_NEURO, true)
 // cross-warp arrival.  A warp first draws its 32 children's sites into
 // shared memory, then mutates them spread over its lanes (about one round of
 // 32 for one site per row on average), so a child with several sites does
-// not hold up the others.  When every variable mutates (per-site probability
-// 1) the reproduction kernel has already mutated.
+// not hold up the others.  Everything that does not read this generation's
+// children (slots, site draws, magnitudes) runs before the wait for the
+// reproduction kernel, overlapping its tail; the kernel lets its successor
+// launch at once (the successor's own wait still orders it after this grid,
+// and so after the reproduction kernel).  When every variable mutates
+// (per-site probability 1) the reproduction kernel has already mutated.
 struct MutShared {
   uint32_t j[kMutThreads / 32][32 * kMaxSites];   // site variable
-  float dg[kMutThreads / 32][32 * kMaxSites];     // term(new) - term(old)
+  float dg[kMutThreads / 32][32 * kMaxSites];     // magnitude M, then term(new) - term(old)
   uint8_t own[kMutThreads / 32][32 * kMaxSites];  // lane of the child
   int slot[kMutThreads / 32][32];
   unsigned zmin[kMutThreads / 32][kMaxM];
@@ -520,7 +524,6 @@ struct MutShared {
 
 template <int PROB>
 __device__ __forceinline__ void mutate_body(const BatchDir &dir) {
-  pdl_wait();      // the children of this generation
   pdl_trigger();
   __shared__ MutShared sh;
   const int run = dir_find(dir, blockIdx.x);
@@ -528,11 +531,14 @@ __device__ __forceinline__ void mutate_body(const BatchDir &dir) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cd0 = (blockIdx.x - dir.prefix[run]) * kMutThreads + warp * 32, cd = cd0 + lane;
   const int N = R.N, P = R.P, m = R.m, d = R.d;
-  const int t = R.ctl->t;
+  // generation counter and child slots: written by the previous generation's
+  // finalize, which completed before the reproduction kernel (this grid's
+  // predecessor) passed its own wait; read through L2
+  const int t = __ldcg(&R.ctl->t);
   const KeyRun kr{R.key0, R.key1};
   int slot = -1;
   if (cd < N) {
-    slot = R.child_slot[(t & 1) * N + cd];
+    slot = __ldcg(R.child_slot + (t & 1) * N + cd);
     if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); slot = -1; }
   }
   sh.slot[warp][lane] = slot;
@@ -565,14 +571,20 @@ __device__ __forceinline__ void mutate_body(const BatchDir &dir) {
     }
   }
   __syncwarp();
+  for (int e = lane; e < total; e += 32) {   // the magnitudes
+    const uint4 w = philox_k(sh.j[warp][e], (uint32_t)(cd0 + sh.own[warp][e]), (uint32_t)t,
+                             TAG_MUTMAG, kr);
+    sh.dg[warp][e] = u24f(w.y);
+  }
+  __syncwarp();
+  pdl_wait();      // the crossed children of this generation
   // ---- the mutations, one site a lane ------------------------------------
   for (int e = lane; e < total; e += 32) {
     const int o = sh.own[warp][e];
     const uint32_t j = sh.j[warp][e];
     float *const px = R.X + (size_t)sh.slot[warp][o] * R.d_pad + j;
     const float x = __ldcg(px);
-    const uint4 w = philox_k(j, (uint32_t)(cd0 + o), (uint32_t)t, TAG_MUTMAG, kr);
-    const float xn = poly_mutate(x, u24f(w.y), R.L, R.U, R.eta_m);
+    const float xn = poly_mutate(x, sh.dg[warp][e], R.L, R.U, R.eta_m);
     __stcg(px, xn);
     sh.dg[warp][e] = (PROB != PROB_NEURO && (int)j >= m - 1)
                          ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f) : 0.0f;

@@ -321,7 +321,9 @@ __device__ __forceinline__ float apd_chord(const float *fp, int m, const float *
 // .wait: the predecessor has completed and its writes are visible) before it
 // reads anything the predecessor wrote, and only then lets its own successor
 // start (launch_dependents).  Waiting before triggering keeps the ordering
-// transitive.  In a kernel launched without the attribute both are no-ops.
+// transitive; a kernel that triggers first (k_mutate) reads nothing that its
+// predecessor writes before its wait.  In a kernel launched without the
+// attribute both are no-ops.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
