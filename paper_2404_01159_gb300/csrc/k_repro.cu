@@ -220,30 +220,35 @@ __device__ __forceinline__ void cross4(const float4 xa, const float4 xb, int Q, 
 
 // The same for a float4 that holds some of x_1..x_{m-1} (j < mh, kept out
 // of g) or reaches past the last variable (j >= d): g-terms per variable.
+// The accumulators travel by value (no address taken, so they stay in
+// registers in the caller's loops).
+struct Acc2 {
+  float2 a1, a2;
+};
 template <int PROB>
-__device__ __noinline__ void cross4_edge(const float4 xa, const float4 xb, int Q, int p, int t,
+__device__ __noinline__ Acc2 cross4_edge(const float4 xa, const float4 xb, int Q, int p, int t,
                                          bool nocross, float ie, float L, float U, const KeyRun kp,
-                                         float4 *y1, float4 *y2, float2 &acc1, float2 &acc2,
-                                         int mh, int d) {
+                                         float4 *y1, float4 *y2, Acc2 acc, int mh, int d) {
   float2 z1 = make_float2(0.f, 0.f), z2 = z1;
   float4 c1, c2;
   cross4<PROB_NEURO>(xa, xb, Q, p, t, nocross, ie, L, U, kp, &c1, &c2, z1, z2);
   *y1 = c1;
   if (y2) *y2 = c2;
-  if (PROB == PROB_NEURO) return;
+  if (PROB == PROB_NEURO) return acc;
   const float u1[4] = {c1.x, c1.y, c1.z, c1.w}, u2[4] = {c2.x, c2.y, c2.z, c2.w};
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const int j = 4 * Q + v;
     if (j < mh || j >= d) continue;
     if (v & 1) {
-      acc1.y = g_term1(PROB, u1[v], acc1.y);
-      acc2.y = g_term1(PROB, u2[v], acc2.y);
+      acc.a1.y = g_term1(PROB, u1[v], acc.a1.y);
+      acc.a2.y = g_term1(PROB, u2[v], acc.a2.y);
     } else {
-      acc1.x = g_term1(PROB, u1[v], acc1.x);
-      acc2.x = g_term1(PROB, u2[v], acc2.x);
+      acc.a1.x = g_term1(PROB, u1[v], acc.a1.x);
+      acc.a2.x = g_term1(PROB, u2[v], acc.a2.x);
     }
   }
+  return acc;
 }
 
 // Mutation of one crossed variable in place; returns term(new) - term(old).
@@ -364,9 +369,6 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   const uint32_t rq = (uint32_t)R.d_pad >> 2;      // float4s per row
   const uint32_t q1 = (uint32_t)ch1 * rq, q2 = has2 ? (uint32_t)ch2 * rq : 0u;
   const float L = R.L, U = R.U, ie = R.inv_eta_c1;
-  // the keys as the out-of-line functions take them (a value, not a
-  // reference to the parameter block)
-  const KeyRun kr{R.key0, R.key1};
   // float4s [Qs, Qe) hold neither x_1..x_{m-1} nor variables past d
   const int mh = R.m - 1, Qs = (mh + 3) >> 2, Qe = d >> 2;
 
@@ -415,9 +417,13 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
           cross4<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie, L, U, kp, y1 + qi,
                        y2 ? y2 + qi : nullptr, acc1, acc2);
       } else {
-        for (int qi = wl; qi < n4; qi += 32)
-          cross4_edge<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie, L, U, kr,
-                            y1 + qi, y2 ? y2 + qi : nullptr, acc1, acc2, mh, d);
+        for (int qi = wl; qi < n4; qi += 32) {
+          const Acc2 a = cross4_edge<PROB>(sa[qi], sa[64 + qi], 2 * gs + qi, p, t, nocross, ie,
+                                           L, U, KeyRun{R.key0, R.key1}, y1 + qi,
+                                           y2 ? y2 + qi : nullptr, Acc2{acc1, acc2}, mh, d);
+          acc1 = a.a1;
+          acc2 = a.a2;
+        }
       }
       __syncwarp();
     }
@@ -433,9 +439,13 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
       if (Q >= Qs && Q < Qe)
         cross4<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kp,
                      X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2);
-      else
-        cross4_edge<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross, ie, L, U, kr,
-                          X4 + q1 + Q, has2 ? X4 + q2 + Q : nullptr, acc1, acc2, mh, d);
+      else {
+        const Acc2 a = cross4_edge<PROB>(__ldg(X4 + o1 + Q), __ldg(X4 + o2 + Q), Q, p, t, nocross,
+                                         ie, L, U, KeyRun{R.key0, R.key1}, X4 + q1 + Q,
+                                         has2 ? X4 + q2 + Q : nullptr, Acc2{acc1, acc2}, mh, d);
+        acc1 = a.a1;
+        acc2 = a.a2;
+      }
     }
   }
   // ---- mutation pass: the sites of this segment ----------------------------
@@ -445,8 +455,8 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   if (active && R.T_m > 0 && (TS < 32 || R.T_m >= (1u << 24))) {
     for (int c = lane; c < 2; c += TS) {
       if (c == 1 && !has2) break;
-      const float dg = mutate_sites<PROB>(R, kr, c ? p + P : p, c ? ch2 : ch1, t, 8 * g0,
-                                          8 * gE);
+      const float dg = mutate_sites<PROB>(R, KeyRun{R.key0, R.key1}, c ? p + P : p,
+                                          c ? ch2 : ch1, t, 8 * g0, 8 * gE);
       if (c == 0) acc1.x += dg; else acc2.x += dg;
     }
   }
