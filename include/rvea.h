@@ -89,7 +89,8 @@ typedef struct {
     double eta_m;     /* mutation distribution index xi, > 0                 */
     double p_c;       /* crossover probability per pair, [0,1]               */
     double p_m;       /* mutation rate: per-site probability p_m / d, >= 0   */
-    double lower;     /* box [lower, upper] of every decision variable       */
+    double lower;     /* box [lower, upper] of every decision variable; the
+                         DTLZ problems require [0, 1], their domain          */
     double upper;
     uint64_t seed;    /* Philox4x32-10 key                                   */
     const rvea_neuro_dynamics *neuro;   /* required iff problem == NEURO     */
@@ -116,7 +117,8 @@ rvea_status rvea_init(int m, int d, int N, int H, double alpha, double f_r,
                       int problem, int t_max, void *dev_workspace, size_t bytes,
                       void *cuda_stream, rvea_run **out);
 
-/* As rvea_init with every parameter explicit (needed for the rollout). */
+/* As rvea_init with every parameter explicit (needed for the rollout).
+ * Also RVEA_ERR_ARG for a DTLZ problem on a box other than [0, 1]. */
 rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t bytes,
                          void *cuda_stream, rvea_run **out);
 

@@ -705,6 +705,8 @@ rvea_status validate(const rvea_config *c) {
     return RVEA_ERR_ARG;
   // mutation: up to 8 expected sites per row (the count is capped at 32), or every site
   if (c->p_m > 8.0 && c->p_m < (double)c->d) return RVEA_ERR_ARG;
+  // the DTLZ problems are defined on the unit box
+  if (c->problem != PROB_NEURO && (c->lower != 0.0 || c->upper != 1.0)) return RVEA_ERR_ARG;
   if (c->problem < 0 || c->problem > 2) return RVEA_ERR_ARG;
   if (c->problem == RVEA_NEURO_LINEAR) {
     // the rollout's shape: h1 = h2 = 64 (the tensor-core tiling), ns <= 32

@@ -186,29 +186,40 @@ __device__ __forceinline__ float sbx_B(uint32_t q, bool nocross, float ie) {
 
 // Children of two adjacent variables: with s = x1 + x2 and e = x1 - x2,
 // c1 = ((1+B) x1 + (1-B) x2) / 2 = (s + B e) / 2 and c2 = s - c1, clipped to
-// [L, U].  Equal parents give equal children exactly.
+// [L, U].  Equal parents give equal children exactly.  UNIT: the box is
+// [0, 1] (the DTLZ problems), where the clip is the saturation modifier of
+// the operation that makes each child, one instruction instead of three.
+template <bool UNIT>
 __device__ __forceinline__ void sbx_pair(float2 x1, float2 x2, float2 B, float L, float U,
                                          float2 &c1, float2 &c2) {
   const float2 sm = add2(x1, x2), df = sub2(x1, x2);
-  c1 = mul2(splat2(0.5f), fma2(B, df, sm));
-  c2 = sub2(sm, c1);
-  c1 = make_float2(clampf(c1.x, L, U), clampf(c1.y, L, U));
-  c2 = make_float2(clampf(c2.x, L, U), clampf(c2.y, L, U));
+  const float2 tt = fma2(B, df, sm);
+  const float2 c1u = mul2(splat2(0.5f), tt);
+  if (UNIT) {
+    c1 = make_float2(__saturatef(0.5f * tt.x), __saturatef(0.5f * tt.y));
+    c2 = make_float2(__saturatef(sm.x - c1u.x), __saturatef(sm.y - c1u.y));
+  } else {
+    const float2 c2u = sub2(sm, c1u);
+    c1 = make_float2(clampf(c1u.x, L, U), clampf(c1u.y, L, U));
+    c2 = make_float2(clampf(c2u.x, L, U), clampf(c2u.y, L, U));
+  }
 }
 
 // Main-pass work on four adjacent variables (float4 Q of the row) of both
 // children: SBX from Philox SBX (Q, p, t), clip, store, accumulate g-terms.
-template <int PROB, class KP>
+// (EVAL false: without the g-terms.)  The DTLZ problems live on the unit box.
+template <int PROB, class KP, bool EVAL = true>
 __device__ __forceinline__ void cross4(const float4 xa, const float4 xb, int Q, int p, int t,
                                        bool nocross, float ie, float L, float U, const KP &kp,
                                        float4 *y1, float4 *y2, float2 &acc1, float2 &acc2) {
+  constexpr bool kUnit = PROB != PROB_NEURO;
   const uint4 r = philox_k((uint32_t)Q, (uint32_t)p, (uint32_t)t, TAG_SBX, kp);
   float2 a0, a1, b0, b1;   // children 1 and 2, variables (0,1) and (2,3)
-  sbx_pair(make_float2(xa.x, xa.y), make_float2(xb.x, xb.y),
-           make_float2(sbx_B(r.x, nocross, ie), sbx_B(r.y, nocross, ie)), L, U, a0, b0);
-  sbx_pair(make_float2(xa.z, xa.w), make_float2(xb.z, xb.w),
-           make_float2(sbx_B(r.z, nocross, ie), sbx_B(r.w, nocross, ie)), L, U, a1, b1);
-  if (PROB != PROB_NEURO) {
+  sbx_pair<kUnit>(make_float2(xa.x, xa.y), make_float2(xb.x, xb.y),
+                  make_float2(sbx_B(r.x, nocross, ie), sbx_B(r.y, nocross, ie)), L, U, a0, b0);
+  sbx_pair<kUnit>(make_float2(xa.z, xa.w), make_float2(xb.z, xb.w),
+                  make_float2(sbx_B(r.z, nocross, ie), sbx_B(r.w, nocross, ie)), L, U, a1, b1);
+  if (EVAL && PROB != PROB_NEURO) {
     acc1 = g_terms2(PROB, a0, acc1);
     acc1 = g_terms2(PROB, a1, acc1);
     acc2 = g_terms2(PROB, b0, acc2);
@@ -231,7 +242,7 @@ __device__ __noinline__ Acc2 cross4_edge(const float4 xa, const float4 xb, int Q
                                          float4 *y1, float4 *y2, Acc2 acc, int mh, int d) {
   float2 z1 = make_float2(0.f, 0.f), z2 = z1;
   float4 c1, c2;
-  cross4<PROB_NEURO>(xa, xb, Q, p, t, nocross, ie, L, U, kp, &c1, &c2, z1, z2);
+  cross4<PROB, KeyRun, false>(xa, xb, Q, p, t, nocross, ie, L, U, kp, &c1, &c2, z1, z2);
   *y1 = c1;
   if (y2) *y2 = c2;
   if (PROB == PROB_NEURO) return acc;

@@ -73,3 +73,19 @@ def test_init_rejects_bad_arguments_without_gpu(native):
     assert init(3, 12, 105, 13, eta=0.0) == native.ERR_ARG
     assert init(3, 12, 105, 13, problem=7) == native.ERR_ARG
     assert not h.value
+
+
+def test_init_ex_requires_the_unit_box_for_dtlz(native):
+    """The DTLZ problems are defined on [0, 1]^d: another box is refused
+    before any device work (the reproduction kernels clip by saturation)."""
+    L = native.lib()
+    h = C.c_void_p()
+    ws = C.c_void_p(1 << 20)   # never dereferenced: validation fails first
+    cfg = native.Config(m=3, d=12, N=105, H=13, problem=0, t_max=100, alpha=2.0, f_r=0.1,
+                        eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, lower=-1.0, upper=1.0,
+                        seed=0, neuro=None)
+    assert L.rvea_init_ex(C.byref(cfg), ws, 1 << 30, None, C.byref(h)) == native.ERR_ARG
+    cfg.problem, cfg.lower = 1, 0.0
+    cfg.upper = 2.0
+    assert L.rvea_init_ex(C.byref(cfg), ws, 1 << 30, None, C.byref(h)) == native.ERR_ARG
+    assert not h.value
