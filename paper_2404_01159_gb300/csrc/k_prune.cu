@@ -17,6 +17,13 @@
 // keeping the larger dot and, on equal dots, the smaller vector index.  The
 // result is therefore the full scan's result bit for bit, found after
 // scanning ~2 tiles instead of all of them (lattice of 9870 vectors, m = 3).
+// The test itself needs f'.c of every tile, computed in the first pass (the
+// closest centre); a lane keeps its kPruneKeep largest ones and the largest of
+// the rest.  Every threshold (1) is at least
+//   min(B, B cmin) - S smax - slack   (cmin: smallest cos(rho) of the run,
+//                                       smax: largest sin(rho)),
+// so when the rest stay below that bound (less a rounding margin) only the
+// kept tiles can pass, and the second pass tests those alone.
 //
 // One persistent CTA per SM stages the tile-ordered vectors and the tile
 // table in shared memory with TMA bulk copies; its warps take four solutions
@@ -28,6 +35,7 @@ namespace rvea {
 
 constexpr int kPruneThreads = 1024;
 constexpr int kPruneCand = 4;   // candidate tiles kept per lane before the fallback
+constexpr int kPruneKeep = 4;   // largest centre dots a lane keeps from the first pass
 
 // f'.v in the fixed order of the full scan: first product, then fma over k.
 template <int M>
@@ -63,7 +71,7 @@ __device__ __forceinline__ T tld(const T *p) {
 template <int M, bool G>
 __device__ __forceinline__ void prune_group(const RunDesc &R, int base, const float4 *sV,
                                             const float4 *sC, const float2 *sCS, const int2 *sR,
-                                            const float *z, float pen) {
+                                            const float *z, float pen, float2 cs_bound) {
   const int lane = threadIdx.x & 31, sub = lane & 7;
   const int T = R.ntiles, N = R.N, n = R.n_comb;
   const int t_gen = R.ctl->t;
@@ -89,13 +97,34 @@ __device__ __forceinline__ void prune_group(const RunDesc &R, int base, const fl
     const bool live = slot >= 0 && nf > 0.0f;
     const int TT = live ? T : 0;
 
-    // pass 1: the tile whose centre is closest in angle
-    float dc1 = -INFINITY;
-    int t1 = 0;
+    // pass 1: the tile whose centre is closest in angle; the lane's
+    // kPruneKeep largest centre dots (descending) and the largest of the rest
+    float kd[kPruneKeep];
+    int kt[kPruneKeep];
+#pragma unroll
+    for (int c = 0; c < kPruneKeep; ++c) { kd[c] = -INFINITY; kt[c] = 0; }
+    float rest = -INFINITY;
     for (int t = sub; t < TT; t += 8) {
       const float dc = pdot<M>(f, tld<G>(sC + t));
-      if (dc > dc1) { dc1 = dc; t1 = t; }
+      if (dc > kd[kPruneKeep - 1]) {
+        rest = fmaxf(rest, kd[kPruneKeep - 1]);
+        float vd = dc;
+        int vt = t;
+#pragma unroll
+        for (int c = 0; c < kPruneKeep; ++c) {   // insertion: strict, so equal dots keep order
+          if (vd > kd[c]) {
+            const float od = kd[c];
+            const int ot = kt[c];
+            kd[c] = vd; kt[c] = vt;
+            vd = od; vt = ot;
+          }
+        }
+      } else {
+        rest = fmaxf(rest, dc);
+      }
     }
+    float dc1 = kd[0];
+    int t1 = kt[0];
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) {
       const float od = __shfl_xor_sync(0xffffffffu, dc1, off);
@@ -119,11 +148,28 @@ __device__ __forceinline__ void prune_group(const RunDesc &R, int base, const fl
     const float Bn = (best - 1e-6f * nf) * (1.0f - 4e-7f);
     const float Sn = sqrtf(fmaxf(0.0f, (nf - Bn) + 4e-7f * nf) * (nf + fabsf(Bn)));
     const float slack = 3e-6f * nf;
+    // a lower bound of every tile's threshold, less the rounding of the
+    // thresholds' two fmas and of the bound itself
+    const float lb = fminf(Bn, Bn * cs_bound.x) - Sn * cs_bound.y - slack -
+                     1e-6f * (fabsf(Bn) + Sn + slack);
     // pass 2: tiles that may hold a larger (or equal) dot
     int cand[kPruneCand];
     int nc = 0;
     bool over = false;
-    for (int t = sub; t < TT; t += 8) {
+    if (rest < lb) {   // only kept tiles can pass
+#pragma unroll
+      for (int k = 0; k < kPruneKeep; ++k) {
+        const int t = kt[k];
+        if (kd[k] == -INFINITY || t == t1) continue;
+        const float2 cs = tld<G>(sCS + t);
+        if (kd[k] >= fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack))) {
+#pragma unroll
+          for (int c = 0; c < kPruneCand; ++c)
+            if (c == nc) cand[c] = t;
+          ++nc;
+        }
+      }
+    } else for (int t = sub; t < TT; t += 8) {
       const float2 cs = tld<G>(sCS + t);
       const float thr = fmaf(Bn, cs.x, fmaf(-Sn, cs.y, -slack));
       if (t != t1 && pdot<M>(f, tld<G>(sC + t)) >= thr) {
@@ -137,18 +183,29 @@ __device__ __forceinline__ void prune_group(const RunDesc &R, int base, const fl
         }
       }
     }
-    // scan the candidates in lockstep (same instructions, per-lane tiles)
+    // scan the candidates: the union of the 8 lanes' lists, each tile split
+    // over the solution's 8 lanes (members sub, sub + 8, ...); every group
+    // of 8 walks its own list, the warp steps until all are done
     int ncmax = nc;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) ncmax = max(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, off));
+    const int gbase = lane & 24;
 #pragma unroll
     for (int c = 0; c < kPruneCand; ++c) {
       if (c >= ncmax) break;
-      if (c < nc) {
-        const int2 rg = tld<G>(sR + cand[c]);
-        for (int q = 0; q < rg.y; ++q) {
-          const float4 v = tld<G>(sV + rg.x + q);
-          keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
+      const int mine = c < nc ? cand[c] : -1;
+      unsigned m = (__ballot_sync(0xffffffffu, c < nc) >> gbase) & 0xFFu;
+      while (__any_sync(0xffffffffu, m != 0u)) {
+        const bool had = m != 0u;
+        const int src = had ? __ffs(m) - 1 : 0;
+        m &= m - 1u;
+        const int t = __shfl_sync(0xffffffffu, mine, gbase | src);
+        if (had && t >= 0) {
+          const int2 rg = tld<G>(sR + t);
+          for (int q = sub; q < rg.y; q += 8) {
+            const float4 v = tld<G>(sV + rg.x + q);
+            keep(pdot<M>(f, v), vidx<M>(R, v, rg.x + q), best, bj);
+          }
         }
       }
     }
@@ -187,11 +244,33 @@ __device__ __forceinline__ void prune_group(const RunDesc &R, int base, const fl
   }
 }
 
+// (smallest cos(rho), largest sin(rho)) over the T tiles of the staged
+// table; a barrier for the whole CTA.  (1, 0) when there are no tiles.
+__device__ __forceinline__ float2 tile_bounds(const float2 *sCS, int T) {
+  __shared__ unsigned s_b[2];
+  if (threadIdx.x == 0) { s_b[0] = 0xFFFFFFFFu; s_b[1] = 0u; }
+  __syncthreads();
+  unsigned lo = 0xFFFFFFFFu, hi = 0u;
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    const float2 cs = sCS[t];
+    lo = min(lo, f2ord(cs.x));
+    hi = max(hi, f2ord(cs.y));
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&s_b[0], lo);
+    atomicMax(&s_b[1], hi);
+  }
+  __syncthreads();
+  return T > 0 ? make_float2(ord2f(s_b[0]), ord2f(s_b[1])) : make_float2(1.0f, 0.0f);
+}
+
 // One run, tables in shared memory: warps take four solutions at a time from
 // the run's work counter.
 template <int M>
 __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
-                           const float2 *sCS, const int2 *sR) {
+                           const float2 *sCS, const int2 *sR, float2 csb) {
   const int lane = threadIdx.x & 31;
   const float pen = (float)R.m * powf((float)R.ctl->t / (float)R.t_max, R.alpha);
   float z[4];
@@ -202,7 +281,7 @@ __device__ void prune_loop(const RunDesc &R, const float4 *sV, const float4 *sC,
     if (lane == 0) base = atomicAdd(&R.ctl->sel_cnt, 4);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= R.n_comb) break;
-    prune_group<M, false>(R, base, sV, sC, sCS, sR, z, pen);
+    prune_group<M, false>(R, base, sV, sC, sCS, sR, z, pen, csb);
   }
 }
 
@@ -239,12 +318,13 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
   }
   // the tables (k_tiles, earlier than the predecessor) are staged above; the
   // population's objectives come from the reproduction kernel
+  const float2 csb = tile_bounds(sCS, T);
   pdl_wait();
   pdl_trigger();
   switch (R.m) {
-    case 2: prune_loop<2>(R, sV, sC, sCS, sR); break;
-    case 3: prune_loop<3>(R, sV, sC, sCS, sR); break;
-    default: prune_loop<4>(R, sV, sC, sCS, sR); break;
+    case 2: prune_loop<2>(R, sV, sC, sCS, sR, csb); break;
+    case 3: prune_loop<3>(R, sV, sC, sCS, sR, csb); break;
+    default: prune_loop<4>(R, sV, sC, sCS, sR, csb); break;
   }
 }
 
@@ -270,6 +350,7 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const 
   const int total = dir.prefix[dir.n];
   int cached = -1;
   uint32_t phase = 0;
+  float2 csb = make_float2(1.0f, 0.0f);
   for (;;) {
     __syncthreads();   // the previous chunk is done with the tables
     if (threadIdx.x == 0) s_chunk = atomicAdd(&cc->sel_cnt, 1);
@@ -305,6 +386,7 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const 
         return;
       }
       cached = run;
+      csb = tile_bounds(sCS, T);
     }
     const float pen = (float)R.m * powf((float)R.ctl->t / (float)R.t_max, R.alpha);
     float z[4];
@@ -314,9 +396,9 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned_batch(const 
     const int nsol = min(kPruneChunk, R.n_comb - base0);
     for (int g = 4 * warp; g < nsol; g += 4 * (kPruneThreads / 32)) {
       switch (R.m) {
-        case 2: prune_group<2, false>(R, base0 + g, sV, sC, sCS, sR, z, pen); break;
-        case 3: prune_group<3, false>(R, base0 + g, sV, sC, sCS, sR, z, pen); break;
-        default: prune_group<4, false>(R, base0 + g, sV, sC, sCS, sR, z, pen); break;
+        case 2: prune_group<2, false>(R, base0 + g, sV, sC, sCS, sR, z, pen, csb); break;
+        case 3: prune_group<3, false>(R, base0 + g, sV, sC, sCS, sR, z, pen, csb); break;
+        default: prune_group<4, false>(R, base0 + g, sV, sC, sCS, sR, z, pen, csb); break;
       }
     }
   }
