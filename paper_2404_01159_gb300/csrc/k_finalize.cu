@@ -79,8 +79,13 @@ k_finalize(const __grid_constant__ BatchDir dir) {
 // pass finds max32 over reference-vector tiles staged in shared memory; only
 // the i whose float dot is within 1e-5 of it (the float error of a dot of
 // unit vectors is below 1e-6) are re-evaluated in FP64, so the FP64 maximum
-// is exact.  One block = 32 vectors j x 8 interleaved slices of i.
+// is exact.  One block = 32 vectors j x 8 interleaved slices of i.  Each
+// thread keeps its kGKeep largest float dots from the pass: when its
+// smallest kept dot is below the window, every i of its slice inside the
+// window is kept and rechecked directly; otherwise (a slice with more than
+// kGKeep dots in the window) the block makes a second float pass.
 constexpr int kGTileF4 = 2048;   // float4s of one shared-memory tile (32 KB)
+constexpr int kGKeep = 4;
 
 __device__ __forceinline__ void gamma_load_tile(const RunDesc &R, int base, int nv, int m4,
                                                 float4 *tile) {
@@ -126,7 +131,10 @@ __device__ void gamma_block_t(const RunDesc &R, int jb, float4 *tile) {
   }
   const double *vjp = R.V64 + (size_t)(act ? j : 0) * M;
   constexpr int kGTile = kGTileF4 / M4;
-  float mx = -INFINITY;
+  float kd[kGKeep];   // the kGKeep largest float dots of this slice, descending
+  int ki[kGKeep];
+#pragma unroll
+  for (int c = 0; c < kGKeep; ++c) { kd[c] = -INFINITY; ki[c] = 0; }
   for (int base = 0; base < N; base += kGTile) {
     const int nv = min(kGTile, N - base);
     __syncthreads();
@@ -144,15 +152,34 @@ __device__ void gamma_block_t(const RunDesc &R, int jb, float4 *tile) {
           d = fmaf(vf[4 * q + 2], v.z, d);
           d = fmaf(vf[4 * q + 3], v.w, d);
         }
-        if (base + u != j) mx = fmaxf(mx, d);
+        if (d > kd[kGKeep - 1] && base + u != j) {
+          float vd = d;
+          int vi = base + u;
+#pragma unroll
+          for (int c = 0; c < kGKeep; ++c) {
+            if (vd > kd[c]) {
+              const float od = kd[c];
+              const int oi = ki[c];
+              kd[c] = vd; ki[c] = vi;
+              vd = od; vi = oi;
+            }
+          }
+        }
       }
     }
   }
+  float mx = kd[0];
 #pragma unroll
   for (int off = 1; off < 8; off <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   const float thr = mx - 1e-5f;
   double best = -2.0;
-  for (int base = 0; base < N; base += kGTile) {
+  if (!__syncthreads_or(act && kd[kGKeep - 1] >= thr)) {
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < kGKeep; ++c)
+        if (kd[c] >= thr) best = fmax(best, dot64(R.V64 + (size_t)ki[c] * M, vjp, M));
+    }
+  } else for (int base = 0; base < N; base += kGTile) {
     const int nv = min(kGTile, N - base);
     __syncthreads();
     gamma_load_tile(R, base, nv, M4, tile);
