@@ -48,6 +48,21 @@ __device__ __forceinline__ float dotv(const float *fp, const float4 *v) {
   return d;
 }
 
+// The dots of two solutions (a, b) with one vector, packed: lane x of each
+// .f32x2 instruction is dotv of a, lane y that of b (the same IEEE
+// operations in the same order, so the rescan's scalar dotv matches).
+template <int M>
+__device__ __forceinline__ float2 dotv2(const float2 *fab, const float4 *v) {
+  float2 d = mul2(fab[0], splat2(v[0].x));
+#pragma unroll
+  for (int k = 1; k < M; ++k) {
+    const float4 q = v[k >> 2];
+    const float c = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+    d = fma2(fab[k], splat2(c), d);
+  }
+  return d;
+}
+
 // Chunk scan for two solutions: the running maximum of each 32-vector
 // sub-tile costs one FMNMX per dot; a sub-tile replaces the best only on a
 // strict improvement, so `sub` is the first sub-tile holding the maximum.
@@ -55,9 +70,9 @@ template <int M>
 __device__ void scan_chunk(const float4 *__restrict__ sv, int nv, const float *fpa,
                            const float *fpb, float &besta, int &suba, float &bestb, int &subb) {
   constexpr int M4 = (M + 3) / 4;
-  float fa[M], fb[M];
+  float2 fab[M];
 #pragma unroll
-  for (int k = 0; k < M; ++k) { fa[k] = fpa[k]; fb[k] = fpb[k]; }
+  for (int k = 0; k < M; ++k) fab[k] = make_float2(fpa[k], fpb[k]);
   for (int sub = 0; sub * 32 < nv; ++sub) {
     const int n = min(32, nv - sub * 32);
     const float4 *p = sv + (size_t)sub * 32 * M4;
@@ -68,16 +83,18 @@ __device__ void scan_chunk(const float4 *__restrict__ sv, int nv, const float *f
         float4 v[M4];
 #pragma unroll
         for (int q = 0; q < M4; ++q) v[q] = p[jj * M4 + q];
-        ma = fmaxf(ma, dotv<M>(fa, v));
-        mb = fmaxf(mb, dotv<M>(fb, v));
+        const float2 d = dotv2<M>(fab, v);
+        ma = fmaxf(ma, d.x);
+        mb = fmaxf(mb, d.y);
       }
     } else {
       for (int jj = 0; jj < n; ++jj) {
         float4 v[M4];
 #pragma unroll
         for (int q = 0; q < M4; ++q) v[q] = p[jj * M4 + q];
-        ma = fmaxf(ma, dotv<M>(fa, v));
-        mb = fmaxf(mb, dotv<M>(fb, v));
+        const float2 d = dotv2<M>(fab, v);
+        ma = fmaxf(ma, d.x);
+        mb = fmaxf(mb, d.y);
       }
     }
     if (ma > besta) { besta = ma; suba = sub; }
