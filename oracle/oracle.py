@@ -21,7 +21,7 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DTLZ2, DTLZ1, NEURO = 0, 1, 2
+DTLZ2, DTLZ1, NEURO, DTLZ3, DTLZ4 = 0, 1, 2, 3, 4
 TAG_INIT, TAG_MATE, TAG_PAIR, TAG_SBX, TAG_MUTSITE, TAG_MUTMAG, TAG_NOISE = 1, 2, 3, 4, 5, 6, 7
 
 

@@ -241,7 +241,8 @@ void orc_init_population(const orc_params *p, double *X)
 /* ------------------------------------------------------------------------ */
 /* Objectives.  The paper names DTLZ1/DTLZ2 (Sec. 4.1, Appendix C) without   */
 /* printing them; the formulas are the standard DTLZ definitions with        */
-/* 1-based x, g over x_m..x_d, k = d - m + 1.                                */
+/* 1-based x, g over x_m..x_d, k = d - m + 1.  DTLZ3/DTLZ4 (the rest of the  */
+/* suite of Sec. 4.1's benchmark family) follow the same published source.  */
 /* ------------------------------------------------------------------------ */
 static void dtlz2(int32_t m, int32_t d, const double *x, double *f)
 {
@@ -269,6 +270,39 @@ static void dtlz1(int32_t m, int32_t d, const double *x, double *f)
         double v = 0.5 * (1.0 + g);
         for (int32_t i = 1; i <= m - k; ++i) v *= x[i - 1];
         if (k > 1) v *= 1.0 - x[m - k];
+        f[k - 1] = v;
+    }
+}
+
+/* DTLZ3 (Deb, Thiele, Laumanns, Zitzler 2005): the spherical shape of DTLZ2
+ * with the multimodal g of DTLZ1 (3^k - 1 local fronts). */
+static void dtlz3(int32_t m, int32_t d, const double *x, double *f)
+{
+    int32_t kk = d - m + 1;
+    double s = 0.0;
+    for (int32_t j = m - 1; j < d; ++j) {
+        double y = x[j] - 0.5;
+        s += y * y - cos(20.0 * M_PI * y);
+    }
+    double g = 100.0 * ((double)kk + s);
+    for (int32_t k = 1; k <= m; ++k) {
+        double v = 1.0 + g;
+        for (int32_t i = 1; i <= m - k; ++i) v *= cos(x[i - 1] * M_PI / 2.0);
+        if (k > 1) v *= sin(x[m - k] * M_PI / 2.0);
+        f[k - 1] = v;
+    }
+}
+
+/* DTLZ4 (same source): DTLZ2 with the position variables x_1..x_{m-1}
+ * mapped to x_i^alpha, alpha = 100 (a front biased towards the f_m axis). */
+static void dtlz4(int32_t m, int32_t d, const double *x, double *f)
+{
+    double g = 0.0;
+    for (int32_t j = m - 1; j < d; ++j) g += (x[j] - 0.5) * (x[j] - 0.5);
+    for (int32_t k = 1; k <= m; ++k) {
+        double v = 1.0 + g;
+        for (int32_t i = 1; i <= m - k; ++i) v *= cos(pow(x[i - 1], 100.0) * M_PI / 2.0);
+        if (k > 1) v *= sin(pow(x[m - k], 100.0) * M_PI / 2.0);
         f[k - 1] = v;
     }
 }
@@ -346,6 +380,8 @@ void orc_evaluate(const orc_params *p, int32_t n, const double *X, double *F,
         double *f = F + (int64_t)i * m;
         if (p->problem == ORC_DTLZ2) dtlz2(m, d, x, f);
         else if (p->problem == ORC_DTLZ1) dtlz1(m, d, x, f);
+        else if (p->problem == ORC_DTLZ3) dtlz3(m, d, x, f);
+        else if (p->problem == ORC_DTLZ4) dtlz4(m, d, x, f);
         else neuro_rollout(nd, x, xi, f);
     }
     free(xi);

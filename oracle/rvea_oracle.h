@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2 };
+enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2, ORC_DTLZ3 = 3, ORC_DTLZ4 = 4 };
 enum { ORC_TAG_INIT = 1, ORC_TAG_MATE = 2, ORC_TAG_PAIR = 3, ORC_TAG_SBX = 4,
        ORC_TAG_MUTSITE = 5, ORC_TAG_MUTMAG = 6, ORC_TAG_NOISE = 7 };
 

@@ -193,7 +193,7 @@ def _hand_rows():
 
 def test_dtlz_hand_worked(orc):
     rows = _hand_rows()
-    assert len(rows) == 3
+    assert len(rows) == 7
     for prob, m, d, x, fx in rows:
         p = orc.make_params(m=m, d=d, N=1, H=0, problem=prob)
         F = orc.evaluate(p, np.array([x]))
@@ -215,6 +215,30 @@ def test_dtlz_fronts(orc, m, d):
     X2[:, m - 1:] = 0.3
     assert (orc.evaluate(orc.make_params(m=m, d=d, N=64, H=0, problem=orc.DTLZ2), X2)
             >= F2 - 1e-15).all()
+
+
+@pytest.mark.parametrize("m,d", [(2, 12), (3, 12), (5, 30), (3, 5000)])
+def test_dtlz3_dtlz4_against_dtlz1_dtlz2(orc, m, d):
+    """DTLZ3 is DTLZ2's unit-norm shape scaled by DTLZ1's 1 + g (DTLZ1's
+    objectives sum to (1 + g)/2); DTLZ4 is DTLZ2 of x with the position
+    variables raised to the 100th power; both fronts (x_m.. = 1/2) are the
+    unit sphere."""
+    rng = np.random.default_rng(m * 7919 + d)
+    X = rng.uniform(0, 1, (64, d))
+    X[:8, : m - 1] = rng.uniform(0.9, 1.0, (8, m - 1))   # where the 100th power is not tiny
+
+    def ev(prob, x):
+        return orc.evaluate(orc.make_params(m=m, d=d, N=64, H=0, problem=prob), x)
+    F1, F2, F3, F4 = (ev(pr, X) for pr in (orc.DTLZ1, orc.DTLZ2, orc.DTLZ3, orc.DTLZ4))
+    shape = F2 / np.linalg.norm(F2, axis=1, keepdims=True)
+    assert np.allclose(F3, 2.0 * F1.sum(1, keepdims=True) * shape, rtol=1e-12, atol=0)
+    Xp = X.copy()
+    Xp[:, : m - 1] = X[:, : m - 1] ** 100
+    assert np.allclose(F4, ev(orc.DTLZ2, Xp), rtol=1e-12, atol=1e-300)
+    Xf = X.copy()
+    Xf[:, m - 1:] = 0.5
+    for prob in (orc.DTLZ3, orc.DTLZ4):
+        assert np.allclose(np.linalg.norm(ev(prob, Xf), axis=1), 1.0, rtol=0, atol=1e-12)
 
 
 def test_init_population(orc):
