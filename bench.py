@@ -33,6 +33,8 @@ METRIC = "RVEA generations/s & HBM GB/s vs roofline (plain vs batched); serve p5
 WORKLOADS = {
     "dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000),
     "dtlz2_m3_d12_N105": dict(m=3, d=12, N=105, H=13, problem=0, t_max=100),
+    "dtlz3_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=3, t_max=1000),
+    "dtlz4_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=4, t_max=1000),
 }
 COMMON = dict(alpha=2.0, f_r=0.1, eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
 

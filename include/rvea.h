@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
     RVEA_DTLZ2_SPHERE = 0,  /* spherical front, |f| = 1 on the front       */
     RVEA_DTLZ1_LINEAR = 1,  /* multimodal linear front, sum f = 1/2        */
-    RVEA_NEURO_LINEAR = 2   /* MLP policy rollout on linear dynamics       */
+    RVEA_NEURO_LINEAR = 2,  /* MLP policy rollout on linear dynamics       */
+    RVEA_DTLZ3_SPHERE = 3,  /* DTLZ1's multimodal g on DTLZ2's sphere      */
+    RVEA_DTLZ4_SPHERE = 4   /* DTLZ2 with x_i^100 position variables       */
 } rvea_problem;
 
 /* Synthetic linear dynamics of the neuroevolution objective (the stand-in

@@ -17,7 +17,7 @@ _lib = None
 
 OK, ERR_ARG, ERR_LATTICE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
-DTLZ2_SPHERE, DTLZ1_LINEAR, NEURO_LINEAR = 0, 1, 2
+DTLZ2_SPHERE, DTLZ1_LINEAR, NEURO_LINEAR, DTLZ3_SPHERE, DTLZ4_SPHERE = 0, 1, 2, 3, 4
 
 
 class NeuroDynamics(C.Structure):

@@ -31,15 +31,25 @@ __global__ void k_reprob_neuro(const __grid_constant__ BatchDir dir);
 __global__ void k_reprob_dtlz1s(const __grid_constant__ BatchDir dir);
 __global__ void k_reprob_dtlz2s(const __grid_constant__ BatchDir dir);
 __global__ void k_reprob_neuros(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz4(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz3s(const __grid_constant__ BatchDir dir);
+__global__ void k_reprob_dtlz4s(const __grid_constant__ BatchDir dir);
 __global__ void k_repro1_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1s_dtlz1(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1s_dtlz2(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_repro1s_neuro(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1_dtlz3(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1_dtlz4(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1s_dtlz3(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
+__global__ void k_repro1s_dtlz4(const __grid_constant__ BatchDir dir, const __grid_constant__ RoundKeys rk);
 __global__ void k_mutate_dtlz1(const __grid_constant__ BatchDir dir);
 __global__ void k_mutate_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_mutate_neuro(const __grid_constant__ BatchDir dir);
+__global__ void k_mutate_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_mutate_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_init(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
@@ -343,6 +353,14 @@ void set_kernel_attrs() {
   set((const void *)k_repro1s_dtlz1);
   set((const void *)k_repro1s_dtlz2);
   set((const void *)k_repro1s_neuro);
+  set((const void *)k_reprob_dtlz3);
+  set((const void *)k_reprob_dtlz4);
+  set((const void *)k_reprob_dtlz3s);
+  set((const void *)k_reprob_dtlz4s);
+  set((const void *)k_repro1_dtlz3);
+  set((const void *)k_repro1_dtlz4);
+  set((const void *)k_repro1s_dtlz3);
+  set((const void *)k_repro1s_dtlz4);
   set((const void *)k_init);
   set((const void *)k_select);
   set((const void *)k_select_pruned);
@@ -456,6 +474,8 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
     switch (r->hd.problem) {
       case PROB_DTLZ1: launch_pdl(k_repro1s_dtlz1, grid, kReproThreads, sm, st, dr, rk); break;
       case PROB_DTLZ2: launch_pdl(k_repro1s_dtlz2, grid, kReproThreads, sm, st, dr, rk); break;
+      case PROB_DTLZ3: launch_pdl(k_repro1s_dtlz3, grid, kReproThreads, sm, st, dr, rk); break;
+      case PROB_DTLZ4: launch_pdl(k_repro1s_dtlz4, grid, kReproThreads, sm, st, dr, rk); break;
       default: launch_pdl(k_repro1s_neuro, grid, kReproThreads, sm, st, dr, rk); break;
     }
     return;
@@ -463,6 +483,8 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
   switch (r->hd.problem) {
     case PROB_DTLZ1: launch_pdl(k_repro1_dtlz1, grid, kReproThreads, 0, st, dr, rk); break;
     case PROB_DTLZ2: launch_pdl(k_repro1_dtlz2, grid, kReproThreads, 0, st, dr, rk); break;
+    case PROB_DTLZ3: launch_pdl(k_repro1_dtlz3, grid, kReproThreads, 0, st, dr, rk); break;
+    case PROB_DTLZ4: launch_pdl(k_repro1_dtlz4, grid, kReproThreads, 0, st, dr, rk); break;
     default: launch_pdl(k_repro1_neuro, grid, kReproThreads, 0, st, dr, rk); break;
   }
 }
@@ -477,6 +499,8 @@ void launch_mutate1(const rvea_run *r, cudaStream_t st) {
   switch (r->hd.problem) {
     case PROB_DTLZ1: launch_pdl(k_mutate_dtlz1, nb, kMutThreads, 0, st, dm); break;
     case PROB_DTLZ2: launch_pdl(k_mutate_dtlz2, nb, kMutThreads, 0, st, dm); break;
+    case PROB_DTLZ3: launch_pdl(k_mutate_dtlz3, nb, kMutThreads, 0, st, dm); break;
+    case PROB_DTLZ4: launch_pdl(k_mutate_dtlz4, nb, kMutThreads, 0, st, dm); break;
     default: launch_pdl(k_mutate_neuro, nb, kMutThreads, 0, st, dm); break;
   }
 }
@@ -487,7 +511,7 @@ void launch_mutate1(const rvea_run *r, cudaStream_t st) {
 // gamma_by_flag, gamma and the tile tables of the runs that adapted.
 rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, bool gamma_by_flag,
                               cudaEvent_t *ev = nullptr) {
-  static thread_local BatchDir dr, ds, dp, df, dd, dt, dg[6];
+  static thread_local BatchDir dr, ds, dp, df, dd, dt, dg[2 * kProblems];
   int pr = 0, ps = 0, pp = 0, pd = 0, pt = 0;
   int sms = 0, smp = 0, ns = 0, np = 0;
   dr.n = df.n = dd.n = n;
@@ -537,8 +561,8 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     launch_mutate1(runs[0], st);
   } else {
     // one launch per (problem, load path) group, each with its own directory
-    int pg[6] = {0, 0, 0, 0, 0, 0};
-    for (int g = 0; g < 6; ++g) dg[g].n = 0;
+    int pg[2 * kProblems] = {};
+    for (int g = 0; g < 2 * kProblems; ++g) dg[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
       const int g = r->hd.problem * 2 + (r->repro_smem > 0 ? 1 : 0);
@@ -550,7 +574,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       pg[g] += r->sh.n_repro;
       ++D.n;
     }
-    for (int g = 0; g < 6; ++g) {
+    for (int g = 0; g < 2 * kProblems; ++g) {
       if (dg[g].n == 0) continue;
       dg[g].prefix[dg[g].n] = pg[g];
       const int sm = (g & 1) ? kStagedSmem : 0;
@@ -560,13 +584,17 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
         case 2: launch_pdl(k_reprob_dtlz1, pg[g], kReproThreads, sm, st, dg[g]); break;
         case 3: launch_pdl(k_reprob_dtlz1s, pg[g], kReproThreads, sm, st, dg[g]); break;
         case 4: launch_pdl(k_reprob_neuro, pg[g], kReproThreads, sm, st, dg[g]); break;
-        default: launch_pdl(k_reprob_neuros, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 5: launch_pdl(k_reprob_neuros, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 6: launch_pdl(k_reprob_dtlz3, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 7: launch_pdl(k_reprob_dtlz3s, pg[g], kReproThreads, sm, st, dg[g]); break;
+        case 8: launch_pdl(k_reprob_dtlz4, pg[g], kReproThreads, sm, st, dg[g]); break;
+        default: launch_pdl(k_reprob_dtlz4s, pg[g], kReproThreads, sm, st, dg[g]); break;
       }
     }
     // mutation / evaluation of the 32-lane-team runs, one launch per problem
-    static thread_local BatchDir dm[3];
-    int pm[3] = {0, 0, 0};
-    for (int g = 0; g < 3; ++g) dm[g].n = 0;
+    static thread_local BatchDir dm[kProblems];
+    int pm[kProblems] = {};
+    for (int g = 0; g < kProblems; ++g) dm[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
       if (r->sh.team != 32) continue;
@@ -578,12 +606,14 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       pm[r->hd.problem] += (r->sh.N + kMutThreads - 1) / kMutThreads;
       ++D.n;
     }
-    for (int g = 0; g < 3; ++g) {
+    for (int g = 0; g < kProblems; ++g) {
       if (dm[g].n == 0) continue;
       dm[g].prefix[dm[g].n] = pm[g];
       switch (g) {
         case PROB_DTLZ1: launch_pdl(k_mutate_dtlz1, pm[g], kMutThreads, 0, st, dm[g]); break;
         case PROB_DTLZ2: launch_pdl(k_mutate_dtlz2, pm[g], kMutThreads, 0, st, dm[g]); break;
+        case PROB_DTLZ3: launch_pdl(k_mutate_dtlz3, pm[g], kMutThreads, 0, st, dm[g]); break;
+        case PROB_DTLZ4: launch_pdl(k_mutate_dtlz4, pm[g], kMutThreads, 0, st, dm[g]); break;
         default: launch_pdl(k_mutate_neuro, pm[g], kMutThreads, 0, st, dm[g]); break;
       }
     }
@@ -707,7 +737,7 @@ rvea_status validate(const rvea_config *c) {
   if (c->p_m > 8.0 && c->p_m < (double)c->d) return RVEA_ERR_ARG;
   // the DTLZ problems are defined on the unit box
   if (c->problem != PROB_NEURO && (c->lower != 0.0 || c->upper != 1.0)) return RVEA_ERR_ARG;
-  if (c->problem < 0 || c->problem > 2) return RVEA_ERR_ARG;
+  if (c->problem < 0 || c->problem >= kProblems) return RVEA_ERR_ARG;
   if (c->problem == RVEA_NEURO_LINEAR) {
     // the rollout's shape: h1 = h2 = 64 (the tensor-core tiling), ns <= 32
     // (one lane per state component), na <= 16 (one 16-row tile), and d the

@@ -84,7 +84,7 @@ constexpr float kS13 = (float)(kPI * kPI * kPI * kPI * kPI * kPI * kPI * kPI * k
 __device__ __forceinline__ float2 g_terms2(int problem, float2 x, float2 acc) {
   const float2 y = add2(x, splat2(-0.5f));
   acc = fma2(y, y, acc);
-  if (problem == PROB_DTLZ1) {
+  if (multimodal_g(problem)) {
     const float2 z = mul2(y, splat2(10.0f));
     const float2 nn = make_float2(rintf(-z.x), rintf(-z.y));
     const float2 r = fma2(splat2(10.0f), y, nn);
@@ -106,7 +106,7 @@ __device__ __forceinline__ float2 g_terms2(int problem, float2 x, float2 acc) {
 __device__ __forceinline__ float g_term1(int problem, float x, float acc) {
   const float y = x + (-0.5f);
   acc = fmaf(y, y, acc);
-  if (problem == PROB_DTLZ1) {
+  if (multimodal_g(problem)) {
     const float z = y * 10.0f;
     const float r = fmaf(10.0f, y, rintf(-z));
     const float r2 = r * r;
@@ -123,8 +123,13 @@ __device__ __forceinline__ float g_term1(int problem, float x, float acc) {
 }
 
 // Objectives from g and the first m-1 variables (standard DTLZ forms).
-__device__ void dtlz_objectives(int problem, int m, float gsum, const float *head, float *f) {
-  if (problem == PROB_DTLZ1) {
+// gsum is the sum of the g-terms: sum (x - 1/2)^2 for DTLZ2/DTLZ4, and
+// k + sum ((x - 1/2)^2 - cos 20 pi (x - 1/2)) for DTLZ1/DTLZ3 (g = 100 gsum).
+// DTLZ4 maps the position variables to x^100.  One instance per problem, so
+// a problem's kernels carry only its own form.
+template <int PROB>
+__device__ void dtlz_objectives_t(int m, float gsum, const float *head, float *f) {
+  if (PROB == PROB_DTLZ1) {
     const float base = 0.5f * (1.0f + 100.0f * gsum);
     for (int k = 1; k <= m; ++k) {
       float v = base;
@@ -132,14 +137,33 @@ __device__ void dtlz_objectives(int problem, int m, float gsum, const float *hea
       if (k > 1) v *= 1.0f - head[m - k];
       f[k - 1] = v;
     }
-  } else {
+  } else if (PROB == PROB_DTLZ4) {
     const float base = 1.0f + gsum;
+    float h[kMaxM];
+    for (int i = 0; i < m - 1; ++i) h[i] = powf(head[i], 100.0f);
+    for (int k = 1; k <= m; ++k) {
+      float v = base;
+      for (int i = 1; i <= m - k; ++i) v *= cospif(0.5f * h[i - 1]);
+      if (k > 1) v *= sinpif(0.5f * h[m - k]);
+      f[k - 1] = v;
+    }
+  } else {   // DTLZ2, DTLZ3
+    const float base = 1.0f + (PROB == PROB_DTLZ3 ? 100.0f * gsum : gsum);
     for (int k = 1; k <= m; ++k) {
       float v = base;
       for (int i = 1; i <= m - k; ++i) v *= cospif(0.5f * head[i - 1]);
       if (k > 1) v *= sinpif(0.5f * head[m - k]);
       f[k - 1] = v;
     }
+  }
+}
+
+__device__ void dtlz_objectives(int problem, int m, float gsum, const float *head, float *f) {
+  switch (problem) {
+    case PROB_DTLZ1: dtlz_objectives_t<PROB_DTLZ1>(m, gsum, head, f); return;
+    case PROB_DTLZ3: dtlz_objectives_t<PROB_DTLZ3>(m, gsum, head, f); return;
+    case PROB_DTLZ4: dtlz_objectives_t<PROB_DTLZ4>(m, gsum, head, f); return;
+    default: dtlz_objectives_t<PROB_DTLZ2>(m, gsum, head, f); return;
   }
 }
 
@@ -313,7 +337,7 @@ __device__ __forceinline__ void evaluate_child(const RunDesc &R, int slot, float
   const float *row = R.X + (size_t)slot * R.d_pad;
   float head[kMaxM], f[kMaxM];
   for (int j = 0; j < mh; ++j) head[j] = __ldcg(row + j);
-  dtlz_objectives(PROB, m, g, head, f);
+  dtlz_objectives_t<PROB>(m, g, head, f);
   for (int kk = 0; kk < m; ++kk) {
     R.F[(size_t)kk * n2 + slot] = f[kk];
     atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
@@ -497,9 +521,13 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   }
 RVEA_REPRO1(k_repro1_dtlz1, PROB_DTLZ1, false)
 RVEA_REPRO1(k_repro1_dtlz2, PROB_DTLZ2, false)
+RVEA_REPRO1(k_repro1_dtlz3, PROB_DTLZ3, false)
+RVEA_REPRO1(k_repro1_dtlz4, PROB_DTLZ4, false)
 RVEA_REPRO1(k_repro1_neuro, PROB_NEURO, false)
 RVEA_REPRO1(k_repro1s_dtlz1, PROB_DTLZ1, true)
 RVEA_REPRO1(k_repro1s_dtlz2, PROB_DTLZ2, true)
+RVEA_REPRO1(k_repro1s_dtlz3, PROB_DTLZ3, true)
+RVEA_REPRO1(k_repro1s_dtlz4, PROB_DTLZ4, true)
 RVEA_REPRO1(k_repro1s_neuro, PROB_NEURO, true)
 #undef RVEA_REPRO1
 
@@ -513,9 +541,13 @@ RVEA_REPRO1(k_repro1s_neuro, PROB_NEURO, true)
   }
 RVEA_REPROB(k_reprob_dtlz1, PROB_DTLZ1, false)
 RVEA_REPROB(k_reprob_dtlz2, PROB_DTLZ2, false)
+RVEA_REPROB(k_reprob_dtlz3, PROB_DTLZ3, false)
+RVEA_REPROB(k_reprob_dtlz4, PROB_DTLZ4, false)
 RVEA_REPROB(k_reprob_neuro, PROB_NEURO, false)
 RVEA_REPROB(k_reprob_dtlz1s, PROB_DTLZ1, true)
 RVEA_REPROB(k_reprob_dtlz2s, PROB_DTLZ2, true)
+RVEA_REPROB(k_reprob_dtlz3s, PROB_DTLZ3, true)
+RVEA_REPROB(k_reprob_dtlz4s, PROB_DTLZ4, true)
 RVEA_REPROB(k_reprob_neuros, PROB_NEURO, true)
 #undef RVEA_REPROB
 
@@ -623,7 +655,7 @@ __device__ __forceinline__ void mutate_body(const BatchDir &dir) {
     const float *row = R.X + (size_t)slot * R.d_pad;
     float head[kMaxM];
     for (int jj = 0; jj < m - 1; ++jj) head[jj] = __ldcg(row + jj);
-    dtlz_objectives(PROB, m, g + dg, head, f);
+    dtlz_objectives_t<PROB>(m, g + dg, head, f);
     for (int kk = 0; kk < m; ++kk) R.F[(size_t)kk * 2 * N + slot] = f[kk];
   }
   // the ideal point: a CTA's minimum per objective, then one atomic each
@@ -644,6 +676,8 @@ __device__ __forceinline__ void mutate_body(const BatchDir &dir) {
   }
 RVEA_MUTATE(k_mutate_dtlz1, PROB_DTLZ1)
 RVEA_MUTATE(k_mutate_dtlz2, PROB_DTLZ2)
+RVEA_MUTATE(k_mutate_dtlz3, PROB_DTLZ3)
+RVEA_MUTATE(k_mutate_dtlz4, PROB_DTLZ4)
 RVEA_MUTATE(k_mutate_neuro, PROB_NEURO)
 #undef RVEA_MUTATE
 

@@ -32,7 +32,12 @@ enum : uint32_t {
   TAG_MUTSITE = 5, TAG_MUTMAG = 6, TAG_NOISE = 7
 };
 
-enum : int { PROB_DTLZ2 = 0, PROB_DTLZ1 = 1, PROB_NEURO = 2 };
+enum : int { PROB_DTLZ2 = 0, PROB_DTLZ1 = 1, PROB_NEURO = 2, PROB_DTLZ3 = 3, PROB_DTLZ4 = 4 };
+constexpr int kProblems = 5;
+// DTLZ1 and DTLZ3 share the multimodal g (Rastrigin-like terms)
+__host__ __device__ constexpr bool multimodal_g(int problem) {
+  return problem == PROB_DTLZ1 || problem == PROB_DTLZ3;
+}
 
 // Device status word bits.
 enum : int { ST_TIMEOUT = 1, ST_BADINDEX = 2 };

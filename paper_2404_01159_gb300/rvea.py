@@ -13,11 +13,12 @@ from typing import Optional, Sequence
 import numpy as np
 import torch
 
-from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, NEURO_LINEAR, Config, NeuroDynamics, Plan, ServerStats,
-                      RveaError, check, lib)
+from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, DTLZ3_SPHERE, DTLZ4_SPHERE, NEURO_LINEAR,
+                      Config, NeuroDynamics, Plan, ServerStats, RveaError, check, lib)
 
 __all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
-           "DTLZ2_SPHERE", "DTLZ1_LINEAR", "NEURO_LINEAR", "lattice_size"]
+           "DTLZ2_SPHERE", "DTLZ1_LINEAR", "DTLZ3_SPHERE", "DTLZ4_SPHERE", "NEURO_LINEAR",
+           "lattice_size"]
 
 
 def _stream(stream) -> int:

@@ -86,7 +86,8 @@ def test_batch_graph_equals_alone(orc):
     from paper_2404_01159_gb300 import Batch, autotune, set_plan
     shapes = [(3, 12, 105, 13, 0, 1, 30), (3, 2500, 1275, 49, 1, 2, 40), (10, 30, 220, 3, 0, 3, 50),
               (2, 300, 1200, 1199, 0, 4, 20), (5, 1500, 126, 5, 1, 5, 30), (3, 3, 105, 13, 1, 6, 60),
-              (4, 64, 1771, 20, 0, 7, 40)]
+              (4, 64, 1771, 20, 0, 7, 40), (3, 1100, 105, 13, 3, 8, 30),
+              (2, 1300, 100, 99, 4, 9, 30), (5, 60, 126, 5, 3, 10, 30)]
     ps = [params(orc, m, d, N, H, pr, t_max=tm, seed=s) for (m, d, N, H, pr, s, tm) in shapes]
     alone = [make_run(p) for p in ps]
     batch = [make_run(p) for p in ps]

@@ -26,9 +26,9 @@ def _cuda():
 # (m, d, N, H, problem): cfg0 shape, a ragged DTLZ1 case spanning several
 # reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10;
 # (d > 1024) take the shared-memory-staged reproduction path, with segments
-# of several chunks, a partial last chunk and row padding; the last two are
-# large populations (N = 4200, 2100 pairs) on the register and the staged
-# load path.
+# of several chunks, a partial last chunk and row padding; two are large
+# populations (N = 4200, 2100 pairs) on the register and the staged load
+# path; the last four are DTLZ3 and DTLZ4 on both paths.
 SHAPES = [
     (3, 12, 105, 13, 0),
     (3, 1001, 210, 19, 1),
@@ -41,6 +41,11 @@ SHAPES = [
     (2, 4099, 100, 99, 0),
     (2, 30, 4200, 4199, 1),
     (2, 1100, 4200, 4199, 0),
+    # DTLZ3 (problem 3) and DTLZ4 (problem 4), small d and staged
+    (3, 40, 105, 13, 3),
+    (3, 1500, 105, 13, 3),
+    (3, 60, 105, 13, 4),
+    (2, 2000, 100, 99, 4),
 ]
 
 
@@ -219,7 +224,7 @@ def test_batch_equals_alone(orc):
     from paper_2404_01159_gb300 import step_batch
     shapes = [(3, 12, 105, 13, 0, 1), (3, 1001, 210, 19, 1, 2), (10, 30, 220, 3, 0, 3),
               (2, 203, 100, 99, 1, 4), (3, 64, 1275, 49, 1, 5), (2, 40, 1200, 1199, 0, 6),
-              (4, 20, 1771, 20, 0, 7)]
+              (4, 20, 1771, 20, 0, 7), (3, 40, 105, 13, 3, 8), (3, 1200, 210, 19, 4, 9)]
     ps = [params(orc, m, d, N, H, pr, t_max=30, seed=s) for (m, d, N, H, pr, s) in shapes]
     alone = [make_run(p) for p in ps]
     batch = [make_run(p) for p in ps]
