@@ -283,3 +283,17 @@ def generation(p: Params, V0, st: State, nd=None):
 def adapt_period(p: Params) -> int:
     import math
     return max(1, int(math.floor(p.f_r * p.t_max + 0.5)))
+
+
+def igd(F, valid, R):
+    """Inverted generational distance (Appendix C, numerical benchmarks, the
+    IGD equation): the mean over the reference points f* in R of the
+    Euclidean distance to the nearest objective vector of a valid member of
+    the population F (n x m), in FP64."""
+    P = np.asarray(F, dtype=np.float64)[np.asarray(valid, dtype=bool)]
+    R = np.asarray(R, dtype=np.float64)
+    if len(P) == 0 or len(R) == 0:
+        raise ValueError("IGD needs a valid member and a reference point")
+    d = np.sqrt(((R[:, None, :] - P[None, :, :]) ** 2).sum(axis=2))
+    return float(d.min(axis=1).mean())
+

@@ -263,3 +263,30 @@ def test_mating_uniform_over_valid(orc):
     # draw e uses word e % 4 of counter (e/4, 0, t, MATE) and (w*K) >> 32
     w = orc.philox([1, 0, 7, orc.TAG_MATE], [7, 0])
     assert par[5] == vlist[(w[1] * 4) >> 32]
+
+
+def test_igd(orc):
+    """IGD (Appendix C): zero when the population contains every reference
+    point; a closed form for one reference point; invalid members ignored;
+    a pure-Python brute force on a small random case."""
+    R = np.array([[1.0, 0.0], [0.0, 1.0], [0.6, 0.8]])
+    assert orc.igd(R, np.ones(3, np.uint8), R) == 0.0
+    P = np.array([[3.0, 4.0], [100.0, 100.0]])
+    assert orc.igd(P, np.array([1, 0], np.uint8), np.zeros((1, 2))) == 5.0
+    assert orc.igd(P, np.array([1, 1], np.uint8), np.array([[97.0, 96.0]])) == 5.0
+    with pytest.raises(ValueError):
+        orc.igd(P, np.zeros(2, np.uint8), R)
+    rng = np.random.default_rng(3)
+    F = rng.uniform(0, 2, (7, 3))
+    v = np.array([1, 0, 1, 1, 0, 1, 1], np.uint8)
+    Rr = rng.uniform(0, 1, (5, 3))
+    total = 0.0
+    for r in Rr.tolist():
+        best = None
+        for f, ok in zip(F.tolist(), v.tolist()):
+            if not ok:
+                continue
+            dist = sum((a - b) ** 2 for a, b in zip(r, f)) ** 0.5
+            best = dist if best is None else min(best, dist)
+        total += best
+    assert abs(orc.igd(F, v, Rr) - total / len(Rr)) < 1e-14
