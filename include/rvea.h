@@ -239,6 +239,18 @@ int rvea_generation(const rvea_run *run);
 rvea_status rvea_step_profiled(rvea_run *run, int n_generations, void *cuda_stream,
                                double *phase_ms, int n_phases);
 
+/* Inverted generational distance (Appendix C, the IGD equation) of the
+ * run's current population against n_ref reference points: the mean over
+ * the points of the Euclidean distance to the nearest objective vector of a
+ * valid member.  ref: n_ref x m float32, row-major, device memory (or mapped
+ * host memory); *out (host) receives the value; synchronises `cuda_stream`
+ * and uses the run's staging area (stream-ordered with the run's other
+ * calls).  Distances in float32, their roots and sum in FP64.  RVEA_ERR_ARG
+ * for a NULL or non-device pointer, n_ref < 1, or more than about 2048 N
+ * points; RVEA_ERR_STATE when the population has no valid member. */
+rvea_status rvea_igd(const rvea_run *run, const float *ref, int n_ref, double *out,
+                     void *cuda_stream);
+
 /* Kernel launches rvea_step enqueues for one generation of `run` (adapting:
  * a generation with t % ceil(f_r t_max) == 0, which also rescales V); -1 if
  * run is NULL. */

@@ -93,6 +93,8 @@ def lib():
         L.rvea_population.argtypes = [vp, vp, vp, vp]
         L.rvea_population.restype = i32
         L.rvea_objectives.argtypes = [vp, vp, vp, vp]
+        L.rvea_igd.argtypes = [vp, vp, i32, C.POINTER(C.c_double), vp]
+        L.rvea_igd.restype = i32
         L.rvea_objectives.restype = i32
         L.rvea_sync_status.argtypes = [vp]
         L.rvea_sync_status.restype = i32

@@ -61,6 +61,8 @@ __global__ void k_gather_obj(const RunDesc *Rp, float *dst, uint8_t *valid);
 __global__ void k_gather_children(const RunDesc *Rp, float *X, float *F);
 __global__ void k_copy_selection(const RunDesc *Rp, int *assoc, int *surv);
 __global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin, int t);
+__global__ void k_igd_partial(const RunDesc *Rp, const float *ref, int n_ref, double *partial);
+__global__ void k_igd_final(const double *partial, int nb, int n_ref, double *out);
 __global__ void k_op_prep(const RunDesc *Rp);
 __global__ void k_op_zstar(const RunDesc *Rp);
 __global__ void k_op_finish(const RunDesc *Rp);
@@ -1449,6 +1451,29 @@ rvea_status rvea_objectives(const rvea_run *r, float *dst, uint8_t *valid, void 
   }
   k_gather_obj<<<(sh.N + 255) / 256, 256, 0, st>>>(r->d_desc, dx, dv);
   return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_igd(const rvea_run *r, const float *ref, int n_ref, double *out,
+                     void *cuda_stream) {
+  if (!r || !ref || !out || n_ref < 1) return RVEA_ERR_ARG;
+  const float *rd = static_cast<const float *>(dev_addr(const_cast<float *>(ref)));
+  if (!rd) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int nb = (n_ref + 255) / 256;
+  // block partials and the result in the run's staging area
+  const size_t stage_bytes = (size_t)r->sh.N * (kMaxM + 1) * 4;
+  if ((size_t)(nb + 1) * 8 > stage_bytes) return RVEA_ERR_ARG;
+  double *part = wsp<double>(r, r->lay.stage);
+  k_igd_partial<<<nb, 256, 0, st>>>(r->d_desc, rd, n_ref, part);
+  RV_TRY(cudaGetLastError());
+  k_igd_final<<<1, 32, 0, st>>>(part, nb, n_ref, part + nb);
+  RV_TRY(cudaGetLastError());
+  double v = 0.0;
+  RV_TRY(cudaMemcpyAsync(&v, part + nb, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RV_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(v)) return RVEA_ERR_STATE;   // no valid member
+  *out = v;
+  return RVEA_OK;
 }
 
 rvea_status rvea_export_state(const rvea_run *r, float *X, float *F, uint8_t *valid, double *V,

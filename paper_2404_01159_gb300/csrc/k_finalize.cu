@@ -249,6 +249,76 @@ __global__ void __launch_bounds__(256) k_gamma_op(const __grid_constant__ RunDes
   gamma_block(D, blockIdx.x);
 }
 
+// ---- inverted generational distance (Appendix C, the IGD equation) ----------
+// One thread per reference point: the squared distance to every valid member
+// of the current population (staged in shared memory kIgdTile members at a
+// time, compacted), the root of the minimum in FP64, then the block's sum in
+// a fixed tree into partial[blockIdx.x]; k_igd_final adds the partials in
+// order.  The minimum is exact whatever the member order.
+constexpr int kIgdThreads = 256;
+constexpr int kIgdTile = 512;
+
+__global__ void __launch_bounds__(kIgdThreads)
+k_igd_partial(const RunDesc *__restrict__ Rp, const float *__restrict__ ref, int n_ref,
+              double *__restrict__ partial) {
+  __shared__ float sF[kMaxM * kIgdTile];   // objective k of member i at k * kIgdTile + i
+  __shared__ int s_cnt;
+  __shared__ double s_w[kIgdThreads / 32];
+  const RunDesc &R = *Rp;
+  const int m = R.m, N = R.N, n2 = 2 * N;
+  const int *cur = R.slotmap + (R.ctl->t & 1) * N;
+  const int r = blockIdx.x * kIgdThreads + threadIdx.x;
+  float rv[kMaxM];
+#pragma unroll
+  for (int k = 0; k < kMaxM; ++k) rv[k] = (r < n_ref && k < m) ? ref[(size_t)r * m + k] : 0.0f;
+  float best = INFINITY;
+  for (int base = 0; base < N; base += kIgdTile) {
+    __syncthreads();   // the previous tile is no longer read
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int nt = min(kIgdTile, N - base);
+    for (int q = threadIdx.x; q < nt; q += kIgdThreads) {
+      const int slot = cur[base + q];
+      if (slot < 0 || slot >= n2) continue;
+      const int pos = atomicAdd(&s_cnt, 1);
+      for (int k = 0; k < m; ++k) sF[k * kIgdTile + pos] = R.F[(size_t)k * n2 + slot];
+    }
+    __syncthreads();
+    const int c = s_cnt;
+    if (r < n_ref) {
+      for (int i = 0; i < c; ++i) {
+        float d2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kMaxM; ++k) {
+          if (k < m) {
+            const float e = rv[k] - sF[k * kIgdTile + i];
+            d2 = fmaf(e, e, d2);
+          }
+        }
+        best = fminf(best, d2);
+      }
+    }
+  }
+  double v = r < n_ref ? sqrt((double)best) : 0.0;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kIgdThreads / 32; ++w) s += s_w[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_igd_final(const double *__restrict__ partial, int nb, int n_ref,
+                            double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[b];
+  *out = s / (double)n_ref;
+}
+
 // ---- state transfer -------------------------------------------------------
 // Population rows in slot order -> dst (N x d); invalid rows NaN.
 __global__ void k_gather_pop(const RunDesc *__restrict__ Rp, float *dst, uint8_t *valid) {

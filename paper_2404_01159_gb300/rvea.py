@@ -144,6 +144,17 @@ class Run:
               "rvea_objectives")
         return out, valid
 
+    def igd(self, ref: torch.Tensor, stream=None) -> float:
+        """Inverted generational distance of the current population against
+        the reference points `ref` (n_ref x m float32 on the run's device)."""
+        ref = ref.to(device=self.device, dtype=torch.float32).contiguous()
+        if ref.dim() != 2 or ref.shape[1] != self.m:
+            raise ValueError("ref must be n_ref x m")
+        out = C.c_double()
+        check(lib().rvea_igd(self._h, _ptr(ref), int(ref.shape[0]), C.byref(out),
+                             C.c_void_p(_stream(stream))), "rvea_igd")
+        return float(out.value)
+
     def export_state(self, stream=None) -> dict:
         dev = self.device
         X = torch.empty((self.N, self.d), dtype=torch.float32, device=dev)

@@ -274,3 +274,22 @@ def test_full_size_dtlz1_sampled(orc):
         run.sync_status()
     finally:
         orc.set_threads(1)
+
+
+@pytest.mark.parametrize("shape", [(3, 12, 105, 13, 0), (3, 300, 1275, 49, 1), (2, 1500, 100, 99, 4)])
+def test_igd_matches_oracle(orc, shape):
+    """IGD of the GPU population (Appendix C) against the oracle's definition
+    on the same objective vectors, with the problem's front as reference:
+    the unit sphere (DTLZ2/DTLZ4, the unit lattice) or the simplex sum f =
+    1/2 (DTLZ1, the lattice halved)."""
+    m, d, N, H, prob = shape
+    p = params(orc, m, d, N, H, prob, t_max=50, seed=21)
+    run = make_run(p)
+    run.step(7)
+    st = to_np(run.export_state())
+    L = orc.lattice(m, H)
+    R = (0.5 * L / H if prob == 1 else orc.lattice_unit(L)).astype(np.float32)
+    g = run.igd(torch.tensor(R, device="cuda"))
+    o = orc.igd(st["F"].astype(np.float64), st["valid"], R.astype(np.float64))
+    assert abs(g - o) <= 1e-5 * o + 1e-7, (g, o)
+    run.sync_status()
