@@ -297,3 +297,39 @@ def igd(F, valid, R):
     d = np.sqrt(((R[:, None, :] - P[None, :, :]) ** 2).sum(axis=2))
     return float(d.min(axis=1).mean())
 
+
+
+def hypervolume(F, valid, ref):
+    """Hypervolume (Appendix C, the HV equation): the measure of the union,
+    over the valid members f of F (n x m, m = 2 or 3) that dominate the
+    reference point (f < ref in every objective), of the boxes [f, ref], in
+    FP64.  m = 3 by slicing: the members sorted by f3 cut [min f3, ref3] into
+    slabs, each slab's area is the 2-D hypervolume of the members at or below
+    it; the 2-D hypervolume is the staircase of the members sorted by f1,
+    each step as wide as the gap to the next f1 and as high as ref2 minus the
+    smallest f2 so far."""
+    P = np.asarray(F, dtype=np.float64)[np.asarray(valid, dtype=bool)]
+    ref = np.asarray(ref, dtype=np.float64)
+    m = P.shape[1]
+    if m not in (2, 3) or ref.shape != (m,):
+        raise ValueError("hypervolume: m = 2 or 3, ref of length m")
+    P = P[(P < ref).all(axis=1)]
+
+    def area(Q):   # 2-D: Q sorted by f1
+        Q = Q[np.argsort(Q[:, 0], kind="stable")]
+        a, low = 0.0, ref[1]
+        for j in range(len(Q)):
+            low = min(low, Q[j, 1])
+            right = Q[j + 1, 0] if j + 1 < len(Q) else ref[0]
+            a += (right - Q[j, 0]) * (ref[1] - low)
+        return a
+
+    if m == 2:
+        return float(area(P)) if len(P) else 0.0
+    P = P[np.argsort(P[:, 2], kind="stable")]
+    vol = 0.0
+    for i in range(len(P)):
+        top = P[i + 1, 2] if i + 1 < len(P) else ref[2]
+        if top > P[i, 2]:
+            vol += (top - P[i, 2]) * area(P[: i + 1, :2])
+    return float(vol)

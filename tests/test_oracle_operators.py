@@ -290,3 +290,37 @@ def test_igd(orc):
             best = dist if best is None else min(best, dist)
         total += best
     assert abs(orc.igd(F, v, Rr) - total / len(Rr)) < 1e-14
+
+
+def _hv_grid(points, ref):
+    """Brute force on integer coordinates: the unit cells [a, a + 1) below
+    ref that some point weakly dominates (p <= a in every objective)."""
+    import itertools
+    count = 0
+    for a in itertools.product(*[range(int(r)) for r in ref]):
+        if any(all(pk <= ak for pk, ak in zip(p, a)) for p in points):
+            count += 1
+    return count
+
+
+def test_hypervolume(orc):
+    """HV (Appendix C): one box; two boxes by inclusion-exclusion; members
+    that do not dominate the reference point, or are invalid, add nothing;
+    integer point sets against a brute-force count of unit cells (m = 2, 3)."""
+    one = np.ones(1, np.uint8)
+    assert orc.hypervolume(np.array([[1.0, 2.0, 0.5]]), one, [3.0, 3.0, 1.0]) == 2.0 * 1.0 * 0.5
+    a, b, r = np.array([1.0, 3.0]), np.array([2.0, 1.0]), np.array([4.0, 4.0])
+    inter = np.prod(r - np.maximum(a, b))
+    assert abs(orc.hypervolume(np.stack([a, b]), np.ones(2, np.uint8), r)
+               - (np.prod(r - a) + np.prod(r - b) - inter)) < 1e-15
+    F = np.array([[1.0, 1.0], [5.0, 0.5], [0.5, 0.5]])
+    assert orc.hypervolume(F, np.array([1, 1, 0], np.uint8), [4.0, 4.0]) == 9.0
+    rng = np.random.default_rng(11)
+    for m, ref in ((2, (7, 7)), (3, (5, 5, 5)), (3, (6, 4, 5))):
+        for _ in range(6):
+            n = int(rng.integers(1, 9))
+            P = rng.integers(0, 6, (n, m)).astype(np.float64)
+            v = rng.integers(0, 2, n).astype(np.uint8)
+            v[0] = 1
+            pts = [p for p, ok in zip(P.tolist(), v.tolist()) if ok]
+            assert orc.hypervolume(P, v, ref) == _hv_grid(pts, ref), (P, v, ref)
