@@ -251,6 +251,17 @@ rvea_status rvea_step_profiled(rvea_run *run, int n_generations, void *cuda_stre
 rvea_status rvea_igd(const rvea_run *run, const float *ref, int n_ref, double *out,
                      void *cuda_stream);
 
+/* Hypervolume (Appendix C, the HV equation) of the run's current population,
+ * m = 2 or 3: the measure of the union of the boxes [f, ref] over the valid
+ * members f that dominate ref (f < ref in every objective); objectives as
+ * stored (normalise through ref).  ref: host, m finite values; *out (host)
+ * receives the value; synchronises `cuda_stream` and uses the run's staging
+ * area.  O(N^2) work (members ranked by counting, one warp per f3 slab), in
+ * FP64 from the float32 objectives.  RVEA_ERR_ARG for NULL pointers, m > 3
+ * or a non-finite ref. */
+rvea_status rvea_hypervolume(const rvea_run *run, const double *ref, double *out,
+                             void *cuda_stream);
+
 /* Kernel launches rvea_step enqueues for one generation of `run` (adapting:
  * a generation with t % ceil(f_r t_max) == 0, which also rescales V); -1 if
  * run is NULL. */

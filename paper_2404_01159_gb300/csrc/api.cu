@@ -23,6 +23,7 @@
 
 #include "../../include/rvea.h"
 #include "rvea_device.cuh"
+#include "metrics.cuh"
 
 namespace rvea {
 __global__ void k_reprob_dtlz1(const __grid_constant__ BatchDir dir);
@@ -63,6 +64,10 @@ __global__ void k_copy_selection(const RunDesc *Rp, int *assoc, int *surv);
 __global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin, int t);
 __global__ void k_igd_partial(const RunDesc *Rp, const float *ref, int n_ref, double *partial);
 __global__ void k_igd_final(const double *partial, int nb, int n_ref, double *out);
+__global__ void k_hv_compact(const RunDesc *Rp, HvRef ref, HvScratch S);
+__global__ void k_hv_rank(HvScratch S);
+__global__ void k_hv_slices(HvScratch S, HvRef ref);
+__global__ void k_hv_final(HvScratch S, double *out);
 __global__ void k_op_prep(const RunDesc *Rp);
 __global__ void k_op_zstar(const RunDesc *Rp);
 __global__ void k_op_finish(const RunDesc *Rp);
@@ -1472,6 +1477,36 @@ rvea_status rvea_igd(const rvea_run *r, const float *ref, int n_ref, double *out
   RV_TRY(cudaMemcpyAsync(&v, part + nb, sizeof(double), cudaMemcpyDeviceToHost, st));
   RV_TRY(cudaStreamSynchronize(st));
   if (!std::isfinite(v)) return RVEA_ERR_STATE;   // no valid member
+  *out = v;
+  return RVEA_OK;
+}
+
+rvea_status rvea_hypervolume(const rvea_run *r, const double *ref, double *out, void *cuda_stream) {
+  if (!r || !ref || !out) return RVEA_ERR_ARG;
+  const int m = r->sh.m, N = r->sh.N;
+  if (m != 2 && m != 3) return RVEA_ERR_ARG;
+  for (int k = 0; k < m; ++k)
+    if (!std::isfinite(ref[k])) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // scratch in the run's staging area (N (kMaxM + 1) 4 bytes >= 44 N + 16)
+  uint8_t *base = wsp<uint8_t>(r, r->lay.stage);
+  double *dd = reinterpret_cast<double *>(base);
+  int *ii = reinterpret_cast<int *>(base + (size_t)32 * N);
+  HvScratch S{dd, dd + N, dd + 2 * (size_t)N, dd + 3 * (size_t)N,
+              ii, ii + N, ii + 2 * (size_t)N, ii + 3 * (size_t)N};
+  double *dout = reinterpret_cast<double *>(base + (((size_t)44 * N + 4 + 7) & ~(size_t)7));
+  const HvRef hr{ref[0], ref[1], m == 3 ? ref[2] : 1.0};
+  k_hv_compact<<<1, 1024, 0, st>>>(r->d_desc, hr, S);
+  RV_TRY(cudaGetLastError());
+  k_hv_rank<<<(N + 255) / 256, 256, 0, st>>>(S);
+  RV_TRY(cudaGetLastError());
+  k_hv_slices<<<(N + 7) / 8, 256, 0, st>>>(S, hr);
+  RV_TRY(cudaGetLastError());
+  k_hv_final<<<1, 32, 0, st>>>(S, dout);
+  RV_TRY(cudaGetLastError());
+  double v = 0.0;
+  RV_TRY(cudaMemcpyAsync(&v, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RV_TRY(cudaStreamSynchronize(st));
   *out = v;
   return RVEA_OK;
 }

@@ -10,6 +10,7 @@
 // FP64 (Algorithm 2, "update reference vectors").  gamma (Eq. 5) follows in
 // k_gamma.
 #include "finalize_steps.cuh"
+#include "metrics.cuh"
 
 namespace rvea {
 
@@ -317,6 +318,124 @@ __global__ void k_igd_final(const double *__restrict__ partial, int nb, int n_re
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += partial[b];
   *out = s / (double)n_ref;
+}
+
+// ---- hypervolume (Appendix C, the HV equation), m = 2 or 3 -----------------
+// (scratch layout: metrics.cuh)  The volume is cut into slabs along
+// f3 at the members' f3 values; a slab's area is the 2-D hypervolume of the
+// members at or below it, summed as bands: in f1 order, a member that lowers
+// the running minimum of f2 from mprev to f2 adds (ref1 - f1) (mprev - f2).
+// One CTA of 1024 threads: compaction in slot order (block scan of flags).
+__global__ void __launch_bounds__(1024)
+k_hv_compact(const RunDesc *__restrict__ Rp, HvRef ref, HvScratch S) {
+  __shared__ int s_w[32];
+  __shared__ int s_base;
+  const RunDesc &R = *Rp;
+  const int N = R.N, n2 = 2 * N, m = R.m;
+  const int *cur = R.slotmap + (R.ctl->t & 1) * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_base = 0;
+  for (int base = 0; base < N; base += 1024) {
+    const int j = base + threadIdx.x;
+    double a = 0.0, b = 0.0, c = 0.0;
+    bool ok = false;
+    if (j < N) {
+      const int slot = cur[j];
+      if (slot >= 0 && slot < n2) {
+        a = (double)R.F[slot];
+        b = (double)R.F[(size_t)n2 + slot];
+        c = m == 3 ? (double)R.F[2 * (size_t)n2 + slot] : 0.0;
+        ok = a < ref.r1 && b < ref.r2 && c < ref.r3;
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    int before = s_base;
+    for (int w = 0; w < warp; ++w) before += s_w[w];
+    const int pos = before + __popc(bal & ((1u << lane) - 1u));
+    if (ok) {
+      S.f1[pos] = a;
+      S.f2[pos] = b;
+      S.f3[pos] = c;
+    }
+    __syncthreads();   // every thread has read s_base and s_w
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < 32; ++w) tot += s_w[w];
+      s_base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *S.count = s_base;
+}
+
+// Member p's rank by (f1, index) and by (f3, index), and the inverse
+// permutations: a count over all members.
+__global__ void __launch_bounds__(256) k_hv_rank(HvScratch S) {
+  const int n = *S.count;
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  if (p >= n) return;
+  const double a = S.f1[p], c = S.f3[p];
+  int r1 = 0, r3 = 0;
+  for (int q = 0; q < n; ++q) {
+    const double aq = S.f1[q], cq = S.f3[q];
+    r1 += (aq < a || (aq == a && q < p)) ? 1 : 0;
+    r3 += (cq < c || (cq == c && q < p)) ? 1 : 0;
+  }
+  S.byF1[r1] = p;
+  S.byF3[r3] = p;
+  S.rank3[p] = r3;
+}
+
+// One warp per slab i (the members of f3 rank <= i, up to the next f3).
+__global__ void __launch_bounds__(256) k_hv_slices(HvScratch S, HvRef ref) {
+  const int n = *S.count;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;   // whole warps
+  const double z = S.f3[S.byF3[i]];
+  const double zn = i + 1 < n ? S.f3[S.byF3[i + 1]] : ref.r3;
+  const double h = zn - z;
+  if (!(h > 0.0)) {
+    if (lane == 0) S.vol[i] = 0.0;
+    return;
+  }
+  double area = 0.0, carry = ref.r2;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int sidx = c0 + lane;
+    int p = 0;
+    bool incl = false;
+    if (sidx < n) {
+      p = S.byF1[sidx];
+      incl = S.rank3[p] <= i;
+    }
+    const double f2 = incl ? S.f2[p] : INFINITY;
+    double pm = fmin(f2, carry);   // inclusive running minimum
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, pm, off);
+      if (lane >= off) pm = fmin(pm, y);
+    }
+    double prev = __shfl_up_sync(0xffffffffu, pm, 1);
+    if (lane == 0) prev = carry;
+    if (incl) area += (ref.r1 - S.f1[p]) * fmax(0.0, prev - f2);
+    carry = __shfl_sync(0xffffffffu, pm, 31);
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) area += __shfl_xor_sync(0xffffffffu, area, off);
+  if (lane == 0) S.vol[i] = h * area;
+}
+
+// The slabs' volumes in a fixed order: lane l sums slabs l, l + 32, ...,
+// then a fixed tree.
+__global__ void k_hv_final(HvScratch S, double *out) {
+  const int n = *S.count, lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += S.vol[i];
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (threadIdx.x == 0) *out = s;
 }
 
 // ---- state transfer -------------------------------------------------------

@@ -155,6 +155,17 @@ class Run:
                              C.c_void_p(_stream(stream))), "rvea_igd")
         return float(out.value)
 
+    def hypervolume(self, ref, stream=None) -> float:
+        """Hypervolume of the current population (m = 2 or 3) against the
+        reference point `ref` (m values)."""
+        if len(ref) != self.m:
+            raise ValueError("ref must have m values")
+        r = (C.c_double * self.m)(*[float(v) for v in ref])
+        out = C.c_double()
+        check(lib().rvea_hypervolume(self._h, r, C.byref(out), C.c_void_p(_stream(stream))),
+              "rvea_hypervolume")
+        return float(out.value)
+
     def export_state(self, stream=None) -> dict:
         dev = self.device
         X = torch.empty((self.N, self.d), dtype=torch.float32, device=dev)

@@ -293,3 +293,25 @@ def test_igd_matches_oracle(orc, shape):
     o = orc.igd(st["F"].astype(np.float64), st["valid"], R.astype(np.float64))
     assert abs(g - o) <= 1e-5 * o + 1e-7, (g, o)
     run.sync_status()
+
+
+@pytest.mark.parametrize("shape", [(3, 12, 105, 13, 0), (3, 300, 1275, 49, 1),
+                                   (2, 1500, 100, 99, 4), (2, 40, 1200, 1199, 0)])
+def test_hypervolume_matches_oracle(orc, shape):
+    """Hypervolume of the GPU population (Appendix C) against the oracle's
+    slicing on the same objective vectors, for a reference point beyond
+    every member and for one at the per-objective 75th percentile (members
+    beyond it drop out on both sides)."""
+    m, d, N, H, prob = shape
+    p = params(orc, m, d, N, H, prob, t_max=50, seed=23)
+    run = make_run(p)
+    run.step(6)
+    st = to_np(run.export_state())
+    F = st["F"].astype(np.float64)
+    Fv = F[st["valid"].astype(bool)]
+    for ref in (1.1 * Fv.max(axis=0), np.percentile(Fv, 75, axis=0)):
+        g = run.hypervolume(ref.tolist())
+        o = orc.hypervolume(F, st["valid"], ref)
+        assert abs(g - o) <= 1e-9 * o, (g, o, ref)
+    assert o <= orc.hypervolume(F, st["valid"], 1.1 * Fv.max(axis=0))
+    run.sync_status()
