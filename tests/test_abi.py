@@ -89,3 +89,16 @@ def test_init_ex_requires_the_unit_box_for_dtlz(native):
     cfg.upper = 2.0
     assert L.rvea_init_ex(C.byref(cfg), ws, 1 << 30, None, C.byref(h)) == native.ERR_ARG
     assert not h.value
+
+
+def test_metrics_and_counters_reject_null_without_gpu(native):
+    """The metric and counter entry points check their handles before any
+    device work: NULL run / batch / output pointers are refused."""
+    L = native.lib()
+    out = C.c_double(-1.0)
+    ref = (C.c_double * 3)(1.0, 1.0, 1.0)
+    assert L.rvea_hypervolume(None, ref, C.byref(out), None) == native.ERR_ARG
+    assert L.rvea_igd(None, C.c_void_p(1 << 20), 4, C.byref(out), None) == native.ERR_ARG
+    assert out.value == -1.0
+    assert L.rvea_launches_per_generation(None, 0) == -1
+    assert L.rvea_batch_launches_per_step(None) == -1
