@@ -262,6 +262,15 @@ rvea_status rvea_igd(const rvea_run *run, const float *ref, int n_ref, double *o
 rvea_status rvea_hypervolume(const rvea_run *run, const double *ref, double *out,
                              void *cuda_stream);
 
+/* Failure-detection self-test: one kernel waits, with a limit of `polls`
+ * (1..2^20) mbarrier polls, on a barrier that nothing arrives at, as the
+ * reproduction and association kernels wait for their copies.  Returns
+ * RVEA_ERR_TIMEOUT when the wait gave up and reported it (the designed
+ * outcome; the context stays usable), RVEA_OK if the barrier completed
+ * (cannot happen), RVEA_ERR_ARG for polls out of range, RVEA_ERR_CUDA on a
+ * launch or copy error.  Synchronises `cuda_stream`; uses no run. */
+rvea_status rvea_selftest_wait(int polls, void *cuda_stream);
+
 /* Kernel launches rvea_step enqueues for one generation of `run` (adapting:
  * a generation with t % ceil(f_r t_max) == 0, which also rescales V); -1 if
  * run is NULL. */

@@ -95,6 +95,8 @@ def lib():
         L.rvea_objectives.argtypes = [vp, vp, vp, vp]
         L.rvea_igd.argtypes = [vp, vp, i32, C.POINTER(C.c_double), vp]
         L.rvea_igd.restype = i32
+        L.rvea_selftest_wait.argtypes = [i32, vp]
+        L.rvea_selftest_wait.restype = i32
         L.rvea_hypervolume.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.rvea_hypervolume.restype = i32
         L.rvea_objectives.restype = i32

@@ -102,3 +102,5 @@ def test_metrics_and_counters_reject_null_without_gpu(native):
     assert out.value == -1.0
     assert L.rvea_launches_per_generation(None, 0) == -1
     assert L.rvea_batch_launches_per_step(None) == -1
+    assert L.rvea_selftest_wait(0, None) == native.ERR_ARG
+    assert L.rvea_selftest_wait(1 << 21, None) == native.ERR_ARG

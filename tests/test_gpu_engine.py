@@ -122,3 +122,15 @@ def test_launch_counts(orc):
         assert 5 <= b.launches_per_step() <= 9
     finally:
         b.free()
+
+
+def test_bounded_wait_reports_timeout(orc):
+    """Failure detection without a fault: a kernel waits on an mbarrier that
+    nothing arrives at, with a short poll limit, and reports the timeout to
+    the host; the context stays usable (a run steps cleanly afterwards)."""
+    from paper_2404_01159_gb300 import _native
+    L = _native.lib()
+    assert L.rvea_selftest_wait(64, None) == _native.ERR_TIMEOUT
+    run = make_run(params(orc, 3, 12, 105, 13, 0, t_max=10, seed=1))
+    run.step(2)
+    run.sync_status()
