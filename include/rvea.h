@@ -368,13 +368,17 @@ rvea_status rvea_server_create(void *dev_arena, size_t arena_bytes, int max_live
                                rvea_server **out);
 
 /* Queue a request (DTLZ problems; cfg->neuro must be NULL); *id_out gets its
- * id (1, 2, ...).  Validation of cfg happens at admission. */
+ * id (1, 2, ...).  cfg is validated here, on the host: RVEA_ERR_ARG for an
+ * invalid configuration (rvea_workspace_bytes_ex returns 0, a lattice
+ * mismatch included) or generations < 1, RVEA_ERR_NOMEM when its workspace
+ * exceeds the whole arena; nothing is queued then. */
 rvea_status rvea_server_submit(rvea_server *srv, const rvea_config *cfg, int generations,
                                int64_t *id_out);
 
 /* Admission, then one generation of every live run, on `cuda_stream`.
  * Admission synchronises the stream (initialisation uploads).  stats may be
- * NULL.  A request that fails validation at admission returns its error. */
+ * NULL.  A request whose initialisation fails on the device is dropped and
+ * its error returned. */
 rvea_status rvea_server_step(rvea_server *srv, void *cuda_stream, rvea_server_stats *stats);
 
 /* Ids of runs whose budget was spent since the last poll (up to cap); their

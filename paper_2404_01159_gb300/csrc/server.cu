@@ -86,6 +86,7 @@ struct Live {
 
 struct rvea_server {
   uint8_t *arena_base = nullptr;
+  size_t arena_bytes = 0;
   Arena arena;
   int max_live = 0;
   int tune = 1;
@@ -108,6 +109,7 @@ rvea_status rvea_server_create(void *dev_arena, size_t arena_bytes, int max_live
   rvea_server *s = new (std::nothrow) rvea_server(arena_bytes);
   if (!s) return RVEA_ERR_NOMEM;
   s->arena_base = static_cast<uint8_t *>(dev_arena);
+  s->arena_bytes = arena_bytes;
   s->max_live = max_live;
   s->tune = autotune ? 1 : 0;
   *out = s;
@@ -117,9 +119,11 @@ rvea_status rvea_server_create(void *dev_arena, size_t arena_bytes, int max_live
 rvea_status rvea_server_submit(rvea_server *s, const rvea_config *cfg, int generations,
                                int64_t *id_out) {
   if (!s || !cfg || generations < 1 || cfg->neuro) return RVEA_ERR_ARG;
-  // a request whose workspace can never fit is refused at once
-  const size_t need = rvea_workspace_bytes(cfg->m, cfg->d, cfg->N);
+  // an invalid configuration, or one whose workspace can never fit the
+  // arena, is refused at once (it would otherwise block the queue's head)
+  const size_t need = rvea_workspace_bytes_ex(cfg);
   if (need == 0) return RVEA_ERR_ARG;
+  if (align_up(need) > s->arena_bytes) return RVEA_ERR_NOMEM;
   Request r;
   r.id = s->next_id++;
   r.cfg = *cfg;
@@ -134,16 +138,17 @@ rvea_status rvea_server_step(rvea_server *s, void *cuda_stream, rvea_server_stat
   // admission, in arrival order, while the head of the queue fits
   int admitted = 0;
   while (!s->queue.empty() && (int)s->live.size() < s->max_live) {
-    const Request &q = s->queue.front();
-    const size_t bytes = rvea_workspace_bytes(q.cfg.m, q.cfg.d, q.cfg.N);
+    const Request q = s->queue.front();
+    const size_t bytes = rvea_workspace_bytes_ex(&q.cfg);
     const size_t off = s->arena.alloc(bytes);
     if (off == SIZE_MAX) break;
     rvea_run *run = nullptr;
     rvea_status st = rvea_init_ex(&q.cfg, s->arena_base + off, bytes, cuda_stream, &run);
     if (st == RVEA_OK && s->tune) st = rvea_autotune(run, cuda_stream, 1, nullptr);
-    if (st != RVEA_OK) {
+    if (st != RVEA_OK) {   // a device error: the request is dropped, the error returned
       if (run) rvea_free(run);
       s->arena.release(off, bytes);
+      s->queue.pop_front();
       return st;
     }
     s->live.push_back(Live{q.id, run, off, bytes, q.generations});

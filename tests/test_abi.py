@@ -104,3 +104,37 @@ def test_metrics_and_counters_reject_null_without_gpu(native):
     assert L.rvea_batch_launches_per_step(None) == -1
     assert L.rvea_selftest_wait(0, None) == native.ERR_ARG
     assert L.rvea_selftest_wait(1 << 21, None) == native.ERR_ARG
+
+
+def test_server_admission_refusals_without_gpu(native):
+    """Serving loop, host side only (no step runs, so the arena is never
+    touched): an invalid request or one that can never fit the arena is
+    refused at submission and not queued; a valid one is queued with id 1;
+    nothing is finished; fetching an unknown id is a state error."""
+    L = native.lib()
+    srv = C.c_void_p()
+    arena_bytes = 64 << 20
+    assert L.rvea_server_create(C.c_void_p(1 << 20), arena_bytes, 4, 0, C.byref(srv)) == native.OK
+    try:
+        def cfg(**kw):
+            base = dict(m=3, d=12, N=105, H=13, problem=0, t_max=100, alpha=2.0, f_r=0.1,
+                        eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, lower=0.0, upper=1.0,
+                        seed=0, neuro=None)
+            base.update(kw)
+            return native.Config(**base)
+        rid = C.c_int64(0)
+        sub = lambda c, g=10: L.rvea_server_submit(srv, C.byref(c), g, C.byref(rid))
+        assert sub(cfg(N=100)) == native.ERR_ARG            # not the lattice size of H = 13
+        assert sub(cfg(eta_c=0.0)) == native.ERR_ARG
+        assert sub(cfg(), g=0) == native.ERR_ARG
+        big = cfg(m=3, d=5000, N=9870, H=139)                 # ~0.4 GB > the 64 MB arena
+        assert L.rvea_workspace_bytes(3, 5000, 9870) > arena_bytes
+        assert sub(big) == native.ERR_NOMEM
+        assert rid.value == 0                                  # nothing queued so far
+        assert sub(cfg()) == native.OK and rid.value == 1
+        ids = (C.c_int64 * 4)()
+        n = C.c_int(-1)
+        assert L.rvea_server_poll(srv, ids, 4, C.byref(n)) == native.OK and n.value == 0
+        assert L.rvea_server_fetch(srv, 1, None, None, None, None) == native.ERR_STATE
+    finally:
+        L.rvea_server_free(srv)
