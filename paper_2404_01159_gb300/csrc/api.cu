@@ -24,6 +24,7 @@
 #include "../../include/rvea.h"
 #include "rvea_device.cuh"
 #include "metrics.cuh"
+#include "nvtx_range.h"
 
 namespace rvea {
 __global__ void k_reprob_dtlz1(const __grid_constant__ BatchDir dir);
@@ -988,6 +989,7 @@ rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
   while (G > 0) {
     const int p = r->p_adapt;
     if (r->use_graph && p > 1 && G >= p && (r->t % p) == 1) {
+      const NvtxRange nr("rvea generations (one adaptation period, graph)", r->t);
       rvea_status s = ensure_block_graph(r);
       if (s != RVEA_OK) return s;
       RV_TRY(cudaGraphLaunch(r->block_graph, st));
@@ -996,7 +998,11 @@ rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
       r->has_last_gen = true;
       continue;
     }
-    const rvea_status s = enqueue_one(r, st);
+    rvea_status s;
+    {
+      const NvtxRange nr("rvea generation", r->t);
+      s = enqueue_one(r, st);
+    }
     if (s != RVEA_OK) return s;
     r->t += 1;
     G -= 1;
@@ -1273,6 +1279,7 @@ int rvea_batch_launches_per_step(const rvea_batch *b) { return b ? b->kernels : 
 rvea_status rvea_batch_step(rvea_batch *b, int G, void *cuda_stream) {
   if (!b || G < 0) return RVEA_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const NvtxRange nr("rvea batched generations", G);
   for (int q = 0; q < G; ++q) RV_TRY(cudaGraphLaunch(b->exec, st));
   for (rvea_run *r : b->runs) {
     r->t += G;

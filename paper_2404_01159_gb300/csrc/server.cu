@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/rvea.h"
+#include "nvtx_range.h"
 
 namespace {
 
@@ -135,6 +136,7 @@ rvea_status rvea_server_submit(rvea_server *s, const rvea_config *cfg, int gener
 
 rvea_status rvea_server_step(rvea_server *s, void *cuda_stream, rvea_server_stats *stats) {
   if (!s) return RVEA_ERR_ARG;
+  const rvea::NvtxRange nr("rvea server step", (int64_t)s->live.size());
   // admission, in arrival order, while the head of the queue fits
   int admitted = 0;
   while (!s->queue.empty() && (int)s->live.size() < s->max_live) {
