@@ -1,6 +1,6 @@
-"""The replica path of bench.py on CPU: two gloo ranks on 127.0.0.1, each
+"""bench.py on CPU.  The replica path: two gloo ranks on 127.0.0.1, each
 with its own time; the job's time is the slowest rank's and the value counts
-the generations of every rank."""
+the generations of every rank.  The reference arm: its JSON line."""
 import os
 import socket
 import sys
@@ -47,3 +47,21 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(3.0, None, "cpu") == 3.0
     assert bench.replica_value(1, 10, 2.0) == 5000.0
+
+
+def test_reference_arm_json_line_on_cpu():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints
+    one JSON line with the contract's keys, here on the small workload."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "dtlz2_m3_d12_N105", "--steps", "3", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, check=True).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "steps", "warmup", "higher_is_better",
+                "cpu_baseline", "e2e", "config"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "dtlz2_m3_d12_N105"
