@@ -82,6 +82,10 @@ def lib():
         L.orc_generation.argtypes = [P(Params), C.c_int32, f64, P(Neuro),
                                      f64, f64, u8, f64, f64, f64, f64, i32, i32, i32]
         L.orc_generation.restype = C.c_int32
+        L.orc_random_offspring.argtypes = [P(Params), C.c_int32, f64]
+        L.orc_de_picks.argtypes = [P(Params), C.c_int32, C.c_int32, C.c_int32, i32]
+        L.orc_de_offspring.argtypes = [P(Params), C.c_int32, f64, C.c_int32, i32,
+                                       C.c_double, C.c_double, f64]
         L.orc_set_threads.argtypes = [C.c_int32]
         L.orc_get_threads.restype = C.c_int32
         _lib = L
@@ -219,6 +223,33 @@ def mutation(p: Params, t, Xc):
     mask = np.zeros((p.N, p.d), dtype=np.uint8)
     lib().orc_mutation(C.byref(p), t, _p(Xm, C.c_double), _p(mask, C.c_uint8))
     return Xm, mask
+
+
+def random_offspring(p: Params, t):
+    """Random reproduction (the extensibility experiment's baseline): N x d
+    uniform offspring on [L, U]."""
+    X = np.zeros((p.N, p.d))
+    lib().orc_random_offspring(C.byref(p), t, _p(X, C.c_double))
+    return X
+
+
+def de_picks(p: Params, t, K, o):
+    """(target position, r1, r2, r3 positions in the valid list, j_rand) of
+    DE offspring o."""
+    out = np.zeros(5, dtype=np.int32)
+    lib().orc_de_picks(C.byref(p), t, K, o, _p(out, C.c_int32))
+    return tuple(int(v) for v in out)
+
+
+def de_offspring(p: Params, t, X, vlist, F=0.5, CR=0.9):
+    """DE/rand/1/bin offspring (N x d) of the population X (rows by slot)
+    with the valid list vlist."""
+    X = _f64(X)
+    vl = np.ascontiguousarray(vlist, dtype=np.int32)
+    out = np.zeros((p.N, p.d))
+    lib().orc_de_offspring(C.byref(p), t, _p(X, C.c_double), len(vl), _p(vl, C.c_int32),
+                           float(F), float(CR), _p(out, C.c_double))
+    return out
 
 
 def select(F, valid, V, gam, t, t_max, alpha):

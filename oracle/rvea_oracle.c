@@ -407,6 +407,89 @@ void orc_mating(const orc_params *p, int32_t t, int32_t K, const int32_t *vlist,
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Alternative reproduction operators of the extensibility experiment (Sec.  */
+/* 4.4 and Appendix C: GA, PSO, DE, CSO and random reproduction inside the   */
+/* same environmental selection).  The paper cites them without printing     */
+/* them; these follow the published operators.  Offspring o = 0..N-1 fill   */
+/* the N offspring rows as SBX's do.                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Random reproduction (the experiment's baseline): x_oj = L + (U - L) u24,
+ * u24 from RANDOM (j/4, o, t) word j%4. */
+void orc_random_offspring(const orc_params *p, int32_t t, double *Xout)
+{
+    const int32_t N = p->N, d = p->d;
+    for (int32_t o = 0; o < N; ++o)
+        for (int32_t j = 0; j < d; ++j) {
+            uint32_t w[4];
+            philox(p, (uint32_t)(j / 4), (uint32_t)o, (uint32_t)t, ORC_TAG_RANDOM, w);
+            Xout[(int64_t)o * d + j] = p->L + (p->U - p->L) * u24(w[j % 4]);
+        }
+}
+
+/* DE/rand/1/bin draws of offspring o (Storn and Price 1997): out[0] = the
+ * target's position o mod K in the valid list, out[1..3] = the positions of
+ * r1, r2, r3, out[4] = j_rand.  With K >= 4 the three are a uniformly random
+ * ordered triple of distinct positions other than the target's, drawn one
+ * after another without replacement from DE_PICK (o, 0, t) words 0..2
+ * (a in [0, K-1), b in [0, K-2), c in [0, K-3), each index = (w n) >> 32,
+ * counted over the positions not yet taken); with K < 4 each is drawn with
+ * replacement over all K.  j_rand = (w d) >> 32 of word 3. */
+void orc_de_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out)
+{
+    uint32_t w[4];
+    philox(p, (uint32_t)o, 0u, (uint32_t)t, ORC_TAG_DE_PICK, w);
+    const int32_t tpos = o % K;
+    out[0] = tpos;
+    if (K >= 4) {
+        /* positions 0..K-2 of the list without the target */
+        int32_t a = (int32_t)(((uint64_t)w[0] * (uint64_t)(K - 1)) >> 32);
+        int32_t b = (int32_t)(((uint64_t)w[1] * (uint64_t)(K - 2)) >> 32);
+        int32_t c = (int32_t)(((uint64_t)w[2] * (uint64_t)(K - 3)) >> 32);
+        if (b >= a) b += 1;
+        const int32_t lo = a < b ? a : b, hi = a < b ? b : a;
+        if (c >= lo) c += 1;
+        if (c >= hi) c += 1;
+        const int32_t q[3] = {a, b, c};
+        for (int32_t k = 0; k < 3; ++k) out[1 + k] = q[k] < tpos ? q[k] : q[k] + 1;
+    } else {
+        for (int32_t k = 0; k < 3; ++k)
+            out[1 + k] = (int32_t)(((uint64_t)w[k] * (uint64_t)K) >> 32);
+    }
+    out[4] = (int32_t)(((uint64_t)w[3] * (uint64_t)p->d) >> 32);
+}
+
+/* DE/rand/1/bin as the reproduction operator: offspring o takes the target
+ * x_t = X[vlist[o mod K]] and v = x_r1 + F (x_r2 - x_r3) (orc_de_picks);
+ * u_j = v_j where the CR coin of j fires or j = j_rand, else x_t,j; the coin
+ * fires iff u24 < ceil(CR 2^24) / 2^24, u24 from DE_CR (j/4, o, t) word j%4;
+ * then u is clipped to [L, U].  X: population rows by slot. */
+void orc_de_offspring(const orc_params *p, int32_t t, const double *X, int32_t K,
+                      const int32_t *vlist, double F, double CR, double *Xout)
+{
+    const int32_t N = p->N, d = p->d;
+    const uint32_t thr = (uint32_t)ceil(CR * 16777216.0);
+    for (int32_t o = 0; o < N; ++o) {
+        int32_t pk[5];
+        orc_de_picks(p, t, K, o, pk);
+        const double *xt = X + (int64_t)vlist[pk[0]] * d;
+        const double *x1 = X + (int64_t)vlist[pk[1]] * d;
+        const double *x2 = X + (int64_t)vlist[pk[2]] * d;
+        const double *x3 = X + (int64_t)vlist[pk[3]] * d;
+        double *u = Xout + (int64_t)o * d;
+        for (int32_t j = 0; j < d; ++j) {
+            uint32_t w[4];
+            philox(p, (uint32_t)(j / 4), (uint32_t)o, (uint32_t)t, ORC_TAG_DE_CR, w);
+            const int take = (w[j % 4] >> 8) < thr || j == pk[4];
+            double v = take ? x1[j] + F * (x2[j] - x3[j]) : xt[j];
+            if (v < p->L) v = p->L;
+            if (v > p->U) v = p->U;
+            u[j] = v;
+        }
+    }
+}
+
 /* Tensorized SBX, Appendix B (the two B equations and X_cross):
  *   B  = sgn(R1 - 1/2) [H(1/2 - Mc)(2Mc)^(1/(eta+1)) + (1 - H(1/2 - Mc))(2 - 2Mc)^(-1/(eta+1))]
  *   B  = [1 - rep(H(R3 - p_c))] [(1 - H(R2 - 1/2)) B + H(R2 - 1/2)] + rep(H(R3 - p_c))

@@ -35,7 +35,8 @@ extern "C" {
 
 enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2, ORC_DTLZ3 = 3, ORC_DTLZ4 = 4 };
 enum { ORC_TAG_INIT = 1, ORC_TAG_MATE = 2, ORC_TAG_PAIR = 3, ORC_TAG_SBX = 4,
-       ORC_TAG_MUTSITE = 5, ORC_TAG_MUTMAG = 6, ORC_TAG_NOISE = 7 };
+       ORC_TAG_MUTSITE = 5, ORC_TAG_MUTMAG = 6, ORC_TAG_NOISE = 7,
+       ORC_TAG_DE_PICK = 8, ORC_TAG_DE_CR = 9, ORC_TAG_RANDOM = 10 };
 
 typedef struct {
     int32_t m, d, N, H;
@@ -84,6 +85,10 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
                        double *Xchild, double *Fchild, int32_t *parents,
                        int32_t *assoc, int32_t *survivor);
 
+void orc_random_offspring(const orc_params *p, int32_t t, double *Xout);
+void orc_de_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out);
+void orc_de_offspring(const orc_params *p, int32_t t, const double *X, int32_t K,
+                      const int32_t *vlist, double F, double CR, double *Xout);
 void orc_set_threads(int32_t n);
 int32_t orc_get_threads(void);
 

@@ -1,0 +1,126 @@
+"""Pins of the oracle's alternative reproduction operators (the extensibility
+experiment, Sec. 4.4 / Appendix C): random reproduction and DE/rand/1/bin.
+Each pin checks a property the published operator fixes, independently of
+the oracle's own arithmetic."""
+import itertools
+
+import numpy as np
+import pytest
+
+
+def _p(orc, **kw):
+    base = dict(m=3, d=6, N=8, H=0, problem=orc.DTLZ2, t_max=100, seed=3)
+    base.update(kw)
+    return orc.make_params(**base)
+
+
+def test_random_offspring(orc):
+    """Uniform on the box, on the 24-bit grid, a different draw per
+    generation, the same on a repeat."""
+    p = _p(orc, N=500, d=40)
+    X = orc.random_offspring(p, 5)
+    assert X.shape == (500, 40) and X.min() >= 0.0 and X.max() < 1.0
+    assert np.array_equal(X * 2**24, np.floor(X * 2**24))
+    n = X.size
+    assert abs(X.mean() - 0.5) < 5 * np.sqrt(1 / 12 / n)
+    assert abs(X.var() - 1 / 12) < 5 * np.sqrt(1 / 180 / n)
+    assert np.array_equal(X, orc.random_offspring(p, 5))
+    assert not np.array_equal(X, orc.random_offspring(p, 6))
+    pb = _p(orc, N=50, d=10, L=-1.0, U=1.0)
+    Xb = orc.random_offspring(pb, 1)
+    assert Xb.min() >= -1.0 and Xb.max() < 1.0
+
+
+def test_de_picks_distinct_and_uniform(orc):
+    """r1, r2, r3 are distinct and differ from the target; as an ordered
+    triple over the other K - 1 positions they are uniform (chi-square over
+    the 24 triples of K = 5); j_rand is uniform over the d variables."""
+    p = _p(orc, d=7)
+    K, n = 5, 24000
+    counts = {}
+    jr = np.zeros(7)
+    for o in range(n):
+        tpos, a, b, c, j = orc.de_picks(p, 2, K, o)
+        assert tpos == o % K
+        assert len({tpos, a, b, c}) == 4 and all(0 <= q < K for q in (a, b, c))
+        others = [q for q in range(K) if q != tpos]
+        key = (others.index(a), others.index(b), others.index(c))
+        counts[key] = counts.get(key, 0) + 1
+        jr[j] += 1
+    assert len(counts) == 24
+    e = n / 24
+    chi2 = sum((v - e) ** 2 / e for v in counts.values())
+    assert chi2 < 80, chi2          # 23 degrees of freedom; p ~ 1e-7 at 80
+    e7 = n / 7
+    assert sum((v - e7) ** 2 / e7 for v in jr) < 45   # 6 degrees of freedom
+    # fewer than four valid members: with replacement, in range
+    for o in range(200):
+        tpos, a, b, c, _ = orc.de_picks(p, 2, 3, o)
+        assert all(0 <= q < 3 for q in (tpos, a, b, c))
+
+
+def test_de_offspring_special_cases(orc):
+    """F = 0, CR = 1: every offspring is its base vector x_r1.  CR = 0: only
+    variable j_rand leaves the target.  Invalid members (absent from the
+    valid list) are never used.  The CR coin fires at rate CR."""
+    rng = np.random.default_rng(7)
+    p = _p(orc, N=12, d=9)
+    X = rng.uniform(0, 1, (12, 9))
+    vlist = np.array([0, 2, 3, 5, 7, 8, 11])
+    U0 = orc.de_offspring(p, 4, X, vlist, F=0.0, CR=1.0)
+    for o in range(12):
+        _, a, _, _, _ = orc.de_picks(p, 4, len(vlist), o)
+        assert np.array_equal(U0[o], X[vlist[a]])
+    valid_rows = {tuple(X[v]) for v in vlist}
+    assert all(tuple(u) in valid_rows for u in U0)
+    Uc = orc.de_offspring(p, 4, X, vlist, F=0.5, CR=0.0)
+    for o in range(12):
+        tpos, a, b, c, j = orc.de_picks(p, 4, len(vlist), o)
+        xt = X[vlist[tpos]]
+        keep = np.arange(9) != j
+        assert np.array_equal(Uc[o][keep], xt[keep])
+        v = X[vlist[a], j] + 0.5 * (X[vlist[b], j] - X[vlist[c], j])
+        assert Uc[o, j] == min(max(v, 0.0), 1.0)
+    pw = _p(orc, N=40, d=400)
+    Xw2 = rng.uniform(0.25, 0.75, (40, 400))   # inside the box: only taken variables change
+    U = orc.de_offspring(pw, 1, Xw2, np.arange(40), F=0.5, CR=0.3)
+    taken = 0
+    total = 0
+    for o in range(40):
+        tpos, a, b, c, j = orc.de_picks(pw, 1, 40, o)
+        diff = U[o] != Xw2[tpos]
+        diff[j] = False
+        taken += diff.sum()
+        total += 399
+    rate = taken / total
+    assert abs(rate - 0.3) < 5 * np.sqrt(0.3 * 0.7 / total), rate
+
+
+def test_de_offspring_brute_force(orc):
+    """CR = 1: every offspring is clip(x_a + F (x_b - x_c)) for an ordered
+    triple of distinct members other than its target (o mod K), found by
+    trying all of them."""
+    rng = np.random.default_rng(9)
+    N, d, F = 6, 5, 0.7
+    p = _p(orc, N=N, d=d)
+    X = rng.uniform(0, 1, (N, d))
+    U = orc.de_offspring(p, 3, X, np.arange(N), F=F, CR=1.0)
+    for o in range(N):
+        t = o % N
+        cands = [q for q in range(N) if q != t]
+        ok = any(np.array_equal(U[o], np.clip(X[a] + F * (X[b] - X[c]), 0.0, 1.0))
+                 for a, b, c in itertools.permutations(cands, 3))
+        assert ok, o
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_de_offspring_tiny_valid_lists(orc, K):
+    """With fewer than four valid members the draws repeat members; with one,
+    every offspring is that member."""
+    p = _p(orc, N=5, d=4)
+    X = np.random.default_rng(1).uniform(0, 1, (5, 4))
+    vlist = np.arange(K) + 1
+    U = orc.de_offspring(p, 1, X, vlist, F=0.5, CR=0.9)
+    assert np.isfinite(U).all() and U.min() >= 0 and U.max() <= 1
+    if K == 1:
+        assert (U == X[1]).all()
