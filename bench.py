@@ -209,7 +209,7 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
-BATCHED = "batched256_cfg3"
+BATCHED = "batched256_uneven"
 
 
 def batch_bytes(insts) -> int:
@@ -329,8 +329,8 @@ def main_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-SERVE = "serve_cfg4"
-NEURO = "neuro100_cfg2"
+SERVE = "serve_poisson200"
+NEURO = "neuro100x100_steps1000"
 
 
 def main_neuro(args, rank, world, local):

@@ -23,8 +23,9 @@ def _cuda():
     _native.lib()
 
 
-# (m, d, N, H, problem): cfg0 shape, a ragged DTLZ1 case spanning several
-# reproduction CTAs / selection blocks / vector tiles, and m = 2 / 5 / 10;
+# (m, d, N, H, problem): the small DTLZ2 benchmark shape, a ragged DTLZ1 case
+# spanning several reproduction CTAs / selection blocks / vector tiles, and
+# m = 2 / 5 / 10;
 # (d > 1024) take the shared-memory-staged reproduction path, with segments
 # of several chunks, a partial last chunk and row padding; two are large
 # populations (N = 4200, 2100 pairs) on the register and the staged load

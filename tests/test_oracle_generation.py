@@ -14,7 +14,7 @@ import pytest
 from scipy import stats
 
 
-def _cfg0(orc, **kw):
+def _small(orc, **kw):
     base = dict(m=3, d=12, N=105, H=13, problem=orc.DTLZ2, t_max=100, alpha=2.0,
                 f_r=0.1, seed=3)
     base.update(kw)
@@ -27,7 +27,7 @@ def igd(F, front):
 
 
 def test_generation_is_composition(orc):
-    p = _cfg0(orc)
+    p = _small(orc)
     V0, st = orc.initial_state(p)
     for _ in range(3):
         orc.generation(p, V0, st)
@@ -57,7 +57,7 @@ def test_generation_is_composition(orc):
 
 
 def test_thread_count_invariance(orc):
-    p = _cfg0(orc, d=40, N=210, H=19)
+    p = _small(orc, d=40, N=210, H=19)
     res = []
     for th in (1, 4):
         orc.set_threads(th)
@@ -73,7 +73,7 @@ def test_thread_count_invariance(orc):
 
 
 def test_adaptation_schedule(orc):
-    p = _cfg0(orc, t_max=30, f_r=0.2)       # period 6
+    p = _small(orc, t_max=30, f_r=0.2)       # period 6
     assert orc.adapt_period(p) == 6
     V0, st = orc.initial_state(p)
     prev = st.V.copy()
@@ -89,7 +89,7 @@ def test_adaptation_schedule(orc):
 
 
 def test_free_running_quality_dtlz2(orc):
-    p = _cfg0(orc)
+    p = _small(orc)
     V0, st = orc.initial_state(p)
     front = orc.lattice_unit(orc.lattice(3, 30))
     igd0 = igd(st.F, front)
