@@ -64,7 +64,7 @@ __device__ __forceinline__ float2 dotv2(const float2 *fab, const float4 *v) {
 }
 
 // Chunk scan for two solutions: the running maximum of each 32-vector
-// sub-tile costs one FMNMX per dot; a sub-tile replaces the best only on a
+// sub-tile costs one fmaxf per dot; a sub-tile replaces the best only on a
 // strict improvement, so `sub` is the first sub-tile holding the maximum.
 template <int M>
 __device__ void scan_chunk(const float4 *__restrict__ sv, int nv, const float *fpa,
