@@ -284,7 +284,9 @@ rvea_status rvea_export_state(const rvea_run *run, float *X, float *F, uint8_t *
                               double *V, double *gamma, void *cuda_stream);
 
 /* Replace the run state (same layouts as rvea_export_state; all required)
- * and set the next generation index to t >= 1.  F is taken as given. */
+ * and set the next generation index to t >= 1.  F is taken as given.
+ * RVEA_ERR_ARG, with the run unchanged, when no member is valid (mating
+ * would have nothing to draw from).  Synchronises `cuda_stream`. */
 rvea_status rvea_import_state(rvea_run *run, const float *X, const float *F,
                               const uint8_t *valid, const double *V,
                               const double *gamma, int t, void *cuda_stream);
@@ -300,6 +302,27 @@ rvea_status rvea_offspring(const rvea_run *run, float *X, float *F, void *cuda_s
  * parent) and survivor (N i32; combined index kept by vector j, or -1). */
 rvea_status rvea_last_selection(const rvea_run *run, int32_t *assoc, int32_t *survivor,
                                 void *cuda_stream);
+
+/* Draw recording, for inspection and bit-exact testing of the random
+ * decisions of Appendix B: with enable != 0 every later generation of the
+ * run also writes, into its workspace, (i) the vector slot drawn for each
+ * parent (the mating draws that partition X into X1 and X2; draw e < P is
+ * the first parent of pair e, draw P + e its second, P = ceil(N/2)) and
+ * (ii) the mutation sites of each child c = 0..N-1 (the variables where the
+ * mask C of the polynomial mutation is 1).  Off by default; recording costs
+ * about 4 (2P + 33 N) bytes of writes per generation.  Enqueued on
+ * `cuda_stream`; applies to direct launches and graph replays alike. */
+rvea_status rvea_record_draws(rvea_run *run, int enable, void *cuda_stream);
+
+/* The draws of the last completed generation, which must have run with
+ * recording on (else RVEA_ERR_STATE).  parents: 2P int32, the vector slot
+ * (0..N-1, slot order of the parent population) of each draw.  sites:
+ * N x 33 int32, row c = [k, s_1..s_k, unused...]: k the number of mutation
+ * sites of child c (-1 when every variable mutates: per-site probability 1)
+ * and s_i the 0-based variables in draw order (distinct).  Host or device
+ * pointers, either may be NULL. */
+rvea_status rvea_last_draws(const rvea_run *run, int32_t *parents, int32_t *sites,
+                            void *cuda_stream);
 
 /* ---- stateless operators ---------------------------------------------- */
 
@@ -325,16 +348,20 @@ rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid,
  * process whose device memory is all reserved by another caching allocator.
  * (The paper has no counterpart: this is a deployment variant of rvea_select.)
  * Same arguments and results as rvea_select, bit for bit, without the
- * scratch argument: the scratch is a 4 MiB array inside the library, reserved
- * on every GPU that loads the library until the process exits.  Limits:
- * n <= 65536, r <= 16384, and the shape's scratch must fit the 4 MiB;
- * larger sizes return RVEA_ERR_NOMEM before any GPU work.  The call itself
- * allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
- * The first call on a device looks up the array's device address and sets
- * the selection kernel's shared-memory limit, with that device current:
- * make that first call before any stream capture.  Every call shares the one
- * array and clears what it reads; calls whose GPU work overlaps (e.g. on
- * unordered streams) race and corrupt each other's results. */
+ * scratch argument: the scratch is a 4 MiB array inside the library.
+ * Limits: n <= 65536, r <= 16384, and the shape's scratch must fit the
+ * 4 MiB; larger sizes return RVEA_ERR_NOMEM before any GPU work.
+ * Set-up: the array lives in its own GPU module of the library, which CUDA
+ * loads on a device -- reserving the 4 MiB there until the process exits --
+ * at the first call on that device (lazy module loading, CUDA's default;
+ * with CUDA_MODULE_LOADING=EAGER, when the process first uses the device).
+ * That first call also looks up the array's device address and sets the
+ * selection kernel's shared-memory limit, with the device current: make it
+ * before the caller's device memory is fully reserved and before any stream
+ * capture.  After it, a call allocates no device memory and no host memory
+ * (no cudaMalloc/cudaFree, no allocating library call).  Every call shares
+ * the one array and clears what it reads; calls whose GPU work overlaps (e.g.
+ * on unordered streams) race and corrupt each other's results. */
 rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *valid,
                                 int r, const float *V, const float *gamma,
                                 int t, int t_max, float alpha,
@@ -377,8 +404,11 @@ rvea_status rvea_server_submit(rvea_server *srv, const rvea_config *cfg, int gen
 
 /* Admission, then one generation of every live run, on `cuda_stream`.
  * Admission synchronises the stream (initialisation uploads).  stats may be
- * NULL.  A request whose initialisation fails on the device is dropped and
- * its error returned. */
+ * NULL.  A request whose admission fails (initialisation or tuning returns
+ * an error) ends there: rvea_server_poll reports its id like a finished
+ * one and rvea_server_fetch returns its error; the step goes on with the
+ * other requests.  The step's own return value reports the batched
+ * generations only. */
 rvea_status rvea_server_step(rvea_server *srv, void *cuda_stream, rvea_server_stats *stats);
 
 /* Ids of runs whose budget was spent since the last poll (up to cap); their
@@ -387,7 +417,8 @@ rvea_status rvea_server_poll(rvea_server *srv, int64_t *ids, int cap, int *n_out
 
 /* Copy a finished run's population (N x d) and objectives (N x m, valid
  * flags N) to X / F / valid (host or device; each may be NULL), synchronise
- * the stream and release the run.  RVEA_ERR_STATE if id is not finished or
+ * the stream and release the run.  For a request whose admission failed,
+ * its error (nothing is copied).  RVEA_ERR_STATE if id is not finished or
  * already fetched. */
 rvea_status rvea_server_fetch(rvea_server *srv, int64_t id, float *X, float *F, uint8_t *valid,
                               void *cuda_stream);

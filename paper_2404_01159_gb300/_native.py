@@ -122,6 +122,10 @@ def lib():
         L.rvea_offspring.restype = i32
         L.rvea_last_selection.argtypes = [vp, vp, vp, vp]
         L.rvea_last_selection.restype = i32
+        L.rvea_record_draws.argtypes = [vp, i32, vp]
+        L.rvea_record_draws.restype = i32
+        L.rvea_last_draws.argtypes = [vp, vp, vp, vp]
+        L.rvea_last_draws.restype = i32
         L.rvea_select_scratch_bytes.argtypes = [i32, i32, i32]
         L.rvea_select_scratch_bytes.restype = sz
         L.rvea_select.argtypes = [i32, i32, vp, vp, i32, vp, vp, i32, i32, flt, vp, vp, vp, sz, vp]

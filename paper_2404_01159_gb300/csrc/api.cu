@@ -87,8 +87,6 @@ using namespace rvea;
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kSMs = 152;
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int pow2ceil(int x) {
@@ -99,7 +97,7 @@ int pow2ceil(int x) {
 
 struct Shape {
   int m, m4, d, d_pad, G, N, P, n_comb, team, ppc, nseg, sg;
-  int n_repro, n_init, n_sel, nblk, nch, chunk;
+  int n_repro, n_init, nblk;
   int n_sel_max;   // work items of the finest full-scan plan (table size)
   int tmax;     // tiles of the pruned selection (0: not used)
 };
@@ -138,15 +136,10 @@ Shape make_shape(int m, int d, int N) {
   s.sg = (s.G + s.nseg - 1) / s.nseg;   // balanced segments: no mostly idle last one
   s.n_repro = (s.P * s.nseg + s.ppc - 1) / s.ppc;
   s.n_init = (N + s.ppc - 1) / s.ppc;
-  const SelPlan sp = sel_plan(s.n_comb, N, s.m4, kSMs);
-  s.nblk = sp.nblk;
-  s.nch = sp.nch;
-  s.chunk = sp.chunk;
-  s.n_sel = s.nblk * s.nch;
-  {
-    const SelPlan fine = sel_plan(s.n_comb, N, s.m4, kSMs, kSelPerSmMax);
-    s.n_sel_max = std::max(s.n_sel, fine.nblk * fine.nch);
-  }
+  // the full-scan item table holds the finest plan of any device: every
+  // solution block x every kVTile-vector tile
+  s.nblk = (s.n_comb + kSelBlock - 1) / kSelBlock;
+  s.n_sel_max = s.nblk * ((N + kVTile - 1) / kVTile);
   s.tmax = 0;
   if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap)
     s.tmax = prune_tiles_bound(N);
@@ -155,8 +148,8 @@ Shape make_shape(int m, int d, int N) {
 
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
-      ctl, desc, repro, init, sel, stage, psum, Vt, tperm, trng, tcen, tcs, noise,
-      dynA, dynB, total;
+      ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, Vt, tperm, trng, tcen, tcs,
+      noise, dynA, dynB, total;
 };
 
 Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
@@ -193,6 +186,8 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.sel = take((size_t)s.n_sel_max * sizeof(SelItem));
   L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
+  L.rec_par = take((size_t)2 * s.P * 4);
+  L.rec_sites = take((size_t)s.N * (1 + kMaxSites) * 4);
   const size_t T = (size_t)s.tmax;
   L.Vt = take(s.tmax ? (size_t)s.N * 16 : 0);
   L.tperm = take(s.tmax ? (size_t)s.N * 4 : 0);
@@ -406,6 +401,8 @@ struct rvea_run {
   cudaGraphExec_t block_graph = nullptr;
   bool use_graph = true;
   bool has_last_gen = false;      // a generation ran since init / import
+  bool recording = false;         // draws recorded by the generations now enqueued
+  bool last_gen_recorded = false; // the last generation ran with recording on
 };
 
 namespace {
@@ -463,7 +460,7 @@ void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t sm
 // of one chunk follow.
 void build_sel_items(rvea_run *r) {
   const Shape &sh = r->sh;
-  const SelPlan sp = sel_plan(sh.n_comb, sh.N, sh.m4, kSMs, r->sel_per_sm);
+  const SelPlan sp = sel_plan(sh.n_comb, sh.N, sh.m4, r->num_sms, r->sel_per_sm);
   r->sel_host.clear();
   for (int b = 0; b < sp.nblk; ++b)
     for (int c = 0; c < sp.nch; ++c)
@@ -666,7 +663,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   launch_pdl(k_finalize, pd, 1024, 0, st, dd);
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
-    k_gamma<<<2 * kSMs, 256, 0, st>>>(df, 0);
+    k_gamma<<<2 * runs[0]->num_sms, 256, 0, st>>>(df, 0);
     if (np > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
   }
   if (ev) cudaEventRecord(ev[5], st);
@@ -677,7 +674,7 @@ rvea_status launch_gamma_force(rvea_run *r, cudaStream_t st) {
   static thread_local BatchDir d;
   dir_single(d, r, nullptr, 1);
   const int nb = (r->sh.N + 31) / 32;
-  k_gamma<<<std::min(nb, 4 * kSMs), 256, 0, st>>>(d, 1);
+  k_gamma<<<std::min(nb, 4 * r->num_sms), 256, 0, st>>>(d, 1);
   return cuerr(cudaGetLastError());
 }
 
@@ -826,6 +823,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   r->p_adapt = std::max(1, (int)std::floor(cfg->f_r * (double)cfg->t_max + 0.5));
   r->t = 1;
   cudaGetDevice(&r->device);
+  r->num_sms = current_sm_count();
   const char *ng = std::getenv("RVEA_NO_GRAPH");
   r->use_graph = !(ng && ng[0] == '1');
 
@@ -906,7 +904,6 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     D.tcs = wsp<float2>(r, lay.tcs);
     r->prune_smem_bytes = (int)prune_smem(sh.N, D.ntiles);
   }
-  cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
   std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f), V32lo((size_t)sh.N * sh.m);
   for (int j = 0; j < sh.N; ++j)
     for (int k = 0; k < sh.m; ++k) {
@@ -996,6 +993,7 @@ rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
       r->t += p;
       G -= p;
       r->has_last_gen = true;
+      r->last_gen_recorded = r->recording;
       continue;
     }
     rvea_status s;
@@ -1007,6 +1005,7 @@ rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
     r->t += 1;
     G -= 1;
     r->has_last_gen = true;
+    r->last_gen_recorded = r->recording;
   }
   return RVEA_OK;
 }
@@ -1025,6 +1024,7 @@ rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream
     runs[q]->t += 1;
     runs[q]->last_stream = st;
     runs[q]->has_last_gen = true;
+    runs[q]->last_gen_recorded = runs[q]->recording;
   }
   return RVEA_OK;
 }
@@ -1284,7 +1284,7 @@ rvea_status rvea_batch_step(rvea_batch *b, int G, void *cuda_stream) {
   for (rvea_run *r : b->runs) {
     r->t += G;
     r->last_stream = st;
-    if (G > 0) r->has_last_gen = true;
+    if (G > 0) { r->has_last_gen = true; r->last_gen_recorded = r->recording; }
   }
   return RVEA_OK;
 }
@@ -1313,6 +1313,7 @@ rvea_status rvea_batch_step_profiled(rvea_batch *b, int G, void *cuda_stream, do
       r->t += 1;
       r->last_stream = st;
       r->has_last_gen = true;
+      r->last_gen_recorded = r->recording;
     }
   }
   for (int q = 0; q < 6; ++q) cudaEventDestroy(ev[q]);
@@ -1362,7 +1363,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   dir_single(dpb, one, nullptr, (r->sh.n_comb + kPruneChunkHost - 1) / kPruneChunkHost);
   const int nbd = (r->sh.N + 1023) / 1024;
   dir_single(dd, one, nullptr, nbd);
-  const int nbg = std::min((r->sh.N + 31) / 32, 4 * kSMs);
+  const int nbg = std::min((r->sh.N + 31) / 32, 4 * r->num_sms);
   for (int g = 0; g < G && s == RVEA_OK; ++g) {
     cudaEvent_t *e = &ev[(size_t)g * 6];
     cudaEventRecord(e[0], st);
@@ -1395,6 +1396,7 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     s = cuerr(cudaGetLastError());
     r->t += 1;
     r->has_last_gen = true;
+    r->last_gen_recorded = r->recording;
   }
   if (s == RVEA_OK) s = cuerr(cudaStreamSynchronize(st));
   // e[0] reproduction e[5] children e[1] selection e[2] finalize e[3] gamma e[4]
@@ -1537,6 +1539,14 @@ rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const
   if (!r || !X || !F || !valid || !V || !gamma || t < 1) return RVEA_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const Shape &sh = r->sh;
+  {
+    // a population without a valid member leaves mating nothing to draw
+    // from: refused here, before any device state changes
+    std::vector<uint8_t> hv(sh.N);
+    RV_TRY(cudaStreamSynchronize(st));
+    RV_TRY(cudaMemcpy(hv.data(), valid, sh.N, cudaMemcpyDefault));
+    if (std::none_of(hv.begin(), hv.end(), [](uint8_t v) { return v != 0; })) return RVEA_ERR_ARG;
+  }
   float *sf = wsp<float>(r, r->lay.stage);
   uint8_t *sv = reinterpret_cast<uint8_t *>(sf + (size_t)sh.N * sh.m);
   RV_TRY(cudaMemcpy2DAsync(r->hd.X, (size_t)sh.d_pad * 4, X, (size_t)sh.d * 4, (size_t)sh.d * 4,
@@ -1576,6 +1586,35 @@ rvea_status rvea_last_selection(const rvea_run *r, int32_t *assoc, int32_t *surv
   if ((assoc && !da) || (survivor && !ds)) return RVEA_ERR_ARG;
   k_copy_selection<<<(r->sh.n_comb + 255) / 256, 256, 0, st>>>(r->d_desc, da, ds);
   return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_record_draws(rvea_run *r, int enable, void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  r->hd.rec_par = enable ? wsp<int>(r, r->lay.rec_par) : nullptr;
+  r->hd.rec_sites = enable ? wsp<int>(r, r->lay.rec_sites) : nullptr;
+  // the kernels read the descriptor from device memory, so direct launches
+  // and graph replays both see the change; the sources live in the handle
+  RV_TRY(cudaMemcpyAsync(&r->d_desc->rec_par, &r->hd.rec_par, sizeof(int *),
+                         cudaMemcpyHostToDevice, st));
+  RV_TRY(cudaMemcpyAsync(&r->d_desc->rec_sites, &r->hd.rec_sites, sizeof(int *),
+                         cudaMemcpyHostToDevice, st));
+  r->recording = enable != 0;
+  return RVEA_OK;
+}
+
+rvea_status rvea_last_draws(const rvea_run *r, int32_t *parents, int32_t *sites,
+                            void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  if (!r->has_last_gen || !r->last_gen_recorded) return RVEA_ERR_STATE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (parents)
+    RV_TRY(cudaMemcpyAsync(parents, r->ws + r->lay.rec_par, (size_t)2 * r->sh.P * 4,
+                           cudaMemcpyDefault, st));
+  if (sites)
+    RV_TRY(cudaMemcpyAsync(sites, r->ws + r->lay.rec_sites,
+                           (size_t)r->sh.N * (1 + kMaxSites) * 4, cudaMemcpyDefault, st));
+  return RVEA_OK;
 }
 
 rvea_status rvea_sync_status(rvea_run *r) {
@@ -1663,7 +1702,7 @@ rvea_status rvea_select(int m, int n, const float *F, const uint8_t *valid, int 
   D.valid_in = valid;
   D.survivor_out = survivor;
   // items: every solution block x every vector chunk
-  const SelPlan sp = sel_plan(n, r, m4, kSMs);
+  const SelPlan sp = sel_plan(n, r, m4, current_sm_count());
   std::vector<SelItem> items;
   items.reserve((size_t)sp.nblk * sp.nch);
   for (int b = 0; b < sp.nblk; ++b)

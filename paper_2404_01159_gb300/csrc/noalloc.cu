@@ -8,7 +8,14 @@
 // enqueued), or code whose device memory is entirely reserved by another
 // framework's caching allocator.  For them this file keeps the scratch that
 // rvea_select would take from the caller in a file-scope device array of a
-// fixed maximum size, reserved when the library is loaded.
+// fixed maximum size.  The array belongs to this file's GPU module: under
+// CUDA's lazy module loading (the default) the module, and with it the
+// array, is loaded on a device by the first call there (the address lookup
+// below); with CUDA_MODULE_LOADING=EAGER it is loaded with the library's
+// other modules when the process first uses the device.  Either way a later
+// call maps nothing new, and no call asks an allocator for memory: the
+// descriptor and the work-item table are written by a kernel straight from
+// its parameters, with no host-side buffer.
 //
 // The same kernels as rvea_select run on that array, so results are the same
 // bit for bit.  Every call shares the one array: two calls whose work
@@ -21,7 +28,6 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "../../include/rvea.h"
 #include "rvea_device.cuh"
@@ -41,11 +47,27 @@ constexpr size_t kNoAllocBytes = size_t(4) << 20;   // 4 MiB per device
 constexpr int kNoAllocMaxN = 65536;                  // solutions
 constexpr int kNoAllocMaxR = 16384;                  // reference vectors
 constexpr int kDevicesMax = 64;
-constexpr int kSMCount = 152;
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // device symbol: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_select_scratch[kNoAllocBytes];
+
+// Writes the run descriptor and the full-scan work items into the scratch,
+// and the zero-padded float4 rows of V, from the kernel's parameters.
+__global__ void k_noalloc_setup(const __grid_constant__ RunDesc D, RunDesc *out, SelItem *items,
+                                int nblk, int nch, int chunk, const float *V, float *V32) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  if (tid == 0) *out = D;
+  const int r = D.N, m = D.m, w = 4 * D.m4;
+  for (int q = tid; q < nblk * nch; q += nth) {
+    const int b = q / nch, c = q - b * nch;
+    items[q] = SelItem{b, min(r, c * chunk), min(r, (c + 1) * chunk), nch};
+  }
+  for (int q = tid; q < r * w; q += nth) {
+    const int j = q / w, k = q - j * w;
+    V32[q] = k < m ? V[(size_t)j * m + k] : 0.0f;
+  }
+}
 
 std::mutex g_mu;
 void *g_scratch_addr[kDevicesMax] = {};
@@ -118,7 +140,7 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
     return RVEA_ERR_ARG;
   // work items: every block of solutions x every chunk of vectors
   const int m4 = (m + 3) / 4;
-  const SelPlan sp = sel_plan(n, r, m4, kSMCount);
+  const SelPlan sp = sel_plan(n, r, m4, current_sm_count());
   const int nblk = sp.nblk, nch = sp.nch;
   const int n_items = nblk * nch;
   if (n > kNoAllocMaxN || r > kNoAllocMaxR) return RVEA_ERR_NOMEM;
@@ -130,11 +152,6 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   if (s0 != RVEA_OK) return s0;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   float *V32 = reinterpret_cast<float *>(ws + c.v32);
-  // zero-padded float4 rows of V (the padding must read as zero)
-  if (cudaMemsetAsync(V32, 0, (size_t)r * m4 * 16, st) != cudaSuccess) return RVEA_ERR_CUDA;
-  if (cudaMemcpy2DAsync(V32, (size_t)m4 * 16, V, (size_t)m * 4, (size_t)m * 4, r,
-                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return RVEA_ERR_CUDA;
   RunDesc D;
   std::memset(&D, 0, sizeof(D));
   D.m = m; D.m4 = m4; D.N = r; D.n_comb = n; D.t_max = t_max; D.alpha = alpha;
@@ -149,17 +166,11 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   D.F_aos = F;
   D.valid_in = valid;
   D.survivor_out = survivor;
-  std::vector<SelItem> items;
-  items.reserve(n_items);
-  for (int b = 0; b < nblk; ++b)
-    for (int q = 0; q < nch; ++q)
-      items.push_back(SelItem{b, std::min(r, q * sp.chunk), std::min(r, (q + 1) * sp.chunk), nch});
   RunDesc *dD = reinterpret_cast<RunDesc *>(ws + c.desc);
-  // pageable sources: staged by the driver before these calls return
-  if (cudaMemcpyAsync(dD, &D, sizeof(D), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(ws + c.items, items.data(), items.size() * sizeof(SelItem),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return RVEA_ERR_CUDA;
+  SelItem *items = reinterpret_cast<SelItem *>(ws + c.items);
+  const int nset = std::max(n_items, r * 4 * m4);
+  k_noalloc_setup<<<std::min(1024, (nset + 255) / 256), 256, 0, st>>>(D, dD, items, nblk, nch,
+                                                                        sp.chunk, V, V32);
   // k_op_prep clears best, amax, the arrival counters and the control block
   k_op_prep<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, st>>>(dD);
   k_op_zstar<<<(n + 255) / 256, 256, 0, st>>>(dD);
@@ -168,7 +179,7 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
   dir.prefix[0] = 0;
   dir.prefix[1] = n_items;
   dir.desc[0] = dD;
-  dir.items[0] = ws + c.items;
+  dir.items[0] = items;
   k_select<<<(unsigned)n_items, kSelThreads, std::min(r, sp.chunk) * m4 * 16, st>>>(dir);
   k_op_finish<<<(r + 255) / 256, 256, 0, st>>>(dD);
   return cudaGetLastError() == cudaSuccess ? RVEA_OK : RVEA_ERR_CUDA;

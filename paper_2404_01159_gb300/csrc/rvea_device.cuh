@@ -86,6 +86,11 @@ struct RunDesc {
   int *assoc;          // [n_comb]   vector of each solution, -1 if invalid
   int *surv;           // [N]        combined index kept by vector j, -1 if none
   float *psum;         // [P][2][nseg] partial g sums of the segments of each pair
+  // draw recording (inspection; null when off): the vector slot of each
+  // parent draw e, and each child's mutation-site count (-1: every site)
+  // followed by its sites in draw order
+  int *rec_par;        // [2P]
+  int *rec_sites;      // [N][1 + kMaxSites]
   int *blk_cnt;        // [n_comb/256] arrival counters of the selection blocks
   float *V32;          // [N][m4*4]  reference vectors, zero padded
   float *V32lo;        // [N][m]     V64 - V32 rounded to float (null: zero)
@@ -157,6 +162,26 @@ inline SelPlan sel_plan(int n, int r, int m4, int sms, int per_sm = 8) {
   p.nch = (tiles + tpc - 1) / tpc;
   p.chunk = tpc * kVTile;
   return p;
+}
+
+// SM count of the current device, read once per device (the grid sizes and
+// the selection work plans follow it); 152, a GB300's count, if it cannot be
+// read.
+inline int current_sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  int n = __atomic_load_n(&cache[dev], __ATOMIC_RELAXED);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 152;
+  }
+  __atomic_store_n(&cache[dev], n, __ATOMIC_RELAXED);
+  return n;
 }
 
 __device__ __forceinline__ int dir_find(const BatchDir &dir, int b) {

@@ -95,6 +95,7 @@ struct rvea_server {
   std::deque<Request> queue;
   std::vector<Live> live;
   std::map<int64_t, Live> done;        // budget spent, result not fetched yet
+  std::map<int64_t, rvea_status> failed;   // admission failed, error not fetched yet
   std::vector<int64_t> done_unpolled;
   long long gens_run = 0;
   explicit rvea_server(size_t bytes) : arena(bytes) {}
@@ -147,11 +148,14 @@ rvea_status rvea_server_step(rvea_server *s, void *cuda_stream, rvea_server_stat
     rvea_run *run = nullptr;
     rvea_status st = rvea_init_ex(&q.cfg, s->arena_base + off, bytes, cuda_stream, &run);
     if (st == RVEA_OK && s->tune) st = rvea_autotune(run, cuda_stream, 1, nullptr);
-    if (st != RVEA_OK) {   // a device error: the request is dropped, the error returned
+    if (st != RVEA_OK) {
+      // the request ends here: poll reports its id, fetch returns this error
       if (run) rvea_free(run);
       s->arena.release(off, bytes);
+      s->failed[q.id] = st;
+      s->done_unpolled.push_back(q.id);
       s->queue.pop_front();
-      return st;
+      continue;
     }
     s->live.push_back(Live{q.id, run, off, bytes, q.generations});
     s->queue.pop_front();
@@ -182,7 +186,7 @@ rvea_status rvea_server_step(rvea_server *s, void *cuda_stream, rvea_server_stat
   if (stats) {
     stats->live = (int)s->live.size();
     stats->queued = (int)s->queue.size();
-    stats->finished = (int)s->done.size();
+    stats->finished = (int)(s->done.size() + s->failed.size());
     stats->admitted = admitted;
     stats->arena_used = s->arena.used();
     stats->generations = s->gens_run;
@@ -202,6 +206,12 @@ rvea_status rvea_server_poll(rvea_server *s, int64_t *ids, int cap, int *n_out) 
 rvea_status rvea_server_fetch(rvea_server *s, int64_t id, float *X, float *F, uint8_t *valid,
                               void *cuda_stream) {
   if (!s) return RVEA_ERR_ARG;
+  const auto fit = s->failed.find(id);
+  if (fit != s->failed.end()) {   // admission failed: its error, once
+    const rvea_status st = fit->second;
+    s->failed.erase(fit);
+    return st;
+  }
   auto it = s->done.find(id);
   if (it == s->done.end()) return RVEA_ERR_STATE;
   Live l = it->second;

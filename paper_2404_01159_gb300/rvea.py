@@ -195,6 +195,22 @@ class Run:
               "rvea_offspring")
         return X, F
 
+    def record_draws(self, enable: bool = True, stream=None) -> None:
+        """Make later generations record their mating draws and mutation
+        sites (rvea_record_draws)."""
+        check(lib().rvea_record_draws(self._h, 1 if enable else 0, C.c_void_p(_stream(stream))),
+              "rvea_record_draws")
+
+    def last_draws(self, stream=None):
+        """(parents (2 ceil(N/2),) int32 vector slots, counts (N,) int32 with -1
+        for every site, sites (N, 32) int32) of the last generation."""
+        P = (self.N + 1) // 2
+        par = torch.empty(2 * P, dtype=torch.int32, device=self.device)
+        sites = torch.empty((self.N, 33), dtype=torch.int32, device=self.device)
+        check(lib().rvea_last_draws(self._h, _ptr(par), _ptr(sites), C.c_void_p(_stream(stream))),
+              "rvea_last_draws")
+        return par, sites[:, 0].contiguous(), sites[:, 1:].contiguous()
+
     def last_selection(self, stream=None):
         assoc = torch.empty(2 * self.N, dtype=torch.int32, device=self.device)
         surv = torch.empty(self.N, dtype=torch.int32, device=self.device)

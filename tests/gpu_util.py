@@ -10,7 +10,9 @@ Tolerances (stated once, used everywhere):
   * gamma (FP64): |g_gpu - g_orc| <= 64 eps / sin(g) + 1e-12 g: arccos of a
     cosine near 1 loses eps / sin(theta) (theta ~ 1e-3 rad at N = 9870);
   * association: exact unless the two vectors' dot products with f' differ
-    by less than `tie_rel` ||f'|| (float32 dot of unit vectors);
+    by less than `tie_rel` ||f'|| = 1e-6 ||f'|| (float32 dots of unit vectors:
+    each carries at most ~m 2^-24 ||f'|| of rounding, plus the float32
+    rounding of the vector, ~2^-24 per component);
   * survivors: exact unless explained by such an association tie or by two
     APD values within 1e-5 relative.
 """
@@ -79,7 +81,7 @@ def assert_gamma(g, o):
     assert (err <= tol).all(), float((err / tol).max())
 
 
-def selection_mismatches(Fc, validc, V, gpu_assoc, gpu_surv, o, tie_rel=2e-6):
+def selection_mismatches(Fc, validc, V, gpu_assoc, gpu_surv, o, tie_rel=1e-6):
     """Unexplained differences between a GPU selection and the oracle's.
 
     Fc, validc: the combined population as the oracle saw it (FP64)."""
@@ -122,6 +124,36 @@ def selection_mismatches(Fc, validc, V, gpu_assoc, gpu_surv, o, tie_rel=2e-6):
                 continue
         bad_surv.append(j)
     return bad_assoc, bad_surv
+
+
+def draws_mask(counts, sites, d):
+    """Mutation mask (N x d uint8) from recorded site lists: row c has ones at
+    sites[c, :counts[c]] (every variable when counts[c] == -1).  Also checks
+    that each list holds distinct variables in [0, d)."""
+    counts = np.asarray(counts)
+    sites = np.asarray(sites)
+    N = len(counts)
+    mask = np.zeros((N, d), dtype=np.uint8)
+    for c in range(N):
+        k = int(counts[c])
+        if k < 0:
+            mask[c, :] = 1
+            continue
+        s = sites[c, :k]
+        assert len(set(s.tolist())) == k and (s >= 0).all() and (s < d).all(), (c, s)
+        mask[c, s] = 1
+    return mask
+
+
+def assert_draws(orc, p, t, run, oracle_parents):
+    """The mating draws and mutation masks of the run's last generation
+    (recorded on the GPU) equal the oracle's, bit for bit."""
+    gpar, gcnt, gsites = (x.cpu().numpy() for x in run.last_draws())
+    assert np.array_equal(gpar, np.asarray(oracle_parents)), \
+        int((gpar != np.asarray(oracle_parents)).sum())
+    _, omask = orc.mutation(p, t, np.zeros((p.N, p.d)))
+    gmask = draws_mask(gcnt, gsites, p.d)
+    assert np.array_equal(gmask, omask), int((gmask != omask).sum())
 
 
 def igd(F, front):

@@ -138,3 +138,38 @@ def test_server_admission_refusals_without_gpu(native):
         assert L.rvea_server_fetch(srv, 1, None, None, None, None) == native.ERR_STATE
     finally:
         L.rvea_server_free(srv)
+
+
+def test_server_reports_failed_admission_by_id(native):
+    """A request whose admission fails is not lost: the step goes on, poll
+    reports its id, fetch returns its error once.  Made without a GPU (the
+    initialisation's CUDA calls fail on a machine with no device), so the
+    test only runs where CUDA is unavailable; the arena address is never
+    dereferenced."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("the failure is made by the absence of a device")
+    L = native.lib()
+    srv = C.c_void_p()
+    assert L.rvea_server_create(C.c_void_p(1 << 20), 64 << 20, 4, 0, C.byref(srv)) == native.OK
+    try:
+        cfg = native.Config(m=3, d=12, N=105, H=13, problem=0, t_max=100, alpha=2.0, f_r=0.1,
+                            eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, lower=0.0, upper=1.0,
+                            seed=0, neuro=None)
+        ids = []
+        for _ in range(2):
+            rid = C.c_int64(0)
+            assert L.rvea_server_submit(srv, C.byref(cfg), 5, C.byref(rid)) == native.OK
+            ids.append(rid.value)
+        st = native.ServerStats()
+        assert L.rvea_server_step(srv, None, C.byref(st)) == native.OK
+        assert st.queued == 0 and st.live == 0 and st.finished == 2
+        out = (C.c_int64 * 4)()
+        n = C.c_int(-1)
+        assert L.rvea_server_poll(srv, out, 4, C.byref(n)) == native.OK
+        assert sorted(out[q] for q in range(n.value)) == ids
+        for rid in ids:
+            assert L.rvea_server_fetch(srv, rid, None, None, None, None) == native.ERR_CUDA
+            assert L.rvea_server_fetch(srv, rid, None, None, None, None) == native.ERR_STATE
+    finally:
+        L.rvea_server_free(srv)

@@ -54,9 +54,13 @@ def test_noalloc_select_matches_select():
                              _p(s_ref), C.c_void_p(sp), need, stream) == OK
         a_na = torch.full((n,), -9, dtype=torch.int32, device="cuda")
         s_na = torch.full((r,), -9, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         assert L.rvea_select_noalloc(m, n, _p(F), _p(valid), r, _p(V), _p(g), t, 10, 2.0,
                                      _p(a_na), _p(s_na), stream) == OK
         torch.cuda.synchronize()
+        if seed > 0:   # after the first call on the device, nothing more is reserved
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert torch.equal(a_ref, a_na)
         assert torch.equal(s_ref, s_na)
         assert (s_na >= -1).all() and (s_na < n).all()
