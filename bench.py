@@ -218,15 +218,16 @@ def batch_bytes(insts) -> int:
     return sum((2 * ((i.N + 1) // 2) + i.N) * i.d * 4 for i in insts)
 
 
-def main_batched(args, rank, world, local):
+def main_batched(args, rank, world, local, emit=True, steps=None, warmup=None, with_cpu=True):
     """Uneven runs stepped together: one CUDA graph per batched generation,
     plans from the autotuner; the same runs stepped one after another is the
-    sequential comparison."""
+    sequential comparison.  Returns the JSON line (printed when emit)."""
     import torch
     torch.cuda.set_device(local)
     from paper_2404_01159_gb300 import Batch, Run, autotune
     from paper_2404_01159_gb300.workloads import batched_set
-    K, W = args.steps, max(3, args.warmup)
+    K = args.steps if steps is None else steps
+    W = max(3, args.warmup if warmup is None else warmup)
     insts = batched_set(256, 500, seed0=rank * 256)
     t0 = time.perf_counter()
     runs = [Run(**i.run_kwargs()) for i in insts]
@@ -277,15 +278,17 @@ def main_batched(args, rank, world, local):
     achieved = nb / (ms / K * 1e-3) / 1e9
     modes = {}
     for pl in plans:
-        key = ("pruned-smem", "pruned-L1")[pl["sel_mode"] - 1] if pl["sel_mode"] else \
+        key = ("pruned-smem", "pruned-L1", "fused-tail")[pl["sel_mode"] - 1] if pl["sel_mode"] else \
             f"scan/{pl['sel_per_sm']}"
         key += "+staged" if pl["repro_staged"] else "+direct"
         modes[key] = modes.get(key, 0) + 1
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and with_cpu:
         cpu = cpu_baseline_batched(insts, args.cpu_seconds)
+    for r in runs:
+        r.free()
     if rank != 0:
-        return
+        return None
     line = {
         "metric": METRIC,
         "value": value,
@@ -326,7 +329,9 @@ def main_batched(args, rank, world, local):
         "gpu_launches": K * launches_per_step,
         "clocks": sampler.summary() if sampler else None,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 SERVE = "serve_poisson200"
@@ -448,15 +453,19 @@ def cpu_baseline_neuro(kw, dyn, seconds=20.0):
                       f"the time"}
 
 
-def main_serve(args, rank, world, local):
+def main_serve(args, rank, world, local, emit=True, rate=None, seconds=None, drain=None):
     """Serving: Poisson arrivals of runs (m, d, N, budget drawn per request),
     admitted by an HBM budget, their generations batched across live runs
-    each step; time-to-result from arrival to the step that finished it."""
+    each step; time-to-result from arrival to the step that finished it.
+    Returns the JSON line (printed when emit)."""
     import torch
     torch.cuda.set_device(local)
     from paper_2404_01159_gb300 import Server
     from paper_2404_01159_gb300.workloads import request_stream
-    reqs = request_stream(args.serve_rate, args.serve_seconds, seed=rank)
+    rate = args.serve_rate if rate is None else rate
+    seconds = args.serve_seconds if seconds is None else seconds
+    drain = args.serve_drain_seconds if drain is None else drain
+    reqs = request_stream(rate, seconds, seed=rank)
     budget = int(args.serve_budget_gb * 1e9)
     srv = Server(budget, max_live=args.serve_max_live, autotune=True)
     props = torch.cuda.get_device_properties(local)
@@ -468,7 +477,7 @@ def main_serve(args, rank, world, local):
         sampler.start()
     arrival, budget_of, lat = {}, {}, []
     k, steps, gens_done, live_sum = 0, 0, 0, 0
-    cap_s = args.serve_seconds + args.serve_drain_seconds
+    cap_s = seconds + drain
     outstanding = 0
     t0 = time.perf_counter()
     while True:
@@ -502,7 +511,7 @@ def main_serve(args, rank, world, local):
         sampler.stop()
     srv.free()
     if rank != 0:
-        return
+        return None
     lat.sort()
     pct = (lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None)
     line = {
@@ -518,8 +527,8 @@ def main_serve(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded Poisson request stream, closed-form DTLZ objectives)",
-        "config": {"workload": SERVE, "rate_per_s": args.serve_rate,
-                   "arrivals_s": args.serve_seconds, "requests": len(reqs),
+        "config": {"workload": SERVE, "rate_per_s": rate,
+                   "arrivals_s": seconds, "requests": len(reqs),
                    "hbm_budget_gb": args.serve_budget_gb, "max_live": args.serve_max_live,
                    "m": "uniform {2,3,5,10}", "N": "100..9870", "d": "30..5000 log-uniform",
                    "generations": "U{50..1000}", **COMMON},
@@ -534,7 +543,44 @@ def main_serve(args, rank, world, local):
         "gpu_launches": None,
         "clocks": sampler.summary() if sampler else None,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def sub_batched(args, local):
+    """The batched form inside the default line: 256 uneven runs, a few graph
+    replays, against the same runs stepped one after another."""
+    try:
+        b = main_batched(args, 0, 1, local, emit=False, steps=10, warmup=3, with_cpu=False)
+        return {"workload": BATCHED, "value": b["value"], "unit": b["unit"],
+                "ms_per_step": b["ms_per_step"], "steps": b["steps"],
+                "sequential": b["sequential"]["value"],
+                "batched_over_sequential": b["batched_over_sequential"],
+                "roofline_frac": b["roofline"]["frac"], "gpu_launches": b["gpu_launches"],
+                "phase_ms_per_generation": b["phase_ms_per_generation"],
+                "setup_s": b["setup_s"], "clocks": b["clocks"]}
+    except Exception as e:   # the headline line must survive
+        return {"workload": BATCHED, "error": repr(e)[:300]}
+
+
+def sub_serve(args, local, rates=(50.0, 200.0), seconds=8.0, drain=40.0):
+    """The served form inside the default line: a short Poisson window at a
+    rate below capacity and at the configuration's 200 requests/s."""
+    out = {"workload": SERVE, "arrivals_s": seconds, "hbm_budget_gb": args.serve_budget_gb,
+           "rates": []}
+    for rate in rates:
+        try:
+            sv = main_serve(args, 0, 1, local, emit=False, rate=rate, seconds=seconds, drain=drain)
+            out["rates"].append({"rate_per_s": rate, "value": sv["value"], "unit": sv["unit"],
+                                 "p50_s": sv["serve"]["p50_s"], "p99_s": sv["serve"]["p99_s"],
+                                 "completed": sv["serve"]["completed"],
+                                 "submitted": sv["serve"]["submitted"],
+                                 "mean_live_runs": sv["serve"]["mean_live_runs"],
+                                 "wall_s": sv["serve"]["wall_s"], "clocks": sv["clocks"]})
+        except Exception as e:
+            out["rates"].append({"rate_per_s": rate, "error": repr(e)[:300]})
+    return out
 
 
 def cpu_baseline_batched(insts, seconds=20.0):
@@ -577,6 +623,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--e2e-generations", type=int, default=1000,
+                    help="generations of the end-to-end pass (at least --steps)")
+    ap.add_argument("--soak-seconds", type=float, default=1.5,
+                    help="untimed run after the timed region, under the clock sampler")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="omit the batched and served sub-results of the default line")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -644,12 +696,21 @@ def main():
     run.step(K)
     e1.record()
     e1.synchronize()
+    # untimed soak of the same generation loop, so that the clock sampler sees
+    # the GPU under this load (the timed region alone is a few milliseconds)
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < args.soak_seconds:
+        run.step(200)
+        torch.cuda.synchronize()
+    soak_s = time.perf_counter() - t_soak
     if sampler:
         sampler.stop()
     barrier()
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, dist, "cuda")
     run.sync_status()
+    from paper_2404_01159_gb300 import get_plan
+    plan_mode = get_plan(run)["sel_mode"]
     p_adapt = max(1, int(kw["f_r"] * kw["t_max"] + 0.5))
     n_adapt = sum(1 for t in range(t_first, t_first + K) if t % p_adapt == 0)
     launches = (K - n_adapt) * run.launches_per_generation(False) + \
@@ -670,7 +731,7 @@ def main():
 
     # ---- end to end through the public API, host buffers --------------------
     N, m, d = wl["N"], wl["m"], wl["d"]
-    Ke = K
+    Ke = max(K, args.e2e_generations)
     e2e_s = None
     if not args.no_e2e:
         hF = torch.empty((N, m), dtype=torch.float32, pin_memory=True)
@@ -726,20 +787,33 @@ def main():
                      "algorithmic_bytes_per_launch": bytes_rep,
                      "avg_launch_ms": repro_ms,
                      "timing": f"CUDA events around each launch, {Kp} generations"},
-        "phase_ms_per_generation": {"repro": phases[0] / Kp, "mutate_eval": phases[4] / Kp,
-                                    "select": phases[1] / Kp, "finalize": phases[2] / Kp,
-                                    "gamma": phases[3] / Kp},
+        "phase_ms_per_generation": (
+            {"repro": phases[0] / Kp,
+             "tail_fused": phases[1] / Kp,
+             "gamma_tiles_grid": phases[3] / Kp,
+             "what": "tail_fused: mutation/evaluation, association and finalize in one "
+                     "persistent launch"}
+            if plan_mode == 3 else
+            {"repro": phases[0] / Kp, "mutate_eval": phases[4] / Kp,
+             "select": phases[1] / Kp, "finalize": phases[2] / Kp,
+             "gamma_tiles_grid": phases[3] / Kp}),
+        "plan": plan_mode,
         "whole_generation_hbm_gbs": bytes_rep / (ms / K * 1e-3) / 1e9,
         "whole_generation_frac": bytes_rep / (ms / K * 1e-3) / 1e9 / hbm_peak,
         "cpu_baseline": cpu,
         "e2e": None if e2e_s is None else {
             "value": world * Ke / e2e_s, "unit": "generations/s",
             "h2d_bytes_per_step": h2d_init / Ke, "d2h_bytes_per_step": d2h / Ke,
+            "generations": Ke,
             "what": "init from host config + per-generation objectives to pinned host "
-                    "+ final population to pinned host"},
+                    "+ final population to pinned host, over max(steps, 1000) generations"},
         "gpu_launches": launches,
-        "clocks": clocks,
+        "clocks": None if clocks is None else dict(
+            clocks, window=f"timed region + {soak_s:.1f} s untimed soak of the same loop"),
     }
+    if world == 1 and not args.no_sub:
+        line["batched"] = sub_batched(args, local)
+        line["serve"] = sub_serve(args, local)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

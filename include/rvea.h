@@ -96,7 +96,24 @@ typedef struct {
     double upper;
     uint64_t seed;    /* Philox4x32-10 key                                   */
     const rvea_neuro_dynamics *neuro;   /* required iff problem == NEURO     */
+    int reproduction; /* rvea_reproduction (0: SBX + polynomial mutation)   */
+    double de_F;      /* DE/rand/1/bin scale factor, (0, 2]                  */
+    double de_CR;     /* DE/rand/1/bin crossover rate, [0, 1]                */
 } rvea_config;
+
+/* Reproduction operators (Sec. 4.4, the extensibility experiment: the same
+ * selection with another offspring generator).  RVEA_REPRO_DE and
+ * RVEA_REPRO_RANDOM replace SBX and polynomial mutation: DE/rand/1/bin (Storn
+ * and Price) makes offspring o from the target at position o mod K of the
+ * valid list and an ordered triple of other distinct members, v = x_r1 +
+ * F (x_r2 - x_r3), binomial crossover with rate CR and one forced variable,
+ * clipped to the box; random reproduction draws every variable uniformly on
+ * the box.  DTLZ problems only. */
+typedef enum {
+    RVEA_REPRO_SBX_PM = 0,
+    RVEA_REPRO_DE = 1,
+    RVEA_REPRO_RANDOM = 2
+} rvea_reproduction;
 
 /* Bytes of device workspace a run of this shape needs (0 if invalid).
  * DTLZ problems only; the rollout problem adds its noise table and dynamics:
@@ -144,8 +161,14 @@ rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream
  *              is always 1..16);
  *              1: the exact pruned search with its tile tables in shared
  *                 memory (one run per launch); 2: the same search with the
- *                 tables read through L1 (the form batches use).  Modes 1, 2
- *                 need m <= 4 and N >= 1000;
+ *                 tables read through L1 (the form batches use);
+ *              3: mode 1's search inside one persistent launch (one CTA per
+ *                 SM) that also mutates and evaluates the children and
+ *                 builds the next population (the "fused tail"), grid
+ *                 phases separated by time-limited grid barriers; DTLZ
+ *                 problems, stepped alone (in a batch it runs as mode 2).
+ *                 Modes 1-3 need m <= 4 and N >= 1000; a run that has mode 3
+ *                 starts in it;
  *   repro_staged 1: parents staged in shared memory by TMA bulk copies
  *                 (runs with d > 1024), 0: loaded directly.
  * repro_us / sel_us: the autotuner's median launch times (0 if untuned). */
@@ -315,7 +338,7 @@ rvea_status rvea_last_selection(const rvea_run *run, int32_t *assoc, int32_t *su
 rvea_status rvea_record_draws(rvea_run *run, int enable, void *cuda_stream);
 
 /* The draws of the last completed generation, which must have run with
- * recording on (else RVEA_ERR_STATE).  parents: 2P int32, the vector slot
+ * recording on and with SBX reproduction (else RVEA_ERR_STATE).  parents: 2P int32, the vector slot
  * (0..N-1, slot order of the parent population) of each draw.  sites:
  * N x 33 int32, row c = [k, s_1..s_k, unused...]: k the number of mutation
  * sites of child c (-1 when every variable mutates: per-site probability 1)

@@ -30,7 +30,8 @@ class Params(C.Structure):
                 ("problem", C.c_int32), ("t_max", C.c_int32),
                 ("alpha", C.c_double), ("f_r", C.c_double), ("eta_c", C.c_double),
                 ("eta_m", C.c_double), ("p_c", C.c_double), ("p_m", C.c_double),
-                ("L", C.c_double), ("U", C.c_double), ("seed", C.c_uint64)]
+                ("L", C.c_double), ("U", C.c_double), ("seed", C.c_uint64),
+                ("op", C.c_int32), ("de_F", C.c_double), ("de_CR", C.c_double)]
 
 
 class Neuro(C.Structure):
@@ -114,10 +115,14 @@ def philox(ctr, key):
     return [int(x) for x in o]
 
 
+OP_SBX_PM, OP_DE, OP_RANDOM = 0, 1, 2
+
+
 def make_params(m, d, N, H, problem=DTLZ2, t_max=100, alpha=2.0, f_r=0.1,
-                eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, L=0.0, U=1.0, seed=0):
+                eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, L=0.0, U=1.0, seed=0,
+                op=OP_SBX_PM, de_F=0.5, de_CR=0.9):
     return Params(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
-                  L, U, seed)
+                  L, U, seed, op, de_F, de_CR)
 
 
 def lattice_count(m, H) -> int:

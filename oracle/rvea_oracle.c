@@ -749,19 +749,28 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
     if (K == 0) { free(vlist); return -1; }
 
     int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * P));
-    orc_mating(p, t, K, vlist, par);
-    double *X1 = (double *)malloc(sizeof(double) * (size_t)P * d);
-    double *X2 = (double *)malloc(sizeof(double) * (size_t)P * d);
-    for (int32_t q = 0; q < P; ++q) {
-        memcpy(X1 + (int64_t)q * d, X + (int64_t)par[q] * d, sizeof(double) * (size_t)d);
-        memcpy(X2 + (int64_t)q * d, X + (int64_t)par[P + q] * d, sizeof(double) * (size_t)d);
-    }
     double *Xc = (double *)malloc(sizeof(double) * (size_t)(2 * P) * d);
-    orc_sbx(p, t, X1, X2, Xc);
-    free(X1);
-    free(X2);
-    /* keep the first N rows of X_cross */
-    orc_mutation(p, t, Xc, NULL);
+    if (p->op == ORC_OP_DE) {
+        /* the extensibility experiment's operators replace SBX and mutation */
+        for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
+        orc_de_offspring(p, t, X, K, vlist, p->de_F, p->de_CR, Xc);
+    } else if (p->op == ORC_OP_RANDOM) {
+        for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
+        orc_random_offspring(p, t, Xc);
+    } else {
+        orc_mating(p, t, K, vlist, par);
+        double *X1 = (double *)malloc(sizeof(double) * (size_t)P * d);
+        double *X2 = (double *)malloc(sizeof(double) * (size_t)P * d);
+        for (int32_t q = 0; q < P; ++q) {
+            memcpy(X1 + (int64_t)q * d, X + (int64_t)par[q] * d, sizeof(double) * (size_t)d);
+            memcpy(X2 + (int64_t)q * d, X + (int64_t)par[P + q] * d, sizeof(double) * (size_t)d);
+        }
+        orc_sbx(p, t, X1, X2, Xc);
+        free(X1);
+        free(X2);
+        /* keep the first N rows of X_cross */
+        orc_mutation(p, t, Xc, NULL);
+    }
     double *Fc = (double *)malloc(sizeof(double) * (size_t)N * m);
     orc_evaluate(p, N, Xc, Fc, nd, t);
 

@@ -44,7 +44,13 @@ typedef struct {
     int32_t t_max;
     double alpha, f_r, eta_c, eta_m, p_c, p_m, L, U;
     uint64_t seed;
+    int32_t op;               /* reproduction: ORC_OP_SBX_PM, ORC_OP_DE, ORC_OP_RANDOM */
+    double de_F, de_CR;       /* DE/rand/1/bin scale factor and crossover rate   */
 } orc_params;
+
+/* Reproduction operators (Sec. 4.4, the extensibility experiment): SBX with
+ * polynomial mutation (Appendix B), DE/rand/1/bin, random reproduction. */
+enum { ORC_OP_SBX_PM = 0, ORC_OP_DE = 1, ORC_OP_RANDOM = 2 };
 
 /* Synthetic linear-dynamics rollout used as the neuroevolution objective. */
 typedef struct {

@@ -18,6 +18,7 @@ _lib = None
 OK, ERR_ARG, ERR_LATTICE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 DTLZ2_SPHERE, DTLZ1_LINEAR, NEURO_LINEAR, DTLZ3_SPHERE, DTLZ4_SPHERE = 0, 1, 2, 3, 4
+REPRO_SBX_PM, REPRO_DE, REPRO_RANDOM = 0, 1, 2
 
 
 class NeuroDynamics(C.Structure):
@@ -32,7 +33,8 @@ class Config(C.Structure):
                 ("alpha", C.c_double), ("f_r", C.c_double), ("eta_c", C.c_double),
                 ("eta_m", C.c_double), ("p_c", C.c_double), ("p_m", C.c_double),
                 ("lower", C.c_double), ("upper", C.c_double), ("seed", C.c_uint64),
-                ("neuro", C.POINTER(NeuroDynamics))]
+                ("neuro", C.POINTER(NeuroDynamics)), ("reproduction", C.c_int),
+                ("de_F", C.c_double), ("de_CR", C.c_double)]
 
 
 class Plan(C.Structure):

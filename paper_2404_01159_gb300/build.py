@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "librvea.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["k_repro.cu", "k_select.cu", "k_prune.cu", "k_finalize.cu", "api.cu", "noalloc.cu",
+UNITS = ["k_repro.cu", "k_select.cu", "k_prune.cu", "k_finalize.cu", "k_tail.cu", "k_grid.cu", "api.cu", "noalloc.cu",
          "server.cu", "k_rollout.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -53,6 +53,10 @@ __global__ void k_mutate_neuro(const __grid_constant__ BatchDir dir);
 __global__ void k_mutate_dtlz3(const __grid_constant__ BatchDir dir);
 __global__ void k_mutate_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_init(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_op_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_op_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_op_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_op_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
 __global__ void k_gamma(const __grid_constant__ BatchDir dir, int force);
@@ -78,6 +82,14 @@ __global__ void k_noise(const __grid_constant__ BatchDir dir, int init);
 __global__ void k_rollout(const __grid_constant__ BatchDir dir, int init);
 __global__ void k_select_pruned_batch(const __grid_constant__ BatchDir dir);
 __global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force);
+__global__ void k_tail_dtlz1(const RunDesc *Rp);
+__global__ void k_tail_dtlz2(const RunDesc *Rp);
+__global__ void k_tail_dtlz3(const RunDesc *Rp);
+__global__ void k_tail_dtlz4(const RunDesc *Rp);
+__global__ void k_grid_scale(const RunDesc *Rp);
+__global__ void k_grid_count(const RunDesc *Rp);
+__global__ void k_grid_scan(const RunDesc *Rp);
+__global__ void k_grid_fill(const RunDesc *Rp);
 }  // namespace rvea
 
 using namespace rvea;
@@ -100,6 +112,7 @@ struct Shape {
   int n_repro, n_init, nblk;
   int n_sel_max;   // work items of the finest full-scan plan (table size)
   int tmax;     // tiles of the pruned selection (0: not used)
+  int gG, gcells, gcap;   // direction grid of the association (gG = 0: none)
 };
 
 // Pruned selection: m <= 4 and the tile-ordered vectors plus the tile table
@@ -143,13 +156,23 @@ Shape make_shape(int m, int d, int N) {
   s.tmax = 0;
   if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap)
     s.tmax = prune_tiles_bound(N);
+  // direction grid (m = 2, 3, with the tile tables it is built from): steps
+  // of 1/(4H) (m = 2) or 1/(2H) (m = 3) per barycentric axis, a fraction of
+  // the lattice spacing 1/H, so that a cell lists a handful of vectors
+  s.gG = s.gcells = s.gcap = 0;
+  if (s.tmax > 0 && (m == 2 || m == 3)) {
+    const int H = m == 2 ? N - 1 : (int)std::llround((std::sqrt(8.0 * N + 1.0) - 3.0) / 2.0);
+    s.gG = m == 2 ? 4 * H : 2 * H;
+    s.gcells = m == 2 ? s.gG : s.gG * s.gG;
+    s.gcap = std::max(4096, 2 * s.gcells);   // overflow lists (cells past 15 candidates)
+  }
   return s;
 }
 
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
-      ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, Vt, tperm, trng, tcen, tcs,
-      noise, dynA, dynB, total;
+      ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, otag, occ_cnt, vcnt, zacc, Vt,
+      tperm, trng, tcen, tcs, gcell, gcnt, gover, gscale, vrange, fcomb, noise, dynA, dynB, total;
 };
 
 Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
@@ -188,12 +211,22 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
   L.rec_par = take((size_t)2 * s.P * 4);
   L.rec_sites = take((size_t)s.N * (1 + kMaxSites) * 4);
+  L.otag = take((size_t)2 * s.N * 4);
+  L.occ_cnt = take((size_t)kTailMaxCtas * 4);
+  L.vcnt = take((size_t)kTailMaxCtas * 4);
+  L.zacc = take((size_t)2 * kMaxM * 4);
   const size_t T = (size_t)s.tmax;
   L.Vt = take(s.tmax ? (size_t)s.N * 16 : 0);
   L.tperm = take(s.tmax ? (size_t)s.N * 4 : 0);
   L.trng = take(T * 8 + 16);
   L.tcen = take(T * 16);
   L.tcs = take(T * 8 + 16);
+  L.gcell = take((size_t)s.gcells * 32);
+  L.gcnt = take((size_t)s.gcells * 4);
+  L.gover = take((size_t)s.gcap * 2);
+  L.gscale = take(kMaxM * 4);
+  L.vrange = take(kMaxM * 8);
+  L.fcomb = take((size_t)2 * s.m * s.n_comb * 4);
   L.noise = take((size_t)steps_max * ns_max * 4);
   L.dynA = take((size_t)ns_max * ns_max * 4);
   L.dynB = take((size_t)ns_max * na_max * 4);
@@ -317,6 +350,7 @@ int site_count_thresholds(double q, int d, uint32_t *thr) {
 
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
+int g_tail_dyn_max = 0;   // dynamic shared memory the fused tail kernel can take
 
 thread_local cudaError_t g_last_err = cudaSuccess;
 thread_local const char *g_last_where = "";
@@ -368,6 +402,15 @@ void set_kernel_attrs() {
   set((const void *)k_select);
   set((const void *)k_select_pruned);
   set((const void *)k_select_pruned_batch);
+  set((const void *)k_tail_dtlz1);
+  {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void *)k_tail_dtlz1) == cudaSuccess)
+      g_tail_dyn_max = optin - (int)fa.sharedSizeBytes;
+  }
+  set((const void *)k_tail_dtlz2);
+  set((const void *)k_tail_dtlz3);
+  set((const void *)k_tail_dtlz4);
 
   g_attr_err = e;
 }
@@ -494,10 +537,29 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
   }
 }
 
+// Reproduction by DE/rand/1/bin or random reproduction (the runs whose
+// operator is not SBX): one kernel per problem over a directory of such
+// runs, one warp per offspring.
+constexpr int kOpWarps = kReproThreads / 32;
+void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st) {
+  switch (problem) {
+    case PROB_DTLZ1: launch_pdl(k_repro_op_dtlz1, grid, kReproThreads, 0, st, d); break;
+    case PROB_DTLZ3: launch_pdl(k_repro_op_dtlz3, grid, kReproThreads, 0, st, d); break;
+    case PROB_DTLZ4: launch_pdl(k_repro_op_dtlz4, grid, kReproThreads, 0, st, d); break;
+    default: launch_pdl(k_repro_op_dtlz2, grid, kReproThreads, 0, st, d); break;
+  }
+}
+void launch_repro_op1(const rvea_run *r, cudaStream_t st) {
+  static thread_local BatchDir d;
+  const int nb = (r->sh.N + kOpWarps - 1) / kOpWarps;
+  dir_single(d, r, nullptr, nb);
+  launch_repro_op(d, r->hd.problem, nb, st);
+}
+
 // Mutation and evaluation of the children of a run reproduced by 32-lane
 // teams (d > 1024), after its reproduction kernel; nothing for other runs.
 void launch_mutate1(const rvea_run *r, cudaStream_t st) {
-  if (r->sh.team != 32) return;
+  if (r->sh.team != 32 || r->hd.op != 0) return;
   static thread_local BatchDir dm;
   const int nb = (r->sh.N + kMutThreads - 1) / kMutThreads;
   dir_single(dm, r, nullptr, nb);
@@ -508,6 +570,28 @@ void launch_mutate1(const rvea_run *r, cudaStream_t st) {
     case PROB_DTLZ4: launch_pdl(k_mutate_dtlz4, nb, kMutThreads, 0, st, dm); break;
     default: launch_pdl(k_mutate_neuro, nb, kMutThreads, 0, st, dm); break;
   }
+}
+
+// The fused tail (k_tail: mutation and evaluation, association, finalize in
+// one persistent launch) serves one run of a DTLZ problem with the pruned
+// search, when each CTA's share of the pool-row bitmap fits its buffer, its
+// children fit its mutating warps and the search tables its shared memory.
+int tail_grid(const rvea_run *r) { return std::min(r->num_sms, kTailMaxCtas); }
+bool tail_ok(const rvea_run *r) {
+  return r->hd.ntiles > 0 && r->hd.problem != PROB_NEURO &&
+         (2 * r->sh.N + 31) / 32 <= 64 * tail_grid(r) &&
+         (r->sh.N + 31) / 32 <= kTailMutWarps * tail_grid(r) &&
+         r->prune_smem_bytes <= g_tail_dyn_max;
+}
+void launch_tail(const rvea_run *r, cudaStream_t st, bool pdl) {
+  const int g = tail_grid(r), sm = r->prune_smem_bytes;
+  const RunDesc *d = r->d_desc;
+  void (*k)(const RunDesc *) = r->hd.problem == PROB_DTLZ1   ? k_tail_dtlz1
+                               : r->hd.problem == PROB_DTLZ3 ? k_tail_dtlz3
+                               : r->hd.problem == PROB_DTLZ4 ? k_tail_dtlz4
+                                                             : k_tail_dtlz2;
+  if (pdl) launch_pdl(k, g, kTailThreads, sm, st, d);
+  else k<<<g, kTailThreads, sm, st>>>(d);
 }
 
 // Enqueue one generation of every run in `runs` (one launch per phase): the
@@ -561,15 +645,41 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   dp.prefix[np] = pp;
   dt.prefix[np] = pt;
   if (ev) cudaEventRecord(ev[0], st);
+  const bool fused = n == 1 && runs[0]->sel_mode == 3;
   if (n == 1) {
-    launch_repro1(runs[0], dr, pr, st);
-    launch_mutate1(runs[0], st);
+    if (runs[0]->hd.op != 0) {
+      launch_repro_op1(runs[0], st);
+    } else {
+      launch_repro1(runs[0], dr, pr, st);
+      if (!fused) launch_mutate1(runs[0], st);
+    }
   } else {
     // one launch per (problem, load path) group, each with its own directory
     int pg[2 * kProblems] = {};
     for (int g = 0; g < 2 * kProblems; ++g) dg[g].n = 0;
+    // the runs with another operator: one launch per problem
+    static thread_local BatchDir dop[kProblems];
+    int pop[kProblems] = {};
+    for (int g = 0; g < kProblems; ++g) dop[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
+      if (r->hd.op == 0) continue;
+      BatchDir &D = dop[r->hd.problem];
+      D.prefix[D.n] = pop[r->hd.problem];
+      D.desc[D.n] = r->d_desc;
+      D.key[D.n] = make_uint2(r->hd.key0, r->hd.key1);
+      D.items[D.n] = nullptr;
+      pop[r->hd.problem] += (r->sh.N + kOpWarps - 1) / kOpWarps;
+      ++D.n;
+    }
+    for (int g = 0; g < kProblems; ++g) {
+      if (dop[g].n == 0) continue;
+      dop[g].prefix[dop[g].n] = pop[g];
+      launch_repro_op(dop[g], g, pop[g], st);
+    }
+    for (int q = 0; q < n; ++q) {
+      const rvea_run *r = runs[q];
+      if (r->hd.op != 0) continue;
       const int g = r->hd.problem * 2 + (r->repro_smem > 0 ? 1 : 0);
       BatchDir &D = dg[g];
       D.prefix[D.n] = pg[g];
@@ -602,7 +712,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     for (int g = 0; g < kProblems; ++g) dm[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
-      if (r->sh.team != 32) continue;
+      if (r->sh.team != 32 || r->hd.op != 0) continue;
       BatchDir &D = dm[r->hd.problem];
       D.prefix[D.n] = pm[r->hd.problem];
       D.desc[D.n] = r->d_desc;
@@ -650,7 +760,9 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     }
   }
   if (ev) cudaEventRecord(ev[1], st);
-  if (np > 0) {
+  if (fused) {
+    launch_tail(runs[0], st, true);
+  } else if (np > 0) {
     if (n == 1 && runs[0]->sel_mode == 1)
       launch_pdl(k_select_pruned, runs[0]->num_sms, 1024, runs[0]->prune_smem_bytes, st,
                  (const RunDesc *)runs[0]->d_desc);
@@ -660,7 +772,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   if (ev) cudaEventRecord(ev[2], st);
   if (ns > 0) launch_pdl(k_select, ps, kSelThreads, sms, st, ds);
   if (ev) cudaEventRecord(ev[3], st);
-  launch_pdl(k_finalize, pd, 1024, 0, st, dd);
+  if (!fused) launch_pdl(k_finalize, pd, 1024, 0, st, dd);
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
     k_gamma<<<2 * runs[0]->num_sms, 256, 0, st>>>(df, 0);
@@ -678,10 +790,18 @@ rvea_status launch_gamma_force(rvea_run *r, cudaStream_t st) {
   return cuerr(cudaGetLastError());
 }
 
-// Tile table of the pruned selection after a change of V.
+// Tile table of the pruned selection after a change of V, then the direction
+// grid built from it (marked current for this V when it fits its buffer).
 rvea_status launch_tiles(rvea_run *r, cudaStream_t st) {
   if (r->hd.ntiles == 0) return RVEA_OK;
   k_tiles<<<(r->hd.ntiles + 7) / 8, 256, 0, st>>>(r->d_desc);
+  if (r->hd.gG > 0) {
+    const int nb = (r->hd.gcells + 7) / 8;   // one warp per cell
+    k_grid_scale<<<1, 32, 0, st>>>(r->d_desc);
+    k_grid_count<<<nb, 256, 0, st>>>(r->d_desc);
+    k_grid_scan<<<1, 1024, 0, st>>>(r->d_desc);
+    k_grid_fill<<<nb, 256, 0, st>>>(r->d_desc);
+  }
   return cuerr(cudaGetLastError());
 }
 
@@ -743,6 +863,12 @@ rvea_status validate(const rvea_config *c) {
   // the DTLZ problems are defined on the unit box
   if (c->problem != PROB_NEURO && (c->lower != 0.0 || c->upper != 1.0)) return RVEA_ERR_ARG;
   if (c->problem < 0 || c->problem >= kProblems) return RVEA_ERR_ARG;
+  // the other reproduction operators (DTLZ problems)
+  if (c->reproduction < 0 || c->reproduction > 2) return RVEA_ERR_ARG;
+  if (c->reproduction != 0 && c->problem == PROB_NEURO) return RVEA_ERR_ARG;
+  if (c->reproduction == 1 &&
+      (!(c->de_F > 0) || c->de_F > 2 || !(c->de_CR >= 0) || c->de_CR > 1))
+    return RVEA_ERR_ARG;
   if (c->problem == RVEA_NEURO_LINEAR) {
     // the rollout's shape: h1 = h2 = 64 (the tensor-core tiling), ns <= 32
     // (one lane per state component), na <= 16 (one 16-row tile), and d the
@@ -838,6 +964,9 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.eta_m = (float)cfg->eta_m;
   D.T_c = event_threshold24(cfg->p_c);
   D.T_m = event_threshold24(cfg->p_m / (double)cfg->d);
+  D.op = cfg->reproduction;
+  D.de_F = (float)cfg->de_F;
+  D.T_cr = event_threshold24(cfg->de_CR);
   if (D.T_m > 0u && D.T_m < (1u << 24))
     D.n_mthr = site_count_thresholds((double)D.T_m / 16777216.0, sh.d, D.mthr);
   D.key0 = (uint32_t)cfg->seed;
@@ -873,6 +1002,19 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gamma32 = wsp<float>(r, lay.g32);
   D.ctl = wsp<Ctl>(r, lay.ctl);
   D.psum = wsp<float>(r, lay.psum);
+  D.otag = wsp<int>(r, lay.otag);
+  D.occ_cnt = wsp<unsigned>(r, lay.occ_cnt);
+  D.vcnt = wsp<int>(r, lay.vcnt);
+  D.zacc = wsp<unsigned>(r, lay.zacc);
+  D.gG = sh.gG;
+  D.gcells = sh.gcells;
+  D.gcap = sh.gcap;
+  D.gcell = wsp<uint16_t>(r, lay.gcell);
+  D.gcnt = wsp<int>(r, lay.gcnt);
+  D.gover = wsp<uint16_t>(r, lay.gover);
+  D.gscale = wsp<float>(r, lay.gscale);
+  D.vrange = wsp<double>(r, lay.vrange);
+  D.fcomb = wsp<float>(r, lay.fcomb);
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
   r->repro_smem = sh.team == 32 ? kStagedSmem : 0;   // staged path (the default for 32-lane teams)
@@ -904,6 +1046,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     D.tcs = wsp<float2>(r, lay.tcs);
     r->prune_smem_bytes = (int)prune_smem(sh.N, D.ntiles);
   }
+  if (tail_ok(r)) r->sel_mode = 3;
   std::vector<float> V32((size_t)sh.N * sh.m4 * 4, 0.0f), V32lo((size_t)sh.N * sh.m);
   for (int j = 0; j < sh.N; ++j)
     for (int k = 0; k < sh.m; ++k) {
@@ -915,6 +1058,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   std::memset(&c0, 0, sizeof(c0));
   c0.t = 1;
   c0.K = sh.N;
+  c0.grid_ver = -1;
   for (int k = 0; k < kMaxM; ++k) c0.zkey[k] = 0xFFFFFFFFu;
 
   rvea_status s = RVEA_OK;
@@ -931,6 +1075,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.V32, V32.data(), V32.size() * 4);
   up(lay.V32lo, V32lo.data(), V32lo.size() * 4);
   up(lay.ctl, &c0, sizeof(c0));
+  const std::vector<double> ones(kMaxM, 1.0);
+  up(lay.vrange, ones.data(), kMaxM * 8);
   if (nd) {
     up(lay.dynA, dynA.data(), dynA.size() * 4);
     up(lay.dynB, dynB.data(), dynB.size() * 4);
@@ -1036,7 +1182,8 @@ rvea_status rvea_step_batch(rvea_run *const *runs, int n_runs, void *cuda_stream
 namespace {
 
 rvea_status apply_plan(rvea_run *r, const rvea_plan &pl, cudaStream_t st) {
-  if (pl.sel_mode < 0 || pl.sel_mode > 2 || (pl.sel_mode > 0 && r->hd.ntiles == 0))
+  if (pl.sel_mode < 0 || pl.sel_mode > 3 || (pl.sel_mode > 0 && r->hd.ntiles == 0) ||
+      (pl.sel_mode == 3 && !tail_ok(r)))
     return RVEA_ERR_ARG;
   if (pl.sel_per_sm < 1 || pl.sel_per_sm > kSelPerSmMax) return RVEA_ERR_ARG;
   if (pl.repro_staged && r->sh.team != 32) return RVEA_ERR_ARG;
@@ -1162,7 +1309,9 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
   rvea_plan best = before;
   // reproduction: direct loads, and TMA staging for 32-lane teams
   double best_rep = 1e30;
-  for (int staged = 0; staged <= (r->sh.team == 32 ? 1 : 0) && s == RVEA_OK; ++staged) {
+  if (r->hd.op != 0) {
+    best_rep = timed([&] { launch_repro_op1(r, st); }, false);
+  } else for (int staged = 0; staged <= (r->sh.team == 32 ? 1 : 0) && s == RVEA_OK; ++staged) {
     r->repro_smem = staged ? kStagedSmem : 0;
     const double us = timed([&] { launch_repro1(r, dr, r->sh.n_repro, st); }, false);
     if (us < best_rep) { best_rep = us; best.repro_staged = staged; }
@@ -1201,6 +1350,9 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // the pruned search in shared memory runs inside the fused tail where the
+  // run has one (the same search, without the launch boundaries around it)
+  if (best.sel_mode == 1 && tail_ok(r)) best.sel_mode = 3;
   // the tables above were rebuilt for the candidates: force the chosen plan
   r->sel_per_sm = -1;
   r->repro_smem = before.repro_staged ? kStagedSmem : 0;
@@ -1331,10 +1483,13 @@ int rvea_generation(const rvea_run *r) { return r ? r->t : -1; }
 
 int rvea_launches_per_generation(const rvea_run *r, int adapting) {
   if (!r) return -1;
+  // gamma, then the tile table and the direction grid (4 launches)
+  const int adapt_n = adapting ? 1 + (r->hd.ntiles > 0 ? 1 : 0) + (r->hd.gG > 0 ? 4 : 0) : 0;
+  if (r->sel_mode == 3) return 2 + adapt_n;   // reproduction, fused tail
   int n = 3;                                        // reproduction, selection, finalize
-  if (r->sh.team == 32) n += 1;                     // k_mutate
+  if (r->sh.team == 32 && r->hd.op == 0) n += 1;    // k_mutate
   if (r->hd.problem == PROB_NEURO) n += 2;          // noise, rollout
-  if (adapting) n += 1 + (r->hd.ntiles > 0 ? 1 : 0);   // gamma, tile table
+  n += adapt_n;
   return n;
 }
 
@@ -1367,9 +1522,10 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
   for (int g = 0; g < G && s == RVEA_OK; ++g) {
     cudaEvent_t *e = &ev[(size_t)g * 6];
     cudaEventRecord(e[0], st);
-    launch_repro1(r, dr, r->sh.n_repro, st);
+    if (r->hd.op != 0) launch_repro_op1(r, st);
+    else launch_repro1(r, dr, r->sh.n_repro, st);
     cudaEventRecord(e[5], st);
-    launch_mutate1(r, st);
+    if (r->sel_mode != 3) launch_mutate1(r, st);
     if (r->hd.problem == PROB_NEURO) {
       const int nb_noise = (r->hd.steps * r->hd.ns + 255) / 256;
       const int nb_roll = (r->sh.N + kRollPolicies - 1) / kRollPolicies;
@@ -1379,14 +1535,16 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
       k_rollout<<<nb_roll, 32 * kRollPolicies, 0, st>>>(dro1, 0);
     }
     cudaEventRecord(e[1], st);
-    if (r->sel_mode == 1)
+    if (r->sel_mode == 3)   // the fused tail: mutation, association and finalize
+      launch_tail(r, st, false);
+    else if (r->sel_mode == 1)
       k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
     else if (r->sel_mode == 2)
       k_select_pruned_batch<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(dpb);
     else
       k_select<<<r->n_sel, kSelThreads, r->sel_smem, st>>>(ds);
     cudaEventRecord(e[2], st);
-    k_finalize<<<nbd, 1024, 0, st>>>(dd);
+    if (r->sel_mode != 3) k_finalize<<<nbd, 1024, 0, st>>>(dd);
     cudaEventRecord(e[3], st);
     if (r->t % r->p_adapt == 0) {
       k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
@@ -1606,7 +1764,7 @@ rvea_status rvea_record_draws(rvea_run *r, int enable, void *cuda_stream) {
 rvea_status rvea_last_draws(const rvea_run *r, int32_t *parents, int32_t *sites,
                             void *cuda_stream) {
   if (!r) return RVEA_ERR_ARG;
-  if (!r->has_last_gen || !r->last_gen_recorded) return RVEA_ERR_STATE;
+  if (!r->has_last_gen || !r->last_gen_recorded || r->hd.op != 0) return RVEA_ERR_STATE;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (parents)
     RV_TRY(cudaMemcpyAsync(parents, r->ws + r->lay.rec_par, (size_t)2 * r->sh.P * 4,

@@ -153,30 +153,16 @@ __device__ inline void fin_lists(const RunDesc &R, int nblk, FinShared &sh) {
     if (tid < m) {
       const double r = (double)ord2f(sh.z[kMaxM + tid]) - (double)ord2f(sh.z[tid]);
       sh.rng[tid] = r < 1e-12 ? 1e-12 : r;
+      R.vrange[tid] = sh.rng[tid];
     }
     __syncthreads();
-    for (int jj = tid; jj < N; jj += kFinDecode) {
-      const double *v0p = R.V0 + (size_t)jj * m;
-      double w[kMaxM];
-      double s2 = 0.0;
-      for (int k = 0; k < m; ++k) {
-        w[k] = v0p[k] * sh.rng[k];
-        s2 += w[k] * w[k];
-      }
-      const double nrm = sqrt(s2);
-      float *v32 = R.V32 + (size_t)jj * R.m4 * 4;
-      for (int k = 0; k < m; ++k) {
-        const double v = w[k] / nrm;
-        R.V64[(size_t)jj * m + k] = v;
-        v32[k] = (float)v;
-        R.V32lo[(size_t)jj * m + k] = (float)(v - (double)(float)v);
-      }
-    }
+    for (int jj = tid; jj < N; jj += kFinDecode) adapt_row(R, jj, sh.rng);
   }
   __syncthreads();   // every thread has read t and the counters
   if (tid == 0) {
     R.ctl->K = K;
     R.ctl->adapted = adapt ? 1 : 0;
+    if (adapt && K > 0) R.ctl->v_ver += 1;
     R.ctl->fin_cnt = 0;
     R.ctl->sel_cnt = 0;
     R.ctl->t = t + 1;

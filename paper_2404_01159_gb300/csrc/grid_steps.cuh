@@ -1,0 +1,129 @@
+// Direction grid of the exact association (Algorithm 1 lines 5-6, Eq. 2)
+// for m = 2, 3.
+//
+// The association of a solution depends only on the direction of f' = F - z*
+// (f' >= 0).  A direction is the point a of the simplex (a_k = u_k / sum u,
+// u = f' (.) w, w > 0 a per-run scale: 1 at first, 1 / range after each
+// adaptation, so that the grid follows the rescaled reference vectors), and
+// the grid cuts the first m - 1 barycentric coordinates into G equal steps.
+// For each cell the build (k_grid_count / k_grid_fill) lists every reference
+// vector that can be the float32 argmax of f'.v for some direction in the
+// cell: with c the cell's centre direction and rho the largest angle from c
+// to the cell (its corners, widened by more than the rounding of a in
+// float32), a vector b found near c gives every direction d in the cell a
+// best cosine of at least L = cos(angle(c, v_b) + rho); a vector j can reach
+// the argmax at d only if cos(d, v_j) >= L - 2 eps (eps bounds the float32
+// dot error relative to |f'|, below 1e-6), which needs
+//   angle(c, v_j) <= R = rho + acos(L - 2 eps).
+// Every such j is listed (the test runs in float32 with margins that only
+// ever admit more vectors).  The lookup then scans the cell's list with the
+// full scan's arithmetic (same products, larger dot, on equal dots the
+// smaller index), so the result is the full scan's, bit for bit, after about
+// half a dozen dot products instead of the tile search.
+//
+// The grid is valid for one set of reference vectors: the control block's
+// v_ver counts changes of V (adaptation, import) and grid_ver records the V
+// the grid was built for; a kernel uses the grid only when they agree (and
+// the build fitted its buffer), and otherwise the tile search.
+#pragma once
+#include "prune_steps.cuh"
+
+namespace rvea {
+
+constexpr int kGridRec = 16;      // uint16 per cell record (32 bytes)
+constexpr int kGridInline = 15;   // candidates held in the record itself
+
+// Cell of the direction of f' (>= 0, not 0): the first M - 1 scaled
+// barycentric coordinates, each cut into G steps.
+template <int M>
+__device__ __forceinline__ int grid_cell(const float *f, const float *w, int G) {
+  float u[M], s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    u[k] = f[k] * w[k];
+    s += u[k];
+  }
+  const float inv = (float)G / s;
+  int cell = 0, mul = 1;
+#pragma unroll
+  for (int k = 0; k < M - 1; ++k) {
+    const int c = min(G - 1, max(0, (int)(u[k] * inv)));
+    cell += c * mul;
+    mul *= G;
+  }
+  return cell;
+}
+
+// Association of solution i through the grid, then its APD vote (Eq. 4), as
+// prune_group does.  One thread per solution; sV: the tile-order vectors
+// (vector index in the fourth lane).
+// fc: the combined objectives of this generation by combined index (NaN for
+// an invalid parent), or null to read them through the slot maps.
+template <int M>
+__device__ __forceinline__ void grid_assoc(const RunDesc &R, int i, const float4 *sV,
+                                           const float *z, const float *w, float pen,
+                                           const float *fc) {
+  const int N = R.N, n = R.n_comb;
+  if (i >= n) return;
+  float f[4] = {0.f, 0.f, 0.f, 0.f};
+  if (fc) {
+    float F0[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) F0[k] = __ldcg(fc + (size_t)k * n + i);
+    if (F0[0] != F0[0]) {   // an invalid parent
+      R.assoc[i] = -1;
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) f[k] = F0[k] - z[k];
+  } else {
+    const int par = R.ctl->t & 1;
+    const int slot = i < N ? R.slotmap[par * N + i] : R.child_slot[par * N + (i - N)];
+    if (slot < 0) {
+      R.assoc[i] = -1;
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) f[k] = __ldcg(R.F + (size_t)k * n + slot) - z[k];
+  }
+  float s2 = f[0] * f[0];
+#pragma unroll
+  for (int k = 1; k < M; ++k) s2 = fmaf(f[k], f[k], s2);
+  int bj = 0;   // f' = 0: every dot is +0, the full scan keeps vector 0
+  if (sqrtf(s2) > 0.0f) {
+    const int cell = grid_cell<M>(f, w, R.gG);
+    // the cell's 32-byte record: count, then up to kGridInline candidates
+    const uint4 *rp = reinterpret_cast<const uint4 *>(R.gcell + (size_t)cell * kGridRec);
+    const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    const uint32_t wd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    const int n = (int)(wd[0] & 0xFFFFu);
+    float best = -INFINITY;
+    bj = 0x7FFFFFFF;
+    if (n <= kGridInline) {
+#pragma unroll
+      for (int e = 0; e < kGridInline; ++e) {
+        if (e < n) {
+          const uint32_t q = (wd[(e + 1) >> 1] >> (16 * ((e + 1) & 1))) & 0xFFFFu;
+          const float4 v = sV[q];
+          keep(pdot<M>(f, v), __float_as_int(v.w), best, bj);
+        }
+      }
+    } else {
+      const int at = (int)((wd[0] >> 16) | ((wd[1] & 0xFFFFu) << 16));
+      for (int e = 0; e < n; ++e) {
+        const float4 v = sV[R.gover[at + e]];
+        keep(pdot<M>(f, v), __float_as_int(v.w), best, bj);
+      }
+    }
+  }
+  if (bj < 0 || bj >= N) {
+    set_status(R.ctl, ST_BADINDEX);
+    return;
+  }
+  const float apd = apd_chord(f, M, R.V32 + (size_t)bj * R.m4 * 4, R.V32lo + (size_t)bj * M,
+                              R.gamma32[bj], pen);
+  R.assoc[i] = bj;
+  atomicMin(&R.best[bj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
+}
+
+}  // namespace rvea

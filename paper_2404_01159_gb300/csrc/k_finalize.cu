@@ -511,7 +511,7 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
     R.best[j] = ~0ull;
     R.surv[j] = -1;
   }
-  for (int i = tid; i < n2; i += kFinThreads) { R.amax[i] = 0ull; R.assoc[i] = -1; }
+  for (int i = tid; i < n2; i += kFinThreads) { R.amax[i] = 0ull; R.assoc[i] = -1; R.otag[i] = 0; }
   for (int w = tid; w < (n2 + 31) / 32; w += kFinThreads) R.obits[w] = 0u;
   for (int b = tid; b < (n2 + kSelBlock - 1) / kSelBlock; b += kFinThreads) R.blk_cnt[b] = 0;
   // valid list
@@ -541,7 +541,11 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
     R.ctl->adapted = 0;
     R.ctl->fin_cnt = 0;
     R.ctl->sel_cnt = 0;
+    R.ctl->bar = 0ull;
+    R.ctl->v_ver += 1;   // V was replaced
+    R.ctl->fcomb_t = 0;
   }
+  if (tid < m) R.vrange[tid] = 1.0;
 }
 
 // Initial slot map and lists after k_init: slot j = row j, children go to

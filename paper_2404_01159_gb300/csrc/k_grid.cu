@@ -1,0 +1,259 @@
+// Build of the direction grid of the association (grid_steps.cuh): after
+// every change of the reference vectors (initialisation, adaptation), once
+// the tile tables are current.  One warp per cell, two passes over the cells
+// (count, then fill at the scanned offsets) and a scan between them.
+#include "grid_steps.cuh"
+
+namespace rvea {
+
+constexpr float kGridPad = 4e-6f;   // cell widening in barycentric units (float rounding of a)
+constexpr float kDotTol = 3e-6f;    // float32 cosine error allowance of the build's tests
+constexpr float kCandEps = 2e-6f;   // 2 eps: dot error of the association relative to |f'|
+constexpr float kAngTol = 2e-5f;    // allowance for the float32 angles below (radians)
+
+// The cell's candidate test: centre direction and cos / sin of R (float,
+// rounded outwards), or live = false for a cell that lies outside the
+// simplex (never looked up).  Every lane computes the same values.
+struct CellGeom {
+  float c[4];
+  float cosR, sinR;
+  float corner[4][3];   // the padded cell's corner directions (M - 1 <= 2 axes)
+  float vb[4];          // a reference vector close to c
+  float delta2;         // (largest chord centre-corner)^2, the curvature allowance
+  bool live;
+};
+
+template <int M>
+__device__ CellGeom cell_geom(const RunDesc &R, int cell, const float4 *Vt) {
+  CellGeom g;
+  g.live = false;
+  const int G = R.gG, lane = threadIdx.x & 31;
+  int ck[2] = {0, 0};
+  int rem = cell;
+  for (int k = 0; k < M - 1; ++k) { ck[k] = rem % G; rem /= G; }
+  float lo[2], hi[2], sl = 0.0f;
+  for (int k = 0; k < M - 1; ++k) {
+    lo[k] = (float)ck[k] / (float)G - kGridPad;
+    hi[k] = (float)(ck[k] + 1) / (float)G + kGridPad;
+    sl += lo[k];
+  }
+  if (sl > 1.0f) return g;
+  float w[M];
+  for (int k = 0; k < M; ++k) w[k] = R.gscale[k];
+  // a point a of the scaled simplex -> unit direction a / w
+  auto dir = [&](const float *a, float *x) {
+    float s2 = 0.0f, last = 1.0f;
+    for (int k = 0; k < M - 1; ++k) last -= a[k];
+    for (int k = 0; k < M; ++k) {
+      x[k] = (k < M - 1 ? a[k] : last) / w[k];
+      s2 += x[k] * x[k];
+    }
+    const float inv = rsqrtf(s2);
+    for (int k = 0; k < M; ++k) x[k] *= inv;
+  };
+  float a[2], c[M];
+  for (int k = 0; k < M - 1; ++k) a[k] = 0.5f * (lo[k] + hi[k]);
+  dir(a, c);
+  // rho from the longest chord centre-corner (well conditioned for small angles)
+  float chord = 0.0f;
+  for (int msk = 0; msk < (1 << (M - 1)); ++msk) {
+    for (int k = 0; k < M - 1; ++k) a[k] = (msk >> k) & 1 ? hi[k] : lo[k];
+    float x[M], d2 = 0.0f;
+    dir(a, x);
+    for (int k = 0; k < M; ++k) {
+      d2 += (x[k] - c[k]) * (x[k] - c[k]);
+      g.corner[msk][k] = x[k];
+    }
+    chord = fmaxf(chord, sqrtf(d2));
+  }
+  g.delta2 = (chord + 1e-5f) * (chord + 1e-5f);
+  const float kPi = 3.14159265f;
+  const float rho = 2.0f * asinf(fminf(1.0f, 0.5f * chord)) + kAngTol;
+  for (int k = 0; k < 4; ++k) g.c[k] = k < M ? c[k] : 0.0f;
+  // a vector close to c: the best member of the tile whose centre is closest
+  float bt = -INFINITY;
+  int tb = 0;
+  for (int t = lane; t < R.ntiles; t += 32) {
+    const float d = pdot<M>(g.c, R.tcen[t]);
+    if (d > bt) { bt = d; tb = t; }
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, bt, off);
+    const int ot = __shfl_xor_sync(0xffffffffu, tb, off);
+    if (od > bt || (od == bt && ot < tb)) { bt = od; tb = ot; }
+  }
+  const int2 rg = R.trng[tb];
+  float cb = -INFINITY;
+  int qb = rg.x;
+  for (int q = lane; q < rg.y; q += 32) {
+    const float d = pdot<M>(g.c, Vt[rg.x + q]);
+    if (d > cb) { cb = d; qb = rg.x + q; }
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, cb, off);
+    const int oq = __shfl_xor_sync(0xffffffffu, qb, off);
+    if (od > cb || (od == cb && oq < qb)) { cb = od; qb = oq; }
+  }
+  {
+    const float4 v = Vt[qb];
+    g.vb[0] = v.x; g.vb[1] = v.y; g.vb[2] = v.z; g.vb[3] = 0.0f;
+  }
+  // angle to that vector (bounded above), the lower bound Lb of the best
+  // cosine over the cell, the candidate radius R (bounded above)
+  const float thb = acosf(fmaxf(-1.0f, fminf(1.0f, cb - kDotTol))) + kAngTol;
+  const float Lb = cosf(fminf(kPi, thb + rho)) - kDotTol;
+  const float Rr = fminf(kPi, rho + acosf(fmaxf(-1.0f, Lb - kCandEps)) + kAngTol);
+  g.cosR = cosf(Rr) - kDotTol;
+  g.sinR = fminf(1.0f, sinf(Rr) + kDotTol);
+  g.live = true;
+  return g;
+}
+
+// A finer necessary condition for member v (float): with u = v - v_b and any
+// direction d of the cell, d.v >= d.v_b - 2 eps requires
+//   c.u + max_corner (x - c).u + delta^2 |u| >= -2 eps
+// ((d - c).u is at most its value at a corner of the cell, up to the
+// curvature of the cell on the sphere, below delta^2 |u|).  It keeps the
+// lists short where the cell is elongated in angle.
+template <int M>
+__device__ __forceinline__ bool support_test(const CellGeom &g, float4 v) {
+  const float u[3] = {v.x - g.vb[0], v.y - g.vb[1], M > 2 ? v.z - g.vb[2] : 0.0f};
+  float cu = 0.0f, uu = 0.0f;
+#pragma unroll
+  for (int k = 0; k < M; ++k) { cu = fmaf(g.c[k], u[k], cu); uu = fmaf(u[k], u[k], uu); }
+  float sup = -INFINITY;
+#pragma unroll
+  for (int msk = 0; msk < (1 << (M - 1)); ++msk) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) s = fmaf(g.corner[msk][k] - g.c[k], u[k], s);
+    sup = fmaxf(sup, s);
+  }
+  return cu + sup + g.delta2 * sqrtf(uu) >= -(kCandEps + 2.0f * kDotTol);
+}
+
+// Count (FILL = false) or write (FILL = true) the candidates of every cell:
+// the tiles whose centre lies within R + rho_t of c, then their members
+// within R that pass the support test.
+template <int M, bool FILL>
+__device__ void grid_cells(const RunDesc &R) {
+  const int lane = threadIdx.x & 31;
+  const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (cell >= R.gcells) return;
+  if (FILL && __ldcg(&R.ctl->grid_ver) != __ldcg(&R.ctl->v_ver)) return;   // did not fit
+  const float4 *Vt = R.Vt;
+  const CellGeom g = cell_geom<M>(R, cell, Vt);
+  int n = 0;
+  // inline records hold up to kGridInline candidates; longer lists go to the
+  // overflow area at the offset the scan stored in the record
+  uint16_t *rec = R.gcell + (size_t)cell * kGridRec;
+  int at = 0;
+  bool inl = true;
+  if (FILL) {
+    const int cnt = rec[0];
+    inl = cnt <= kGridInline;
+    at = inl ? 0 : (int)((uint32_t)rec[1] | ((uint32_t)rec[2] << 16));
+  }
+  if (g.live) {
+    const bool wide = g.cosR < 0.0f;   // R > pi/2: every tile
+    const float cR = g.cosR, sR = g.sinR;
+    const float thr_m = g.cosR - kDotTol;
+    for (int t0 = 0; t0 < R.ntiles; t0 += 32) {
+      const int t = t0 + lane;
+      bool pass = false;
+      if (t < R.ntiles) {
+        const float2 cs = R.tcs[t];
+        const float d = pdot<M>(g.c, R.tcen[t]);
+        pass = wide || d >= fmaf(cR, cs.x, -sR * cs.y) - kDotTol;
+      }
+      unsigned tm = __ballot_sync(0xffffffffu, pass);
+      while (tm) {
+        const int tt = t0 + __ffs(tm) - 1;
+        tm &= tm - 1;
+        const int2 rg = R.trng[tt];
+        for (int q0 = 0; q0 < rg.y; q0 += 32) {
+          const int q = q0 + lane;
+          bool in = false;
+          if (q < rg.y) {
+            const float4 v = Vt[rg.x + q];
+            in = pdot<M>(g.c, v) >= thr_m && support_test<M>(g, v);
+          }
+          const unsigned mm = __ballot_sync(0xffffffffu, in);
+          if (FILL && in) {
+            const int e = n + __popc(mm & ((1u << lane) - 1u));
+            if (inl) rec[1 + e] = (uint16_t)(rg.x + q);
+            else R.gover[at + e] = (uint16_t)(rg.x + q);
+          }
+          n += __popc(mm);
+        }
+      }
+    }
+  }
+  if (!FILL && lane == 0) R.gcnt[cell] = n;
+}
+
+__global__ void __launch_bounds__(256) k_grid_count(const RunDesc *__restrict__ Rp) {
+  const RunDesc &R = *Rp;
+  if (R.m == 2) grid_cells<2, false>(R); else grid_cells<3, false>(R);
+}
+__global__ void __launch_bounds__(256) k_grid_fill(const RunDesc *__restrict__ Rp) {
+  const RunDesc &R = *Rp;
+  if (R.m == 2) grid_cells<2, true>(R); else grid_cells<3, true>(R);
+}
+
+// Exclusive scan of the overflow lists (cells with more than kGridInline
+// candidates), one CTA; every record gets its count and, for an overflow
+// cell, its offset.  The grid is marked current for this V when the overflow
+// lists fit their buffer.
+__global__ void __launch_bounds__(1024) k_grid_scan(const RunDesc *__restrict__ Rp) {
+  __shared__ int s_w[32];
+  const RunDesc &R = *Rp;
+  const int n = R.gcells, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + 1023) / 1024, a0 = min(n, tid * per), a1 = min(n, a0 + per);
+  auto ovf = [&](int c) { const int k = R.gcnt[c]; return k > kGridInline ? k : 0; };
+  int sum = 0;
+  for (int c = a0; c < a1; ++c) sum += ovf(c);
+  int incl = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int v = s_w[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += y;
+    }
+    s_w[lane] = v;
+  }
+  __syncthreads();
+  int run = (warp > 0 ? s_w[warp - 1] : 0) + incl - sum;
+  for (int c = a0; c < a1; ++c) {
+    uint16_t *rec = R.gcell + (size_t)c * kGridRec;
+    const int k = R.gcnt[c];
+    rec[0] = (uint16_t)min(k, 0xFFFF);
+    if (k > kGridInline) {
+      rec[1] = (uint16_t)(run & 0xFFFF);
+      rec[2] = (uint16_t)((uint32_t)run >> 16);
+      run += k;
+    }
+  }
+  if (tid == 1023) {
+    const int total = s_w[31];
+    if (total <= R.gcap) R.ctl->grid_ver = R.ctl->v_ver;
+  }
+}
+
+// Grid scale w = 1 / range of the last adaptation (1 before any), as float.
+__global__ void k_grid_scale(const RunDesc *__restrict__ Rp) {
+  const RunDesc &R = *Rp;
+  if (threadIdx.x < R.m) R.gscale[threadIdx.x] = (float)(1.0 / R.vrange[threadIdx.x]);
+}
+
+}  // namespace rvea

@@ -3,7 +3,7 @@
 // of runs in one persistent launch, and the tile tables after a change of V.
 // The search itself (tile bounds, candidate scan, APD vote) is in
 // prune_steps.cuh.
-#include "prune_steps.cuh"
+#include "grid_steps.cuh"
 
 namespace rvea {
 
@@ -43,6 +43,20 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
   const float2 csb = tile_bounds(sCS, T);
   pdl_wait();
   pdl_trigger();
+  if (R.gG > 0 && __ldcg(&R.ctl->grid_ver) == __ldcg(&R.ctl->v_ver)) {
+    // the direction grid: one thread per solution
+    const float pen = (float)R.m * powf((float)R.ctl->t / (float)R.t_max, R.alpha);
+    float z[4], w[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = k < R.m ? ord2f(R.ctl->zkey[k]) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = k < R.m ? R.gscale[k] : 1.0f;
+    for (int i = threadIdx.x * gridDim.x + blockIdx.x; i < R.n_comb; i += gridDim.x * blockDim.x) {
+      if (R.m == 2) grid_assoc<2>(R, i, sV, z, w, pen, nullptr);
+      else grid_assoc<3>(R, i, sV, z, w, pen, nullptr);
+    }
+    return;
+  }
   switch (R.m) {
     case 2: prune_loop<2>(R, sV, sC, sCS, sR, csb); break;
     case 3: prune_loop<3>(R, sV, sC, sCS, sR, csb); break;

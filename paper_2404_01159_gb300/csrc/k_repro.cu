@@ -570,6 +570,145 @@ RVEA_MUTATE(k_mutate_dtlz4, PROB_DTLZ4)
 RVEA_MUTATE(k_mutate_neuro, PROB_NEURO)
 #undef RVEA_MUTATE
 
+// Reproduction by the other operators of the extensibility experiment
+// (Sec. 4.4 and Appendix C; the paper names them, this follows the published
+// operators): DE/rand/1/bin (Storn and Price 1997) or random reproduction.
+// They replace SBX and polynomial mutation and make the N offspring rows
+// directly.  One warp per offspring o:
+//   DE: the target is position o mod K of the valid list, r1, r2, r3 an
+//       ordered triple of other distinct positions drawn one after another
+//       without replacement from DE_PICK (o, 0, t) words 0..2, j_rand from
+//       word 3; u_j = x_r1,j + F (x_r2,j - x_r3,j) where the CR coin of j
+//       (DE_CR (j/4, o, t) word j%4, u24 < CR on the 24-bit grid) fires or
+//       j = j_rand, else the target's x_j; clipped to [L, U];
+//   random: x_j = L + (U - L) u24, RANDOM (j/4, o, t) word j%4.
+// Then the g-terms, objectives and the ideal point, as the other kernels.
+enum : uint32_t { TAG_DE_PICK = 8, TAG_DE_CR = 9, TAG_RANDOM = 10 };
+
+__device__ __forceinline__ int de_pos(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
+
+template <int PROB>
+__device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
+  __shared__ unsigned s_z[kMaxM];
+  pdl_wait();      // the previous generation's lists and slot maps
+  pdl_trigger();
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o = (blockIdx.x - dir.prefix[run]) * (kReproThreads / 32) + warp;
+  const int N = R.N, d = R.d, m = R.m, t = R.ctl->t, K = R.ctl->K;
+  const KeyRun kr{dir.key[run].x, dir.key[run].y};
+  if (threadIdx.x < kMaxM) s_z[threadIdx.x] = 0xFFFFFFFFu;
+  __syncthreads();
+  float f[kMaxM];
+  bool have = false;
+  if (o < N) {
+    int slot = R.child_slot[(t & 1) * N + o];
+    if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); slot = -1; }
+    // DE: the four rows (physical slots) and j_rand, drawn by lane 0
+    int rows[4] = {0, 0, 0, 0}, jr = -1;
+    if (R.op == 1 && lane == 0 && K > 0) {
+      const uint4 w = philox_k((uint32_t)o, 0u, (uint32_t)t, TAG_DE_PICK, kr);
+      const int tp = o % K;
+      int pos[4];
+      pos[0] = tp;
+      if (K >= 4) {
+        const int a = de_pos(w.x, K - 1);
+        int bq = de_pos(w.y, K - 2), c = de_pos(w.z, K - 3);
+        if (bq >= a) bq += 1;
+        const int lo = min(a, bq), hi = max(a, bq);
+        if (c >= lo) c += 1;
+        if (c >= hi) c += 1;
+        pos[1] = a < tp ? a : a + 1;
+        pos[2] = bq < tp ? bq : bq + 1;
+        pos[3] = c < tp ? c : c + 1;
+      } else {
+        pos[1] = de_pos(w.x, K);
+        pos[2] = de_pos(w.y, K);
+        pos[3] = de_pos(w.z, K);
+      }
+      jr = de_pos(w.w, d);
+      for (int q = 0; q < 4; ++q) {
+        const int j = R.vlist[pos[q]];
+        int sl = (j >= 0 && j < N) ? R.slotmap[(t & 1) * N + j] : -1;
+        if (sl < 0 || sl >= 2 * N) { set_status(R.ctl, ST_BADINDEX); sl = 0; }
+        rows[q] = sl;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rows[q] = __shfl_sync(0xffffffffu, rows[q], 0);
+    jr = __shfl_sync(0xffffffffu, jr, 0);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    float2 acc = make_float2(0.f, 0.f);
+    if (slot >= 0) {
+      const float L = R.L, U = R.U, Fde = R.de_F;
+      const int mh = m - 1;
+      const float4 *X4 = reinterpret_cast<const float4 *>(R.X);
+      float4 *Y4 = reinterpret_cast<float4 *>(R.X + (size_t)slot * R.d_pad);
+      const int rq = R.d_pad >> 2;
+      for (int Q = lane; Q < rq; Q += 32) {
+        float u[4];
+        if (R.op == 1) {
+          const uint4 w = philox_k((uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_DE_CR, kr);
+          const float4 xt = __ldg(X4 + (size_t)rows[0] * rq + Q);
+          const float4 x1 = __ldg(X4 + (size_t)rows[1] * rq + Q);
+          const float4 x2 = __ldg(X4 + (size_t)rows[2] * rq + Q);
+          const float4 x3 = __ldg(X4 + (size_t)rows[3] * rq + Q);
+          const float a0[4] = {xt.x, xt.y, xt.z, xt.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
+          const float a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
+          const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int j = 4 * Q + v;
+            const bool take = (ww[v] >> 8) < R.T_cr || j == jr;
+            const float val = take ? fmaf(Fde, a2[v] - a3[v], a1[v]) : a0[v];
+            u[v] = clampf(val, L, U);
+          }
+        } else {
+          const uint4 w = philox_k((uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_RANDOM, kr);
+          const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int v = 0; v < 4; ++v) u[v] = L + (U - L) * u24f(ww[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int j = 4 * Q + v;
+          if (j >= d) u[v] = 0.5f;   // row padding: a g-term of exactly zero
+          else if (j >= mh) {
+            if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
+            else acc.x = g_term1(PROB, u[v], acc.x);
+          }
+        }
+        Y4[Q] = make_float4(u[0], u[1], u[2], u[3]);
+      }
+      const float2 gs = team_sum2(acc, 32);
+      __syncwarp();   // the row is visible to lane 0
+      if (lane == 0) {
+        float head[kMaxM];
+        const float *row = R.X + (size_t)slot * R.d_pad;
+        for (int jj = 0; jj < mh; ++jj) head[jj] = __ldcg(row + jj);
+        dtlz_objectives_t<PROB>(m, gs.x + gs.y, head, f);
+        for (int kk = 0; kk < m; ++kk) R.F[(size_t)kk * 2 * N + slot] = f[kk];
+        have = true;
+      }
+    }
+  }
+  if (have)
+    for (int kk = 0; kk < m; ++kk) atomicMin(&s_z[kk], f2ord(f[kk]));
+  __syncthreads();
+  if (threadIdx.x < m && s_z[threadIdx.x] != 0xFFFFFFFFu)
+    atomicMin(&R.ctl->zkey[threadIdx.x], s_z[threadIdx.x]);
+}
+#define RVEA_REPRO_OP(name, PROB)                                                          \
+  __global__ void __launch_bounds__(kReproThreads) name(const __grid_constant__ BatchDir dir) { \
+    repro_op_body<PROB>(dir);                                                              \
+  }
+RVEA_REPRO_OP(k_repro_op_dtlz1, PROB_DTLZ1)
+RVEA_REPRO_OP(k_repro_op_dtlz2, PROB_DTLZ2)
+RVEA_REPRO_OP(k_repro_op_dtlz3, PROB_DTLZ3)
+RVEA_REPRO_OP(k_repro_op_dtlz4, PROB_DTLZ4)
+#undef RVEA_REPRO_OP
+
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
 // objectives.  DTLZ: x = L + (U-L) u24 from INIT (j/4, i, 0) word j%4.
 // Rollout problem: x = clip(0.1 z), z Box-Muller from INIT (j, i, 0).

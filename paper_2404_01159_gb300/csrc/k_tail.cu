@@ -1,0 +1,535 @@
+// Fused tail of a generation for one run: one persistent launch, one CTA per
+// SM, that takes the children from the reproduction kernel to the next
+// population (Algorithm 2, one loop iteration after X_cross):
+//
+//   A  mutation and evaluation of the children (Appendix B, C / X_mut, and
+//      the DTLZ objectives; only for runs whose reproduction leaves them to a
+//      second kernel, d > 1024), and their share of the ideal point z*
+//      (Algorithm 1 lines 3-4);
+//   -- grid barrier: z* is final --
+//   B  association and APD votes (Algorithm 1 lines 5-15, Eqs. 2, 4): the
+//      exact pruned search, its tables staged in shared memory by TMA while
+//      the reproduction kernel still runs;
+//   -- grid barrier: every vote is in --
+//   C  decode of the per-vector minima into the next slot map (Algorithm 1
+//      line 16), the valid bits, the pool rows the survivors occupy, the
+//      survivors' objective minimum and maximum;
+//   -- grid barrier: the decode is complete --
+//   D  the ascending lists of valid slots (next mating) and free pool rows
+//      (next offspring), from per-CTA counts published in C; the next z*;
+//      on adaptation generations the FP64 rescaling of V (Algorithm 2,
+//      "update reference vectors"); the control block.
+//
+// The arithmetic of every step is that of the separate kernels (k_mutate,
+// k_select_pruned, k_finalize), so the results are the same bit for bit;
+// only the launch boundaries, the last-CTA list building and the per-CTA
+// arrival chain are gone.  The grid barriers wait with a time limit (1 s):
+// a wait that gives up sets ST_TIMEOUT in the status word and its CTA
+// returns, so a broken barrier ends in an error status, never in a hang.
+// Every CTA is resident at once by construction (grid <= SM count, one
+// 1024-thread CTA per SM), and the kernel lets its successor launch only
+// after its last barrier.
+//
+// Data written by another CTA inside this launch is read through L2
+// (__ldcg) after the barrier that orders it.
+#include "eval_steps.cuh"
+#include "grid_steps.cuh"
+
+namespace rvea {
+
+constexpr unsigned long long kBarrierNs = 1000000000ull;   // 1 s
+constexpr int kTailFreeWords = 64;   // pool-row words (32 rows each) per CTA, at most
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long add_release_gpu(unsigned long long *p,
+                                                              unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier over the launch's nb CTAs (all resident).  The arrival
+// counter only grows: every launch adds exactly 3 nb, so an instance's
+// arrivals are the nb values [k nb, (k + 1) nb) and it is complete once the
+// counter reaches (k + 1) nb.  One release-add per CTA, then acquire polls;
+// no reset, so nothing is serialised behind the last arrival.  Returns
+// false, for the whole CTA, when the wait gave up.
+__device__ bool grid_barrier(Ctl *ctl, unsigned nb) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned long long old = add_release_gpu(&ctl->bar, 1ull);
+    const unsigned long long target = (old / nb + 1) * nb;
+    if (ld_acquire_gpu(&ctl->bar) < target) {
+      const unsigned long long t0 = global_ns();
+      for (unsigned it = 1;; ++it) {
+        if (ld_acquire_gpu(&ctl->bar) >= target) break;
+        if ((it & 63u) == 0 && global_ns() - t0 > kBarrierNs) {
+          ok = 0;
+          set_status(ctl, ST_TIMEOUT);
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Phase A: mutation and evaluation of the children (the same draws and
+// operations as k_mutate).  Warp w < kTailMutWarps of CTA b owns the 32
+// children of child-warp cw = w nb + b.  Before the wait for the
+// reproduction kernel (nothing there reads its output): each lane draws its
+// child's site count, the warp lays the sites out in shared memory (Floyd's
+// sampler per child) and draws their magnitudes one site a lane.  After the
+// wait the warp mutates the sites one a lane -- a child with several sites
+// does not hold up the others -- and each lane evaluates its child.  A warp
+// whose sites overflow its list (kTailSites, about 8 times the mean) takes a
+// per-lane path instead.
+constexpr int kTailSites = 256;
+
+struct TailMut {
+  uint32_t j[kTailMutWarps][kTailSites];   // site variable
+  float dg[kTailMutWarps][kTailSites];     // magnitude, then term(new) - term(old)
+  uint8_t own[kTailMutWarps][kTailSites];  // lane of the child
+  int slot[kTailMutWarps][32];
+};
+
+// Per-lane path of a warp whose site list overflowed: the draws again, the
+// mutations one after another; returns the change of the child's g sum.
+template <int PROB, int M>
+__device__ __noinline__ float child_serial(const RunDesc &R, const KeyRun kr, int cd, int t,
+                                           int slot, int k) {
+  const int d = R.d;
+  int js[kMaxSites];
+  uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+  for (int i = 0; i < k; ++i) {
+    const int e = i + 1;
+    if ((e & 3) == 0) w = philox_k((uint32_t)(e >> 2), (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+    const uint32_t J = (uint32_t)(d - k + i);
+    uint32_t r = __umulhi(word(w, e & 3), J + 1u);
+    for (int l = 0; l < i; ++l)
+      if ((uint32_t)js[l] == r) { r = J; break; }
+    js[i] = (int)r;
+  }
+  if (R.rec_sites) {
+    int *const rec = R.rec_sites + (size_t)cd * (1 + kMaxSites);
+    rec[0] = k;
+    for (int i = 0; i < k; ++i) rec[1 + i] = js[i];
+  }
+  float *const row = R.X + (size_t)slot * R.d_pad;
+  float dg = 0.0f;
+  for (int i = 0; i < k; ++i) {
+    const int j = js[i];
+    const float Mm = u24f(philox_k((uint32_t)j, (uint32_t)cd, (uint32_t)t, TAG_MUTMAG, kr).y);
+    const float x = __ldcg(row + j);
+    const float xn = poly_mutate(x, Mm, R.L, R.U, R.eta_m);
+    __stcg(row + j, xn);
+    dg += j >= M - 1 ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f) : 0.0f;
+  }
+  return dg;
+}
+
+// Ascending positions of the set bits of words [w0, w1) (word w from
+// getw(w), bit b = element 32 w + b), written from out[base] on, at most
+// `limit` in total.  One warp.
+template <class GetW>
+__device__ __forceinline__ void warp_compact_by(GetW getw, int w0, int w1, int *out, int base,
+                                                int limit) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int r = w0; r < w1; r += 32) {
+    const int w = r + lane;
+    const uint32_t word = w < w1 ? getw(w) : 0u;
+    const int c = __popc(word);
+    int incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const int at = base + incl - c;
+    const int nw = min(32, w1 - r);
+    for (int i = 0; i < nw; ++i) {
+      const uint32_t wi = __shfl_sync(0xffffffffu, word, i);
+      const int pos = __shfl_sync(0xffffffffu, at, i) + __popc(wi & lt);
+      if (((wi >> lane) & 1u) && pos < limit) out[pos] = 32 * (r + i) + lane;
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// Static shared memory of the kernel, declared once for its three m
+// instances.
+struct TailShared {
+  RunDesc desc;
+  TailMut mut;
+  uint64_t bar;
+  unsigned lo[kMaxM], hi[kMaxM];
+  int red[2][32];
+  uint32_t free_[kTailFreeWords];
+  double rng[kMaxM];
+};
+
+template <int PROB, int M>
+__device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t &s_bar = S.bar;
+  unsigned *const s_lo = S.lo, *const s_hi = S.hi;
+  int (*const s_red)[32] = S.red;
+  TailMut &sm = S.mut;
+  const int N = R.N, n2 = 2 * N, m = R.m, T = R.ntiles;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = gridDim.x, b = blockIdx.x;
+  Ctl *const ctl = R.ctl;
+
+  // ---- prologue: the search tables into shared memory (written by k_tiles,
+  // earlier than the reproduction kernel) ------------------------------------
+  const uint32_t bV = (uint32_t)N * 16, bC = (uint32_t)T * 16, bS = (uint32_t)T * 8;
+  const uint32_t bSr = (bS + 15u) & ~15u;
+  float4 *sV = reinterpret_cast<float4 *>(smem);
+  float4 *sC = reinterpret_cast<float4 *>(smem + bV);
+  float2 *sCS = reinterpret_cast<float2 *>(smem + bV + bC);
+  int2 *sR = reinterpret_cast<int2 *>(smem + bV + bC + bSr);
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
+    tma_load_1d(sV, R.Vt, bV, &s_bar);
+    tma_load_1d(sC, R.tcen, bC, &s_bar);
+    tma_load_1d(sCS, R.tcs, bSr, &s_bar);
+    tma_load_1d(sR, R.trng, bSr, &s_bar);
+  }
+  __syncthreads();
+  const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
+  if (__syncthreads_or(!staged)) {
+    // a copy never arrived: flag it, let the copies land, give up (the other
+    // CTAs' barriers then time out and report the same status)
+    if (tid == 0) {
+      set_status(ctl, ST_TIMEOUT);
+      mbar_wait(&s_bar, 0u, kWaitLimit);
+    }
+    __syncthreads();
+    return;
+  }
+  const float2 csb = tile_bounds(sCS, T);
+  // the generation index and the child slots were written by the previous
+  // generation's tail, which completed before the reproduction kernel (this
+  // grid's predecessor) passed its own wait; read through L2
+  const int t = __ldcg(&ctl->t);
+  const KeyRun kr{R.key0, R.key1};
+  // children are finished here when SBX left them to a second kernel
+  const bool tail_mut = R.team == 32 && R.op == 0 && PROB != PROB_NEURO;
+  // this generation's combined objectives by combined index: the parents
+  // written by the previous generation's decode (when it was this kernel),
+  // the children by phase A below
+  const float *fcur = (tail_mut && __ldcg(&ctl->fcomb_t) == t)
+                          ? R.fcomb + (size_t)(t & 1) * M * n2 : nullptr;
+  const int cw = warp * nb + b, cd0 = 32 * cw, cd = cd0 + lane;
+  const bool mwarp = tail_mut && warp < kTailMutWarps && cd0 < N;
+  int slot = -1, k = 0, off = 0, total = 0;
+  if (mwarp) {
+    if (cd < N) {
+      slot = __ldcg(R.child_slot + (t & 1) * N + cd);
+      if (slot < 0 || slot >= n2) { set_status(ctl, ST_BADINDEX); slot = -1; }
+    }
+    sm.slot[warp][lane] = slot;
+    if (slot >= 0 && R.T_m > 0 && R.T_m < (1u << 24)) {
+      const uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+      const int nthr = R.n_mthr;
+      while (k < nthr && w.x >= R.mthr[k]) ++k;
+    }
+    int incl = k;   // warp prefix of the counts: this child's entries start at off
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    off = incl - k;
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total <= kTailSites) {
+      if (k > 0) {
+        uint32_t *const js = sm.j[warp] + off;
+        uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+        for (int i = 0; i < k; ++i) {
+          const int e = i + 1;
+          if ((e & 3) == 0)
+            w = philox_k((uint32_t)(e >> 2), (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+          const uint32_t J = (uint32_t)(R.d - k + i);
+          uint32_t r = __umulhi(word(w, e & 3), J + 1u);
+          for (int l = 0; l < i; ++l)
+            if (js[l] == r) { r = J; break; }
+          js[i] = r;
+          sm.own[warp][off + i] = (uint8_t)lane;
+        }
+      }
+      if (R.rec_sites && slot >= 0) {
+        int *const rec = R.rec_sites + (size_t)cd * (1 + kMaxSites);
+        rec[0] = R.T_m >= (1u << 24) ? -1 : k;
+        for (int i = 0; i < k; ++i) rec[1 + i] = (int)sm.j[warp][off + i];
+      }
+      __syncwarp();
+      for (int e = lane; e < total; e += 32)   // the magnitudes
+        sm.dg[warp][e] = u24f(philox_k(sm.j[warp][e], (uint32_t)(cd0 + sm.own[warp][e]),
+                                       (uint32_t)t, TAG_MUTMAG, kr).y);
+      __syncwarp();
+    }
+  }
+
+  pdl_wait();   // the reproduction kernel's children
+
+  // ---- A: mutation and evaluation of the children, z* ----------------------
+  if (tid < kMaxM) { s_lo[tid] = 0xFFFFFFFFu; s_hi[tid] = 0u; }
+  if (b == 0) {
+    if (tid < kMaxM) { R.zacc[tid] = 0xFFFFFFFFu; R.zacc[kMaxM + tid] = 0u; }
+    for (int q = tid; q < nb; q += kTailThreads) R.occ_cnt[q] = 0u;
+  }
+  __syncthreads();
+  if (tail_mut) {
+    if (mwarp) {
+      // this child's segment partials and position variables, loaded while
+      // the warp mutates
+      float g = 0.0f, head[M > 1 ? M - 1 : 1];
+      float *const row = slot >= 0 ? R.X + (size_t)slot * R.d_pad : nullptr;
+      if (slot >= 0) {
+        const int S = R.nseg, p = cd < R.P ? cd : cd - R.P;
+        const float *ps = R.psum + (size_t)p * 2 * S + (cd < R.P ? 0 : S);
+#pragma unroll 4
+        for (int q = 0; q < S; ++q) g += __ldcg(ps + q);
+#pragma unroll
+        for (int jj = 0; jj < M - 1; ++jj) head[jj] = __ldcg(row + jj);
+      }
+      float dg = 0.0f;
+      bool head_hit = false;
+      if (total <= kTailSites) {
+        for (int e = lane; e < total; e += 32) {   // the mutations, one site a lane
+          const int o = sm.own[warp][e];
+          const uint32_t j = sm.j[warp][e];
+          float *const px = R.X + (size_t)sm.slot[warp][o] * R.d_pad + j;
+          const float x = __ldcg(px);
+          const float xn = poly_mutate(x, sm.dg[warp][e], R.L, R.U, R.eta_m);
+          __stcg(px, xn);
+          sm.dg[warp][e] = (int)j >= M - 1 ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f)
+                                           : 0.0f;
+        }
+        __syncwarp();   // the mutated rows and term changes are visible to the warp
+        for (int i = 0; i < k; ++i) {
+          dg += sm.dg[warp][off + i];
+          head_hit |= (int)sm.j[warp][off + i] < M - 1;
+        }
+      } else if (slot >= 0) {
+        dg = child_serial<PROB, M>(R, kr, cd, t, slot, k);
+        head_hit = true;
+      }
+      if (slot >= 0) {
+        if (head_hit) {   // a site among x_1..x_{m-1}: read them back, mutated
+#pragma unroll
+          for (int jj = 0; jj < M - 1; ++jj) head[jj] = __ldcg(row + jj);
+        }
+        float f[M];
+        dtlz_objectives_t<PROB>(M, g + dg, head, f);
+        float *const fc = R.fcomb + (size_t)(t & 1) * M * n2 + N + cd;
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) {
+          R.F[(size_t)kk * n2 + slot] = f[kk];
+          fc[(size_t)kk * n2] = f[kk];
+          atomicMin(&s_lo[kk], f2ord(f[kk]));
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < m && s_lo[tid] != 0xFFFFFFFFu) atomicMin(&ctl->zkey[tid], s_lo[tid]);
+  }
+  if (!grid_barrier(ctl, nb)) return;
+  if (tid < kMaxM) s_lo[tid] = 0xFFFFFFFFu;   // for the survivors' minimum in C
+
+  // ---- B: association and APD votes ----------------------------------------
+  {
+    const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
+    float z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = k < m ? ord2f(__ldcg(&ctl->zkey[k])) : 0.f;
+    if (M <= 3 && R.gG > 0 && __ldcg(&ctl->grid_ver) == __ldcg(&ctl->v_ver)) {
+      // the direction grid: one thread per solution
+      float w[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w[k] = k < M ? R.gscale[k] : 1.0f;
+      for (int i = tid * nb + b; i < R.n_comb; i += nb * kTailThreads)
+        grid_assoc<M <= 3 ? M : 3>(R, i, sV, z, w, pen, fcur);
+    } else {
+      const int groups = (R.n_comb + 3) >> 2, gw = warp * nb + b, nw = nb * (kTailThreads / 32);
+      for (int g = gw; g < groups; g += nw) prune_group<M, false>(R, 4 * g, sV, sC, sCS, sR, z, pen, csb);
+    }
+  }
+  if (!grid_barrier(ctl, nb)) return;
+
+  // ---- C: decode of this CTA's vector words --------------------------------
+  // vector words [v0, v1) (32 vectors each) and pool-row words [o0, o1) (32
+  // rows each) belong to this CTA in C and D
+  const int nvw = (N + 31) >> 5, now = (n2 + 31) >> 5;
+  const int pv = (nvw + nb - 1) / nb, po = (now + nb - 1) / nb;
+  const int v0 = min(nvw, b * pv), v1 = min(nvw, v0 + pv);
+  const int o0 = min(now, b * po), o1 = min(now, o0 + po);
+  {
+    const int *cur = R.slotmap + (t & 1) * N;
+    int *nmap = R.slotmap + ((t + 1) & 1) * N;
+    const int *ccur = R.child_slot + (t & 1) * N;
+    int nvalid = 0;
+    float *const fnext = R.fcomb + (size_t)((t + 1) & 1) * M * n2;
+    for (int vw = v0 + warp; vw < v1; vw += kTailThreads / 32) {
+      const int j = 32 * vw + lane;
+      int s = -1, i = -1;
+      if (j < N) {
+        const unsigned long long key = __ldcg(R.best + j);
+        R.best[j] = ~0ull;
+        if (key != ~0ull) {
+          i = (int)(uint32_t)(key & 0xFFFFFFFFull);
+          if (i >= 0 && i < N) s = cur[i];
+          else if (i >= N && i < n2) s = ccur[i - N];
+          if (s < 0 || s >= n2) { set_status(ctl, ST_BADINDEX); s = -1; i = -1; }
+        }
+        nmap[j] = s;
+        R.surv[j] = i;
+        if (s >= 0) {
+          R.otag[s] = t;
+          atomicAdd(&R.occ_cnt[min(nb - 1, (s >> 5) / po)], 1u);
+        }
+      }
+      const uint32_t vmask = __ballot_sync(0xffffffffu, s >= 0);
+      if (lane == 0) R.vbits[vw] = vmask;
+      nvalid += __popc(vmask);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        unsigned lo = 0xFFFFFFFFu, hi = 0u;
+        float fv = __int_as_float(0x7fffffff);   // NaN: an invalid slot of P_{t+1}
+        if (s >= 0) {
+          fv = fcur ? __ldcg(fcur + (size_t)k * n2 + i) : __ldcg(R.F + (size_t)k * n2 + s);
+          lo = hi = f2ord(fv);
+        }
+        if (j < N) fnext[(size_t)k * n2 + j] = fv;
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) { atomicMin(&s_lo[k], lo); atomicMax(&s_hi[k], hi); }
+      }
+    }
+    if (lane == 0) s_red[0][warp] = nvalid;
+  }
+  __syncthreads();
+  if (tid < m && s_lo[tid] != 0xFFFFFFFFu) {
+    atomicMin(&R.zacc[tid], s_lo[tid]);
+    atomicMax(&R.zacc[kMaxM + tid], s_hi[tid]);
+  }
+  if (tid == 0) {
+    int c = 0;
+    for (int w = 0; w < kTailThreads / 32; ++w) c += s_red[0][w];
+    R.vcnt[b] = c;
+  }
+  if (!grid_barrier(ctl, nb)) return;
+
+  // ---- D: lists, next z*, adaptation, control block ------------------------
+  // prefix of the valid slots and of the free rows over the CTAs before this
+  // one, and the totals
+  int pre_v = 0, tot_v = 0, pre_f = 0;
+  {
+    int a = 0, av = 0, af = 0;
+    if (tid < nb) {
+      const int vq = __ldcg(R.vcnt + tid);
+      const int q0 = min(now, tid * po), q1 = min(now, q0 + po);
+      const int rows = max(0, min(n2, 32 * q1) - 32 * q0);
+      const int fq = rows - (int)__ldcg(R.occ_cnt + tid);
+      a = vq;
+      av = tid < b ? vq : 0;
+      af = tid < b ? fq : 0;
+    }
+    a = __reduce_add_sync(0xffffffffu, a);
+    av = __reduce_add_sync(0xffffffffu, av);
+    af = __reduce_add_sync(0xffffffffu, af);
+    __syncthreads();   // s_red reused
+    if (lane == 0) { s_red[0][warp] = a; s_red[1][warp] = av; }
+    __syncthreads();
+    for (int w = 0; w < kTailThreads / 32; ++w) { tot_v += s_red[0][w]; pre_v += s_red[1][w]; }
+    __syncthreads();
+    if (lane == 0) s_red[0][warp] = af;
+    __syncthreads();
+    for (int w = 0; w < kTailThreads / 32; ++w) pre_f += s_red[0][w];
+  }
+  const int K = tot_v;
+  if (warp == 0) {   // ascending valid slots of this CTA's vector words
+    warp_compact_by([&](int w) { return __ldcg(R.vbits + w); }, v0, v1, R.vlist, pre_v, N);
+  } else if (warp == 1) {   // ascending free pool rows of this CTA's row words
+    uint32_t *const s_free = S.free_;
+    for (int w = o0; w < o1; ++w) {
+      const int row = 32 * w + lane;
+      const bool occ = row >= n2 || __ldcg(R.otag + row) == t;
+      const uint32_t fw = __ballot_sync(0xffffffffu, !occ);
+      if (lane == 0) s_free[w - o0] = fw;
+    }
+    __syncwarp();
+    warp_compact_by([&](int w) { return s_free[w - o0]; }, o0, o1,
+                    R.child_slot + ((t + 1) & 1) * N, pre_f, N);
+  }
+  if (b == 0 && tid < m) ctl->zkey[tid] = __ldcg(R.zacc + tid);
+  const bool adapt = (t % R.p_adapt) == 0;
+  if (adapt && K > 0) {
+    // range_k = max - min over the survivors, floored at 1e-12, in FP64
+    double *const s_rng = S.rng;
+    if (tid < m) {
+      const double r = (double)ord2f(__ldcg(R.zacc + kMaxM + tid)) -
+                       (double)ord2f(__ldcg(R.zacc + tid));
+      s_rng[tid] = r < 1e-12 ? 1e-12 : r;
+      if (b == 0) R.vrange[tid] = s_rng[tid];
+    }
+    __syncthreads();
+    const int pj = (N + nb - 1) / nb;
+    const int j0 = min(N, b * pj), j1 = min(N, j0 + pj);
+    for (int jj = j0 + tid; jj < j1; jj += kTailThreads) adapt_row(R, jj, s_rng);
+  }
+  if (b == 0 && tid == 0) {
+    ctl->K = K;
+    ctl->adapted = adapt ? 1 : 0;
+    if (adapt && K > 0) ctl->v_ver += 1;
+    ctl->fin_cnt = 0;
+    ctl->sel_cnt = 0;
+    ctl->fcomb_t = t + 1;
+    ctl->t = t + 1;
+  }
+  pdl_trigger();
+}
+
+// The descriptor is copied into shared memory first: its fields are read in
+// every phase, and after each wait and barrier a global load of them would
+// go back to L2.
+__device__ __forceinline__ void stage_desc(const RunDesc *Rp, RunDesc *sD) {
+  const int *src = reinterpret_cast<const int *>(Rp);
+  int *dst = reinterpret_cast<int *>(sD);
+  for (int q = threadIdx.x; q < (int)(sizeof(RunDesc) / 4); q += blockDim.x) dst[q] = src[q];
+  __syncthreads();
+}
+#define RVEA_TAIL(name, PROB)                                                              \
+  __global__ void __launch_bounds__(kTailThreads, 1) name(const RunDesc *__restrict__ Rp) { \
+    __shared__ __align__(16) TailShared S;                                                 \
+    stage_desc(Rp, &S.desc);                                                               \
+    switch (S.desc.m) {                                                                    \
+      case 2: tail_body<PROB, 2>(S.desc, S); break;                                        \
+      case 3: tail_body<PROB, 3>(S.desc, S); break;                                        \
+      default: tail_body<PROB, 4>(S.desc, S); break;                                       \
+    }                                                                                      \
+  }
+RVEA_TAIL(k_tail_dtlz1, PROB_DTLZ1)
+RVEA_TAIL(k_tail_dtlz2, PROB_DTLZ2)
+RVEA_TAIL(k_tail_dtlz3, PROB_DTLZ3)
+RVEA_TAIL(k_tail_dtlz4, PROB_DTLZ4)
+#undef RVEA_TAIL
+
+}  // namespace rvea

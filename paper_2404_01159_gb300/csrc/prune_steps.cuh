@@ -86,7 +86,7 @@ __device__ __forceinline__ void prune_group(const RunDesc &R, int base, const fl
     float f[4] = {0.f, 0.f, 0.f, 0.f};
     if (slot >= 0) {
 #pragma unroll
-      for (int k = 0; k < M; ++k) f[k] = R.F[(size_t)k * n + slot] - z[k];
+      for (int k = 0; k < M; ++k) f[k] = __ldcg(R.F + (size_t)k * n + slot) - z[k];
     }
     float s2 = f[0] * f[0];
 #pragma unroll

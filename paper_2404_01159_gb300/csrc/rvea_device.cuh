@@ -25,6 +25,9 @@ constexpr int kMaxSites = 32;      // cap of the mutation-site count of one row
 constexpr int kStages = 2;         // staged reproduction: chunks per warp in shared memory
 constexpr int kStageWarpBytes = kStages * 2 * 1024;   // per warp: kStages x 2 parents x 1 KB
 constexpr int kStagedSmem = (kReproThreads / 32) * (kStageWarpBytes + kStages * 8);
+constexpr int kTailThreads = 1024;  // CTA size of the fused tail kernel (one CTA per SM)
+constexpr int kTailMaxCtas = 256;   // its largest grid
+constexpr int kTailMutWarps = 8;    // its warps per CTA that mutate (32 children each)
 
 // Philox counter tags (word 3 of the counter).
 enum : uint32_t {
@@ -51,6 +54,12 @@ struct Ctl {
   int fin_cnt;         // arrival counter of the finalize CTAs
   int sel_cnt;         // work counter of the pruned selection kernel
   unsigned zkey[kMaxM];   // ideal point z*, order-preserving uint encoding
+  int v_ver;           // changes of V so far (adaptation, import)
+  int fcomb_t;         // generation whose combined objectives fcomb holds (0: none)
+  int grid_ver;        // the v_ver the direction grid was built for (-1: none)
+  unsigned long long bar;   // grid barrier of the fused tail kernel: arrivals
+                            // since initialisation (a multiple of its grid
+                            // between launches)
 };
 
 struct RunDesc {
@@ -66,6 +75,9 @@ struct RunDesc {
   int repro_staged;    // 1: parents staged in shared memory by TMA (32-lane teams)
   int sg;              // groups per segment, ceil(G / nseg) <= kLaneGroups * team
   int op_mode;         // 1: stateless selection (identity slots, AoS F)
+  int op;              // reproduction: 0 SBX + polynomial mutation, 1 DE/rand/1/bin, 2 random
+  float de_F;          // DE scale factor
+  uint32_t T_cr;       // DE crossover coin: fires iff (w >> 8) < T_cr
   // parameters
   float L, U, alpha, inv_eta_c1, eta_m;
   uint32_t T_c, T_m;   // 24-bit event thresholds (fires iff k < T)
@@ -91,6 +103,22 @@ struct RunDesc {
   // followed by its sites in draw order
   int *rec_par;        // [2P]
   int *rec_sites;      // [N][1 + kMaxSites]
+  // fused tail kernel (one persistent launch: mutation, association, finalize)
+  int *otag;           // [2N]       generation t whose survivors occupy pool row s (0: none)
+  unsigned *occ_cnt;   // [kTailMaxCtas] occupied pool rows in each CTA's row range
+  int *vcnt;           // [kTailMaxCtas] valid slots in each CTA's vector range
+  unsigned *zacc;      // [2][kMaxM] survivors' minimum / maximum (order-preserving)
+  float *fcomb;        // [2][m][2N] objectives of the combined population by combined
+                       //            index (parents i < N in slot order, NaN when
+                       //            invalid; children N + c), for generation parity t & 1
+  // direction grid of the association (m = 2, 3; gG = 0: none)
+  int gG, gcells, gcap;   // steps per barycentric axis, cells, candidate capacity
+  uint16_t *gcell;     // [gcells][16] record: count, then up to 15 tile-order positions
+                       //              (or, past 15, the offset of the list in gover)
+  int *gcnt;           // [gcells]     candidates of each cell (build)
+  uint16_t *gover;     // [gcap]       candidate lists of the cells with more than 15
+  float *gscale;       // [kMaxM]      w = 1 / range of the grid's V
+  double *vrange;      // [kMaxM]      objective range of the last adaptation (1: none)
   int *blk_cnt;        // [n_comb/256] arrival counters of the selection blocks
   float *V32;          // [N][m4*4]  reference vectors, zero padded
   float *V32lo;        // [N][m]     V64 - V32 rounded to float (null: zero)
@@ -343,6 +371,31 @@ __device__ __forceinline__ float apd_chord(const float *fp, int m, const float *
   }
   const float th = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(w2) / nf));
   return (1.0f + pen * th / gam) * nf;
+}
+
+// Reference-vector adaptation of vector j (Algorithm 2, "update reference
+// vectors"): V_j = V0_j (.) range / |V0_j (.) range| in FP64, written as V64,
+// its float32 copy and the float32 remainder.  Every kernel that adapts calls
+// this one function, and its operations are spelled out (products, sums, a
+// correctly rounded square root and division, no contraction), so the bits do
+// not depend on which kernel adapts.
+__device__ __forceinline__ void adapt_row(const RunDesc &R, int jj, const double *rng) {
+  const int m = R.m;
+  const double *v0p = R.V0 + (size_t)jj * m;
+  double w[kMaxM];
+  double s2 = 0.0;
+  for (int k = 0; k < m; ++k) {
+    w[k] = __dmul_rn(v0p[k], rng[k]);
+    s2 = __dadd_rn(s2, __dmul_rn(w[k], w[k]));
+  }
+  const double nrm = __dsqrt_rn(s2);
+  float *v32 = R.V32 + (size_t)jj * R.m4 * 4;
+  for (int k = 0; k < m; ++k) {
+    const double v = __ddiv_rn(w[k], nrm);
+    R.V64[(size_t)jj * m + k] = v;
+    v32[k] = (float)v;
+    R.V32lo[(size_t)jj * m + k] = (float)__dsub_rn(v, (double)(float)v);
+  }
 }
 
 // Programmatic dependent launch.  The kernels of a generation are launched

@@ -48,6 +48,7 @@ class Run:
                  eta_c: float = 20.0, eta_m: float = 20.0, p_c: float = 1.0,
                  p_m: float = 1.0, lower: Optional[float] = None,
                  upper: Optional[float] = None, seed: int = 0, neuro=None,
+                 reproduction: int = 0, de_F: float = 0.5, de_CR: float = 0.9,
                  device=None, stream=None):
         self.device = torch.device("cuda" if device is None else device)
         if lower is None:
@@ -58,7 +59,7 @@ class Run:
         self.problem, self.t_max = problem, t_max
         L = lib()
         cfg = Config(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
-                     lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None)
+                     lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None, reproduction, de_F, de_CR)
         self._neuro_keep = None
         if neuro is not None:
             A = np.ascontiguousarray(neuro["A"], dtype=np.float64)

@@ -36,7 +36,8 @@ def test_every_plan_gives_the_same_bits(orc, shape):
     p = params(orc, m, d, N, H, prob, t_max=40, seed=9)   # adapts every 4th generation
     ref = make_run(p)
     base = get_plan(ref)
-    modes = [(0, 4), (0, 8), (0, 16)] + ([(1, 8), (2, 8)] if base["sel_mode"] > 0 else [])
+    modes = [(0, 4), (0, 8), (0, 16)] + ([(1, 8), (2, 8)] if base["sel_mode"] > 0 else []) + \
+        ([(3, 8)] if base["sel_mode"] == 3 else [])
     staged = [0, 1] if d > 1024 else [0]
     ref.step(10)
     for (mode, per_sm), st in itertools.product(modes, staged):
@@ -109,11 +110,18 @@ def test_launch_counts(orc):
     evaluation when d > 1024], selection, finalize, [gamma and the tile table
     when it adapts]; a batched generation counts the kernel nodes of its
     graph."""
-    from paper_2404_01159_gb300 import Batch
+    from paper_2404_01159_gb300 import Batch, get_plan, set_plan
     big = make_run(params(orc, 3, 2500, 1275, 49, 1, t_max=40, seed=4))
     small = make_run(params(orc, 3, 12, 105, 13, 0, t_max=40, seed=5))
+    # alone, the pruned-search run starts in the fused tail: reproduction + tail;
+    # an adapting generation adds gamma, the tile table and the direction grid
+    # (scale, count, scan, fill)
+    assert get_plan(big)["sel_mode"] == 3
+    assert big.launches_per_generation(False) == 2
+    assert big.launches_per_generation(True) == 2 + 1 + 1 + 4
+    set_plan(big, 1, 8, 1)
     assert big.launches_per_generation(False) == 4
-    assert big.launches_per_generation(True) in (5, 6)
+    assert big.launches_per_generation(True) == 4 + 1 + 1 + 4
     assert small.launches_per_generation(False) == 3
     assert small.launches_per_generation(True) in (4, 5)
     b = Batch([big, small])

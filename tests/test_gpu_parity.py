@@ -88,12 +88,23 @@ def test_teacher_forced_mutation_rates(orc, shape, p_m):
     _teacher_forced(orc, shape, 3, p_m=p_m)
 
 
+# The extensibility experiment's operators in place of SBX and mutation
+# (Sec. 4.4): DE/rand/1/bin (op 1) and random reproduction (op 2), on the
+# small and staged sizes, one run in the fused tail (N = 1275).
+@pytest.mark.parametrize("shape,op", [((3, 12, 105, 13, 0), 1), ((3, 1001, 210, 19, 1), 1),
+                                      ((3, 2500, 1275, 49, 1), 1), ((10, 30, 220, 3, 0), 1),
+                                      ((2, 30, 100, 99, 0), 2), ((3, 1500, 105, 13, 3), 2)])
+def test_teacher_forced_other_operators(orc, shape, op):
+    _teacher_forced(orc, shape, 6, op=op)
+
+
 def _teacher_forced(orc, shape, gens, **kw):
     m, d, N, H, prob = shape
     p = params(orc, m, d, N, H, prob, t_max=40, seed=5, **kw)   # adapts every 4th gen
     V0 = orc.lattice_unit(orc.lattice(m, H))
     run = make_run(p)
-    run.record_draws(True)
+    if p.op == 0:
+        run.record_draws(True)
     for gen in range(gens):
         st = run.export_state()
         ost = _state_to_oracle(orc, st)
@@ -105,8 +116,10 @@ def _teacher_forced(orc, shape, gens, **kw):
         gx, gf = run.offspring()
         ga, gsurv = run.last_selection()
         gx, gf = gx.cpu().numpy(), gf.cpu().numpy()
-        # mating indices and mutation masks: bit-exact
-        assert_draws(orc, p, t, run, out["parents"])
+        if p.op == 0:   # mating indices and mutation masks: bit-exact
+            assert_draws(orc, p, t, run, out["parents"])
+        if p.op == 2:   # random reproduction: u24 on the box, exact in float32
+            assert np.array_equal(gx.astype(np.float64), out["Xchild"])
         assert_children(gx, out["Xchild"], p.L, p.U)
         # float32 objectives of the same decision vectors: 1e-5 relative
         assert_objectives(gf, orc.evaluate(p, gx.astype(np.float64), t))

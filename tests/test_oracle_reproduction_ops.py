@@ -124,3 +124,23 @@ def test_de_offspring_tiny_valid_lists(orc, K):
     assert np.isfinite(U).all() and U.min() >= 0 and U.max() <= 1
     if K == 1:
         assert (U == X[1]).all()
+
+
+@pytest.mark.parametrize("op", [1, 2])
+def test_generation_uses_the_operator(orc, op):
+    """A generation with the DE (op 1) or random (op 2) operator makes its
+    offspring with that operator (the same rows as the operator called alone
+    on the generation's population and valid list), evaluates them and
+    selects as the SBX generation does."""
+    p = orc.make_params(m=3, d=9, N=105, H=13, problem=orc.DTLZ1, t_max=20, seed=4, op=op,
+                        de_F=0.7, de_CR=0.6)
+    V0, st = orc.initial_state(p)
+    st.valid[[3, 17, 40]] = 0
+    X, vlist = st.X.copy(), np.nonzero(st.valid)[0]
+    t = st.t
+    out = orc.generation(p, V0, st)
+    want = orc.de_offspring(p, t, X, vlist, 0.7, 0.6) if op == 1 else orc.random_offspring(p, t)
+    assert np.array_equal(out["Xchild"], want)
+    assert np.array_equal(out["Fchild"], orc.evaluate(p, want, t))
+    assert (out["parents"] == -1).all()
+    assert (out["survivor"] >= -1).all() and (np.bincount(out["survivor"][out["survivor"] >= 0]) <= 1).all()
