@@ -497,7 +497,7 @@ def main_serve(args, rank, world, local, emit=True, rate=None, seconds=None, dra
         st = srv.step()
         torch.cuda.current_stream().synchronize()
         steps += 1
-        live_sum += st["live"] + st["admitted"]
+        live_sum += st["live"]
         tdone = time.perf_counter() - t0
         for rid in srv.poll():
             srv.fetch(rid)
@@ -583,6 +583,91 @@ def sub_serve(args, local, rates=(50.0, 200.0), seconds=8.0, drain=40.0):
     return out
 
 
+SWEEPS = {
+    # the paper's speed sweeps (Sec. 4.1): population sizes 2^5 .. 2^14 at
+    # d = 100, and dimensions 2^9 .. 2^18 at n = 100; DTLZ1, m = 3, 100
+    # generations.  A size that is not a lattice size runs on the largest
+    # Das-Dennis lattice with at most that many points (rvea_lattice_for).
+    "sweep_pop_d100": dict(axis="n", points=[2 ** k for k in range(5, 15)], d=100, n=None),
+    "sweep_dim_n100": dict(axis="d", points=[2 ** k for k in range(9, 19)], d=None, n=100),
+}
+
+
+def main_sweep(args, rank, world, local, name):
+    """One line for a whole sweep: per point the GPU time per generation
+    (CUDA events around 100 generations after a warm-up), achieved bytes per
+    second of the reproduction against the HBM copy rate, and the FP64
+    oracle's time per generation on the host cores over a bounded sample."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2404_01159_gb300 import Run, lattice_for, lattice_size
+    sw = SWEEPS[name]
+    hbm_peak, peak_kind = peaks()
+    K, W = max(args.steps, 100), max(3, args.warmup)
+    cores = os.cpu_count() or 1
+    pts, cpu_left = [], args.cpu_seconds
+    for x in sw["points"]:
+        n = x if sw["axis"] == "n" else sw["n"]
+        d = x if sw["axis"] == "d" else sw["d"]
+        H = lattice_for(3, n)
+        N = lattice_size(3, H)
+        kw = dict(m=3, d=d, N=N, H=H, problem=1, t_max=100, **COMMON)
+        run = Run(seed=11, **kw)
+        run.step(W)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run.step(K)
+        e1.record()
+        e1.synchronize()
+        run.sync_status()
+        ms = e0.elapsed_time(e1) / K
+        wl = dict(m=3, d=d, N=N)
+        gbs = repro_bytes(wl) / (ms * 1e-3) / 1e9
+        pt = {"n_requested": n, "N": N, "H": H, "d": d, "ms_per_generation": ms,
+              "generations_per_s": 1e3 / ms, "whole_generation_gbs": gbs,
+              "whole_generation_frac": gbs / hbm_peak}
+        del run
+        if world == 1 and not args.no_cpu_baseline and cpu_left > 0:
+            from oracle import oracle as orc
+            orc.set_threads(cores)
+            p = orc.make_params(m=3, d=d, N=N, H=H, problem=1, t_max=100, seed=11, **COMMON)
+            V0, st = orc.initial_state(p)
+            t0, g = time.perf_counter(), 0
+            while g < 3 and (g == 0 or time.perf_counter() - t0 < 2.0):
+                orc.generation(p, V0, st)
+                g += 1
+            dt = (time.perf_counter() - t0) / g
+            cpu_left -= time.perf_counter() - t0
+            pt["oracle_s_per_generation"] = dt
+            pt["gpu_over_oracle"] = dt / (ms * 1e-3)
+        pts.append(pt)
+    if rank != 0:
+        return
+    last = pts[-1]
+    line = {
+        "metric": METRIC, "value": last["generations_per_s"], "unit": "generations/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": last["ms_per_generation"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Philox initial population, closed-form DTLZ1)",
+        "config": {"workload": name, "axis": sw["axis"], "m": 3, "problem": "DTLZ1",
+                   "generations_timed": K, **COMMON,
+                   "l2": "no flush between generations (the small points fit in L2; "
+                         "their throughput is launch- and latency-bound, as in the paper)"},
+        "points": pts,
+        "roofline": {"kernel": "whole generation at the last point", "bound": "hbm",
+                     "achieved": last["whole_generation_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                     "frac": last["whole_generation_frac"], "peak_kind": peak_kind,
+                     "traffic": None},
+        "cpu_baseline": {"kind": "oracle", "cores": cores,
+                         "sample": "up to 3 FP64 oracle generations per point, bounded"},
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batched(insts, seconds=20.0):
     """The FP64 oracle on the host cores over a bounded sample of the same
     runs: one generation each of as many runs (in order) as fit in
@@ -613,7 +698,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dtlz1_m3_d5000_N9870",
-                    choices=sorted(WORKLOADS) + [BATCHED, SERVE, NEURO])
+                    choices=sorted(WORKLOADS) + [BATCHED, SERVE, NEURO] + sorted(SWEEPS))
     ap.add_argument("--serve-rate", type=float, default=200.0, help="requests per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window")
     ap.add_argument("--serve-drain-seconds", type=float, default=60.0,
@@ -633,6 +718,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload in SWEEPS:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle arm times the single-run workload; the sweep line "
+                              "carries the oracle's time per point"}))
+            return
+        main_sweep(args, rank, world, local, args.workload)
+        return
     if args.workload == NEURO:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":

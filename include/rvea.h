@@ -115,6 +115,14 @@ typedef enum {
     RVEA_REPRO_RANDOM = 2
 } rvea_reproduction;
 
+/* Lattice divisions H for a requested population size n that need not be a
+ * lattice size (the speed sweeps of Sec. 4.1 use n = 2^5 .. 2^14 and n =
+ * 100): the largest H with C(H+m-1, m-1) <= n, so that the reference
+ * vectors are the largest Das-Dennis lattice with at most n points -- what a
+ * uniform-point generator gives -- and the run's N is that lattice's size.
+ * -1 if m < 2 or even H = 1 has more than n points.  Host only. */
+int rvea_lattice_for(int m, int n);
+
 /* Bytes of device workspace a run of this shape needs (0 if invalid).
  * DTLZ problems only; the rollout problem adds its noise table and dynamics:
  * use rvea_workspace_bytes_ex. */
@@ -393,15 +401,20 @@ rvea_status rvea_select_noalloc(int m, int n, const float *F, const uint8_t *val
 /* ---- serving loop (continuous batching) ---------------------------------
  * Not in the paper: a request loop over independent runs.  Requests (a run
  * configuration and a generation budget) queue on the host.  Each
- * rvea_server_step first admits queued requests, in arrival order, while
- * their workspaces fit the caller's device arena (the HBM budget) and fewer
- * than max_live runs are live -- admission initialises the run on the
- * device and, with autotune != 0, picks its kernel variants (rvea_autotune,
- * cached per shape) -- and then enqueues one generation of every live run,
- * packed into batched launches (rvea_step_batch, 320 runs each).  A run
- * whose budget is spent leaves the batch; its state stays in the arena until
- * rvea_server_fetch copies the result out and frees the memory.  Every
- * run's result is the bits it gets stepped alone.  Not thread-safe. */
+ * rvea_server_step first enqueues one generation of every live run, packed
+ * into batched launches (rvea_step_batch, 320 runs each), on the caller's
+ * stream; runs whose budget is spent leave the batch.  Then, while the GPU
+ * works on that step, it admits queued requests whose workspaces fit the
+ * caller's device arena (the HBM budget) while fewer than max_live runs are
+ * live: in arrival order, and past a head request that does not fit yet
+ * (backfill, looking at up to 64 requests) unless that head has been passed
+ * over for 32 steps, when admission waits for the arena to drain for it.
+ * Admission initialises the run and, with autotune != 0, picks its kernel
+ * variants (rvea_autotune, cached per shape), on a stream of the server's
+ * own; the next step's launches wait for that work on the device.  A
+ * finished run's state stays in the arena until rvea_server_fetch copies
+ * the result out and frees the memory.  Every run's result is the bits it
+ * gets stepped alone.  Not thread-safe. */
 typedef struct rvea_server rvea_server;
 typedef struct {
     int live;             /* runs in the batch after this step            */
@@ -425,13 +438,13 @@ rvea_status rvea_server_create(void *dev_arena, size_t arena_bytes, int max_live
 rvea_status rvea_server_submit(rvea_server *srv, const rvea_config *cfg, int generations,
                                int64_t *id_out);
 
-/* Admission, then one generation of every live run, on `cuda_stream`.
- * Admission synchronises the stream (initialisation uploads).  stats may be
- * NULL.  A request whose admission fails (initialisation or tuning returns
- * an error) ends there: rvea_server_poll reports its id like a finished
- * one and rvea_server_fetch returns its error; the step goes on with the
- * other requests.  The step's own return value reports the batched
- * generations only. */
+/* One generation of every live run on `cuda_stream`, then admission (see
+ * above; it synchronises the server's own stream, not cuda_stream).  stats
+ * may be NULL; stats->live counts the runs after admission.  A request whose
+ * admission fails (initialisation or tuning returns an error) ends there:
+ * rvea_server_poll reports its id like a finished one and rvea_server_fetch
+ * returns its error; the step goes on with the other requests.  The step's
+ * own return value reports the batched generations and the stream wiring. */
 rvea_status rvea_server_step(rvea_server *srv, void *cuda_stream, rvea_server_stats *stats);
 
 /* Ids of runs whose budget was spent since the last poll (up to cap); their

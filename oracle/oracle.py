@@ -65,6 +65,8 @@ def lib():
         L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
         L.orc_lattice_count.argtypes = [C.c_int32, C.c_int32]
         L.orc_lattice_count.restype = C.c_int64
+        L.orc_lattice_for.argtypes = [C.c_int32, C.c_int32]
+        L.orc_lattice_for.restype = C.c_int32
         L.orc_lattice.argtypes = [C.c_int32, C.c_int32, C.c_int32, i32]
         L.orc_lattice.restype = C.c_int32
         L.orc_lattice_unit.argtypes = [C.c_int32, C.c_int32, i32, f64]
@@ -127,6 +129,12 @@ def make_params(m, d, N, H, problem=DTLZ2, t_max=100, alpha=2.0, f_r=0.1,
 
 def lattice_count(m, H) -> int:
     return int(lib().orc_lattice_count(m, H))
+
+
+def lattice_for(m, n) -> int:
+    """H of the largest lattice with at most n points (the population of a
+    run asked for n, which need not be a lattice size), -1 if none."""
+    return int(lib().orc_lattice_for(m, n))
 
 
 def lattice(m, H):

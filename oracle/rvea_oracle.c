@@ -99,6 +99,19 @@ int64_t orc_lattice_count(int32_t m, int32_t H)
     return c;
 }
 
+/* Population size n that is not a lattice size (the speed sweeps of Sec.
+ * 4.1 use n = 2^5 .. 2^14): the reference vectors are the largest Das-Dennis
+ * lattice with at most n points, as a uniform-point generator gives them,
+ * and the population is that lattice's size.  Returns its H (>= 1), or -1
+ * when even H = 1 has more than n points. */
+int32_t orc_lattice_for(int32_t m, int32_t n)
+{
+    if (m < 2 || orc_lattice_count(m, 1) > n) return -1;
+    int32_t H = 1;
+    while (orc_lattice_count(m, H + 1) <= n) ++H;
+    return H;
+}
+
 static int32_t lattice_rec(int32_t m, int32_t pos, int32_t left, int32_t *cur,
                            int32_t *K, int32_t N, int32_t row)
 {

@@ -64,6 +64,7 @@ typedef struct {
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
 int64_t orc_lattice_count(int32_t m, int32_t H);
+int32_t orc_lattice_for(int32_t m, int32_t n);
 int32_t orc_lattice(int32_t m, int32_t H, int32_t N, int32_t *K);
 void orc_lattice_unit(int32_t m, int32_t N, const int32_t *K, double *V0);
 void orc_gamma(int32_t m, int32_t r, const double *V, double *gamma);

@@ -2,9 +2,9 @@
 evaluation and reference-vector guided selection per call, in hand-written
 CUDA behind a small C ABI (include/rvea.h)."""
 from .rvea import (DTLZ1_LINEAR, DTLZ2_SPHERE, DTLZ3_SPHERE, DTLZ4_SPHERE, NEURO_LINEAR, Batch,
-                   Run, RveaError, Server, autotune, gamma, get_plan, lattice_size, select,
+                   Run, RveaError, Server, autotune, gamma, get_plan, lattice_for, lattice_size, select,
                    set_plan, step_batch, workspace_bytes)
 
 __all__ = ["Run", "Batch", "Server", "RveaError", "step_batch", "autotune", "get_plan", "set_plan",
-           "select", "gamma", "workspace_bytes", "lattice_size", "DTLZ2_SPHERE", "DTLZ1_LINEAR",
+           "select", "gamma", "workspace_bytes", "lattice_size", "lattice_for", "DTLZ2_SPHERE", "DTLZ1_LINEAR",
            "NEURO_LINEAR", "DTLZ3_SPHERE", "DTLZ4_SPHERE"]

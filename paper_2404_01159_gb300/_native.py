@@ -80,6 +80,8 @@ def lib():
         L = C.CDLL(_build.LIB)
         vp, sz, i32, u64, dbl, flt = C.c_void_p, C.c_size_t, C.c_int, C.c_uint64, C.c_double, C.c_float
         run_pp = C.POINTER(C.c_void_p)
+        L.rvea_lattice_for.argtypes = [i32, i32]
+        L.rvea_lattice_for.restype = i32
         L.rvea_workspace_bytes.argtypes = [i32, i32, i32]
         L.rvea_workspace_bytes.restype = sz
         L.rvea_workspace_bytes_ex.argtypes = [C.POINTER(Config)]

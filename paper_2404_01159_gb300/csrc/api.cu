@@ -898,6 +898,13 @@ size_t rvea_workspace_bytes_ex(const rvea_config *cfg) {
   return make_layout(s, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0).total;
 }
 
+int rvea_lattice_for(int m, int n) {
+  if (m < 2 || m > kMaxM || lattice_size(m, 1) > (int64_t)n) return -1;
+  int H = 1;
+  while (lattice_size(m, H + 1) <= (int64_t)n) ++H;
+  return H;
+}
+
 size_t rvea_workspace_bytes(int m, int d, int N) {
   if (m < 2 || m > kMaxM || d < m || d > (1 << 22) || N < 2 || N > 32768) return 0;
   const Shape s = make_shape(m, d, N);

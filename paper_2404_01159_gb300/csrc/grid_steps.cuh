@@ -126,4 +126,119 @@ __device__ __forceinline__ void grid_assoc(const RunDesc &R, int i, const float4
   atomicMin(&R.best[bj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
 }
 
+// The same association with eight lanes per solution (lanes 8g .. 8g+7 of a
+// warp take solution i of group g; every lane of the warp must call it):
+// each lane scans two of the cell's candidates and fetches, for the better
+// one, the float remainder of the vector and gamma, so that after the group
+// reduces (larger dot, then smaller index) the lane holding the winner
+// computes the APD and votes without another round trip.
+template <int M>
+__device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float4 *sV,
+                                            const float *z, const float *w, float pen,
+                                            const float *fc) {
+  const int N = R.N, n = R.n_comb, lane = threadIdx.x & 31, sub = lane & 7, gb = lane & 24;
+  const bool act = i < n;
+  float f[4] = {0.f, 0.f, 0.f, 0.f};
+  bool valid = false;
+  if (act) {
+    if (fc) {
+      float F0[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) F0[k] = __ldcg(fc + (size_t)k * n + i);
+      valid = F0[0] == F0[0];   // NaN: an invalid parent
+#pragma unroll
+      for (int k = 0; k < M; ++k) f[k] = F0[k] - z[k];
+    } else {
+      const int par = R.ctl->t & 1;
+      const int slot = i < N ? R.slotmap[par * N + i] : R.child_slot[par * N + (i - N)];
+      valid = slot >= 0;
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < M; ++k) f[k] = __ldcg(R.F + (size_t)k * n + slot) - z[k];
+      }
+    }
+  }
+  float s2 = f[0] * f[0];
+#pragma unroll
+  for (int k = 1; k < M; ++k) s2 = fmaf(f[k], f[k], s2);
+  const bool live = act && valid && sqrtf(s2) > 0.0f;
+  // the cell record, one 4-byte word per lane of the group
+  uint32_t wd = 0;
+  if (live) {
+    const int cell = grid_cell<M>(f, w, R.gG);
+    wd = __ldg(reinterpret_cast<const uint32_t *>(R.gcell + (size_t)cell * kGridRec) + sub);
+  }
+  // every lane takes part in every shuffle (groups of one warp may take
+  // different branches below, which hold no warp-wide operation)
+  const uint32_t w0 = __shfl_sync(0xffffffffu, wd, gb);
+  const uint32_t w1 = __shfl_sync(0xffffffffu, wd, gb | 1);
+  uint32_t we[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)   // the word of element e + 1, e = sub + 8 h (e <= 14 used)
+    we[h] = __shfl_sync(0xffffffffu, wd, gb | min(7, (sub + 8 * h + 1) >> 1));
+  const int cnt = live ? (int)(w0 & 0xFFFFu) : 0;
+  float best = -INFINITY;
+  int bj = 0x7FFFFFFF, bq = -1;
+  if (cnt <= kGridInline) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = sub + 8 * h;   // element e + 1 of the record
+      if (e < cnt) {
+        const int q = (int)((we[h] >> (16 * ((e + 1) & 1))) & 0xFFFFu);
+        const float4 v = sV[q];
+        const int j = __float_as_int(v.w);
+        const float dt = pdot<M>(f, v);
+        if (dt > best || (dt == best && j < bj)) { best = dt; bj = j; bq = q; }
+      }
+    }
+  } else {
+    const int at = (int)((w0 >> 16) | ((w1 & 0xFFFFu) << 16));
+    for (int e = sub; e < cnt; e += 8) {
+      const int q = R.gover[at + e];
+      const float4 v = sV[q];
+      const int j = __float_as_int(v.w);
+      const float dt = pdot<M>(f, v);
+      if (dt > best || (dt == best && j < bj)) { best = dt; bj = j; bq = q; }
+    }
+  }
+  // the remainder and gamma of this lane's best, fetched before the reduction
+  float lo[4] = {0.f, 0.f, 0.f, 0.f}, gam = 1.0f;
+  if (bq >= 0 && bj < N) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) lo[k] = __ldg(R.V32lo + (size_t)bj * M + k);
+    gam = __ldg(R.gamma32 + bj);
+  }
+  float gbest = best;
+  int gbj = bj;
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, gbest, off);
+    const int oj = __shfl_xor_sync(0xffffffffu, gbj, off);
+    if (od > gbest || (od == gbest && oj < gbj)) { gbest = od; gbj = oj; }
+  }
+  if (!act) return;
+  if (!valid) {
+    if (sub == 0) R.assoc[i] = -1;
+    return;
+  }
+  if (!live) {   // f' = 0: every dot is +0, the full scan keeps vector 0; APD = 0
+    if (sub == 0) {
+      R.assoc[i] = 0;
+      atomicMin(&R.best[0], (unsigned long long)(uint32_t)i);
+    }
+    return;
+  }
+  if (gbj < 0 || gbj >= N) {
+    if (sub == 0) set_status(R.ctl, ST_BADINDEX);
+    return;
+  }
+  if (bq >= 0 && bj == gbj) {   // the lane that holds the winner
+    const float4 v = sV[bq];
+    const float hi[4] = {v.x, v.y, v.z, 0.0f};
+    const float apd = apd_chord(f, M, hi, lo, gam, pen);
+    R.assoc[i] = gbj;
+    atomicMin(&R.best[gbj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
+  }
+}
+
 }  // namespace rvea

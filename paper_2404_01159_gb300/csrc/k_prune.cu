@@ -51,9 +51,11 @@ __global__ void __launch_bounds__(kPruneThreads, 1) k_select_pruned(const RunDes
     for (int k = 0; k < 4; ++k) z[k] = k < R.m ? ord2f(R.ctl->zkey[k]) : 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) w[k] = k < R.m ? R.gscale[k] : 1.0f;
-    for (int i = threadIdx.x * gridDim.x + blockIdx.x; i < R.n_comb; i += gridDim.x * blockDim.x) {
-      if (R.m == 2) grid_assoc<2>(R, i, sV, z, w, pen, nullptr);
-      else grid_assoc<3>(R, i, sV, z, w, pen, nullptr);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = warp * gridDim.x + blockIdx.x, nw = gridDim.x * (blockDim.x >> 5);
+    for (int g = gw; 4 * g < R.n_comb; g += nw) {
+      if (R.m == 2) grid_assoc8<2>(R, 4 * g + (lane >> 3), sV, z, w, pen, nullptr);
+      else grid_assoc8<3>(R, 4 * g + (lane >> 3), sV, z, w, pen, nullptr);
     }
     return;
   }

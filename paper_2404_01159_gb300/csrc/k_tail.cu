@@ -365,8 +365,10 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
       float w[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) w[k] = k < M ? R.gscale[k] : 1.0f;
-      for (int i = tid * nb + b; i < R.n_comb; i += nb * kTailThreads)
-        grid_assoc<M <= 3 ? M : 3>(R, i, sV, z, w, pen, fcur);
+      // eight lanes per solution, groups of four solutions spread over the CTAs
+      const int gw = warp * nb + b, nw = nb * (kTailThreads / 32);
+      for (int g = gw; 4 * g < R.n_comb; g += nw)
+        grid_assoc8<M <= 3 ? M : 3>(R, 4 * g + (lane >> 3), sV, z, w, pen, fcur);
     } else {
       const int groups = (R.n_comb + 3) >> 2, gw = warp * nb + b, nw = nb * (kTailThreads / 32);
       for (int g = gw; g < groups; g += nw) prune_group<M, false>(R, 4 * g, sV, sC, sCS, sR, z, pen, csb);
@@ -440,30 +442,26 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   // ---- D: lists, next z*, adaptation, control block ------------------------
   // prefix of the valid slots and of the free rows over the CTAs before this
   // one, and the totals
-  int pre_v = 0, tot_v = 0, pre_f = 0;
-  {
+  int pre_v, tot_v, pre_f;
+  if (warp == 0) {   // one warp reads the nb counts, the others wait
     int a = 0, av = 0, af = 0;
-    if (tid < nb) {
-      const int vq = __ldcg(R.vcnt + tid);
-      const int q0 = min(now, tid * po), q1 = min(now, q0 + po);
+    for (int q = lane; q < nb; q += 32) {
+      const int vq = __ldcg(R.vcnt + q);
+      const int q0 = min(now, q * po), q1 = min(now, q0 + po);
       const int rows = max(0, min(n2, 32 * q1) - 32 * q0);
-      const int fq = rows - (int)__ldcg(R.occ_cnt + tid);
-      a = vq;
-      av = tid < b ? vq : 0;
-      af = tid < b ? fq : 0;
+      const int fq = rows - (int)__ldcg(R.occ_cnt + q);
+      a += vq;
+      if (q < b) { av += vq; af += fq; }
     }
     a = __reduce_add_sync(0xffffffffu, a);
     av = __reduce_add_sync(0xffffffffu, av);
     af = __reduce_add_sync(0xffffffffu, af);
-    __syncthreads();   // s_red reused
-    if (lane == 0) { s_red[0][warp] = a; s_red[1][warp] = av; }
-    __syncthreads();
-    for (int w = 0; w < kTailThreads / 32; ++w) { tot_v += s_red[0][w]; pre_v += s_red[1][w]; }
-    __syncthreads();
-    if (lane == 0) s_red[0][warp] = af;
-    __syncthreads();
-    for (int w = 0; w < kTailThreads / 32; ++w) pre_f += s_red[0][w];
+    if (lane == 0) { s_red[1][0] = a; s_red[1][1] = av; s_red[1][2] = af; }
   }
+  __syncthreads();
+  tot_v = s_red[1][0];
+  pre_v = s_red[1][1];
+  pre_f = s_red[1][2];
   const int K = tot_v;
   if (warp == 0) {   // ascending valid slots of this CTA's vector words
     warp_compact_by([&](int w) { return __ldcg(R.vbits + w); }, v0, v1, R.vlist, pre_v, N);

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <new>
 #include <vector>
@@ -92,14 +93,22 @@ struct rvea_server {
   int max_live = 0;
   int tune = 1;
   int64_t next_id = 1;
-  std::deque<Request> queue;
+  std::list<Request> queue;
   std::vector<Live> live;
   std::map<int64_t, Live> done;        // budget spent, result not fetched yet
   std::map<int64_t, rvea_status> failed;   // admission failed, error not fetched yet
   std::vector<int64_t> done_unpolled;
   long long gens_run = 0;
+  cudaStream_t init_stream = nullptr;   // admissions' initialisation and tuning
+  cudaEvent_t init_done = nullptr;      // the last admission's work, for the step stream
+  int head_skips = 0;                   // steps the queue's head has been passed over
   explicit rvea_server(size_t bytes) : arena(bytes) {}
 };
+
+namespace {
+constexpr int kBackfillLookahead = 64;   // queued requests an admission round looks at
+constexpr int kHeadSkipsMax = 32;        // steps a waiting head can be passed over
+}  // namespace
 
 extern "C" {
 
@@ -138,37 +147,16 @@ rvea_status rvea_server_submit(rvea_server *s, const rvea_config *cfg, int gener
 rvea_status rvea_server_step(rvea_server *s, void *cuda_stream, rvea_server_stats *stats) {
   if (!s) return RVEA_ERR_ARG;
   const rvea::NvtxRange nr("rvea server step", (int64_t)s->live.size());
-  // admission, in arrival order, while the head of the queue fits
-  int admitted = 0;
-  while (!s->queue.empty() && (int)s->live.size() < s->max_live) {
-    const Request q = s->queue.front();
-    const size_t bytes = rvea_workspace_bytes_ex(&q.cfg);
-    const size_t off = s->arena.alloc(bytes);
-    if (off == SIZE_MAX) break;
-    rvea_run *run = nullptr;
-    rvea_status st = rvea_init_ex(&q.cfg, s->arena_base + off, bytes, cuda_stream, &run);
-    if (st == RVEA_OK && s->tune) st = rvea_autotune(run, cuda_stream, 1, nullptr);
-    if (st != RVEA_OK) {
-      // the request ends here: poll reports its id, fetch returns this error
-      if (run) rvea_free(run);
-      s->arena.release(off, bytes);
-      s->failed[q.id] = st;
-      s->done_unpolled.push_back(q.id);
-      s->queue.pop_front();
-      continue;
-    }
-    s->live.push_back(Live{q.id, run, off, bytes, q.generations});
-    s->queue.pop_front();
-    ++admitted;
-  }
-  // one generation of every live run
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // one generation of every live run, enqueued first: the GPU works on it
+  // while the host admits new requests below
   std::vector<rvea_run *> runs;
   runs.reserve(s->live.size());
   for (const Live &l : s->live) runs.push_back(l.run);
   for (size_t a = 0; a < runs.size(); a += kBatchMax) {
     const int n = (int)std::min<size_t>(kBatchMax, runs.size() - a);
-    const rvea_status st = rvea_step_batch(runs.data() + a, n, cuda_stream);
-    if (st != RVEA_OK) return st;
+    const rvea_status sr = rvea_step_batch(runs.data() + a, n, cuda_stream);
+    if (sr != RVEA_OK) return sr;
   }
   s->gens_run += (long long)runs.size();
   // runs whose budget is spent leave the batch
@@ -183,6 +171,66 @@ rvea_status rvea_server_step(rvea_server *s, void *cuda_stream, rvea_server_stat
     }
   }
   s->live.swap(keep);
+  // admission on the server's own stream (initialisation and tuning
+  // synchronise that stream, not the step's): in arrival order, and past a
+  // head that does not fit yet (backfill) unless the head has waited
+  // kHeadSkipsMax steps already
+  int admitted = 0;
+  bool head_passed = false;
+  // the admission stream and its event, made at the first admission (a
+  // server can be created and fed requests without a device)
+  bool have_stream = s->init_stream != nullptr;
+  if (!have_stream && !s->queue.empty()) {
+    have_stream = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&s->init_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!have_stream) {
+      cudaGetLastError();
+      if (s->init_stream) cudaStreamDestroy(s->init_stream);
+      s->init_stream = nullptr;
+      s->init_done = nullptr;
+    }
+  }
+  int looked = 0;
+  for (auto it = s->queue.begin();
+       it != s->queue.end() && (int)s->live.size() < s->max_live && looked < kBackfillLookahead;
+       ++looked) {
+    const Request q = *it;
+    const size_t bytes = rvea_workspace_bytes_ex(&q.cfg);
+    const size_t off = s->arena.alloc(bytes);
+    if (off == SIZE_MAX) {
+      if (it == s->queue.begin()) {
+        head_passed = true;
+        if (s->head_skips >= kHeadSkipsMax) break;   // let the arena drain for the head
+      }
+      ++it;
+      continue;
+    }
+    rvea_run *run = nullptr;
+    rvea_status sa = have_stream
+                         ? rvea_init_ex(&q.cfg, s->arena_base + off, bytes, s->init_stream, &run)
+                         : RVEA_ERR_CUDA;
+    if (sa == RVEA_OK && s->tune) sa = rvea_autotune(run, s->init_stream, 1, nullptr);
+    const bool was_head = it == s->queue.begin();
+    it = s->queue.erase(it);
+    if (was_head) s->head_skips = 0;
+    if (sa != RVEA_OK) {
+      // the request ends here: poll reports its id, fetch returns this error
+      if (run) rvea_free(run);
+      s->arena.release(off, bytes);
+      s->failed[q.id] = sa;
+      s->done_unpolled.push_back(q.id);
+      continue;
+    }
+    s->live.push_back(Live{q.id, run, off, bytes, q.generations});
+    ++admitted;
+  }
+  if (head_passed && !s->queue.empty()) ++s->head_skips;
+  if (admitted > 0) {
+    // the next step's launches on the step stream follow the new runs' set-up
+    if (cudaEventRecord(s->init_done, s->init_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(st, s->init_done, 0) != cudaSuccess)
+      return RVEA_ERR_CUDA;
+  }
   if (stats) {
     stats->live = (int)s->live.size();
     stats->queued = (int)s->queue.size();
@@ -233,6 +281,8 @@ void rvea_server_free(rvea_server *s) {
   if (!s) return;
   for (Live &l : s->live) rvea_free(l.run);
   for (auto &kv : s->done) rvea_free(kv.second.run);
+  if (s->init_done) cudaEventDestroy(s->init_done);
+  if (s->init_stream) cudaStreamDestroy(s->init_stream);
   delete s;
 }
 

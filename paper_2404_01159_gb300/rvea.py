@@ -18,7 +18,7 @@ from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, DTLZ3_SPHERE, DTLZ4_SPHERE, NE
 
 __all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
            "DTLZ2_SPHERE", "DTLZ1_LINEAR", "DTLZ3_SPHERE", "DTLZ4_SPHERE", "NEURO_LINEAR",
-           "lattice_size"]
+           "lattice_size", "lattice_for"]
 
 
 def _stream(stream) -> int:
@@ -34,6 +34,12 @@ def _ptr(t: Optional[torch.Tensor]):
 def lattice_size(m: int, H: int) -> int:
     from math import comb
     return comb(H + m - 1, m - 1)
+
+
+def lattice_for(m: int, n: int) -> int:
+    """H of the largest lattice with at most n points: the reference vectors
+    (and population size) of a run asked for n solutions."""
+    return int(lib().rvea_lattice_for(int(m), int(n)))
 
 
 def workspace_bytes(m: int, d: int, N: int) -> int:

@@ -173,3 +173,12 @@ def test_server_reports_failed_admission_by_id(native):
             assert L.rvea_server_fetch(srv, rid, None, None, None, None) == native.ERR_STATE
     finally:
         L.rvea_server_free(srv)
+
+
+def test_lattice_for_matches_the_oracle(native, orc):
+    """The library's H for a requested population size equals the oracle's
+    (host arithmetic, no GPU)."""
+    L = native.lib()
+    for m in (2, 3, 4, 5):
+        for n in [2 ** k for k in range(1, 15)] + [100, 9870, 9871, 32768]:
+            assert L.rvea_lattice_for(m, n) == orc.lattice_for(m, n), (m, n)

@@ -108,3 +108,24 @@ def test_adapt_zero_range_floor(orc):
 def test_objective_range(orc):
     F = np.array([[1.0, 5.0], [3.0, -1.0], [100.0, 100.0]])
     assert np.array_equal(orc.objective_range(F, np.array([1, 1, 0])), [2.0, 6.0])
+
+
+def test_lattice_for_population_size(orc):
+    """A population size n that is not a lattice size maps to the largest
+    lattice with at most n points: the paper's sweep sizes n = 2^5 .. 2^14
+    (m = 3) and n = 100, pinned by the count formula on both sides of H and
+    by hand-counted cases (C(8,2) = 28 <= 32 < 36 = C(9,2), C(14,2) = 91 <=
+    100 < 105)."""
+    from math import comb
+    assert orc.lattice_for(3, 32) == 6 and comb(8, 2) == 28
+    assert orc.lattice_for(3, 100) == 12 and comb(14, 2) == 91
+    assert orc.lattice_for(3, 105) == 13
+    assert orc.lattice_for(2, 100) == 99
+    assert orc.lattice_for(3, 2) == -1
+    for m in (2, 3, 5):
+        for n in [2 ** k for k in range(5, 15)] + [100, 9870, 9871]:
+            H = orc.lattice_for(m, n)
+            if H < 0:
+                assert comb(m, m - 1) > n
+                continue
+            assert comb(H + m - 1, m - 1) <= n < comb(H + m, m - 1)
