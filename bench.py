@@ -74,7 +74,7 @@ def peaks():
 
 def source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("k_repro.cu", "rvea_device.cuh"):
+    for f in ("k_repro.cu", "rvea_device.cuh", "eval_steps.cuh"):
         with open(os.path.join(ROOT, "paper_2404_01159_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -352,6 +352,23 @@ def main_neuro(args, rank, world, local):
     n_runs, N, H, t_max = 100, 100, 99, 100
     kw = dict(m=2, d=d, N=N, H=H, problem=NEURO_LINEAR, t_max=t_max, alpha=2.0, f_r=0.1,
               eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
+    # the FP32 CUDA-core form of the policy GEMVs, timed on the same workload
+    # first, as the comparison with the configuration's BF16 tensor-core form
+    runs32 = [Run(seed=rank * n_runs + q, neuro=dict(dyn, gemv=1), **kw) for q in range(n_runs)]
+    batch32 = Batch(runs32)
+    batch32.step(W)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    batch32.step(K)
+    f1.record()
+    f1.synchronize()
+    ms32 = f0.elapsed_time(f1)
+    ph32 = batch32.step_profiled(max(1, min(K, 5)))
+    for r in runs32:
+        r.sync_status()
+    batch32.free()
+    del runs32, batch32
     runs = [Run(seed=rank * n_runs + q, neuro=dyn, **kw) for q in range(n_runs)]
     for r in runs:
         autotune(r)
@@ -409,6 +426,14 @@ def main_neuro(args, rank, world, local):
                    "l2": "rollouts are compute-bound; weights stay on chip for 1000 steps",
                    "parallelism": "one CUDA graph per batched generation"},
         "policies_per_s": n_runs * N * K / (ms * 1e-3),
+        "fp32_cuda_cores": {
+            "value": n_runs * K / (ms32 * 1e-3), "unit": "run-generations/s",
+            "ms_per_step": ms32 / K,
+            "rollout_ms": ph32[0] / max(1, min(K, 5)),
+            "gemm_tflops": gemm_flop / (ph32[0] / max(1, min(K, 5)) * 1e-3) / 1e12,
+            "speedup_over_bf16_tensor": ms / ms32,
+            "what": "the same workload with the policy GEMVs in FP32 on the CUDA cores "
+                    "(weights in shared memory, rvea_neuro_dynamics.gemv = 1)"},
         "roofline": {"kernel": "k_rollout (1000-step rollout of every child)", "bound": "tensor",
                      "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
                      "frac": achieved / tf_peak, "peak_kind": "measured bf16 dense (burst)",

@@ -75,6 +75,10 @@ typedef struct {
     double sigma;
     const double *A;
     const double *B;
+    int gemv;         /* 0: the policy GEMVs on the tensor cores, BF16 operands
+                         split in hi and lo parts, FP32 accumulate; 1: on the
+                         CUDA cores in FP32 (weights in shared memory: needs
+                         ns <= 24 and na <= 8, else RVEA_ERR_ARG)            */
 } rvea_neuro_dynamics;
 
 /* All parameters of one optimisation run. */

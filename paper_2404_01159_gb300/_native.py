@@ -24,7 +24,8 @@ REPRO_SBX_PM, REPRO_DE, REPRO_RANDOM = 0, 1, 2
 class NeuroDynamics(C.Structure):
     _fields_ = [("ns", C.c_int), ("na", C.c_int), ("h1", C.c_int), ("h2", C.c_int),
                 ("steps", C.c_int), ("sigma", C.c_double),
-                ("A", C.POINTER(C.c_double)), ("B", C.POINTER(C.c_double))]
+                ("A", C.POINTER(C.c_double)), ("B", C.POINTER(C.c_double)),
+                ("gemv", C.c_int)]
 
 
 class Config(C.Structure):

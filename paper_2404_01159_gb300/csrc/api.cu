@@ -80,6 +80,9 @@ __global__ void k_select_pruned(const RunDesc *Rp);
 __global__ void k_tiles(const RunDesc *Rp);
 __global__ void k_noise(const __grid_constant__ BatchDir dir, int init);
 __global__ void k_rollout(const __grid_constant__ BatchDir dir, int init);
+__global__ void k_rollout_f32(const __grid_constant__ BatchDir dir, int init);
+size_t rollout_f32_smem(int ns, int na);
+constexpr int kRollF32Policies = 8;   // policies (warps) per CTA of the FP32 rollout
 __global__ void k_select_pruned_batch(const __grid_constant__ BatchDir dir);
 __global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force);
 __global__ void k_tail_dtlz1(const RunDesc *Rp);
@@ -402,6 +405,7 @@ void set_kernel_attrs() {
   set((const void *)k_select);
   set((const void *)k_select_pruned);
   set((const void *)k_select_pruned_batch);
+  set((const void *)k_rollout_f32);
   set((const void *)k_tail_dtlz1);
   {
     cudaFuncAttributes fa;
@@ -534,6 +538,42 @@ void launch_repro1(const rvea_run *r, const BatchDir &dr, int grid, cudaStream_t
     case PROB_DTLZ3: launch_pdl(k_repro1_dtlz3, grid, kReproThreads, 0, st, dr, rk); break;
     case PROB_DTLZ4: launch_pdl(k_repro1_dtlz4, grid, kReproThreads, 0, st, dr, rk); break;
     default: launch_pdl(k_repro1_neuro, grid, kReproThreads, 0, st, dr, rk); break;
+  }
+}
+
+// Rollouts of the children (or of the initial population, init = 1) of the
+// rollout-problem runs among `runs`: one directory per GEMV form.
+void launch_rollouts(rvea_run *const *runs, int n, cudaStream_t st, int init, bool pdl) {
+  static thread_local BatchDir dm, df;
+  int nm = 0, nf = 0, pm = 0, pf = 0;
+  size_t smf = 0;
+  for (int q = 0; q < n; ++q) {
+    const rvea_run *r = runs[q];
+    if (r->hd.problem != PROB_NEURO) continue;
+    const bool f32 = r->hd.roll_f32 != 0;
+    BatchDir &D = f32 ? df : dm;
+    int &k = f32 ? nf : nm;
+    int &p = f32 ? pf : pm;
+    D.prefix[k] = p;
+    D.desc[k] = r->d_desc;
+    D.key[k] = make_uint2(r->hd.key0, r->hd.key1);
+    D.items[k] = nullptr;
+    p += f32 ? (r->sh.N + kRollF32Policies - 1) / kRollF32Policies
+             : (r->sh.N + kRollPolicies - 1) / kRollPolicies;
+    if (f32) smf = std::max(smf, rollout_f32_smem(r->hd.ns, r->hd.na));
+    ++k;
+  }
+  if (nm > 0) {
+    dm.n = nm;
+    dm.prefix[nm] = pm;
+    if (pdl) launch_pdl(k_rollout, pm, 32 * kRollPolicies, 0, st, dm, init);
+    else k_rollout<<<pm, 32 * kRollPolicies, 0, st>>>(dm, init);
+  }
+  if (nf > 0) {
+    df.n = nf;
+    df.prefix[nf] = pf;
+    if (pdl) launch_pdl(k_rollout_f32, pf, 32 * kRollF32Policies, smf, st, df, init);
+    else k_rollout_f32<<<pf, 32 * kRollF32Policies, smf, st>>>(df, init);
   }
 }
 
@@ -736,27 +776,23 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   {
     // evaluation of the rollout problem's children: noise of generation t,
     // then one warp per policy
-    static thread_local BatchDir dn, dro;
-    int nn = 0, pn = 0, pro = 0;
+    static thread_local BatchDir dn;
+    int nn = 0, pn = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
       if (r->hd.problem != PROB_NEURO) continue;
-      const uint2 key = make_uint2(r->hd.key0, r->hd.key1);
       dn.prefix[nn] = pn;
-      dro.prefix[nn] = pro;
-      dn.desc[nn] = dro.desc[nn] = r->d_desc;
-      dn.key[nn] = dro.key[nn] = key;
-      dn.items[nn] = dro.items[nn] = nullptr;
+      dn.desc[nn] = r->d_desc;
+      dn.key[nn] = make_uint2(r->hd.key0, r->hd.key1);
+      dn.items[nn] = nullptr;
       pn += (r->hd.steps * r->hd.ns + 255) / 256;
-      pro += (r->sh.N + kRollPolicies - 1) / kRollPolicies;
       ++nn;
     }
     if (nn > 0) {
-      dn.n = dro.n = nn;
+      dn.n = nn;
       dn.prefix[nn] = pn;
-      dro.prefix[nn] = pro;
       launch_pdl(k_noise, pn, 256, 0, st, dn, 0);
-      launch_pdl(k_rollout, pro, 32 * kRollPolicies, 0, st, dro, 0);
+      launch_rollouts(runs, n, st, 0, true);
     }
   }
   if (ev) cudaEventRecord(ev[1], st);
@@ -877,6 +913,9 @@ rvea_status validate(const rvea_config *c) {
     if (!nd || !nd->A || !nd->B || nd->h1 != 64 || nd->h2 != 64 || nd->ns < 1 || nd->ns > 32 ||
         nd->na < 1 || nd->na > 16 || nd->steps < 1 || !(nd->sigma >= 0) || c->m != 2)
       return RVEA_ERR_ARG;
+    // the FP32 form keeps eight policies' weights in shared memory
+    if (nd->gemv < 0 || nd->gemv > 1 || (nd->gemv == 1 && (nd->ns > 24 || nd->na > 8)))
+      return RVEA_ERR_ARG;
     if (c->d != nd->h1 * nd->ns + nd->h1 + nd->h2 * nd->h1 + nd->h2 + nd->na * nd->h2 + nd->na)
       return RVEA_ERR_ARG;
   }
@@ -984,6 +1023,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   if (nd) {
     D.ns = nd->ns; D.na = nd->na; D.h1 = nd->h1; D.h2 = nd->h2; D.steps = nd->steps;
     D.sigma = (float)nd->sigma;
+    D.roll_f32 = nd->gemv;
     D.noise = wsp<float>(r, lay.noise);
     D.dynA = wsp<float>(r, lay.dynA);
     D.dynB = wsp<float>(r, lay.dynB);
@@ -1099,8 +1139,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     if (nd) {   // the initial population's rollouts (noise of t = 0)
       dir_single(d, r, nullptr, (nd->steps * nd->ns + 255) / 256);
       k_noise<<<(nd->steps * nd->ns + 255) / 256, 256, 0, st>>>(d, 1);
-      dir_single(d, r, nullptr, (sh.N + kRollPolicies - 1) / kRollPolicies);
-      k_rollout<<<(sh.N + kRollPolicies - 1) / kRollPolicies, 32 * kRollPolicies, 0, st>>>(d, 1);
+      rvea_run *one[1] = {r};
+      launch_rollouts(one, 1, st, 1, false);
     }
     dir_single(d, r, nullptr, 1);
     k_init_lists<<<dim3((sh.N + 255) / 256, 1), 256, 0, st>>>(d);
@@ -1535,11 +1575,9 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     if (r->sel_mode != 3) launch_mutate1(r, st);
     if (r->hd.problem == PROB_NEURO) {
       const int nb_noise = (r->hd.steps * r->hd.ns + 255) / 256;
-      const int nb_roll = (r->sh.N + kRollPolicies - 1) / kRollPolicies;
       dir_single(dn1, one, nullptr, nb_noise);
-      dir_single(dro1, one, nullptr, nb_roll);
       k_noise<<<nb_noise, 256, 0, st>>>(dn1, 0);
-      k_rollout<<<nb_roll, 32 * kRollPolicies, 0, st>>>(dro1, 0);
+      launch_rollouts(&r, 1, st, 0, false);
     }
     cudaEventRecord(e[1], st);
     if (r->sel_mode == 3)   // the fused tail: mutation, association and finalize

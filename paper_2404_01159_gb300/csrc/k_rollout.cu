@@ -276,4 +276,156 @@ k_rollout(const __grid_constant__ BatchDir dir, int init) {
   }
 }
 
+// The same rollout with the policy GEMVs on the CUDA cores in FP32 (the
+// configuration's other form, rvea_neuro_dynamics.gemv = 1): one warp per
+// policy, the policy's weights copied once into shared memory in FP32 and
+// read there every step.  Lane l owns the hidden rows l and l + 32 of both
+// layers; the weights of a layer are stored as float4 blocks
+// [column / 4][row], so the 32 lanes of a warp read 32 consecutive 16-byte
+// blocks (no bank conflict), and the input vector is broadcast from shared
+// memory.  The output layer sums over the 64 inputs with a butterfly.  The
+// dynamics and the objectives are as in the MMA form.  Dynamic shared
+// memory: A, B, then per warp W1 (ceil(ns/4) x 64 float4), W2 (16 x 64
+// float4), W3 (na x 64), b1, b2, b3, and the step's state and hidden vectors.
+constexpr int kRF32Warps = 8;
+
+struct RF32Layout {
+  int nc1;                       // float4 column blocks of W1 (ns padded to 4)
+  int offA, offB, per_warp;      // floats
+  int w1, w2, w3, b1, b2, b3, sv, h1;   // offsets within a warp's slab (floats)
+};
+__host__ __device__ inline RF32Layout rf32_layout(int ns, int na) {
+  RF32Layout L;
+  L.nc1 = (ns + 3) / 4;
+  L.offA = 0;
+  L.offB = ((kRollNsMax * kRollNsMax + 3) / 4) * 4;
+  const int dyn = L.offB + ((kRollNsMax * kRollNaMax + 3) / 4) * 4;
+  int o = 0;
+  L.w1 = o; o += L.nc1 * kRollH * 4;
+  L.w2 = o; o += (kRollH / 4) * kRollH * 4;
+  L.w3 = o; o += na * kRollH;
+  L.b1 = o; o += kRollH;
+  L.b2 = o; o += kRollH;
+  L.b3 = o; o += ((na + 3) / 4) * 4;
+  L.sv = o; o += L.nc1 * 4;
+  L.h1 = o; o += kRollH;
+  L.per_warp = ((o + 3) / 4) * 4;
+  L.offA = dyn;   // the slabs follow A and B
+  return L;
+}
+
+__global__ void __launch_bounds__(kRF32Warps * 32)
+k_rollout_f32(const __grid_constant__ BatchDir dir, int init) {
+  pdl_wait();
+  extern __shared__ __align__(16) float rsm[];
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ns = R.ns, na = R.na, steps = R.steps, N = R.N;
+  const RF32Layout Ly = rf32_layout(ns, na);
+  float *sA = rsm, *sB = rsm + ((kRollNsMax * kRollNsMax + 3) / 4) * 4;
+  for (int e = threadIdx.x; e < ns * ns; e += blockDim.x) sA[e] = R.dynA[e];
+  for (int e = threadIdx.x; e < ns * na; e += blockDim.x) sB[e] = R.dynB[e];
+  __syncthreads();
+  const int c = (blockIdx.x - dir.prefix[run]) * kRF32Warps + warp;
+  if (c >= N) return;
+  const int t = R.ctl->t;
+  int slot = c;
+  if (!init) slot = R.child_slot[(t & 1) * N + c];
+  if (slot < 0 || slot >= 2 * N) {
+    if (lane == 0) set_status(R.ctl, ST_BADINDEX);
+    return;
+  }
+  const float *x = R.X + (size_t)slot * R.d_pad;
+  const float *W1 = x, *b1 = W1 + kRollH * ns, *W2 = b1 + kRollH, *b2 = W2 + kRollH * kRollH;
+  const float *W3 = b2 + kRollH, *b3 = W3 + na * kRollH;
+  float *const slab = rsm + Ly.offA + warp * Ly.per_warp;
+  float4 *const w1s = reinterpret_cast<float4 *>(slab + Ly.w1);
+  float4 *const w2s = reinterpret_cast<float4 *>(slab + Ly.w2);
+  float *const w3s = slab + Ly.w3, *const bs1 = slab + Ly.b1, *const bs2 = slab + Ly.b2;
+  float *const bs3 = slab + Ly.b3, *const sv = slab + Ly.sv, *const h1 = slab + Ly.h1;
+  // the weights into shared memory, once
+  for (int e = lane; e < Ly.nc1 * kRollH; e += 32) {
+    const int c4 = e / kRollH, r = e - c4 * kRollH;
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = 4 * c4 + u < ns ? __ldg(W1 + (size_t)r * ns + 4 * c4 + u) : 0.0f;
+    w1s[e] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  for (int e = lane; e < (kRollH / 4) * kRollH; e += 32) {
+    const int c4 = e / kRollH, r = e - c4 * kRollH;
+    w2s[e] = __ldg(reinterpret_cast<const float4 *>(W2 + (size_t)r * kRollH) + c4);
+  }
+  for (int e = lane; e < na * kRollH; e += 32) w3s[e] = __ldg(W3 + e);
+  for (int e = lane; e < kRollH; e += 32) { bs1[e] = __ldg(b1 + e); bs2[e] = __ldg(b2 + e); }
+  if (lane < na) bs3[lane] = __ldg(b3 + lane);
+  if (lane < 4 * Ly.nc1) sv[lane] = 0.0f;
+  __syncwarp();
+  const float sigma = R.sigma;
+  const float *xi = R.noise;
+  const int r0 = lane, r1 = lane + 32;
+  const float *Ar = sA + lane * ns, *Br = sB + lane * na;
+  float s = 0.0f, f1 = 0.0f, f2 = 0.0f;
+#pragma unroll 1
+  for (int tau = 0; tau < steps; ++tau) {
+    // layer 1
+    float a0 = bs1[r0], a1 = bs1[r1], c0 = 0.0f, c1 = 0.0f;
+    for (int c4 = 0; c4 < Ly.nc1; ++c4) {
+      const float4 v = reinterpret_cast<const float4 *>(sv)[c4];
+      const float4 p = w1s[c4 * kRollH + r0], q = w1s[c4 * kRollH + r1];
+      a0 = fmaf(p.x, v.x, a0); c0 = fmaf(p.y, v.y, c0); a0 = fmaf(p.z, v.z, a0); c0 = fmaf(p.w, v.w, c0);
+      a1 = fmaf(q.x, v.x, a1); c1 = fmaf(q.y, v.y, c1); a1 = fmaf(q.z, v.z, a1); c1 = fmaf(q.w, v.w, c1);
+    }
+    h1[r0] = tanh_approx(a0 + c0);
+    h1[r1] = tanh_approx(a1 + c1);
+    __syncwarp();
+    // layer 2: four accumulation chains per row
+    float e0[4] = {bs2[r0], 0.0f, 0.0f, 0.0f}, e1[4] = {bs2[r1], 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+    for (int c4 = 0; c4 < kRollH / 4; ++c4) {
+      const float4 v = reinterpret_cast<const float4 *>(h1)[c4];
+      const float4 p = w2s[c4 * kRollH + r0], q = w2s[c4 * kRollH + r1];
+      e0[0] = fmaf(p.x, v.x, e0[0]); e0[1] = fmaf(p.y, v.y, e0[1]);
+      e0[2] = fmaf(p.z, v.z, e0[2]); e0[3] = fmaf(p.w, v.w, e0[3]);
+      e1[0] = fmaf(q.x, v.x, e1[0]); e1[1] = fmaf(q.y, v.y, e1[1]);
+      e1[2] = fmaf(q.z, v.z, e1[2]); e1[3] = fmaf(q.w, v.w, e1[3]);
+    }
+    const float g0 = tanh_approx((e0[0] + e0[1]) + (e0[2] + e0[3]));
+    const float g1 = tanh_approx((e1[0] + e1[1]) + (e1[2] + e1[3]));
+    // layer 3 and the dynamics' action term: u_o on every lane
+    float zb = 0.0f;
+    for (int o = 0; o < na; ++o) {
+      float pr = fmaf(w3s[o * kRollH + r0], g0, w3s[o * kRollH + r1] * g1);
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, off);
+      const float u = tanh_approx(pr + bs3[o]);
+      f2 = fmaf(u, u, f2);
+      if (lane < ns) zb = fmaf(Br[o], u, zb);
+    }
+    // dynamics: lane k computes s'[k]
+    float za = 0.0f;
+    if (lane < ns) {
+      for (int j = 0; j < ns; ++j) za = fmaf(Ar[j], sv[j], za);
+    }
+    s = lane < ns ? fmaf(sigma, __ldg(xi + (size_t)tau * ns + lane), za + zb) : 0.0f;
+    __syncwarp();   // every lane has read sv and h1
+    if (lane < ns) sv[lane] = s;
+    f1 -= __shfl_sync(0xffffffffu, s, 0);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    const int n2 = 2 * N;
+    R.F[slot] = f1;
+    R.F[(size_t)n2 + slot] = f2;
+    atomicMin(&R.ctl->zkey[0], f2ord(f1));
+    atomicMin(&R.ctl->zkey[1], f2ord(f2));
+  }
+}
+
+// Dynamic shared memory of k_rollout_f32 for this shape (bytes).
+size_t rollout_f32_smem(int ns, int na) {
+  const RF32Layout L = rf32_layout(ns, na);
+  return (size_t)(L.offA + kRF32Warps * L.per_warp) * sizeof(float);
+}
+
 }  // namespace rvea

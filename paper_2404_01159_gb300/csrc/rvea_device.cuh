@@ -145,6 +145,7 @@ struct RunDesc {
   const float *dynB;   // [ns][na]
   int ns, na, h1, h2, steps;
   float sigma;
+  int roll_f32;        // 1: policy GEMVs on the CUDA cores in FP32, 0: BF16 tensor cores
 };
 
 // Work item of the reproduction kernel: one CTA, consecutive work units of one

@@ -73,7 +73,7 @@ class Run:
             nd = NeuroDynamics(A.shape[0], B.shape[1], neuro.get("h1", 64), neuro.get("h2", 64),
                                neuro.get("steps", 1000), neuro.get("sigma", 0.01),
                                A.ctypes.data_as(C.POINTER(C.c_double)),
-                               B.ctypes.data_as(C.POINTER(C.c_double)))
+                               B.ctypes.data_as(C.POINTER(C.c_double)), int(neuro.get("gemv", 0)))
             self._neuro_keep = (A, B, nd)
             cfg.neuro = C.pointer(nd)
         nbytes = int(L.rvea_workspace_bytes_ex(C.byref(cfg)))

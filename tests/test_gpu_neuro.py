@@ -17,10 +17,10 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _setup(orc, N, H, steps, seed, t_max=40):
+def _setup(orc, N, H, steps, seed, t_max=40, gemv=0):
     from paper_2404_01159_gb300 import NEURO_LINEAR, Run
     from paper_2404_01159_gb300.workloads import neuro_dynamics, policy_size
-    dyn = neuro_dynamics(seed, steps=steps)
+    dyn = dict(neuro_dynamics(seed, steps=steps), gemv=gemv)
     d = policy_size()
     p = params(orc, 2, d, N, H, orc.NEURO, t_max=t_max, seed=seed, L=-1.0, U=1.0)
     nd = orc.NeuroData(dyn["A"], dyn["B"], steps=steps, sigma=dyn["sigma"])
@@ -28,8 +28,11 @@ def _setup(orc, N, H, steps, seed, t_max=40):
     return p, nd, run
 
 
-def test_initial_population_and_rollout(orc):
-    p, nd, run = _setup(orc, 10, 9, 200, 3)
+# gemv 0: the policy GEMVs on the tensor cores (BF16 hi/lo, FP32 accumulate);
+# gemv 1: on the CUDA cores in FP32
+@pytest.mark.parametrize("gemv", [0, 1])
+def test_initial_population_and_rollout(orc, gemv):
+    p, nd, run = _setup(orc, 10, 9, 200, 3, gemv=gemv)
     st = to_np(run.export_state())
     X0 = orc.init_population(p)
     # Box-Muller weights: float32 on the GPU, FP64 in the oracle
@@ -40,8 +43,9 @@ def test_initial_population_and_rollout(orc):
     run.sync_status()
 
 
-def test_teacher_forced_neuro_generations(orc):
-    p, nd, run = _setup(orc, 10, 9, 100, 5)
+@pytest.mark.parametrize("gemv", [0, 1])
+def test_teacher_forced_neuro_generations(orc, gemv):
+    p, nd, run = _setup(orc, 10, 9, 100, 5, gemv=gemv)
     V0 = orc.lattice_unit(orc.lattice(2, 9))
     for gen in range(5):
         st = run.export_state()
@@ -66,12 +70,13 @@ def test_teacher_forced_neuro_generations(orc):
     run.sync_status()
 
 
-def test_full_size_rollout_sampled(orc):
+@pytest.mark.parametrize("gemv", [0, 1])
+def test_full_size_rollout_sampled(orc, gemv):
     """The 100-policy, 1000-step configuration of the neuroevolution
     workload: every policy of the initial population against the oracle."""
     import os
     orc.set_threads(os.cpu_count() or 1)
-    p, nd, run = _setup(orc, 100, 99, 1000, 0, t_max=1000)
+    p, nd, run = _setup(orc, 100, 99, 1000, 0, t_max=1000, gemv=gemv)
     st = to_np(run.export_state())
     of = orc.evaluate(p, st["X"].astype(np.float64), 0, nd)
     assert_rollout_objectives(st["F"], of)

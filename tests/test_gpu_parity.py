@@ -98,6 +98,21 @@ def test_teacher_forced_other_operators(orc, shape, op):
     _teacher_forced(orc, shape, 6, op=op)
 
 
+# Population sizes of the paper's speed sweeps that are not lattice sizes
+# (Sec. 4.1: n = 2^k at d = 100, d = 2^k at n = 100): the run takes the
+# largest Das-Dennis lattice with at most n points (n = 128 -> H = 14,
+# N = 120; n = 1024 -> H = 43, N = 990; n = 100 -> H = 12, N = 91), on the
+# register path, the fused tail and the staged path.
+@pytest.mark.parametrize("n,d", [(128, 100), (1024, 100), (100, 4096)])
+def test_teacher_forced_sweep_sizes(orc, n, d):
+    from paper_2404_01159_gb300 import lattice_for, lattice_size
+    H = lattice_for(3, n)
+    assert H == orc.lattice_for(3, n)
+    N = lattice_size(3, H)
+    assert N <= n < lattice_size(3, H + 1)
+    _teacher_forced(orc, (3, d, N, H, 1), 4)
+
+
 def _teacher_forced(orc, shape, gens, **kw):
     m, d, N, H, prob = shape
     p = params(orc, m, d, N, H, prob, t_max=40, seed=5, **kw)   # adapts every 4th gen
