@@ -217,7 +217,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.otag = take((size_t)2 * s.N * 4);
   L.occ_cnt = take((size_t)kTailMaxCtas * 4);
   L.vcnt = take((size_t)kTailMaxCtas * 4);
-  L.zacc = take((size_t)2 * kMaxM * 4);
+  L.zacc = take((size_t)3 * kTailMaxCtas * 4 * 4);
   const size_t T = (size_t)s.tmax;
   L.Vt = take(s.tmax ? (size_t)s.N * 16 : 0);
   L.tperm = take(s.tmax ? (size_t)s.N * 4 : 0);

@@ -180,6 +180,11 @@ struct TailShared {
   int red[2][32];
   uint32_t free_[kTailFreeWords];
   double rng[kMaxM];
+  unsigned z[4];          // z* of the combined population (order-preserving)
+  unsigned zr[8];         // survivors' minimum (0..3) and maximum (4..7)
+  unsigned zpar[4];       // the parents' z*, read before the dependency wait
+  float gw[4];            // direction-grid scale of the current vectors
+  int grid_ok;            // the direction grid matches the current vectors
 };
 
 template <int PROB, int M>
@@ -236,6 +241,18 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   // the children by phase A below
   const float *fcur = (tail_mut && __ldcg(&ctl->fcomb_t) == t)
                           ? R.fcomb + (size_t)(t & 1) * M * n2 : nullptr;
+  // Also final before the wait: the parents' z* (set by the previous
+  // generation's decode; when SBX finished the children, the reproduction
+  // kernel adds theirs to it, so it is read after the wait instead), and
+  // whether the direction grid matches the vectors (its build ran after the
+  // previous tail) with its scale.
+  if (tid == 0) {
+    S.grid_ok = M <= 3 && R.gG > 0 && __ldcg(&ctl->grid_ver) == __ldcg(&ctl->v_ver);
+    for (int q = 0; q < 4; ++q) {
+      S.gw[q] = q < M && M <= 3 && R.gG > 0 ? __ldcg(R.gscale + q) : 1.0f;
+      S.zpar[q] = tail_mut && q < M ? __ldcg(&ctl->zkey[q]) : 0xFFFFFFFFu;
+    }
+  }
   const int cw = warp * nb + b, cd0 = 32 * cw, cd = cd0 + lane;
   const bool mwarp = tail_mut && warp < kTailMutWarps && cd0 < N;
   int slot = -1, k = 0, off = 0, total = 0;
@@ -291,10 +308,8 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
 
   // ---- A: mutation and evaluation of the children, z* ----------------------
   if (tid < kMaxM) { s_lo[tid] = 0xFFFFFFFFu; s_hi[tid] = 0u; }
-  if (b == 0) {
-    if (tid < kMaxM) { R.zacc[tid] = 0xFFFFFFFFu; R.zacc[kMaxM + tid] = 0u; }
+  if (b == 0)
     for (int q = tid; q < nb; q += kTailThreads) R.occ_cnt[q] = 0u;
-  }
   __syncthreads();
   if (tail_mut) {
     if (mwarp) {
@@ -348,23 +363,36 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
         }
       }
     }
-    __syncthreads();
-    if (tid < m && s_lo[tid] != 0xFFFFFFFFu) atomicMin(&ctl->zkey[tid], s_lo[tid]);
   }
+  // this CTA's minimum of its children (plane 0 of zacc): a plain store per
+  // CTA, where one atomic per CTA on the same words would queue the loads
+  // of z* after the barrier behind all of them
+  __syncthreads();
+  if (tid < 4) R.zacc[b * 4 + tid] = s_lo[tid];
   if (!grid_barrier(ctl, nb)) return;
   if (tid < kMaxM) s_lo[tid] = 0xFFFFFFFFu;   // for the survivors' minimum in C
 
   // ---- B: association and APD votes ----------------------------------------
   {
+    if (warp == 0) {   // z* = min(the parents' z*, every CTA's children)
+      // entry e of plane 0 is objective e % 4 of CTA e / 4; lane l takes the
+      // entries e = l (mod 32), all of objective l % 4
+      unsigned zl = lane < 4 ? (tail_mut ? S.zpar[lane] : __ldcg(&ctl->zkey[lane])) : 0xFFFFFFFFu;
+      for (int e = lane; e < 4 * nb; e += 32) zl = min(zl, __ldcg(R.zacc + e));
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) zl = min(zl, __shfl_xor_sync(0xffffffffu, zl, o));
+      if (lane < 4) S.z[lane] = zl;
+    }
     const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
+    __syncthreads();
     float z[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) z[k] = k < m ? ord2f(__ldcg(&ctl->zkey[k])) : 0.f;
-    if (M <= 3 && R.gG > 0 && __ldcg(&ctl->grid_ver) == __ldcg(&ctl->v_ver)) {
-      // the direction grid: one thread per solution
+    for (int k = 0; k < 4; ++k) z[k] = k < m ? ord2f(S.z[k]) : 0.f;
+    if (S.grid_ok) {
+      // the direction grid
       float w[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) w[k] = k < M ? R.gscale[k] : 1.0f;
+      for (int k = 0; k < 3; ++k) w[k] = S.gw[k];
       // eight lanes per solution, groups of four solutions spread over the CTAs
       const int gw = warp * nb + b, nw = nb * (kTailThreads / 32);
       for (int g = gw; 4 * g < R.n_comb; g += nw)
@@ -428,9 +456,9 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     if (lane == 0) s_red[0][warp] = nvalid;
   }
   __syncthreads();
-  if (tid < m && s_lo[tid] != 0xFFFFFFFFu) {
-    atomicMin(&R.zacc[tid], s_lo[tid]);
-    atomicMax(&R.zacc[kMaxM + tid], s_hi[tid]);
+  if (tid < 4) {   // planes 1 and 2 of zacc: this CTA's survivors' minimum and maximum
+    R.zacc[(nb + b) * 4 + tid] = s_lo[tid];
+    R.zacc[(2 * nb + b) * 4 + tid] = s_hi[tid];
   }
   if (tid == 0) {
     int c = 0;
@@ -458,6 +486,20 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     af = __reduce_add_sync(0xffffffffu, af);
     if (lane == 0) { s_red[1][0] = a; s_red[1][1] = av; s_red[1][2] = af; }
   }
+  const bool adapt = (t % R.p_adapt) == 0;
+  if (warp == 2 && (b == 0 || adapt)) {   // the survivors' minimum and maximum over the CTAs
+    unsigned lo = 0xFFFFFFFFu, hi = 0u;      // of objective lane % 4, as in B
+    for (int e = lane; e < 4 * nb; e += 32) {
+      lo = min(lo, __ldcg(R.zacc + 4 * nb + e));
+      hi = max(hi, __ldcg(R.zacc + 8 * nb + e));
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane < 4) { S.zr[lane] = lo; S.zr[4 + lane] = hi; }
+  }
   __syncthreads();
   tot_v = s_red[1][0];
   pre_v = s_red[1][1];
@@ -477,14 +519,12 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     warp_compact_by([&](int w) { return s_free[w - o0]; }, o0, o1,
                     R.child_slot + ((t + 1) & 1) * N, pre_f, N);
   }
-  if (b == 0 && tid < m) ctl->zkey[tid] = __ldcg(R.zacc + tid);
-  const bool adapt = (t % R.p_adapt) == 0;
+  if (b == 0 && tid < m) ctl->zkey[tid] = S.zr[tid];
   if (adapt && K > 0) {
     // range_k = max - min over the survivors, floored at 1e-12, in FP64
     double *const s_rng = S.rng;
     if (tid < m) {
-      const double r = (double)ord2f(__ldcg(R.zacc + kMaxM + tid)) -
-                       (double)ord2f(__ldcg(R.zacc + tid));
+      const double r = (double)ord2f(S.zr[4 + tid]) - (double)ord2f(S.zr[tid]);
       s_rng[tid] = r < 1e-12 ? 1e-12 : r;
       if (b == 0) R.vrange[tid] = s_rng[tid];
     }

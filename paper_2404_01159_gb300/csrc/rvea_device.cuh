@@ -107,7 +107,8 @@ struct RunDesc {
   int *otag;           // [2N]       generation t whose survivors occupy pool row s (0: none)
   unsigned *occ_cnt;   // [kTailMaxCtas] occupied pool rows in each CTA's row range
   int *vcnt;           // [kTailMaxCtas] valid slots in each CTA's vector range
-  unsigned *zacc;      // [2][kMaxM] survivors' minimum / maximum (order-preserving)
+  unsigned *zacc;      // [3][kTailMaxCtas][4] per-CTA minima of the children, minima and
+                       // maxima of the survivors (order-preserving)
   float *fcomb;        // [2][m][2N] objectives of the combined population by combined
                        //            index (parents i < N in slot order, NaN when
                        //            invalid; children N + c), for generation parity t & 1
