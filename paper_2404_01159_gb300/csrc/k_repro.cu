@@ -108,7 +108,8 @@ __device__ __forceinline__ void sbx_pair(float2 x1, float2 x2, float2 B, float L
 
 // Main-pass work on four adjacent variables (float4 Q of the row) of both
 // children: SBX from Philox SBX (Q, p, t), clip, store, accumulate g-terms.
-// (EVAL false: without the g-terms.)  The DTLZ problems live on the unit box.
+// (EVAL false: without the g-terms, into float4s of the caller's registers rather than pool
+// rows.)  The DTLZ problems live on the unit box.
 template <int PROB, class KP, bool EVAL = true>
 __device__ __forceinline__ void cross4(const float4 xa, const float4 xb, int Q, int p, int t,
                                        bool nocross, float ie, float L, float U, const KP &kp,
@@ -126,8 +127,13 @@ __device__ __forceinline__ void cross4(const float4 xa, const float4 xb, int Q, 
     acc2 = g_terms2(PROB, b0, acc2);
     acc2 = g_terms2(PROB, b1, acc2);
   }
-  *y1 = make_float4(a0.x, a0.y, a1.x, a1.y);
-  if (y2) *y2 = make_float4(b0.x, b0.y, b1.x, b1.y);
+  if (EVAL) {   // rows of the pool: streaming stores (evict-first in L2)
+    __stcs(y1, make_float4(a0.x, a0.y, a1.x, a1.y));
+    if (y2) __stcs(y2, make_float4(b0.x, b0.y, b1.x, b1.y));
+  } else {      // the edge path's float4s in registers
+    *y1 = make_float4(a0.x, a0.y, a1.x, a1.y);
+    if (y2) *y2 = make_float4(b0.x, b0.y, b1.x, b1.y);
+  }
 }
 
 // The same for a float4 that holds some of x_1..x_{m-1} (j < mh, kept out
@@ -144,8 +150,8 @@ __device__ __noinline__ Acc2 cross4_edge(const float4 xa, const float4 xb, int Q
   float2 z1 = make_float2(0.f, 0.f), z2 = z1;
   float4 c1, c2;
   cross4<PROB, KeyRun, false>(xa, xb, Q, p, t, nocross, ie, L, U, kp, &c1, &c2, z1, z2);
-  *y1 = c1;
-  if (y2) *y2 = c2;
+  __stcs(y1, c1);
+  if (y2) __stcs(y2, c2);
   if (PROB == PROB_NEURO) return acc;
   const float u1[4] = {c1.x, c1.y, c1.z, c1.w}, u2[4] = {c2.x, c2.y, c2.z, c2.w};
 #pragma unroll
@@ -313,8 +319,9 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
       const uint32_t bytes = (uint32_t)(min(gE, gs + 32) - gs) * 32u;
       fence_proxy_async_smem();   // this stage's earlier reads come first
       mbar_expect_tx(&bar[q], 2u * bytes);
-      tma_load_1d(sb + q * 128, Xf + r1 + 8 * gs, bytes, &bar[q]);
-      tma_load_1d(sb + q * 128 + 64, Xf + r2 + 8 * gs, bytes, &bar[q]);
+      const uint64_t pol = policy_evict_first();
+      tma_load_1d_hint(sb + q * 128, Xf + r1 + 8 * gs, bytes, &bar[q], pol);
+      tma_load_1d_hint(sb + q * 128 + 64, Xf + r2 + 8 * gs, bytes, &bar[q], pol);
     };
     if (wl == 0)
       for (int c = 0; c < min(kStages - 1, nch); ++c) issue(c);

@@ -435,6 +435,24 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// L2 policy for data streamed through once (the reproduction kernel's parent
+// rows and child rows): evicted first, so that the 0.4 GB a generation
+// moves does not push the selection's tables, partial sums and code out of
+// L2 between the kernels.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// tma_load_1d with an L2 cache policy.
+__device__ __forceinline__ void tma_load_1d_hint(void *dst, const void *src, uint32_t bytes,
+                                                 uint64_t *bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
 // Bounded wait on phase `parity` of `bar`: returns false after `limit` polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
   const uint32_t a = smem_u32(bar);
