@@ -228,7 +228,7 @@ def main_batched(args, rank, world, local, emit=True, steps=None, warmup=None, w
     from paper_2404_01159_gb300.workloads import batched_set
     K = args.steps if steps is None else steps
     W = max(3, args.warmup if warmup is None else warmup)
-    insts = batched_set(256, 500, seed0=rank * 256)
+    insts = batched_set(args.batched_runs, 500, seed0=rank * args.batched_runs)
     t0 = time.perf_counter()
     runs = [Run(**i.run_kwargs()) for i in insts]
     torch.cuda.synchronize()
@@ -730,6 +730,8 @@ def main():
                     help="time allowed after the arrival window")
     ap.add_argument("--serve-budget-gb", type=float, default=80.0)
     ap.add_argument("--serve-max-live", type=int, default=320)
+    ap.add_argument("--batched-runs", type=int, default=256,
+                    help="runs of the batched workload (256; fewer only to profile a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")

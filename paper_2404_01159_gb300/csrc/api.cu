@@ -115,6 +115,7 @@ struct Shape {
   int n_repro, n_init, nblk;
   int n_sel_max;   // work items of the finest full-scan plan (table size)
   int tmax;     // tiles of the pruned selection (0: not used)
+  int tglob;    // 1: tables too large for shared memory (fused tail only, from L2)
   int gG, gcells, gcap;   // direction grid of the association (gG = 0: none)
 };
 
@@ -127,6 +128,7 @@ constexpr int kPruneChunkHost = 2048;   // solutions per work chunk of the batch
 constexpr int kRollPolicies = 2;        // policies (warps) per CTA of the rollout kernel
 constexpr size_t kPruneSmemCap = 200 * 1024;
 int prune_tiles_bound(int N) { return N / 16 + 2; }
+constexpr int kGridMaxN = 65535;   // the grid's cell lists hold 16-bit table positions
 size_t prune_smem(int N, int T) {
   const size_t bS = ((size_t)T * 8 + 15) & ~size_t(15);
   return (size_t)N * 16 + (size_t)T * 16 + 2 * bS;
@@ -157,8 +159,15 @@ Shape make_shape(int m, int d, int N) {
   s.nblk = (s.n_comb + kSelBlock - 1) / kSelBlock;
   s.n_sel_max = s.nblk * ((N + kVTile - 1) / kVTile);
   s.tmax = 0;
-  if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap)
+  s.tglob = 0;
+  if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap) {
     s.tmax = prune_tiles_bound(N);
+  } else if (m <= 3 && N >= kPruneMinN && N <= kGridMaxN) {
+    // past shared memory (N above ~12.7 k at m = 3): the tables and the
+    // direction grid still serve the fused tail, read through L2
+    s.tmax = prune_tiles_bound(N);
+    s.tglob = 1;
+  }
   // direction grid (m = 2, 3, with the tile tables it is built from): steps
   // of 1/(4H) (m = 2) or 1/(2H) (m = 3) per barycentric axis, a fraction of
   // the lattice spacing 1/H, so that a cell lists a handful of vectors
@@ -621,10 +630,12 @@ bool tail_ok(const rvea_run *r) {
   return r->hd.ntiles > 0 && r->hd.problem != PROB_NEURO &&
          (2 * r->sh.N + 31) / 32 <= 64 * tail_grid(r) &&
          (r->sh.N + 31) / 32 <= kTailMutWarps * tail_grid(r) &&
-         r->prune_smem_bytes <= g_tail_dyn_max;
+         (r->hd.tables_global || r->prune_smem_bytes <= g_tail_dyn_max);
 }
+// dynamic shared memory of the fused tail: the staged tables, or none
+int tail_smem(const rvea_run *r) { return r->hd.tables_global ? 0 : r->prune_smem_bytes; }
 void launch_tail(const rvea_run *r, cudaStream_t st, bool pdl) {
-  const int g = tail_grid(r), sm = r->prune_smem_bytes;
+  const int g = tail_grid(r), sm = tail_smem(r);
   const RunDesc *d = r->d_desc;
   void (*k)(const RunDesc *) = r->hd.problem == PROB_DTLZ1   ? k_tail_dtlz1
                                : r->hd.problem == PROB_DTLZ3 ? k_tail_dtlz3
@@ -642,7 +653,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
                               cudaEvent_t *ev = nullptr) {
   static thread_local BatchDir dr, ds, dp, df, dd, dt, dg[2 * kProblems];
   int pr = 0, ps = 0, pp = 0, pd = 0, pt = 0;
-  int sms = 0, smp = 0, ns = 0, np = 0;
+  int sms = 0, smp = 0, ns = 0, np = 0, nt = 0;
   dr.n = df.n = dd.n = n;
   for (int q = 0; q < n; ++q) {
     const rvea_run *r = runs[q];
@@ -656,7 +667,18 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     df.items[q] = dd.items[q] = nullptr;
     pd += (r->sh.N + 1023) / 1024;
     pr += r->sh.n_repro;
-    if (r->sel_mode == 0) {
+    // tables in L2 (too large for shared memory) serve only the fused tail,
+    // which steps a run alone: in a batch such a run takes the full scan,
+    // its tiles kept current
+    if (r->sel_mode != 0 && r->hd.ntiles > 0) {
+      dt.prefix[nt] = pt;
+      dt.desc[nt] = r->d_desc;
+      dt.key[nt] = key;
+      dt.items[nt] = nullptr;
+      pt += (r->hd.ntiles + 7) / 8;
+      ++nt;
+    }
+    if (r->sel_mode == 0 || (n > 1 && r->hd.tables_global)) {
       ds.prefix[ns] = ps;
       ds.desc[ns] = r->d_desc;
       ds.key[ns] = key;
@@ -666,13 +688,11 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       ++ns;
     } else {
       dp.prefix[np] = pp;
-      dt.prefix[np] = pt;
-      dp.desc[np] = dt.desc[np] = r->d_desc;
-      dp.key[np] = dt.key[np] = key;
-      dp.items[np] = dt.items[np] = nullptr;
+      dp.desc[np] = r->d_desc;
+      dp.key[np] = key;
+      dp.items[np] = nullptr;
       pp += (r->sh.n_comb + kPruneChunkHost - 1) / kPruneChunkHost;
       smp = std::max(smp, r->prune_smem_bytes);
-      pt += (r->hd.ntiles + 7) / 8;
       ++np;
     }
   }
@@ -681,9 +701,10 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   dd.prefix[n] = pd;
   ds.n = ns;
   ds.prefix[ns] = ps;
-  dp.n = dt.n = np;
+  dp.n = np;
   dp.prefix[np] = pp;
-  dt.prefix[np] = pt;
+  dt.n = nt;
+  dt.prefix[nt] = pt;
   if (ev) cudaEventRecord(ev[0], st);
   const bool fused = n == 1 && runs[0]->sel_mode == 3;
   if (n == 1) {
@@ -812,7 +833,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
     k_gamma<<<2 * runs[0]->num_sms, 256, 0, st>>>(df, 0);
-    if (np > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
+    if (nt > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
   }
   if (ev) cudaEventRecord(ev[5], st);
   return cuerr(cudaGetLastError());
@@ -1083,7 +1104,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     if ((int)trng.size() > sh.tmax) trng.clear();   // cannot happen; keeps the bound honest
   }
   D.ntiles = (int)trng.size();
-  r->sel_mode = D.ntiles > 0 ? 1 : 0;
+  D.tables_global = D.ntiles > 0 && sh.tglob ? 1 : 0;
+  r->sel_mode = D.ntiles > 0 && !D.tables_global ? 1 : 0;
   D.repro_staged = sh.team == 32 ? 1 : 0;
   if (D.ntiles > 0) {
     D.Vt = wsp<float4>(r, lay.Vt);
@@ -1230,6 +1252,7 @@ namespace {
 
 rvea_status apply_plan(rvea_run *r, const rvea_plan &pl, cudaStream_t st) {
   if (pl.sel_mode < 0 || pl.sel_mode > 3 || (pl.sel_mode > 0 && r->hd.ntiles == 0) ||
+      ((pl.sel_mode == 1 || pl.sel_mode == 2) && r->hd.tables_global) ||
       (pl.sel_mode == 3 && !tail_ok(r)))
     return RVEA_ERR_ARG;
   if (pl.sel_per_sm < 1 || pl.sel_per_sm > kSelPerSmMax) return RVEA_ERR_ARG;
@@ -1383,7 +1406,7 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
     const double us = timed([&] { k_select<<<r->n_sel, kSelThreads, r->sel_smem, st>>>(ds); }, false);
     if (us < best_sel) { best_sel = us; best.sel_mode = 0; best.sel_per_sm = per_sm[q]; }
   }
-  if (r->hd.ntiles > 0 && s == RVEA_OK) {
+  if (r->hd.ntiles > 0 && !r->hd.tables_global && s == RVEA_OK) {
     double us = timed([&] {
       k_select_pruned<<<r->num_sms, 1024, r->prune_smem_bytes, st>>>(r->d_desc);
     }, true);
@@ -1400,6 +1423,10 @@ rvea_status rvea_autotune(rvea_run *r, void *cuda_stream, int use_cache, rvea_pl
   // the pruned search in shared memory runs inside the fused tail where the
   // run has one (the same search, without the launch boundaries around it)
   if (best.sel_mode == 1 && tail_ok(r)) best.sel_mode = 3;
+  // tables past shared memory: the fused tail's grid search (O(N) work
+  // against the full scan's O(N^2)) is taken without a timing, which it
+  // cannot have without advancing the run
+  if (r->hd.tables_global && tail_ok(r)) best.sel_mode = 3;
   // the tables above were rebuilt for the candidates: force the chosen plan
   r->sel_per_sm = -1;
   r->repro_smem = before.repro_staged ? kStagedSmem : 0;

@@ -200,33 +200,37 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   Ctl *const ctl = R.ctl;
 
   // ---- prologue: the search tables into shared memory (written by k_tiles,
-  // earlier than the reproduction kernel) ------------------------------------
+  // earlier than the reproduction kernel), unless they exceed it: then the
+  // kernel reads them where they are, through L2 --------------------------------
+  const bool gtab = R.tables_global != 0;
   const uint32_t bV = (uint32_t)N * 16, bC = (uint32_t)T * 16, bS = (uint32_t)T * 8;
   const uint32_t bSr = (bS + 15u) & ~15u;
-  float4 *sV = reinterpret_cast<float4 *>(smem);
-  float4 *sC = reinterpret_cast<float4 *>(smem + bV);
-  float2 *sCS = reinterpret_cast<float2 *>(smem + bV + bC);
-  int2 *sR = reinterpret_cast<int2 *>(smem + bV + bC + bSr);
-  if (tid == 0) {
-    mbar_init(&s_bar, 1);
-    fence_mbar_init();
-    mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
-    tma_load_1d(sV, R.Vt, bV, &s_bar);
-    tma_load_1d(sC, R.tcen, bC, &s_bar);
-    tma_load_1d(sCS, R.tcs, bSr, &s_bar);
-    tma_load_1d(sR, R.trng, bSr, &s_bar);
-  }
-  __syncthreads();
-  const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
-  if (__syncthreads_or(!staged)) {
-    // a copy never arrived: flag it, let the copies land, give up (the other
-    // CTAs' barriers then time out and report the same status)
+  const float4 *sV = gtab ? R.Vt : reinterpret_cast<const float4 *>(smem);
+  const float4 *sC = gtab ? R.tcen : reinterpret_cast<const float4 *>(smem + bV);
+  const float2 *sCS = gtab ? R.tcs : reinterpret_cast<const float2 *>(smem + bV + bC);
+  const int2 *sR = gtab ? R.trng : reinterpret_cast<const int2 *>(smem + bV + bC + bSr);
+  if (!gtab) {
     if (tid == 0) {
-      set_status(ctl, ST_TIMEOUT);
-      mbar_wait(&s_bar, 0u, kWaitLimit);
+      mbar_init(&s_bar, 1);
+      fence_mbar_init();
+      mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
+      tma_load_1d(smem, R.Vt, bV, &s_bar);
+      tma_load_1d(smem + bV, R.tcen, bC, &s_bar);
+      tma_load_1d(smem + bV + bC, R.tcs, bSr, &s_bar);
+      tma_load_1d(smem + bV + bC + bSr, R.trng, bSr, &s_bar);
     }
     __syncthreads();
-    return;
+    const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
+    if (__syncthreads_or(!staged)) {
+      // a copy never arrived: flag it, let the copies land, give up (the
+      // other CTAs' barriers then time out and report the same status)
+      if (tid == 0) {
+        set_status(ctl, ST_TIMEOUT);
+        mbar_wait(&s_bar, 0u, kWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
   }
   const float2 csb = tile_bounds(sCS, T);
   // the generation index and the child slots were written by the previous

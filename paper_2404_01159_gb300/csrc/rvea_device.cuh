@@ -130,6 +130,8 @@ struct RunDesc {
   Ctl *ctl;
   // pruned selection: reference vectors grouped into spatially compact tiles
   int ntiles;          // 0: the pruned kernel is not used for this run
+  int tables_global;   // 1: the tables exceed shared memory; the fused tail reads them
+                       //    from global memory (L2) and the pruned kernels are not used
   float4 *Vt;          // [N]        V32 in tile order (m <= 4)
   int *tperm;          // [N]        tile-order position -> vector index j
   int2 *trng;          // [ntiles]   (first position, count <= 64) of each tile

@@ -50,6 +50,36 @@ def test_every_plan_gives_the_same_bits(orc, shape):
         run.sync_status()
 
 
+# A population whose vector tables exceed shared memory (N = 16290, m = 3:
+# 261 KB of vectors): the fused tail reads its tables and the direction grid
+# through L2, the shared-memory pruned kernels are refused, and the full scan
+# gives the same bits over generations that adapt (the grid is rebuilt) and
+# one stepped in a batch (full scan there, tiles kept current).
+def test_tables_past_shared_memory(orc):
+    from paper_2404_01159_gb300 import RveaError, get_plan, set_plan, step_batch
+    p = params(orc, 3, 100, 16290, 179, 1, t_max=40, seed=4)   # adapts every 4th generation
+    run = make_run(p)
+    assert get_plan(run)["sel_mode"] == 3
+    for mode in (1, 2):
+        with pytest.raises(RveaError):
+            set_plan(run, mode)
+    ref = make_run(p)
+    set_plan(ref, 0)
+    run.step(6)
+    ref.step(6)
+    _same(ref, run)
+    other = make_run(params(orc, 3, 40, 105, 13, 0, t_max=40, seed=5))
+    for _ in range(3):              # t 7..9: an adaptation inside the batch
+        step_batch([run, other])
+    ref.step(3)
+    _same(ref, run)
+    run.step(4)                     # alone again, fused tail, tiles current
+    ref.step(4)
+    _same(ref, run)
+    run.sync_status()
+    ref.sync_status()
+
+
 def test_variant_the_shape_lacks_is_refused(orc):
     from paper_2404_01159_gb300 import RveaError, set_plan
     run = make_run(params(orc, 5, 40, 126, 5, 0))

@@ -101,9 +101,11 @@ def test_teacher_forced_other_operators(orc, shape, op):
 # Population sizes of the paper's speed sweeps that are not lattice sizes
 # (Sec. 4.1: n = 2^k at d = 100, d = 2^k at n = 100): the run takes the
 # largest Das-Dennis lattice with at most n points (n = 128 -> H = 14,
-# N = 120; n = 1024 -> H = 43, N = 990; n = 100 -> H = 12, N = 91), on the
-# register path, the fused tail and the staged path.
-@pytest.mark.parametrize("n,d", [(128, 100), (1024, 100), (100, 4096)])
+# N = 120; n = 1024 -> H = 43, N = 990; n = 100 -> H = 12, N = 91;
+# n = 16384 -> H = 179, N = 16290, tables past shared memory), on the
+# register path, the fused tail (tables in shared memory and in L2) and the
+# staged path.
+@pytest.mark.parametrize("n,d", [(128, 100), (1024, 100), (100, 4096), (16384, 100)])
 def test_teacher_forced_sweep_sizes(orc, n, d):
     from paper_2404_01159_gb300 import lattice_for, lattice_size
     H = lattice_for(3, n)
