@@ -23,6 +23,7 @@
 
 #include "../../include/rvea.h"
 #include "rvea_device.cuh"
+#include "grid_steps.cuh"
 #include "metrics.cuh"
 #include "nvtx_range.h"
 
@@ -853,7 +854,7 @@ rvea_status launch_tiles(rvea_run *r, cudaStream_t st) {
   if (r->hd.ntiles == 0) return RVEA_OK;
   k_tiles<<<(r->hd.ntiles + 7) / 8, 256, 0, st>>>(r->d_desc);
   if (r->hd.gG > 0) {
-    const int nb = (r->hd.gcells + 7) / 8;   // one warp per cell
+    const int nb = grid_build_blocks(r->hd.gG, r->sh.m);   // one CTA per block of cells
     k_grid_scale<<<1, 32, 0, st>>>(r->d_desc);
     k_grid_count<<<nb, 256, 0, st>>>(r->d_desc);
     k_grid_scan<<<1, 1024, 0, st>>>(r->d_desc);

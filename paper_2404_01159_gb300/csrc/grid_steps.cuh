@@ -32,6 +32,15 @@ namespace rvea {
 
 constexpr int kGridRec = 16;      // uint16 per cell record (32 bytes)
 constexpr int kGridInline = 15;   // candidates held in the record itself
+// cells per block of the build: one CTA lists the candidate tiles of a
+// block once for all its cells (64 consecutive cells for m = 2, 8 x 8 for
+// m = 3); grid_build_blocks gives the launch's CTA count
+constexpr int kGridSpan2 = 64;
+constexpr int kGridSpan3 = 8;
+__host__ __device__ inline int grid_build_blocks(int G, int m) {
+  const int span = m == 2 ? kGridSpan2 : kGridSpan3, nbx = (G + span - 1) / span;
+  return m == 2 ? nbx : nbx * nbx;
+}
 
 // Cell of the direction of f' (>= 0, not 0): the first M - 1 scaled
 // barycentric coordinates, each cut into G steps.

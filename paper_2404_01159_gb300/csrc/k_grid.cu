@@ -10,6 +10,7 @@ constexpr float kGridPad = 4e-6f;   // cell widening in barycentric units (float
 constexpr float kDotTol = 3e-6f;    // float32 cosine error allowance of the build's tests
 constexpr float kCandEps = 2e-6f;   // 2 eps: dot error of the association relative to |f'|
 constexpr float kAngTol = 2e-5f;    // allowance for the float32 angles below (radians)
+constexpr int kGridBlockList = 512;  // tiles a block's list holds
 
 // The cell's candidate test: centre direction and cos / sin of R (float,
 // rounded outwards), or live = false for a cell that lies outside the
@@ -23,18 +24,19 @@ struct CellGeom {
   bool live;
 };
 
+// The same for a region of cells [c0, c0 + span) per axis (a cell: span 1;
+// a block of cells: its union).  The vector close to the centre is sought
+// among the tiles list[0 .. nl) (every tile with list == null).
 template <int M>
-__device__ CellGeom cell_geom(const RunDesc &R, int cell, const float4 *Vt) {
+__device__ CellGeom region_geom(const RunDesc &R, const int *ck, int span, const float4 *Vt,
+                                const int *list, int nl) {
   CellGeom g;
   g.live = false;
   const int G = R.gG, lane = threadIdx.x & 31;
-  int ck[2] = {0, 0};
-  int rem = cell;
-  for (int k = 0; k < M - 1; ++k) { ck[k] = rem % G; rem /= G; }
   float lo[2], hi[2], sl = 0.0f;
   for (int k = 0; k < M - 1; ++k) {
     lo[k] = (float)ck[k] / (float)G - kGridPad;
-    hi[k] = (float)(ck[k] + 1) / (float)G + kGridPad;
+    hi[k] = (float)min(G, ck[k] + span) / (float)G + kGridPad;
     sl += lo[k];
   }
   if (sl > 1.0f) return g;
@@ -73,9 +75,10 @@ __device__ CellGeom cell_geom(const RunDesc &R, int cell, const float4 *Vt) {
   // a vector close to c: the best member of the tile whose centre is closest
   float bt = -INFINITY;
   int tb = 0;
-  for (int t = lane; t < R.ntiles; t += 32) {
+  for (int e = lane; e < nl; e += 32) {
+    const int t = list ? list[e] : e;
     const float d = pdot<M>(g.c, R.tcen[t]);
-    if (d > bt) { bt = d; tb = t; }
+    if (d > bt || (d == bt && t < tb)) { bt = d; tb = t; }
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
@@ -134,17 +137,15 @@ __device__ __forceinline__ bool support_test(const CellGeom &g, float4 v) {
   return cu + sup + g.delta2 * sqrtf(uu) >= -(kCandEps + 2.0f * kDotTol);
 }
 
-// Count (FILL = false) or write (FILL = true) the candidates of every cell:
-// the tiles whose centre lies within R + rho_t of c, then their members
-// within R that pass the support test.
+// Count (FILL = false) or write (FILL = true) the candidates of one cell:
+// the tiles of the list whose centre lies within R + rho_t of c, then their
+// members within R that pass the support test.
 template <int M, bool FILL>
-__device__ void grid_cells(const RunDesc &R) {
+__device__ void grid_one(const RunDesc &R, const int *ck, const int *list, int nl) {
   const int lane = threadIdx.x & 31;
-  const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (cell >= R.gcells) return;
-  if (FILL && __ldcg(&R.ctl->grid_ver) != __ldcg(&R.ctl->v_ver)) return;   // did not fit
+  const int cell = M == 2 ? ck[0] : ck[0] + ck[1] * R.gG;
   const float4 *Vt = R.Vt;
-  const CellGeom g = cell_geom<M>(R, cell, Vt);
+  const CellGeom g = region_geom<M>(R, ck, 1, Vt, list, nl);
   int n = 0;
   // inline records hold up to kGridInline candidates; longer lists go to the
   // overflow area at the offset the scan stored in the record
@@ -157,22 +158,23 @@ __device__ void grid_cells(const RunDesc &R) {
     at = inl ? 0 : (int)((uint32_t)rec[1] | ((uint32_t)rec[2] << 16));
   }
   if (g.live) {
-    const bool wide = g.cosR < 0.0f;   // R > pi/2: every tile
+    const bool wide = g.cosR < 0.0f;   // R > pi/2: every tile of the list
     const float cR = g.cosR, sR = g.sinR;
     const float thr_m = g.cosR - kDotTol;
-    for (int t0 = 0; t0 < R.ntiles; t0 += 32) {
-      const int t = t0 + lane;
+    for (int e0 = 0; e0 < nl; e0 += 32) {
+      const int e = e0 + lane;
       bool pass = false;
-      if (t < R.ntiles) {
+      if (e < nl) {
+        const int t = list ? list[e] : e;
         const float2 cs = R.tcs[t];
         const float d = pdot<M>(g.c, R.tcen[t]);
         pass = wide || d >= fmaf(cR, cs.x, -sR * cs.y) - kDotTol;
       }
       unsigned tm = __ballot_sync(0xffffffffu, pass);
       while (tm) {
-        const int tt = t0 + __ffs(tm) - 1;
+        const int ee = e0 + __ffs(tm) - 1;
         tm &= tm - 1;
-        const int2 rg = R.trng[tt];
+        const int2 rg = R.trng[list ? list[ee] : ee];
         for (int q0 = 0; q0 < rg.y; q0 += 32) {
           const int q = q0 + lane;
           bool in = false;
@@ -182,9 +184,9 @@ __device__ void grid_cells(const RunDesc &R) {
           }
           const unsigned mm = __ballot_sync(0xffffffffu, in);
           if (FILL && in) {
-            const int e = n + __popc(mm & ((1u << lane) - 1u));
-            if (inl) rec[1 + e] = (uint16_t)(rg.x + q);
-            else R.gover[at + e] = (uint16_t)(rg.x + q);
+            const int k = n + __popc(mm & ((1u << lane) - 1u));
+            if (inl) rec[1 + k] = (uint16_t)(rg.x + q);
+            else R.gover[at + k] = (uint16_t)(rg.x + q);
           }
           n += __popc(mm);
         }
@@ -194,13 +196,66 @@ __device__ void grid_cells(const RunDesc &R) {
   if (!FILL && lane == 0) R.gcnt[cell] = n;
 }
 
+// One CTA per block of cells (kGridSpan2 cells for m = 2, kGridSpan3 x
+// kGridSpan3 for m = 3): warp 0 lists the tiles that can hold a candidate
+// of any cell of the block (the block taken as one region: every vector
+// that can be the argmax for a direction in one of its cells lies within
+// the block's radius, so its tile is listed), then the warps take the
+// block's cells, each testing only the listed tiles.  A list longer than
+// the buffer falls back to every tile.
+template <int M, bool FILL>
+__device__ void grid_block(const RunDesc &R) {
+  __shared__ int s_list[kGridBlockList];
+  __shared__ int s_n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = R.gG, span = M == 2 ? kGridSpan2 : kGridSpan3;
+  const int nbx = (G + span - 1) / span;
+  if (FILL && __ldcg(&R.ctl->grid_ver) != __ldcg(&R.ctl->v_ver)) return;   // did not fit
+  int b0[2] = {0, 0};
+  {
+    int rem = blockIdx.x;
+    for (int k = 0; k < M - 1; ++k) { b0[k] = (rem % nbx) * span; rem /= nbx; }
+  }
+  if (warp == 0) {
+    const CellGeom gb = region_geom<M>(R, b0, span, R.Vt, nullptr, R.ntiles);
+    int n = 0;
+    if (gb.live) {
+      const bool wide = gb.cosR < 0.0f;
+      for (int t0 = 0; t0 < R.ntiles; t0 += 32) {
+        const int t = t0 + lane;
+        bool pass = false;
+        if (t < R.ntiles) {
+          const float2 cs = R.tcs[t];
+          const float d = pdot<M>(gb.c, R.tcen[t]);
+          pass = wide || d >= fmaf(gb.cosR, cs.x, -gb.sinR * cs.y) - kDotTol;
+        }
+        const unsigned tm = __ballot_sync(0xffffffffu, pass);
+        const int e = n + __popc(tm & ((1u << lane) - 1u));
+        if (pass && e < kGridBlockList) s_list[e] = t;
+        n += __popc(tm);
+      }
+    }
+    if (lane == 0) s_n = gb.live ? n : -1;
+  }
+  __syncthreads();
+  const int nl = s_n;
+  if (nl < 0) return;   // the block lies outside the simplex: so do its cells
+  const bool all = nl > kGridBlockList;
+  const int per = M == 2 ? span : span * span;
+  for (int q = warp; q < per; q += nw) {
+    int ck[2] = {b0[0] + (M == 2 ? q : q % span), M == 2 ? 0 : b0[1] + q / span};
+    if (ck[0] >= G || (M == 3 && ck[1] >= G)) continue;
+    grid_one<M, FILL>(R, ck, all ? nullptr : s_list, all ? R.ntiles : nl);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_grid_count(const RunDesc *__restrict__ Rp) {
   const RunDesc &R = *Rp;
-  if (R.m == 2) grid_cells<2, false>(R); else grid_cells<3, false>(R);
+  if (R.m == 2) grid_block<2, false>(R); else grid_block<3, false>(R);
 }
 __global__ void __launch_bounds__(256) k_grid_fill(const RunDesc *__restrict__ Rp) {
   const RunDesc &R = *Rp;
-  if (R.m == 2) grid_cells<2, true>(R); else grid_cells<3, true>(R);
+  if (R.m == 2) grid_block<2, true>(R); else grid_block<3, true>(R);
 }
 
 // Exclusive scan of the overflow lists (cells with more than kGridInline

@@ -217,9 +217,11 @@ __device__ __noinline__ float mutate_sites(const RunDesc &R, const KeyRun kp, in
 }
 
 // Objectives of one child (pool row `slot`) from its g and x_1..x_{m-1} read
-// back from the row (after its mutation), and its share of the ideal point.
+// back from the row (after its mutation), and its share of the ideal point
+// (into the CTA's minimum zmin in shared memory: one atomic per child on the
+// same global words would serialise the kernel at large N).
 template <int PROB>
-__device__ __forceinline__ void evaluate_child(const RunDesc &R, int slot, float g) {
+__device__ __forceinline__ void evaluate_child(const RunDesc &R, int slot, float g, unsigned *zmin) {
   const int m = R.m, mh = m - 1, n2 = 2 * R.N;
   const float *row = R.X + (size_t)slot * R.d_pad;
   float head[kMaxM], f[kMaxM];
@@ -227,15 +229,16 @@ __device__ __forceinline__ void evaluate_child(const RunDesc &R, int slot, float
   dtlz_objectives_t<PROB>(m, g, head, f);
   for (int kk = 0; kk < m; ++kk) {
     R.F[(size_t)kk * n2 + slot] = f[kk];
-    atomicMin(&R.ctl->zkey[kk], f2ord(f[kk]));
+    atomicMin(&zmin[kk], f2ord(f[kk]));
   }
 }
 
 // A pair of a team of fewer than 32 lanes (one segment): both children.
 template <int PROB>
-__device__ __noinline__ void finish_pair(const RunDesc &R, float g1, float g2, int ch1, int ch2) {
-  evaluate_child<PROB>(R, ch1, g1);
-  if (ch2 >= 0) evaluate_child<PROB>(R, ch2, g2);
+__device__ __noinline__ void finish_pair(const RunDesc &R, float g1, float g2, int ch1, int ch2,
+                                         unsigned *zmin) {
+  evaluate_child<PROB>(R, ch1, g1, zmin);
+  if (ch2 >= 0) evaluate_child<PROB>(R, ch2, g2, zmin);
 }
 
 template <int PROB, bool STAGED, class KP>
@@ -254,6 +257,14 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
   const bool active = p < P;
   const int t = R.ctl->t;
   const int *cslot = R.child_slot + (t & 1) * N;
+  // teams of fewer than 32 lanes evaluate their children here: the CTA's
+  // minimum of their objectives, one global atomic per objective at the end
+  __shared__ unsigned s_zmin[kMaxM];
+  const bool evals = PROB != PROB_NEURO && TS < 32;   // uniform over the CTA (one run)
+  if (evals) {
+    if (threadIdx.x < kMaxM) s_zmin[threadIdx.x] = 0xFFFFFFFFu;
+    __syncthreads();
+  }
 
   // ---- phase 0: the pair's two mating draws and crossover gate ------------
   uint32_t v0 = 0, v1 = 0, v2 = 0;
@@ -397,8 +408,13 @@ __device__ __forceinline__ void repro_body(const BatchDir &dir, const KP &kp) {
       ps[seg] = gs.x;
       ps[S + seg] = gs.y;
     } else {
-      finish_pair<PROB>(R, gs.x, gs.y, ch1, ch2);
+      finish_pair<PROB>(R, gs.x, gs.y, ch1, ch2, s_zmin);
     }
+  }
+  if (evals) {
+    __syncthreads();
+    if (threadIdx.x < R.m && s_zmin[threadIdx.x] != 0xFFFFFFFFu)
+      atomicMin(&R.ctl->zkey[threadIdx.x], s_zmin[threadIdx.x]);
   }
 }
 
