@@ -185,7 +185,7 @@ Shape make_shape(int m, int d, int N) {
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
       ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, otag, occ_cnt, vcnt, zacc, Vt,
-      tperm, trng, tcen, tcs, gcell, gcnt, gover, gscale, vrange, fcomb, noise, dynA, dynB, total;
+      tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, gscale, vrange, fcomb, noise, dynA, dynB, total;
 };
 
 Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
@@ -236,6 +236,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.tcs = take(T * 8 + 16);
   L.gcell = take((size_t)s.gcells * 32);
   L.gcnt = take((size_t)s.gcells * 4);
+  L.gblk = take((size_t)(s.gG > 0 ? grid_build_blocks(s.gG, s.m) : 0) * 4);
   L.gover = take((size_t)s.gcap * 2);
   L.gscale = take(kMaxM * 4);
   L.vrange = take(kMaxM * 8);
@@ -625,12 +626,13 @@ void launch_mutate1(const rvea_run *r, cudaStream_t st) {
 // The fused tail (k_tail: mutation and evaluation, association, finalize in
 // one persistent launch) serves one run of a DTLZ problem with the pruned
 // search, when each CTA's share of the pool-row bitmap fits its buffer, its
-// children fit its mutating warps and the search tables its shared memory.
+// children fit its lanes (eight a child) and the search tables its shared
+// memory (or, past that, the tables are read through L2).
 int tail_grid(const rvea_run *r) { return std::min(r->num_sms, kTailMaxCtas); }
 bool tail_ok(const rvea_run *r) {
   return r->hd.ntiles > 0 && r->hd.problem != PROB_NEURO &&
          (2 * r->sh.N + 31) / 32 <= 64 * tail_grid(r) &&
-         (r->sh.N + 31) / 32 <= kTailMutWarps * tail_grid(r) &&
+         r->sh.N <= 4 * (kTailThreads / 32) * tail_grid(r) &&   // a group of 8 lanes a child
          (r->hd.tables_global || r->prune_smem_bytes <= g_tail_dyn_max);
 }
 // dynamic shared memory of the fused tail: the staged tables, or none
@@ -1080,6 +1082,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gcap = sh.gcap;
   D.gcell = wsp<uint16_t>(r, lay.gcell);
   D.gcnt = wsp<int>(r, lay.gcnt);
+  D.gblk = wsp<int>(r, lay.gblk);
   D.gover = wsp<uint16_t>(r, lay.gover);
   D.gscale = wsp<float>(r, lay.gscale);
   D.vrange = wsp<double>(r, lay.vrange);

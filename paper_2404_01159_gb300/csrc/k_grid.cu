@@ -11,6 +11,7 @@ constexpr float kDotTol = 3e-6f;    // float32 cosine error allowance of the bui
 constexpr float kCandEps = 2e-6f;   // 2 eps: dot error of the association relative to |f'|
 constexpr float kAngTol = 2e-5f;    // allowance for the float32 angles below (radians)
 constexpr int kGridBlockList = 512;  // tiles a block's list holds
+constexpr double kGridMaxSkew = 16.0;  // largest range ratio the grid is built for
 
 // The cell's candidate test: centre direction and cos / sin of R (float,
 // rounded outwards), or live = false for a cell that lies outside the
@@ -141,22 +142,15 @@ __device__ __forceinline__ bool support_test(const CellGeom &g, float4 v) {
 // the tiles of the list whose centre lies within R + rho_t of c, then their
 // members within R that pass the support test.
 template <int M, bool FILL>
-__device__ void grid_one(const RunDesc &R, const int *ck, const int *list, int nl) {
+__device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl, bool inl, int at) {
   const int lane = threadIdx.x & 31;
   const int cell = M == 2 ? ck[0] : ck[0] + ck[1] * R.gG;
   const float4 *Vt = R.Vt;
   const CellGeom g = region_geom<M>(R, ck, 1, Vt, list, nl);
   int n = 0;
   // inline records hold up to kGridInline candidates; longer lists go to the
-  // overflow area at the offset the scan stored in the record
+  // overflow area at offset `at`
   uint16_t *rec = R.gcell + (size_t)cell * kGridRec;
-  int at = 0;
-  bool inl = true;
-  if (FILL) {
-    const int cnt = rec[0];
-    inl = cnt <= kGridInline;
-    at = inl ? 0 : (int)((uint32_t)rec[1] | ((uint32_t)rec[2] << 16));
-  }
   if (g.live) {
     const bool wide = g.cosR < 0.0f;   // R > pi/2: every tile of the list
     const float cR = g.cosR, sR = g.sinR;
@@ -193,7 +187,11 @@ __device__ void grid_one(const RunDesc &R, const int *ck, const int *list, int n
       }
     }
   }
-  if (!FILL && lane == 0) R.gcnt[cell] = n;
+  if (!FILL && lane == 0) {
+    R.gcnt[cell] = n;
+    rec[0] = (uint16_t)min(n, 0xFFFF);
+  }
+  return n;
 }
 
 // One CTA per block of cells (kGridSpan2 cells for m = 2, kGridSpan3 x
@@ -206,11 +204,15 @@ __device__ void grid_one(const RunDesc &R, const int *ck, const int *list, int n
 template <int M, bool FILL>
 __device__ void grid_block(const RunDesc &R) {
   __shared__ int s_list[kGridBlockList];
-  __shared__ int s_n;
+  __shared__ int s_n, s_ovf;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = R.gG, span = M == 2 ? kGridSpan2 : kGridSpan3;
   const int nbx = (G + span - 1) / span;
+  if (__ldcg(&R.ctl->grid_skip)) return;   // vectors too skewed: no grid for them
   if (FILL && __ldcg(&R.ctl->grid_ver) != __ldcg(&R.ctl->v_ver)) return;   // did not fit
+  // count: this block's overflow candidates (cells past kGridInline); fill:
+  // the next free position of the block's range of the overflow area
+  if (threadIdx.x == 0) s_ovf = 0;
   int b0[2] = {0, 0};
   {
     int rem = blockIdx.x;
@@ -239,13 +241,36 @@ __device__ void grid_block(const RunDesc &R) {
   }
   __syncthreads();
   const int nl = s_n;
-  if (nl < 0) return;   // the block lies outside the simplex: so do its cells
   const bool all = nl > kGridBlockList;
   const int per = M == 2 ? span : span * span;
-  for (int q = warp; q < per; q += nw) {
-    int ck[2] = {b0[0] + (M == 2 ? q : q % span), M == 2 ? 0 : b0[1] + q / span};
-    if (ck[0] >= G || (M == 3 && ck[1] >= G)) continue;
-    grid_one<M, FILL>(R, ck, all ? nullptr : s_list, all ? R.ntiles : nl);
+  const int base = FILL ? __ldcg(R.gblk + blockIdx.x) : 0;
+  if (nl >= 0) {   // else the block lies outside the simplex, and so do its cells
+    for (int q = warp; q < per; q += nw) {
+      int ck[2] = {b0[0] + (M == 2 ? q : q % span), M == 2 ? 0 : b0[1] + q / span};
+      if (ck[0] >= G || (M == 3 && ck[1] >= G)) continue;
+      const int cell = M == 2 ? ck[0] : ck[0] + ck[1] * G;
+      bool inl = true;
+      int at = 0;
+      if (FILL) {   // an overflow cell claims its range and records it
+        const int cnt = __ldcg(R.gcnt + cell);
+        inl = cnt <= kGridInline;
+        if (!inl) {
+          if (lane == 0) at = base + atomicAdd(&s_ovf, cnt);
+          at = __shfl_sync(0xffffffffu, at, 0);
+          if (lane == 0) {
+            uint16_t *rec = R.gcell + (size_t)cell * kGridRec;
+            rec[1] = (uint16_t)(at & 0xFFFF);
+            rec[2] = (uint16_t)((uint32_t)at >> 16);
+          }
+        }
+      }
+      const int n = grid_one<M, FILL>(R, ck, all ? nullptr : s_list, all ? R.ntiles : nl, inl, at);
+      if (!FILL && lane == 0 && n > kGridInline) atomicAdd(&s_ovf, n);
+    }
+  }
+  if (!FILL) {
+    __syncthreads();
+    if (threadIdx.x == 0) R.gblk[blockIdx.x] = s_ovf;
   }
 }
 
@@ -258,18 +283,18 @@ __global__ void __launch_bounds__(256) k_grid_fill(const RunDesc *__restrict__ R
   if (R.m == 2) grid_block<2, true>(R); else grid_block<3, true>(R);
 }
 
-// Exclusive scan of the overflow lists (cells with more than kGridInline
-// candidates), one CTA; every record gets its count and, for an overflow
-// cell, its offset.  The grid is marked current for this V when the overflow
-// lists fit their buffer.
+// Exclusive scan of the blocks' overflow totals into their offsets in the
+// overflow area (in place), one CTA.  The grid is marked current for this V
+// when the overflow lists fit their buffer (and the vectors were not too
+// skewed to build it).
 __global__ void __launch_bounds__(1024) k_grid_scan(const RunDesc *__restrict__ Rp) {
   __shared__ int s_w[32];
   const RunDesc &R = *Rp;
-  const int n = R.gcells, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (__ldcg(&R.ctl->grid_skip)) return;
+  const int n = grid_build_blocks(R.gG, R.m), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int per = (n + 1023) / 1024, a0 = min(n, tid * per), a1 = min(n, a0 + per);
-  auto ovf = [&](int c) { const int k = R.gcnt[c]; return k > kGridInline ? k : 0; };
   int sum = 0;
-  for (int c = a0; c < a1; ++c) sum += ovf(c);
+  for (int c = a0; c < a1; ++c) sum += R.gblk[c];
   int incl = sum;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -290,14 +315,9 @@ __global__ void __launch_bounds__(1024) k_grid_scan(const RunDesc *__restrict__ 
   __syncthreads();
   int run = (warp > 0 ? s_w[warp - 1] : 0) + incl - sum;
   for (int c = a0; c < a1; ++c) {
-    uint16_t *rec = R.gcell + (size_t)c * kGridRec;
-    const int k = R.gcnt[c];
-    rec[0] = (uint16_t)min(k, 0xFFFF);
-    if (k > kGridInline) {
-      rec[1] = (uint16_t)(run & 0xFFFF);
-      rec[2] = (uint16_t)((uint32_t)run >> 16);
-      run += k;
-    }
+    const int k = R.gblk[c];
+    R.gblk[c] = run;
+    run += k;
   }
   if (tid == 1023) {
     const int total = s_w[31];
@@ -306,9 +326,21 @@ __global__ void __launch_bounds__(1024) k_grid_scan(const RunDesc *__restrict__ 
 }
 
 // Grid scale w = 1 / range of the last adaptation (1 before any), as float.
+// The build is skipped (grid_skip) when the ranges differ by more than
+// kGridMaxSkew: the candidate lists then grow long (the vectors crowd into
+// part of the cells), the build costs more than the lookups save, and the
+// search falls back to the tiles.
 __global__ void k_grid_scale(const RunDesc *__restrict__ Rp) {
   const RunDesc &R = *Rp;
   if (threadIdx.x < R.m) R.gscale[threadIdx.x] = (float)(1.0 / R.vrange[threadIdx.x]);
+  if (threadIdx.x == 0) {
+    double lo = R.vrange[0], hi = R.vrange[0];
+    for (int k = 1; k < R.m; ++k) {
+      lo = fmin(lo, R.vrange[k]);
+      hi = fmax(hi, R.vrange[k]);
+    }
+    R.ctl->grid_skip = hi > kGridMaxSkew * lo ? 1 : 0;
+  }
 }
 
 }  // namespace rvea

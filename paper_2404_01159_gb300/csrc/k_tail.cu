@@ -87,27 +87,9 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned nb) {
   return s_ok != 0;
 }
 
-// Phase A: mutation and evaluation of the children (the same draws and
-// operations as k_mutate).  Warp w < kTailMutWarps of CTA b owns the 32
-// children of child-warp cw = w nb + b.  Before the wait for the
-// reproduction kernel (nothing there reads its output): each lane draws its
-// child's site count, the warp lays the sites out in shared memory (Floyd's
-// sampler per child) and draws their magnitudes one site a lane.  After the
-// wait the warp mutates the sites one a lane -- a child with several sites
-// does not hold up the others -- and each lane evaluates its child.  A warp
-// whose sites overflow its list (kTailSites, about 8 times the mean) takes a
-// per-lane path instead.
-constexpr int kTailSites = 256;
-
-struct TailMut {
-  uint32_t j[kTailMutWarps][kTailSites];   // site variable
-  float dg[kTailMutWarps][kTailSites];     // magnitude, then term(new) - term(old)
-  uint8_t own[kTailMutWarps][kTailSites];  // lane of the child
-  int slot[kTailMutWarps][32];
-};
-
-// Per-lane path of a warp whose site list overflowed: the draws again, the
-// mutations one after another; returns the change of the child's g sum.
+// Phase A (the same draws and operations as k_mutate): the path of a child
+// with more sites than its group has lanes: the draws again, the mutations
+// one after another; returns the change of the child's g sum.
 template <int PROB, int M>
 __device__ __noinline__ float child_serial(const RunDesc &R, const KeyRun kr, int cd, int t,
                                            int slot, int k) {
@@ -174,7 +156,6 @@ __device__ __forceinline__ void warp_compact_by(GetW getw, int w0, int w1, int *
 // instances.
 struct TailShared {
   RunDesc desc;
-  TailMut mut;
   uint64_t bar;
   unsigned lo[kMaxM], hi[kMaxM];
   int red[2][32];
@@ -193,7 +174,6 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   uint64_t &s_bar = S.bar;
   unsigned *const s_lo = S.lo, *const s_hi = S.hi;
   int (*const s_red)[32] = S.red;
-  TailMut &sm = S.mut;
   const int N = R.N, n2 = 2 * N, m = R.m, T = R.ntiles;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = gridDim.x, b = blockIdx.x;
@@ -209,30 +189,16 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   const float4 *sC = gtab ? R.tcen : reinterpret_cast<const float4 *>(smem + bV);
   const float2 *sCS = gtab ? R.tcs : reinterpret_cast<const float2 *>(smem + bV + bC);
   const int2 *sR = gtab ? R.trng : reinterpret_cast<const int2 *>(smem + bV + bC + bSr);
-  if (!gtab) {
-    if (tid == 0) {
-      mbar_init(&s_bar, 1);
-      fence_mbar_init();
-      mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
-      tma_load_1d(smem, R.Vt, bV, &s_bar);
-      tma_load_1d(smem + bV, R.tcen, bC, &s_bar);
-      tma_load_1d(smem + bV + bC, R.tcs, bSr, &s_bar);
-      tma_load_1d(smem + bV + bC + bSr, R.trng, bSr, &s_bar);
-    }
-    __syncthreads();
-    const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
-    if (__syncthreads_or(!staged)) {
-      // a copy never arrived: flag it, let the copies land, give up (the
-      // other CTAs' barriers then time out and report the same status)
-      if (tid == 0) {
-        set_status(ctl, ST_TIMEOUT);
-        mbar_wait(&s_bar, 0u, kWaitLimit);
-      }
-      __syncthreads();
-      return;
-    }
+  // (the copies land while phase A runs: phase B is the first to read them)
+  if (!gtab && tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(&s_bar, bV + bC + 2 * bSr);
+    tma_load_1d(smem, R.Vt, bV, &s_bar);
+    tma_load_1d(smem + bV, R.tcen, bC, &s_bar);
+    tma_load_1d(smem + bV + bC, R.tcs, bSr, &s_bar);
+    tma_load_1d(smem + bV + bC + bSr, R.trng, bSr, &s_bar);
   }
-  const float2 csb = tile_bounds(sCS, T);
   // the generation index and the child slots were written by the previous
   // generation's tail, which completed before the reproduction kernel (this
   // grid's predecessor) passed its own wait; read through L2
@@ -257,55 +223,50 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
       S.zpar[q] = tail_mut && q < M ? __ldcg(&ctl->zkey[q]) : 0xFFFFFFFFu;
     }
   }
-  const int cw = warp * nb + b, cd0 = 32 * cw, cd = cd0 + lane;
-  const bool mwarp = tail_mut && warp < kTailMutWarps && cd0 < N;
-  int slot = -1, k = 0, off = 0, total = 0;
-  if (mwarp) {
-    if (cd < N) {
-      slot = __ldcg(R.child_slot + (t & 1) * N + cd);
-      if (slot < 0 || slot >= n2) { set_status(ctl, ST_BADINDEX); slot = -1; }
+  // Phase A takes each child with a group of eight lanes (four children a
+  // warp, spread over the CTAs first).  Before the wait: the child's slot,
+  // its site count and sites (Floyd's sampler, every lane of the group
+  // computing the same draws and lane i keeping site i) and lane i's
+  // magnitude; a child with more than eight sites is left to lane 0 alone
+  // after the wait.
+  const int sub = lane & 7, gl = lane & 24;
+  const int cd = 4 * (warp * nb + b) + (lane >> 3);   // this group's child
+  const bool child = tail_mut && cd < N;
+  int slot = -1, k = 0;
+  if (child) {
+    slot = __ldcg(R.child_slot + (t & 1) * N + cd);
+    if (slot < 0 || slot >= n2) {
+      if (sub == 0) set_status(ctl, ST_BADINDEX);
+      slot = -1;
     }
-    sm.slot[warp][lane] = slot;
     if (slot >= 0 && R.T_m > 0 && R.T_m < (1u << 24)) {
       const uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
       const int nthr = R.n_mthr;
       while (k < nthr && w.x >= R.mthr[k]) ++k;
     }
-    int incl = k;   // warp prefix of the counts: this child's entries start at off
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+  }
+  const bool ovf = k > 8;                 // the child's sites do not fit its lanes
+  const int kin = ovf ? 0 : k;
+  const int kmax = __reduce_max_sync(0xffffffffu, kin);
+  uint32_t js = 0u;                        // site sub of the child (sub < kin)
+  {
+    uint4 w = kin > 0 ? philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr) : make_uint4(0, 0, 0, 0);
+    for (int i = 0; i < kmax; ++i) {       // every lane of the warp takes every step
+      const int e = i + 1;
+      if ((e & 3) == 0 && i < kin)
+        w = philox_k((uint32_t)(e >> 2), (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
+      const uint32_t J = (uint32_t)(R.d - kin + i);
+      uint32_t r = i < kin ? __umulhi(word(w, e & 3), J + 1u) : 0u;
+      const bool hit = sub < i && js == r;   // drawn already by this child
+      if ((__ballot_sync(0xffffffffu, hit) >> gl) & 0xFFu) r = J;
+      if (sub == i) js = r;
     }
-    off = incl - k;
-    total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total <= kTailSites) {
-      if (k > 0) {
-        uint32_t *const js = sm.j[warp] + off;
-        uint4 w = philox_k(0u, (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
-        for (int i = 0; i < k; ++i) {
-          const int e = i + 1;
-          if ((e & 3) == 0)
-            w = philox_k((uint32_t)(e >> 2), (uint32_t)cd, (uint32_t)t, TAG_MUTSITE, kr);
-          const uint32_t J = (uint32_t)(R.d - k + i);
-          uint32_t r = __umulhi(word(w, e & 3), J + 1u);
-          for (int l = 0; l < i; ++l)
-            if (js[l] == r) { r = J; break; }
-          js[i] = r;
-          sm.own[warp][off + i] = (uint8_t)lane;
-        }
-      }
-      if (R.rec_sites && slot >= 0) {
-        int *const rec = R.rec_sites + (size_t)cd * (1 + kMaxSites);
-        rec[0] = R.T_m >= (1u << 24) ? -1 : k;
-        for (int i = 0; i < k; ++i) rec[1 + i] = (int)sm.j[warp][off + i];
-      }
-      __syncwarp();
-      for (int e = lane; e < total; e += 32)   // the magnitudes
-        sm.dg[warp][e] = u24f(philox_k(sm.j[warp][e], (uint32_t)(cd0 + sm.own[warp][e]),
-                                       (uint32_t)t, TAG_MUTMAG, kr).y);
-      __syncwarp();
-    }
+  }
+  const float mag = sub < kin ? u24f(philox_k(js, (uint32_t)cd, (uint32_t)t, TAG_MUTMAG, kr).y) : 0.0f;
+  if (R.rec_sites && slot >= 0 && !ovf) {
+    int *const rec = R.rec_sites + (size_t)cd * (1 + kMaxSites);
+    if (sub == 0) rec[0] = R.T_m >= (1u << 24) ? -1 : k;
+    if (sub < kin) rec[1 + sub] = (int)js;
   }
 
   pdl_wait();   // the reproduction kernel's children
@@ -315,56 +276,56 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   if (b == 0)
     for (int q = tid; q < nb; q += kTailThreads) R.occ_cnt[q] = 0u;
   __syncthreads();
-  if (tail_mut) {
-    if (mwarp) {
-      // this child's segment partials and position variables, loaded while
-      // the warp mutates
-      float g = 0.0f, head[M > 1 ? M - 1 : 1];
-      float *const row = slot >= 0 ? R.X + (size_t)slot * R.d_pad : nullptr;
-      if (slot >= 0) {
-        const int S = R.nseg, p = cd < R.P ? cd : cd - R.P;
-        const float *ps = R.psum + (size_t)p * 2 * S + (cd < R.P ? 0 : S);
-#pragma unroll 4
-        for (int q = 0; q < S; ++q) g += __ldcg(ps + q);
+  if (tail_mut && cd - (lane >> 3) < N) {   // a warp with at least one child (warp-uniform)
+    const bool live = slot >= 0;
+    float *const row = live ? R.X + (size_t)slot * R.d_pad : nullptr;
+    // the pair's segment partials, added in segment order (lanes load eight
+    // at a time, every lane adds); the position variables
+    const int S = R.nseg, pp = cd < R.P ? cd : cd - R.P;
+    const float *ps = R.psum + (size_t)pp * 2 * S + (cd < R.P ? 0 : S);
+    float g = 0.0f;
+    for (int q0 = 0; q0 < S; q0 += 8) {
+      const float v = live && q0 + sub < S ? __ldcg(ps + q0 + sub) : 0.0f;
+      for (int u = 0; u < 8 && q0 + u < S; ++u) g += __shfl_sync(0xffffffffu, v, gl | u);
+    }
+    float hv = live && sub < M - 1 ? __ldcg(row + sub) : 0.0f;
+    // the mutations, site i on lane i of the group
+    float dgi = 0.0f;
+    bool hhit = false;
+    if (live && sub < kin) {
+      float *const px = row + js;
+      const float x = __ldcg(px);
+      const float xn = poly_mutate(x, mag, R.L, R.U, R.eta_m);
+      __stcg(px, xn);
+      dgi = (int)js >= M - 1 ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f) : 0.0f;
+      hhit = (int)js < M - 1;
+    }
+    float dg = 0.0f;   // the term changes in draw order
+    for (int i = 0; i < kmax; ++i) {
+      const float v = __shfl_sync(0xffffffffu, dgi, gl | i);
+      if (i < kin) dg += v;
+    }
+    if (live && ovf && sub == 0) {
+      dg = child_serial<PROB, M>(R, kr, cd, t, slot, k);
+      hhit = true;
+    }
+    // a site among x_1..x_{m-1}: read them back, mutated
+    const bool ghit = ((__ballot_sync(0xffffffffu, hhit) >> gl) & 0xFFu) != 0u;
+    __syncwarp();   // the group's stores above are visible to its lanes
+    if (ghit && live && sub < M - 1) hv = __ldcg(row + sub);
+    dg = __shfl_sync(0xffffffffu, dg, gl);
+    float head[M > 1 ? M - 1 : 1];
 #pragma unroll
-        for (int jj = 0; jj < M - 1; ++jj) head[jj] = __ldcg(row + jj);
-      }
-      float dg = 0.0f;
-      bool head_hit = false;
-      if (total <= kTailSites) {
-        for (int e = lane; e < total; e += 32) {   // the mutations, one site a lane
-          const int o = sm.own[warp][e];
-          const uint32_t j = sm.j[warp][e];
-          float *const px = R.X + (size_t)sm.slot[warp][o] * R.d_pad + j;
-          const float x = __ldcg(px);
-          const float xn = poly_mutate(x, sm.dg[warp][e], R.L, R.U, R.eta_m);
-          __stcg(px, xn);
-          sm.dg[warp][e] = (int)j >= M - 1 ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f)
-                                           : 0.0f;
-        }
-        __syncwarp();   // the mutated rows and term changes are visible to the warp
-        for (int i = 0; i < k; ++i) {
-          dg += sm.dg[warp][off + i];
-          head_hit |= (int)sm.j[warp][off + i] < M - 1;
-        }
-      } else if (slot >= 0) {
-        dg = child_serial<PROB, M>(R, kr, cd, t, slot, k);
-        head_hit = true;
-      }
-      if (slot >= 0) {
-        if (head_hit) {   // a site among x_1..x_{m-1}: read them back, mutated
+    for (int jj = 0; jj < M - 1; ++jj) head[jj] = __shfl_sync(0xffffffffu, hv, gl | jj);
+    if (live && sub == 0) {
+      float f[M];
+      dtlz_objectives_t<PROB>(M, g + dg, head, f);
+      float *const fc = R.fcomb + (size_t)(t & 1) * M * n2 + N + cd;
 #pragma unroll
-          for (int jj = 0; jj < M - 1; ++jj) head[jj] = __ldcg(row + jj);
-        }
-        float f[M];
-        dtlz_objectives_t<PROB>(M, g + dg, head, f);
-        float *const fc = R.fcomb + (size_t)(t & 1) * M * n2 + N + cd;
-#pragma unroll
-        for (int kk = 0; kk < M; ++kk) {
-          R.F[(size_t)kk * n2 + slot] = f[kk];
-          fc[(size_t)kk * n2] = f[kk];
-          atomicMin(&s_lo[kk], f2ord(f[kk]));
-        }
+      for (int kk = 0; kk < M; ++kk) {
+        R.F[(size_t)kk * n2 + slot] = f[kk];
+        fc[(size_t)kk * n2] = f[kk];
+        atomicMin(&s_lo[kk], f2ord(f[kk]));
       }
     }
   }
@@ -375,17 +336,46 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   if (tid < 4) R.zacc[b * 4 + tid] = s_lo[tid];
   if (!grid_barrier(ctl, nb)) return;
   if (tid < kMaxM) s_lo[tid] = 0xFFFFFFFFu;   // for the survivors' minimum in C
+  if (!gtab) {   // the tables staged in the prologue
+    const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
+    if (__syncthreads_or(!staged)) {
+      // a copy never arrived: flag it, let the copies land, give up (the
+      // other CTAs' next barrier then times out and reports the same status)
+      if (tid == 0) {
+        set_status(ctl, ST_TIMEOUT);
+        mbar_wait(&s_bar, 0u, kWaitLimit);
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  const float2 csb = tile_bounds(sCS, T);
 
   // ---- B: association and APD votes ----------------------------------------
   {
     if (warp == 0) {   // z* = min(the parents' z*, every CTA's children)
-      // entry e of plane 0 is objective e % 4 of CTA e / 4; lane l takes the
-      // entries e = l (mod 32), all of objective l % 4
-      unsigned zl = lane < 4 ? (tail_mut ? S.zpar[lane] : __ldcg(&ctl->zkey[lane])) : 0xFFFFFFFFu;
-      for (int e = lane; e < 4 * nb; e += 32) zl = min(zl, __ldcg(R.zacc + e));
+      // lane l reads the four minima of CTAs l, l + 32, ... (all loads in
+      // flight together: nb <= kTailMaxCtas = 8 x 32)
+      uint4 v[kTailMaxCtas / 32];
 #pragma unroll
-      for (int o = 4; o < 32; o <<= 1) zl = min(zl, __shfl_xor_sync(0xffffffffu, zl, o));
-      if (lane < 4) S.z[lane] = zl;
+      for (int i = 0; i < kTailMaxCtas / 32; ++i) {
+        const int q = lane + 32 * i;
+        v[i] = q < nb ? __ldcg(reinterpret_cast<const uint4 *>(R.zacc) + q)
+                      : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+      }
+      unsigned z0 = v[0].x, z1 = v[0].y, z2 = v[0].z, z3 = v[0].w;
+#pragma unroll
+      for (int i = 1; i < kTailMaxCtas / 32; ++i) {
+        z0 = min(z0, v[i].x); z1 = min(z1, v[i].y); z2 = min(z2, v[i].z); z3 = min(z3, v[i].w);
+      }
+      z0 = __reduce_min_sync(0xffffffffu, z0);
+      z1 = __reduce_min_sync(0xffffffffu, z1);
+      z2 = __reduce_min_sync(0xffffffffu, z2);
+      z3 = __reduce_min_sync(0xffffffffu, z3);
+      if (lane < 4) {
+        const unsigned zp = tail_mut ? S.zpar[lane] : __ldcg(&ctl->zkey[lane]);
+        S.z[lane] = min(zp, lane == 0 ? z0 : lane == 1 ? z1 : lane == 2 ? z2 : z3);
+      }
     }
     const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
     __syncthreads();

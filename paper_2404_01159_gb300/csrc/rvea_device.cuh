@@ -27,7 +27,6 @@ constexpr int kStageWarpBytes = kStages * 2 * 1024;   // per warp: kStages x 2 p
 constexpr int kStagedSmem = (kReproThreads / 32) * (kStageWarpBytes + kStages * 8);
 constexpr int kTailThreads = 1024;  // CTA size of the fused tail kernel (one CTA per SM)
 constexpr int kTailMaxCtas = 256;   // its largest grid
-constexpr int kTailMutWarps = 8;    // its warps per CTA that mutate (32 children each)
 
 // Philox counter tags (word 3 of the counter).
 enum : uint32_t {
@@ -57,6 +56,7 @@ struct Ctl {
   int v_ver;           // changes of V so far (adaptation, import)
   int fcomb_t;         // generation whose combined objectives fcomb holds (0: none)
   int grid_ver;        // the v_ver the direction grid was built for (-1: none)
+  int grid_skip;       // 1: the current vectors are too skewed for the grid (not built)
   unsigned long long bar;   // grid barrier of the fused tail kernel: arrivals
                             // since initialisation (a multiple of its grid
                             // between launches)
@@ -117,6 +117,8 @@ struct RunDesc {
   uint16_t *gcell;     // [gcells][16] record: count, then up to 15 tile-order positions
                        //              (or, past 15, the offset of the list in gover)
   int *gcnt;           // [gcells]     candidates of each cell (build)
+  int *gblk;           // [build blocks] overflow candidates of each block of cells, then
+                       //              their offset in gover
   uint16_t *gover;     // [gcap]       candidate lists of the cells with more than 15
   float *gscale;       // [kMaxM]      w = 1 / range of the grid's V
   double *vrange;      // [kMaxM]      objective range of the last adaptation (1: none)

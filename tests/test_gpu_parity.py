@@ -79,8 +79,10 @@ def test_teacher_forced_generations(orc, shape):
 
 # Mutation rates other than one site per row: several sites per row (p_m = 4
 # and the largest accepted, 8, with sites in every segment of a staged row)
-# and every site (p_m = d).
+# and every site (p_m = d); the fused tail with p_m = 8 (children with
+# more sites than their group of eight lanes take the one-lane path).
 @pytest.mark.parametrize("shape,p_m", [((3, 300, 105, 13, 1), 8.0),
+                                       ((3, 2500, 1275, 49, 1), 8.0),
                                        ((3, 2500, 105, 13, 0), 4.0),
                                        ((3, 40, 105, 13, 0), 40.0),
                                        ((2, 1500, 100, 99, 1), 1500.0)])
