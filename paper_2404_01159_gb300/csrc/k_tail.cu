@@ -165,6 +165,7 @@ struct TailShared {
   unsigned zr[8];         // survivors' minimum (0..3) and maximum (4..7)
   unsigned zpar[4];       // the parents' z*, read before the dependency wait
   float gw[4];            // direction-grid scale of the current vectors
+  float pen;              // the APD penalty M (t / t_max)^alpha (Eq. 4)
   int grid_ok;            // the direction grid matches the current vectors
 };
 
@@ -217,6 +218,7 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   // whether the direction grid matches the vectors (its build ran after the
   // previous tail) with its scale.
   if (tid == 0) {
+    S.pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
     S.grid_ok = M <= 3 && R.gG > 0 && __ldcg(&ctl->grid_ver) == __ldcg(&ctl->v_ver);
     for (int q = 0; q < 4; ++q) {
       S.gw[q] = q < M && M <= 3 && R.gG > 0 ? __ldcg(R.gscale + q) : 1.0f;
@@ -336,26 +338,12 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   if (tid < 4) R.zacc[b * 4 + tid] = s_lo[tid];
   if (!grid_barrier(ctl, nb)) return;
   if (tid < kMaxM) s_lo[tid] = 0xFFFFFFFFu;   // for the survivors' minimum in C
-  if (!gtab) {   // the tables staged in the prologue
-    const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
-    if (__syncthreads_or(!staged)) {
-      // a copy never arrived: flag it, let the copies land, give up (the
-      // other CTAs' next barrier then times out and reports the same status)
-      if (tid == 0) {
-        set_status(ctl, ST_TIMEOUT);
-        mbar_wait(&s_bar, 0u, kWaitLimit);
-      }
-      __syncthreads();
-      return;
-    }
-  }
-  const float2 csb = tile_bounds(sCS, T);
-
   // ---- B: association and APD votes ----------------------------------------
   {
     if (warp == 0) {   // z* = min(the parents' z*, every CTA's children)
       // lane l reads the four minima of CTAs l, l + 32, ... (all loads in
-      // flight together: nb <= kTailMaxCtas = 8 x 32)
+      // flight together, nb <= kTailMaxCtas = 8 x 32, and in flight while
+      // the CTA waits for its tables below)
       uint4 v[kTailMaxCtas / 32];
 #pragma unroll
       for (int i = 0; i < kTailMaxCtas / 32; ++i) {
@@ -377,7 +365,20 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
         S.z[lane] = min(zp, lane == 0 ? z0 : lane == 1 ? z1 : lane == 2 ? z2 : z3);
       }
     }
-    const float pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
+    if (!gtab) {   // the tables staged in the prologue
+      const bool staged = mbar_wait(&s_bar, 0u, kWaitLimit);
+      if (__syncthreads_or(!staged)) {
+        // a copy never arrived: flag it, let the copies land, give up (the
+        // other CTAs' next barrier then times out and reports the same status)
+        if (tid == 0) {
+          set_status(ctl, ST_TIMEOUT);
+          mbar_wait(&s_bar, 0u, kWaitLimit);
+        }
+        __syncthreads();
+        return;
+      }
+    }
+    const float pen = S.pen;
     __syncthreads();
     float z[4];
 #pragma unroll
@@ -391,7 +392,8 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
       const int gw = warp * nb + b, nw = nb * (kTailThreads / 32);
       for (int g = gw; 4 * g < R.n_comb; g += nw)
         grid_assoc8<M <= 3 ? M : 3>(R, 4 * g + (lane >> 3), sV, z, w, pen, fcur);
-    } else {
+    } else {   // the tile search (a CTA-uniform branch)
+      const float2 csb = tile_bounds(sCS, T);
       const int groups = (R.n_comb + 3) >> 2, gw = warp * nb + b, nw = nb * (kTailThreads / 32);
       for (int g = gw; g < groups; g += nw) prune_group<M, false>(R, 4 * g, sV, sC, sCS, sR, z, pen, csb);
     }
@@ -414,11 +416,18 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     for (int vw = v0 + warp; vw < v1; vw += kTailThreads / 32) {
       const int j = 32 * vw + lane;
       int s = -1, i = -1;
+      float fci[M];   // the winner's objectives by combined index, loaded with its slot
+#pragma unroll
+      for (int k = 0; k < M; ++k) fci[k] = 0.0f;
       if (j < N) {
         const unsigned long long key = __ldcg(R.best + j);
         R.best[j] = ~0ull;
         if (key != ~0ull) {
           i = (int)(uint32_t)(key & 0xFFFFFFFFull);
+          if (fcur && i >= 0 && i < n2) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) fci[k] = __ldcg(fcur + (size_t)k * n2 + i);
+          }
           if (i >= 0 && i < N) s = cur[i];
           else if (i >= N && i < n2) s = ccur[i - N];
           if (s < 0 || s >= n2) { set_status(ctl, ST_BADINDEX); s = -1; i = -1; }
@@ -438,7 +447,7 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
         unsigned lo = 0xFFFFFFFFu, hi = 0u;
         float fv = __int_as_float(0x7fffffff);   // NaN: an invalid slot of P_{t+1}
         if (s >= 0) {
-          fv = fcur ? __ldcg(fcur + (size_t)k * n2 + i) : __ldcg(R.F + (size_t)k * n2 + s);
+          fv = fcur ? fci[k] : __ldcg(R.F + (size_t)k * n2 + s);
           lo = hi = f2ord(fv);
         }
         if (j < N) fnext[(size_t)k * n2 + j] = fv;
