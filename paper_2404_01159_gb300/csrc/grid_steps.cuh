@@ -135,17 +135,23 @@ __device__ __forceinline__ void grid_assoc(const RunDesc &R, int i, const float4
   atomicMin(&R.best[bj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
 }
 
-// The same association with eight lanes per solution (lanes 8g .. 8g+7 of a
-// warp take solution i of group g; every lane of the warp must call it):
-// each lane scans two of the cell's candidates and fetches, for the better
-// one, the float remainder of the vector and gamma, so that after the group
-// reduces (larger dot, then smaller index) the lane holding the winner
-// computes the APD and votes without another round trip.
-template <int M>
-__device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float4 *sV,
+// The same association with L = 8 or 4 lanes per solution (lanes L g ..
+// L g + L - 1 of a warp take solution i of group g; every lane of the warp
+// must call it): each lane scans the candidates e = sub, sub + L, ... of the
+// cell and fetches, for its best one, the float remainder of the vector and
+// gamma, so that after the group reduces (larger dot, then smaller index)
+// the lane holding the winner computes the APD and votes without another
+// round trip.  Four lanes serve twice as many solutions a warp, for when
+// eight would leave warps with a second round.
+template <int M, int L = 8>
+__device__ __forceinline__ void grid_assocL(const RunDesc &R, int i, const float4 *sV,
                                             const float *z, const float *w, float pen,
                                             const float *fc) {
-  const int N = R.N, n = R.n_comb, lane = threadIdx.x & 31, sub = lane & 7, gb = lane & 24;
+  static_assert(L == 8 || L == 4, "8 or 4 lanes per solution");
+  constexpr int NW = 8 / L;                  // record words a lane holds
+  constexpr int NE = (kGridInline + L - 1) / L;   // inline candidates a lane scans
+  const int N = R.N, n = R.n_comb, lane = threadIdx.x & 31, sub = lane & (L - 1),
+            gb = lane & ~(L - 1);
   const bool act = i < n;
   float f[4] = {0.f, 0.f, 0.f, 0.f};
   bool valid = false;
@@ -171,27 +177,39 @@ __device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float
 #pragma unroll
   for (int k = 1; k < M; ++k) s2 = fmaf(f[k], f[k], s2);
   const bool live = act && valid && sqrtf(s2) > 0.0f;
-  // the cell record, one 4-byte word per lane of the group
-  uint32_t wd = 0;
+  // the cell record, words sub, sub + L of it on this lane
+  uint32_t wd[NW];
+#pragma unroll
+  for (int u = 0; u < NW; ++u) wd[u] = 0u;
   if (live) {
     const int cell = grid_cell<M>(f, w, R.gG);
-    wd = __ldg(reinterpret_cast<const uint32_t *>(R.gcell + (size_t)cell * kGridRec) + sub);
+    const uint32_t *rw = reinterpret_cast<const uint32_t *>(R.gcell + (size_t)cell * kGridRec);
+#pragma unroll
+    for (int u = 0; u < NW; ++u) wd[u] = __ldg(rw + sub + L * u);
   }
   // every lane takes part in every shuffle (groups of one warp may take
   // different branches below, which hold no warp-wide operation)
-  const uint32_t w0 = __shfl_sync(0xffffffffu, wd, gb);
-  const uint32_t w1 = __shfl_sync(0xffffffffu, wd, gb | 1);
-  uint32_t we[2];
+  const uint32_t w0 = __shfl_sync(0xffffffffu, wd[0], gb);
+  const uint32_t w1 = __shfl_sync(0xffffffffu, wd[0], gb | 1);
+  uint32_t we[NE];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)   // the word of element e + 1, e = sub + 8 h (e <= 14 used)
-    we[h] = __shfl_sync(0xffffffffu, wd, gb | min(7, (sub + 8 * h + 1) >> 1));
+  for (int h = 0; h < NE; ++h) {   // the word of element e + 1, e = sub + L h (e <= 14 used)
+    const int wi = min(7, (sub + L * h + 1) >> 1);
+    uint32_t got = 0u;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) {
+      const uint32_t x = __shfl_sync(0xffffffffu, wd[u], gb | (wi & (L - 1)));
+      if (wi / L == u) got = x;
+    }
+    we[h] = got;
+  }
   const int cnt = live ? (int)(w0 & 0xFFFFu) : 0;
   float best = -INFINITY;
   int bj = 0x7FFFFFFF, bq = -1;
   if (cnt <= kGridInline) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = sub + 8 * h;   // element e + 1 of the record
+    for (int h = 0; h < NE; ++h) {
+      const int e = sub + L * h;   // element e + 1 of the record
       if (e < cnt) {
         const int q = (int)((we[h] >> (16 * ((e + 1) & 1))) & 0xFFFFu);
         const float4 v = sV[q];
@@ -202,7 +220,7 @@ __device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float
     }
   } else {
     const int at = (int)((w0 >> 16) | ((w1 & 0xFFFFu) << 16));
-    for (int e = sub; e < cnt; e += 8) {
+    for (int e = sub; e < cnt; e += L) {
       const int q = R.gover[at + e];
       const float4 v = sV[q];
       const int j = __float_as_int(v.w);
@@ -220,7 +238,7 @@ __device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float
   float gbest = best;
   int gbj = bj;
 #pragma unroll
-  for (int off = 1; off < 8; off <<= 1) {
+  for (int off = 1; off < L; off <<= 1) {
     const float od = __shfl_xor_sync(0xffffffffu, gbest, off);
     const int oj = __shfl_xor_sync(0xffffffffu, gbj, off);
     if (od > gbest || (od == gbest && oj < gbj)) { gbest = od; gbj = oj; }
@@ -248,6 +266,14 @@ __device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float
     R.assoc[i] = gbj;
     atomicMin(&R.best[gbj], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
   }
+}
+
+// Eight lanes per solution.
+template <int M>
+__device__ __forceinline__ void grid_assoc8(const RunDesc &R, int i, const float4 *sV,
+                                            const float *z, const float *w, float pen,
+                                            const float *fc) {
+  grid_assocL<M, 8>(R, i, sV, z, w, pen, fc);
 }
 
 }  // namespace rvea

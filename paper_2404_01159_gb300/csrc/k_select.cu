@@ -63,53 +63,62 @@ __device__ __forceinline__ float2 dotv2(const float2 *fab, const float4 *v) {
   return d;
 }
 
-// Chunk scan for two solutions: the running maximum of each 32-vector
-// sub-tile costs one fmaxf per dot; a sub-tile replaces the best only on a
-// strict improvement, so `sub` is the first sub-tile holding the maximum.
-template <int M>
-__device__ void scan_chunk(const float4 *__restrict__ sv, int nv, const float *fpa,
-                           const float *fpb, float &besta, int &suba, float &bestb, int &subb) {
-  constexpr int M4 = (M + 3) / 4;
-  float2 fab[M];
-#pragma unroll
-  for (int k = 0; k < M; ++k) fab[k] = make_float2(fpa[k], fpb[k]);
+// Chunk scan for W solutions of a thread, two per packed instruction: the
+// running maximum of each 32-vector sub-tile costs one fmaxf per dot; a
+// sub-tile replaces the best only on a strict improvement, so `bsub` is the
+// first sub-tile holding the maximum.  Every loaded vector serves all W
+// solutions.
+template <int M, int W>
+__device__ void scan_chunk(const float4 *__restrict__ sv, int nv, const float2 (*fab)[M],
+                           float *best, int *bsub) {
+  constexpr int M4 = (M + 3) / 4, NP = W / 2;
   for (int sub = 0; sub * 32 < nv; ++sub) {
     const int n = min(32, nv - sub * 32);
     const float4 *p = sv + (size_t)sub * 32 * M4;
-    float ma = -INFINITY, mb = -INFINITY;
+    float mx[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) mx[q] = -INFINITY;
     if (n == 32) {
-#pragma unroll 8
+#pragma unroll 4
       for (int jj = 0; jj < 32; ++jj) {
         float4 v[M4];
 #pragma unroll
         for (int q = 0; q < M4; ++q) v[q] = p[jj * M4 + q];
-        const float2 d = dotv2<M>(fab, v);
-        ma = fmaxf(ma, d.x);
-        mb = fmaxf(mb, d.y);
+#pragma unroll
+        for (int h = 0; h < NP; ++h) {
+          const float2 d = dotv2<M>(fab[h], v);
+          mx[2 * h] = fmaxf(mx[2 * h], d.x);
+          mx[2 * h + 1] = fmaxf(mx[2 * h + 1], d.y);
+        }
       }
     } else {
       for (int jj = 0; jj < n; ++jj) {
         float4 v[M4];
 #pragma unroll
         for (int q = 0; q < M4; ++q) v[q] = p[jj * M4 + q];
-        const float2 d = dotv2<M>(fab, v);
-        ma = fmaxf(ma, d.x);
-        mb = fmaxf(mb, d.y);
+#pragma unroll
+        for (int h = 0; h < NP; ++h) {
+          const float2 d = dotv2<M>(fab[h], v);
+          mx[2 * h] = fmaxf(mx[2 * h], d.x);
+          mx[2 * h + 1] = fmaxf(mx[2 * h + 1], d.y);
+        }
       }
     }
-    if (ma > besta) { besta = ma; suba = sub; }
-    if (mb > bestb) { bestb = mb; subb = sub; }
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (mx[q] > best[q]) { best[q] = mx[q]; bsub[q] = sub; }
   }
 }
 
-// First vector of sub-tile `sub` whose dot equals `best` (same arithmetic).
-template <int M>
-__device__ int find_first(const float4 *__restrict__ sv, int nv, int sub, const float *fpin,
+// First vector of sub-tile `sub` whose dot equals `best` (the same
+// arithmetic: lane Y of the packed pair is the solution).
+template <int M, bool Y>
+__device__ int find_first(const float4 *__restrict__ sv, int nv, int sub, const float2 *fab,
                           float best) {
   constexpr int M4 = (M + 3) / 4;
   float fp[M];
 #pragma unroll
-  for (int k = 0; k < M; ++k) fp[k] = fpin[k];
+  for (int k = 0; k < M; ++k) fp[k] = Y ? fab[k].y : fab[k].x;
   const int j0 = sub * 32, j1 = min(nv, j0 + 32);
   for (int jj = j0; jj < j1; ++jj) {
     float4 v[M4];
@@ -118,38 +127,6 @@ __device__ int find_first(const float4 *__restrict__ sv, int nv, int sub, const 
     if (dotv<M>(fp, v) == best) return jj;
   }
   return j0;
-}
-
-template <int M>
-__device__ void scan_pair(const float4 *sv, int nv, const float *fpa, const float *fpb,
-                          bool va, bool vb, int &ja, float &ba, int &jb, float &bb) {
-  int sa = 0, sb = 0;
-  ba = -INFINITY;
-  bb = -INFINITY;
-  scan_chunk<M>(sv, nv, fpa, fpb, ba, sa, bb, sb);
-  ja = va ? find_first<M>(sv, nv, sa, fpa, ba) : 0;
-  jb = vb ? find_first<M>(sv, nv, sb, fpb, bb) : 0;
-}
-
-__device__ void scan_pair_rt(int m, const float4 *sv, int nv, const float *fpa, const float *fpb,
-                             bool va, bool vb, int &ja, float &ba, int &jb, float &bb) {
-  switch (m) {
-    case 2: scan_pair<2>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 3: scan_pair<3>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 4: scan_pair<4>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 5: scan_pair<5>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 6: scan_pair<6>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 7: scan_pair<7>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 8: scan_pair<8>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 9: scan_pair<9>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 10: scan_pair<10>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 11: scan_pair<11>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 12: scan_pair<12>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 13: scan_pair<13>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 14: scan_pair<14>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    case 15: scan_pair<15>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-    default: scan_pair<16>(sv, nv, fpa, fpb, va, vb, ja, ba, jb, bb); return;
-  }
 }
 
 // APD (Eq. 4) of a solution and its vote in best[j].
@@ -169,8 +146,109 @@ __device__ __forceinline__ void apd_vote(const RunDesc &R, int i, const float *f
   atomicMin(&R.best[j], ((unsigned long long)__float_as_uint(apd) << 32) | (uint32_t)i);
 }
 
-// One item: 256 solutions (two per thread) x one chunk of reference vectors,
-// the chunk staged in shared memory by one 1-D TMA bulk copy.
+// f' of solution `slot` (0 for an invalid one).
+template <int M>
+__device__ __forceinline__ void load_fp(const RunDesc &R, int slot, float *fp) {
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    fp[k] = slot >= 0 ? sol_f(R, slot, k) - ord2f(R.ctl->zkey[k]) : 0.0f;
+}
+
+// W of the thread's solutions, from q0 on: scan, first index, merge into amax.
+template <int M, int W>
+__device__ __forceinline__ void select_group(const RunDesc &R, const SelItem &it, const float4 *s_v,
+                                             int nv, const int *idx, const int *slot, int q0) {
+  float2 fab[W / 2][M];
+#pragma unroll
+  for (int h = 0; h < W / 2; ++h) {
+    float fa[M], fb[M];
+    load_fp<M>(R, slot[q0 + 2 * h], fa);
+    load_fp<M>(R, slot[q0 + 2 * h + 1], fb);
+#pragma unroll
+    for (int k = 0; k < M; ++k) fab[h][k] = make_float2(fa[k], fb[k]);
+  }
+  float best[W];
+  int bsub[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) { best[q] = -INFINITY; bsub[q] = 0; }
+  scan_chunk<M, W>(s_v, nv, fab, best, bsub);
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    if (slot[q0 + q] < 0) continue;
+    const int j = (q & 1) ? find_first<M, true>(s_v, nv, bsub[q], fab[q >> 1], best[q])
+                          : find_first<M, false>(s_v, nv, bsub[q], fab[q >> 1], best[q]);
+    atomicMax(&R.amax[idx[q0 + q]], ((unsigned long long)f2ord(best[q]) << 32) |
+                                        (unsigned long long)(0xFFFFFFFFu - (uint32_t)(it.v0 + j)));
+  }
+}
+
+// One item: kSelBlock solutions (kSelSols per thread, kSelThreads apart) x
+// one chunk of reference vectors, the chunk staged in shared memory by one
+// 1-D TMA bulk copy.  Up to m = 10 one pass scans the chunk for all four
+// solutions of a thread; past that, two passes of two (registers).
+template <int M>
+__device__ void select_item(const RunDesc &R, const SelItem &it, float4 *s_v, uint64_t *s_bar,
+                            int *s_last) {
+  constexpr int M4 = (M + 3) / 4;
+  int idx[kSelSols], slot[kSelSols];
+#pragma unroll
+  for (int q = 0; q < kSelSols; ++q) {
+    idx[q] = it.sblk * kSelBlock + q * kSelThreads + threadIdx.x;
+    slot[q] = sol_slot(R, idx[q]);
+  }
+  const int nv = it.v1 - it.v0;
+  const uint32_t bytes = (uint32_t)(nv * M4 * 16);
+  if (threadIdx.x == 0) {
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(s_bar, bytes);
+    tma_load_1d(s_v, reinterpret_cast<const float4 *>(R.V32) + (size_t)it.v0 * M4, bytes, s_bar);
+  }
+  __syncthreads();   // barrier initialised before anyone waits on it
+  const bool ok = mbar_wait(s_bar, 0u, kWaitLimit);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      set_status(R.ctl, ST_TIMEOUT);
+      mbar_wait(s_bar, 0u, kWaitLimit);   // give the copy a bounded chance to land
+    }
+    __syncthreads();
+    return;
+  }
+  bool any = false;
+#pragma unroll
+  for (int q = 0; q < kSelSols; ++q) any |= slot[q] >= 0;
+  if (any) {
+    if (M <= 10) {
+      select_group<M, kSelSols>(R, it, s_v, nv, idx, slot, 0);
+    } else {
+#pragma unroll 1
+      for (int q0 = 0; q0 < kSelSols; q0 += 2) select_group<M, 2>(R, it, s_v, nv, idx, slot, q0);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();   // cumulative: orders the block's atomics before the arrival
+    const int prev = atomicAdd(&R.blk_cnt[it.sblk], 1);
+    *s_last = (prev == it.nchunks - 1);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+
+  // ---- last chunk of this block: APD and per-vector argmin ---------------
+  __threadfence();
+#pragma unroll 1
+  for (int q = 0; q < kSelSols; ++q) {
+    if (slot[q] >= 0) {
+      float fp[M];
+      load_fp<M>(R, slot[q], fp);
+      apd_vote(R, idx[q], fp);
+    } else if (idx[q] < R.n_comb) {
+      R.assoc[idx[q]] = -1;
+    }
+  }
+  if (threadIdx.x == 0) R.blk_cnt[it.sblk] = 0;
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 k_select(const __grid_constant__ BatchDir dir) {
   pdl_wait();
@@ -178,66 +256,26 @@ k_select(const __grid_constant__ BatchDir dir) {
   extern __shared__ __align__(128) float4 s_v[];     // [chunk vectors * m4]
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_last;
-
   const int run = dir_find(dir, blockIdx.x);
   const RunDesc &R = *dir.desc[run];
   const SelItem it = static_cast<const SelItem *>(dir.items[run])[blockIdx.x - dir.prefix[run]];
-  const int m = R.m, m4 = R.m4;
-  const int ia = it.sblk * 2 * kSelThreads + threadIdx.x, ib = ia + kSelThreads;
-  const int sa = sol_slot(R, ia), sb = sol_slot(R, ib);
-  const int nv = it.v1 - it.v0;
-  const uint32_t bytes = (uint32_t)(nv * m4 * 16);
-  if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
-    fence_mbar_init();
-    mbar_expect_tx(&s_bar, bytes);
-    tma_load_1d(s_v, reinterpret_cast<const float4 *>(R.V32) + (size_t)it.v0 * m4, bytes, &s_bar);
+  switch (R.m) {
+    case 2: select_item<2>(R, it, s_v, &s_bar, &s_last); return;
+    case 3: select_item<3>(R, it, s_v, &s_bar, &s_last); return;
+    case 4: select_item<4>(R, it, s_v, &s_bar, &s_last); return;
+    case 5: select_item<5>(R, it, s_v, &s_bar, &s_last); return;
+    case 6: select_item<6>(R, it, s_v, &s_bar, &s_last); return;
+    case 7: select_item<7>(R, it, s_v, &s_bar, &s_last); return;
+    case 8: select_item<8>(R, it, s_v, &s_bar, &s_last); return;
+    case 9: select_item<9>(R, it, s_v, &s_bar, &s_last); return;
+    case 10: select_item<10>(R, it, s_v, &s_bar, &s_last); return;
+    case 11: select_item<11>(R, it, s_v, &s_bar, &s_last); return;
+    case 12: select_item<12>(R, it, s_v, &s_bar, &s_last); return;
+    case 13: select_item<13>(R, it, s_v, &s_bar, &s_last); return;
+    case 14: select_item<14>(R, it, s_v, &s_bar, &s_last); return;
+    case 15: select_item<15>(R, it, s_v, &s_bar, &s_last); return;
+    default: select_item<16>(R, it, s_v, &s_bar, &s_last); return;
   }
-  float fpa[kMaxM], fpb[kMaxM];
-#pragma unroll
-  for (int k = 0; k < kMaxM; ++k) { fpa[k] = 0.0f; fpb[k] = 0.0f; }
-  for (int k = 0; k < m; ++k) {
-    const float z = ord2f(R.ctl->zkey[k]);
-    if (sa >= 0) fpa[k] = sol_f(R, sa, k) - z;
-    if (sb >= 0) fpb[k] = sol_f(R, sb, k) - z;
-  }
-  __syncthreads();   // barrier initialised before anyone waits on it
-  const bool ok = mbar_wait(&s_bar, 0u, kWaitLimit);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      set_status(R.ctl, ST_TIMEOUT);
-      mbar_wait(&s_bar, 0u, kWaitLimit);   // give the copy a bounded chance to land
-    }
-    __syncthreads();
-    return;
-  }
-  if (sa >= 0 || sb >= 0) {
-    int ja, jb;
-    float ba, bb;
-    scan_pair_rt(m, s_v, nv, fpa, fpb, sa >= 0, sb >= 0, ja, ba, jb, bb);
-    if (sa >= 0)
-      atomicMax(&R.amax[ia], ((unsigned long long)f2ord(ba) << 32) |
-                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(it.v0 + ja)));
-    if (sb >= 0)
-      atomicMax(&R.amax[ib], ((unsigned long long)f2ord(bb) << 32) |
-                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(it.v0 + jb)));
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();   // cumulative: orders the block's atomics before the arrival
-    const int prev = atomicAdd(&R.blk_cnt[it.sblk], 1);
-    s_last = (prev == it.nchunks - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-
-  // ---- last chunk of this block: APD and per-vector argmin ---------------
-  __threadfence();
-  if (sa >= 0) apd_vote(R, ia, fpa);
-  else if (ia < R.n_comb) R.assoc[ia] = -1;
-  if (sb >= 0) apd_vote(R, ib, fpb);
-  else if (ib < R.n_comb) R.assoc[ib] = -1;
-  if (threadIdx.x == 0) R.blk_cnt[it.sblk] = 0;
 }
 
 // ---- stateless selection: preparation and survivor extraction ------------
@@ -248,7 +286,7 @@ __global__ void k_op_prep(const RunDesc *__restrict__ Rp) {
   const int nth = gridDim.x * blockDim.x;
   for (int j = tid; j < R.N; j += nth) R.best[j] = ~0ull;
   for (int i = tid; i < R.n_comb; i += nth) R.amax[i] = 0ull;
-  const int nblk = (R.n_comb + 2 * kSelThreads - 1) / (2 * kSelThreads);
+  const int nblk = (R.n_comb + kSelBlock - 1) / kSelBlock;
   for (int b = tid; b < nblk; b += nth) R.blk_cnt[b] = 0;
   if (tid == 0) {
     R.ctl->t = R.t_op;

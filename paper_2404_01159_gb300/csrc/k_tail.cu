@@ -388,10 +388,16 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
       float w[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) w[k] = S.gw[k];
-      // eight lanes per solution, groups of four solutions spread over the CTAs
+      // eight lanes per solution (groups of four solutions spread over the
+      // CTAs), or four where eight would give some warps a second group
       const int gw = warp * nb + b, nw = nb * (kTailThreads / 32);
-      for (int g = gw; 4 * g < R.n_comb; g += nw)
-        grid_assoc8<M <= 3 ? M : 3>(R, 4 * g + (lane >> 3), sV, z, w, pen, fcur);
+      if (R.n_comb <= 4 * nw) {
+        for (int g = gw; 4 * g < R.n_comb; g += nw)
+          grid_assocL<M <= 3 ? M : 3, 8>(R, 4 * g + (lane >> 3), sV, z, w, pen, fcur);
+      } else {
+        for (int g = gw; 8 * g < R.n_comb; g += nw)
+          grid_assocL<M <= 3 ? M : 3, 4>(R, 8 * g + (lane >> 2), sV, z, w, pen, fcur);
+      }
     } else {   // the tile search (a CTA-uniform branch)
       const float2 csb = tile_bounds(sCS, T);
       const int groups = (R.n_comb + 3) >> 2, gw = warp * nb + b, nw = nb * (kTailThreads / 32);

@@ -17,8 +17,9 @@ constexpr int kMaxM = 16;          // objectives
 constexpr int kReproThreads = 256; // CTA size of the reproduction kernel
 constexpr int kMutThreads = 128;   // CTA size of the mutation / evaluation kernel (one child a thread)
 constexpr int kLaneGroups = 8;     // 8-variable groups per lane per reproduction unit
-constexpr int kSelThreads = 128;   // selection CTA size (two solutions per thread)
-constexpr int kSelBlock = 2 * kSelThreads;   // solutions per selection work item
+constexpr int kSelThreads = 128;   // selection CTA size
+constexpr int kSelSols = 4;        // solutions per thread (a multiple of 2: packed pairs)
+constexpr int kSelBlock = kSelSols * kSelThreads;   // solutions per selection work item
 constexpr int kVTile = 512;        // reference vectors per shared-memory tile
 constexpr int kFinThreads = 1024;  // CTA size of the per-run finalize kernel
 constexpr int kMaxSites = 32;      // cap of the mutation-site count of one row
