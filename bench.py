@@ -352,55 +352,56 @@ def main_neuro(args, rank, world, local):
     n_runs, N, H, t_max = 100, 100, 99, 100
     kw = dict(m=2, d=d, N=N, H=H, problem=NEURO_LINEAR, t_max=t_max, alpha=2.0, f_r=0.1,
               eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
-    # the FP32 CUDA-core form of the policy GEMVs, timed on the same workload
-    # first, as the comparison with the configuration's BF16 tensor-core form
-    runs32 = [Run(seed=rank * n_runs + q, neuro=dict(dyn, gemv=1), **kw) for q in range(n_runs)]
-    batch32 = Batch(runs32)
-    batch32.step(W)
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record()
-    batch32.step(K)
-    f1.record()
-    f1.synchronize()
-    ms32 = f0.elapsed_time(f1)
-    ph32 = batch32.step_profiled(max(1, min(K, 5)))
-    for r in runs32:
-        r.sync_status()
-    batch32.free()
-    del runs32, batch32
-    runs = [Run(seed=rank * n_runs + q, neuro=dyn, **kw) for q in range(n_runs)]
-    for r in runs:
-        autotune(r)
-    batch = Batch(runs)
-    batch.step(W)
-    torch.cuda.synchronize()
-    props = torch.cuda.get_device_properties(local)
-    gid = str(getattr(props, "uuid", "")) or str(local)
-    if gid and not gid.startswith("GPU-") and len(gid) >= 32:
-        gid = "GPU-" + gid
-    sampler = ClockSampler(gid) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    batch.step(K)
-    e1.record()
-    e1.synchronize()
-    if sampler:
-        sampler.stop()
-    ms = e0.elapsed_time(e1)
     Kp = max(1, min(K, 5))
-    phases = batch.step_profiled(Kp)
-    launches_per_step = batch.launches_per_step()
-    for r in runs:
-        r.sync_status()
-    batch.free()
+
+    def timed(gemv, sample):
+        """K batched generations of the 100 runs with the given GEMV form:
+        (ms, per-phase ms, launches per step, clock summary)."""
+        runs = [Run(seed=rank * n_runs + q, neuro=dict(dyn, gemv=gemv), **kw) for q in range(n_runs)]
+        for r in runs:
+            autotune(r)
+        batch = Batch(runs)
+        batch.step(W)
+        torch.cuda.synchronize()
+        sampler = None
+        if sample:
+            props = torch.cuda.get_device_properties(local)
+            gid = str(getattr(props, "uuid", "")) or str(local)
+            if gid and not gid.startswith("GPU-") and len(gid) >= 32:
+                gid = "GPU-" + gid
+            sampler = ClockSampler(gid)
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.step(K)
+        e1.record()
+        e1.synchronize()
+        if sampler:   # the same loop, untimed, so that the clock record has samples
+            t_soak = time.perf_counter()
+            while time.perf_counter() - t_soak < args.soak_seconds:
+                batch.step(K)
+                torch.cuda.synchronize()
+            sampler.stop()
+        ms = e0.elapsed_time(e1)
+        phases = batch.step_profiled(Kp)
+        lps = batch.launches_per_step()
+        for r in runs:
+            r.sync_status()
+        batch.free()
+        return ms, phases, lps, (sampler.summary() if sampler else None)
+
+    # the form the workload runs in: the policy GEMVs in FP32 on the CUDA
+    # cores (gemv = 1, hidden-layer weights register-resident); the BF16
+    # tensor-core form (gemv = 0) is timed beside it as the comparison
+    ms, phases, launches_per_step, clocks = timed(1, rank == 0)
+    ms16, ph16, _, _ = timed(0, False)
     steps = dyn["steps"]
     gemm_flop = n_runs * N * steps * 2 * (64 * 17 + 64 * 64 + 6 * 64)
     eval_ms = phases[0] / Kp
     tf_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    # FP32 CUDA-core peak: 152 SMs x 128 FMA/clock x 2 flop x 2.07 GHz
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = gemm_flop / (eval_ms * 1e-3) / 1e12
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -418,30 +419,31 @@ def main_neuro(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16x3 tensor GEMV, f32 dynamics",
+        "dtype": "f32 GEMV (CUDA cores), f32 dynamics",
         "data": "synthetic (seeded policies N(0, 0.1), seeded linear dynamics, rho(A) = 0.95)",
         "config": {"workload": NEURO, "runs": n_runs, "policies_per_run": N, "d": d,
                    "mlp": "17-64-64-6 tanh", "rollout_steps": steps, "sigma": dyn["sigma"],
-                   "t_max": t_max, "m": 2, "H": H,
+                   "t_max": t_max, "m": 2, "H": H, "gemv": 1,
                    "l2": "rollouts are compute-bound; weights stay on chip for 1000 steps",
                    "parallelism": "one CUDA graph per batched generation"},
         "policies_per_s": n_runs * N * K / (ms * 1e-3),
-        "fp32_cuda_cores": {
-            "value": n_runs * K / (ms32 * 1e-3), "unit": "run-generations/s",
-            "ms_per_step": ms32 / K,
-            "rollout_ms": ph32[0] / max(1, min(K, 5)),
-            "gemm_tflops": gemm_flop / (ph32[0] / max(1, min(K, 5)) * 1e-3) / 1e12,
-            "speedup_over_bf16_tensor": ms / ms32,
-            "what": "the same workload with the policy GEMVs in FP32 on the CUDA cores "
-                    "(weights in shared memory, rvea_neuro_dynamics.gemv = 1)"},
-        "roofline": {"kernel": "k_rollout (1000-step rollout of every child)", "bound": "tensor",
-                     "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s",
-                     "frac": achieved / tf_peak, "peak_kind": "measured bf16 dense (burst)",
+        "bf16_tensor_cores": {
+            "value": n_runs * K / (ms16 * 1e-3), "unit": "run-generations/s",
+            "ms_per_step": ms16 / K,
+            "rollout_ms": ph16[0] / Kp,
+            "gemm_tflops": gemm_flop / (ph16[0] / Kp * 1e-3) / 1e12,
+            "frac_of_bf16_peak": gemm_flop / (ph16[0] / Kp * 1e-3) / 1e12 / tf_peak,
+            "fp32_speedup_over_this": ms16 / ms,
+            "what": "the same workload with the policy GEMVs on the tensor cores (mma.sync "
+                    "BF16 hi/lo operands, FP32 accumulate, rvea_neuro_dynamics.gemv = 0)"},
+        "roofline": {"kernel": "k_rollout_f32 (1000-step rollout of every child)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak,
+                     "peak_kind": "derived: FP32 FMA rate, 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                      "traffic": None, "algorithmic_flop_per_launch": gemm_flop,
                      "avg_launch_ms": eval_ms,
                      "what": "useful policy-GEMM flops (2 x 5568 MAC per step per policy) over "
-                             "the reproduction+rollout phase; the MMA tiles issue 24x as many "
-                             "(one column of 8, three BF16 passes)"},
+                             "the reproduction+rollout phase"},
         "phase_ms_per_generation": {"repro_rollout": phases[0] / Kp,
                                     "select_pruned": phases[1] / Kp,
                                     "select_scan": phases[2] / Kp, "finalize": phases[3] / Kp,
@@ -449,7 +451,7 @@ def main_neuro(args, rank, world, local):
         "cpu_baseline": cpu,
         "e2e": None,
         "gpu_launches": K * launches_per_step,
-        "clocks": sampler.summary() if sampler else None,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 

@@ -83,7 +83,7 @@ __global__ void k_noise(const __grid_constant__ BatchDir dir, int init);
 __global__ void k_rollout(const __grid_constant__ BatchDir dir, int init);
 __global__ void k_rollout_f32(const __grid_constant__ BatchDir dir, int init);
 size_t rollout_f32_smem(int ns, int na);
-constexpr int kRollF32Policies = 8;   // policies (warps) per CTA of the FP32 rollout
+constexpr int kRollF32Policies = 2;   // policies (warps) per CTA of the FP32 rollout
 __global__ void k_select_pruned_batch(const __grid_constant__ BatchDir dir);
 __global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force);
 __global__ void k_tail_dtlz1(const RunDesc *Rp);

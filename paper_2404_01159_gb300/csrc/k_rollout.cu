@@ -278,57 +278,72 @@ k_rollout(const __grid_constant__ BatchDir dir, int init) {
 
 // The same rollout with the policy GEMVs on the CUDA cores in FP32 (the
 // configuration's other form, rvea_neuro_dynamics.gemv = 1): one warp per
-// policy, the policy's weights copied once into shared memory in FP32 and
-// read there every step.  Lane l owns the hidden rows l and l + 32 of both
-// layers; the weights of a layer are stored as float4 blocks
-// [column / 4][row], so the 32 lanes of a warp read 32 consecutive 16-byte
-// blocks (no bank conflict), and the input vector is broadcast from shared
-// memory.  The output layer sums over the 64 inputs with a butterfly.  The
-// dynamics and the objectives are as in the MMA form.  Dynamic shared
-// memory: A, B, then per warp W1 (ceil(ns/4) x 64 float4), W2 (16 x 64
-// float4), W3 (na x 64), b1, b2, b3, and the step's state and hidden vectors.
-constexpr int kRF32Warps = 8;
+// policy, its 64 x 64 hidden layer register-resident.  Lane l owns rows l
+// and l + 32 of both hidden layers: W2's two rows (128 floats) and W3's
+// columns l and l + 32 stay in its registers for the whole rollout, W1
+// (transposed, float4 blocks [column / 4][row]) in shared memory, so that a
+// step reads from shared memory only the broadcast input vectors and W1.
+// Layer 3 reduces the lanes' partial sums of all actions at once (one
+// multi-value reduce-scatter); the next step's noise is loaded a step ahead.
+// The dynamics and the objectives are as in the MMA form (lane k owns state
+// component k; A and B transposed in shared memory).  NS4: ns padded to a
+// multiple of 4 (ns <= kRF32NsMax, na <= kRF32NaMax).
+constexpr int kRF32Warps = 2;     // policies per CTA
+constexpr int kRF32NsMax = 24;
+constexpr int kRF32NaMax = 8;
 
-struct RF32Layout {
-  int nc1;                       // float4 column blocks of W1 (ns padded to 4)
-  int offA, offB, per_warp;      // floats
-  int w1, w2, w3, b1, b2, b3, sv, h1;   // offsets within a warp's slab (floats)
+struct RF32Shared {
+  float AT[kRF32NsMax][32];                 // AT[i][k] = A[k][i], zero past ns
+  float BT[kRF32NaMax][32];                 // BT[o][k] = B[k][o], zero past ns, na
+  float4 w1[kRF32Warps][kRF32NsMax / 4][kRollH];
+  float4 sv[kRF32Warps][kRF32NsMax / 4];    // the state (zero past ns)
+  float4 h1[kRF32Warps][kRollH / 4];        // the first hidden layer's output
+  float w3[kRF32Warps][kRF32NaMax][kRollH]; // W3 (zero rows past na)
+  float b3[kRF32Warps][kRF32NaMax];
 };
-__host__ __device__ inline RF32Layout rf32_layout(int ns, int na) {
-  RF32Layout L;
-  L.nc1 = (ns + 3) / 4;
-  L.offA = 0;
-  L.offB = ((kRollNsMax * kRollNsMax + 3) / 4) * 4;
-  const int dyn = L.offB + ((kRollNsMax * kRollNaMax + 3) / 4) * 4;
-  int o = 0;
-  L.w1 = o; o += L.nc1 * kRollH * 4;
-  L.w2 = o; o += (kRollH / 4) * kRollH * 4;
-  L.w3 = o; o += na * kRollH;
-  L.b1 = o; o += kRollH;
-  L.b2 = o; o += kRollH;
-  L.b3 = o; o += ((na + 3) / 4) * 4;
-  L.sv = o; o += L.nc1 * 4;
-  L.h1 = o; o += kRollH;
-  L.per_warp = ((o + 3) / 4) * 4;
-  L.offA = dyn;   // the slabs follow A and B
-  return L;
+
+// Sum over the warp of eight values per lane, every lane ending with all
+// eight sums: a reduce-scatter (each exchange halves the values a lane
+// keeps: 4 + 2 + 1 shuffles), two more butterfly steps, then the eight sums
+// gathered from the lanes that hold them (8 shuffles): 17 shuffles on a
+// chain of 6 exchanges, where eight separate butterflies take 40.
+__device__ __forceinline__ void warp_sum8(float (&v)[8], int lane) {
+  // offset 16: lanes < 16 keep values 0-3, the others 4-7
+  const bool hi16 = lane & 16;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float send = hi16 ? v[q] : v[q + 4];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 16);
+    v[q] = (hi16 ? v[q + 4] : v[q]) + got;
+  }
+  // offset 8: keep 2 of the 4 (values 2k, 2k+1 of the kept half)
+  const bool hi8 = lane & 8;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float send = hi8 ? v[q] : v[q + 2];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 8);
+    v[q] = (hi8 ? v[q + 2] : v[q]) + got;
+  }
+  // offset 4: keep 1 of the 2
+  {
+    const bool hi4 = lane & 4;
+    const float send = hi4 ? v[0] : v[1];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 4);
+    v[0] = (hi4 ? v[1] : v[0]) + got;
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  // lane l now holds the sum of value 4 (l >> 4 & 1) + 2 (l >> 3 & 1) + (l >> 2 & 1)
+  const float mine = v[0];
+#pragma unroll
+  for (int o = 0; o < 8; ++o)
+    v[o] = __shfl_sync(0xffffffffu, mine, ((o >> 2) & 1) * 16 + ((o >> 1) & 1) * 8 + (o & 1) * 4);
 }
 
-__global__ void __launch_bounds__(kRF32Warps * 32)
-k_rollout_f32(const __grid_constant__ BatchDir dir, int init) {
-  pdl_wait();
-  extern __shared__ __align__(16) float rsm[];
-  const int run = dir_find(dir, blockIdx.x);
-  const RunDesc &R = *dir.desc[run];
+template <int NS4>
+__device__ __forceinline__ void rollout_reg(const RunDesc &R, RF32Shared &S, int c, int init) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ns = R.ns, na = R.na, steps = R.steps, N = R.N;
-  const RF32Layout Ly = rf32_layout(ns, na);
-  float *sA = rsm, *sB = rsm + ((kRollNsMax * kRollNsMax + 3) / 4) * 4;
-  for (int e = threadIdx.x; e < ns * ns; e += blockDim.x) sA[e] = R.dynA[e];
-  for (int e = threadIdx.x; e < ns * na; e += blockDim.x) sB[e] = R.dynB[e];
-  __syncthreads();
-  const int c = (blockIdx.x - dir.prefix[run]) * kRF32Warps + warp;
-  if (c >= N) return;
   const int t = R.ctl->t;
   int slot = c;
   if (!init) slot = R.child_slot[(t & 1) * N + c];
@@ -339,77 +354,92 @@ k_rollout_f32(const __grid_constant__ BatchDir dir, int init) {
   const float *x = R.X + (size_t)slot * R.d_pad;
   const float *W1 = x, *b1 = W1 + kRollH * ns, *W2 = b1 + kRollH, *b2 = W2 + kRollH * kRollH;
   const float *W3 = b2 + kRollH, *b3 = W3 + na * kRollH;
-  float *const slab = rsm + Ly.offA + warp * Ly.per_warp;
-  float4 *const w1s = reinterpret_cast<float4 *>(slab + Ly.w1);
-  float4 *const w2s = reinterpret_cast<float4 *>(slab + Ly.w2);
-  float *const w3s = slab + Ly.w3, *const bs1 = slab + Ly.b1, *const bs2 = slab + Ly.b2;
-  float *const bs3 = slab + Ly.b3, *const sv = slab + Ly.sv, *const h1 = slab + Ly.h1;
-  // the weights into shared memory, once
-  for (int e = lane; e < Ly.nc1 * kRollH; e += 32) {
+  const int r0 = lane, r1 = lane + 32;
+  // W1, W3 into shared memory, W2's two rows into registers, once
+  for (int e = lane; e < (NS4 / 4) * kRollH; e += 32) {
     const int c4 = e / kRollH, r = e - c4 * kRollH;
     float v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) v[u] = 4 * c4 + u < ns ? __ldg(W1 + (size_t)r * ns + 4 * c4 + u) : 0.0f;
-    w1s[e] = make_float4(v[0], v[1], v[2], v[3]);
+    S.w1[warp][c4][r] = make_float4(v[0], v[1], v[2], v[3]);
   }
-  for (int e = lane; e < (kRollH / 4) * kRollH; e += 32) {
-    const int c4 = e / kRollH, r = e - c4 * kRollH;
-    w2s[e] = __ldg(reinterpret_cast<const float4 *>(W2 + (size_t)r * kRollH) + c4);
+  for (int e = lane; e < kRF32NaMax * kRollH; e += 32)
+    S.w3[warp][e / kRollH][e % kRollH] = e / kRollH < na ? __ldg(W3 + e) : 0.0f;
+  if (lane < NS4 / 4) S.sv[warp][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < kRF32NaMax) S.b3[warp][lane] = lane < na ? __ldg(b3 + lane) : 0.0f;
+  float w2a[kRollH], w2b[kRollH];
+#pragma unroll
+  for (int c4 = 0; c4 < kRollH / 4; ++c4) {
+    const float4 p = __ldg(reinterpret_cast<const float4 *>(W2 + (size_t)r0 * kRollH) + c4);
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(W2 + (size_t)r1 * kRollH) + c4);
+    w2a[4 * c4] = p.x; w2a[4 * c4 + 1] = p.y; w2a[4 * c4 + 2] = p.z; w2a[4 * c4 + 3] = p.w;
+    w2b[4 * c4] = q.x; w2b[4 * c4 + 1] = q.y; w2b[4 * c4 + 2] = q.z; w2b[4 * c4 + 3] = q.w;
   }
-  for (int e = lane; e < na * kRollH; e += 32) w3s[e] = __ldg(W3 + e);
-  for (int e = lane; e < kRollH; e += 32) { bs1[e] = __ldg(b1 + e); bs2[e] = __ldg(b2 + e); }
-  if (lane < na) bs3[lane] = __ldg(b3 + lane);
-  if (lane < 4 * Ly.nc1) sv[lane] = 0.0f;
+  const float bb1a = __ldg(b1 + r0), bb1b = __ldg(b1 + r1);
+  const float bb2a = __ldg(b2 + r0), bb2b = __ldg(b2 + r1);
   __syncwarp();
   const float sigma = R.sigma;
   const float *xi = R.noise;
-  const int r0 = lane, r1 = lane + 32;
-  const float *Ar = sA + lane * ns, *Br = sB + lane * na;
-  float s = 0.0f, f1 = 0.0f, f2 = 0.0f;
+  const float4 *sv = S.sv[warp];
+  const float4 *h1 = S.h1[warp];
+  float *const h1f = reinterpret_cast<float *>(S.h1[warp]);
+  const bool dyn = lane < ns;   // lane k owns state component k
+  float f1 = 0.0f, f2 = 0.0f;
+  float xin = dyn && steps > 0 ? __ldg(xi + lane) : 0.0f;   // this step's noise, loaded a step ahead
 #pragma unroll 1
   for (int tau = 0; tau < steps; ++tau) {
-    // layer 1
-    float a0 = bs1[r0], a1 = bs1[r1], c0 = 0.0f, c1 = 0.0f;
-    for (int c4 = 0; c4 < Ly.nc1; ++c4) {
-      const float4 v = reinterpret_cast<const float4 *>(sv)[c4];
-      const float4 p = w1s[c4 * kRollH + r0], q = w1s[c4 * kRollH + r1];
+    const float xic = xin;
+    if (dyn && tau + 1 < steps) xin = __ldg(xi + (size_t)(tau + 1) * ns + lane);
+    // layer 1: rows r0, r1, two accumulation chains each
+    float a0 = bb1a, c0 = 0.0f, a1 = bb1b, c1 = 0.0f;
+#pragma unroll
+    for (int c4 = 0; c4 < NS4 / 4; ++c4) {
+      const float4 v = sv[c4];
+      const float4 p = S.w1[warp][c4][r0], q = S.w1[warp][c4][r1];
       a0 = fmaf(p.x, v.x, a0); c0 = fmaf(p.y, v.y, c0); a0 = fmaf(p.z, v.z, a0); c0 = fmaf(p.w, v.w, c0);
       a1 = fmaf(q.x, v.x, a1); c1 = fmaf(q.y, v.y, c1); a1 = fmaf(q.z, v.z, a1); c1 = fmaf(q.w, v.w, c1);
     }
-    h1[r0] = tanh_approx(a0 + c0);
-    h1[r1] = tanh_approx(a1 + c1);
+    h1f[r0] = tanh_approx(a0 + c0);
+    h1f[r1] = tanh_approx(a1 + c1);
+    // the state part of the dynamics (independent of the policy): A s
+    float za = 0.0f, zc = 0.0f;
+#pragma unroll
+    for (int c4 = 0; c4 < NS4 / 4; ++c4) {
+      const float4 v = sv[c4];
+      za = fmaf(S.AT[4 * c4][lane], v.x, za);
+      zc = fmaf(S.AT[4 * c4 + 1][lane], v.y, zc);
+      za = fmaf(S.AT[4 * c4 + 2][lane], v.z, za);
+      zc = fmaf(S.AT[4 * c4 + 3][lane], v.w, zc);
+    }
     __syncwarp();
-    // layer 2: four accumulation chains per row
-    float e0[4] = {bs2[r0], 0.0f, 0.0f, 0.0f}, e1[4] = {bs2[r1], 0.0f, 0.0f, 0.0f};
-#pragma unroll 4
+    // layer 2: W2 rows from registers, four accumulation chains per row
+    float e0[4] = {bb2a, 0.0f, 0.0f, 0.0f}, e1[4] = {bb2b, 0.0f, 0.0f, 0.0f};
+#pragma unroll
     for (int c4 = 0; c4 < kRollH / 4; ++c4) {
-      const float4 v = reinterpret_cast<const float4 *>(h1)[c4];
-      const float4 p = w2s[c4 * kRollH + r0], q = w2s[c4 * kRollH + r1];
-      e0[0] = fmaf(p.x, v.x, e0[0]); e0[1] = fmaf(p.y, v.y, e0[1]);
-      e0[2] = fmaf(p.z, v.z, e0[2]); e0[3] = fmaf(p.w, v.w, e0[3]);
-      e1[0] = fmaf(q.x, v.x, e1[0]); e1[1] = fmaf(q.y, v.y, e1[1]);
-      e1[2] = fmaf(q.z, v.z, e1[2]); e1[3] = fmaf(q.w, v.w, e1[3]);
+      const float4 v = h1[c4];
+      e0[0] = fmaf(w2a[4 * c4], v.x, e0[0]); e0[1] = fmaf(w2a[4 * c4 + 1], v.y, e0[1]);
+      e0[2] = fmaf(w2a[4 * c4 + 2], v.z, e0[2]); e0[3] = fmaf(w2a[4 * c4 + 3], v.w, e0[3]);
+      e1[0] = fmaf(w2b[4 * c4], v.x, e1[0]); e1[1] = fmaf(w2b[4 * c4 + 1], v.y, e1[1]);
+      e1[2] = fmaf(w2b[4 * c4 + 2], v.z, e1[2]); e1[3] = fmaf(w2b[4 * c4 + 3], v.w, e1[3]);
     }
     const float g0 = tanh_approx((e0[0] + e0[1]) + (e0[2] + e0[3]));
     const float g1 = tanh_approx((e1[0] + e1[1]) + (e1[2] + e1[3]));
-    // layer 3 and the dynamics' action term: u_o on every lane
-    float zb = 0.0f;
-    for (int o = 0; o < na; ++o) {
-      float pr = fmaf(w3s[o * kRollH + r0], g0, w3s[o * kRollH + r1] * g1);
+    // layer 3: every lane's share of the actions, summed over the warp
+    float pr[kRF32NaMax];
 #pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, off);
-      const float u = tanh_approx(pr + bs3[o]);
+    for (int o = 0; o < kRF32NaMax; ++o) pr[o] = fmaf(S.w3[warp][o][r0], g0, S.w3[warp][o][r1] * g1);
+    warp_sum8(pr, lane);
+    float zb = 0.0f;
+#pragma unroll
+    for (int o = 0; o < kRF32NaMax; ++o) {
+      const float u = o < na ? tanh_approx(pr[o] + S.b3[warp][o]) : 0.0f;
       f2 = fmaf(u, u, f2);
-      if (lane < ns) zb = fmaf(Br[o], u, zb);
+      zb = fmaf(S.BT[o][lane], u, zb);
     }
-    // dynamics: lane k computes s'[k]
-    float za = 0.0f;
-    if (lane < ns) {
-      for (int j = 0; j < ns; ++j) za = fmaf(Ar[j], sv[j], za);
-    }
-    s = lane < ns ? fmaf(sigma, __ldg(xi + (size_t)tau * ns + lane), za + zb) : 0.0f;
-    __syncwarp();   // every lane has read sv and h1
-    if (lane < ns) sv[lane] = s;
+    // dynamics: lane k computes s'[k] = A s + B u + sigma xi
+    const float s = dyn ? fmaf(sigma, xic, (za + zc) + zb) : 0.0f;
+    __syncwarp();   // every lane has read the state and h1
+    if (dyn) reinterpret_cast<float *>(S.sv[warp])[lane] = s;
     f1 -= __shfl_sync(0xffffffffu, s, 0);
     __syncwarp();
   }
@@ -422,10 +452,35 @@ k_rollout_f32(const __grid_constant__ BatchDir dir, int init) {
   }
 }
 
-// Dynamic shared memory of k_rollout_f32 for this shape (bytes).
-size_t rollout_f32_smem(int ns, int na) {
-  const RF32Layout L = rf32_layout(ns, na);
-  return (size_t)(L.offA + kRF32Warps * L.per_warp) * sizeof(float);
+__global__ void __launch_bounds__(kRF32Warps * 32)
+k_rollout_f32(const __grid_constant__ BatchDir dir, int init) {
+  pdl_wait();
+  __shared__ __align__(16) RF32Shared S;
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int ns = R.ns, na = R.na;
+  for (int e = threadIdx.x; e < kRF32NsMax * 32; e += blockDim.x) {
+    const int i = e / 32, k = e % 32;   // AT[i][k] = A[k][i]
+    S.AT[i][k] = i < ns && k < ns ? R.dynA[k * ns + i] : 0.0f;
+  }
+  for (int e = threadIdx.x; e < kRF32NaMax * 32; e += blockDim.x) {
+    const int o = e / 32, k = e % 32;   // BT[o][k] = B[k][o]
+    S.BT[o][k] = o < na && k < ns ? R.dynB[k * na + o] : 0.0f;
+  }
+  __syncthreads();
+  const int c = (blockIdx.x - dir.prefix[run]) * kRF32Warps + (threadIdx.x >> 5);
+  if (c >= R.N) return;
+  switch ((ns + 3) / 4) {
+    case 1: rollout_reg<4>(R, S, c, init); return;
+    case 2: rollout_reg<8>(R, S, c, init); return;
+    case 3: rollout_reg<12>(R, S, c, init); return;
+    case 4: rollout_reg<16>(R, S, c, init); return;
+    case 5: rollout_reg<20>(R, S, c, init); return;
+    default: rollout_reg<24>(R, S, c, init); return;
+  }
 }
+
+// Dynamic shared memory of k_rollout_f32 (its tables are static).
+size_t rollout_f32_smem(int, int) { return 0; }
 
 }  // namespace rvea
