@@ -236,7 +236,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.tcs = take(T * 8 + 16);
   L.gcell = take((size_t)s.gcells * 32);
   L.gcnt = take((size_t)s.gcells * 4);
-  L.gblk = take((size_t)(s.gG > 0 ? grid_build_blocks(s.gG, s.m) : 0) * 4);
+  L.gblk = take((size_t)(s.gG > 0 ? grid_build_blocks(s.gG, s.m) + 1 : 0) * 4);
   L.gover = take((size_t)s.gcap * 2);
   L.gscale = take(kMaxM * 4);
   L.vrange = take(kMaxM * 8);
@@ -835,8 +835,8 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   if (!fused) launch_pdl(k_finalize, pd, 1024, 0, st, dd);
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
-    k_gamma<<<2 * runs[0]->num_sms, 256, 0, st>>>(df, 0);
     if (nt > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
+    k_gamma<<<2 * runs[0]->num_sms, 256, 0, st>>>(df, 0);
   }
   if (ev) cudaEventRecord(ev[5], st);
   return cuerr(cudaGetLastError());
@@ -873,8 +873,8 @@ rvea_status enqueue_one(rvea_run *r, cudaStream_t st) {
   rvea_status s = launch_generation(one, 1, st, false);
   if (s != RVEA_OK) return s;
   if (r->t % r->p_adapt == 0) {
-    s = launch_gamma_force(r, st);
-    if (s == RVEA_OK) s = launch_tiles(r, st);
+    s = launch_tiles(r, st);   // the tiles first: gamma searches them
+    if (s == RVEA_OK) s = launch_gamma_force(r, st);
   }
   return s;
 }
@@ -1132,6 +1132,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   c0.t = 1;
   c0.K = sh.N;
   c0.grid_ver = -1;
+  c0.tiles_ver = -1;
   for (int k = 0; k < kMaxM; ++k) c0.zkey[k] = 0xFFFFFFFFu;
 
   rvea_status s = RVEA_OK;
@@ -1171,8 +1172,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     dir_single(d, r, nullptr, 1);
     k_init_lists<<<dim3((sh.N + 255) / 256, 1), 256, 0, st>>>(d);
     s = cuerr(cudaGetLastError());
-    if (s == RVEA_OK) s = launch_gamma_force(r, st);
     if (s == RVEA_OK) s = launch_tiles(r, st);
+    if (s == RVEA_OK) s = launch_gamma_force(r, st);
   }
   // pageable host sources above must stay valid until their copies are done
   if (s == RVEA_OK) s = cuerr(cudaStreamSynchronize(st));
@@ -1623,8 +1624,8 @@ rvea_status rvea_step_profiled(rvea_run *r, int G, void *cuda_stream, double *ph
     if (r->sel_mode != 3) k_finalize<<<nbd, 1024, 0, st>>>(dd);
     cudaEventRecord(e[3], st);
     if (r->t % r->p_adapt == 0) {
-      k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
       launch_tiles(r, st);
+      k_gamma<<<nbg, 256, 0, st>>>(dg, 1);
     }
     cudaEventRecord(e[4], st);
     s = cuerr(cudaGetLastError());

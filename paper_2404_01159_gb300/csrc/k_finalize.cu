@@ -232,6 +232,115 @@ __device__ void gamma_block(const RunDesc &R, int jb) {
   }
 }
 
+// gamma_j through the k-d tiles of the vectors (m <= 4, tables current for
+// this V): one thread per vector j.  The float pass scans the tile whose
+// centre is closest to v_j, then every tile that can hold a vector i != j
+// with a float dot >= b - 2e-5 (b the best so far; the tile's centre dot
+// against cos(acos(b') + rho) with rho rounded outwards and 1e-5 of slack,
+// which only admits more tiles); the final float maximum b is then the full
+// pass's max32, and the FP64 recheck of every i with a float dot within
+// 1e-5 of it (in the tiles that can hold one) gives gamma_j bit for bit as
+// the full pass does: both take the FP64 maximum over a set that holds the
+// true maximiser, with the same dot64.
+template <int M>
+__device__ __forceinline__ float gdot(const float *a, float4 b) {
+  float d = a[0] * b.x;
+  if (M > 1) d = fmaf(a[1], b.y, d);
+  if (M > 2) d = fmaf(a[2], b.z, d);
+  if (M > 3) d = fmaf(a[3], b.w, d);
+  return d;
+}
+
+// Eight lanes per vector j (lanes 8g .. 8g+7 of a warp; every lane of the
+// warp calls it): the lanes split the tile loops, reduce over the group
+// between the passes, and the group's first lane writes gamma_j.
+template <int M>
+__device__ void gamma_group(const RunDesc &R, int j) {
+  const int T = R.ntiles, lane = threadIdx.x & 31, sub = lane & 7;
+  const bool act = j < R.N;
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) v[k] = R.V32[(size_t)j * 4 + k];   // m <= 4: one float4 a row
+  }
+  auto member = [&](int pos) { return M < 4 ? __float_as_int(R.Vt[pos].w) : R.tperm[pos]; };
+  auto admits = [&](int t, float bt_) {
+    const float Bt = fmaxf(-1.0f, bt_);
+    const float S = sqrtf(fmaxf(0.0f, 1.0f - Bt * Bt));
+    const float2 cs = R.tcs[t];
+    return gdot<M>(v, R.tcen[t]) >= fmaf(Bt, cs.x, -S * cs.y) - 1e-5f;
+  };
+  // the closest centre (ties: the smaller tile)
+  float bc = -INFINITY;
+  int bt = 0x7FFFFFFF;
+  for (int t = sub; t < T; t += 8) {
+    const float d = gdot<M>(v, R.tcen[t]);
+    if (d > bc) { bc = d; bt = t; }
+  }
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) {
+    const float od = __shfl_xor_sync(0xffffffffu, bc, off);
+    const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+    if (od > bc || (od == bc && ot < bt)) { bc = od; bt = ot; }
+  }
+  float b = -2.0f;
+  if (act && bt < T) {   // its members, split over the group
+    const int2 rg = R.trng[bt];
+    for (int q = sub; q < rg.y; q += 8)
+      if (member(rg.x + q) != j) b = fmaxf(b, gdot<M>(v, R.Vt[rg.x + q]));
+  }
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
+  // every other tile that can hold a dot within 2e-5 of b, one lane a tile
+  const float b0 = b - 2e-5f;
+  if (act) {
+    for (int t = sub; t < T; t += 8) {
+      if (t == bt || !admits(t, b0)) continue;
+      const int2 rg = R.trng[t];
+      for (int q = 0; q < rg.y; ++q)
+        if (member(rg.x + q) != j) b = fmaxf(b, gdot<M>(v, R.Vt[rg.x + q]));
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
+  // FP64 recheck of the float maxima within 1e-5 of b
+  const float thr = b - 1e-5f;
+  const double *vjp = R.V64 + (size_t)(act ? j : 0) * M;
+  double best = -2.0;
+  if (act) {
+    for (int t = sub; t < T; t += 8) {
+      if (t != bt && !admits(t, thr - 1e-5f)) continue;
+      const int2 rg = R.trng[t];
+      for (int q = 0; q < rg.y; ++q) {
+        const int i = member(rg.x + q);
+        if (i != j && gdot<M>(v, R.Vt[rg.x + q]) >= thr)
+          best = fmax(best, dot64(R.V64 + (size_t)i * M, vjp, M));
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+  if (act && sub == 0) {
+    double g = acos(fmin(1.0, fmax(-1.0, best)));
+    if (!(g >= 1e-12)) g = 1e-12;
+    R.gamma64[j] = g;
+    if (R.gamma32) R.gamma32[j] = (float)g;
+  }
+}
+
+__device__ void gamma_tiles(const RunDesc &R) {
+  const int lane = threadIdx.x & 31;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int base = 4 * wg; base < R.N; base += 4 * nw) {   // warp-uniform: four vectors a warp
+    const int j = base + (lane >> 3);
+    switch (R.m) {
+      case 2: gamma_group<2>(R, j); break;
+      case 3: gamma_group<3>(R, j); break;
+      default: gamma_group<4>(R, j); break;
+    }
+  }
+}
+
 // Persistent over the directory: every run with ctl->adapted set (or every
 // run when `force`) has its vector blocks of 32 spread over the grid.
 __global__ void __launch_bounds__(256)
@@ -240,6 +349,10 @@ k_gamma(const __grid_constant__ BatchDir dir, int force) {
   for (int r = 0; r < dir.n; ++r) {
     const RunDesc &R = *dir.desc[r];
     if (!force && R.ctl->adapted == 0) continue;
+    if (R.ntiles > 0 && R.m <= 4 && R.ctl->tiles_ver == R.ctl->v_ver) {   // uniform over the grid
+      gamma_tiles(R);
+      continue;
+    }
     const int nb = (R.N + 31) / 32;
     for (int jb = blockIdx.x; jb < nb; jb += gridDim.x) gamma_block(R, jb);
   }

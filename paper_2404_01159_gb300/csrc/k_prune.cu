@@ -198,6 +198,8 @@ __device__ __forceinline__ void tile_one(const RunDesc &R, int t) {
 __global__ void k_tiles(const RunDesc *__restrict__ Rp) {
   pdl_wait();
   tile_one(*Rp, blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+  // the kernels after this one (gamma, the grid) see the tables as current
+  if (blockIdx.x == 0 && threadIdx.x == 0) Rp->ctl->tiles_ver = Rp->ctl->v_ver;
 }
 
 // The same over a batch (dir.prefix counts CTAs of 8 tiles): runs whose
@@ -208,6 +210,7 @@ __global__ void k_tiles_batch(const __grid_constant__ BatchDir dir, int force) {
   const RunDesc &R = *dir.desc[run];
   if (!force && R.ctl->adapted == 0) return;
   tile_one(R, (blockIdx.x - dir.prefix[run]) * (blockDim.x >> 5) + (threadIdx.x >> 5));
+  if (blockIdx.x == dir.prefix[run] && threadIdx.x == 0) R.ctl->tiles_ver = R.ctl->v_ver;
 }
 
 }  // namespace rvea

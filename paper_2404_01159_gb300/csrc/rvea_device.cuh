@@ -58,6 +58,7 @@ struct Ctl {
   int fcomb_t;         // generation whose combined objectives fcomb holds (0: none)
   int grid_ver;        // the v_ver the direction grid was built for (-1: none)
   int grid_skip;       // 1: the current vectors are too skewed for the grid (not built)
+  int tiles_ver;       // the v_ver the tile tables were built for (-1: none)
   unsigned long long bar;   // grid barrier of the fused tail kernel: arrivals
                             // since initialisation (a multiple of its grid
                             // between launches)
