@@ -177,10 +177,13 @@ __device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl
             in = pdot<M>(g.c, v) >= thr_m && support_test<M>(g, v);
           }
           const unsigned mm = __ballot_sync(0xffffffffu, in);
-          if (FILL && in) {
+          if (in) {
             const int k = n + __popc(mm & ((1u << lane) - 1u));
-            if (inl) rec[1 + k] = (uint16_t)(rg.x + q);
-            else R.gover[at + k] = (uint16_t)(rg.x + q);
+            if (!FILL) {   // the count pass writes the first kGridInline in place;
+              if (k < kGridInline) rec[1 + k] = (uint16_t)(rg.x + q);   // the fill pass
+            } else {       // only the cells past kGridInline, into their list
+              R.gover[at + k] = (uint16_t)(rg.x + q);
+            }
           }
           n += __popc(mm);
         }
@@ -210,6 +213,8 @@ __device__ void grid_block(const RunDesc &R) {
   const int nbx = (G + span - 1) / span;
   if (__ldcg(&R.ctl->grid_skip)) return;   // vectors too skewed: no grid for them
   if (FILL && __ldcg(&R.ctl->grid_ver) != __ldcg(&R.ctl->v_ver)) return;   // did not fit
+  // fill: a block without overflow cells was finished by the count pass
+  if (FILL && __ldcg(R.gblk + blockIdx.x + 1) == __ldcg(R.gblk + blockIdx.x)) return;
   // count: this block's overflow candidates (cells past kGridInline); fill:
   // the next free position of the block's range of the overflow area
   if (threadIdx.x == 0) s_ovf = 0;
@@ -254,7 +259,8 @@ __device__ void grid_block(const RunDesc &R) {
       if (FILL) {   // an overflow cell claims its range and records it
         const int cnt = __ldcg(R.gcnt + cell);
         inl = cnt <= kGridInline;
-        if (!inl) {
+        if (inl) continue;   // written by the count pass
+        {
           if (lane == 0) at = base + atomicAdd(&s_ovf, cnt);
           at = __shfl_sync(0xffffffffu, at, 0);
           if (lane == 0) {
@@ -321,6 +327,7 @@ __global__ void __launch_bounds__(1024) k_grid_scan(const RunDesc *__restrict__ 
   }
   if (tid == 1023) {
     const int total = s_w[31];
+    R.gblk[n] = total;   // the end of the last block's range
     if (total <= R.gcap) R.ctl->grid_ver = R.ctl->v_ver;
   }
 }
