@@ -60,16 +60,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Grid-wide barrier over the launch's nb CTAs (all resident).  The arrival
 // counter only grows: every launch adds exactly 3 nb, so an instance's
 // arrivals are the nb values [k nb, (k + 1) nb) and it is complete once the
-// counter reaches (k + 1) nb.  One release-add per CTA, then acquire polls;
-// no reset, so nothing is serialised behind the last arrival.  Returns
-// false, for the whole CTA, when the wait gave up.
-__device__ bool grid_barrier(Ctl *ctl, unsigned nb) {
+// counter reaches `target` = (k + 1) nb.  The launch reads the counter once
+// before its first arrival (floor to a multiple of nb: the launch's base)
+// and derives its three targets, so that an arrival is one release-add
+// with no reply to wait for, then acquire polls; no reset, so nothing is
+// serialised behind the last arrival.  Returns false, for the whole CTA,
+// when the wait gave up.
+__device__ __forceinline__ void red_release_gpu(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ bool grid_barrier(Ctl *ctl, unsigned long long target) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned long long old = add_release_gpu(&ctl->bar, 1ull);
-    const unsigned long long target = (old / nb + 1) * nb;
+    red_release_gpu(&ctl->bar, 1ull);
     if (ld_acquire_gpu(&ctl->bar) < target) {
       const unsigned long long t0 = global_ns();
       for (unsigned it = 1;; ++it) {
@@ -166,6 +171,7 @@ struct TailShared {
   unsigned zpar[4];       // the parents' z*, read before the dependency wait
   float gw[4];            // direction-grid scale of the current vectors
   float pen;              // the APD penalty M (t / t_max)^alpha (Eq. 4)
+  unsigned long long bar0; // the grid barrier counter at this launch's start
   int grid_ok;            // the direction grid matches the current vectors
 };
 
@@ -217,7 +223,10 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   // kernel adds theirs to it, so it is read after the wait instead), and
   // whether the direction grid matches the vectors (its build ran after the
   // previous tail) with its scale.
-  if (tid == 0) {
+  if (tid == kTailThreads - 32) {   // the last warp, which serves no child below 19 k children
+    // the launch's barrier base: the previous launches' arrivals, completed
+    // (a CTA of this launch that arrived already adds less than nb)
+    S.bar0 = (__ldcg(&ctl->bar) / (unsigned long long)nb) * (unsigned long long)nb;
     S.pen = (float)m * powf((float)t / (float)R.t_max, R.alpha);
     S.grid_ok = M <= 3 && R.gG > 0 && __ldcg(&ctl->grid_ver) == __ldcg(&ctl->v_ver);
     for (int q = 0; q < 4; ++q) {
@@ -336,7 +345,7 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   // of z* after the barrier behind all of them
   __syncthreads();
   if (tid < 4) R.zacc[b * 4 + tid] = s_lo[tid];
-  if (!grid_barrier(ctl, nb)) return;
+  if (!grid_barrier(ctl, S.bar0 + (unsigned long long)nb)) return;
   if (tid < kMaxM) s_lo[tid] = 0xFFFFFFFFu;   // for the survivors' minimum in C
   // ---- B: association and APD votes ----------------------------------------
   {
@@ -404,7 +413,7 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
       for (int g = gw; g < groups; g += nw) prune_group<M, false>(R, 4 * g, sV, sC, sCS, sR, z, pen, csb);
     }
   }
-  if (!grid_barrier(ctl, nb)) return;
+  if (!grid_barrier(ctl, S.bar0 + 2ull * nb)) return;
 
   // ---- C: decode of this CTA's vector words --------------------------------
   // vector words [v0, v1) (32 vectors each) and pool-row words [o0, o1) (32
@@ -474,7 +483,7 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     for (int w = 0; w < kTailThreads / 32; ++w) c += s_red[0][w];
     R.vcnt[b] = c;
   }
-  if (!grid_barrier(ctl, nb)) return;
+  if (!grid_barrier(ctl, S.bar0 + 3ull * nb)) return;
 
   // ---- D: lists, next z*, adaptation, control block ------------------------
   // prefix of the valid slots and of the free rows over the CTAs before this
