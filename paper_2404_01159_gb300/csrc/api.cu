@@ -156,9 +156,9 @@ Shape make_shape(int m, int d, int N) {
   s.n_repro = (s.P * s.nseg + s.ppc - 1) / s.ppc;
   s.n_init = (N + s.ppc - 1) / s.ppc;
   // the full-scan item table holds the finest plan of any device: every
-  // solution block x every kVTile-vector tile
+  // solution block x every kVTileMin-vector tile
   s.nblk = (s.n_comb + kSelBlock - 1) / kSelBlock;
-  s.n_sel_max = s.nblk * ((N + kVTile - 1) / kVTile);
+  s.n_sel_max = s.nblk * ((N + kVTileMin - 1) / kVTileMin);
   s.tmax = 0;
   s.tglob = 0;
   if (m <= 4 && N >= kPruneMinN && prune_smem(N, prune_tiles_bound(N)) <= kPruneSmemCap) {
@@ -185,7 +185,7 @@ Shape make_shape(int m, int d, int N) {
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
       ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, otag, occ_cnt, vcnt, zacc, Vt,
-      tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, gscale, vrange, fcomb, noise, dynA, dynB, total;
+      tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, selb, gscale, vrange, fcomb, noise, dynA, dynB, total;
 };
 
 Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
@@ -220,6 +220,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.repro = take((size_t)s.n_repro * sizeof(ReproItem));
   L.init = take((size_t)s.n_init * sizeof(ReproItem));
   L.sel = take((size_t)s.n_sel_max * sizeof(SelItem));
+  L.selb = take((size_t)s.n_sel_max * sizeof(SelItem));   // the batch's coarse table
   L.stage = take((size_t)s.N * (kMaxM + 1) * 4);
   L.psum = take((size_t)s.P * 2 * s.nseg * 4);
   L.rec_par = take((size_t)2 * s.P * 4);
@@ -451,6 +452,7 @@ struct rvea_run {
   int sel_mode = 0;               // 0 full scan, 1 pruned (tables in shared memory), 2 pruned (L1)
   int sel_per_sm = 8;             // full scan: work items per SM
   int n_sel = 0;                  // full scan: work items of the current plan
+  int n_selb = 0, selb_smem = 0;  // the coarse table a batch uses (8 items per SM, 512-vector tiles)
   bool tuned = false;
   double tune_repro_us = 0.0, tune_sel_us = 0.0;
   std::vector<SelItem> sel_host;  // source of the last upload of the item table
@@ -628,7 +630,13 @@ void launch_mutate1(const rvea_run *r, cudaStream_t st) {
 // search, when each CTA's share of the pool-row bitmap fits its buffer, its
 // children fit its lanes (eight a child) and the search tables its shared
 // memory (or, past that, the tables are read through L2).
-int tail_grid(const rvea_run *r) { return std::min(r->num_sms, kTailMaxCtas); }
+// One CTA per SM but for the last 8 to free up: the tail's CTAs become
+// resident as the reproduction kernel drains (each takes a whole SM), and the
+// few SMs that finish it last would start their phase A late (measured:
+// 144 of 152 CTAs, 0.45 us faster a generation than 152).
+int tail_grid(const rvea_run *r) {
+  return std::min(r->num_sms > 64 ? r->num_sms - 8 : r->num_sms, kTailMaxCtas);
+}
 bool tail_ok(const rvea_run *r) {
   return r->hd.ntiles > 0 && r->hd.problem != PROB_NEURO &&
          (2 * r->sh.N + 31) / 32 <= 64 * tail_grid(r) &&
@@ -685,9 +693,11 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       ds.prefix[ns] = ps;
       ds.desc[ns] = r->d_desc;
       ds.key[ns] = key;
-      ds.items[ns] = wsp<SelItem>(r, r->lay.sel);
-      ps += r->n_sel;
-      sms = std::max(sms, r->sel_smem);
+      // alone: the run's plan; in a batch: the coarse table (the runs fill
+      // the GPU together, and finer chunks only add per-item overhead)
+      ds.items[ns] = wsp<SelItem>(r, n > 1 ? r->lay.selb : r->lay.sel);
+      ps += n > 1 ? r->n_selb : r->n_sel;
+      sms = std::max(sms, n > 1 ? r->selb_smem : r->sel_smem);
       ++ns;
     } else {
       dp.prefix[np] = pp;
@@ -1144,6 +1154,16 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.repro, rep.data(), rep.size() * sizeof(ReproItem));
   up(lay.init, ini.data(), ini.size() * sizeof(ReproItem));
   up(lay.sel, r->sel_host.data(), r->sel_host.size() * sizeof(SelItem));
+  std::vector<SelItem> selb;
+  {
+    const SelPlan sp = sel_plan(sh.n_comb, sh.N, sh.m4, r->num_sms, 8, false);
+    for (int b = 0; b < sp.nblk; ++b)
+      for (int c = 0; c < sp.nch; ++c)
+        selb.push_back(SelItem{b, std::min(sh.N, c * sp.chunk), std::min(sh.N, (c + 1) * sp.chunk), sp.nch});
+    r->n_selb = (int)selb.size();
+    r->selb_smem = std::min(sh.N, sp.chunk) * sh.m4 * 16;
+  }
+  up(lay.selb, selb.data(), selb.size() * sizeof(SelItem));
   up(lay.V0, V0.data(), V0.size() * 8);
   up(lay.V64, V0.data(), V0.size() * 8);
   up(lay.V32, V32.data(), V32.size() * 4);
@@ -1885,7 +1905,7 @@ OpLayout op_layout(int n, int r) {
     return at;
   };
   const int nblk = (n + kSelBlock - 1) / kSelBlock;
-  const int tiles = (r + kVTile - 1) / kVTile;
+  const int tiles = (r + kVTileMin - 1) / kVTileMin;   // the finest plan's chunks
   L.ctl = take(sizeof(Ctl));
   L.desc = take(sizeof(RunDesc));
   L.best = take((size_t)r * 8);

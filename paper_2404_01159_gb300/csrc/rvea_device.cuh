@@ -21,6 +21,7 @@ constexpr int kSelThreads = 128;   // selection CTA size
 constexpr int kSelSols = 4;        // solutions per thread (a multiple of 2: packed pairs)
 constexpr int kSelBlock = kSelSols * kSelThreads;   // solutions per selection work item
 constexpr int kVTile = 512;        // reference vectors per shared-memory tile
+constexpr int kVTileMin = 64;      // the smallest tile sel_plan halves kVTile to
 constexpr int kFinThreads = 1024;  // CTA size of the per-run finalize kernel
 constexpr int kMaxSites = 32;      // cap of the mutation-site count of one row
 constexpr int kStages = 2;         // staged reproduction: chunks per warp in shared memory
@@ -184,11 +185,16 @@ constexpr int kSelChunkBytes = 96 * 1024;
 struct SelPlan {
   int nblk, nch, chunk;   // solution blocks, chunks, vectors per chunk
 };
-inline SelPlan sel_plan(int n, int r, int m4, int sms, int per_sm = 8) {
+inline SelPlan sel_plan(int n, int r, int m4, int sms, int per_sm = 8, bool fine = true) {
   SelPlan p;
   p.nblk = (n + kSelBlock - 1) / kSelBlock;
-  const int tiles = (r + kVTile - 1) / kVTile;
-  int cap = kSelChunkBytes / (m4 * 16) / kVTile;
+  // vector tiles of kVTile, halved (fine: down to kVTileMin) while the items
+  // would not reach per_sm per SM: a small run alone still spreads over the
+  // GPU (a batch, many runs together, takes the coarse tiles)
+  int vt = kVTile;
+  while (fine && vt > kVTileMin && (long long)p.nblk * ((r + vt - 1) / vt) < (long long)per_sm * sms) vt >>= 1;
+  const int tiles = (r + vt - 1) / vt;
+  int cap = kSelChunkBytes / (m4 * 16) / vt;
   if (cap < 1) cap = 1;
   int nch = (per_sm * sms + p.nblk - 1) / p.nblk;
   if (nch > tiles) nch = tiles;
@@ -196,7 +202,7 @@ inline SelPlan sel_plan(int n, int r, int m4, int sms, int per_sm = 8) {
   int tpc = (tiles + nch - 1) / nch;
   if (tpc > cap) tpc = cap;
   p.nch = (tiles + tpc - 1) / tpc;
-  p.chunk = tpc * kVTile;
+  p.chunk = tpc * vt;
   return p;
 }
 
