@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("alpha", C.c_double), ("f_r", C.c_double), ("eta_c", C.c_double),
                 ("eta_m", C.c_double), ("p_c", C.c_double), ("p_m", C.c_double),
                 ("L", C.c_double), ("U", C.c_double), ("seed", C.c_uint64),
-                ("op", C.c_int32), ("de_F", C.c_double), ("de_CR", C.c_double)]
+                ("op", C.c_int32), ("de_F", C.c_double), ("de_CR", C.c_double),
+                ("cso_phi", C.c_double)]
 
 
 class Neuro(C.Structure):
@@ -89,6 +90,13 @@ def lib():
         L.orc_de_picks.argtypes = [P(Params), C.c_int32, C.c_int32, C.c_int32, i32]
         L.orc_de_offspring.argtypes = [P(Params), C.c_int32, f64, C.c_int32, i32,
                                        C.c_double, C.c_double, f64]
+        L.orc_cso_picks.argtypes = [P(Params), C.c_int32, C.c_int32, C.c_int32, i32]
+        L.orc_cso_offspring.argtypes = [P(Params), C.c_int32, f64, f64, f64, C.c_int32, i32,
+                                        f64, f64, f64]
+        L.orc_generation_ex.argtypes = [P(Params), C.c_int32, f64, P(Neuro),
+                                        f64, f64, u8, f64, f64, f64, f64, f64, f64, i32,
+                                        i32, i32]
+        L.orc_generation_ex.restype = C.c_int32
         L.orc_set_threads.argtypes = [C.c_int32]
         L.orc_get_threads.restype = C.c_int32
         _lib = L
@@ -117,14 +125,33 @@ def philox(ctr, key):
     return [int(x) for x in o]
 
 
-OP_SBX_PM, OP_DE, OP_RANDOM = 0, 1, 2
+OP_SBX_PM, OP_DE, OP_RANDOM, OP_CSO = 0, 1, 2, 3
 
 
 def make_params(m, d, N, H, problem=DTLZ2, t_max=100, alpha=2.0, f_r=0.1,
                 eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, L=0.0, U=1.0, seed=0,
-                op=OP_SBX_PM, de_F=0.5, de_CR=0.9):
+                op=OP_SBX_PM, de_F=0.5, de_CR=0.9, cso_phi=0.0):
     return Params(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
-                  L, U, seed, op, de_F, de_CR)
+                  L, U, seed, op, de_F, de_CR, cso_phi)
+
+
+def cso_picks(p: Params, t: int, K: int, o: int):
+    """Positions in the valid list of offspring o's two competitors (CSO)."""
+    out = np.zeros(2, dtype=np.int32)
+    lib().orc_cso_picks(C.byref(p), int(t), int(K), int(o), _p(out, C.c_int32))
+    return int(out[0]), int(out[1])
+
+
+def cso_offspring(p: Params, t: int, X, Vel, apd, vlist, xbar):
+    """CSO offspring positions and velocities (N x d each)."""
+    X, Vel, apd, xbar = _f64(X), _f64(Vel), _f64(apd), _f64(xbar)
+    vl = np.ascontiguousarray(vlist, dtype=np.int32)
+    Xo = np.zeros((p.N, p.d))
+    Vo = np.zeros((p.N, p.d))
+    lib().orc_cso_offspring(C.byref(p), int(t), _p(X, C.c_double), _p(Vel, C.c_double),
+                            _p(apd, C.c_double), len(vl), _p(vl, C.c_int32),
+                            _p(xbar, C.c_double), _p(Xo, C.c_double), _p(Vo, C.c_double))
+    return Xo, Vo
 
 
 def lattice_count(m, H) -> int:
@@ -287,8 +314,14 @@ def select(F, valid, V, gam, t, t_max, alpha):
 class State:
     """Population in vector-slot order, as the oracle's generation consumes it."""
 
-    def __init__(self, X, F, valid, V, gamma, t):
+    def __init__(self, X, F, valid, V, gamma, t, vel=None, apd=None):
         self.X = np.array(X, dtype=np.float64, order="C", copy=True)
+        # the CSO swarm state: velocities (zero at first) and the APD that
+        # kept each member (+inf before any selection)
+        self.vel = (np.zeros_like(self.X) if vel is None
+                    else np.array(vel, dtype=np.float64, order="C", copy=True))
+        self.apd = (np.full(self.X.shape[0], np.inf) if apd is None
+                    else np.array(apd, dtype=np.float64, order="C", copy=True))
         self.F = np.array(F, dtype=np.float64, order="C", copy=True)
         self.valid = np.array(valid, dtype=np.uint8, order="C", copy=True)
         self.V = np.array(V, dtype=np.float64, order="C", copy=True)
@@ -313,12 +346,13 @@ def generation(p: Params, V0, st: State, nd=None):
     assoc = np.zeros(2 * p.N, dtype=np.int32)
     surv = np.zeros(p.N, dtype=np.int32)
     V0 = _f64(V0)
-    alive = lib().orc_generation(C.byref(p), st.t, _p(V0, C.c_double), _nd(nd),
-                                 _p(st.X, C.c_double), _p(st.F, C.c_double),
-                                 _p(st.valid, C.c_uint8), _p(st.V, C.c_double),
-                                 _p(st.gamma, C.c_double), _p(Xc, C.c_double),
-                                 _p(Fc, C.c_double), _p(par, C.c_int32),
-                                 _p(assoc, C.c_int32), _p(surv, C.c_int32))
+    alive = lib().orc_generation_ex(C.byref(p), st.t, _p(V0, C.c_double), _nd(nd),
+                                    _p(st.X, C.c_double), _p(st.F, C.c_double),
+                                    _p(st.valid, C.c_uint8), _p(st.V, C.c_double),
+                                    _p(st.gamma, C.c_double), _p(st.vel, C.c_double),
+                                    _p(st.apd, C.c_double), _p(Xc, C.c_double),
+                                    _p(Fc, C.c_double), _p(par, C.c_int32),
+                                    _p(assoc, C.c_int32), _p(surv, C.c_int32))
     st.t += 1
     return dict(Xchild=Xc, Fchild=Fc, parents=par, assoc=assoc, survivor=surv,
                 alive=alive)

@@ -503,6 +503,62 @@ void orc_de_offspring(const orc_params *p, int32_t t, const double *X, int32_t K
     }
 }
 
+/* The competitive swarm optimizer (CSO; Cheng and Jin, "A competitive swarm
+ * optimizer for large scale optimization", IEEE T-Cyb 2015) as the
+ * reproduction operator.  The paper names it and plugs it into the same
+ * selection without printing it; the reading (listed with the others in the
+ * design notes): each of the N offspring comes from one competition between
+ * two distinct valid members (positions a then b of the valid list, drawn
+ * without replacement: a = (w0 K) >> 32, b = (w1 (K-1)) >> 32 counted over
+ * the positions other than a, CSO_PICK (o, 0, t) words 0 and 1; with K = 1
+ * the member meets itself).  The winner has the smaller APD from the
+ * selection that kept it (Eq. 4; +inf before any selection), ties to the
+ * smaller population index.  The loser learns (Cheng and Jin's update):
+ *   v' = r1 v_l + r2 (x_w - x_l) + phi r3 (xbar - x_l),   x' = x_l + v',
+ * r1, r2, r3 the u24 words 0, 1, 2 of CSO_R (j, o, t) per variable j, xbar the
+ * mean position of the valid members; x' is clipped to [L, U] (v' is kept as
+ * computed).  Offspring o is (x', v'); winners pass on only as parents. */
+void orc_cso_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out)
+{
+    uint32_t w[4];
+    philox(p, (uint32_t)o, 0u, (uint32_t)t, ORC_TAG_CSO_PICK, w);
+    const int32_t a = (int32_t)(((uint64_t)w[0] * (uint64_t)K) >> 32);
+    int32_t b = a;
+    if (K > 1) {
+        b = (int32_t)(((uint64_t)w[1] * (uint64_t)(K - 1)) >> 32);
+        if (b >= a) b += 1;
+    }
+    out[0] = a;
+    out[1] = b;
+}
+
+void orc_cso_offspring(const orc_params *p, int32_t t, const double *X, const double *Vel,
+                       const double *apd, int32_t K, const int32_t *vlist, const double *xbar,
+                       double *Xout, double *Vout)
+{
+    const int32_t N = p->N, d = p->d;
+    for (int32_t o = 0; o < N; ++o) {
+        int32_t pk[2];
+        orc_cso_picks(p, t, K, o, pk);
+        const int32_t ia = vlist[pk[0]], ib = vlist[pk[1]];
+        const int a_wins = apd[ia] < apd[ib] || (apd[ia] == apd[ib] && ia <= ib);
+        const int32_t iw = a_wins ? ia : ib, il = a_wins ? ib : ia;
+        const double *xw = X + (int64_t)iw * d, *xl = X + (int64_t)il * d;
+        const double *vl = Vel + (int64_t)il * d;
+        for (int32_t j = 0; j < d; ++j) {
+            uint32_t w[4];
+            philox(p, (uint32_t)j, (uint32_t)o, (uint32_t)t, ORC_TAG_CSO_R, w);
+            const double v = u24(w[0]) * vl[j] + u24(w[1]) * (xw[j] - xl[j]) +
+                             p->cso_phi * u24(w[2]) * (xbar[j] - xl[j]);
+            double x = xl[j] + v;
+            if (x < p->L) x = p->L;
+            if (x > p->U) x = p->U;
+            Xout[(int64_t)o * d + j] = x;
+            Vout[(int64_t)o * d + j] = v;
+        }
+    }
+}
+
 /* Tensorized SBX, Appendix B (the two B equations and X_cross):
  *   B  = sgn(R1 - 1/2) [H(1/2 - Mc)(2Mc)^(1/(eta+1)) + (1 - H(1/2 - Mc))(2 - 2Mc)^(-1/(eta+1))]
  *   B  = [1 - rep(H(R3 - p_c))] [(1 - H(R2 - 1/2)) B + H(R2 - 1/2)] + rep(H(R3 - p_c))
@@ -754,6 +810,21 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
                        double *Xchild, double *Fchild, int32_t *parents,
                        int32_t *assoc, int32_t *survivor)
 {
+    return orc_generation_ex(p, t, V0, nd, X, F, valid, V, gamma, NULL, NULL,
+                             Xchild, Fchild, parents, assoc, survivor);
+}
+
+/* The same with the swarm state of the CSO operator: Vel (N x d, velocities
+ * by slot) and apd (N, the APD that kept each member; +inf before any
+ * selection), both updated with the population.  They may be NULL for the
+ * other operators (apd is then not kept). */
+int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
+                          const orc_neuro *nd,
+                          double *X, double *F, uint8_t *valid, double *V, double *gamma,
+                          double *Vel, double *apd,
+                          double *Xchild, double *Fchild, int32_t *parents,
+                          int32_t *assoc, int32_t *survivor)
+{
     const int32_t N = p->N, d = p->d, m = p->m, P = (p->N + 1) / 2;
     int32_t *vlist = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     int32_t K = 0;
@@ -763,6 +834,7 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
 
     int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * P));
     double *Xc = (double *)malloc(sizeof(double) * (size_t)(2 * P) * d);
+    double *Vc = NULL;   /* the offspring's velocities (CSO) */
     if (p->op == ORC_OP_DE) {
         /* the extensibility experiment's operators replace SBX and mutation */
         for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
@@ -770,6 +842,16 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
     } else if (p->op == ORC_OP_RANDOM) {
         for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
         orc_random_offspring(p, t, Xc);
+    } else if (p->op == ORC_OP_CSO) {
+        for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
+        if (!Vel || !apd) { free(vlist); free(par); free(Xc); return -1; }
+        double *xbar = (double *)calloc((size_t)d, sizeof(double));
+        for (int32_t k = 0; k < K; ++k)
+            for (int32_t j = 0; j < d; ++j) xbar[j] += X[(int64_t)vlist[k] * d + j];
+        for (int32_t j = 0; j < d; ++j) xbar[j] /= (double)K;
+        Vc = (double *)malloc(sizeof(double) * (size_t)N * d);
+        orc_cso_offspring(p, t, X, Vel, apd, K, vlist, xbar, Xc, Vc);
+        free(xbar);
     } else {
         orc_mating(p, t, K, vlist, par);
         double *X1 = (double *)malloc(sizeof(double) * (size_t)P * d);
@@ -796,8 +878,9 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
     for (int32_t j = 0; j < N; ++j) { vall[j] = valid[j]; vall[N + j] = 1; }
     int32_t *as = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *sv = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    double *apd_all = (double *)malloc(sizeof(double) * (size_t)n);
     orc_select(m, n, Fall, vall, N, V, gamma, t, p->t_max, p->alpha,
-               NULL, as, NULL, NULL, sv);
+               NULL, as, NULL, apd_all, sv);
 
     if (Xchild) memcpy(Xchild, Xc, sizeof(double) * (size_t)N * d);
     if (Fchild) memcpy(Fchild, Fc, sizeof(double) * (size_t)N * m);
@@ -805,9 +888,11 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
     if (assoc) memcpy(assoc, as, sizeof(int32_t) * (size_t)n);
     if (survivor) memcpy(survivor, sv, sizeof(int32_t) * (size_t)N);
 
-    /* P_{t+1}: slot j holds the survivor of vector j */
+    /* P_{t+1}: slot j holds the survivor of vector j (with its velocity and
+     * the APD it was kept with) */
     double *Xn = (double *)malloc(sizeof(double) * (size_t)N * d);
     double *Fn = (double *)malloc(sizeof(double) * (size_t)N * m);
+    double *Vn = Vel ? (double *)malloc(sizeof(double) * (size_t)N * d) : NULL;
     int32_t alive = 0;
     for (int32_t j = 0; j < N; ++j) {
         int32_t i = sv[j];
@@ -815,6 +900,8 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
             valid[j] = 0;
             for (int32_t k = 0; k < d; ++k) Xn[(int64_t)j * d + k] = NAN;
             for (int32_t k = 0; k < m; ++k) Fn[(int64_t)j * m + k] = NAN;
+            if (Vn) for (int32_t k = 0; k < d; ++k) Vn[(int64_t)j * d + k] = NAN;
+            if (apd) apd[j] = INFINITY;
             continue;
         }
         valid[j] = 1;
@@ -823,9 +910,17 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
         const double *fs = Fall + (int64_t)i * m;
         memcpy(Xn + (int64_t)j * d, xs, sizeof(double) * (size_t)d);
         memcpy(Fn + (int64_t)j * m, fs, sizeof(double) * (size_t)m);
+        if (Vn) {
+            double *vd = Vn + (int64_t)j * d;
+            if (i < N) memcpy(vd, Vel + (int64_t)i * d, sizeof(double) * (size_t)d);
+            else if (Vc) memcpy(vd, Vc + (int64_t)(i - N) * d, sizeof(double) * (size_t)d);
+            else for (int32_t k = 0; k < d; ++k) vd[k] = 0.0;
+        }
+        if (apd) apd[j] = apd_all[i];
     }
     memcpy(X, Xn, sizeof(double) * (size_t)N * d);
     memcpy(F, Fn, sizeof(double) * (size_t)N * m);
+    if (Vn) { memcpy(Vel, Vn, sizeof(double) * (size_t)N * d); free(Vn); }
 
     /* reference-vector adaptation every round(f_r * t_max) generations */
     int32_t period = (int32_t)floor(p->f_r * (double)p->t_max + 0.5);
@@ -837,7 +932,7 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
         orc_gamma(m, N, V, gamma);
     }
 
-    free(Xn); free(Fn); free(as); free(sv); free(vall); free(Fall);
-    free(Fc); free(Xc); free(par); free(vlist);
+    free(Xn); free(Fn); free(as); free(sv); free(vall); free(Fall); free(apd_all);
+    free(Fc); free(Xc); free(Vc); free(par); free(vlist);
     return alive;
 }

@@ -22,6 +22,8 @@
  *   MUTMAG (j,   c, t, 6)  word1 -> M_mut (u24) of site j of child c
  *   INIT   (j,   i, 0, 1)  words 0,1 -> Box-Muller N(0,1) (neuroevolution weights)
  *   NOISE  (k,   s, t, 7)  words 0,1 -> Box-Muller N(0,1), state component k, step s
+ *   CSO_PICK (o, 0, t, 11) words 0,1 -> the two competitors of offspring o
+ *   CSO_R  (j,   o, t, 12) words 0,1,2 -> r1, r2, r3 (u24) of variable j of offspring o
  * where u24(w) = (w >> 8) * 2^-24.
  */
 #ifndef RVEA_ORACLE_H
@@ -36,7 +38,8 @@ extern "C" {
 enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2, ORC_DTLZ3 = 3, ORC_DTLZ4 = 4 };
 enum { ORC_TAG_INIT = 1, ORC_TAG_MATE = 2, ORC_TAG_PAIR = 3, ORC_TAG_SBX = 4,
        ORC_TAG_MUTSITE = 5, ORC_TAG_MUTMAG = 6, ORC_TAG_NOISE = 7,
-       ORC_TAG_DE_PICK = 8, ORC_TAG_DE_CR = 9, ORC_TAG_RANDOM = 10 };
+       ORC_TAG_DE_PICK = 8, ORC_TAG_DE_CR = 9, ORC_TAG_RANDOM = 10,
+       ORC_TAG_CSO_PICK = 11, ORC_TAG_CSO_R = 12 };
 
 typedef struct {
     int32_t m, d, N, H;
@@ -46,11 +49,13 @@ typedef struct {
     uint64_t seed;
     int32_t op;               /* reproduction: ORC_OP_SBX_PM, ORC_OP_DE, ORC_OP_RANDOM */
     double de_F, de_CR;       /* DE/rand/1/bin scale factor and crossover rate   */
+    double cso_phi;           /* CSO: weight of the swarm-centre term            */
 } orc_params;
 
 /* Reproduction operators (Sec. 4.4, the extensibility experiment): SBX with
- * polynomial mutation (Appendix B), DE/rand/1/bin, random reproduction. */
-enum { ORC_OP_SBX_PM = 0, ORC_OP_DE = 1, ORC_OP_RANDOM = 2 };
+ * polynomial mutation (Appendix B), DE/rand/1/bin, random reproduction, the
+ * competitive swarm optimizer. */
+enum { ORC_OP_SBX_PM = 0, ORC_OP_DE = 1, ORC_OP_RANDOM = 2, ORC_OP_CSO = 3 };
 
 /* Synthetic linear-dynamics rollout used as the neuroevolution objective. */
 typedef struct {
@@ -96,6 +101,16 @@ void orc_random_offspring(const orc_params *p, int32_t t, double *Xout);
 void orc_de_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out);
 void orc_de_offspring(const orc_params *p, int32_t t, const double *X, int32_t K,
                       const int32_t *vlist, double F, double CR, double *Xout);
+void orc_cso_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out);
+void orc_cso_offspring(const orc_params *p, int32_t t, const double *X, const double *Vel,
+                       const double *apd, int32_t K, const int32_t *vlist, const double *xbar,
+                       double *Xout, double *Vout);
+int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
+                          const orc_neuro *nd,
+                          double *X, double *F, uint8_t *valid, double *V, double *gamma,
+                          double *Vel, double *apd,
+                          double *Xchild, double *Fchild, int32_t *parents,
+                          int32_t *assoc, int32_t *survivor);
 void orc_set_threads(int32_t n);
 int32_t orc_get_threads(void);
 

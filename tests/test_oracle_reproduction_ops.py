@@ -144,3 +144,121 @@ def test_generation_uses_the_operator(orc, op):
     assert np.array_equal(out["Fchild"], orc.evaluate(p, want, t))
     assert (out["parents"] == -1).all()
     assert (out["survivor"] >= -1).all() and (np.bincount(out["survivor"][out["survivor"] >= 0]) <= 1).all()
+
+
+# ---- the competitive swarm optimizer (CSO; Cheng and Jin 2015) -----------
+
+def test_cso_picks_distinct_and_uniform(orc):
+    """Two distinct positions of the valid list, every ordered pair about
+    equally often; a one-member list meets itself."""
+    p = _p(orc)
+    K, n = 5, 20000
+    counts = np.zeros((K, K), dtype=int)
+    for o in range(n):
+        a, b = orc.cso_picks(p, 3, K, o)
+        assert 0 <= a < K and 0 <= b < K and a != b
+        counts[a, b] += 1
+    off = counts[~np.eye(K, dtype=bool)]
+    exp = n / (K * (K - 1))
+    assert ((off - exp) ** 2 / exp).sum() < 60   # chi-square, 19 dof
+    assert orc.cso_picks(p, 3, 1, 7) == (0, 0)
+
+
+def _competition(orc, p, t, o, vlist, apd):
+    a, b = orc.cso_picks(p, t, len(vlist), o)
+    ia, ib = vlist[a], vlist[b]
+    w = ia if (apd[ia] < apd[ib] or (apd[ia] == apd[ib] and ia <= ib)) else ib
+    return w, (ib if w == ia else ia)
+
+
+def test_cso_loser_moves_towards_winner(orc):
+    """With zero velocities and phi = 0 (a first generation), the loser's new
+    position lies on the segment to the winner, coordinate by coordinate, its
+    velocity is the displacement, and across many variables it covers the
+    segment uniformly (mean 1/2 of the way)."""
+    p = _p(orc, N=40, d=500, cso_phi=0.0)
+    rng = np.random.default_rng(1)
+    X = rng.uniform(size=(40, 500))
+    apd = rng.uniform(size=40)
+    vlist = np.arange(40)
+    Xo, Vo = orc.cso_offspring(p, 2, X, np.zeros_like(X), apd, vlist, X.mean(0))
+    fr = []
+    for o in range(40):
+        w, l = _competition(orc, p, 2, o, vlist, apd)
+        lo, hi = np.minimum(X[w], X[l]), np.maximum(X[w], X[l])
+        assert (Xo[o] >= lo - 1e-15).all() and (Xo[o] <= hi + 1e-15).all()
+        assert np.allclose(Vo[o], Xo[o] - X[l], atol=1e-15)
+        span = X[w] - X[l]
+        ok = np.abs(span) > 1e-3
+        fr.append(((Xo[o] - X[l])[ok] / span[ok]))
+    fr = np.concatenate(fr)
+    assert abs(fr.mean() - 0.5) < 5 * np.sqrt(1 / 12 / fr.size)
+    assert fr.min() >= 0.0 and fr.max() < 1.0
+
+
+def test_cso_winner_rule_and_velocity_term(orc):
+    """The smaller APD wins, ties to the smaller index (all +inf before any
+    selection); with the positions equal, the update is r1 v alone: every
+    coordinate of the new velocity is a fraction in [0, 1) of the old one,
+    of mean 1/2."""
+    p = _p(orc, N=64, d=300, cso_phi=0.0)
+    X = np.full((64, 300), 0.5)
+    Vel = np.random.default_rng(2).uniform(-0.2, 0.2, size=(64, 300))
+    apd = np.full(64, np.inf)
+    vlist = np.arange(64)
+    Xo, Vo = orc.cso_offspring(p, 5, X, Vel, apd, vlist, X.mean(0))
+    ratios = []
+    for o in range(64):
+        w, l = _competition(orc, p, 5, o, vlist, apd)
+        a, b = orc.cso_picks(p, 5, 64, o)
+        assert l == max(a, b)          # ties: the smaller index wins
+        r = Vo[o] / Vel[l]
+        assert (r >= 0).all() and (r < 1).all()
+        assert np.allclose(Xo[o], np.clip(0.5 + Vo[o], 0, 1), atol=1e-15)
+        ratios.append(r)
+    r = np.concatenate(ratios)
+    assert abs(r.mean() - 0.5) < 5 * np.sqrt(1 / 12 / r.size)
+
+
+def test_cso_centre_term_and_clip(orc):
+    """phi pulls the loser towards the swarm centre: with winner = loser (one
+    member) and zero velocity, x' = x + phi r3 (xbar - x), clipped to the
+    box."""
+    p = _p(orc, N=1, d=400, cso_phi=0.3, L=0.0, U=1.0)
+    X = np.random.default_rng(3).uniform(size=(1, 400))
+    xbar = np.full(400, 0.9)
+    Xo, Vo = orc.cso_offspring(p, 1, X, np.zeros_like(X), np.zeros(1), np.array([0]), xbar)
+    frac = Vo[0] / (0.3 * (xbar - X[0]))
+    assert (frac >= 0).all() and (frac < 1).all()
+    assert abs(frac.mean() - 0.5) < 5 * np.sqrt(1 / 12 / 400)
+    assert np.array_equal(Xo[0], np.clip(X[0] + Vo[0], 0.0, 1.0))
+
+
+def test_generation_with_cso_keeps_the_swarm_state(orc):
+    """A CSO generation makes its offspring with the operator (from the
+    population, its velocities, the kept APDs and the swarm centre), and the
+    survivors carry their velocities and the APD that kept them."""
+    p = orc.make_params(m=3, d=9, N=105, H=13, problem=orc.DTLZ1, t_max=20, seed=4,
+                        op=orc.OP_CSO, cso_phi=0.2)
+    V0, st = orc.initial_state(p)
+    orc.generation(p, V0, st)               # every member gets an APD
+    st.valid[[3, 17, 40]] = 0
+    X, Vel, apd, vlist = st.X.copy(), st.vel.copy(), st.apd.copy(), np.nonzero(st.valid)[0]
+    t = st.t
+    F_old, valid_old, V_t, g_t = st.F.copy(), st.valid.copy(), st.V.copy(), st.gamma.copy()
+    out = orc.generation(p, V0, st)
+    want_x, want_v = orc.cso_offspring(p, t, X, Vel, apd, vlist, X[vlist].mean(0))
+    assert np.allclose(out["Xchild"], want_x, rtol=0, atol=1e-12)
+    assert (out["parents"] == -1).all()
+    # the APDs the survivors were kept with: the selection's, recomputed
+    sel = orc.select(np.concatenate([np.nan_to_num(F_old), out["Fchild"]]),
+                     np.concatenate([valid_old, np.ones(p.N, np.uint8)]), V_t, g_t, t,
+                     p.t_max, p.alpha)
+    for j in range(p.N):
+        i = out["survivor"][j]
+        if i < 0:
+            assert not st.valid[j] and np.isinf(st.apd[j])
+            continue
+        src_v = Vel[i] if i < p.N else want_v[i - p.N]
+        assert np.allclose(st.vel[j], src_v, rtol=0, atol=1e-12)
+        assert st.apd[j] == sel["apd"][i]
