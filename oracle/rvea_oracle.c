@@ -515,9 +515,11 @@ void orc_de_offspring(const orc_params *p, int32_t t, const double *X, int32_t K
  * selection that kept it (Eq. 4; +inf before any selection), ties to the
  * smaller population index.  The loser learns (Cheng and Jin's update):
  *   v' = r1 v_l + r2 (x_w - x_l) + phi r3 (xbar - x_l),   x' = x_l + v',
- * r1, r2, r3 the u24 words 0, 1, 2 of CSO_R (j, o, t) per variable j, xbar the
- * mean position of the valid members; x' is clipped to [L, U] (v' is kept as
- * computed).  Offspring o is (x', v'); winners pass on only as parents. */
+ * with r1, r2, r3 of variable j the u24 of word j%4 of CSO_R (3 (j/4) + k,
+ * o, t) for k = 0, 1, 2 (each Philox call serves four consecutive variables),
+ * xbar the mean position of the valid members; x' is clipped to [L, U] (v' is
+ * kept as computed).  Offspring o is (x', v'); winners pass on only as
+ * parents. */
 void orc_cso_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out)
 {
     uint32_t w[4];
@@ -546,10 +548,14 @@ void orc_cso_offspring(const orc_params *p, int32_t t, const double *X, const do
         const double *xw = X + (int64_t)iw * d, *xl = X + (int64_t)il * d;
         const double *vl = Vel + (int64_t)il * d;
         for (int32_t j = 0; j < d; ++j) {
-            uint32_t w[4];
-            philox(p, (uint32_t)j, (uint32_t)o, (uint32_t)t, ORC_TAG_CSO_R, w);
-            const double v = u24(w[0]) * vl[j] + u24(w[1]) * (xw[j] - xl[j]) +
-                             p->cso_phi * u24(w[2]) * (xbar[j] - xl[j]);
+            double r[3];
+            for (int32_t k = 0; k < 3; ++k) {
+                uint32_t w[4];
+                philox(p, (uint32_t)(3 * (j / 4) + k), (uint32_t)o, (uint32_t)t, ORC_TAG_CSO_R, w);
+                r[k] = u24(w[j % 4]);
+            }
+            const double v = r[0] * vl[j] + r[1] * (xw[j] - xl[j]) +
+                             p->cso_phi * r[2] * (xbar[j] - xl[j]);
             double x = xl[j] + v;
             if (x < p->L) x = p->L;
             if (x > p->U) x = p->U;

@@ -23,7 +23,8 @@
  *   INIT   (j,   i, 0, 1)  words 0,1 -> Box-Muller N(0,1) (neuroevolution weights)
  *   NOISE  (k,   s, t, 7)  words 0,1 -> Box-Muller N(0,1), state component k, step s
  *   CSO_PICK (o, 0, t, 11) words 0,1 -> the two competitors of offspring o
- *   CSO_R  (j,   o, t, 12) words 0,1,2 -> r1, r2, r3 (u24) of variable j of offspring o
+ *   CSO_R  (3(j/4)+k, o, t, 12) word j%4 -> r_{k+1} (u24), k = 0,1,2, of variable j of
+ *                          offspring o
  * where u24(w) = (w >> 8) * 2^-24.
  */
 #ifndef RVEA_ORACLE_H
