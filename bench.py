@@ -35,7 +35,20 @@ WORKLOADS = {
     "dtlz2_m3_d12_N105": dict(m=3, d=12, N=105, H=13, problem=0, t_max=100),
     "dtlz3_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=3, t_max=1000),
     "dtlz4_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=4, t_max=1000),
+    # the extensibility experiment's reproduction operators (Sec. 4.4) on the
+    # large-scale configuration: DE/rand/1/bin, random reproduction, CSO
+    "de_dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000,
+                                    reproduction=1, de_F=0.5, de_CR=0.9),
+    "random_dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000,
+                                        reproduction=2),
+    "cso_dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000,
+                                     reproduction=3, cso_phi=0.1),
 }
+OPS = {0: "k_repro (mating + SBX + g-terms; mutation and evaluation in k_mutate when d > 1024)",
+       1: "k_repro_op (DE/rand/1/bin: four rows read, one child row written, evaluation)",
+       2: "k_repro_op (random reproduction: one child row written, evaluation)",
+       3: "k_cso_mean + k_repro_op (CSO: swarm centre over the valid rows; winner, loser and "
+          "loser velocity rows read, child row and velocity written; evaluation)"}
 COMMON = dict(alpha=2.0, f_r=0.1, eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
 
 
@@ -57,10 +70,32 @@ def replica_value(world: int, steps: int, ms_max: float) -> float:
 
 
 def repro_bytes(wl) -> int:
-    """Algorithmic bytes of one reproduction launch: read 2*ceil(N/2) parent
-    rows, write N child rows, d float32 each (objectives are O(N m))."""
-    P = (wl["N"] + 1) // 2
-    return (2 * P + wl["N"]) * wl["d"] * 4
+    """Algorithmic bytes of one generation's reproduction, d float32 per row
+    (objectives are O(N m)).  SBX: read 2*ceil(N/2) parent rows, write N
+    child rows.  DE/rand/1/bin: read four rows (target, r1, r2, r3), write one,
+    per offspring.  Random: write N rows.  CSO: read the winner's and loser's
+    rows and the loser's velocity, write the child's row and velocity, per
+    offspring, plus (phi > 0) one pass over the valid rows for the centre,
+    counted as N rows (all slots valid)."""
+    N, d, op = wl["N"], wl["d"], wl.get("reproduction", 0)
+    if op == 1:
+        return 5 * N * d * 4
+    if op == 2:
+        return N * d * 4
+    if op == 3:
+        return (5 + (1 if wl.get("cso_phi", 0.0) > 0 else 0)) * N * d * 4
+    P = (N + 1) // 2
+    return (2 * P + N) * d * 4
+
+
+def oracle_params(orc, wl, seed=0):
+    """The oracle's parameters of a bench workload (its operator included)."""
+    extra = {}
+    if wl.get("reproduction", 0):
+        extra = dict(op=wl["reproduction"], de_F=wl.get("de_F", 0.5), de_CR=wl.get("de_CR", 0.9),
+                     cso_phi=wl.get("cso_phi", 0.0))
+    return orc.make_params(m=wl["m"], d=wl["d"], N=wl["N"], H=wl["H"], problem=wl["problem"],
+                           t_max=wl["t_max"], seed=seed, **COMMON, **extra)
 
 
 def peaks():
@@ -158,8 +193,7 @@ def cpu_baseline(wl, seconds=20.0):
     from oracle import oracle as orc
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    p = orc.make_params(m=wl["m"], d=wl["d"], N=wl["N"], H=wl["H"], problem=wl["problem"],
-                        t_max=wl["t_max"], seed=0, **COMMON)
+    p = oracle_params(orc, wl)
     V0, st = orc.initial_state(p)
     n = 0
     t0 = time.perf_counter()
@@ -180,8 +214,7 @@ def run_reference(args, wl, rank, world):
     from oracle import oracle as orc
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    p = orc.make_params(m=wl["m"], d=wl["d"], N=wl["N"], H=wl["H"], problem=wl["problem"],
-                        t_max=wl["t_max"], seed=0, **COMMON)
+    p = oracle_params(orc, wl)
     V0, st = orc.initial_state(p)
     for _ in range(min(args.warmup, 1)):
         orc.generation(p, V0, st)
@@ -901,8 +934,7 @@ def main():
                    "l2": f"no flush: {2 * N * d * 4 / 1e6:.0f} MB moved per generation "
                          f"> 129 MB L2 (inputs larger than L2)",
                    "generations": f"t = {t_first}..{t_first + K - 1}"},
-        "roofline": {"kernel": "k_repro (mating + SBX + g-terms; mutation and evaluation "
-                               "in k_mutate when d > 1024)", "bound": "hbm",
+        "roofline": {"kernel": OPS[wl.get("reproduction", 0)], "bound": "hbm",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": profiled_traffic(args.workload),

@@ -105,6 +105,7 @@ typedef struct {
     int reproduction; /* rvea_reproduction (0: SBX + polynomial mutation)   */
     double de_F;      /* DE/rand/1/bin scale factor, (0, 2]                  */
     double de_CR;     /* DE/rand/1/bin crossover rate, [0, 1]                */
+    double cso_phi;   /* CSO: weight of the swarm-centre term, [0, 1]        */
 } rvea_config;
 
 /* Reproduction operators (Sec. 4.4, the extensibility experiment: the same
@@ -114,11 +115,21 @@ typedef struct {
  * valid list and an ordered triple of other distinct members, v = x_r1 +
  * F (x_r2 - x_r3), binomial crossover with rate CR and one forced variable,
  * clipped to the box; random reproduction draws every variable uniformly on
- * the box.  DTLZ problems only. */
+ * the box.  RVEA_REPRO_CSO is the competitive swarm optimizer (Cheng and
+ * Jin, IEEE T-Cyb 2015), which the paper names among the operators it plugs
+ * into the same selection without printing it; read here as: offspring o is
+ * one competition between two distinct valid members (uniform, drawn one
+ * after the other), the one kept with the smaller APD (Eq. 4) wins (ties:
+ * the smaller slot), and the loser learns, v' = r1 v_l + r2 (x_w - x_l) +
+ * phi r3 (xbar - x_l), x' = clip(x_l + v'), with r1..r3 uniform per
+ * variable and xbar the mean position of the valid members.  Velocities
+ * (zero at first) and kept APDs (+inf before the first selection) stay
+ * with the survivors.  DTLZ problems only. */
 typedef enum {
     RVEA_REPRO_SBX_PM = 0,
     RVEA_REPRO_DE = 1,
-    RVEA_REPRO_RANDOM = 2
+    RVEA_REPRO_RANDOM = 2,
+    RVEA_REPRO_CSO = 3
 } rvea_reproduction;
 
 /* Lattice divisions H for a requested population size n that need not be a
@@ -327,6 +338,23 @@ rvea_status rvea_export_state(const rvea_run *run, float *X, float *F, uint8_t *
 rvea_status rvea_import_state(rvea_run *run, const float *X, const float *F,
                               const uint8_t *valid, const double *V,
                               const double *gamma, int t, void *cuda_stream);
+
+/* Swarm state of a run reproduced by CSO (RVEA_REPRO_CSO), in vector-slot
+ * order like rvea_export_state: vel (N x d f32, the velocity of each slot's
+ * member; NaN rows for invalid slots) and apd (N f32, the APD of Eq. 4 with
+ * which the last selection kept the member; +inf before any selection and
+ * for invalid slots).  Either may be NULL.  Device or pinned host memory
+ * only (RVEA_ERR_ARG otherwise); RVEA_ERR_STATE for a run of another
+ * operator.  Asynchronous on `cuda_stream`. */
+rvea_status rvea_export_swarm(const rvea_run *run, float *vel, float *apd, void *cuda_stream);
+
+/* Replace the swarm state of a CSO run (same layouts as rvea_export_swarm,
+ * both required; a pointer to device or host memory).  Call it after
+ * rvea_import_state, which resets velocities to zero and kept APDs to +inf
+ * (the state of a new swarm).  Synchronises `cuda_stream`.  RVEA_ERR_STATE
+ * for a run of another operator. */
+rvea_status rvea_import_swarm(rvea_run *run, const float *vel, const float *apd,
+                              void *cuda_stream);
 
 /* Offspring of the last completed generation, in child order c = 0..N-1
  * (c < ceil(N/2): first child of pair c; otherwise second child of pair

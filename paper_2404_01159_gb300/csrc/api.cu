@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -58,6 +59,11 @@ __global__ void k_repro_op_dtlz1(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_op_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_op_dtlz3(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_op_dtlz4(const __grid_constant__ BatchDir dir);
+__global__ void k_cso_mean(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_cso_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_cso_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_cso_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_cso_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
 __global__ void k_gamma(const __grid_constant__ BatchDir dir, int force);
@@ -66,6 +72,7 @@ __global__ void k_init_lists(const __grid_constant__ BatchDir dir);
 __global__ void k_gather_pop(const RunDesc *Rp, float *dst, uint8_t *valid);
 __global__ void k_gather_obj(const RunDesc *Rp, float *dst, uint8_t *valid);
 __global__ void k_gather_children(const RunDesc *Rp, float *X, float *F);
+__global__ void k_gather_swarm(const RunDesc *Rp, float *vel, float *apd);
 __global__ void k_copy_selection(const RunDesc *Rp, int *assoc, int *surv);
 __global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin, int t);
 __global__ void k_igd_partial(const RunDesc *Rp, const float *ref, int n_ref, double *partial);
@@ -185,10 +192,12 @@ Shape make_shape(int m, int d, int N) {
 struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
       ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, otag, occ_cnt, vcnt, zacc, Vt,
-      tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, selb, gscale, vrange, fcomb, noise, dynA, dynB, total;
+      tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, selb, gscale, vrange, fcomb, noise, dynA, dynB,
+      vel, kapd, xbar, xpart, xcnt, total;
 };
 
-Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
+// swarm: the run uses the CSO operator (velocities, kept APDs, the centre)
+Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max, bool swarm = false) {
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -245,6 +254,13 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max) {
   L.noise = take((size_t)steps_max * ns_max * 4);
   L.dynA = take((size_t)ns_max * ns_max * 4);
   L.dynB = take((size_t)ns_max * na_max * 4);
+  const size_t ncb = (size_t)(s.d_pad + kMeanCols - 1) / kMeanCols;
+  const size_t nch = (size_t)(s.N + kMeanRows - 1) / kMeanRows;
+  L.vel = take(swarm ? (size_t)2 * s.N * s.d_pad * sizeof(float) : 0);
+  L.kapd = take(swarm ? (size_t)s.N * 4 : 0);
+  L.xbar = take(swarm ? (size_t)s.d_pad * 4 : 0);
+  L.xpart = take(swarm ? nch * s.d_pad * 4 : 0);
+  L.xcnt = take(swarm ? ncb * 4 : 0);
   L.total = o;
   return L;
 }
@@ -590,11 +606,20 @@ void launch_rollouts(rvea_run *const *runs, int n, cudaStream_t st, int init, bo
   }
 }
 
-// Reproduction by DE/rand/1/bin or random reproduction (the runs whose
-// operator is not SBX): one kernel per problem over a directory of such
-// runs, one warp per offspring.
+// Reproduction by DE/rand/1/bin, random reproduction or CSO (the runs whose
+// operator is not SBX): one kernel per (problem, CSO or not) over a
+// directory of such runs, one warp per offspring.
 constexpr int kOpWarps = kReproThreads / 32;
-void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st) {
+void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st, bool cso) {
+  if (cso) {
+    switch (problem) {
+      case PROB_DTLZ1: launch_pdl(k_repro_cso_dtlz1, grid, kReproThreads, 0, st, d); break;
+      case PROB_DTLZ3: launch_pdl(k_repro_cso_dtlz3, grid, kReproThreads, 0, st, d); break;
+      case PROB_DTLZ4: launch_pdl(k_repro_cso_dtlz4, grid, kReproThreads, 0, st, d); break;
+      default: launch_pdl(k_repro_cso_dtlz2, grid, kReproThreads, 0, st, d); break;
+    }
+    return;
+  }
   switch (problem) {
     case PROB_DTLZ1: launch_pdl(k_repro_op_dtlz1, grid, kReproThreads, 0, st, d); break;
     case PROB_DTLZ3: launch_pdl(k_repro_op_dtlz3, grid, kReproThreads, 0, st, d); break;
@@ -602,11 +627,37 @@ void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st) 
     default: launch_pdl(k_repro_op_dtlz2, grid, kReproThreads, 0, st, d); break;
   }
 }
+// The CSO runs' swarm centres (k_cso_mean), before their reproduction; runs
+// with phi = 0 do not use the centre.
+int cso_mean_blocks(const rvea_run *r) {
+  return (r->sh.d_pad + kMeanCols - 1) / kMeanCols * ((r->sh.N + kMeanRows - 1) / kMeanRows);
+}
+bool cso_needs_mean(const rvea_run *r) { return r->hd.op == 3 && r->hd.cso_phi != 0.0f; }
+void launch_cso_means(rvea_run *const *runs, int n, cudaStream_t st) {
+  static thread_local BatchDir d;
+  int nd = 0, p = 0;
+  for (int q = 0; q < n; ++q) {
+    const rvea_run *r = runs[q];
+    if (!cso_needs_mean(r)) continue;
+    d.prefix[nd] = p;
+    d.desc[nd] = r->d_desc;
+    d.key[nd] = make_uint2(r->hd.key0, r->hd.key1);
+    d.items[nd] = nullptr;
+    p += cso_mean_blocks(r);
+    ++nd;
+  }
+  if (nd == 0) return;
+  d.n = nd;
+  d.prefix[nd] = p;
+  launch_pdl(k_cso_mean, p, 256, 0, st, d);
+}
 void launch_repro_op1(const rvea_run *r, cudaStream_t st) {
   static thread_local BatchDir d;
+  rvea_run *one[1] = {const_cast<rvea_run *>(r)};
+  launch_cso_means(one, 1, st);
   const int nb = (r->sh.N + kOpWarps - 1) / kOpWarps;
   dir_single(d, r, nullptr, nb);
-  launch_repro_op(d, r->hd.problem, nb, st);
+  launch_repro_op(d, r->hd.problem, nb, st, r->hd.op == 3);
 }
 
 // Mutation and evaluation of the children of a run reproduced by 32-lane
@@ -731,25 +782,27 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     // one launch per (problem, load path) group, each with its own directory
     int pg[2 * kProblems] = {};
     for (int g = 0; g < 2 * kProblems; ++g) dg[g].n = 0;
-    // the runs with another operator: one launch per problem
-    static thread_local BatchDir dop[kProblems];
-    int pop[kProblems] = {};
-    for (int g = 0; g < kProblems; ++g) dop[g].n = 0;
+    // the runs with another operator: one launch per (problem, CSO or not)
+    static thread_local BatchDir dop[2 * kProblems];
+    int pop[2 * kProblems] = {};
+    for (int g = 0; g < 2 * kProblems; ++g) dop[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
       if (r->hd.op == 0) continue;
-      BatchDir &D = dop[r->hd.problem];
-      D.prefix[D.n] = pop[r->hd.problem];
+      const int g = 2 * r->hd.problem + (r->hd.op == 3 ? 1 : 0);
+      BatchDir &D = dop[g];
+      D.prefix[D.n] = pop[g];
       D.desc[D.n] = r->d_desc;
       D.key[D.n] = make_uint2(r->hd.key0, r->hd.key1);
       D.items[D.n] = nullptr;
-      pop[r->hd.problem] += (r->sh.N + kOpWarps - 1) / kOpWarps;
+      pop[g] += (r->sh.N + kOpWarps - 1) / kOpWarps;
       ++D.n;
     }
-    for (int g = 0; g < kProblems; ++g) {
+    launch_cso_means(runs, n, st);
+    for (int g = 0; g < 2 * kProblems; ++g) {
       if (dop[g].n == 0) continue;
       dop[g].prefix[dop[g].n] = pop[g];
-      launch_repro_op(dop[g], g, pop[g], st);
+      launch_repro_op(dop[g], g / 2, pop[g], st, (g & 1) != 0);
     }
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
@@ -934,11 +987,12 @@ rvea_status validate(const rvea_config *c) {
   if (c->problem != PROB_NEURO && (c->lower != 0.0 || c->upper != 1.0)) return RVEA_ERR_ARG;
   if (c->problem < 0 || c->problem >= kProblems) return RVEA_ERR_ARG;
   // the other reproduction operators (DTLZ problems)
-  if (c->reproduction < 0 || c->reproduction > 2) return RVEA_ERR_ARG;
+  if (c->reproduction < 0 || c->reproduction > 3) return RVEA_ERR_ARG;
   if (c->reproduction != 0 && c->problem == PROB_NEURO) return RVEA_ERR_ARG;
   if (c->reproduction == 1 &&
       (!(c->de_F > 0) || c->de_F > 2 || !(c->de_CR >= 0) || c->de_CR > 1))
     return RVEA_ERR_ARG;
+  if (c->reproduction == 3 && (!(c->cso_phi >= 0) || c->cso_phi > 1)) return RVEA_ERR_ARG;
   if (c->problem == RVEA_NEURO_LINEAR) {
     // the rollout's shape: h1 = h2 = 64 (the tensor-core tiling), ns <= 32
     // (one lane per state component), na <= 16 (one 16-row tile), and d the
@@ -968,7 +1022,8 @@ size_t rvea_workspace_bytes_ex(const rvea_config *cfg) {
   if (!cfg || validate(cfg) != RVEA_OK) return 0;
   const Shape s = make_shape(cfg->m, cfg->d, cfg->N);
   const rvea_neuro_dynamics *nd = cfg->problem == RVEA_NEURO_LINEAR ? cfg->neuro : nullptr;
-  return make_layout(s, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0).total;
+  return make_layout(s, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0,
+                     cfg->reproduction == 3).total;
 }
 
 int rvea_lattice_for(int m, int n) {
@@ -1013,7 +1068,8 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255)) return RVEA_ERR_ARG;
   const Shape sh = make_shape(cfg->m, cfg->d, cfg->N);
   const rvea_neuro_dynamics *nd = cfg->problem == RVEA_NEURO_LINEAR ? cfg->neuro : nullptr;
-  const Layout lay = make_layout(sh, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0);
+  const Layout lay = make_layout(sh, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0,
+                                 cfg->reproduction == 3);
   if (bytes < lay.total) return RVEA_ERR_NOMEM;
   std::call_once(g_attr_once, set_kernel_attrs);
   if (g_attr_err != cudaSuccess) return RVEA_ERR_CUDA;
@@ -1047,6 +1103,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.op = cfg->reproduction;
   D.de_F = (float)cfg->de_F;
   D.T_cr = event_threshold24(cfg->de_CR);
+  D.cso_phi = (float)cfg->cso_phi;
   if (D.T_m > 0u && D.T_m < (1u << 24))
     D.n_mthr = site_count_thresholds((double)D.T_m / 16777216.0, sh.d, D.mthr);
   D.key0 = (uint32_t)cfg->seed;
@@ -1097,6 +1154,13 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gscale = wsp<float>(r, lay.gscale);
   D.vrange = wsp<double>(r, lay.vrange);
   D.fcomb = wsp<float>(r, lay.fcomb);
+  if (cfg->reproduction == 3) {   // the swarm state (velocities zero from the clear below)
+    D.vel = wsp<float>(r, lay.vel);
+    D.kapd = wsp<float>(r, lay.kapd);
+    D.xbar = wsp<float>(r, lay.xbar);
+    D.xpart = wsp<float>(r, lay.xpart);
+    D.xcnt = wsp<unsigned>(r, lay.xcnt);
+  }
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
   r->repro_smem = sh.team == 32 ? kStagedSmem : 0;   // staged path (the default for 32-lane teams)
@@ -1171,6 +1235,11 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   up(lay.ctl, &c0, sizeof(c0));
   const std::vector<double> ones(kMaxM, 1.0);
   up(lay.vrange, ones.data(), kMaxM * 8);
+  std::vector<float> kinf;
+  if (cfg->reproduction == 3) {   // no selection has kept a member yet
+    kinf.assign(sh.N, std::numeric_limits<float>::infinity());
+    up(lay.kapd, kinf.data(), kinf.size() * 4);
+  }
   if (nd) {
     up(lay.dynA, dynA.data(), dynA.size() * 4);
     up(lay.dynB, dynB.data(), dynB.size() * 4);
@@ -1584,9 +1653,10 @@ int rvea_launches_per_generation(const rvea_run *r, int adapting) {
   if (!r) return -1;
   // gamma, then the tile table and the direction grid (4 launches)
   const int adapt_n = adapting ? 1 + (r->hd.ntiles > 0 ? 1 : 0) + (r->hd.gG > 0 ? 4 : 0) : 0;
-  if (r->sel_mode == 3) return 2 + adapt_n;   // reproduction, fused tail
+  if (r->sel_mode == 3) return 2 + (cso_needs_mean(r) ? 1 : 0) + adapt_n;   // reproduction, fused tail
   int n = 3;                                        // reproduction, selection, finalize
   if (r->sh.team == 32 && r->hd.op == 0) n += 1;    // k_mutate
+  if (cso_needs_mean(r)) n += 1;                    // the CSO swarm centre
   if (r->hd.problem == PROB_NEURO) n += 2;          // noise, rollout
   n += adapt_n;
   return n;
@@ -1810,6 +1880,8 @@ rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const
   RV_TRY(cudaMemcpyAsync(sv, valid, sh.N, cudaMemcpyDefault, st));
   RV_TRY(cudaMemcpyAsync(r->hd.V64, V, (size_t)sh.N * sh.m * 8, cudaMemcpyDefault, st));
   RV_TRY(cudaMemcpyAsync(r->hd.gamma64, gamma, (size_t)sh.N * 8, cudaMemcpyDefault, st));
+  // CSO: a new swarm (velocities zero; k_import sets the kept APDs to +inf)
+  if (r->hd.vel) RV_TRY(cudaMemsetAsync(r->hd.vel, 0, (size_t)sh.N * sh.d_pad * 4, st));
   k_import<<<1, kFinThreads, 0, st>>>(r->d_desc, sf, sv, t);
   RV_TRY(cudaGetLastError());
   if (launch_tiles(r, st) != RVEA_OK) return RVEA_ERR_CUDA;
@@ -1817,6 +1889,32 @@ rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const
   r->t = t;
   r->last_stream = st;
   r->has_last_gen = false;
+  return RVEA_OK;
+}
+
+rvea_status rvea_export_swarm(const rvea_run *r, float *vel, float *apd, void *cuda_stream) {
+  if (!r) return RVEA_ERR_ARG;
+  if (!r->hd.vel) return RVEA_ERR_STATE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  float *dv = static_cast<float *>(dev_addr(vel));
+  float *da = static_cast<float *>(dev_addr(apd));
+  if ((vel && !dv) || (apd && !da)) return RVEA_ERR_ARG;   // device or pinned memory only
+  if (!vel && !apd) return RVEA_OK;
+  k_gather_swarm<<<r->sh.N, 256, 0, st>>>(r->d_desc, dv, da);
+  return cuerr(cudaGetLastError());
+}
+
+rvea_status rvea_import_swarm(rvea_run *r, const float *vel, const float *apd, void *cuda_stream) {
+  if (!r || !vel || !apd) return RVEA_ERR_ARG;
+  if (!r->hd.vel) return RVEA_ERR_STATE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const Shape &sh = r->sh;
+  // slot j's member sits in pool row j after rvea_import_state
+  RV_TRY(cudaMemcpy2DAsync(r->hd.vel, (size_t)sh.d_pad * 4, vel, (size_t)sh.d * 4, (size_t)sh.d * 4,
+                           sh.N, cudaMemcpyDefault, st));
+  RV_TRY(cudaMemcpyAsync(r->hd.kapd, apd, (size_t)sh.N * 4, cudaMemcpyDefault, st));
+  RV_TRY(cudaStreamSynchronize(st));
+  r->last_stream = st;
   return RVEA_OK;
 }
 

@@ -76,6 +76,8 @@ __device__ inline void fin_decode(const RunDesc &R, int blk, FinShared &sh) {
     nmap[j] = s;
     R.surv[j] = i;
     if (s >= 0) atomicOr(&R.obits[s >> 5], 1u << (s & 31));
+    // CSO: the APD that kept slot j's member (Eq. 4), for the next competitions
+    if (R.kapd) R.kapd[j] = s >= 0 ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000);
   }
   const uint32_t vmask = __ballot_sync(0xffffffffu, s >= 0);
   if (lane == 0 && j < N) R.vbits[j >> 5] = vmask;

@@ -588,6 +588,20 @@ __global__ void k_gather_children(const RunDesc *__restrict__ Rp, float *X, floa
   if (F && threadIdx.x < R.m) F[(size_t)c * R.m + threadIdx.x] = R.F[(size_t)threadIdx.x * R.n_comb + s];
 }
 
+// Swarm state of a CSO run in vector-slot order: each valid slot's velocity
+// row and kept APD (NaN rows and +inf for invalid slots).  One CTA per slot.
+__global__ void k_gather_swarm(const RunDesc *__restrict__ Rp, float *vel, float *apd) {
+  const RunDesc &R = *Rp;
+  const int j = blockIdx.x;
+  const int s = R.slotmap[(R.ctl->t & 1) * R.N + j];
+  if (vel) {
+    const float *v = s >= 0 ? R.vel + (size_t)s * R.d_pad : nullptr;
+    for (int k = threadIdx.x; k < R.d; k += blockDim.x)
+      vel[(size_t)j * R.d + k] = v ? v[k] : __int_as_float(0x7fc00000);
+  }
+  if (apd && threadIdx.x == 0) apd[j] = s >= 0 ? R.kapd[j] : __int_as_float(0x7f800000);
+}
+
 __global__ void k_copy_selection(const RunDesc *__restrict__ Rp, int *assoc, int *surv) {
   const RunDesc &R = *Rp;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -623,6 +637,7 @@ k_import(const RunDesc *__restrict__ Rp, const float *Fin, const uint8_t *vin, i
     R.gamma32[j] = (float)R.gamma64[j];
     R.best[j] = ~0ull;
     R.surv[j] = -1;
+    if (R.kapd) R.kapd[j] = __int_as_float(0x7f800000);   // CSO: no selection kept it yet
   }
   for (int i = tid; i < n2; i += kFinThreads) { R.amax[i] = 0ull; R.assoc[i] = -1; R.otag[i] = 0; }
   for (int w = tid; w < (n2 + 31) / 32; w += kFinThreads) R.obits[w] = 0u;

@@ -606,7 +606,7 @@ RVEA_MUTATE(k_mutate_neuro, PROB_NEURO)
 //       j = j_rand, else the target's x_j; clipped to [L, U];
 //   random: x_j = L + (U - L) u24, RANDOM (j/4, o, t) word j%4.
 // Then the g-terms, objectives and the ideal point, as the other kernels.
-enum : uint32_t { TAG_DE_PICK = 8, TAG_DE_CR = 9, TAG_RANDOM = 10 };
+enum : uint32_t { TAG_DE_PICK = 8, TAG_DE_CR = 9, TAG_RANDOM = 10, TAG_CSO_PICK = 11, TAG_CSO_R = 12 };
 
 __device__ __forceinline__ int de_pos(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
 
@@ -722,6 +722,70 @@ __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
   if (threadIdx.x < m && s_z[threadIdx.x] != 0xFFFFFFFFu)
     atomicMin(&R.ctl->zkey[threadIdx.x], s_z[threadIdx.x]);
 }
+// The swarm centre of the CSO operator, xbar = the mean position of the K
+// valid members (the oracle's order: a sum over the valid list, then / K).
+// CTA (chunk, column block) adds the rows [kMeanRows chunk, +kMeanRows) of
+// the valid list over its kMeanCols variables in float, in list order, into
+// xpart; the last CTA of a column block to arrive adds the chunks' partials
+// in chunk order in FP64 and divides by K, so the result does not depend on
+// the order in which the CTAs ran.  Grid per run: column blocks x
+// ceil(N / kMeanRows) chunks (chunks past K add nothing).
+__global__ void __launch_bounds__(256) k_cso_mean(const __grid_constant__ BatchDir dir) {
+  __shared__ int s_rows[kMeanRows];
+  __shared__ int s_last;
+  pdl_wait();      // the previous generation's lists and slot maps
+  pdl_trigger();
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int N = R.N, t = R.ctl->t, K = R.ctl->K;
+  const int rq = R.d_pad >> 2;
+  const int ncb = (R.d_pad + kMeanCols - 1) / kMeanCols;
+  const int nch = (N + kMeanRows - 1) / kMeanRows;
+  const int b = blockIdx.x - dir.prefix[run];
+  const int cb = b % ncb, ch = b / ncb;
+  const int r0 = ch * kMeanRows, nr = max(0, min(kMeanRows, K - r0));
+  if (threadIdx.x < kMeanRows) {
+    int s = 0;
+    if ((int)threadIdx.x < nr) {
+      const int j = R.vlist[r0 + threadIdx.x];
+      s = (j >= 0 && j < N) ? R.slotmap[(t & 1) * N + j] : -1;
+      if (s < 0 || s >= 2 * N) { set_status(R.ctl, ST_BADINDEX); s = 0; }
+    }
+    s_rows[threadIdx.x] = s;
+  }
+  __syncthreads();
+  const int Q = cb * (kMeanCols / 4) + (int)threadIdx.x;
+  const float4 *X4 = reinterpret_cast<const float4 *>(R.X);
+  float4 *P4 = reinterpret_cast<float4 *>(R.xpart);
+  if (Q < rq) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+    for (int r = 0; r < nr; ++r) {
+      const float4 x = __ldcs(X4 + (size_t)s_rows[r] * rq + Q);
+      acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
+    }
+    P4[(size_t)ch * rq + Q] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&R.xcnt[cb], 1u) == (unsigned)(nch - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (Q < rq) {
+    double sx = 0.0, sy = 0.0, sz = 0.0, sw = 0.0;
+    const int nk = (K + kMeanRows - 1) / kMeanRows;
+    for (int c = 0; c < nk; ++c) {
+      const float4 p = __ldcg(P4 + (size_t)c * rq + Q);
+      sx += p.x; sy += p.y; sz += p.z; sw += p.w;
+    }
+    const double k = (double)max(K, 1);
+    reinterpret_cast<float4 *>(R.xbar)[Q] =
+        make_float4((float)(sx / k), (float)(sy / k), (float)(sz / k), (float)(sw / k));
+  }
+  if (threadIdx.x == 0) R.xcnt[cb] = 0u;   // ready for the next generation
+}
+
 #define RVEA_REPRO_OP(name, PROB)                                                          \
   __global__ void __launch_bounds__(kReproThreads) name(const __grid_constant__ BatchDir dir) { \
     repro_op_body<PROB>(dir);                                                              \
@@ -731,6 +795,140 @@ RVEA_REPRO_OP(k_repro_op_dtlz2, PROB_DTLZ2)
 RVEA_REPRO_OP(k_repro_op_dtlz3, PROB_DTLZ3)
 RVEA_REPRO_OP(k_repro_op_dtlz4, PROB_DTLZ4)
 #undef RVEA_REPRO_OP
+
+// Reproduction by the competitive swarm optimizer (CSO; Cheng and Jin 2015),
+// the operator the paper's neuroevolution experiment picks (Sec. 4.4).  One
+// warp per offspring o: a competition between two distinct valid members,
+// positions a then b of the valid list (CSO_PICK (o, 0, t) words 0 and 1, b
+// drawn over the positions other than a); the smaller kept APD wins (ties:
+// the smaller slot), and the loser learns
+//   v' = r1 v_l + r2 (x_w - x_l) + phi r3 (xbar - x_l),   x' = x_l + v',
+// r1, r2, r3 of variable j from word j%4 of CSO_R (3 (j/4) + k, o, t),
+// k = 0, 1, 2 (r3 only when phi > 0), xbar the swarm centre (k_cso_mean);
+// x' is clipped to [L, U] and (x', v') goes to the child's pool row and its
+// velocity row.  Each lane streams float4s of the winner's and loser's rows
+// and the loser's velocity, the next float4s loaded while the current ones
+// are processed.  Then the g-terms, objectives and the ideal point.
+template <int PROB>
+__device__ __forceinline__ void repro_cso_body(const BatchDir &dir) {
+  __shared__ unsigned s_z[kMaxM];
+  pdl_wait();      // the previous generation's lists, slot maps and kept APDs; the centre
+  pdl_trigger();
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o = (blockIdx.x - dir.prefix[run]) * (kReproThreads / 32) + warp;
+  const int N = R.N, d = R.d, m = R.m, t = R.ctl->t, K = R.ctl->K;
+  const KeyRun kr{dir.key[run].x, dir.key[run].y};
+  if (threadIdx.x < kMaxM) s_z[threadIdx.x] = 0xFFFFFFFFu;
+  __syncthreads();
+  float f[kMaxM];
+  bool have = false;
+  if (o < N) {
+    int slot = R.child_slot[(t & 1) * N + o];
+    if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); slot = -1; }
+    int rw = 0, rl = 0;   // pool rows of the winner and the loser
+    if (lane == 0 && K > 0) {
+      const uint4 w = philox_k((uint32_t)o, 0u, (uint32_t)t, TAG_CSO_PICK, kr);
+      const int a = de_pos(w.x, K);
+      int bq = a;
+      if (K > 1) {
+        bq = de_pos(w.y, K - 1);
+        if (bq >= a) bq += 1;
+      }
+      int ia = R.vlist[a], ib = R.vlist[bq];
+      if (ia < 0 || ia >= N || ib < 0 || ib >= N) { set_status(R.ctl, ST_BADINDEX); ia = ib = 0; }
+      const float pa = R.kapd[ia], pb = R.kapd[ib];
+      const bool a_wins = pa < pb || (pa == pb && ia <= ib);
+      rw = R.slotmap[(t & 1) * N + (a_wins ? ia : ib)];
+      rl = R.slotmap[(t & 1) * N + (a_wins ? ib : ia)];
+      if (rw < 0 || rw >= 2 * N || rl < 0 || rl >= 2 * N) { set_status(R.ctl, ST_BADINDEX); rw = rl = 0; }
+    }
+    rw = __shfl_sync(0xffffffffu, rw, 0);
+    rl = __shfl_sync(0xffffffffu, rl, 0);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    float2 acc = make_float2(0.f, 0.f);
+    if (slot >= 0) {
+      const float L = R.L, U = R.U, phi = R.cso_phi;
+      const int mh = m - 1, rq = R.d_pad >> 2;
+      const float4 *X4 = reinterpret_cast<const float4 *>(R.X);
+      const float4 *V4 = reinterpret_cast<const float4 *>(R.vel);
+      const float4 *XW = X4 + (size_t)rw * rq, *XL = X4 + (size_t)rl * rq, *VL = V4 + (size_t)rl * rq;
+      const float4 *XB = reinterpret_cast<const float4 *>(R.xbar);
+      float4 *Y4 = reinterpret_cast<float4 *>(R.X + (size_t)slot * R.d_pad);
+      float4 *VY = reinterpret_cast<float4 *>(R.vel + (size_t)slot * R.d_pad);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 cw = z4, cl = z4, cv = z4, cb = z4;
+      if (lane < rq) {
+        cw = __ldg(XW + lane);
+        cl = __ldg(XL + lane);
+        cv = __ldg(VL + lane);
+        if (phi != 0.0f) cb = __ldg(XB + lane);
+      }
+      for (int Q = lane; Q < rq; Q += 32) {
+        float4 nw = z4, nl = z4, nv = z4, nb = z4;
+        if (Q + 32 < rq) {
+          nw = __ldg(XW + Q + 32);
+          nl = __ldg(XL + Q + 32);
+          nv = __ldg(VL + Q + 32);
+          if (phi != 0.0f) nb = __ldg(XB + Q + 32);
+        }
+        const uint4 w1 = philox_k(3u * (uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
+        const uint4 w2 = philox_k(3u * (uint32_t)Q + 1u, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
+        const uint4 w3 = phi != 0.0f ? philox_k(3u * (uint32_t)Q + 2u, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr)
+                                     : make_uint4(0u, 0u, 0u, 0u);
+        const float aw[4] = {cw.x, cw.y, cw.z, cw.w}, al[4] = {cl.x, cl.y, cl.z, cl.w};
+        const float av[4] = {cv.x, cv.y, cv.z, cv.w}, ab[4] = {cb.x, cb.y, cb.z, cb.w};
+        float u[4], nvel[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int j = 4 * Q + v;
+          float vv = u24f(word(w1, v)) * av[v];
+          vv = fmaf(u24f(word(w2, v)), aw[v] - al[v], vv);
+          if (phi != 0.0f) vv = fmaf(phi * u24f(word(w3, v)), ab[v] - al[v], vv);
+          if (j >= d) {   // row padding: a g-term of exactly zero, no velocity
+            u[v] = 0.5f;
+            nvel[v] = 0.0f;
+          } else {
+            u[v] = clampf(al[v] + vv, L, U);
+            nvel[v] = vv;
+            if (j >= mh) {
+              if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
+              else acc.x = g_term1(PROB, u[v], acc.x);
+            }
+          }
+        }
+        Y4[Q] = make_float4(u[0], u[1], u[2], u[3]);
+        __stcs(VY + Q, make_float4(nvel[0], nvel[1], nvel[2], nvel[3]));
+        cw = nw; cl = nl; cv = nv; cb = nb;
+      }
+      const float2 gs = team_sum2(acc, 32);
+      __syncwarp();   // the row is visible to lane 0
+      if (lane == 0) {
+        float head[kMaxM];
+        const float *row = R.X + (size_t)slot * R.d_pad;
+        for (int jj = 0; jj < mh; ++jj) head[jj] = __ldcg(row + jj);
+        dtlz_objectives_t<PROB>(m, gs.x + gs.y, head, f);
+        for (int kk = 0; kk < m; ++kk) R.F[(size_t)kk * 2 * N + slot] = f[kk];
+        have = true;
+      }
+    }
+  }
+  if (have)
+    for (int kk = 0; kk < m; ++kk) atomicMin(&s_z[kk], f2ord(f[kk]));
+  __syncthreads();
+  if (threadIdx.x < m && s_z[threadIdx.x] != 0xFFFFFFFFu)
+    atomicMin(&R.ctl->zkey[threadIdx.x], s_z[threadIdx.x]);
+}
+#define RVEA_REPRO_CSO(name, PROB)                                                         \
+  __global__ void __launch_bounds__(kReproThreads, 3) name(const __grid_constant__ BatchDir dir) { \
+    repro_cso_body<PROB>(dir);                                                             \
+  }
+RVEA_REPRO_CSO(k_repro_cso_dtlz1, PROB_DTLZ1)
+RVEA_REPRO_CSO(k_repro_cso_dtlz2, PROB_DTLZ2)
+RVEA_REPRO_CSO(k_repro_cso_dtlz3, PROB_DTLZ3)
+RVEA_REPRO_CSO(k_repro_cso_dtlz4, PROB_DTLZ4)
+#undef RVEA_REPRO_CSO
 
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
 // objectives.  DTLZ: x = L + (U-L) u24 from INIT (j/4, i, 0) word j%4.

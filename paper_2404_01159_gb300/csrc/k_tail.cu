@@ -449,6 +449,8 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
         }
         nmap[j] = s;
         R.surv[j] = i;
+        // CSO: the APD that kept slot j's member (Eq. 4), for the next competitions
+        if (R.kapd) R.kapd[j] = s >= 0 ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000);
         if (s >= 0) {
           R.otag[s] = t;
           atomicAdd(&R.occ_cnt[min(nb - 1, (s >> 5) / po)], 1u);

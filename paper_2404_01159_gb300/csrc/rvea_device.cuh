@@ -29,6 +29,8 @@ constexpr int kStageWarpBytes = kStages * 2 * 1024;   // per warp: kStages x 2 p
 constexpr int kStagedSmem = (kReproThreads / 32) * (kStageWarpBytes + kStages * 8);
 constexpr int kTailThreads = 1024;  // CTA size of the fused tail kernel (one CTA per SM)
 constexpr int kTailMaxCtas = 256;   // its largest grid
+constexpr int kMeanRows = 64;       // CSO swarm centre: population rows per partial sum
+constexpr int kMeanCols = 1024;     // CSO swarm centre: variables per column block (256 x float4)
 
 // Philox counter tags (word 3 of the counter).
 enum : uint32_t {
@@ -78,9 +80,11 @@ struct RunDesc {
   int repro_staged;    // 1: parents staged in shared memory by TMA (32-lane teams)
   int sg;              // groups per segment, ceil(G / nseg) <= kLaneGroups * team
   int op_mode;         // 1: stateless selection (identity slots, AoS F)
-  int op;              // reproduction: 0 SBX + polynomial mutation, 1 DE/rand/1/bin, 2 random
+  int op;              // reproduction: 0 SBX + polynomial mutation, 1 DE/rand/1/bin, 2 random,
+                       //               3 competitive swarm (CSO)
   float de_F;          // DE scale factor
   uint32_t T_cr;       // DE crossover coin: fires iff (w >> 8) < T_cr
+  float cso_phi;       // CSO: weight of the swarm-centre term
   // parameters
   float L, U, alpha, inv_eta_c1, eta_m;
   uint32_t T_c, T_m;   // 24-bit event thresholds (fires iff k < T)
@@ -101,6 +105,12 @@ struct RunDesc {
   int *assoc;          // [n_comb]   vector of each solution, -1 if invalid
   int *surv;           // [N]        combined index kept by vector j, -1 if none
   float *psum;         // [P][2][nseg] partial g sums of the segments of each pair
+  // swarm state of the CSO operator (null for the other operators)
+  float *vel;          // [2N][d_pad] velocity of each pool row (moves with its row)
+  float *kapd;         // [N]        APD that kept vector slot j's member (+inf: none yet)
+  float *xbar;         // [d_pad]    mean position of the valid members (the swarm centre)
+  float *xpart;        // [ceil(N/kMeanRows)][d_pad] float partial sums of the centre
+  unsigned *xcnt;      // [column blocks] arrival counters of the centre's partials
   // draw recording (inspection; null when off): the vector slot of each
   // parent draw e, and each child's mutation-site count (-1: every site)
   // followed by its sites in draw order

@@ -55,7 +55,7 @@ class Run:
                  p_m: float = 1.0, lower: Optional[float] = None,
                  upper: Optional[float] = None, seed: int = 0, neuro=None,
                  reproduction: int = 0, de_F: float = 0.5, de_CR: float = 0.9,
-                 device=None, stream=None):
+                 cso_phi: float = 0.0, device=None, stream=None):
         self.device = torch.device("cuda" if device is None else device)
         if lower is None:
             lower = -1.0 if problem == NEURO_LINEAR else 0.0
@@ -65,7 +65,8 @@ class Run:
         self.problem, self.t_max = problem, t_max
         L = lib()
         cfg = Config(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
-                     lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None, reproduction, de_F, de_CR)
+                     lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None, reproduction, de_F, de_CR,
+                     cso_phi)
         self._neuro_keep = None
         if neuro is not None:
             A = np.ascontiguousarray(neuro["A"], dtype=np.float64)
@@ -194,6 +195,21 @@ class Run:
         check(lib().rvea_import_state(self._h, _ptr(X), _ptr(F), _ptr(valid), _ptr(V),
                                       _ptr(gamma), int(t), C.c_void_p(_stream(stream))),
               "rvea_import_state")
+
+    def export_swarm(self, stream=None):
+        """Velocities (N x d) and kept APDs (N) of a CSO run, by vector slot."""
+        vel = torch.empty((self.N, self.d), dtype=torch.float32, device=self.device)
+        apd = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        check(lib().rvea_export_swarm(self._h, _ptr(vel), _ptr(apd), C.c_void_p(_stream(stream))),
+              "rvea_export_swarm")
+        return vel, apd
+
+    def import_swarm(self, vel, apd, stream=None) -> None:
+        """Replace a CSO run's velocities and kept APDs (after import_state)."""
+        vel = torch.as_tensor(vel, dtype=torch.float32, device=self.device).contiguous()
+        apd = torch.as_tensor(apd, dtype=torch.float32, device=self.device).contiguous()
+        check(lib().rvea_import_swarm(self._h, _ptr(vel), _ptr(apd), C.c_void_p(_stream(stream))),
+              "rvea_import_swarm")
 
     def offspring(self, stream=None):
         X = torch.empty((self.N, self.d), dtype=torch.float32, device=self.device)

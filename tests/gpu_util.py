@@ -34,7 +34,8 @@ def make_run(p):
     from paper_2404_01159_gb300 import Run
     return Run(m=p.m, d=p.d, N=p.N, H=p.H, problem=p.problem, t_max=p.t_max, alpha=p.alpha,
                f_r=p.f_r, eta_c=p.eta_c, eta_m=p.eta_m, p_c=p.p_c, p_m=p.p_m, lower=p.L,
-               upper=p.U, seed=p.seed, reproduction=p.op, de_F=p.de_F, de_CR=p.de_CR)
+               upper=p.U, seed=p.seed, reproduction=p.op, de_F=p.de_F, de_CR=p.de_CR,
+               cso_phi=p.cso_phi)
 
 
 def to_np(st):

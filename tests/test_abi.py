@@ -91,6 +91,31 @@ def test_init_ex_requires_the_unit_box_for_dtlz(native):
     assert not h.value
 
 
+def test_cso_config_and_swarm_calls_without_gpu(native):
+    """The CSO operator (reproduction 3): phi outside [0, 1] is refused; its
+    workspace adds the velocity pool (2N rows of d_pad floats), the kept
+    APDs, the swarm centre and its partial sums; the swarm calls refuse NULL
+    handles and arrays before any device work."""
+    L = native.lib()
+    base = dict(m=3, d=1001, N=210, H=19, problem=1, t_max=100, alpha=2.0, f_r=0.1,
+                eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, lower=0.0, upper=1.0,
+                seed=0, neuro=None, reproduction=native.REPRO_CSO, de_F=0.5, de_CR=0.9)
+    sbx = L.rvea_workspace_bytes(3, 1001, 210)
+    cso = L.rvea_workspace_bytes_ex(C.byref(native.Config(**base, cso_phi=0.1)))
+    d_pad, N = 1008, 210
+    swarm = 2 * N * d_pad * 4 + N * 4 + d_pad * 4 + ((N + 63) // 64) * d_pad * 4
+    assert sbx > 0 and cso >= sbx + swarm and cso < sbx + swarm + 6 * 256
+    for phi in (-0.1, 1.5, float("nan")):
+        assert L.rvea_workspace_bytes_ex(C.byref(native.Config(**base, cso_phi=phi))) == 0
+    cfg = native.Config(**dict(base, reproduction=4), cso_phi=0.1)
+    assert L.rvea_workspace_bytes_ex(C.byref(cfg)) == 0
+    h = C.c_void_p()
+    cfg = native.Config(**dict(base, problem=2), cso_phi=0.1)   # the rollout problem: SBX only
+    assert L.rvea_init_ex(C.byref(cfg), C.c_void_p(1 << 20), 1 << 30, None, C.byref(h)) == native.ERR_ARG
+    assert L.rvea_export_swarm(None, None, None, None) == native.ERR_ARG
+    assert L.rvea_import_swarm(None, C.c_void_p(1 << 20), C.c_void_p(1 << 20), None) == native.ERR_ARG
+
+
 def test_metrics_and_counters_reject_null_without_gpu(native):
     """The metric and counter entry points check their handles before any
     device work: NULL run / batch / output pointers are refused."""

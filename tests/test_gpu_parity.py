@@ -50,10 +50,14 @@ SHAPES = [
 ]
 
 
-def _state_to_oracle(orc, st):
+def _state_to_oracle(orc, st, swarm=None):
     s = to_np(st)
+    vel = apd = None
+    if swarm is not None:   # CSO: the GPU's velocities and kept APDs (float32 values)
+        vel = np.nan_to_num(swarm[0].cpu().numpy().astype(np.float64))
+        apd = swarm[1].cpu().numpy().astype(np.float64)
     return orc.State(s["X"].astype(np.float64), s["F"].astype(np.float64), s["valid"],
-                     s["V"], s["gamma"], s["t"])
+                     s["V"], s["gamma"], s["t"], vel=vel, apd=apd)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -100,6 +104,17 @@ def test_teacher_forced_other_operators(orc, shape, op):
     _teacher_forced(orc, shape, 6, op=op)
 
 
+# The competitive swarm optimizer (op 3, the operator the paper's
+# neuroevolution experiment picks): with and without the swarm-centre term,
+# on the small, staged, fused-tail and m = 10 shapes; velocities and kept
+# APDs are carried through six generations (one adaptation at t = 4).
+@pytest.mark.parametrize("shape,phi", [((3, 12, 105, 13, 0), 0.1), ((3, 1001, 210, 19, 1), 0.0),
+                                       ((3, 2500, 1275, 49, 1), 0.1), ((10, 30, 220, 3, 0), 0.2),
+                                       ((2, 4099, 100, 99, 3), 0.15)])
+def test_teacher_forced_cso(orc, shape, phi):
+    _teacher_forced(orc, shape, 6, op=3, cso_phi=phi)
+
+
 # Population sizes of the paper's speed sweeps that are not lattice sizes
 # (Sec. 4.1: n = 2^k at d = 100, d = 2^k at n = 100): the run takes the
 # largest Das-Dennis lattice with at most n points (n = 128 -> H = 14,
@@ -126,7 +141,8 @@ def _teacher_forced(orc, shape, gens, **kw):
         run.record_draws(True)
     for gen in range(gens):
         st = run.export_state()
-        ost = _state_to_oracle(orc, st)
+        sw = run.export_swarm() if p.op == 3 else None
+        ost = _state_to_oracle(orc, st, sw)
         t = ost.t
         Fpar = ost.F.copy()
         vpar = ost.valid.copy()
@@ -153,6 +169,8 @@ def _teacher_forced(orc, shape, gens, **kw):
         bad_a, bad_s = selection_mismatches(Fc, vc, to_np(st)["V"], ga.cpu().numpy(),
                                             gsurv.cpu().numpy(), o)
         assert not bad_a and not bad_s, (gen, bad_a[:5], bad_s[:5])
+        if p.op == 3:
+            _check_swarm(run, sw, gsurv.cpu().numpy(), out["survivor"], ost, o, N)
         # the adapted reference vectors and gamma follow the GPU's survivors
         nst = to_np(run.export_state())
         assert nst["t"] == t + 1
@@ -164,6 +182,32 @@ def _teacher_forced(orc, shape, gens, **kw):
         else:
             assert np.array_equal(nst["V"], to_np(st)["V"])
     run.sync_status()
+
+
+def _check_swarm(run, sw_prev, gsurv, osurv, ost, o, N):
+    """CSO state after a generation: every kept APD is the APD (Eq. 4) of
+    its survivor in the selection on the GPU's own combined population (where
+    that selection associated the survivor with the same vector: an
+    association tie within the tolerance can put it on a neighbour, whose
+    gamma differs); a parent's velocity moves with it unchanged (bit for
+    bit); a child's velocity matches the oracle's where both kept the same
+    child."""
+    vel, apd = (x.cpu().numpy() for x in run.export_swarm())
+    vprev = sw_prev[0].cpu().numpy()
+    live = gsurv >= 0
+    assert np.isinf(apd[~live]).all()
+    same = live.copy()
+    same[live] = o["assoc"][gsurv[live]] == np.flatnonzero(live)
+    assert same.sum() >= 0.9 * live.sum()
+    ref = o["apd"][gsurv[same]]
+    assert np.allclose(apd[same].astype(np.float64), ref, rtol=1e-5, atol=1e-30), \
+        float((np.abs(apd[same] - ref) / ref).max())
+    par = live & (gsurv < N)
+    assert np.array_equal(vel[par], vprev[gsurv[par]])
+    kid = live & (gsurv >= N) & (osurv == gsurv)
+    assert kid.any()
+    err = np.abs(vel[kid].astype(np.float64) - ost.vel[kid])
+    assert err.max() <= 1e-5, float(err.max())
 
 
 @pytest.mark.parametrize("m,n,r,seed", [(3, 700, 1300, 0), (2, 257, 100, 1), (5, 1000, 126, 2),
