@@ -899,7 +899,13 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
     if (nt > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
-    k_gamma<<<2 * runs[0]->num_sms, 256, 0, st>>>(df, 0);
+    // one pass: every vector block of the largest run has its CTA (the
+    // tile search gives each warp four vectors, a second round would double
+    // the chain), between two and four CTAs per SM
+    int nbg = 0;
+    for (int q = 0; q < n; ++q) nbg = std::max(nbg, (runs[q]->sh.N + 31) / 32);
+    nbg = std::min(std::max(nbg, 2 * runs[0]->num_sms), 4 * runs[0]->num_sms);
+    k_gamma<<<nbg, 256, 0, st>>>(df, 0);
   }
   if (ev) cudaEventRecord(ev[5], st);
   return cuerr(cudaGetLastError());

@@ -197,6 +197,9 @@ __device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl
   return n;
 }
 
+// The count pass runs five CTAs per SM (48 registers): a chain of dependent
+// table reads per cell, so resident warps set its speed (94 -> 83 us at
+// N = 9870; the fill pass, which visits fewer blocks, gained nothing).
 // One CTA per block of cells (kGridSpan2 cells for m = 2, kGridSpan3 x
 // kGridSpan3 for m = 3): warp 0 lists the tiles that can hold a candidate
 // of any cell of the block (the block taken as one region: every vector
@@ -280,7 +283,7 @@ __device__ void grid_block(const RunDesc &R) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_grid_count(const RunDesc *__restrict__ Rp) {
+__global__ void __launch_bounds__(256, 5) k_grid_count(const RunDesc *__restrict__ Rp) {
   const RunDesc &R = *Rp;
   if (R.m == 2) grid_block<2, false>(R); else grid_block<3, false>(R);
 }
