@@ -60,6 +60,7 @@ __global__ void k_repro_op_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_op_dtlz3(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_op_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_cso_mean(const __grid_constant__ BatchDir dir);
+__global__ void k_cso_centre(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz1(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz3(const __grid_constant__ BatchDir dir);
@@ -193,7 +194,7 @@ struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
       ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, otag, occ_cnt, vcnt, zacc, Vt,
       tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, selb, gscale, vrange, fcomb, noise, dynA, dynB,
-      vel, kapd, xbar, xpart, xcnt, total;
+      vel, kapd, xbar, xpart, total;
 };
 
 // swarm: the run uses the CSO operator (velocities, kept APDs, the centre)
@@ -254,13 +255,11 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max, bool s
   L.noise = take((size_t)steps_max * ns_max * 4);
   L.dynA = take((size_t)ns_max * ns_max * 4);
   L.dynB = take((size_t)ns_max * na_max * 4);
-  const size_t ncb = (size_t)(s.d_pad + kMeanCols - 1) / kMeanCols;
   const size_t nch = (size_t)(s.N + kMeanRows - 1) / kMeanRows;
   L.vel = take(swarm ? (size_t)2 * s.N * s.d_pad * sizeof(float) : 0);
   L.kapd = take(swarm ? (size_t)s.N * 4 : 0);
   L.xbar = take(swarm ? (size_t)s.d_pad * 4 : 0);
   L.xpart = take(swarm ? nch * s.d_pad * 4 : 0);
-  L.xcnt = take(swarm ? ncb * 4 : 0);
   L.total = o;
   return L;
 }
@@ -634,22 +633,26 @@ int cso_mean_blocks(const rvea_run *r) {
 }
 bool cso_needs_mean(const rvea_run *r) { return r->hd.op == 3 && r->hd.cso_phi != 0.0f; }
 void launch_cso_means(rvea_run *const *runs, int n, cudaStream_t st) {
-  static thread_local BatchDir d;
-  int nd = 0, p = 0;
+  static thread_local BatchDir d, dc;
+  int nd = 0, p = 0, pc = 0;
   for (int q = 0; q < n; ++q) {
     const rvea_run *r = runs[q];
     if (!cso_needs_mean(r)) continue;
     d.prefix[nd] = p;
-    d.desc[nd] = r->d_desc;
-    d.key[nd] = make_uint2(r->hd.key0, r->hd.key1);
-    d.items[nd] = nullptr;
+    dc.prefix[nd] = pc;
+    d.desc[nd] = dc.desc[nd] = r->d_desc;
+    d.key[nd] = dc.key[nd] = make_uint2(r->hd.key0, r->hd.key1);
+    d.items[nd] = dc.items[nd] = nullptr;
     p += cso_mean_blocks(r);
+    pc += (r->sh.d_pad / 4 + 7) / 8;   // one warp per float4 of variables
     ++nd;
   }
   if (nd == 0) return;
-  d.n = nd;
+  d.n = dc.n = nd;
   d.prefix[nd] = p;
+  dc.prefix[nd] = pc;
   launch_pdl(k_cso_mean, p, 256, 0, st, d);
+  launch_pdl(k_cso_centre, pc, 256, 0, st, dc);
 }
 void launch_repro_op1(const rvea_run *r, cudaStream_t st) {
   static thread_local BatchDir d;
@@ -1165,7 +1168,6 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     D.kapd = wsp<float>(r, lay.kapd);
     D.xbar = wsp<float>(r, lay.xbar);
     D.xpart = wsp<float>(r, lay.xpart);
-    D.xcnt = wsp<unsigned>(r, lay.xcnt);
   }
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
@@ -1659,10 +1661,10 @@ int rvea_launches_per_generation(const rvea_run *r, int adapting) {
   if (!r) return -1;
   // gamma, then the tile table and the direction grid (4 launches)
   const int adapt_n = adapting ? 1 + (r->hd.ntiles > 0 ? 1 : 0) + (r->hd.gG > 0 ? 4 : 0) : 0;
-  if (r->sel_mode == 3) return 2 + (cso_needs_mean(r) ? 1 : 0) + adapt_n;   // reproduction, fused tail
+  if (r->sel_mode == 3) return 2 + (cso_needs_mean(r) ? 2 : 0) + adapt_n;   // reproduction, fused tail
   int n = 3;                                        // reproduction, selection, finalize
   if (r->sh.team == 32 && r->hd.op == 0) n += 1;    // k_mutate
-  if (cso_needs_mean(r)) n += 1;                    // the CSO swarm centre
+  if (cso_needs_mean(r)) n += 2;                    // the CSO swarm centre (two launches)
   if (r->hd.problem == PROB_NEURO) n += 2;          // noise, rollout
   n += adapt_n;
   return n;

@@ -723,16 +723,16 @@ __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
     atomicMin(&R.ctl->zkey[threadIdx.x], s_z[threadIdx.x]);
 }
 // The swarm centre of the CSO operator, xbar = the mean position of the K
-// valid members (the oracle's order: a sum over the valid list, then / K).
-// CTA (chunk, column block) adds the rows [kMeanRows chunk, +kMeanRows) of
-// the valid list over its kMeanCols variables in float, in list order, into
-// xpart; the last CTA of a column block to arrive adds the chunks' partials
-// in chunk order in FP64 and divides by K, so the result does not depend on
-// the order in which the CTAs ran.  Grid per run: column blocks x
-// ceil(N / kMeanRows) chunks (chunks past K add nothing).
+// valid members (the oracle's order: a sum over the valid list, then / K),
+// in two launches.  k_cso_mean: CTA (chunk, column block) adds the rows
+// [kMeanRows chunk, +kMeanRows) of the valid list over its kMeanCols
+// variables in float, in list order, into xpart (grid per run: column blocks
+// x ceil(N / kMeanRows) chunks; chunks past K write zeros).  k_cso_centre:
+// one warp per float4 of variables adds the chunks' partials in FP64, lane l
+// taking chunks l, l + 32, ... in order and the lanes combined by a fixed
+// butterfly, then divides by K: the same bits on every run.
 __global__ void __launch_bounds__(256) k_cso_mean(const __grid_constant__ BatchDir dir) {
   __shared__ int s_rows[kMeanRows];
-  __shared__ int s_last;
   pdl_wait();      // the previous generation's lists and slot maps
   pdl_trigger();
   const int run = dir_find(dir, blockIdx.x);
@@ -740,7 +740,6 @@ __global__ void __launch_bounds__(256) k_cso_mean(const __grid_constant__ BatchD
   const int N = R.N, t = R.ctl->t, K = R.ctl->K;
   const int rq = R.d_pad >> 2;
   const int ncb = (R.d_pad + kMeanCols - 1) / kMeanCols;
-  const int nch = (N + kMeanRows - 1) / kMeanRows;
   const int b = blockIdx.x - dir.prefix[run];
   const int cb = b % ncb, ch = b / ncb;
   const int r0 = ch * kMeanRows, nr = max(0, min(kMeanRows, K - r0));
@@ -755,35 +754,46 @@ __global__ void __launch_bounds__(256) k_cso_mean(const __grid_constant__ BatchD
   }
   __syncthreads();
   const int Q = cb * (kMeanCols / 4) + (int)threadIdx.x;
+  if (Q >= rq) return;
   const float4 *X4 = reinterpret_cast<const float4 *>(R.X);
-  float4 *P4 = reinterpret_cast<float4 *>(R.xpart);
-  if (Q < rq) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 8
-    for (int r = 0; r < nr; ++r) {
-      const float4 x = __ldcs(X4 + (size_t)s_rows[r] * rq + Q);
-      acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
-    }
-    P4[(size_t)ch * rq + Q] = acc;
+  for (int r = 0; r < nr; ++r) {
+    const float4 x = __ldcs(X4 + (size_t)s_rows[r] * rq + Q);
+    acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&R.xcnt[cb], 1u) == (unsigned)(nch - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (Q < rq) {
-    double sx = 0.0, sy = 0.0, sz = 0.0, sw = 0.0;
-    const int nk = (K + kMeanRows - 1) / kMeanRows;
-    for (int c = 0; c < nk; ++c) {
-      const float4 p = __ldcg(P4 + (size_t)c * rq + Q);
-      sx += p.x; sy += p.y; sz += p.z; sw += p.w;
-    }
+  reinterpret_cast<float4 *>(R.xpart)[(size_t)ch * rq + Q] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_cso_centre(const __grid_constant__ BatchDir dir) {
+  pdl_wait();      // the partial sums
+  pdl_trigger();
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int lane = threadIdx.x & 31;
+  const int Q = (blockIdx.x - dir.prefix[run]) * 8 + (int)(threadIdx.x >> 5);
+  const int rq = R.d_pad >> 2;
+  if (Q >= rq) return;   // warp-uniform
+  const int K = R.ctl->K;
+  const int nk = (K + kMeanRows - 1) / kMeanRows;
+  const float4 *P4 = reinterpret_cast<const float4 *>(R.xpart);
+  double sx = 0.0, sy = 0.0, sz = 0.0, sw = 0.0;
+  for (int c = lane; c < nk; c += 32) {
+    const float4 p = __ldcg(P4 + (size_t)c * rq + Q);
+    sx += p.x; sy += p.y; sz += p.z; sw += p.w;
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+    sz += __shfl_xor_sync(0xffffffffu, sz, off);
+    sw += __shfl_xor_sync(0xffffffffu, sw, off);
+  }
+  if (lane == 0) {
     const double k = (double)max(K, 1);
     reinterpret_cast<float4 *>(R.xbar)[Q] =
         make_float4((float)(sx / k), (float)(sy / k), (float)(sz / k), (float)(sw / k));
   }
-  if (threadIdx.x == 0) R.xcnt[cb] = 0u;   // ready for the next generation
 }
 
 #define RVEA_REPRO_OP(name, PROB)                                                          \
@@ -808,7 +818,7 @@ RVEA_REPRO_OP(k_repro_op_dtlz4, PROB_DTLZ4)
 // x' is clipped to [L, U] and (x', v') goes to the child's pool row and its
 // velocity row.  Each lane streams float4s of the winner's and loser's rows
 // and the loser's velocity, the next float4s loaded while the current ones
-// are processed.  Then the g-terms, objectives and the ideal point.
+// are processed (the centre, read by every offspring, comes from L1 / L2).  Then the g-terms, objectives and the ideal point.
 template <int PROB>
 __device__ __forceinline__ void repro_cso_body(const BatchDir &dir) {
   __shared__ unsigned s_z[kMaxM];
@@ -858,40 +868,50 @@ __device__ __forceinline__ void repro_cso_body(const BatchDir &dir) {
       float4 *Y4 = reinterpret_cast<float4 *>(R.X + (size_t)slot * R.d_pad);
       float4 *VY = reinterpret_cast<float4 *>(R.vel + (size_t)slot * R.d_pad);
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 cw = z4, cl = z4, cv = z4, cb = z4;
+      float4 cw = z4, cl = z4, cv = z4;
       if (lane < rq) {
         cw = __ldg(XW + lane);
         cl = __ldg(XL + lane);
         cv = __ldg(VL + lane);
-        if (phi != 0.0f) cb = __ldg(XB + lane);
       }
       for (int Q = lane; Q < rq; Q += 32) {
-        float4 nw = z4, nl = z4, nv = z4, nb = z4;
+        float4 nw = z4, nl = z4, nv = z4;
         if (Q + 32 < rq) {
           nw = __ldg(XW + Q + 32);
           nl = __ldg(XL + Q + 32);
           nv = __ldg(VL + Q + 32);
-          if (phi != 0.0f) nb = __ldg(XB + Q + 32);
         }
-        const uint4 w1 = philox_k(3u * (uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
-        const uint4 w2 = philox_k(3u * (uint32_t)Q + 1u, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
-        const uint4 w3 = phi != 0.0f ? philox_k(3u * (uint32_t)Q + 2u, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr)
-                                     : make_uint4(0u, 0u, 0u, 0u);
+        // the centre (d_pad floats, shared by every offspring) stays in L1 / L2
+        const float4 cb = phi != 0.0f ? __ldg(XB + Q) : z4;
         const float aw[4] = {cw.x, cw.y, cw.z, cw.w}, al[4] = {cl.x, cl.y, cl.z, cl.w};
         const float av[4] = {cv.x, cv.y, cv.z, cv.w}, ab[4] = {cb.x, cb.y, cb.z, cb.w};
+        // the three terms in turn, one Philox call each (one call's words live at a time)
+        float vv[4];
+        {
+          const uint4 w = philox_k(3u * (uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) vv[v] = u24f(word(w, v)) * av[v];
+        }
+        {
+          const uint4 w = philox_k(3u * (uint32_t)Q + 1u, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) vv[v] = fmaf(u24f(word(w, v)), aw[v] - al[v], vv[v]);
+        }
+        if (phi != 0.0f) {
+          const uint4 w = philox_k(3u * (uint32_t)Q + 2u, (uint32_t)o, (uint32_t)t, TAG_CSO_R, kr);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) vv[v] = fmaf(phi * u24f(word(w, v)), ab[v] - al[v], vv[v]);
+        }
         float u[4], nvel[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int j = 4 * Q + v;
-          float vv = u24f(word(w1, v)) * av[v];
-          vv = fmaf(u24f(word(w2, v)), aw[v] - al[v], vv);
-          if (phi != 0.0f) vv = fmaf(phi * u24f(word(w3, v)), ab[v] - al[v], vv);
           if (j >= d) {   // row padding: a g-term of exactly zero, no velocity
             u[v] = 0.5f;
             nvel[v] = 0.0f;
           } else {
-            u[v] = clampf(al[v] + vv, L, U);
-            nvel[v] = vv;
+            u[v] = clampf(al[v] + vv[v], L, U);
+            nvel[v] = vv[v];
             if (j >= mh) {
               if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
               else acc.x = g_term1(PROB, u[v], acc.x);
@@ -900,7 +920,7 @@ __device__ __forceinline__ void repro_cso_body(const BatchDir &dir) {
         }
         Y4[Q] = make_float4(u[0], u[1], u[2], u[3]);
         __stcs(VY + Q, make_float4(nvel[0], nvel[1], nvel[2], nvel[3]));
-        cw = nw; cl = nl; cv = nv; cb = nb;
+        cw = nw; cl = nl; cv = nv;
       }
       const float2 gs = team_sum2(acc, 32);
       __syncwarp();   // the row is visible to lane 0

@@ -110,7 +110,6 @@ struct RunDesc {
   float *kapd;         // [N]        APD that kept vector slot j's member (+inf: none yet)
   float *xbar;         // [d_pad]    mean position of the valid members (the swarm centre)
   float *xpart;        // [ceil(N/kMeanRows)][d_pad] float partial sums of the centre
-  unsigned *xcnt;      // [column blocks] arrival counters of the centre's partials
   // draw recording (inspection; null when off): the vector slot of each
   // parent draw e, and each child's mutation-site count (-1: every site)
   // followed by its sites in draw order
