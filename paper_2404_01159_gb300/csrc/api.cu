@@ -248,7 +248,7 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max, bool s
   L.gcell = take((size_t)s.gcells * 32);
   L.gcnt = take((size_t)s.gcells * 4);
   L.gblk = take((size_t)(s.gG > 0 ? grid_build_blocks(s.gG, s.m) + 1 : 0) * 4);
-  L.gover = take((size_t)s.gcap * 2);
+  L.gover = take(((size_t)(s.gG > 0 ? grid_build_blocks(s.gG, s.m) : 0) * kGridBlockCap + s.gcap) * 2);
   L.gscale = take(kMaxM * 4);
   L.vrange = take(kMaxM * 8);
   L.fcomb = take((size_t)2 * s.m * s.n_comb * 4);
@@ -902,9 +902,9 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
   if (ev) cudaEventRecord(ev[4], st);
   if (gamma_by_flag) {
     if (nt > 0) k_tiles_batch<<<pt, 256, 0, st>>>(dt, 0);
-    // one pass: every vector block of the largest run has its CTA (the
-    // tile search gives each warp four vectors, a second round would double
-    // the chain), between two and four CTAs per SM
+    // one pass: every vector of the largest run has its lanes (the tile
+    // search gives each warp four vectors, a second round would double the
+    // chain), between two and four CTAs per SM
     int nbg = 0;
     for (int q = 0; q < n; ++q) nbg = std::max(nbg, (runs[q]->sh.N + 31) / 32);
     nbg = std::min(std::max(nbg, 2 * runs[0]->num_sms), 4 * runs[0]->num_sms);
@@ -917,7 +917,7 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
 rvea_status launch_gamma_force(rvea_run *r, cudaStream_t st) {
   static thread_local BatchDir d;
   dir_single(d, r, nullptr, 1);
-  const int nb = (r->sh.N + 31) / 32;
+  const int nb = (r->sh.N + 31) / 32;   // the tile search: 32 vectors a CTA
   k_gamma<<<std::min(nb, 4 * r->num_sms), 256, 0, st>>>(d, 1);
   return cuerr(cudaGetLastError());
 }
@@ -1156,6 +1156,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gG = sh.gG;
   D.gcells = sh.gcells;
   D.gcap = sh.gcap;
+  D.gfast_off = sh.gG > 0 ? grid_build_blocks(sh.gG, sh.m) * kGridBlockCap : 0;
   D.gcell = wsp<uint16_t>(r, lay.gcell);
   D.gcnt = wsp<int>(r, lay.gcnt);
   D.gblk = wsp<int>(r, lay.gblk);

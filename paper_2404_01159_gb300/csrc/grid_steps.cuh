@@ -32,6 +32,13 @@ namespace rvea {
 
 constexpr int kGridRec = 16;      // uint16 per cell record (32 bytes)
 constexpr int kGridInline = 15;   // candidates held in the record itself
+// Longer lists: the count pass writes a cell's list (up to kGridWarpBuf
+// candidates) into its block's share of the overflow area, kGridBlockCap
+// entries per block at the start of gover; a list that does not fit is left
+// to the fill pass, which writes it after the shares (from gfast_off on).
+constexpr int kGridBlockCap = 2048;
+constexpr int kGridWarpBuf = 128;
+constexpr int kGridFastBit = 1 << 30;   // gcnt flag: list written by the count pass
 // cells per block of the build: one CTA lists the candidate tiles of a
 // block once for all its cells (64 consecutive cells for m = 2, 8 x 8 for
 // m = 3); grid_build_blocks gives the launch's CTA count

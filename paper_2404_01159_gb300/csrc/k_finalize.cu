@@ -251,12 +251,15 @@ __device__ __forceinline__ float gdot(const float *a, float4 b) {
   return d;
 }
 
-// Eight lanes per vector j (lanes 8g .. 8g+7 of a warp; every lane of the
-// warp calls it): the lanes split the tile loops, reduce over the group
-// between the passes, and the group's first lane writes gamma_j.
+// kGammaLanes lanes per vector j (a group of consecutive lanes of a warp;
+// every lane of the warp calls it): the lanes split the tile loops, reduce
+// over the group between the passes, and the group's first lane writes
+// gamma_j.
+constexpr int kGammaLanes = 8;   // 16 measured slower (57 against 48 us at N = 9870)
 template <int M>
 __device__ void gamma_group(const RunDesc &R, int j) {
-  const int T = R.ntiles, lane = threadIdx.x & 31, sub = lane & 7;
+  constexpr int GL = kGammaLanes;
+  const int T = R.ntiles, lane = threadIdx.x & 31, sub = lane & (GL - 1);
   const bool act = j < R.N;
   float v[4] = {0.f, 0.f, 0.f, 0.f};
   if (act) {
@@ -273,12 +276,12 @@ __device__ void gamma_group(const RunDesc &R, int j) {
   // the closest centre (ties: the smaller tile)
   float bc = -INFINITY;
   int bt = 0x7FFFFFFF;
-  for (int t = sub; t < T; t += 8) {
+  for (int t = sub; t < T; t += GL) {
     const float d = gdot<M>(v, R.tcen[t]);
     if (d > bc) { bc = d; bt = t; }
   }
 #pragma unroll
-  for (int off = 1; off < 8; off <<= 1) {
+  for (int off = 1; off < GL; off <<= 1) {
     const float od = __shfl_xor_sync(0xffffffffu, bc, off);
     const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
     if (od > bc || (od == bc && ot < bt)) { bc = od; bt = ot; }
@@ -286,15 +289,15 @@ __device__ void gamma_group(const RunDesc &R, int j) {
   float b = -2.0f;
   if (act && bt < T) {   // its members, split over the group
     const int2 rg = R.trng[bt];
-    for (int q = sub; q < rg.y; q += 8)
+    for (int q = sub; q < rg.y; q += GL)
       if (member(rg.x + q) != j) b = fmaxf(b, gdot<M>(v, R.Vt[rg.x + q]));
   }
 #pragma unroll
-  for (int off = 1; off < 8; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
+  for (int off = 1; off < GL; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
   // every other tile that can hold a dot within 2e-5 of b, one lane a tile
   const float b0 = b - 2e-5f;
   if (act) {
-    for (int t = sub; t < T; t += 8) {
+    for (int t = sub; t < T; t += GL) {
       if (t == bt || !admits(t, b0)) continue;
       const int2 rg = R.trng[t];
       for (int q = 0; q < rg.y; ++q)
@@ -302,13 +305,13 @@ __device__ void gamma_group(const RunDesc &R, int j) {
     }
   }
 #pragma unroll
-  for (int off = 1; off < 8; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
+  for (int off = 1; off < GL; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
   // FP64 recheck of the float maxima within 1e-5 of b
   const float thr = b - 1e-5f;
   const double *vjp = R.V64 + (size_t)(act ? j : 0) * M;
   double best = -2.0;
   if (act) {
-    for (int t = sub; t < T; t += 8) {
+    for (int t = sub; t < T; t += GL) {
       if (t != bt && !admits(t, thr - 1e-5f)) continue;
       const int2 rg = R.trng[t];
       for (int q = 0; q < rg.y; ++q) {
@@ -319,7 +322,7 @@ __device__ void gamma_group(const RunDesc &R, int j) {
     }
   }
 #pragma unroll
-  for (int off = 1; off < 8; off <<= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+  for (int off = 1; off < GL; off <<= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
   if (act && sub == 0) {
     double g = acos(fmin(1.0, fmax(-1.0, best)));
     if (!(g >= 1e-12)) g = 1e-12;
@@ -331,8 +334,9 @@ __device__ void gamma_group(const RunDesc &R, int j) {
 __device__ void gamma_tiles(const RunDesc &R) {
   const int lane = threadIdx.x & 31;
   const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-  for (int base = 4 * wg; base < R.N; base += 4 * nw) {   // warp-uniform: four vectors a warp
-    const int j = base + (lane >> 3);
+  constexpr int PW = 32 / kGammaLanes;   // vectors a warp
+  for (int base = PW * wg; base < R.N; base += PW * nw) {   // warp-uniform
+    const int j = base + lane / kGammaLanes;
     switch (R.m) {
       case 2: gamma_group<2>(R, j); break;
       case 3: gamma_group<3>(R, j); break;

@@ -141,8 +141,11 @@ __device__ __forceinline__ bool support_test(const CellGeom &g, float4 v) {
 // Count (FILL = false) or write (FILL = true) the candidates of one cell:
 // the tiles of the list whose centre lies within R + rho_t of c, then their
 // members within R that pass the support test.
+// The count pass also keeps the first kGridWarpBuf candidates in `buf` (the
+// warp's shared-memory list), for its own write of an overflow list.
 template <int M, bool FILL>
-__device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl, bool inl, int at) {
+__device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl, bool inl, int at,
+                        uint16_t *buf) {
   const int lane = threadIdx.x & 31;
   const int cell = M == 2 ? ck[0] : ck[0] + ck[1] * R.gG;
   const float4 *Vt = R.Vt;
@@ -181,7 +184,8 @@ __device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl
             const int k = n + __popc(mm & ((1u << lane) - 1u));
             if (!FILL) {   // the count pass writes the first kGridInline in place;
               if (k < kGridInline) rec[1 + k] = (uint16_t)(rg.x + q);   // the fill pass
-            } else {       // only the cells past kGridInline, into their list
+              if (k < kGridWarpBuf) buf[k] = (uint16_t)(rg.x + q);
+            } else {       // only the cells past kGridInline that the count pass left, into their list
               R.gover[at + k] = (uint16_t)(rg.x + q);
             }
           }
@@ -210,7 +214,8 @@ __device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl
 template <int M, bool FILL>
 __device__ void grid_block(const RunDesc &R) {
   __shared__ int s_list[kGridBlockList];
-  __shared__ int s_n, s_ovf;
+  __shared__ uint16_t s_buf[8][kGridWarpBuf];   // count: each warp's current list
+  __shared__ int s_n, s_ovf, s_fast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = R.gG, span = M == 2 ? kGridSpan2 : kGridSpan3;
   const int nbx = (G + span - 1) / span;
@@ -220,7 +225,7 @@ __device__ void grid_block(const RunDesc &R) {
   if (FILL && __ldcg(R.gblk + blockIdx.x + 1) == __ldcg(R.gblk + blockIdx.x)) return;
   // count: this block's overflow candidates (cells past kGridInline); fill:
   // the next free position of the block's range of the overflow area
-  if (threadIdx.x == 0) s_ovf = 0;
+  if (threadIdx.x == 0) { s_ovf = 0; s_fast = 0; }
   int b0[2] = {0, 0};
   {
     int rem = blockIdx.x;
@@ -261,10 +266,10 @@ __device__ void grid_block(const RunDesc &R) {
       int at = 0;
       if (FILL) {   // an overflow cell claims its range and records it
         const int cnt = __ldcg(R.gcnt + cell);
-        inl = cnt <= kGridInline;
+        inl = cnt <= kGridInline || (cnt & kGridFastBit);
         if (inl) continue;   // written by the count pass
         {
-          if (lane == 0) at = base + atomicAdd(&s_ovf, cnt);
+          if (lane == 0) at = R.gfast_off + base + atomicAdd(&s_ovf, cnt);
           at = __shfl_sync(0xffffffffu, at, 0);
           if (lane == 0) {
             uint16_t *rec = R.gcell + (size_t)cell * kGridRec;
@@ -273,8 +278,31 @@ __device__ void grid_block(const RunDesc &R) {
           }
         }
       }
-      const int n = grid_one<M, FILL>(R, ck, all ? nullptr : s_list, all ? R.ntiles : nl, inl, at);
-      if (!FILL && lane == 0 && n > kGridInline) atomicAdd(&s_ovf, n);
+      const int n = grid_one<M, FILL>(R, ck, all ? nullptr : s_list, all ? R.ntiles : nl, inl, at,
+                                      FILL ? nullptr : s_buf[warp]);
+      if (!FILL && n > kGridInline) {
+        // an overflow list: into this block's share when the warp holds it all
+        // and the share has room, else left to the fill pass
+        int fat = -1;
+        if (n <= kGridWarpBuf && lane == 0) {
+          const int off = atomicAdd(&s_fast, n);
+          if (off + n <= kGridBlockCap) fat = blockIdx.x * kGridBlockCap + off;
+        }
+        fat = __shfl_sync(0xffffffffu, fat, 0);
+        __syncwarp();   // the warp's list is complete in s_buf
+        if (fat >= 0) {
+          for (int e = lane; e < n; e += 32) R.gover[fat + e] = s_buf[warp][e];
+          if (lane == 0) {
+            uint16_t *rec = R.gcell + (size_t)cell * kGridRec;
+            rec[1] = (uint16_t)(fat & 0xFFFF);
+            rec[2] = (uint16_t)((uint32_t)fat >> 16);
+            R.gcnt[cell] = n | kGridFastBit;
+          }
+        } else if (lane == 0) {
+          atomicAdd(&s_ovf, n);
+        }
+        __syncwarp();   // s_buf is read before the next cell overwrites it
+      }
     }
   }
   if (!FILL) {

@@ -126,12 +126,13 @@ struct RunDesc {
                        //            invalid; children N + c), for generation parity t & 1
   // direction grid of the association (m = 2, 3; gG = 0: none)
   int gG, gcells, gcap;   // steps per barycentric axis, cells, candidate capacity
+  int gfast_off;       // start of the fill pass's area in gover (after the blocks' shares)
   uint16_t *gcell;     // [gcells][16] record: count, then up to 15 tile-order positions
                        //              (or, past 15, the offset of the list in gover)
   int *gcnt;           // [gcells]     candidates of each cell (build)
   int *gblk;           // [build blocks] overflow candidates of each block of cells, then
                        //              their offset in gover
-  uint16_t *gover;     // [gcap]       candidate lists of the cells with more than 15
+  uint16_t *gover;     // [gfast_off + gcap] candidate lists of the cells with more than 15
   float *gscale;       // [kMaxM]      w = 1 / range of the grid's V
   double *vrange;      // [kMaxM]      objective range of the last adaptation (1: none)
   int *blk_cnt;        // [n_comb/256] arrival counters of the selection blocks
