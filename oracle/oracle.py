@@ -32,7 +32,8 @@ class Params(C.Structure):
                 ("eta_m", C.c_double), ("p_c", C.c_double), ("p_m", C.c_double),
                 ("L", C.c_double), ("U", C.c_double), ("seed", C.c_uint64),
                 ("op", C.c_int32), ("de_F", C.c_double), ("de_CR", C.c_double),
-                ("cso_phi", C.c_double)]
+                ("cso_phi", C.c_double), ("pso_w", C.c_double), ("pso_c1", C.c_double),
+                ("pso_c2", C.c_double)]
 
 
 class Neuro(C.Structure):
@@ -93,9 +94,14 @@ def lib():
         L.orc_cso_picks.argtypes = [P(Params), C.c_int32, C.c_int32, C.c_int32, i32]
         L.orc_cso_offspring.argtypes = [P(Params), C.c_int32, f64, f64, f64, C.c_int32, i32,
                                         f64, f64, f64]
+        L.orc_pso_picks.argtypes = [P(Params), C.c_int32, C.c_int32, C.c_int32, i32]
+        L.orc_pso_offspring.argtypes = [P(Params), C.c_int32, f64, f64, f64, f64, C.c_int32,
+                                        i32, f64, f64]
+        L.orc_pso_pbest.argtypes = [P(Params), C.c_int32, C.c_int32, i32, f64, f64, f64, f64,
+                                    f64, f64]
         L.orc_generation_ex.argtypes = [P(Params), C.c_int32, f64, P(Neuro),
-                                        f64, f64, u8, f64, f64, f64, f64, f64, f64, i32,
-                                        i32, i32]
+                                        f64, f64, u8, f64, f64, f64, f64, f64, f64, f64, f64,
+                                        i32, i32, i32]
         L.orc_generation_ex.restype = C.c_int32
         L.orc_set_threads.argtypes = [C.c_int32]
         L.orc_get_threads.restype = C.c_int32
@@ -125,14 +131,47 @@ def philox(ctr, key):
     return [int(x) for x in o]
 
 
-OP_SBX_PM, OP_DE, OP_RANDOM, OP_CSO = 0, 1, 2, 3
+OP_SBX_PM, OP_DE, OP_RANDOM, OP_CSO, OP_PSO = 0, 1, 2, 3, 4
 
 
 def make_params(m, d, N, H, problem=DTLZ2, t_max=100, alpha=2.0, f_r=0.1,
                 eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, L=0.0, U=1.0, seed=0,
-                op=OP_SBX_PM, de_F=0.5, de_CR=0.9, cso_phi=0.0):
+                op=OP_SBX_PM, de_F=0.5, de_CR=0.9, cso_phi=0.0,
+                pso_w=0.7298, pso_c1=1.49618, pso_c2=1.49618):
     return Params(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
-                  L, U, seed, op, de_F, de_CR, cso_phi)
+                  L, U, seed, op, de_F, de_CR, cso_phi, pso_w, pso_c1, pso_c2)
+
+
+def pso_picks(p: Params, t: int, K: int, o: int):
+    """Positions in the valid list of offspring o's particle and of the two
+    candidates for its leader (PSO)."""
+    out = np.zeros(3, dtype=np.int32)
+    lib().orc_pso_picks(C.byref(p), int(t), int(K), int(o), _p(out, C.c_int32))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def pso_offspring(p: Params, t: int, X, Vel, Pb, apd, vlist):
+    """PSO offspring positions and velocities (N x d each)."""
+    X, Vel, Pb, apd = _f64(X), _f64(Vel), _f64(Pb), _f64(apd)
+    vl = np.ascontiguousarray(vlist, dtype=np.int32)
+    Xo = np.zeros((p.N, p.d))
+    Vo = np.zeros((p.N, p.d))
+    lib().orc_pso_offspring(C.byref(p), int(t), _p(X, C.c_double), _p(Vel, C.c_double),
+                            _p(Pb, C.c_double), _p(apd, C.c_double), len(vl),
+                            _p(vl, C.c_int32), _p(Xo, C.c_double), _p(Vo, C.c_double))
+    return Xo, Vo
+
+
+def pso_pbest(p: Params, t: int, vlist, Pb, FPb, Xc, Fc):
+    """Personal bests (N x d) and their objectives (N x m) of the offspring."""
+    Pb, FPb, Xc, Fc = _f64(Pb), _f64(FPb), _f64(Xc), _f64(Fc)
+    vl = np.ascontiguousarray(vlist, dtype=np.int32)
+    Po = np.zeros((p.N, p.d))
+    FPo = np.zeros((p.N, p.m))
+    lib().orc_pso_pbest(C.byref(p), int(t), len(vl), _p(vl, C.c_int32), _p(Pb, C.c_double),
+                        _p(FPb, C.c_double), _p(Xc, C.c_double), _p(Fc, C.c_double),
+                        _p(Po, C.c_double), _p(FPo, C.c_double))
+    return Po, FPo
 
 
 def cso_picks(p: Params, t: int, K: int, o: int):
@@ -314,7 +353,7 @@ def select(F, valid, V, gam, t, t_max, alpha):
 class State:
     """Population in vector-slot order, as the oracle's generation consumes it."""
 
-    def __init__(self, X, F, valid, V, gamma, t, vel=None, apd=None):
+    def __init__(self, X, F, valid, V, gamma, t, vel=None, apd=None, pbest=None, fpbest=None):
         self.X = np.array(X, dtype=np.float64, order="C", copy=True)
         # the CSO swarm state: velocities (zero at first) and the APD that
         # kept each member (+inf before any selection)
@@ -323,6 +362,12 @@ class State:
         self.apd = (np.full(self.X.shape[0], np.inf) if apd is None
                     else np.array(apd, dtype=np.float64, order="C", copy=True))
         self.F = np.array(F, dtype=np.float64, order="C", copy=True)
+        # the PSO personal bests and their objectives (the positions themselves
+        # at first)
+        self.pbest = (self.X.copy() if pbest is None
+                      else np.array(pbest, dtype=np.float64, order="C", copy=True))
+        self.fpbest = (self.F.copy() if fpbest is None
+                       else np.array(fpbest, dtype=np.float64, order="C", copy=True))
         self.valid = np.array(valid, dtype=np.uint8, order="C", copy=True)
         self.V = np.array(V, dtype=np.float64, order="C", copy=True)
         self.gamma = np.array(gamma, dtype=np.float64, order="C", copy=True)
@@ -350,7 +395,8 @@ def generation(p: Params, V0, st: State, nd=None):
                                     _p(st.X, C.c_double), _p(st.F, C.c_double),
                                     _p(st.valid, C.c_uint8), _p(st.V, C.c_double),
                                     _p(st.gamma, C.c_double), _p(st.vel, C.c_double),
-                                    _p(st.apd, C.c_double), _p(Xc, C.c_double),
+                                    _p(st.apd, C.c_double), _p(st.pbest, C.c_double),
+                                    _p(st.fpbest, C.c_double), _p(Xc, C.c_double),
                                     _p(Fc, C.c_double), _p(par, C.c_int32),
                                     _p(assoc, C.c_int32), _p(surv, C.c_int32))
     st.t += 1

@@ -565,6 +565,93 @@ void orc_cso_offspring(const orc_params *p, int32_t t, const double *X, const do
     }
 }
 
+/* Particle swarm optimization (PSO; Kennedy and Eberhart 1995, with the
+ * inertia weight of Shi and Eberhart 1998) as the reproduction operator.  The
+ * paper names it and plugs it into the same selection without printing it;
+ * the reading (listed with the others in the design notes), after the
+ * multiobjective PSO of Coello, Pulido and Lechuga (2004) with the archive's
+ * role taken by RVEA's population: particle o is the member at position
+ * o mod K of the valid list, with its velocity v and personal best p
+ * (carried with the member, like the velocity); its leader g is the winner
+ * of a binary tournament on the kept APD (Eq. 4) between two distinct valid
+ * members (positions a, then b over the others: PSO_PICK (o, 0, t) words 0
+ * and 1, as the CSO competitors; ties to the smaller slot; with K = 1 the
+ * member itself).  The particle moves:
+ *   v' = w v + c1 r1 (p - x) + c2 r2 (g - x),   x' = clip(x + v'),
+ * r1, r2 of variable j the u24 of word j%4 of PSO_R (2 (j/4) + k, o, t),
+ * k = 0, 1.  out[0] = the particle's position in the list, out[1] = the
+ * leader's. */
+void orc_pso_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out)
+{
+    uint32_t w[4];
+    philox(p, (uint32_t)o, 0u, (uint32_t)t, ORC_TAG_PSO_PICK, w);
+    const int32_t a = (int32_t)(((uint64_t)w[0] * (uint64_t)K) >> 32);
+    int32_t b = a;
+    if (K > 1) {
+        b = (int32_t)(((uint64_t)w[1] * (uint64_t)(K - 1)) >> 32);
+        if (b >= a) b += 1;
+    }
+    out[0] = o % K;
+    out[1] = a;   /* the tournament is decided by the caller from the kept APDs */
+    out[2] = b;
+}
+
+void orc_pso_offspring(const orc_params *p, int32_t t, const double *X, const double *Vel,
+                       const double *Pb, const double *apd, int32_t K, const int32_t *vlist,
+                       double *Xout, double *Vout)
+{
+    const int32_t N = p->N, d = p->d;
+    for (int32_t o = 0; o < N; ++o) {
+        int32_t pk[3];
+        orc_pso_picks(p, t, K, o, pk);
+        const int32_t ip = vlist[pk[0]], ia = vlist[pk[1]], ib = vlist[pk[2]];
+        const int32_t ig = (apd[ia] < apd[ib] || (apd[ia] == apd[ib] && ia <= ib)) ? ia : ib;
+        const double *x = X + (int64_t)ip * d, *v = Vel + (int64_t)ip * d;
+        const double *pb = Pb + (int64_t)ip * d, *g = X + (int64_t)ig * d;
+        for (int32_t j = 0; j < d; ++j) {
+            double r[2];
+            for (int32_t k = 0; k < 2; ++k) {
+                uint32_t w[4];
+                philox(p, (uint32_t)(2 * (j / 4) + k), (uint32_t)o, (uint32_t)t, ORC_TAG_PSO_R, w);
+                r[k] = u24(w[j % 4]);
+            }
+            const double vn = p->pso_w * v[j] + p->pso_c1 * r[0] * (pb[j] - x[j]) +
+                              p->pso_c2 * r[1] * (g[j] - x[j]);
+            double xn = x[j] + vn;
+            if (xn < p->L) xn = p->L;
+            if (xn > p->U) xn = p->U;
+            Xout[(int64_t)o * d + j] = xn;
+            Vout[(int64_t)o * d + j] = vn;
+        }
+    }
+}
+
+/* Personal best of offspring o after its evaluation (the MOPSO rule of
+ * Coello et al.): its new position x' unless the particle's personal best p
+ * dominates it (f(p) <= f(x') in every objective and < in one), when p is
+ * kept.  Pb / FPb: personal bests and their objectives by slot; Xc / Fc: the
+ * offspring and their objectives; Pout / FPout: the offspring's bests. */
+void orc_pso_pbest(const orc_params *p, int32_t t, int32_t K, const int32_t *vlist,
+                   const double *Pb, const double *FPb, const double *Xc, const double *Fc,
+                   double *Pout, double *FPout)
+{
+    const int32_t N = p->N, d = p->d, m = p->m;
+    (void)t;
+    for (int32_t o = 0; o < N; ++o) {
+        const int32_t ip = vlist[o % K];
+        const double *fp = FPb + (int64_t)ip * m, *fx = Fc + (int64_t)o * m;
+        int le = 1, lt = 0;
+        for (int32_t k = 0; k < m; ++k) {
+            if (fp[k] > fx[k]) le = 0;
+            if (fp[k] < fx[k]) lt = 1;
+        }
+        const int keep_old = le && lt;
+        memcpy(Pout + (int64_t)o * d, keep_old ? Pb + (int64_t)ip * d : Xc + (int64_t)o * d,
+               sizeof(double) * (size_t)d);
+        memcpy(FPout + (int64_t)o * m, keep_old ? fp : fx, sizeof(double) * (size_t)m);
+    }
+}
+
 /* Tensorized SBX, Appendix B (the two B equations and X_cross):
  *   B  = sgn(R1 - 1/2) [H(1/2 - Mc)(2Mc)^(1/(eta+1)) + (1 - H(1/2 - Mc))(2 - 2Mc)^(-1/(eta+1))]
  *   B  = [1 - rep(H(R3 - p_c))] [(1 - H(R2 - 1/2)) B + H(R2 - 1/2)] + rep(H(R3 - p_c))
@@ -816,18 +903,19 @@ int32_t orc_generation(const orc_params *p, int32_t t, const double *V0,
                        double *Xchild, double *Fchild, int32_t *parents,
                        int32_t *assoc, int32_t *survivor)
 {
-    return orc_generation_ex(p, t, V0, nd, X, F, valid, V, gamma, NULL, NULL,
+    return orc_generation_ex(p, t, V0, nd, X, F, valid, V, gamma, NULL, NULL, NULL, NULL,
                              Xchild, Fchild, parents, assoc, survivor);
 }
 
-/* The same with the swarm state of the CSO operator: Vel (N x d, velocities
- * by slot) and apd (N, the APD that kept each member; +inf before any
- * selection), both updated with the population.  They may be NULL for the
- * other operators (apd is then not kept). */
+/* The same with the swarm state of the CSO and PSO operators: Vel (N x d,
+ * velocities by slot), apd (N, the APD that kept each member; +inf before
+ * any selection), and for PSO Pb (N x d, personal bests) and FPb (N x m,
+ * their objectives), all updated with the population.  They may be NULL for
+ * the operators that do not use them (apd is then not kept). */
 int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
                           const orc_neuro *nd,
                           double *X, double *F, uint8_t *valid, double *V, double *gamma,
-                          double *Vel, double *apd,
+                          double *Vel, double *apd, double *Pb, double *FPb,
                           double *Xchild, double *Fchild, int32_t *parents,
                           int32_t *assoc, int32_t *survivor)
 {
@@ -840,7 +928,8 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
 
     int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * P));
     double *Xc = (double *)malloc(sizeof(double) * (size_t)(2 * P) * d);
-    double *Vc = NULL;   /* the offspring's velocities (CSO) */
+    double *Vc = NULL;   /* the offspring's velocities (CSO, PSO) */
+    double *Pc = NULL, *FPc = NULL;   /* the offspring's personal bests (PSO) */
     if (p->op == ORC_OP_DE) {
         /* the extensibility experiment's operators replace SBX and mutation */
         for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
@@ -858,6 +947,11 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
         Vc = (double *)malloc(sizeof(double) * (size_t)N * d);
         orc_cso_offspring(p, t, X, Vel, apd, K, vlist, xbar, Xc, Vc);
         free(xbar);
+    } else if (p->op == ORC_OP_PSO) {
+        for (int32_t e = 0; e < 2 * P; ++e) par[e] = -1;
+        if (!Vel || !apd || !Pb || !FPb) { free(vlist); free(par); free(Xc); return -1; }
+        Vc = (double *)malloc(sizeof(double) * (size_t)N * d);
+        orc_pso_offspring(p, t, X, Vel, Pb, apd, K, vlist, Xc, Vc);
     } else {
         orc_mating(p, t, K, vlist, par);
         double *X1 = (double *)malloc(sizeof(double) * (size_t)P * d);
@@ -874,6 +968,11 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
     }
     double *Fc = (double *)malloc(sizeof(double) * (size_t)N * m);
     orc_evaluate(p, N, Xc, Fc, nd, t);
+    if (p->op == ORC_OP_PSO) {
+        Pc = (double *)malloc(sizeof(double) * (size_t)N * d);
+        FPc = (double *)malloc(sizeof(double) * (size_t)N * m);
+        orc_pso_pbest(p, t, K, vlist, Pb, FPb, Xc, Fc, Pc, FPc);
+    }
 
     /* combined population: parents (slot order) then children */
     const int32_t n = 2 * N;
@@ -899,6 +998,8 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
     double *Xn = (double *)malloc(sizeof(double) * (size_t)N * d);
     double *Fn = (double *)malloc(sizeof(double) * (size_t)N * m);
     double *Vn = Vel ? (double *)malloc(sizeof(double) * (size_t)N * d) : NULL;
+    double *Pn = Pb ? (double *)malloc(sizeof(double) * (size_t)N * d) : NULL;
+    double *FPn = FPb ? (double *)malloc(sizeof(double) * (size_t)N * m) : NULL;
     int32_t alive = 0;
     for (int32_t j = 0; j < N; ++j) {
         int32_t i = sv[j];
@@ -907,6 +1008,8 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
             for (int32_t k = 0; k < d; ++k) Xn[(int64_t)j * d + k] = NAN;
             for (int32_t k = 0; k < m; ++k) Fn[(int64_t)j * m + k] = NAN;
             if (Vn) for (int32_t k = 0; k < d; ++k) Vn[(int64_t)j * d + k] = NAN;
+            if (Pn) for (int32_t k = 0; k < d; ++k) Pn[(int64_t)j * d + k] = NAN;
+            if (FPn) for (int32_t k = 0; k < m; ++k) FPn[(int64_t)j * m + k] = NAN;
             if (apd) apd[j] = INFINITY;
             continue;
         }
@@ -922,11 +1025,22 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
             else if (Vc) memcpy(vd, Vc + (int64_t)(i - N) * d, sizeof(double) * (size_t)d);
             else for (int32_t k = 0; k < d; ++k) vd[k] = 0.0;
         }
+        if (Pn) {   /* a parent keeps its personal best; a child carries its own */
+            double *pd = Pn + (int64_t)j * d, *fpd = FPn + (int64_t)j * m;
+            const double *ps = (i < N) ? Pb + (int64_t)i * d
+                             : Pc ? Pc + (int64_t)(i - N) * d : Xc + (int64_t)(i - N) * d;
+            const double *fps = (i < N) ? FPb + (int64_t)i * m
+                              : FPc ? FPc + (int64_t)(i - N) * m : Fc + (int64_t)(i - N) * m;
+            memcpy(pd, ps, sizeof(double) * (size_t)d);
+            memcpy(fpd, fps, sizeof(double) * (size_t)m);
+        }
         if (apd) apd[j] = apd_all[i];
     }
     memcpy(X, Xn, sizeof(double) * (size_t)N * d);
     memcpy(F, Fn, sizeof(double) * (size_t)N * m);
     if (Vn) { memcpy(Vel, Vn, sizeof(double) * (size_t)N * d); free(Vn); }
+    if (Pn) { memcpy(Pb, Pn, sizeof(double) * (size_t)N * d); free(Pn); }
+    if (FPn) { memcpy(FPb, FPn, sizeof(double) * (size_t)N * m); free(FPn); }
 
     /* reference-vector adaptation every round(f_r * t_max) generations */
     int32_t period = (int32_t)floor(p->f_r * (double)p->t_max + 0.5);
@@ -939,6 +1053,6 @@ int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
     }
 
     free(Xn); free(Fn); free(as); free(sv); free(vall); free(Fall); free(apd_all);
-    free(Fc); free(Xc); free(Vc); free(par); free(vlist);
+    free(Fc); free(Xc); free(Vc); free(Pc); free(FPc); free(par); free(vlist);
     return alive;
 }

@@ -25,6 +25,9 @@
  *   CSO_PICK (o, 0, t, 11) words 0,1 -> the two competitors of offspring o
  *   CSO_R  (3(j/4)+k, o, t, 12) word j%4 -> r_{k+1} (u24), k = 0,1,2, of variable j of
  *                          offspring o
+ *   PSO_PICK (o, 0, t, 13) words 0,1 -> the two candidates for offspring o's leader
+ *   PSO_R  (2(j/4)+k, o, t, 14) word j%4 -> r_{k+1} (u24), k = 0,1, of variable j of
+ *                          offspring o
  * where u24(w) = (w >> 8) * 2^-24.
  */
 #ifndef RVEA_ORACLE_H
@@ -40,7 +43,7 @@ enum { ORC_DTLZ2 = 0, ORC_DTLZ1 = 1, ORC_NEURO = 2, ORC_DTLZ3 = 3, ORC_DTLZ4 = 4
 enum { ORC_TAG_INIT = 1, ORC_TAG_MATE = 2, ORC_TAG_PAIR = 3, ORC_TAG_SBX = 4,
        ORC_TAG_MUTSITE = 5, ORC_TAG_MUTMAG = 6, ORC_TAG_NOISE = 7,
        ORC_TAG_DE_PICK = 8, ORC_TAG_DE_CR = 9, ORC_TAG_RANDOM = 10,
-       ORC_TAG_CSO_PICK = 11, ORC_TAG_CSO_R = 12 };
+       ORC_TAG_CSO_PICK = 11, ORC_TAG_CSO_R = 12, ORC_TAG_PSO_PICK = 13, ORC_TAG_PSO_R = 14 };
 
 typedef struct {
     int32_t m, d, N, H;
@@ -51,12 +54,13 @@ typedef struct {
     int32_t op;               /* reproduction: ORC_OP_SBX_PM, ORC_OP_DE, ORC_OP_RANDOM */
     double de_F, de_CR;       /* DE/rand/1/bin scale factor and crossover rate   */
     double cso_phi;           /* CSO: weight of the swarm-centre term            */
+    double pso_w, pso_c1, pso_c2;   /* PSO: inertia weight, cognitive and social  */
 } orc_params;
 
 /* Reproduction operators (Sec. 4.4, the extensibility experiment): SBX with
  * polynomial mutation (Appendix B), DE/rand/1/bin, random reproduction, the
  * competitive swarm optimizer. */
-enum { ORC_OP_SBX_PM = 0, ORC_OP_DE = 1, ORC_OP_RANDOM = 2, ORC_OP_CSO = 3 };
+enum { ORC_OP_SBX_PM = 0, ORC_OP_DE = 1, ORC_OP_RANDOM = 2, ORC_OP_CSO = 3, ORC_OP_PSO = 4 };
 
 /* Synthetic linear-dynamics rollout used as the neuroevolution objective. */
 typedef struct {
@@ -106,10 +110,17 @@ void orc_cso_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t
 void orc_cso_offspring(const orc_params *p, int32_t t, const double *X, const double *Vel,
                        const double *apd, int32_t K, const int32_t *vlist, const double *xbar,
                        double *Xout, double *Vout);
+void orc_pso_picks(const orc_params *p, int32_t t, int32_t K, int32_t o, int32_t *out);
+void orc_pso_offspring(const orc_params *p, int32_t t, const double *X, const double *Vel,
+                       const double *Pb, const double *apd, int32_t K, const int32_t *vlist,
+                       double *Xout, double *Vout);
+void orc_pso_pbest(const orc_params *p, int32_t t, int32_t K, const int32_t *vlist,
+                   const double *Pb, const double *FPb, const double *Xc, const double *Fc,
+                   double *Pout, double *FPout);
 int32_t orc_generation_ex(const orc_params *p, int32_t t, const double *V0,
                           const orc_neuro *nd,
                           double *X, double *F, uint8_t *valid, double *V, double *gamma,
-                          double *Vel, double *apd,
+                          double *Vel, double *apd, double *Pb, double *FPb,
                           double *Xchild, double *Fchild, int32_t *parents,
                           int32_t *assoc, int32_t *survivor);
 void orc_set_threads(int32_t n);

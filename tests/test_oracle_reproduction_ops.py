@@ -1,5 +1,5 @@
 """Pins of the oracle's alternative reproduction operators (the extensibility
-experiment, Sec. 4.4 / Appendix C): random reproduction and DE/rand/1/bin.
+experiment, Sec. 4.4 / Appendix C): random reproduction, DE/rand/1/bin, CSO and PSO.
 Each pin checks a property the published operator fixes, independently of
 the oracle's own arithmetic."""
 import itertools
@@ -262,3 +262,123 @@ def test_generation_with_cso_keeps_the_swarm_state(orc):
         src_v = Vel[i] if i < p.N else want_v[i - p.N]
         assert np.allclose(st.vel[j], src_v, rtol=0, atol=1e-12)
         assert st.apd[j] == sel["apd"][i]
+
+
+# ---- PSO (inertia-weight particle swarm with MOPSO personal bests) ---------
+
+def _leader(orc, p, t, o, vlist, apd):
+    _, a, b = orc.pso_picks(p, t, len(vlist), o)
+    ia, ib = vlist[a], vlist[b]
+    return ia if (apd[ia] < apd[ib] or (apd[ia] == apd[ib] and ia <= ib)) else ib
+
+
+def test_pso_picks(orc):
+    """The particle of offspring o is position o mod K; the two leader
+    candidates are distinct and, as an ordered pair, uniform (chi-square over
+    the 20 pairs of K = 5); with K = 1 the member is its own leader."""
+    p = _p(orc)
+    K, n = 5, 20000
+    counts = np.zeros((K, K))
+    for o in range(n):
+        q, a, b = orc.pso_picks(p, 2, K, o)
+        assert q == o % K and a != b and 0 <= a < K and 0 <= b < K
+        counts[a, b] += 1
+    off = counts[~np.eye(K, dtype=bool)]
+    exp = n / (K * (K - 1))
+    assert ((off - exp) ** 2 / exp).sum() < 60   # chi-square, 19 dof
+    assert orc.pso_picks(p, 3, 1, 7) == (0, 0, 0)
+
+
+def test_pso_inertia_and_still_swarm(orc):
+    """With c1 = c2 = 0 the velocity is w v exactly and the position x + w v
+    clipped; with w = 0 as well the particle stays where it is."""
+    rng = np.random.default_rng(4)
+    X = rng.uniform(size=(30, 200))
+    Vel = rng.uniform(-0.3, 0.3, size=(30, 200))
+    Pb = rng.uniform(size=(30, 200))
+    apd = rng.uniform(size=30)
+    vlist = np.arange(30)
+    p = _p(orc, N=30, d=200, pso_w=0.6, pso_c1=0.0, pso_c2=0.0)
+    Xo, Vo = orc.pso_offspring(p, 3, X, Vel, Pb, apd, vlist)
+    for o in range(30):
+        assert np.array_equal(Vo[o], 0.6 * Vel[o])
+        assert np.array_equal(Xo[o], np.clip(X[o] + 0.6 * Vel[o], 0.0, 1.0))
+    p0 = _p(orc, N=30, d=200, pso_w=0.0, pso_c1=0.0, pso_c2=0.0)
+    Xo, Vo = orc.pso_offspring(p0, 3, X, Vel, Pb, apd, vlist)
+    assert np.array_equal(Xo, X) and not Vo.any()
+
+
+@pytest.mark.parametrize("term", ["cognitive", "social"])
+def test_pso_attraction_terms(orc, term):
+    """One attraction at a time, from rest: the particle moves towards its
+    personal best (c1) or its leader (c2), the winner of the APD tournament,
+    by c r (target - x) with r uniform in [0, 1), mean 1/2, per variable."""
+    c1, c2 = (1.3, 0.0) if term == "cognitive" else (0.0, 1.3)
+    p = _p(orc, N=40, d=400, pso_w=0.0, pso_c1=c1, pso_c2=c2, L=-10.0, U=10.0)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(size=(40, 400))
+    Pb = rng.uniform(size=(40, 400))
+    apd = rng.uniform(size=40)
+    vlist = np.arange(40)
+    Xo, Vo = orc.pso_offspring(p, 6, X, np.zeros_like(X), Pb, apd, vlist)
+    fr = []
+    for o in range(40):
+        tgt = Pb[o] if term == "cognitive" else X[_leader(orc, p, 6, o, vlist, apd)]
+        span = 1.3 * (tgt - X[o])
+        assert np.allclose(Vo[o], Xo[o] - X[o], atol=1e-15)
+        ok = np.abs(span) > 1e-3
+        r = (Xo[o] - X[o])[ok] / span[ok]
+        assert (r >= -1e-12).all() and (r < 1.0).all()
+        fr.append(r)
+    fr = np.concatenate(fr)
+    assert abs(fr.mean() - 0.5) < 5 * np.sqrt(1 / 12 / fr.size)
+
+
+def test_pso_personal_best_rule(orc):
+    """The offspring's personal best is its new position unless the
+    particle's old best dominates it: dominated -> the old best (with its
+    objectives); dominating, incomparable or equal -> the new position."""
+    p = _p(orc, m=2, N=4, d=3)
+    vlist = np.arange(4)
+    Pb = np.arange(12, dtype=float).reshape(4, 3)
+    Xc = -np.arange(12, dtype=float).reshape(4, 3)
+    FPb = np.array([[1.0, 1.0], [1.0, 1.0], [1.0, 1.0], [1.0, 1.0]])
+    Fc = np.array([[2.0, 1.0],     # dominated by the old best
+                   [0.5, 1.0],     # dominates it
+                   [0.5, 2.0],     # incomparable
+                   [1.0, 1.0]])    # equal
+    Po, FPo = orc.pso_pbest(p, 1, vlist, Pb, FPb, Xc, Fc)
+    assert np.array_equal(Po[0], Pb[0]) and np.array_equal(FPo[0], FPb[0])
+    for o in (1, 2, 3):
+        assert np.array_equal(Po[o], Xc[o]) and np.array_equal(FPo[o], Fc[o])
+
+
+def test_generation_with_pso_keeps_the_swarm_state(orc):
+    """A PSO generation makes its offspring with the operator (from the
+    population, velocities, personal bests and kept APDs), and the survivors
+    carry their velocities, personal bests (with objectives) and APDs."""
+    p = orc.make_params(m=3, d=9, N=105, H=13, problem=orc.DTLZ1, t_max=20, seed=4,
+                        op=orc.OP_PSO)
+    V0, st = orc.initial_state(p)
+    assert np.array_equal(st.pbest, st.X) and np.array_equal(st.fpbest, st.F)
+    orc.generation(p, V0, st)
+    st.valid[[3, 17, 40]] = 0
+    X, Vel, Pb, FPb, apd = st.X.copy(), st.vel.copy(), st.pbest.copy(), st.fpbest.copy(), st.apd.copy()
+    vlist = np.nonzero(st.valid)[0]
+    t = st.t
+    out = orc.generation(p, V0, st)
+    want_x, want_v = orc.pso_offspring(p, t, X, Vel, Pb, apd, vlist)
+    assert np.allclose(out["Xchild"], want_x, rtol=0, atol=1e-12)
+    want_p, want_fp = orc.pso_pbest(p, t, vlist, Pb, FPb, want_x, out["Fchild"])
+    for j in range(p.N):
+        i = out["survivor"][j]
+        if i < 0:
+            continue
+        if i < p.N:
+            assert np.array_equal(st.vel[j], Vel[i]) and np.array_equal(st.pbest[j], Pb[i])
+            assert np.array_equal(st.fpbest[j], FPb[i])
+        else:
+            c = i - p.N
+            assert np.allclose(st.vel[j], want_v[c], atol=1e-12)
+            assert np.allclose(st.pbest[j], want_p[c], atol=1e-12)
+            assert np.allclose(st.fpbest[j], want_fp[c], atol=1e-12)
