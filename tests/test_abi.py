@@ -43,8 +43,12 @@ def test_library_exports_every_declared_symbol(native):
 def test_workspace_sizes(native):
     L = native.lib()
     b1 = L.rvea_workspace_bytes(3, 5000, 9870)
-    # the pool (2N rows of d floats) dominates
-    assert 2 * 9870 * 5000 * 4 <= b1 < 2 * 9870 * 5000 * 4 * 1.02
+    # the pool (2N rows of d floats) dominates; the rest is the direction
+    # grid (77284 cells of 32 bytes, 1225 blocks' shares of 2048 overflow
+    # entries of 2 bytes) and tables of O(N) or O(N m)
+    pool = 2 * 9870 * 5000 * 4
+    grid = 278 * 278 * 32 + 1225 * 2048 * 2
+    assert pool + grid <= b1 < (pool + grid) * 1.02
     assert L.rvea_workspace_bytes(1, 10, 10) == 0
     assert L.rvea_workspace_bytes(3, 2, 10) == 0
     assert L.rvea_workspace_bytes(3, 12, 40000) == 0
