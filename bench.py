@@ -43,12 +43,18 @@ WORKLOADS = {
                                         reproduction=2),
     "cso_dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000,
                                      reproduction=3, cso_phi=0.1),
+    "pso_dtlz1_m3_d5000_N9870": dict(m=3, d=5000, N=9870, H=139, problem=1, t_max=1000,
+                                     reproduction=4, pso_w=0.7298, pso_c1=1.49618,
+                                     pso_c2=1.49618),
 }
 OPS = {0: "k_repro (mating + SBX + g-terms; mutation and evaluation in k_mutate when d > 1024)",
        1: "k_repro_op (DE/rand/1/bin: four rows read, one child row written, evaluation)",
        2: "k_repro_op (random reproduction: one child row written, evaluation)",
-       3: "k_cso_mean + k_repro_op (CSO: swarm centre over the valid rows; winner, loser and "
-          "loser velocity rows read, child row and velocity written; evaluation)"}
+       3: "k_cso_mean + k_cso_centre + k_repro_cso (CSO: swarm centre over the valid rows; "
+          "winner, loser and loser velocity rows read, child row and velocity written; "
+          "evaluation)",
+       4: "k_repro_pso (PSO: particle, its velocity and personal best, leader rows read; child "
+          "row, velocity and personal best written; evaluation)"}
 COMMON = dict(alpha=2.0, f_r=0.1, eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
 
 
@@ -76,7 +82,9 @@ def repro_bytes(wl) -> int:
     per offspring.  Random: write N rows.  CSO: read the winner's and loser's
     rows and the loser's velocity, write the child's row and velocity, per
     offspring, plus (phi > 0) one pass over the valid rows for the centre,
-    counted as N rows (all slots valid)."""
+    counted as N rows (all slots valid).  PSO: read the particle's row,
+    velocity and personal best and the leader's row, write the child's row,
+    velocity and personal best, per offspring."""
     N, d, op = wl["N"], wl["d"], wl.get("reproduction", 0)
     if op == 1:
         return 5 * N * d * 4
@@ -84,6 +92,8 @@ def repro_bytes(wl) -> int:
         return N * d * 4
     if op == 3:
         return (5 + (1 if wl.get("cso_phi", 0.0) > 0 else 0)) * N * d * 4
+    if op == 4:
+        return 7 * N * d * 4
     P = (N + 1) // 2
     return (2 * P + N) * d * 4
 
@@ -93,7 +103,8 @@ def oracle_params(orc, wl, seed=0):
     extra = {}
     if wl.get("reproduction", 0):
         extra = dict(op=wl["reproduction"], de_F=wl.get("de_F", 0.5), de_CR=wl.get("de_CR", 0.9),
-                     cso_phi=wl.get("cso_phi", 0.0))
+                     cso_phi=wl.get("cso_phi", 0.0), pso_w=wl.get("pso_w", 0.7298),
+                     pso_c1=wl.get("pso_c1", 1.49618), pso_c2=wl.get("pso_c2", 1.49618))
     return orc.make_params(m=wl["m"], d=wl["d"], N=wl["N"], H=wl["H"], problem=wl["problem"],
                            t_max=wl["t_max"], seed=seed, **COMMON, **extra)
 

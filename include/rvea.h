@@ -106,6 +106,9 @@ typedef struct {
     double de_F;      /* DE/rand/1/bin scale factor, (0, 2]                  */
     double de_CR;     /* DE/rand/1/bin crossover rate, [0, 1]                */
     double cso_phi;   /* CSO: weight of the swarm-centre term, [0, 1]        */
+    double pso_w;     /* PSO: inertia weight, [0, 1] (0.7298 is Clerc's)     */
+    double pso_c1;    /* PSO: cognitive weight, [0, 4] (1.49618)             */
+    double pso_c2;    /* PSO: social weight, [0, 4] (1.49618)                */
 } rvea_config;
 
 /* Reproduction operators (Sec. 4.4, the extensibility experiment: the same
@@ -124,12 +127,23 @@ typedef struct {
  * phi r3 (xbar - x_l), x' = clip(x_l + v'), with r1..r3 uniform per
  * variable and xbar the mean position of the valid members.  Velocities
  * (zero at first) and kept APDs (+inf before the first selection) stay
- * with the survivors.  DTLZ problems only. */
+ * with the survivors.  RVEA_REPRO_PSO is particle swarm optimization
+ * (Kennedy and Eberhart 1995, Shi and Eberhart's inertia weight), also named
+ * by the paper and not printed; read here after the multiobjective PSO of
+ * Coello, Pulido and Lechuga (2004), the population taking the archive's
+ * role: particle o is the member at position o mod K of the valid list, its
+ * leader g the winner of an APD tournament between two distinct valid
+ * members, v' = w v + c1 r1 (p - x) + c2 r2 (g - x), x' = clip(x + v');
+ * the offspring's personal best p is x' unless the particle's personal best
+ * dominates f(x') (then that best is kept).  Velocities (zero at first),
+ * personal bests (the initial positions at first), their objectives and the
+ * kept APDs stay with the survivors.  DTLZ problems only. */
 typedef enum {
     RVEA_REPRO_SBX_PM = 0,
     RVEA_REPRO_DE = 1,
     RVEA_REPRO_RANDOM = 2,
-    RVEA_REPRO_CSO = 3
+    RVEA_REPRO_CSO = 3,
+    RVEA_REPRO_PSO = 4
 } rvea_reproduction;
 
 /* Lattice divisions H for a requested population size n that need not be a
@@ -339,22 +353,26 @@ rvea_status rvea_import_state(rvea_run *run, const float *X, const float *F,
                               const uint8_t *valid, const double *V,
                               const double *gamma, int t, void *cuda_stream);
 
-/* Swarm state of a run reproduced by CSO (RVEA_REPRO_CSO), in vector-slot
- * order like rvea_export_state: vel (N x d f32, the velocity of each slot's
- * member; NaN rows for invalid slots) and apd (N f32, the APD of Eq. 4 with
- * which the last selection kept the member; +inf before any selection and
- * for invalid slots).  Either may be NULL.  Device or pinned host memory
+/* Swarm state of a run reproduced by CSO or PSO, in vector-slot order like
+ * rvea_export_state: vel (N x d f32, the velocity of each slot's member),
+ * apd (N f32, the APD of Eq. 4 with which the last selection kept the
+ * member; +inf before any selection), and for PSO pbest (N x d f32, the
+ * member's personal best) and fpbest (N x m f32, its objectives); NaN rows
+ * and +inf for invalid slots.  Any may be NULL.  Device or pinned host memory
  * only (RVEA_ERR_ARG otherwise); RVEA_ERR_STATE for a run of another
- * operator.  Asynchronous on `cuda_stream`. */
-rvea_status rvea_export_swarm(const rvea_run *run, float *vel, float *apd, void *cuda_stream);
+ * operator, or for pbest / fpbest of a CSO run.  Asynchronous on
+ * `cuda_stream`. */
+rvea_status rvea_export_swarm(const rvea_run *run, float *vel, float *apd, float *pbest,
+                              float *fpbest, void *cuda_stream);
 
-/* Replace the swarm state of a CSO run (same layouts as rvea_export_swarm,
- * both required; a pointer to device or host memory).  Call it after
- * rvea_import_state, which resets velocities to zero and kept APDs to +inf
- * (the state of a new swarm).  Synchronises `cuda_stream`.  RVEA_ERR_STATE
- * for a run of another operator. */
+/* Replace the swarm state of a CSO or PSO run (same layouts as
+ * rvea_export_swarm; vel and apd required, pbest and fpbest required for PSO
+ * and ignored for CSO; device or host memory).  Call it after
+ * rvea_import_state, which starts a new swarm: velocities zero, kept APDs
+ * +inf, personal bests the imported positions and objectives.  Synchronises
+ * `cuda_stream`.  RVEA_ERR_STATE for a run of another operator. */
 rvea_status rvea_import_swarm(rvea_run *run, const float *vel, const float *apd,
-                              void *cuda_stream);
+                              const float *pbest, const float *fpbest, void *cuda_stream);
 
 /* Offspring of the last completed generation, in child order c = 0..N-1
  * (c < ceil(N/2): first child of pair c; otherwise second child of pair

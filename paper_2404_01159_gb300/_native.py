@@ -18,7 +18,7 @@ _lib = None
 OK, ERR_ARG, ERR_LATTICE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 DTLZ2_SPHERE, DTLZ1_LINEAR, NEURO_LINEAR, DTLZ3_SPHERE, DTLZ4_SPHERE = 0, 1, 2, 3, 4
-REPRO_SBX_PM, REPRO_DE, REPRO_RANDOM, REPRO_CSO = 0, 1, 2, 3
+REPRO_SBX_PM, REPRO_DE, REPRO_RANDOM, REPRO_CSO, REPRO_PSO = 0, 1, 2, 3, 4
 
 
 class NeuroDynamics(C.Structure):
@@ -35,7 +35,8 @@ class Config(C.Structure):
                 ("eta_m", C.c_double), ("p_c", C.c_double), ("p_m", C.c_double),
                 ("lower", C.c_double), ("upper", C.c_double), ("seed", C.c_uint64),
                 ("neuro", C.POINTER(NeuroDynamics)), ("reproduction", C.c_int),
-                ("de_F", C.c_double), ("de_CR", C.c_double), ("cso_phi", C.c_double)]
+                ("de_F", C.c_double), ("de_CR", C.c_double), ("cso_phi", C.c_double),
+                ("pso_w", C.c_double), ("pso_c1", C.c_double), ("pso_c2", C.c_double)]
 
 
 class Plan(C.Structure):
@@ -125,9 +126,9 @@ def lib():
         L.rvea_import_state.restype = i32
         L.rvea_offspring.argtypes = [vp, vp, vp, vp]
         L.rvea_offspring.restype = i32
-        L.rvea_export_swarm.argtypes = [vp, vp, vp, vp]
+        L.rvea_export_swarm.argtypes = [vp, vp, vp, vp, vp, vp]
         L.rvea_export_swarm.restype = i32
-        L.rvea_import_swarm.argtypes = [vp, vp, vp, vp]
+        L.rvea_import_swarm.argtypes = [vp, vp, vp, vp, vp, vp]
         L.rvea_import_swarm.restype = i32
         L.rvea_last_selection.argtypes = [vp, vp, vp, vp]
         L.rvea_last_selection.restype = i32

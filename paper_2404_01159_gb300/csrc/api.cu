@@ -65,6 +65,10 @@ __global__ void k_repro_cso_dtlz1(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz3(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz4(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_pso_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_pso_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_pso_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_pso_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_select(const __grid_constant__ BatchDir dir);
 __global__ void k_finalize(const __grid_constant__ BatchDir dir);
 __global__ void k_gamma(const __grid_constant__ BatchDir dir, int force);
@@ -73,7 +77,7 @@ __global__ void k_init_lists(const __grid_constant__ BatchDir dir);
 __global__ void k_gather_pop(const RunDesc *Rp, float *dst, uint8_t *valid);
 __global__ void k_gather_obj(const RunDesc *Rp, float *dst, uint8_t *valid);
 __global__ void k_gather_children(const RunDesc *Rp, float *X, float *F);
-__global__ void k_gather_swarm(const RunDesc *Rp, float *vel, float *apd);
+__global__ void k_gather_swarm(const RunDesc *Rp, float *vel, float *apd, float *pbest, float *fpbest);
 __global__ void k_copy_selection(const RunDesc *Rp, int *assoc, int *surv);
 __global__ void k_import(const RunDesc *Rp, const float *Fin, const uint8_t *vin, int t);
 __global__ void k_igd_partial(const RunDesc *Rp, const float *ref, int n_ref, double *partial);
@@ -194,11 +198,13 @@ struct Layout {
   size_t X, F, slotmap, vbits, obits, zpart, vlist, child, best, amax, assoc, surv, blk, V32, V32lo, V64, V0, g64, g32,
       ctl, desc, repro, init, sel, stage, psum, rec_par, rec_sites, otag, occ_cnt, vcnt, zacc, Vt,
       tperm, trng, tcen, tcs, gcell, gcnt, gblk, gover, selb, gscale, vrange, fcomb, noise, dynA, dynB,
-      vel, kapd, xbar, xpart, total;
+      vel, kapd, xbar, xpart, pb, fpb, total;
 };
 
-// swarm: the run uses the CSO operator (velocities, kept APDs, the centre)
-Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max, bool swarm = false) {
+// op: the run's reproduction operator; CSO (3) and PSO (4) keep velocities
+// and kept APDs, CSO its centre, PSO the personal bests
+Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max, int op = 0) {
+  const bool swarm = op == 3 || op == 4;
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -258,8 +264,10 @@ Layout make_layout(const Shape &s, int steps_max, int ns_max, int na_max, bool s
   const size_t nch = (size_t)(s.N + kMeanRows - 1) / kMeanRows;
   L.vel = take(swarm ? (size_t)2 * s.N * s.d_pad * sizeof(float) : 0);
   L.kapd = take(swarm ? (size_t)s.N * 4 : 0);
-  L.xbar = take(swarm ? (size_t)s.d_pad * 4 : 0);
-  L.xpart = take(swarm ? nch * s.d_pad * 4 : 0);
+  L.xbar = take(op == 3 ? (size_t)s.d_pad * 4 : 0);
+  L.xpart = take(op == 3 ? nch * s.d_pad * 4 : 0);
+  L.pb = take(op == 4 ? (size_t)2 * s.N * s.d_pad * sizeof(float) : 0);
+  L.fpb = take(op == 4 ? (size_t)s.m * s.n_comb * sizeof(float) : 0);
   L.total = o;
   return L;
 }
@@ -609,8 +617,17 @@ void launch_rollouts(rvea_run *const *runs, int n, cudaStream_t st, int init, bo
 // operator is not SBX): one kernel per (problem, CSO or not) over a
 // directory of such runs, one warp per offspring.
 constexpr int kOpWarps = kReproThreads / 32;
-void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st, bool cso) {
-  if (cso) {
+void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st, int op) {
+  if (op == 4) {
+    switch (problem) {
+      case PROB_DTLZ1: launch_pdl(k_repro_pso_dtlz1, grid, kReproThreads, 0, st, d); break;
+      case PROB_DTLZ3: launch_pdl(k_repro_pso_dtlz3, grid, kReproThreads, 0, st, d); break;
+      case PROB_DTLZ4: launch_pdl(k_repro_pso_dtlz4, grid, kReproThreads, 0, st, d); break;
+      default: launch_pdl(k_repro_pso_dtlz2, grid, kReproThreads, 0, st, d); break;
+    }
+    return;
+  }
+  if (op == 3) {
     switch (problem) {
       case PROB_DTLZ1: launch_pdl(k_repro_cso_dtlz1, grid, kReproThreads, 0, st, d); break;
       case PROB_DTLZ3: launch_pdl(k_repro_cso_dtlz3, grid, kReproThreads, 0, st, d); break;
@@ -660,7 +677,7 @@ void launch_repro_op1(const rvea_run *r, cudaStream_t st) {
   launch_cso_means(one, 1, st);
   const int nb = (r->sh.N + kOpWarps - 1) / kOpWarps;
   dir_single(d, r, nullptr, nb);
-  launch_repro_op(d, r->hd.problem, nb, st, r->hd.op == 3);
+  launch_repro_op(d, r->hd.problem, nb, st, r->hd.op);
 }
 
 // Mutation and evaluation of the children of a run reproduced by 32-lane
@@ -785,14 +802,15 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     // one launch per (problem, load path) group, each with its own directory
     int pg[2 * kProblems] = {};
     for (int g = 0; g < 2 * kProblems; ++g) dg[g].n = 0;
-    // the runs with another operator: one launch per (problem, CSO or not)
-    static thread_local BatchDir dop[2 * kProblems];
-    int pop[2 * kProblems] = {};
-    for (int g = 0; g < 2 * kProblems; ++g) dop[g].n = 0;
+    // the runs with another operator: one launch per (problem, kernel: DE
+    // and random, CSO, PSO)
+    static thread_local BatchDir dop[3 * kProblems];
+    int pop[3 * kProblems] = {};
+    for (int g = 0; g < 3 * kProblems; ++g) dop[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
       if (r->hd.op == 0) continue;
-      const int g = 2 * r->hd.problem + (r->hd.op == 3 ? 1 : 0);
+      const int g = 3 * r->hd.problem + (r->hd.op == 3 ? 1 : r->hd.op == 4 ? 2 : 0);
       BatchDir &D = dop[g];
       D.prefix[D.n] = pop[g];
       D.desc[D.n] = r->d_desc;
@@ -802,10 +820,10 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       ++D.n;
     }
     launch_cso_means(runs, n, st);
-    for (int g = 0; g < 2 * kProblems; ++g) {
+    for (int g = 0; g < 3 * kProblems; ++g) {
       if (dop[g].n == 0) continue;
       dop[g].prefix[dop[g].n] = pop[g];
-      launch_repro_op(dop[g], g / 2, pop[g], st, (g & 1) != 0);
+      launch_repro_op(dop[g], g / 3, pop[g], st, g % 3 == 1 ? 3 : g % 3 == 2 ? 4 : 1);
     }
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
@@ -996,12 +1014,15 @@ rvea_status validate(const rvea_config *c) {
   if (c->problem != PROB_NEURO && (c->lower != 0.0 || c->upper != 1.0)) return RVEA_ERR_ARG;
   if (c->problem < 0 || c->problem >= kProblems) return RVEA_ERR_ARG;
   // the other reproduction operators (DTLZ problems)
-  if (c->reproduction < 0 || c->reproduction > 3) return RVEA_ERR_ARG;
+  if (c->reproduction < 0 || c->reproduction > 4) return RVEA_ERR_ARG;
   if (c->reproduction != 0 && c->problem == PROB_NEURO) return RVEA_ERR_ARG;
   if (c->reproduction == 1 &&
       (!(c->de_F > 0) || c->de_F > 2 || !(c->de_CR >= 0) || c->de_CR > 1))
     return RVEA_ERR_ARG;
   if (c->reproduction == 3 && (!(c->cso_phi >= 0) || c->cso_phi > 1)) return RVEA_ERR_ARG;
+  if (c->reproduction == 4 && (!(c->pso_w >= 0) || c->pso_w > 1 || !(c->pso_c1 >= 0) ||
+                               c->pso_c1 > 4 || !(c->pso_c2 >= 0) || c->pso_c2 > 4))
+    return RVEA_ERR_ARG;
   if (c->problem == RVEA_NEURO_LINEAR) {
     // the rollout's shape: h1 = h2 = 64 (the tensor-core tiling), ns <= 32
     // (one lane per state component), na <= 16 (one 16-row tile), and d the
@@ -1032,7 +1053,7 @@ size_t rvea_workspace_bytes_ex(const rvea_config *cfg) {
   const Shape s = make_shape(cfg->m, cfg->d, cfg->N);
   const rvea_neuro_dynamics *nd = cfg->problem == RVEA_NEURO_LINEAR ? cfg->neuro : nullptr;
   return make_layout(s, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0,
-                     cfg->reproduction == 3).total;
+                     cfg->reproduction).total;
 }
 
 int rvea_lattice_for(int m, int n) {
@@ -1078,7 +1099,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   const Shape sh = make_shape(cfg->m, cfg->d, cfg->N);
   const rvea_neuro_dynamics *nd = cfg->problem == RVEA_NEURO_LINEAR ? cfg->neuro : nullptr;
   const Layout lay = make_layout(sh, nd ? nd->steps : 0, nd ? nd->ns : 0, nd ? nd->na : 0,
-                                 cfg->reproduction == 3);
+                                 cfg->reproduction);
   if (bytes < lay.total) return RVEA_ERR_NOMEM;
   std::call_once(g_attr_once, set_kernel_attrs);
   if (g_attr_err != cudaSuccess) return RVEA_ERR_CUDA;
@@ -1113,6 +1134,9 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.de_F = (float)cfg->de_F;
   D.T_cr = event_threshold24(cfg->de_CR);
   D.cso_phi = (float)cfg->cso_phi;
+  D.pso_w = (float)cfg->pso_w;
+  D.pso_c1 = (float)cfg->pso_c1;
+  D.pso_c2 = (float)cfg->pso_c2;
   if (D.T_m > 0u && D.T_m < (1u << 24))
     D.n_mthr = site_count_thresholds((double)D.T_m / 16777216.0, sh.d, D.mthr);
   D.key0 = (uint32_t)cfg->seed;
@@ -1164,11 +1188,17 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   D.gscale = wsp<float>(r, lay.gscale);
   D.vrange = wsp<double>(r, lay.vrange);
   D.fcomb = wsp<float>(r, lay.fcomb);
-  if (cfg->reproduction == 3) {   // the swarm state (velocities zero from the clear below)
-    D.vel = wsp<float>(r, lay.vel);
+  if (cfg->reproduction == 3 || cfg->reproduction == 4) {   // the swarm state (velocities
+    D.vel = wsp<float>(r, lay.vel);                             // zero from the clear below)
     D.kapd = wsp<float>(r, lay.kapd);
+  }
+  if (cfg->reproduction == 3) {
     D.xbar = wsp<float>(r, lay.xbar);
     D.xpart = wsp<float>(r, lay.xpart);
+  }
+  if (cfg->reproduction == 4) {   // personal bests: the initial positions (copied below)
+    D.pb = wsp<float>(r, lay.pb);
+    D.fpb = wsp<float>(r, lay.fpb);
   }
   r->d_desc = wsp<RunDesc>(r, lay.desc);
 
@@ -1245,7 +1275,7 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
   const std::vector<double> ones(kMaxM, 1.0);
   up(lay.vrange, ones.data(), kMaxM * 8);
   std::vector<float> kinf;
-  if (cfg->reproduction == 3) {   // no selection has kept a member yet
+  if (cfg->reproduction == 3 || cfg->reproduction == 4) {   // no selection has kept a member yet
     kinf.assign(sh.N, std::numeric_limits<float>::infinity());
     up(lay.kapd, kinf.data(), kinf.size() * 4);
   }
@@ -1270,6 +1300,11 @@ rvea_status rvea_init_ex(const rvea_config *cfg, void *dev_workspace, size_t byt
     dir_single(d, r, nullptr, 1);
     k_init_lists<<<dim3((sh.N + 255) / 256, 1), 256, 0, st>>>(d);
     s = cuerr(cudaGetLastError());
+    if (s == RVEA_OK && D.pb) {   // PSO: each member's personal best is where it starts
+      s = cuerr(cudaMemcpyAsync(D.pb, D.X, (size_t)sh.N * sh.d_pad * 4, cudaMemcpyDeviceToDevice, st));
+      if (s == RVEA_OK)
+        s = cuerr(cudaMemcpyAsync(D.fpb, D.F, (size_t)sh.m * sh.n_comb * 4, cudaMemcpyDeviceToDevice, st));
+    }
     if (s == RVEA_OK) s = launch_tiles(r, st);
     if (s == RVEA_OK) s = launch_gamma_force(r, st);
   }
@@ -1889,10 +1924,15 @@ rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const
   RV_TRY(cudaMemcpyAsync(sv, valid, sh.N, cudaMemcpyDefault, st));
   RV_TRY(cudaMemcpyAsync(r->hd.V64, V, (size_t)sh.N * sh.m * 8, cudaMemcpyDefault, st));
   RV_TRY(cudaMemcpyAsync(r->hd.gamma64, gamma, (size_t)sh.N * 8, cudaMemcpyDefault, st));
-  // CSO: a new swarm (velocities zero; k_import sets the kept APDs to +inf)
+  // CSO, PSO: a new swarm (velocities zero; k_import sets the kept APDs to
+  // +inf; personal bests where the members are)
   if (r->hd.vel) RV_TRY(cudaMemsetAsync(r->hd.vel, 0, (size_t)sh.N * sh.d_pad * 4, st));
   k_import<<<1, kFinThreads, 0, st>>>(r->d_desc, sf, sv, t);
   RV_TRY(cudaGetLastError());
+  if (r->hd.pb) {
+    RV_TRY(cudaMemcpyAsync(r->hd.pb, r->hd.X, (size_t)sh.N * sh.d_pad * 4, cudaMemcpyDeviceToDevice, st));
+    RV_TRY(cudaMemcpyAsync(r->hd.fpb, r->hd.F, (size_t)sh.m * sh.n_comb * 4, cudaMemcpyDeviceToDevice, st));
+  }
   if (launch_tiles(r, st) != RVEA_OK) return RVEA_ERR_CUDA;
   RV_TRY(cudaStreamSynchronize(st));
   r->t = t;
@@ -1901,27 +1941,43 @@ rvea_status rvea_import_state(rvea_run *r, const float *X, const float *F, const
   return RVEA_OK;
 }
 
-rvea_status rvea_export_swarm(const rvea_run *r, float *vel, float *apd, void *cuda_stream) {
+rvea_status rvea_export_swarm(const rvea_run *r, float *vel, float *apd, float *pbest,
+                              float *fpbest, void *cuda_stream) {
   if (!r) return RVEA_ERR_ARG;
   if (!r->hd.vel) return RVEA_ERR_STATE;
+  if ((pbest || fpbest) && !r->hd.pb) return RVEA_ERR_STATE;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   float *dv = static_cast<float *>(dev_addr(vel));
   float *da = static_cast<float *>(dev_addr(apd));
-  if ((vel && !dv) || (apd && !da)) return RVEA_ERR_ARG;   // device or pinned memory only
-  if (!vel && !apd) return RVEA_OK;
-  k_gather_swarm<<<r->sh.N, 256, 0, st>>>(r->d_desc, dv, da);
+  float *dp = static_cast<float *>(dev_addr(pbest));
+  float *df = static_cast<float *>(dev_addr(fpbest));
+  if ((vel && !dv) || (apd && !da) || (pbest && !dp) || (fpbest && !df))
+    return RVEA_ERR_ARG;   // device or pinned memory only
+  if (!vel && !apd && !pbest && !fpbest) return RVEA_OK;
+  k_gather_swarm<<<r->sh.N, 256, 0, st>>>(r->d_desc, dv, da, dp, df);
   return cuerr(cudaGetLastError());
 }
 
-rvea_status rvea_import_swarm(rvea_run *r, const float *vel, const float *apd, void *cuda_stream) {
+rvea_status rvea_import_swarm(rvea_run *r, const float *vel, const float *apd, const float *pbest,
+                              const float *fpbest, void *cuda_stream) {
   if (!r || !vel || !apd) return RVEA_ERR_ARG;
   if (!r->hd.vel) return RVEA_ERR_STATE;
+  if (r->hd.pb && (!pbest || !fpbest)) return RVEA_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const Shape &sh = r->sh;
   // slot j's member sits in pool row j after rvea_import_state
   RV_TRY(cudaMemcpy2DAsync(r->hd.vel, (size_t)sh.d_pad * 4, vel, (size_t)sh.d * 4, (size_t)sh.d * 4,
                            sh.N, cudaMemcpyDefault, st));
   RV_TRY(cudaMemcpyAsync(r->hd.kapd, apd, (size_t)sh.N * 4, cudaMemcpyDefault, st));
+  if (r->hd.pb) {
+    RV_TRY(cudaMemcpy2DAsync(r->hd.pb, (size_t)sh.d_pad * 4, pbest, (size_t)sh.d * 4,
+                             (size_t)sh.d * 4, sh.N, cudaMemcpyDefault, st));
+    // objectives N x m (by slot) into the m x 2N table: objective k of slot j
+    // (pool row j) at k 2N + j, one strided copy per objective
+    for (int k = 0; k < sh.m; ++k)
+      RV_TRY(cudaMemcpy2DAsync(r->hd.fpb + (size_t)k * sh.n_comb, 4, fpbest + k, (size_t)sh.m * 4, 4,
+                               sh.N, cudaMemcpyDefault, st));
+  }
   RV_TRY(cudaStreamSynchronize(st));
   r->last_stream = st;
   return RVEA_OK;

@@ -592,17 +592,25 @@ __global__ void k_gather_children(const RunDesc *__restrict__ Rp, float *X, floa
   if (F && threadIdx.x < R.m) F[(size_t)c * R.m + threadIdx.x] = R.F[(size_t)threadIdx.x * R.n_comb + s];
 }
 
-// Swarm state of a CSO run in vector-slot order: each valid slot's velocity
-// row and kept APD (NaN rows and +inf for invalid slots).  One CTA per slot.
-__global__ void k_gather_swarm(const RunDesc *__restrict__ Rp, float *vel, float *apd) {
+// Swarm state of a CSO or PSO run in vector-slot order: each valid slot's
+// velocity row, kept APD and (PSO) personal-best row and objectives (NaN and
+// +inf for invalid slots).  One CTA per slot.
+__global__ void k_gather_swarm(const RunDesc *__restrict__ Rp, float *vel, float *apd, float *pbest,
+                               float *fpbest) {
   const RunDesc &R = *Rp;
   const int j = blockIdx.x;
   const int s = R.slotmap[(R.ctl->t & 1) * R.N + j];
+  const float qnan = __int_as_float(0x7fc00000);
   if (vel) {
     const float *v = s >= 0 ? R.vel + (size_t)s * R.d_pad : nullptr;
-    for (int k = threadIdx.x; k < R.d; k += blockDim.x)
-      vel[(size_t)j * R.d + k] = v ? v[k] : __int_as_float(0x7fc00000);
+    for (int k = threadIdx.x; k < R.d; k += blockDim.x) vel[(size_t)j * R.d + k] = v ? v[k] : qnan;
   }
+  if (pbest) {
+    const float *p = s >= 0 ? R.pb + (size_t)s * R.d_pad : nullptr;
+    for (int k = threadIdx.x; k < R.d; k += blockDim.x) pbest[(size_t)j * R.d + k] = p ? p[k] : qnan;
+  }
+  if (fpbest && threadIdx.x < R.m)
+    fpbest[(size_t)j * R.m + threadIdx.x] = s >= 0 ? R.fpb[(size_t)threadIdx.x * R.n_comb + s] : qnan;
   if (apd && threadIdx.x == 0) apd[j] = s >= 0 ? R.kapd[j] : __int_as_float(0x7f800000);
 }
 

@@ -606,7 +606,8 @@ RVEA_MUTATE(k_mutate_neuro, PROB_NEURO)
 //       j = j_rand, else the target's x_j; clipped to [L, U];
 //   random: x_j = L + (U - L) u24, RANDOM (j/4, o, t) word j%4.
 // Then the g-terms, objectives and the ideal point, as the other kernels.
-enum : uint32_t { TAG_DE_PICK = 8, TAG_DE_CR = 9, TAG_RANDOM = 10, TAG_CSO_PICK = 11, TAG_CSO_R = 12 };
+enum : uint32_t { TAG_DE_PICK = 8, TAG_DE_CR = 9, TAG_RANDOM = 10, TAG_CSO_PICK = 11, TAG_CSO_R = 12,
+                  TAG_PSO_PICK = 13, TAG_PSO_R = 14 };
 
 __device__ __forceinline__ int de_pos(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
 
@@ -949,6 +950,165 @@ RVEA_REPRO_CSO(k_repro_cso_dtlz2, PROB_DTLZ2)
 RVEA_REPRO_CSO(k_repro_cso_dtlz3, PROB_DTLZ3)
 RVEA_REPRO_CSO(k_repro_cso_dtlz4, PROB_DTLZ4)
 #undef RVEA_REPRO_CSO
+
+// Reproduction by particle swarm optimization (PSO; Kennedy and Eberhart
+// 1995, the inertia weight of Shi and Eberhart 1998, the personal-best rule
+// of the multiobjective PSO of Coello, Pulido and Lechuga 2004).  One warp
+// per offspring o: the particle is the member at position o mod K of the
+// valid list, its leader the winner of a binary tournament on the kept APD
+// between two distinct valid members (PSO_PICK (o, 0, t) words 0 and 1; ties:
+// the smaller slot), and it moves
+//   v' = w v + c1 r1 (p - x) + c2 r2 (g - x),   x' = clip(x + v'),
+// r1, r2 of variable j from word j%4 of PSO_R (2 (j/4) + k, o, t), k = 0, 1.
+// (x', v') goes to the child's pool row and velocity row, and x' to its
+// personal-best row; after the evaluation, when the particle's personal
+// best dominates f(x') (no worse in every objective, better in one), the
+// warp copies that best (row and objectives) over the child's instead.
+template <int PROB>
+__device__ __forceinline__ void repro_pso_body(const BatchDir &dir) {
+  __shared__ unsigned s_z[kMaxM];
+  pdl_wait();      // the previous generation's lists, slot maps and kept APDs
+  pdl_trigger();
+  const int run = dir_find(dir, blockIdx.x);
+  const RunDesc &R = *dir.desc[run];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o = (blockIdx.x - dir.prefix[run]) * (kReproThreads / 32) + warp;
+  const int N = R.N, d = R.d, m = R.m, t = R.ctl->t, K = R.ctl->K, n2 = 2 * N;
+  const KeyRun kr{dir.key[run].x, dir.key[run].y};
+  if (threadIdx.x < kMaxM) s_z[threadIdx.x] = 0xFFFFFFFFu;
+  __syncthreads();
+  float f[kMaxM];
+  bool have = false;
+  if (o < N) {
+    int slot = R.child_slot[(t & 1) * N + o];
+    if (slot < 0 || slot >= n2) { set_status(R.ctl, ST_BADINDEX); slot = -1; }
+    int rp = 0, rg = 0;   // pool rows of the particle and its leader
+    if (lane == 0 && K > 0) {
+      const uint4 w = philox_k((uint32_t)o, 0u, (uint32_t)t, TAG_PSO_PICK, kr);
+      const int a = de_pos(w.x, K);
+      int bq = a;
+      if (K > 1) {
+        bq = de_pos(w.y, K - 1);
+        if (bq >= a) bq += 1;
+      }
+      int ip = R.vlist[o % K], ia = R.vlist[a], ib = R.vlist[bq];
+      if (ip < 0 || ip >= N || ia < 0 || ia >= N || ib < 0 || ib >= N) {
+        set_status(R.ctl, ST_BADINDEX);
+        ip = ia = ib = 0;
+      }
+      const float pa = R.kapd[ia], pbv = R.kapd[ib];
+      const int ig = (pa < pbv || (pa == pbv && ia <= ib)) ? ia : ib;
+      rp = R.slotmap[(t & 1) * N + ip];
+      rg = R.slotmap[(t & 1) * N + ig];
+      if (rp < 0 || rp >= n2 || rg < 0 || rg >= n2) { set_status(R.ctl, ST_BADINDEX); rp = rg = 0; }
+    }
+    rp = __shfl_sync(0xffffffffu, rp, 0);
+    rg = __shfl_sync(0xffffffffu, rg, 0);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    float2 acc = make_float2(0.f, 0.f);
+    if (slot >= 0) {
+      const float L = R.L, U = R.U, w = R.pso_w, c1 = R.pso_c1, c2 = R.pso_c2;
+      const int mh = m - 1, rq = R.d_pad >> 2;
+      const float4 *X4 = reinterpret_cast<const float4 *>(R.X);
+      const float4 *XP = X4 + (size_t)rp * rq, *XG = X4 + (size_t)rg * rq;
+      const float4 *VP = reinterpret_cast<const float4 *>(R.vel) + (size_t)rp * rq;
+      const float4 *PP = reinterpret_cast<const float4 *>(R.pb) + (size_t)rp * rq;
+      float4 *Y4 = reinterpret_cast<float4 *>(R.X + (size_t)slot * R.d_pad);
+      float4 *VY = reinterpret_cast<float4 *>(R.vel + (size_t)slot * R.d_pad);
+      float4 *PY = reinterpret_cast<float4 *>(R.pb + (size_t)slot * R.d_pad);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 cx = z4, cv = z4, cp = z4, cg = z4;
+      if (lane < rq) {
+        cx = __ldg(XP + lane);
+        cv = __ldg(VP + lane);
+        cp = __ldg(PP + lane);
+        cg = __ldg(XG + lane);
+      }
+      for (int Q = lane; Q < rq; Q += 32) {
+        float4 nx = z4, nv = z4, np = z4, ng = z4;
+        if (Q + 32 < rq) {
+          nx = __ldg(XP + Q + 32);
+          nv = __ldg(VP + Q + 32);
+          np = __ldg(PP + Q + 32);
+          ng = __ldg(XG + Q + 32);
+        }
+        const float ax[4] = {cx.x, cx.y, cx.z, cx.w}, av[4] = {cv.x, cv.y, cv.z, cv.w};
+        const float ap[4] = {cp.x, cp.y, cp.z, cp.w}, ag[4] = {cg.x, cg.y, cg.z, cg.w};
+        float vv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) vv[v] = w * av[v];
+        {
+          const uint4 r = philox_k(2u * (uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_PSO_R, kr);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) vv[v] = fmaf(c1 * u24f(word(r, v)), ap[v] - ax[v], vv[v]);
+        }
+        {
+          const uint4 r = philox_k(2u * (uint32_t)Q + 1u, (uint32_t)o, (uint32_t)t, TAG_PSO_R, kr);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) vv[v] = fmaf(c2 * u24f(word(r, v)), ag[v] - ax[v], vv[v]);
+        }
+        float u[4], nvel[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int j = 4 * Q + v;
+          if (j >= d) {   // row padding: a g-term of exactly zero, no velocity
+            u[v] = 0.5f;
+            nvel[v] = 0.0f;
+          } else {
+            u[v] = clampf(ax[v] + vv[v], L, U);
+            nvel[v] = vv[v];
+            if (j >= mh) {
+              if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
+              else acc.x = g_term1(PROB, u[v], acc.x);
+            }
+          }
+        }
+        const float4 xo = make_float4(u[0], u[1], u[2], u[3]);
+        Y4[Q] = xo;
+        __stcs(VY + Q, make_float4(nvel[0], nvel[1], nvel[2], nvel[3]));
+        PY[Q] = xo;
+        cx = nx; cv = nv; cp = np; cg = ng;
+      }
+      const float2 gs = team_sum2(acc, 32);
+      __syncwarp();   // the row is visible to lane 0
+      int keep_old = 0;
+      if (lane == 0) {
+        float head[kMaxM];
+        const float *row = R.X + (size_t)slot * R.d_pad;
+        for (int jj = 0; jj < mh; ++jj) head[jj] = __ldcg(row + jj);
+        dtlz_objectives_t<PROB>(m, gs.x + gs.y, head, f);
+        bool le = true, lt = false;
+        for (int kk = 0; kk < m; ++kk) {
+          R.F[(size_t)kk * n2 + slot] = f[kk];
+          const float fp = R.fpb[(size_t)kk * n2 + rp];
+          le = le && fp <= f[kk];
+          lt = lt || fp < f[kk];
+        }
+        keep_old = le && lt;
+        for (int kk = 0; kk < m; ++kk)
+          R.fpb[(size_t)kk * n2 + slot] = keep_old ? R.fpb[(size_t)kk * n2 + rp] : f[kk];
+        have = true;
+      }
+      keep_old = __shfl_sync(0xffffffffu, keep_old, 0);
+      if (keep_old)   // the particle's best stays its best: over the child's best row
+        for (int Q = lane; Q < rq; Q += 32) PY[Q] = __ldg(PP + Q);
+    }
+  }
+  if (have)
+    for (int kk = 0; kk < m; ++kk) atomicMin(&s_z[kk], f2ord(f[kk]));
+  __syncthreads();
+  if (threadIdx.x < m && s_z[threadIdx.x] != 0xFFFFFFFFu)
+    atomicMin(&R.ctl->zkey[threadIdx.x], s_z[threadIdx.x]);
+}
+#define RVEA_REPRO_PSO(name, PROB)                                                         \
+  __global__ void __launch_bounds__(kReproThreads, 3) name(const __grid_constant__ BatchDir dir) { \
+    repro_pso_body<PROB>(dir);                                                             \
+  }
+RVEA_REPRO_PSO(k_repro_pso_dtlz1, PROB_DTLZ1)
+RVEA_REPRO_PSO(k_repro_pso_dtlz2, PROB_DTLZ2)
+RVEA_REPRO_PSO(k_repro_pso_dtlz3, PROB_DTLZ3)
+RVEA_REPRO_PSO(k_repro_pso_dtlz4, PROB_DTLZ4)
+#undef RVEA_REPRO_PSO
 
 // Initial population (Algorithm 2, initialisation), slots 0..N-1, and its
 // objectives.  DTLZ: x = L + (U-L) u24 from INIT (j/4, i, 0) word j%4.

@@ -81,10 +81,11 @@ struct RunDesc {
   int sg;              // groups per segment, ceil(G / nseg) <= kLaneGroups * team
   int op_mode;         // 1: stateless selection (identity slots, AoS F)
   int op;              // reproduction: 0 SBX + polynomial mutation, 1 DE/rand/1/bin, 2 random,
-                       //               3 competitive swarm (CSO)
+                       //               3 competitive swarm (CSO), 4 particle swarm (PSO)
   float de_F;          // DE scale factor
   uint32_t T_cr;       // DE crossover coin: fires iff (w >> 8) < T_cr
   float cso_phi;       // CSO: weight of the swarm-centre term
+  float pso_w, pso_c1, pso_c2;   // PSO: inertia weight, cognitive and social weights
   // parameters
   float L, U, alpha, inv_eta_c1, eta_m;
   uint32_t T_c, T_m;   // 24-bit event thresholds (fires iff k < T)
@@ -105,9 +106,11 @@ struct RunDesc {
   int *assoc;          // [n_comb]   vector of each solution, -1 if invalid
   int *surv;           // [N]        combined index kept by vector j, -1 if none
   float *psum;         // [P][2][nseg] partial g sums of the segments of each pair
-  // swarm state of the CSO operator (null for the other operators)
+  // swarm state of the CSO and PSO operators (null for the other operators)
   float *vel;          // [2N][d_pad] velocity of each pool row (moves with its row)
   float *kapd;         // [N]        APD that kept vector slot j's member (+inf: none yet)
+  float *pb;           // [2N][d_pad] PSO: personal best of each pool row's member
+  float *fpb;          // [m][2N]    PSO: objectives of those personal bests
   float *xbar;         // [d_pad]    mean position of the valid members (the swarm centre)
   float *xpart;        // [ceil(N/kMeanRows)][d_pad] float partial sums of the centre
   // draw recording (inspection; null when off): the vector slot of each

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, DTLZ3_SPHERE, DTLZ4_SPHERE, NEURO_LINEAR,
-                      Config, NeuroDynamics, Plan, ServerStats, RveaError, check, lib)
+                      REPRO_PSO, Config, NeuroDynamics, Plan, ServerStats, RveaError, check, lib)
 
 __all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
            "DTLZ2_SPHERE", "DTLZ1_LINEAR", "DTLZ3_SPHERE", "DTLZ4_SPHERE", "NEURO_LINEAR",
@@ -55,18 +55,20 @@ class Run:
                  p_m: float = 1.0, lower: Optional[float] = None,
                  upper: Optional[float] = None, seed: int = 0, neuro=None,
                  reproduction: int = 0, de_F: float = 0.5, de_CR: float = 0.9,
-                 cso_phi: float = 0.0, device=None, stream=None):
+                 cso_phi: float = 0.0, pso_w: float = 0.7298, pso_c1: float = 1.49618,
+                 pso_c2: float = 1.49618, device=None, stream=None):
         self.device = torch.device("cuda" if device is None else device)
         if lower is None:
             lower = -1.0 if problem == NEURO_LINEAR else 0.0
         if upper is None:
             upper = 1.0
         self.m, self.d, self.N, self.H = m, d, N, H
+        self.reproduction = reproduction
         self.problem, self.t_max = problem, t_max
         L = lib()
         cfg = Config(m, d, N, H, problem, t_max, alpha, f_r, eta_c, eta_m, p_c, p_m,
                      lower, upper, seed & 0xFFFFFFFFFFFFFFFF, None, reproduction, de_F, de_CR,
-                     cso_phi)
+                     cso_phi, pso_w, pso_c1, pso_c2)
         self._neuro_keep = None
         if neuro is not None:
             A = np.ascontiguousarray(neuro["A"], dtype=np.float64)
@@ -197,19 +199,27 @@ class Run:
               "rvea_import_state")
 
     def export_swarm(self, stream=None):
-        """Velocities (N x d) and kept APDs (N) of a CSO run, by vector slot."""
-        vel = torch.empty((self.N, self.d), dtype=torch.float32, device=self.device)
-        apd = torch.empty(self.N, dtype=torch.float32, device=self.device)
-        check(lib().rvea_export_swarm(self._h, _ptr(vel), _ptr(apd), C.c_void_p(_stream(stream))),
-              "rvea_export_swarm")
-        return vel, apd
+        """Velocities (N x d) and kept APDs (N) of a CSO or PSO run, by vector
+        slot; for PSO also the personal bests (N x d) and their objectives
+        (N x m), else None."""
+        dev = self.device
+        vel = torch.empty((self.N, self.d), dtype=torch.float32, device=dev)
+        apd = torch.empty(self.N, dtype=torch.float32, device=dev)
+        pso = self.reproduction == REPRO_PSO
+        pb = torch.empty((self.N, self.d), dtype=torch.float32, device=dev) if pso else None
+        fpb = torch.empty((self.N, self.m), dtype=torch.float32, device=dev) if pso else None
+        check(lib().rvea_export_swarm(self._h, _ptr(vel), _ptr(apd), _ptr(pb), _ptr(fpb),
+                                      C.c_void_p(_stream(stream))), "rvea_export_swarm")
+        return vel, apd, pb, fpb
 
-    def import_swarm(self, vel, apd, stream=None) -> None:
-        """Replace a CSO run's velocities and kept APDs (after import_state)."""
-        vel = torch.as_tensor(vel, dtype=torch.float32, device=self.device).contiguous()
-        apd = torch.as_tensor(apd, dtype=torch.float32, device=self.device).contiguous()
-        check(lib().rvea_import_swarm(self._h, _ptr(vel), _ptr(apd), C.c_void_p(_stream(stream))),
-              "rvea_import_swarm")
+    def import_swarm(self, vel, apd, pbest=None, fpbest=None, stream=None) -> None:
+        """Replace a CSO or PSO run's swarm state (after import_state)."""
+        dev = self.device
+        f32 = lambda a: None if a is None else torch.as_tensor(
+            a, dtype=torch.float32, device=dev).contiguous()
+        vel, apd, pbest, fpbest = f32(vel), f32(apd), f32(pbest), f32(fpbest)
+        check(lib().rvea_import_swarm(self._h, _ptr(vel), _ptr(apd), _ptr(pbest), _ptr(fpbest),
+                                      C.c_void_p(_stream(stream))), "rvea_import_swarm")
 
     def offspring(self, stream=None):
         X = torch.empty((self.N, self.d), dtype=torch.float32, device=self.device)

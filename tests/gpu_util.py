@@ -35,7 +35,7 @@ def make_run(p):
     return Run(m=p.m, d=p.d, N=p.N, H=p.H, problem=p.problem, t_max=p.t_max, alpha=p.alpha,
                f_r=p.f_r, eta_c=p.eta_c, eta_m=p.eta_m, p_c=p.p_c, p_m=p.p_m, lower=p.L,
                upper=p.U, seed=p.seed, reproduction=p.op, de_F=p.de_F, de_CR=p.de_CR,
-               cso_phi=p.cso_phi)
+               cso_phi=p.cso_phi, pso_w=p.pso_w, pso_c1=p.pso_c1, pso_c2=p.pso_c2)
 
 
 def to_np(st):

@@ -111,13 +111,36 @@ def test_cso_config_and_swarm_calls_without_gpu(native):
     assert sbx > 0 and cso >= sbx + swarm and cso < sbx + swarm + 6 * 256
     for phi in (-0.1, 1.5, float("nan")):
         assert L.rvea_workspace_bytes_ex(C.byref(native.Config(**base, cso_phi=phi))) == 0
-    cfg = native.Config(**dict(base, reproduction=4), cso_phi=0.1)
+    cfg = native.Config(**dict(base, reproduction=5), cso_phi=0.1)
     assert L.rvea_workspace_bytes_ex(C.byref(cfg)) == 0
     h = C.c_void_p()
     cfg = native.Config(**dict(base, problem=2), cso_phi=0.1)   # the rollout problem: SBX only
     assert L.rvea_init_ex(C.byref(cfg), C.c_void_p(1 << 20), 1 << 30, None, C.byref(h)) == native.ERR_ARG
-    assert L.rvea_export_swarm(None, None, None, None) == native.ERR_ARG
-    assert L.rvea_import_swarm(None, C.c_void_p(1 << 20), C.c_void_p(1 << 20), None) == native.ERR_ARG
+    assert L.rvea_export_swarm(None, None, None, None, None, None) == native.ERR_ARG
+    a = C.c_void_p(1 << 20)
+    assert L.rvea_import_swarm(None, a, a, a, a, None) == native.ERR_ARG
+
+
+def test_pso_config_without_gpu(native):
+    """The PSO operator (reproduction 4): inertia outside [0, 1] or a weight
+    outside [0, 4] is refused; its workspace adds the velocity and
+    personal-best pools (2N rows of d_pad floats each), the personal bests'
+    objectives and the kept APDs, and no swarm centre."""
+    L = native.lib()
+    base = dict(m=3, d=1001, N=210, H=19, problem=1, t_max=100, alpha=2.0, f_r=0.1,
+                eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0, lower=0.0, upper=1.0,
+                seed=0, neuro=None, reproduction=native.REPRO_PSO, de_F=0.5, de_CR=0.9,
+                cso_phi=0.0)
+    sbx = L.rvea_workspace_bytes(3, 1001, 210)
+    pso = L.rvea_workspace_bytes_ex(C.byref(native.Config(**base, pso_w=0.7298, pso_c1=1.5,
+                                                          pso_c2=1.5)))
+    d_pad, N, m = 1008, 210, 3
+    swarm = 2 * (2 * N * d_pad * 4) + m * 2 * N * 4 + N * 4
+    assert sbx > 0 and swarm <= pso - sbx < swarm + 6 * 256
+    for w, c1, c2 in ((-0.1, 1.5, 1.5), (1.2, 1.5, 1.5), (0.5, 4.5, 1.5), (0.5, 1.5, -1.0),
+                      (float("nan"), 1.5, 1.5)):
+        cfg = native.Config(**base, pso_w=w, pso_c1=c1, pso_c2=c2)
+        assert L.rvea_workspace_bytes_ex(C.byref(cfg)) == 0
 
 
 def test_metrics_and_counters_reject_null_without_gpu(native):

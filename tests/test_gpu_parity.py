@@ -52,12 +52,15 @@ SHAPES = [
 
 def _state_to_oracle(orc, st, swarm=None):
     s = to_np(st)
-    vel = apd = None
-    if swarm is not None:   # CSO: the GPU's velocities and kept APDs (float32 values)
+    vel = apd = pb = fpb = None
+    if swarm is not None:   # CSO, PSO: the GPU's swarm state (float32 values)
         vel = np.nan_to_num(swarm[0].cpu().numpy().astype(np.float64))
         apd = swarm[1].cpu().numpy().astype(np.float64)
+        if swarm[2] is not None:
+            pb = np.nan_to_num(swarm[2].cpu().numpy().astype(np.float64))
+            fpb = np.nan_to_num(swarm[3].cpu().numpy().astype(np.float64))
     return orc.State(s["X"].astype(np.float64), s["F"].astype(np.float64), s["valid"],
-                     s["V"], s["gamma"], s["t"], vel=vel, apd=apd)
+                     s["V"], s["gamma"], s["t"], vel=vel, apd=apd, pbest=pb, fpbest=fpb)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -115,6 +118,16 @@ def test_teacher_forced_cso(orc, shape, phi):
     _teacher_forced(orc, shape, 6, op=3, cso_phi=phi)
 
 
+# Particle swarm optimization (op 4): Clerc's constriction weights and a
+# stronger inertia, on the small, staged, fused-tail and m = 10 shapes;
+# velocities, personal bests and kept APDs carried through six generations.
+@pytest.mark.parametrize("shape,w", [((3, 12, 105, 13, 0), 0.7298), ((3, 1001, 210, 19, 1), 0.9),
+                                     ((3, 2500, 1275, 49, 1), 0.7298), ((10, 30, 220, 3, 0), 0.5),
+                                     ((2, 4099, 100, 99, 4), 0.7298)])
+def test_teacher_forced_pso(orc, shape, w):
+    _teacher_forced(orc, shape, 6, op=4, pso_w=w)
+
+
 # Population sizes of the paper's speed sweeps that are not lattice sizes
 # (Sec. 4.1: n = 2^k at d = 100, d = 2^k at n = 100): the run takes the
 # largest Das-Dennis lattice with at most n points (n = 128 -> H = 14,
@@ -141,7 +154,7 @@ def _teacher_forced(orc, shape, gens, **kw):
         run.record_draws(True)
     for gen in range(gens):
         st = run.export_state()
-        sw = run.export_swarm() if p.op == 3 else None
+        sw = run.export_swarm() if p.op in (3, 4) else None
         ost = _state_to_oracle(orc, st, sw)
         t = ost.t
         Fpar = ost.F.copy()
@@ -169,8 +182,10 @@ def _teacher_forced(orc, shape, gens, **kw):
         bad_a, bad_s = selection_mismatches(Fc, vc, to_np(st)["V"], ga.cpu().numpy(),
                                             gsurv.cpu().numpy(), o)
         assert not bad_a and not bad_s, (gen, bad_a[:5], bad_s[:5])
-        if p.op == 3:
+        if p.op in (3, 4):
             _check_swarm(run, sw, gsurv.cpu().numpy(), out["survivor"], ost, o, N)
+        if p.op == 4:
+            _check_pbest(run, sw, st, gx, gf, gsurv.cpu().numpy(), out["survivor"], ost, N)
         # the adapted reference vectors and gamma follow the GPU's survivors
         nst = to_np(run.export_state())
         assert nst["t"] == t + 1
@@ -192,7 +207,7 @@ def _check_swarm(run, sw_prev, gsurv, osurv, ost, o, N):
     gamma differs); a parent's velocity moves with it unchanged (bit for
     bit); a child's velocity matches the oracle's where both kept the same
     child."""
-    vel, apd = (x.cpu().numpy() for x in run.export_swarm())
+    vel, apd = (x.cpu().numpy() for x in run.export_swarm()[:2])
     vprev = sw_prev[0].cpu().numpy()
     live = gsurv >= 0
     assert np.isinf(apd[~live]).all()
@@ -208,6 +223,39 @@ def _check_swarm(run, sw_prev, gsurv, osurv, ost, o, N):
     assert kid.any()
     err = np.abs(vel[kid].astype(np.float64) - ost.vel[kid])
     assert err.max() <= 1e-5, float(err.max())
+
+
+def _check_pbest(run, sw_prev, st_prev, gx, gf, gsurv, osurv, ost, N):
+    """PSO personal bests after a generation.  The GPU's decision for each
+    kept child, taken on its own float32 objectives, is the dominance rule
+    recomputed here on the same float32 values (the old best is kept iff it
+    dominates the child), and the row and objectives are that choice bit for
+    bit; a kept parent keeps its best bit for bit; where the oracle kept the
+    same child and took the same decision, its best matches within 1e-5."""
+    _, _, pb, fpb = (x.cpu().numpy() for x in run.export_swarm())
+    pb_prev, fpb_prev = sw_prev[2].cpu().numpy(), sw_prev[3].cpu().numpy()
+    valid_prev = to_np(st_prev)["valid"]
+    vlist = np.flatnonzero(valid_prev)
+    K = len(vlist)
+    live = gsurv >= 0
+    par = live & (gsurv < N)
+    assert np.array_equal(pb[par], pb_prev[gsurv[par]])
+    assert np.array_equal(fpb[par], fpb_prev[gsurv[par]])
+    agree = 0
+    kids = np.flatnonzero(live & (gsurv >= N))
+    for j in kids:
+        c = gsurv[j] - N
+        ip = vlist[c % K]
+        fo, fc = fpb_prev[ip], gf[c]
+        keep_old = bool(np.all(fo <= fc) and np.any(fo < fc))
+        want_p, want_f = (pb_prev[ip], fo) if keep_old else (gx[c], fc)
+        assert np.array_equal(pb[j], want_p) and np.array_equal(fpb[j], want_f), (j, keep_old)
+        if osurv[j] == gsurv[j]:
+            o_keep = np.array_equal(ost.pbest[j], pb_prev[ip].astype(np.float64))
+            if o_keep == keep_old:
+                agree += 1
+                assert np.abs(ost.pbest[j] - pb[j]).max() <= 1e-5
+    assert agree >= 0.9 * np.sum(osurv[kids] == gsurv[kids])
 
 
 @pytest.mark.parametrize("m,n,r,seed", [(3, 700, 1300, 0), (2, 257, 100, 1), (5, 1000, 126, 2),
