@@ -149,11 +149,12 @@ __device__ __forceinline__ void grid_assoc(const RunDesc &R, int i, const float4
 // gamma, so that after the group reduces (larger dot, then smaller index)
 // the lane holding the winner computes the APD and votes without another
 // round trip.  Four lanes serve twice as many solutions a warp, for when
-// eight would leave warps with a second round.
+// eight would leave warps with a second round.  `pre` (or null): solution
+// i's objectives from fc, loaded by the caller ahead of z*.
 template <int M, int L = 8>
 __device__ __forceinline__ void grid_assocL(const RunDesc &R, int i, const float4 *sV,
                                             const float *z, const float *w, float pen,
-                                            const float *fc) {
+                                            const float *fc, const float *pre = nullptr) {
   static_assert(L == 8 || L == 4, "8 or 4 lanes per solution");
   constexpr int NW = 8 / L;                  // record words a lane holds
   constexpr int NE = (kGridInline + L - 1) / L;   // inline candidates a lane scans
@@ -166,7 +167,7 @@ __device__ __forceinline__ void grid_assocL(const RunDesc &R, int i, const float
     if (fc) {
       float F0[M];
 #pragma unroll
-      for (int k = 0; k < M; ++k) F0[k] = __ldcg(fc + (size_t)k * n + i);
+      for (int k = 0; k < M; ++k) F0[k] = pre ? pre[k] : __ldcg(fc + (size_t)k * n + i);
       valid = F0[0] == F0[0];   // NaN: an invalid parent
 #pragma unroll
       for (int k = 0; k < M; ++k) f[k] = F0[k] - z[k];

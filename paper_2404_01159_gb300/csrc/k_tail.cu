@@ -294,18 +294,21 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     // at a time, every lane adds); the position variables
     const int S = R.nseg, pp = cd < R.P ? cd : cd - R.P;
     const float *ps = R.psum + (size_t)pp * 2 * S + (cd < R.P ? 0 : S);
+    // the group's loads first, all in flight together: the first eight
+    // partials, the position variables and the sites' values
+    const float v0 = live && sub < S ? __ldcg(ps + sub) : 0.0f;
+    float hv = live && sub < M - 1 ? __ldcg(row + sub) : 0.0f;
+    float *const px = live ? row + js : nullptr;
+    const float x = live && sub < kin ? __ldcg(px) : 0.0f;
     float g = 0.0f;
     for (int q0 = 0; q0 < S; q0 += 8) {
-      const float v = live && q0 + sub < S ? __ldcg(ps + q0 + sub) : 0.0f;
+      const float v = q0 == 0 ? v0 : (live && q0 + sub < S ? __ldcg(ps + q0 + sub) : 0.0f);
       for (int u = 0; u < 8 && q0 + u < S; ++u) g += __shfl_sync(0xffffffffu, v, gl | u);
     }
-    float hv = live && sub < M - 1 ? __ldcg(row + sub) : 0.0f;
     // the mutations, site i on lane i of the group
     float dgi = 0.0f;
     bool hhit = false;
     if (live && sub < kin) {
-      float *const px = row + js;
-      const float x = __ldcg(px);
       const float xn = poly_mutate(x, mag, R.L, R.U, R.eta_m);
       __stcg(px, xn);
       dgi = (int)js >= M - 1 ? g_term1(PROB, xn, 0.0f) - g_term1(PROB, x, 0.0f) : 0.0f;
@@ -349,6 +352,17 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   if (tid < kMaxM) s_lo[tid] = 0xFFFFFFFFu;   // for the survivors' minimum in C
   // ---- B: association and APD votes ----------------------------------------
   {
+    // the direction grid's first group of solutions (the only one, unless
+    // the population outgrows the grid's lanes): their objectives are loaded
+    // here, in flight while warp 0 gathers z*
+    constexpr int MG = M <= 3 ? M : 3;
+    const int gw = warp * nb + b, nw = nb * (kTailThreads / 32);
+    const bool l8 = R.n_comb <= 4 * nw;
+    const int i0 = l8 ? 4 * gw + (lane >> 3) : 8 * gw + (lane >> 2);
+    const bool use_pre = S.grid_ok && fcur != nullptr && i0 < R.n_comb;
+    float pre[MG];
+#pragma unroll
+    for (int k = 0; k < MG; ++k) pre[k] = use_pre ? __ldcg(fcur + (size_t)k * n2 + i0) : 0.0f;
     if (warp == 0) {   // z* = min(the parents' z*, every CTA's children)
       // lane l reads the four minima of CTAs l, l + 32, ... (all loads in
       // flight together, nb <= kTailMaxCtas = 8 x 32, and in flight while
@@ -399,17 +413,18 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
       for (int k = 0; k < 3; ++k) w[k] = S.gw[k];
       // eight lanes per solution (groups of four solutions spread over the
       // CTAs), or four where eight would give some warps a second group
-      const int gw = warp * nb + b, nw = nb * (kTailThreads / 32);
-      if (R.n_comb <= 4 * nw) {
+      if (l8) {
         for (int g = gw; 4 * g < R.n_comb; g += nw)
-          grid_assocL<M <= 3 ? M : 3, 8>(R, 4 * g + (lane >> 3), sV, z, w, pen, fcur);
+          grid_assocL<MG, 8>(R, 4 * g + (lane >> 3), sV, z, w, pen, fcur,
+                             g == gw && use_pre ? pre : nullptr);
       } else {
         for (int g = gw; 8 * g < R.n_comb; g += nw)
-          grid_assocL<M <= 3 ? M : 3, 4>(R, 8 * g + (lane >> 2), sV, z, w, pen, fcur);
+          grid_assocL<MG, 4>(R, 8 * g + (lane >> 2), sV, z, w, pen, fcur,
+                             g == gw && use_pre ? pre : nullptr);
       }
     } else {   // the tile search (a CTA-uniform branch)
       const float2 csb = tile_bounds(sCS, T);
-      const int groups = (R.n_comb + 3) >> 2, gw = warp * nb + b, nw = nb * (kTailThreads / 32);
+      const int groups = (R.n_comb + 3) >> 2;
       for (int g = gw; g < groups; g += nw) prune_group<M, false>(R, 4 * g, sV, sC, sCS, sR, z, pen, csb);
     }
   }
