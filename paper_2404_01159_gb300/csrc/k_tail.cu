@@ -165,6 +165,7 @@ struct TailShared {
   unsigned lo[kMaxM], hi[kMaxM];
   int red[2][32];
   uint32_t free_[kTailFreeWords];
+  uint32_t vb_[kTailFreeWords];   // this CTA's valid-flag words of P_{t+1} (C -> D)
   double rng[kMaxM];
   unsigned z[4];          // z* of the combined population (order-preserving)
   unsigned zr[8];         // survivors' minimum (0..3) and maximum (4..7)
@@ -472,7 +473,10 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
         }
       }
       const uint32_t vmask = __ballot_sync(0xffffffffu, s >= 0);
-      if (lane == 0) R.vbits[vw] = vmask;
+      if (lane == 0) {
+        R.vbits[vw] = vmask;
+        S.vb_[vw - v0] = vmask;   // v1 - v0 <= the pool-row words a CTA holds
+      }
       nvalid += __popc(vmask);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -520,6 +524,14 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
     av = __reduce_add_sync(0xffffffffu, av);
     af = __reduce_add_sync(0xffffffffu, af);
     if (lane == 0) { s_red[1][0] = a; s_red[1][1] = av; s_red[1][2] = af; }
+  } else if (warp == 1) {   // meanwhile: the free pool rows of this CTA's row words
+    uint32_t *const s_free = S.free_;
+    for (int w = o0; w < o1; ++w) {
+      const int row = 32 * w + lane;
+      const bool occ = row >= n2 || __ldcg(R.otag + row) == t;
+      const uint32_t fw = __ballot_sync(0xffffffffu, !occ);
+      if (lane == 0) s_free[w - o0] = fw;
+    }
   }
   const bool adapt = (t % R.p_adapt) == 0;
   if (warp == 2 && (b == 0 || adapt)) {   // the survivors' minimum and maximum over the CTAs
@@ -540,17 +552,10 @@ __device__ __forceinline__ void tail_body(const RunDesc &R, TailShared &S) {
   pre_v = s_red[1][1];
   pre_f = s_red[1][2];
   const int K = tot_v;
-  if (warp == 0) {   // ascending valid slots of this CTA's vector words
-    warp_compact_by([&](int w) { return __ldcg(R.vbits + w); }, v0, v1, R.vlist, pre_v, N);
+  if (warp == 0) {   // ascending valid slots of this CTA's vector words (from C)
+    warp_compact_by([&](int w) { return S.vb_[w - v0]; }, v0, v1, R.vlist, pre_v, N);
   } else if (warp == 1) {   // ascending free pool rows of this CTA's row words
     uint32_t *const s_free = S.free_;
-    for (int w = o0; w < o1; ++w) {
-      const int row = 32 * w + lane;
-      const bool occ = row >= n2 || __ldcg(R.otag + row) == t;
-      const uint32_t fw = __ballot_sync(0xffffffffu, !occ);
-      if (lane == 0) s_free[w - o0] = fw;
-    }
-    __syncwarp();
     warp_compact_by([&](int w) { return s_free[w - o0]; }, o0, o1,
                     R.child_slot + ((t + 1) & 1) * N, pre_f, N);
   }
