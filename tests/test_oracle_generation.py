@@ -27,6 +27,9 @@ def igd(F, front):
 
 
 def test_generation_is_composition(orc):
+    """Algorithm 2's loop body glues the separately pinned operators in the
+    paper's order: mating, SBX, mutation, evaluation, selection of the union
+    of parents and children, the survivors into their vectors' slots."""
     p = _small(orc)
     V0, st = orc.initial_state(p)
     for _ in range(3):
