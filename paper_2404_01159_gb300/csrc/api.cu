@@ -701,12 +701,13 @@ void launch_mutate1(const rvea_run *r, cudaStream_t st) {
 // search, when each CTA's share of the pool-row bitmap fits its buffer, its
 // children fit its lanes (eight a child) and the search tables its shared
 // memory (or, past that, the tables are read through L2).
-// One CTA per SM but for the last 8 to free up: the tail's CTAs become
+// One CTA per SM but for the last 24 to free up: the tail's CTAs become
 // resident as the reproduction kernel drains (each takes a whole SM), and the
-// few SMs that finish it last would start their phase A late (measured:
-// 144 of 152 CTAs, 0.45 us faster a generation than 152).
+// SMs that finish it last would start their phase A late (measured over
+// 10000 generations on 152 SMs: 152 CTAs 97.5, 144 CTAs 97.07, 136 CTAs
+// 96.84, 128 CTAs 96.44, 120 CTAs 96.48 us a generation).
 int tail_grid(const rvea_run *r) {
-  return std::min(r->num_sms > 64 ? r->num_sms - 8 : r->num_sms, kTailMaxCtas);
+  return std::min(r->num_sms > 64 ? r->num_sms - 24 : r->num_sms, kTailMaxCtas);
 }
 bool tail_ok(const rvea_run *r) {
   return r->hd.ntiles > 0 && r->hd.problem != PROB_NEURO &&
