@@ -340,8 +340,9 @@ int rvea_launches_per_generation(const rvea_run *run, int adapting);
 
 /* Full run state in slot order: X (N x d f32), F (N x m f32), valid (N u8),
  * V (N x m f64, current reference vectors), gamma (N f64).  Any output may
- * be NULL.  Host or device pointers.  Together with rvea_generation this is
- * a checkpoint: Philox is counter-based, so no generator state exists. */
+ * be NULL.  Host or device pointers.  Together with rvea_generation (and,
+ * for the CSO and PSO operators, rvea_export_swarm) this is a checkpoint:
+ * Philox is counter-based, so no generator state exists. */
 rvea_status rvea_export_state(const rvea_run *run, float *X, float *F, uint8_t *valid,
                               double *V, double *gamma, void *cuda_stream);
 
