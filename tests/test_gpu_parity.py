@@ -369,6 +369,31 @@ def test_checkpoint_roundtrip_bit_identical(orc):
     assert sa["t"] == sb["t"] == 14
 
 
+@pytest.mark.parametrize("op,kw", [(3, dict(cso_phi=0.1)), (4, dict(pso_w=0.7298))])
+def test_checkpoint_roundtrip_swarm(orc, op, kw):
+    """A CSO or PSO run resumed from its exported state and swarm state
+    (velocities, kept APDs, personal bests) continues bit for bit; without
+    the swarm state the resumed run starts a new swarm and differs."""
+    p = params(orc, 3, 1001, 210, 19, 1, t_max=40, seed=9, op=op, **kw)
+    a = make_run(p)
+    a.step(7)
+    st, sw = a.export_state(), a.export_swarm()
+    b = make_run(p)
+    b.import_state(st["X"], st["F"], st["valid"], st["V"], st["gamma"], st["t"])
+    b.import_swarm(*sw)
+    c = make_run(p)
+    c.import_state(st["X"], st["F"], st["valid"], st["V"], st["gamma"], st["t"])
+    for r in (a, b, c):
+        r.step(6)
+    sa, sb, sc = (to_np(r.export_state()) for r in (a, b, c))
+    for k in ("X", "F", "valid", "V", "gamma"):
+        assert np.array_equal(sa[k], sb[k], equal_nan=True), k
+    wa, wb = ([x.cpu().numpy() for x in r.export_swarm() if x is not None] for r in (a, b))
+    for x, y in zip(wa, wb):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert not np.array_equal(sa["X"], sc["X"], equal_nan=True)
+
+
 def test_import_refuses_population_without_valid_member(orc):
     """A state with no valid member is refused (mating would have nothing to
     draw from) and the run keeps its state."""
