@@ -48,8 +48,8 @@ WORKLOADS = {
                                      pso_c2=1.49618),
 }
 OPS = {0: "k_repro (mating + SBX + g-terms; mutation and evaluation in k_mutate when d > 1024)",
-       1: "k_repro_op (DE/rand/1/bin: four rows read, one child row written, evaluation)",
-       2: "k_repro_op (random reproduction: one child row written, evaluation)",
+       1: "k_repro_de (DE/rand/1/bin: four rows read, one child row written, evaluation)",
+       2: "k_repro_rand (random reproduction: one child row written, evaluation)",
        3: "k_cso_mean + k_cso_centre + k_repro_cso (CSO: swarm centre over the valid rows; "
           "winner, loser and loser velocity rows read, child row and velocity written; "
           "evaluation)",

@@ -55,10 +55,14 @@ __global__ void k_mutate_neuro(const __grid_constant__ BatchDir dir);
 __global__ void k_mutate_dtlz3(const __grid_constant__ BatchDir dir);
 __global__ void k_mutate_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_init(const __grid_constant__ BatchDir dir);
-__global__ void k_repro_op_dtlz1(const __grid_constant__ BatchDir dir);
-__global__ void k_repro_op_dtlz2(const __grid_constant__ BatchDir dir);
-__global__ void k_repro_op_dtlz3(const __grid_constant__ BatchDir dir);
-__global__ void k_repro_op_dtlz4(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_de_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_de_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_de_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_de_dtlz4(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_rand_dtlz1(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_rand_dtlz2(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_rand_dtlz3(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_rand_dtlz4(const __grid_constant__ BatchDir dir);
 __global__ void k_cso_mean(const __grid_constant__ BatchDir dir);
 __global__ void k_cso_centre(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz1(const __grid_constant__ BatchDir dir);
@@ -636,11 +640,20 @@ void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st, 
     }
     return;
   }
+  if (op == 1) {
+    switch (problem) {
+      case PROB_DTLZ1: launch_pdl(k_repro_de_dtlz1, grid, kReproThreads, 0, st, d); break;
+      case PROB_DTLZ3: launch_pdl(k_repro_de_dtlz3, grid, kReproThreads, 0, st, d); break;
+      case PROB_DTLZ4: launch_pdl(k_repro_de_dtlz4, grid, kReproThreads, 0, st, d); break;
+      default: launch_pdl(k_repro_de_dtlz2, grid, kReproThreads, 0, st, d); break;
+    }
+    return;
+  }
   switch (problem) {
-    case PROB_DTLZ1: launch_pdl(k_repro_op_dtlz1, grid, kReproThreads, 0, st, d); break;
-    case PROB_DTLZ3: launch_pdl(k_repro_op_dtlz3, grid, kReproThreads, 0, st, d); break;
-    case PROB_DTLZ4: launch_pdl(k_repro_op_dtlz4, grid, kReproThreads, 0, st, d); break;
-    default: launch_pdl(k_repro_op_dtlz2, grid, kReproThreads, 0, st, d); break;
+    case PROB_DTLZ1: launch_pdl(k_repro_rand_dtlz1, grid, kReproThreads, 0, st, d); break;
+    case PROB_DTLZ3: launch_pdl(k_repro_rand_dtlz3, grid, kReproThreads, 0, st, d); break;
+    case PROB_DTLZ4: launch_pdl(k_repro_rand_dtlz4, grid, kReproThreads, 0, st, d); break;
+    default: launch_pdl(k_repro_rand_dtlz2, grid, kReproThreads, 0, st, d); break;
   }
 }
 // The CSO runs' swarm centres (k_cso_mean), before their reproduction; runs
@@ -803,15 +816,15 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
     // one launch per (problem, load path) group, each with its own directory
     int pg[2 * kProblems] = {};
     for (int g = 0; g < 2 * kProblems; ++g) dg[g].n = 0;
-    // the runs with another operator: one launch per (problem, kernel: DE
-    // and random, CSO, PSO)
-    static thread_local BatchDir dop[3 * kProblems];
-    int pop[3 * kProblems] = {};
-    for (int g = 0; g < 3 * kProblems; ++g) dop[g].n = 0;
+    // the runs with another operator: one launch per (problem, operator:
+    // DE, random, CSO, PSO)
+    static thread_local BatchDir dop[4 * kProblems];
+    int pop[4 * kProblems] = {};
+    for (int g = 0; g < 4 * kProblems; ++g) dop[g].n = 0;
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];
       if (r->hd.op == 0) continue;
-      const int g = 3 * r->hd.problem + (r->hd.op == 3 ? 1 : r->hd.op == 4 ? 2 : 0);
+      const int g = 4 * r->hd.problem + (r->hd.op - 1);
       BatchDir &D = dop[g];
       D.prefix[D.n] = pop[g];
       D.desc[D.n] = r->d_desc;
@@ -821,10 +834,10 @@ rvea_status launch_generation(rvea_run *const *runs, int n, cudaStream_t st, boo
       ++D.n;
     }
     launch_cso_means(runs, n, st);
-    for (int g = 0; g < 3 * kProblems; ++g) {
+    for (int g = 0; g < 4 * kProblems; ++g) {
       if (dop[g].n == 0) continue;
       dop[g].prefix[dop[g].n] = pop[g];
-      launch_repro_op(dop[g], g / 3, pop[g], st, g % 3 == 1 ? 3 : g % 3 == 2 ? 4 : 1);
+      launch_repro_op(dop[g], g / 4, pop[g], st, g % 4 + 1);
     }
     for (int q = 0; q < n; ++q) {
       const rvea_run *r = runs[q];

@@ -611,7 +611,28 @@ enum : uint32_t { TAG_DE_PICK = 8, TAG_DE_CR = 9, TAG_RANDOM = 10, TAG_CSO_PICK 
 
 __device__ __forceinline__ int de_pos(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
 
+// The g-terms of float4 Q of a child row into acc (x: its even variables, y:
+// its odd ones), the position variables j < mh left out.  Past them, two
+// packed steps (g_terms2 is g_term1 on each lane, and the row padding, 0.5,
+// adds an exact zero), else element by element: the same bits either way.
 template <int PROB>
+__device__ __forceinline__ float2 gterms4(const float *u, int Q, int mh, int d, float2 acc) {
+  if (4 * Q >= mh) {
+    acc = g_terms2(PROB, make_float2(u[0], u[1]), acc);
+    return g_terms2(PROB, make_float2(u[2], u[3]), acc);
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int j = 4 * Q + v;
+    if (j >= mh && j < d) {
+      if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
+      else acc.x = g_term1(PROB, u[v], acc.x);
+    }
+  }
+  return acc;
+}
+
+template <int PROB, int OP>   // OP 1: DE/rand/1/bin, 2: random reproduction
 __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
   __shared__ unsigned s_z[kMaxM];
   pdl_wait();      // the previous generation's lists and slot maps
@@ -631,7 +652,7 @@ __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
     if (slot < 0 || slot >= 2 * N) { set_status(R.ctl, ST_BADINDEX); slot = -1; }
     // DE: the four rows (physical slots) and j_rand, drawn by lane 0
     int rows[4] = {0, 0, 0, 0}, jr = -1;
-    if (R.op == 1 && lane == 0 && K > 0) {
+    if (OP == 1 && lane == 0 && K > 0) {
       const uint4 w = philox_k((uint32_t)o, 0u, (uint32_t)t, TAG_DE_PICK, kr);
       const int tp = o % K;
       int pos[4];
@@ -670,16 +691,31 @@ __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
       const float4 *X4 = reinterpret_cast<const float4 *>(R.X);
       float4 *Y4 = reinterpret_cast<float4 *>(R.X + (size_t)slot * R.d_pad);
       const int rq = R.d_pad >> 2;
+      // DE: the four rows streamed in, the next float4s loaded while the
+      // current ones are processed (four more loads in flight per lane)
+      const float4 *T0 = X4 + (size_t)rows[0] * rq, *T1 = X4 + (size_t)rows[1] * rq;
+      const float4 *T2 = X4 + (size_t)rows[2] * rq, *T3 = X4 + (size_t)rows[3] * rq;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 c0 = z4, c1 = z4, c2 = z4, c3 = z4;
+      if (OP == 1 && lane < rq) {
+        c0 = __ldg(T0 + lane);
+        c1 = __ldg(T1 + lane);
+        c2 = __ldg(T2 + lane);
+        c3 = __ldg(T3 + lane);
+      }
       for (int Q = lane; Q < rq; Q += 32) {
         float u[4];
-        if (R.op == 1) {
+        if (OP == 1) {
+          float4 n0 = z4, n1 = z4, n2 = z4, n3 = z4;
+          if (Q + 32 < rq) {
+            n0 = __ldg(T0 + Q + 32);
+            n1 = __ldg(T1 + Q + 32);
+            n2 = __ldg(T2 + Q + 32);
+            n3 = __ldg(T3 + Q + 32);
+          }
           const uint4 w = philox_k((uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_DE_CR, kr);
-          const float4 xt = __ldg(X4 + (size_t)rows[0] * rq + Q);
-          const float4 x1 = __ldg(X4 + (size_t)rows[1] * rq + Q);
-          const float4 x2 = __ldg(X4 + (size_t)rows[2] * rq + Q);
-          const float4 x3 = __ldg(X4 + (size_t)rows[3] * rq + Q);
-          const float a0[4] = {xt.x, xt.y, xt.z, xt.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
-          const float a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
+          const float a0[4] = {c0.x, c0.y, c0.z, c0.w}, a1[4] = {c1.x, c1.y, c1.z, c1.w};
+          const float a2[4] = {c2.x, c2.y, c2.z, c2.w}, a3[4] = {c3.x, c3.y, c3.z, c3.w};
           const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
@@ -688,6 +724,7 @@ __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
             const float val = take ? fmaf(Fde, a2[v] - a3[v], a1[v]) : a0[v];
             u[v] = clampf(val, L, U);
           }
+          c0 = n0; c1 = n1; c2 = n2; c3 = n3;
         } else {
           const uint4 w = philox_k((uint32_t)Q, (uint32_t)o, (uint32_t)t, TAG_RANDOM, kr);
           const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
@@ -695,14 +732,9 @@ __device__ __forceinline__ void repro_op_body(const BatchDir &dir) {
           for (int v = 0; v < 4; ++v) u[v] = L + (U - L) * u24f(ww[v]);
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int j = 4 * Q + v;
-          if (j >= d) u[v] = 0.5f;   // row padding: a g-term of exactly zero
-          else if (j >= mh) {
-            if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
-            else acc.x = g_term1(PROB, u[v], acc.x);
-          }
-        }
+        for (int v = 0; v < 4; ++v)
+          if (4 * Q + v >= d) u[v] = 0.5f;   // row padding: a g-term of exactly zero
+        acc = gterms4<PROB>(u, Q, mh, d, acc);
         Y4[Q] = make_float4(u[0], u[1], u[2], u[3]);
       }
       const float2 gs = team_sum2(acc, 32);
@@ -797,14 +829,18 @@ __global__ void __launch_bounds__(256) k_cso_centre(const __grid_constant__ Batc
   }
 }
 
-#define RVEA_REPRO_OP(name, PROB)                                                          \
+#define RVEA_REPRO_OP(name, PROB, OP)                                                      \
   __global__ void __launch_bounds__(kReproThreads) name(const __grid_constant__ BatchDir dir) { \
-    repro_op_body<PROB>(dir);                                                              \
+    repro_op_body<PROB, OP>(dir);                                                          \
   }
-RVEA_REPRO_OP(k_repro_op_dtlz1, PROB_DTLZ1)
-RVEA_REPRO_OP(k_repro_op_dtlz2, PROB_DTLZ2)
-RVEA_REPRO_OP(k_repro_op_dtlz3, PROB_DTLZ3)
-RVEA_REPRO_OP(k_repro_op_dtlz4, PROB_DTLZ4)
+RVEA_REPRO_OP(k_repro_de_dtlz1, PROB_DTLZ1, 1)
+RVEA_REPRO_OP(k_repro_de_dtlz2, PROB_DTLZ2, 1)
+RVEA_REPRO_OP(k_repro_de_dtlz3, PROB_DTLZ3, 1)
+RVEA_REPRO_OP(k_repro_de_dtlz4, PROB_DTLZ4, 1)
+RVEA_REPRO_OP(k_repro_rand_dtlz1, PROB_DTLZ1, 2)
+RVEA_REPRO_OP(k_repro_rand_dtlz2, PROB_DTLZ2, 2)
+RVEA_REPRO_OP(k_repro_rand_dtlz3, PROB_DTLZ3, 2)
+RVEA_REPRO_OP(k_repro_rand_dtlz4, PROB_DTLZ4, 2)
 #undef RVEA_REPRO_OP
 
 // Reproduction by the competitive swarm optimizer (CSO; Cheng and Jin 2015),
@@ -913,12 +949,9 @@ __device__ __forceinline__ void repro_cso_body(const BatchDir &dir) {
           } else {
             u[v] = clampf(al[v] + vv[v], L, U);
             nvel[v] = vv[v];
-            if (j >= mh) {
-              if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
-              else acc.x = g_term1(PROB, u[v], acc.x);
-            }
           }
         }
+        acc = gterms4<PROB>(u, Q, mh, d, acc);
         Y4[Q] = make_float4(u[0], u[1], u[2], u[3]);
         __stcs(VY + Q, make_float4(nvel[0], nvel[1], nvel[2], nvel[3]));
         cw = nw; cl = nl; cv = nv;
@@ -1057,12 +1090,9 @@ __device__ __forceinline__ void repro_pso_body(const BatchDir &dir) {
           } else {
             u[v] = clampf(ax[v] + vv[v], L, U);
             nvel[v] = vv[v];
-            if (j >= mh) {
-              if (v & 1) acc.y = g_term1(PROB, u[v], acc.y);
-              else acc.x = g_term1(PROB, u[v], acc.x);
-            }
           }
         }
+        acc = gterms4<PROB>(u, Q, mh, d, acc);
         const float4 xo = make_float4(u[0], u[1], u[2], u[3]);
         Y4[Q] = xo;
         __stcs(VY + Q, make_float4(nvel[0], nvel[1], nvel[2], nvel[3]));
