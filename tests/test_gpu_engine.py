@@ -135,6 +135,36 @@ def test_batch_graph_equals_alone(orc):
     b.free()
 
 
+def test_batch_of_operators_equals_alone(orc):
+    """Runs of every reproduction operator (SBX, DE, random, CSO with and
+    without the centre, PSO) over the DTLZ problems, on the register and
+    staged sizes and the fused-tail size, stepped together as batched
+    generations (one launch per problem and operator) and alone: the same
+    bits, swarm state included."""
+    from paper_2404_01159_gb300 import Batch
+    shapes = [(3, 12, 105, 13, 0, dict(op=0)), (3, 1001, 210, 19, 1, dict(op=1)),
+              (2, 30, 100, 99, 3, dict(op=2)), (3, 2500, 1275, 49, 1, dict(op=3, cso_phi=0.1)),
+              (10, 30, 220, 3, 0, dict(op=3, cso_phi=0.0)), (3, 1500, 105, 13, 4, dict(op=4)),
+              (2, 4099, 100, 99, 1, dict(op=4, pso_w=0.5)), (5, 77, 126, 5, 1, dict(op=1))]
+    ps = [params(orc, m, d, N, H, pr, t_max=20, seed=40 + i, **kw)
+          for i, (m, d, N, H, pr, kw) in enumerate(shapes)]
+    alone = [make_run(p) for p in ps]
+    batch = [make_run(p) for p in ps]
+    b = Batch(batch)
+    for _ in range(2):
+        for r in alone:
+            r.step(3)
+        b.step(3)
+    for p, ra, rb in zip(ps, alone, batch):
+        _same(ra, rb)
+        if p.op in (3, 4):
+            for x, y in zip(ra.export_swarm(), rb.export_swarm()):
+                if x is not None:
+                    assert np.array_equal(x.cpu().numpy(), y.cpu().numpy(), equal_nan=True)
+        rb.sync_status()
+    b.free()
+
+
 def test_launch_counts(orc):
     """The launches a generation enqueues: reproduction, [mutation and
     evaluation when d > 1024], selection, finalize, [gamma and the tile table
