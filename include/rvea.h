@@ -334,7 +334,7 @@ rvea_status rvea_hypervolume(const rvea_run *run, const double *ref, double *out
 rvea_status rvea_selftest_wait(int polls, void *cuda_stream);
 
 /* Kernel launches rvea_step enqueues for one generation of `run` (adapting:
- * a generation with t % ceil(f_r t_max) == 0, which also rescales V); -1 if
+ * a generation with t % round(f_r t_max) == 0, which also rescales V); -1 if
  * run is NULL. */
 int rvea_launches_per_generation(const rvea_run *run, int adapting);
 
