@@ -27,13 +27,17 @@ struct CellGeom {
 
 // The same for a region of cells [c0, c0 + span) per axis (a cell: span 1;
 // a block of cells: its union).  The vector close to the centre is sought
-// among the tiles list[0 .. nl) (every tile with list == null).
-template <int M>
+// among the tiles list[0 .. nl) (every tile with list == null).  SERIAL
+// false: the warp scans the tiles and members together (every lane must
+// call it and gets the result); true: the calling thread scans them alone,
+// in order, keeping the first maximum (the same choice as the warp's
+// smaller-index tie-break), so that a warp computes 32 cells at once.
+template <int M, bool SERIAL = false>
 __device__ CellGeom region_geom(const RunDesc &R, const int *ck, int span, const float4 *Vt,
                                 const int *list, int nl) {
   CellGeom g;
   g.live = false;
-  const int G = R.gG, lane = threadIdx.x & 31;
+  const int G = R.gG, lane = SERIAL ? 0 : (threadIdx.x & 31), stride = SERIAL ? 1 : 32;
   float lo[2], hi[2], sl = 0.0f;
   for (int k = 0; k < M - 1; ++k) {
     lo[k] = (float)ck[k] / (float)G - kGridPad;
@@ -76,29 +80,33 @@ __device__ CellGeom region_geom(const RunDesc &R, const int *ck, int span, const
   // a vector close to c: the best member of the tile whose centre is closest
   float bt = -INFINITY;
   int tb = 0;
-  for (int e = lane; e < nl; e += 32) {
+  for (int e = lane; e < nl; e += stride) {
     const int t = list ? list[e] : e;
     const float d = pdot<M>(g.c, R.tcen[t]);
     if (d > bt || (d == bt && t < tb)) { bt = d; tb = t; }
   }
+  if (!SERIAL) {
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const float od = __shfl_xor_sync(0xffffffffu, bt, off);
-    const int ot = __shfl_xor_sync(0xffffffffu, tb, off);
-    if (od > bt || (od == bt && ot < tb)) { bt = od; tb = ot; }
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, bt, off);
+      const int ot = __shfl_xor_sync(0xffffffffu, tb, off);
+      if (od > bt || (od == bt && ot < tb)) { bt = od; tb = ot; }
+    }
   }
   const int2 rg = R.trng[tb];
   float cb = -INFINITY;
   int qb = rg.x;
-  for (int q = lane; q < rg.y; q += 32) {
+  for (int q = lane; q < rg.y; q += stride) {
     const float d = pdot<M>(g.c, Vt[rg.x + q]);
     if (d > cb) { cb = d; qb = rg.x + q; }
   }
+  if (!SERIAL) {
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const float od = __shfl_xor_sync(0xffffffffu, cb, off);
-    const int oq = __shfl_xor_sync(0xffffffffu, qb, off);
-    if (od > cb || (od == cb && oq < qb)) { cb = od; qb = oq; }
+    for (int off = 16; off >= 1; off >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, cb, off);
+      const int oq = __shfl_xor_sync(0xffffffffu, qb, off);
+      if (od > cb || (od == cb && oq < qb)) { cb = od; qb = oq; }
+    }
   }
   {
     const float4 v = Vt[qb];
@@ -144,12 +152,11 @@ __device__ __forceinline__ bool support_test(const CellGeom &g, float4 v) {
 // The count pass also keeps the first kGridWarpBuf candidates in `buf` (the
 // warp's shared-memory list), for its own write of an overflow list.
 template <int M, bool FILL>
-__device__ int grid_one(const RunDesc &R, const int *ck, const int *list, int nl, bool inl, int at,
-                        uint16_t *buf) {
+__device__ int grid_one(const RunDesc &R, const int *ck, const CellGeom &g, const int *list, int nl,
+                        bool inl, int at, uint16_t *buf) {
   const int lane = threadIdx.x & 31;
   const int cell = M == 2 ? ck[0] : ck[0] + ck[1] * R.gG;
   const float4 *Vt = R.Vt;
-  const CellGeom g = region_geom<M>(R, ck, 1, Vt, list, nl);
   int n = 0;
   // inline records hold up to kGridInline candidates; longer lists go to the
   // overflow area at offset `at`
@@ -215,6 +222,7 @@ template <int M, bool FILL>
 __device__ void grid_block(const RunDesc &R) {
   __shared__ int s_list[kGridBlockList];
   __shared__ uint16_t s_buf[8][kGridWarpBuf];   // count: each warp's current list
+  __shared__ CellGeom s_geo[kGridSpan2 > kGridSpan3 * kGridSpan3 ? kGridSpan2 : kGridSpan3 * kGridSpan3];
   __shared__ int s_n, s_ovf, s_fast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = R.gG, span = M == 2 ? kGridSpan2 : kGridSpan3;
@@ -258,6 +266,17 @@ __device__ void grid_block(const RunDesc &R) {
   const int per = M == 2 ? span : span * span;
   const int base = FILL ? __ldcg(R.gblk + blockIdx.x) : 0;
   if (nl >= 0) {   // else the block lies outside the simplex, and so do its cells
+    // the cells' geometry first, one thread a cell (no lane repeats the
+    // trigonometry and the scans of another's cell)
+    for (int q = threadIdx.x; q < per; q += blockDim.x) {
+      const int ck[2] = {b0[0] + (M == 2 ? q : q % span), M == 2 ? 0 : b0[1] + q / span};
+      CellGeom g;
+      g.live = false;
+      if (ck[0] < G && (M == 2 || ck[1] < G))
+        g = region_geom<M, true>(R, ck, 1, R.Vt, all ? nullptr : s_list, all ? R.ntiles : nl);
+      s_geo[q] = g;
+    }
+    __syncthreads();
     for (int q = warp; q < per; q += nw) {
       int ck[2] = {b0[0] + (M == 2 ? q : q % span), M == 2 ? 0 : b0[1] + q / span};
       if (ck[0] >= G || (M == 3 && ck[1] >= G)) continue;
@@ -278,8 +297,8 @@ __device__ void grid_block(const RunDesc &R) {
           }
         }
       }
-      const int n = grid_one<M, FILL>(R, ck, all ? nullptr : s_list, all ? R.ntiles : nl, inl, at,
-                                      FILL ? nullptr : s_buf[warp]);
+      const int n = grid_one<M, FILL>(R, ck, s_geo[q], all ? nullptr : s_list, all ? R.ntiles : nl,
+                                      inl, at, FILL ? nullptr : s_buf[warp]);
       if (!FILL && n > kGridInline) {
         // an overflow list: into this block's share when the warp holds it all
         // and the share has room, else left to the fill pass
