@@ -1,7 +1,10 @@
 // Build of the direction grid of the association (grid_steps.cuh): after
 // every change of the reference vectors (initialisation, adaptation), once
-// the tile tables are current.  One warp per cell, two passes over the cells
-// (count, then fill at the scanned offsets) and a scan between them.
+// the tile tables are current.  One CTA per block of cells: the block's tile
+// list, each cell's geometry (one thread a cell), then one warp per cell for
+// its candidates.  The count pass writes every list it can hold (inline, or
+// into the block's share of the overflow area); a scan and the fill pass
+// place the few that do not fit.
 #include "grid_steps.cuh"
 
 namespace rvea {
