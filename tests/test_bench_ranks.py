@@ -65,3 +65,29 @@ def test_reference_arm_json_line_on_cpu():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "dtlz2_m3_d12_N105"
+
+
+def test_operator_workloads_bytes_and_oracle_params():
+    """The operator workloads' algorithmic bytes per generation (rows of d
+    float32 read and written per offspring, as the kernels' definitions
+    fix them) and the oracle parameters each maps to."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle as orc
+    N, d, row = 9870, 5000, 5000 * 4
+    W = bench.WORKLOADS
+    assert bench.repro_bytes(W["dtlz1_m3_d5000_N9870"]) == (2 * 4935 + N) * row
+    assert bench.repro_bytes(W["de_dtlz1_m3_d5000_N9870"]) == 5 * N * row
+    assert bench.repro_bytes(W["random_dtlz1_m3_d5000_N9870"]) == N * row
+    assert bench.repro_bytes(W["cso_dtlz1_m3_d5000_N9870"]) == 6 * N * row    # phi > 0: the centre
+    assert bench.repro_bytes(dict(W["cso_dtlz1_m3_d5000_N9870"], cso_phi=0.0)) == 5 * N * row
+    assert bench.repro_bytes(W["pso_dtlz1_m3_d5000_N9870"]) == 7 * N * row
+    for name, op in (("dtlz1_m3_d5000_N9870", orc.OP_SBX_PM), ("de_dtlz1_m3_d5000_N9870", orc.OP_DE),
+                     ("random_dtlz1_m3_d5000_N9870", orc.OP_RANDOM),
+                     ("cso_dtlz1_m3_d5000_N9870", orc.OP_CSO), ("pso_dtlz1_m3_d5000_N9870", orc.OP_PSO)):
+        p = bench.oracle_params(orc, W[name])
+        assert p.op == op and (p.N, p.d, p.m, p.H, p.problem) == (N, d, 3, 139, 1)
+    assert abs(bench.oracle_params(orc, W["cso_dtlz1_m3_d5000_N9870"]).cso_phi - 0.1) < 1e-12
+    p = bench.oracle_params(orc, W["pso_dtlz1_m3_d5000_N9870"])
+    assert (p.pso_w, p.pso_c1, p.pso_c2) == (0.7298, 1.49618, 1.49618)
+    assert set(bench.OPS) == {0, 1, 2, 3, 4}
