@@ -398,10 +398,12 @@ def main_neuro(args, rank, world, local):
               eta_c=20.0, eta_m=20.0, p_c=1.0, p_m=1.0)
     Kp = max(1, min(K, 5))
 
-    def timed(gemv, sample):
-        """K batched generations of the 100 runs with the given GEMV form:
-        (ms, per-phase ms, launches per step, clock summary)."""
-        runs = [Run(seed=rank * n_runs + q, neuro=dict(dyn, gemv=gemv), **kw) for q in range(n_runs)]
+    def timed(gemv, sample, **op):
+        """K batched generations of the 100 runs with the given GEMV form (and
+        reproduction operator): (ms, per-phase ms, launches per step, clock
+        summary)."""
+        runs = [Run(seed=rank * n_runs + q, neuro=dict(dyn, gemv=gemv), **kw, **op)
+                for q in range(n_runs)]
         for r in runs:
             autotune(r)
         batch = Batch(runs)
@@ -439,6 +441,9 @@ def main_neuro(args, rank, world, local):
     # tensor-core form (gemv = 0) is timed beside it as the comparison
     ms, phases, launches_per_step, clocks = timed(1, rank == 0)
     ms16, ph16, _, _ = timed(0, False)
+    # the same runs reproduced by CSO (the swarm the paper's neuroevolution
+    # experiment picks), phi = 0.1
+    ms_cso, ph_cso, _, _ = timed(1, False, reproduction=3, cso_phi=0.1)
     steps = dyn["steps"]
     gemm_flop = n_runs * N * steps * 2 * (64 * 17 + 64 * 64 + 6 * 64)
     eval_ms = phases[0] / Kp
@@ -496,6 +501,10 @@ def main_neuro(args, rank, world, local):
         "e2e": None,
         "gpu_launches": K * launches_per_step,
         "clocks": clocks,
+        "cso": {"value": n_runs * K / (ms_cso * 1e-3), "unit": "run-generations/s",
+                "ms_per_step": ms_cso / K, "repro_rollout_ms": ph_cso[0] / Kp,
+                "what": "the same runs reproduced by CSO (phi = 0.1: swarm centre, "
+                        "competitions, learning), the children evaluated by the FP32 rollout"},
     }
     print(json.dumps(line), flush=True)
 

@@ -69,6 +69,7 @@ __global__ void k_repro_cso_dtlz1(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz3(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_cso_dtlz4(const __grid_constant__ BatchDir dir);
+__global__ void k_repro_cso_neuro(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_pso_dtlz1(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_pso_dtlz2(const __grid_constant__ BatchDir dir);
 __global__ void k_repro_pso_dtlz3(const __grid_constant__ BatchDir dir);
@@ -636,6 +637,7 @@ void launch_repro_op(const BatchDir &d, int problem, int grid, cudaStream_t st, 
       case PROB_DTLZ1: launch_pdl(k_repro_cso_dtlz1, grid, kReproThreads, 0, st, d); break;
       case PROB_DTLZ3: launch_pdl(k_repro_cso_dtlz3, grid, kReproThreads, 0, st, d); break;
       case PROB_DTLZ4: launch_pdl(k_repro_cso_dtlz4, grid, kReproThreads, 0, st, d); break;
+      case PROB_NEURO: launch_pdl(k_repro_cso_neuro, grid, kReproThreads, 0, st, d); break;
       default: launch_pdl(k_repro_cso_dtlz2, grid, kReproThreads, 0, st, d); break;
     }
     return;
@@ -1029,7 +1031,9 @@ rvea_status validate(const rvea_config *c) {
   if (c->problem < 0 || c->problem >= kProblems) return RVEA_ERR_ARG;
   // the other reproduction operators (DTLZ problems)
   if (c->reproduction < 0 || c->reproduction > 4) return RVEA_ERR_ARG;
-  if (c->reproduction != 0 && c->problem == PROB_NEURO) return RVEA_ERR_ARG;
+  // the rollout problem: SBX with mutation or CSO (the swarm the paper's
+  // neuroevolution experiment picks), whose children the rollout evaluates
+  if (c->reproduction != 0 && c->reproduction != 3 && c->problem == PROB_NEURO) return RVEA_ERR_ARG;
   if (c->reproduction == 1 &&
       (!(c->de_F > 0) || c->de_F > 2 || !(c->de_CR >= 0) || c->de_CR > 1))
     return RVEA_ERR_ARG;

@@ -951,14 +951,15 @@ __device__ __forceinline__ void repro_cso_body(const BatchDir &dir) {
             nvel[v] = vv[v];
           }
         }
-        acc = gterms4<PROB>(u, Q, mh, d, acc);
+        if (PROB != PROB_NEURO) acc = gterms4<PROB>(u, Q, mh, d, acc);
         Y4[Q] = make_float4(u[0], u[1], u[2], u[3]);
         __stcs(VY + Q, make_float4(nvel[0], nvel[1], nvel[2], nvel[3]));
         cw = nw; cl = nl; cv = nv;
       }
       const float2 gs = team_sum2(acc, 32);
       __syncwarp();   // the row is visible to lane 0
-      if (lane == 0) {
+      // the rollout problem's children are evaluated by the rollout kernel
+      if (PROB != PROB_NEURO && lane == 0) {
         float head[kMaxM];
         const float *row = R.X + (size_t)slot * R.d_pad;
         for (int jj = 0; jj < mh; ++jj) head[jj] = __ldcg(row + jj);
@@ -982,6 +983,7 @@ RVEA_REPRO_CSO(k_repro_cso_dtlz1, PROB_DTLZ1)
 RVEA_REPRO_CSO(k_repro_cso_dtlz2, PROB_DTLZ2)
 RVEA_REPRO_CSO(k_repro_cso_dtlz3, PROB_DTLZ3)
 RVEA_REPRO_CSO(k_repro_cso_dtlz4, PROB_DTLZ4)
+RVEA_REPRO_CSO(k_repro_cso_neuro, PROB_NEURO)
 #undef RVEA_REPRO_CSO
 
 // Reproduction by particle swarm optimization (PSO; Kennedy and Eberhart

@@ -114,7 +114,9 @@ def test_cso_config_and_swarm_calls_without_gpu(native):
     cfg = native.Config(**dict(base, reproduction=5), cso_phi=0.1)
     assert L.rvea_workspace_bytes_ex(C.byref(cfg)) == 0
     h = C.c_void_p()
-    cfg = native.Config(**dict(base, problem=2), cso_phi=0.1)   # the rollout problem: SBX only
+    # the rollout problem takes SBX or CSO: DE is refused (as is any run of it
+    # without its dynamics)
+    cfg = native.Config(**dict(base, problem=2, reproduction=native.REPRO_DE), cso_phi=0.1)
     assert L.rvea_init_ex(C.byref(cfg), C.c_void_p(1 << 20), 1 << 30, None, C.byref(h)) == native.ERR_ARG
     assert L.rvea_export_swarm(None, None, None, None, None, None) == native.ERR_ARG
     a = C.c_void_p(1 << 20)
