@@ -137,7 +137,9 @@ typedef struct {
  * the offspring's personal best p is x' unless the particle's personal best
  * dominates f(x') (then that best is kept).  Velocities (zero at first),
  * personal bests (the initial positions at first), their objectives and the
- * kept APDs stay with the survivors.  DTLZ problems only. */
+ * kept APDs stay with the survivors.  DE, random reproduction and PSO serve
+ * the DTLZ problems; CSO serves them and the rollout problem (whose
+ * children the rollout evaluates). */
 typedef enum {
     RVEA_REPRO_SBX_PM = 0,
     RVEA_REPRO_DE = 1,
