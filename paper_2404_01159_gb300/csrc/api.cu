@@ -487,6 +487,7 @@ struct rvea_run {
   cudaStream_t last_stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t block_graph = nullptr;
+  cudaGraphExec_t plain_graph = nullptr;   // kPlainGens generations without an adaptation
   bool use_graph = true;
   bool has_last_gen = false;      // a generation ran since init / import
   bool recording = false;         // draws recorded by the generations now enqueued
@@ -985,6 +986,29 @@ rvea_status enqueue_one(rvea_run *r, cudaStream_t st) {
   return s;
 }
 
+// kPlainGens generations none of which adapts, captured once: rvea_step
+// replays it for stretches of generations that hold no adaptation (the
+// kernels read the generation index from the control block, so the same
+// graph serves any such stretch).
+constexpr int kPlainGens = 8;
+rvea_status ensure_plain_graph(rvea_run *r) {
+  if (r->plain_graph) return RVEA_OK;
+  if (!r->cap_stream) RV_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+  RV_TRY(cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int t_save = r->t;
+  rvea_status s = RVEA_OK;
+  r->t = 1;   // p_adapt > 1: generation 1 does not adapt
+  for (int q = 0; q < kPlainGens && s == RVEA_OK; ++q) s = enqueue_one(r, r->cap_stream);
+  r->t = t_save;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(r->cap_stream, &g);
+  if (s != RVEA_OK) { if (g) cudaGraphDestroy(g); return s; }
+  if (e != cudaSuccess) return RVEA_ERR_CUDA;
+  const cudaError_t e2 = cudaGraphInstantiate(&r->plain_graph, g, 0);
+  cudaGraphDestroy(g);
+  return cuerr(e2);
+}
+
 rvea_status ensure_block_graph(rvea_run *r) {
   if (r->block_graph) return RVEA_OK;
   if (!r->cap_stream) RV_TRY(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
@@ -1354,6 +1378,16 @@ rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
   if (!r || G < 0) return RVEA_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   r->last_stream = st;
+  if (G > 0 && r->use_graph && r->p_adapt > 1) {
+    // the graphs are captured at the first step, not in the middle of a run
+    // of generations that might be timed
+    if (r->p_adapt > kPlainGens) {
+      const rvea_status s = ensure_plain_graph(r);
+      if (s != RVEA_OK) return s;
+    }
+    const rvea_status s = ensure_block_graph(r);
+    if (s != RVEA_OK) return s;
+  }
   while (G > 0) {
     const int p = r->p_adapt;
     if (r->use_graph && p > 1 && G >= p && (r->t % p) == 1) {
@@ -1363,6 +1397,19 @@ rvea_status rvea_step(rvea_run *r, int G, void *cuda_stream) {
       RV_TRY(cudaGraphLaunch(r->block_graph, st));
       r->t += p;
       G -= p;
+      r->has_last_gen = true;
+      r->last_gen_recorded = r->recording;
+      continue;
+    }
+    // a stretch of kPlainGens generations before the next adaptation (the
+    // next multiple of p at or after t)
+    if (r->use_graph && p > 1 && G >= kPlainGens && (r->t + p - 1) / p * p >= r->t + kPlainGens) {
+      const NvtxRange nr("rvea generations (no adaptation, graph)", r->t);
+      rvea_status s = ensure_plain_graph(r);
+      if (s != RVEA_OK) return s;
+      RV_TRY(cudaGraphLaunch(r->plain_graph, st));
+      r->t += kPlainGens;
+      G -= kPlainGens;
       r->has_last_gen = true;
       r->last_gen_recorded = r->recording;
       continue;
@@ -1436,6 +1483,10 @@ rvea_status apply_plan(rvea_run *r, const rvea_plan &pl, cudaStream_t st) {
   if (r->block_graph) {   // captured with the old variants
     cudaGraphExecDestroy(r->block_graph);
     r->block_graph = nullptr;
+  }
+  if (r->plain_graph) {
+    cudaGraphExecDestroy(r->plain_graph);
+    r->plain_graph = nullptr;
   }
   // host sources of the copies above live in the run; finish them here
   RV_TRY(cudaStreamSynchronize(st));
@@ -2067,6 +2118,7 @@ rvea_status rvea_sync_status(rvea_run *r) {
 void rvea_free(rvea_run *r) {
   if (!r) return;
   if (r->block_graph) cudaGraphExecDestroy(r->block_graph);
+  if (r->plain_graph) cudaGraphExecDestroy(r->plain_graph);
   if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
   delete r;
 }

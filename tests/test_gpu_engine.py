@@ -165,6 +165,22 @@ def test_batch_of_operators_equals_alone(orc):
     b.free()
 
 
+@pytest.mark.parametrize("shape", [(3, 1001, 210, 19, 1), (3, 2500, 1275, 49, 1)])
+def test_graph_stretches_equal_single_steps(orc, shape):
+    """rvea_step replays captured stretches of non-adapting generations (and
+    whole adaptation periods) as CUDA graphs; stepping one generation at a
+    time gives the same bits, across an adaptation (t = 100)."""
+    m, d, N, H, pr = shape
+    p = params(orc, m, d, N, H, pr, t_max=1000, seed=12)
+    a, b = make_run(p), make_run(p)
+    a.step(3)
+    a.step(107)   # t = 4..110: stretches of 8, then the adaptation at 100 step by step
+    for _ in range(110):
+        b.step(1)
+    _same(a, b)
+    a.sync_status()
+
+
 def test_launch_counts(orc):
     """The launches a generation enqueues: reproduction, [mutation and
     evaluation when d > 1024], selection, finalize, [gamma and the tile table
