@@ -382,3 +382,32 @@ def test_generation_with_pso_keeps_the_swarm_state(orc):
             assert np.allclose(st.vel[j], want_v[c], atol=1e-12)
             assert np.allclose(st.pbest[j], want_p[c], atol=1e-12)
             assert np.allclose(st.fpbest[j], want_fp[c], atol=1e-12)
+
+
+def test_cso_draws_are_distinct_per_term(orc):
+    """r1, r2 and r3 of the same offspring and variable are different
+    uniforms: each is read off its term alone (one member: the velocity term;
+    two members a unit apart with zero velocity: the winner term; the centre
+    term with phi), and the three are pairwise uncorrelated."""
+    d, t, o_n = 400, 3, 8
+    # r1: one member (winner = loser), unit velocity, phi = 0 -> v' = r1
+    p1 = _p(orc, N=o_n, d=d, cso_phi=0.0, L=-10.0, U=10.0)
+    X1 = np.zeros((1, d))
+    _, V1 = orc.cso_offspring(p1, t, X1, np.ones((1, d)), np.zeros(1), np.array([0]), X1[0])
+    # r2: two members a unit apart, zero velocity -> |v'| = r2
+    p2 = _p(orc, N=o_n, d=d, cso_phi=0.0, L=-10.0, U=10.0)
+    X2 = np.stack([np.zeros(d), np.ones(d)])
+    _, V2 = orc.cso_offspring(p2, t, X2, np.zeros((2, d)), np.array([1.0, 2.0]),
+                              np.array([0, 1]), X2.mean(0))
+    # r3: one member, zero velocity, centre a unit away, phi = 1 -> v' = r3
+    p3 = _p(orc, N=o_n, d=d, cso_phi=1.0, L=-10.0, U=10.0)
+    _, V3 = orc.cso_offspring(p3, t, X1, np.zeros((1, d)), np.zeros(1), np.array([0]),
+                              np.ones(d))
+    r1, r2, r3 = V1.ravel(), np.abs(V2).ravel(), V3.ravel()
+    for r in (r1, r2, r3):
+        assert r.min() >= 0.0 and r.max() < 1.0
+        assert abs(r.mean() - 0.5) < 5 * np.sqrt(1 / 12 / r.size)
+    bound = 5 / np.sqrt(r1.size)
+    for a, b in ((r1, r2), (r1, r3), (r2, r3)):
+        assert not np.array_equal(a, b)
+        assert abs(np.corrcoef(a, b)[0, 1]) < bound
