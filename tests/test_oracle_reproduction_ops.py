@@ -411,3 +411,26 @@ def test_cso_draws_are_distinct_per_term(orc):
     for a, b in ((r1, r2), (r1, r3), (r2, r3)):
         assert not np.array_equal(a, b)
         assert abs(np.corrcoef(a, b)[0, 1]) < bound
+
+
+def test_pso_draws_are_distinct_per_term(orc):
+    """PSO's r1 (personal best) and r2 (leader) of the same offspring and
+    variable are different uniforms: each is read off its term alone, and the
+    two are uncorrelated."""
+    d, t, n = 400, 4, 8
+    # r1: w = c2 = 0, zero velocity, personal best a unit away -> v' = r1
+    p1 = _p(orc, N=n, d=d, pso_w=0.0, pso_c1=1.0, pso_c2=0.0, L=-10.0, U=10.0)
+    X = np.stack([np.ones(d), np.zeros(d)])   # member 0 (apd 1) leads, member 1 follows
+    Z = np.zeros((2, d))
+    _, V1 = orc.pso_offspring(p1, t, X, Z, X + 1.0, np.array([1.0, 2.0]), np.array([0, 1]))
+    # r2: w = c1 = 0, zero velocity; the odd offspring move member 1 towards
+    # member 0, a unit away -> v' = r2
+    p2 = _p(orc, N=n, d=d, pso_w=0.0, pso_c1=0.0, pso_c2=1.0, L=-10.0, U=10.0)
+    _, V2 = orc.pso_offspring(p2, t, X, Z, X, np.array([1.0, 2.0]), np.array([0, 1]))
+    assert not V2[0::2].any()                 # member 0 is its own leader
+    r1, r2 = V1[1::2].ravel(), V2[1::2].ravel()
+    for r in (r1, r2):
+        assert r.min() >= 0.0 and r.max() < 1.0
+        assert abs(r.mean() - 0.5) < 5 * np.sqrt(1 / 12 / r.size)
+    assert not np.array_equal(r1, r2)
+    assert abs(np.corrcoef(r1, r2)[0, 1]) < 5 / np.sqrt(r1.size)
