@@ -14,10 +14,12 @@ import numpy as np
 import torch
 
 from ._native import (DTLZ1_LINEAR, DTLZ2_SPHERE, DTLZ3_SPHERE, DTLZ4_SPHERE, NEURO_LINEAR,
-                      REPRO_PSO, Config, NeuroDynamics, Plan, ServerStats, RveaError, check, lib)
+                      REPRO_CSO, REPRO_DE, REPRO_PSO, REPRO_RANDOM, REPRO_SBX_PM, Config,
+                      NeuroDynamics, Plan, ServerStats, RveaError, check, lib)
 
 __all__ = ["Run", "step_batch", "select", "gamma", "workspace_bytes", "RveaError",
            "DTLZ2_SPHERE", "DTLZ1_LINEAR", "DTLZ3_SPHERE", "DTLZ4_SPHERE", "NEURO_LINEAR",
+           "REPRO_SBX_PM", "REPRO_DE", "REPRO_RANDOM", "REPRO_CSO", "REPRO_PSO",
            "lattice_size", "lattice_for"]
 
 
